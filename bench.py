@@ -1,0 +1,412 @@
+"""Benchmark of the balanced splat render path on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path over one synthetic frame:
+  a1 projection -> a2 binning + sort -> a3 work list -> a5 balanced forward
+  -> L2 loss gradient (torch) -> a6 balanced backward.
+Workload: 1920x1080, 1M Gaussians, 80% in one cluster covering ~5% of the image (the
+imbalanced single-view configuration), forward + backward.
+
+The metric is Gaussian-pixel pairs per second: pairs = (pixel, list entry) pairs the
+sequential rule visits (sum of n_eval over the frame), divided by the step time.  The
+JSON line also carries ms/frame, the plain pixel-wise 16x16 static-grid kernel on the
+same inputs, the roofline of the dominant render kernel and the FP64 CPU oracle timed on
+a bounded sample of the same frame.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd render ms/frame & Gaussian-pixel pairs/s vs pixel-wise kernel, 1 GB300"
+WORKLOAD = "imbalanced single view 1920x1080, 1M Gaussians (80% clustered), fwd+bwd"
+
+# Algorithmic per-pair operation counts of the sequential rule (Algorithm 5 and its
+# derivative), counted at source level as the minimum a kernel must issue:
+#  forward, every evaluated pair: dx, dy (2), power (5), o*G and min (2), two tests (2) = 11
+#          FP32-pipe ops + 1 MUFU ex2; every accumulated pair: 1-alpha, T', test, w, 5 FMA = 9;
+#  backward, every pair before the last contributor: 11 + 1 ex2 (recompute);
+#          every accumulated pair: 45 FP32-pipe ops + 1 MUFU rcp.
+FWD_EVAL_FP32, FWD_EVAL_MUFU, FWD_ACC_FP32 = 11, 1, 9
+BWD_EVAL_FP32, BWD_EVAL_MUFU, BWD_ACC_FP32, BWD_ACC_MUFU = 11, 1, 45, 1
+FP32_LANES_PER_SM_CLK = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cfg2")
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- oracle leg
+
+_ORACLE_SETUP = {}
+
+
+def oracle_setup(scene):
+    """Oracle projection + binning of the frame (done once, outside any timed region)."""
+    key = id(scene)
+    if key not in _ORACLE_SETUP:
+        import oracle
+        g, cam = scene["gaussians"], scene["cameras"][0]
+        pp = oracle.preprocess(g["means3D"], g["log_scales"], g["quats"], g["opacities"], cam)
+        m2, co, dp = (pp[k].astype(np.float32) for k in ("means2D", "conic_opacity", "depth"))
+        pl, rg = oracle.bin_tiles(m2, pp["radius"], dp, cam["W"], cam["H"])
+        _ORACLE_SETUP[key] = (m2, co, dp, pl, rg)
+    return _ORACLE_SETUP[key]
+
+
+def oracle_sample_run(scene, budget_s: float, rng_seed: int = 0):
+    """Times the FP64 oracle's render forward + backward on a bounded sample of the frame's
+    tiles (chosen uniformly at random), sized to about ``budget_s`` seconds of CPU work.
+    Returns (pairs/s, cores, description, measured pairs, seconds)."""
+    import oracle
+    g, cam = scene["gaussians"], scene["cameras"][0]
+    W, H = cam["W"], cam["H"]
+    m2, co, dp, pl, rg = oracle_setup(scene)
+    tx = (W + 15) // 16
+    T = rg.shape[0]
+    rng = np.random.default_rng(rng_seed)
+    order = rng.permutation(T)
+    cl = g["colors"]
+
+    def run(tiles):
+        pix = []
+        for t in tiles:
+            x0, y0 = (t % tx) * 16, (t // tx) * 16
+            ys, xs = np.mgrid[y0:min(y0 + 16, H), x0:min(x0 + 16, W)]
+            pix.append((ys * W + xs).ravel())
+        pix = np.concatenate(pix)
+        t0 = time.perf_counter()
+        out = oracle.render(m2, co, cl, dp, pl, rg, W, H, pixels=pix)
+        gC = np.zeros((3, H, W))
+        gC.reshape(3, -1)[:, pix] = out["color"]
+        oracle.render_backward(m2, co, cl, dp, pl, rg, W, H, gC, tiles=np.asarray(tiles, np.int64))
+        dt = time.perf_counter() - t0
+        return int(out["n_eval"].sum()), dt
+
+    n = 16
+    pairs, dt = run(order[:n])
+    while dt < budget_s / 4 and n < T:
+        n = min(T, n * 4)
+        pairs, dt = run(order[:n])
+    desc = f"{n} random 16x16 tiles of {T} ({100.0 * n / T:.1f}% of the frame), render fwd+bwd"
+    return pairs / dt, oracle.num_threads(), desc, pairs, dt
+
+
+def reference_arm(args):
+    rank, world, _ = dist_init(args)
+    if rank != 0:
+        return
+    from paper_2412_17378_gb300 import scenes
+    scene = scenes.scene_config(args.config, args.scale)
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample_run(scene, per_step / 4)
+    t_all, p_all = 0.0, 0
+    rate = cores = desc = None
+    for k in range(args.steps):
+        rate, cores, desc, pairs, dt = oracle_sample_run(scene, per_step, rng_seed=k)
+        t_all += dt
+        p_all += pairs
+    value = p_all / t_all
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded; stands in for the paper's internal dataset)",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    rank, world, local = dist_init(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2412_17378_gb300 import raster, scenes
+
+    scene = scenes.scene_config(args.config, args.scale)
+    g, cam = scene["gaussians"], scene["cameras"][0]
+    W, H = cam["W"], cam["H"]
+    dev = torch.device("cuda", local)
+    host = {k: torch.from_numpy(v).pin_memory() for k, v in g.items()}
+    target_h = torch.from_numpy(scenes.target_image(2, W, H)).pin_memory()
+    d = {k: v.to(dev) for k, v in host.items()}
+    target = target_h.to(dev)
+    N = d["means3D"].shape[0]
+    plan = raster.Plan(device=local)
+    tile = (16, 16)
+    pl_buf = [None]
+
+    def step(mode="auto", gin=d, tgt=target):
+        pre = raster.preprocess(plan, gin["means3D"], gin["log_scales"], gin["quats"], gin["opacities"], cam, tile)
+        pl, rg, K = raster.bin_and_sort(plan, pre["means2D"], pre["radii"], pre["depths"], W, H, tile, pl_buf[0])
+        pl_buf[0] = pl
+        fw = raster.render_forward(plan, pre["means2D"], pre["conic_opacity"], gin["colors"], pre["depths"], pl, K, rg,
+                                   W, H, tile, (0.0, 0.0, 0.0), mode)
+        dL = torch.sub(fw["color"], tgt)
+        gr = raster.render_backward(plan, pre["means2D"], pre["conic_opacity"], gin["colors"], pre["depths"], pl, K,
+                                    rg, W, H, fw["final_T"], fw["n_contrib"], dL, None, None, tile, (0.0, 0.0, 0.0),
+                                    mode)
+        return pre, (pl, rg, K), fw, gr, dL
+
+    # ---- frame statistics (evaluated / contributing pairs, backward pairs) ----
+    plan.reset_stats()
+    pre, binning, fw, _, _ = step("auto")
+    st = plan.stats()
+    eval_pairs, contrib_pairs = st["eval_pairs"], st["contrib_pairs"]
+    bwd_pairs = int(fw["n_contrib"].sum().item())
+    K = binning[2]
+    rgh = binning[1].cpu().numpy()
+    lens = rgh[:, 1] - rgh[:, 0]
+
+    # ---- autotune: heavy-tile threshold and pixels per Gaussian-wise item ----
+    tuned = {}
+    if not args.no_tune:
+        best = None
+        for thr in (256, 1024, 4096, 1 << 30):
+            for P in (2, 4):
+                if thr == (1 << 30) and P != 4:
+                    continue
+                plan.set(heavy_threshold=thr, gw_pixels=P)
+                plan.timing(True)
+                for _ in range(2):
+                    step("auto")
+                torch.cuda.synchronize()
+                plan.kernel_ms()
+                for _ in range(2):
+                    step("auto")
+                f_ms, nf, b_ms, nb = plan.kernel_ms()
+                plan.timing(False)
+                t = f_ms / max(nf, 1) + b_ms / max(nb, 1)
+                if best is None or t < best[0]:
+                    best = (t, thr, P)
+        plan.set(heavy_threshold=best[1], gw_pixels=best[2])
+        tuned = {"heavy_threshold": best[1], "gw_pixels": best[2], "render_ms": round(best[0], 4)}
+
+    # ---- warmup + timed region ----
+    for _ in range(args.warmup):
+        step("auto")
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    plan.reset_stats()
+    launches0 = plan.stats()["host_launches"]
+    plan.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        step("auto")
+    e1.record()
+    torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    f_ms, nf, b_ms, nb = plan.kernel_ms()
+    plan.timing(False)
+    clk = clocks.stop()
+    st_t = plan.stats()
+    launches = st_t["host_launches"] - launches0
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    fwd_ms, bwd_ms = f_ms / max(nf, 1), b_ms / max(nb, 1)
+    value = eval_pairs * world / (ms_step / 1e3)
+
+    # ---- plain pixel-wise 16x16 static grid on the same inputs (render kernels only) ----
+    plan.timing(True)
+    for _ in range(2):
+        step("static")
+    torch.cuda.synchronize()
+    plan.kernel_ms()
+    for _ in range(max(3, args.steps // 2)):
+        step("static")
+    sf_ms, snf, sb_ms, snb = plan.kernel_ms()
+    plan.timing(False)
+    static_fwd, static_bwd = sf_ms / max(snf, 1), sb_ms / max(snb, 1)
+
+    # ---- end to end through the public API with host buffers ----
+    # every step copies its inputs from pinned host memory and reads the loss back
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + target_h.numel() * target_h.element_size()
+    dbuf = {k: torch.empty_like(v) for k, v in d.items()}
+    tbuf = torch.empty_like(target)
+    loss_h = torch.empty(1, pin_memory=True)
+    for _ in range(2):
+        for k in host:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        tbuf.copy_(target_h, non_blocking=True)
+        _, _, _, _, dL = step("auto", dbuf, tbuf)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for k in host:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        tbuf.copy_(target_h, non_blocking=True)
+        _, _, _, _, dL = step("auto", dbuf, tbuf)
+        loss_h.copy_((0.5 * (dL * dL).sum()).reshape(1), non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_value = eval_pairs * world / e2e_s
+
+    # ---- roofline of the dominant render kernel ----
+    sms = plan.num_sms
+    fp32_rate, ex2_rate = raster.probe_pipe_rates(plan)
+    peaks, peak_src = load_peaks()
+    clk_peak = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+
+    def t_min(fp32_ops, mufu_ops, clk):
+        return max(fp32_ops / (sms * FP32_LANES_PER_SM_CLK * clk), mufu_ops / (sms * ex2_rate * clk))
+
+    fwd_ops = (FWD_EVAL_FP32 * eval_pairs + FWD_ACC_FP32 * contrib_pairs, FWD_EVAL_MUFU * eval_pairs)
+    bwd_ops = (BWD_EVAL_FP32 * bwd_pairs + BWD_ACC_FP32 * contrib_pairs,
+               BWD_EVAL_MUFU * bwd_pairs + BWD_ACC_MUFU * contrib_pairs)
+    dom = "forward" if fwd_ms >= bwd_ms else "backward"
+    ops, dur = (fwd_ops, fwd_ms) if dom == "forward" else (bwd_ops, bwd_ms)
+    tmin = t_min(*ops, clk_peak)
+    achieved = eval_pairs / (dur / 1e3)
+    peak = eval_pairs / tmin
+    clk_meas = (clk.get("sm_mhz") or 0) * 1e6
+    roof = {"bound": "alu", "kernel": f"k_{dom}_balanced", "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
+            "model": "max(FP32-pipe ops / (SMs*128*clk), MUFU ops / (SMs*ex2_rate*clk)) at the max SM clock",
+            "peak_source": f"derived from unit counts; SM clock {clk_peak/1e6:.0f} MHz ({peak_src}); "
+                           f"probed ex2 {ex2_rate:.1f}/SM/clk, fp32 {fp32_rate:.1f}/SM/clk",
+            "frac_at_measured_clock": (achieved / (eval_pairs / t_min(*ops, clk_meas))) if clk_meas else None}
+
+    # ---- FP64 CPU oracle on a bounded sample (rank 0, one GPU only) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, desc, _, _ = oracle_sample_run(scene, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; stands in for the paper's internal dataset)",
+        "config": {"workload": WORKLOAD, "gaussians": N, "width": W, "height": H, "tile": "16x16",
+                   "l2": "working set per step > L2 (sort buffers of K entries), no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU", "tuned": tuned},
+        "ms_per_frame": ms_step,
+        "render_ms_per_frame": {"forward": fwd_ms, "backward": bwd_ms, "total": fwd_ms + bwd_ms},
+        "pixelwise_static": {"forward_ms": static_fwd, "backward_ms": static_bwd,
+                             "total_ms": static_fwd + static_bwd,
+                             "pairs_per_s_render": eval_pairs / ((static_fwd + static_bwd) / 1e3),
+                             "speedup_render": (static_fwd + static_bwd) / (fwd_ms + bwd_ms)},
+        "frame": {"eval_pairs": eval_pairs, "contrib_pairs": contrib_pairs, "bwd_pairs": bwd_pairs,
+                  "entries": K, "tile_list_max": int(lens.max()), "tile_list_mean": float(lens.mean()),
+                  "tile_list_p99": float(np.percentile(lens, 99))},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches),
+        "gpu_launches_per_step": int(launches) // args.steps,
+        "gpu_launches_note": "libbgs kernels launched in the timed region, not counting CUB sort/scan kernels",
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

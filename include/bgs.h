@@ -1,0 +1,201 @@
+/*
+ * bgs.h -- C ABI of the balanced Gaussian-splat renderer (libbgs.so, sm_103a).
+ *
+ * The library implements the data-parallel hot path of Balanced 3DGS (Gui et al.,
+ * arXiv 2412.17378): the tile-based front-to-back alpha-compositing render kernel of
+ * 3D Gaussian Splatting ("renderCUDA"), its backward pass, and the projection and
+ * binning steps that produce its inputs.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every array argument is a DEVICE pointer to caller-owned, contiguous memory
+ *    (float32 / int32 / uint32 as typed), unless the comment says "host".  The library
+ *    never frees caller memory and never keeps a caller pointer after the call returns.
+ *  - `stream` is a cudaStream_t passed as void*; every call only enqueues work on it
+ *    (except where a comment says the call synchronises).  NULL = legacy default stream.
+ *  - Scratch memory (sort buffers, work lists, queue counters, gradient accumulators)
+ *    belongs to the plan.  It is allocated with cudaMalloc on first need and grown on
+ *    later calls; bgs_plan_reserve() sizes it up front.  Nothing is allocated while the
+ *    stream is being captured into a CUDA graph: a call that would need to grow the
+ *    workspace then fails with BGS_ERR_CAPACITY.
+ *  - A plan may be used by one host thread and one stream at a time.
+ *  - Return value: BGS_OK or a negative status.  bgs_last_error() gives a message
+ *    (thread-local).  Outputs are unspecified after a failed call.
+ *  - Image outputs are planar: color is [3, H, W], the others [H, W].
+ *  - Pixel (x, y) is evaluated at coordinates (x, y) of the means2D frame.
+ *
+ * Per-pair rule (Eq. 3-4 and Algorithm 5, Appendix A of the paper; constants from
+ * standard 3DGS since the paper omits them): for the depth-sorted Gaussians of the
+ * pixel's tile, power = -1/2 (a dx^2 + c dy^2) - b dx dy with d = mean - pixel; skip if
+ * power > 0; alpha = min(0.99, o exp(power)); skip if alpha < 1/255; T' = T (1 - alpha);
+ * stop before accumulating if T' < 1e-4; else C += c alpha T, D += depth alpha T,
+ * A += alpha T, T = T'.  Finally C += T bg.
+ */
+#ifndef BGS_H
+#define BGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define BGS_OK 0
+#define BGS_ERR_INVALID (-1)      /* bad argument (null pointer, size, tile shape, mode)   */
+#define BGS_ERR_CAPACITY (-2)     /* caller buffer or plan workspace too small; see needed */
+#define BGS_ERR_CUDA (-3)         /* a CUDA runtime call failed                             */
+#define BGS_ERR_DEVICE_CHECK (-4) /* a device-side check tripped (reported by bgs_check)    */
+
+/* ---- device-check bits (bgs_check / bgs_plan_stats) -------------------------------- */
+#define BGS_CHECK_INDEX 1u        /* point_list held an index >= N                         */
+#define BGS_CHECK_RANGE 2u        /* a tile range pointed past num_entries                 */
+#define BGS_CHECK_OVERFLOW 4u     /* binning produced more entries than the capacity        */
+#define BGS_CHECK_QUEUE 8u        /* the work queue did not drain exactly once              */
+
+/* ---- render modes (Sec. 4 of the paper and its selector, Sec. 4.4) ------------------ */
+#define BGS_MODE_AUTO 0     /* persistent queue; per-tile choice: Gaussian-wise for tiles whose
+                               list is longer than plan.heavy_threshold, else pixel-wise        */
+#define BGS_MODE_PIXEL 1    /* persistent queue (Sec. 4.1), every item pixel-wise               */
+#define BGS_MODE_GAUSSIAN 2 /* persistent queue, every item Gaussian-wise (Sec. 4.2-4.3)        */
+#define BGS_MODE_STATIC 3   /* plain pixel-wise static grid, one block per tile (Algorithm 4)  */
+
+/* ---- camera (Eq. 2: W = viewmat rotation, J = Jacobian of the pinhole map) ---------- */
+typedef struct bgs_camera {
+    int32_t width, height;   /* image size in pixels                                      */
+    float fx, fy, cx, cy;    /* pinhole intrinsics: u = fx x/z + cx, v = fy y/z + cy       */
+    float viewmat[16];       /* row-major 4x4 world->camera transform (camera looks at +z) */
+    float near_plane;        /* Gaussians with camera z <= near_plane are culled (0.2)     */
+    float lowpass;           /* added to the diagonal of the 2D covariance (0.3)           */
+} bgs_camera;
+
+/* ---- plan: tuning knobs + owned workspace ----------------------------------------- */
+typedef struct bgs_plan_desc {
+    int32_t heavy_threshold; /* AUTO mode: list length above which a tile is Gaussian-wise  */
+    int32_t gw_pixels;       /* pixels one Gaussian-wise warp item covers: 1, 2, 4 or 8     */
+    int32_t queue_chunk;     /* work items a warp claims per atomicAdd on the queue (>= 1)  */
+    int32_t blocks_per_sm;   /* persistent grid = SMs x blocks_per_sm; 0 = max resident     */
+    int32_t lpt_order;       /* 1: work items ordered heaviest tile first; 0: tile order    */
+    int32_t device;          /* CUDA device ordinal; -1 = the current device at creation    */
+} bgs_plan_desc;
+
+typedef struct bgs_plan bgs_plan;
+
+/* Counters accumulated by the render kernels since the last bgs_plan_reset_stats(). */
+typedef struct bgs_stats {
+    uint64_t eval_pairs;     /* (pixel, list entry) pairs the sequential rule visits       */
+    uint64_t contrib_pairs;  /* pairs accumulated into a pixel                              */
+    uint64_t items;          /* work items executed by the persistent kernels               */
+    uint32_t check_bits;     /* BGS_CHECK_* bits raised by device checks                    */
+    uint32_t last_num_items; /* work items in the last work list                            */
+    uint64_t host_launches;  /* kernels of this library launched through the plan so far,
+                                not counting the sort / scan kernels of the CUB library     */
+} bgs_stats;
+
+/* Fills *desc with defaults (threshold 512, 4 px per Gaussian-wise item, chunk 1,
+   max resident blocks, LPT order on, current device). */
+void bgs_plan_desc_default(bgs_plan_desc *desc);
+/* Creates a plan bound to desc->device.  Allocates a small device control block. */
+int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out);
+int bgs_plan_destroy(bgs_plan *plan);
+/* Replaces the tuning knobs (device unchanged). */
+int bgs_plan_set(bgs_plan *plan, const bgs_plan_desc *desc);
+int bgs_plan_get(const bgs_plan *plan, bgs_plan_desc *desc);
+/* Grows the workspace for up to max_gaussians Gaussians, max_entries duplicated
+   (Gaussian, tile) entries, max_tiles tiles and max_pixels pixels (all views together). */
+int bgs_plan_reserve(bgs_plan *plan, int64_t max_gaussians, int64_t max_entries, int64_t max_tiles,
+                     int64_t max_pixels);
+/* Workspace bytes bgs_plan_reserve would hold for these sizes. */
+size_t bgs_workspace_size(const bgs_plan *plan, int64_t max_gaussians, int64_t max_entries,
+                          int64_t max_tiles, int64_t max_pixels);
+/* Synchronises `stream`; returns BGS_ERR_DEVICE_CHECK (and clears the bits) if a device
+   check tripped since the last call, else BGS_OK. */
+int bgs_check(bgs_plan *plan, void *stream);
+/* Synchronises `stream` and copies the counters (host pointer). */
+int bgs_plan_stats(bgs_plan *plan, bgs_stats *out, void *stream);
+int bgs_plan_reset_stats(bgs_plan *plan, void *stream);
+/* Turns CUDA-event timing of the render kernels on (1) or off (0).  While on, every
+   forward / backward render-kernel launch outside stream capture is bracketed by two
+   events on the launching stream. */
+int bgs_plan_timing(bgs_plan *plan, int enable);
+/* Sums the recorded forward / backward kernel durations (ms) and their launch counts,
+   then forgets them (waits for the recorded events). */
+int bgs_plan_kernel_ms(bgs_plan *plan, double *fwd_ms, int32_t *fwd_n, double *bwd_ms, int32_t *bwd_n);
+/* Number of SMs of the plan's device (host). */
+int bgs_plan_num_sms(const bgs_plan *plan);
+const char *bgs_last_error(void);
+
+/* ---- a1: projection (Eq. 1-3) ------------------------------------------------------
+   Per Gaussian i: camera-space p = V [mean, 1]; culled if p.z <= near_plane.
+   Sigma = R S S^T R^T with R from the normalised quaternion (w, x, y, z) and
+   S = diag(exp(log_scale)); Sigma' = J W Sigma W^T J^T + lowpass I with J the
+   Jacobian of the pinhole map at the tangent-clamped point (|x/z| <= 1.3 W/(2 fx)).
+   Outputs: means2D [N,2] = (fx x/z + cx, fy y/z + cy); conic_opacity [N,4] =
+   (a, b, c, o) with (a b; b c) = Sigma'^-1 and o = opacities[i]; depths [N] = p.z;
+   radii [N] = ceil(3 sqrt(lambda_max)) with the eigenvalue discriminant floored at 0.1
+   (0 when culled or when the Gaussian touches no tile); tiles_touched [N] = area of the
+   tile rectangle (see bgs_bin_and_sort).  Inputs: means3D [N,3], log_scales [N,3],
+   quats [N,4], opacities [N] (already in (0,1)).  cam is a host pointer. */
+int bgs_preprocess(bgs_plan *plan, int64_t N, const float *means3D, const float *log_scales,
+                   const float *quats, const float *opacities, const bgs_camera *cam, int32_t tile_w,
+                   int32_t tile_h, float *means2D, float *conic_opacity, float *depths, int32_t *radii,
+                   uint32_t *tiles_touched, void *stream);
+
+/* ---- a2: binning with key duplication (point_list of Algorithms 1-6) ---------------
+   Gaussian i with radius r > 0 covers the tiles x in [floor((u-r)/tw),
+   floor((u+(r+tw-1))/tw)), y likewise, clamped to the tile grid (float32, one rounding
+   per operation).  For every covered tile one entry (key = tile << 32 | float bits of
+   depth, value = i) is emitted; entries are radix-sorted by key, stably, so ties in
+   depth keep ascending i.  point_list [capacity] receives the sorted values and
+   ranges [T,2] (T = tiles_x * tiles_y) the half-open span of each tile (0,0 if empty).
+   If the entry count K exceeds `capacity`, nothing is written to point_list, *needed
+   (host, nullable) receives K and BGS_ERR_CAPACITY is returned.  *num_rendered (host,
+   nullable) receives K.  This call synchronises the stream once to read K. */
+int bgs_bin_and_sort(bgs_plan *plan, int64_t N, const float *means2D, const int32_t *radii,
+                     const float *depths, int32_t W, int32_t H, int32_t tile_w, int32_t tile_h,
+                     uint32_t *point_list, int64_t capacity, uint32_t *ranges, int64_t *num_rendered,
+                     int64_t *needed, void *stream);
+
+/* ---- a3-a5: render forward -------------------------------------------------------
+   Inputs (the paper's XY, CO, F, D, PL): means2D [N,2], conic_opacity [N,4],
+   colors [N,3], depths [N], point_list [num_entries] (values < N), ranges [T,2].
+   bg: host float[3].  Outputs (OC, OD, OA): out_color [3,H,W], out_depth [H,W],
+   out_alpha [H,W] (= sum of weights = 1 - final_T), final_T [H,W], n_contrib [H,W]
+   (list position + 1 of the last accumulated pair, 0 if none), n_eval [H,W] (nullable:
+   pairs the sequential rule visits).  mode: BGS_MODE_*.  All modes give the same result
+   up to float32 reassociation. */
+int bgs_render_forward(bgs_plan *plan, int64_t N, const float *means2D, const float *conic_opacity,
+                       const float *colors, const float *depths, const uint32_t *point_list,
+                       int64_t num_entries, const uint32_t *ranges, int32_t W, int32_t H, int32_t tile_w,
+                       int32_t tile_h, const float *bg, int32_t mode, float *out_color, float *out_depth,
+                       float *out_alpha, float *final_T, int32_t *n_contrib, int32_t *n_eval, void *stream);
+
+/* ---- a6: render backward ----------------------------------------------------------
+   Gradient of L through the forward above, recomputing the blend back to front from
+   final_T and n_contrib (no per-pair state is stored).  Inputs: the forward's inputs,
+   its final_T / n_contrib, dL_dcolor [3,H,W], dL_ddepth [H,W] (nullable),
+   dL_dalpha [H,W] (nullable).  Outputs (overwritten): dL_dmeans2D [N,2],
+   dL_dconic [N,3] (w.r.t. a, b, c exactly as used in power), dL_dopacity [N],
+   dL_dcolors [N,3], dL_ddepths [N] (nullable).  Where o exp(power) > 0.99 the alpha
+   clamp is active and the pair passes no gradient to o or to the Gaussian's shape. */
+int bgs_render_backward(bgs_plan *plan, int64_t N, const float *means2D, const float *conic_opacity,
+                        const float *colors, const float *depths, const uint32_t *point_list,
+                        int64_t num_entries, const uint32_t *ranges, int32_t W, int32_t H, int32_t tile_w,
+                        int32_t tile_h, const float *bg, int32_t mode, const float *final_T,
+                        const int32_t *n_contrib, const float *dL_dcolor, const float *dL_ddepth,
+                        const float *dL_dalpha, float *dL_dmeans2D, float *dL_dconic, float *dL_dopacity,
+                        float *dL_dcolors, float *dL_ddepths, void *stream);
+
+/* ---- diagnostics -------------------------------------------------------------------
+   Measures sustained per-SM issue rates of the FP32 pipe (FFMA) and of the MUFU ex2
+   unit with dependent-chain-free loops on every SM; writes operations per SM per clock
+   cycle (host) using the SM clock counter.  Synchronises. */
+int bgs_probe_pipe_rates(bgs_plan *plan, double *fp32_per_sm_clk, double *ex2_per_sm_clk, void *stream);
+/* y[i] = 2^x[i] with the exponential the render kernels use (ex2.approx.ftz). */
+int bgs_debug_exp2(const float *x, float *y, int64_t n, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BGS_H */

@@ -1,0 +1,157 @@
+// bgs_internal.cuh -- shared declarations of the CUDA library (device helpers, the
+// plan's control block, per-pair blend rule, kernel launchers).  Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bgs.h"
+
+namespace bgs {
+
+// ---- constants of the per-pair rule (Algorithm 5 with standard 3DGS constants) -------
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kLog2e = 1.4426950408889634f;  // log2(e): exp(x) = 2^(x log2 e)
+constexpr float kLn2 = 0.6931471805599453f;    // ln(2)
+
+// ---- device control block (one per plan) --------------------------------------------
+struct DevCtrl {
+    unsigned int queue_head;    // persistent-kernel work queue cursor
+    unsigned int num_items;     // work items in the current list
+    unsigned int check_bits;    // BGS_CHECK_* raised by device checks
+    unsigned int pad0;
+    unsigned long long num_entries;  // K written by binning
+    unsigned long long eval_pairs;
+    unsigned long long contrib_pairs;
+    unsigned long long items_done;
+};
+
+// ---- packed per-Gaussian record used by the render kernels (48 bytes) ---------------
+//   a = (mx, my, qa, qb), b = (qc, o, depth, 0), c = (r, g, b, 0)
+//   with (qa, qb, qc) = -log2(e) (a/2, b, c/2), so that the natural-log power of the
+//   pair is ln2 * (qa dx^2 + qb dx dy + qc dy^2) and exp(power) = 2^(qa dx^2 + ...).
+struct __align__(16) Rec {
+    float4 a, b, c;
+};
+
+// One work item of the persistent kernels.
+//   x = tile id (global over views), y = kind << 31 | sub-item index inside the tile.
+constexpr unsigned int kKindGauss = 1u << 31;
+
+// ---- small device helpers ------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void raise_check(DevCtrl *ctrl, unsigned int bit) {
+    atomicOr(&ctrl->check_bits, bit);
+}
+
+// Packs one Gaussian's render inputs into a Rec (the conic is pre-scaled by -log2(e)/2).
+__device__ __forceinline__ Rec make_rec(const float *__restrict__ means2D, const float *__restrict__ conic_opacity,
+                                        const float *__restrict__ colors, const float *__restrict__ depths,
+                                        unsigned int g) {
+    Rec r;
+    const float2 m = reinterpret_cast<const float2 *>(means2D)[g];
+    const float4 co = reinterpret_cast<const float4 *>(conic_opacity)[g];
+    r.a = make_float4(m.x, m.y, -0.5f * kLog2e * co.x, -kLog2e * co.y);
+    r.b = make_float4(-0.5f * kLog2e * co.z, co.w, depths[g], 0.f);
+    r.c = make_float4(colors[3 * g], colors[3 * g + 1], colors[3 * g + 2], 0.f);
+    return r;
+}
+
+// power2 = log2(e) * power of the pair (pixel px, py) -- identical code in every kernel,
+// forward and backward, so that skip / stop decisions agree bit for bit.
+__device__ __forceinline__ float pair_power2(float4 a, float qc, float px, float py, float &dx, float &dy) {
+    dx = a.x - px;
+    dy = a.y - py;
+    return (a.z * dx + a.w * dy) * dx + qc * dy * dy;
+}
+
+__device__ __forceinline__ float pair_alpha(float power2, float o, float &G) {
+    G = ex2_approx(power2);
+    return fminf(kAlphaMax, o * G);
+}
+
+// ---- launch parameter blocks -----------------------------------------------------------
+struct FwdArgs {
+    const Rec *recs;             // packed records [N]
+    const float *means2D, *conic_opacity, *colors, *depths;  // ABI arrays (static kernel)
+    const uint32_t *point_list;
+    const uint2 *ranges;
+    long long N;
+    long long num_entries;
+    int W, H, tile_w, tile_h, tiles_x, tiles_y;
+    float bg[3];
+    float *out_color, *out_depth, *out_alpha, *final_T;
+    int *n_contrib, *n_eval;
+    DevCtrl *ctrl;
+    const uint2 *items;          // work list (persistent kernels)
+    int gw_pixels;
+    int chunk;
+};
+
+struct BwdArgs {
+    const Rec *recs;
+    const float *means2D, *conic_opacity, *colors, *depths;
+    const uint32_t *point_list;
+    const uint2 *ranges;
+    long long N;
+    long long num_entries;
+    int W, H, tile_w, tile_h, tiles_x, tiles_y;
+    float bg[3];
+    const float *final_T;
+    const int *n_contrib;
+    const float *dL_dcolor, *dL_ddepth, *dL_dalpha;
+    float4 *grad_acc;            // [N][3] float4 accumulators (10 used of 12)
+    DevCtrl *ctrl;
+    const uint2 *items;
+    int chunk;
+};
+
+// ---- launchers (each returns cudaGetLastError() of its launch) ------------------------
+cudaError_t launch_preprocess(long long N, const float *means3D, const float *log_scales, const float *quats,
+                              const float *opacities, const bgs_camera &cam, int tile_w, int tile_h,
+                              float *means2D, float *conic_opacity, float *depths, int *radii,
+                              uint32_t *tiles_touched, cudaStream_t s);
+
+cudaError_t launch_touched(long long N, const float *means2D, const int *radii, int W, int H, int tile_w,
+                           int tile_h, uint32_t *touched, cudaStream_t s);
+cudaError_t launch_duplicate(long long N, const float *means2D, const int *radii, const float *depths,
+                             const unsigned long long *offsets, int W, int H, int tile_w, int tile_h,
+                             unsigned long long *keys, uint32_t *vals, long long capacity, cudaStream_t s);
+cudaError_t launch_count_total(long long N, const uint32_t *touched, const unsigned long long *offsets,
+                               DevCtrl *ctrl, cudaStream_t s);
+cudaError_t launch_ranges(const unsigned long long *keys, long long K, uint2 *ranges, cudaStream_t s);
+
+cudaError_t launch_pack(long long N, const float *means2D, const float *conic_opacity, const float *colors,
+                        const float *depths, Rec *recs, cudaStream_t s);
+
+// work list: per-tile keys/counts, then emission in (optionally sorted) tile order
+cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int W, int H, int tile_w, int tile_h,
+                               int tiles_x, int mode, int heavy_threshold, int gw_pixels, uint32_t *tile_key,
+                               uint32_t *tile_idx, cudaStream_t s);
+cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, int W, int H,
+                                 int tile_w, int tile_h, int tiles_x, int mode, int heavy_threshold,
+                                 int gw_pixels, uint32_t *counts, cudaStream_t s);
+cudaError_t launch_emit_items(const uint32_t *order, const uint32_t *counts, const uint32_t *offsets,
+                              int num_tiles, const uint2 *ranges, int mode, int heavy_threshold, uint2 *items,
+                              DevCtrl *ctrl, cudaStream_t s);
+
+cudaError_t launch_forward_static(const FwdArgs &a, cudaStream_t s);
+cudaError_t launch_forward_balanced(const FwdArgs &a, int grid, cudaStream_t s);
+int forward_balanced_block_threads();
+const void *forward_balanced_kernel(int gw_pixels);
+
+cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s);
+cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s);
+int backward_balanced_block_threads();
+const void *backward_balanced_kernel();
+cudaError_t launch_grad_finalize(long long N, const float4 *acc, float *dL_dmeans2D, float *dL_dconic,
+                                 float *dL_dopacity, float *dL_dcolors, float *dL_ddepths, cudaStream_t s);
+
+}  // namespace bgs

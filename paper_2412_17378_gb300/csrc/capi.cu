@@ -1,0 +1,662 @@
+// capi.cu -- the C ABI (include/bgs.h): plan, workspace, argument checks and the
+// host-side sequencing of the kernels of each entry point.
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "bgs_internal.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(BGS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define BGS_CUDA(call, what)                         \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+int bits_for(long long v) {
+    int b = 1;
+    while ((1ll << b) <= v) ++b;
+    return b;
+}
+
+}  // namespace
+
+struct bgs_plan {
+    bgs_plan_desc desc;
+    int device = 0;
+    int num_sms = 0;
+    bgs::DevCtrl *ctrl = nullptr;
+    // optional CUDA-event timing of the two render kernels (forward, backward)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_fwd, ev_bwd;
+    unsigned long long host_launches = 0;
+    // binning
+    Buf touched, offsets, keys_in, keys_out, vals_in, cub_tmp;
+    // render
+    Buf recs, tile_key, tile_key2, tile_idx, tile_idx2, counts, item_off, items, grad_acc;
+};
+
+namespace {
+
+int ensure(bgs_plan *p, Buf &b, size_t bytes, cudaStream_t s, const char *what) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return BGS_OK;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone)
+        return fail(BGS_ERR_CAPACITY, "workspace '%s' needs %zu bytes while the stream is being captured; "
+                                      "call bgs_plan_reserve before capture", what, bytes);
+    (void)p;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree(workspace)");
+    }
+    const size_t grown = bytes + bytes / 8 + 256;
+    cudaError_t e = cudaMalloc(&b.p, grown);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return fail(BGS_ERR_CUDA, "cudaMalloc(%zu) for workspace '%s': %s", grown, what, cudaGetErrorString(e));
+    }
+    b.bytes = grown;
+    return BGS_OK;
+}
+
+cudaEvent_t take_event(bgs_plan *p) {
+    if (!p->ev_pool.empty()) {
+        cudaEvent_t e = p->ev_pool.back();
+        p->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone;
+}
+
+// Records an event pair around one render-kernel launch when timing is on.
+struct KernelTimer {
+    bgs_plan *p;
+    cudaStream_t s;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *dst;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KernelTimer(bgs_plan *p_, cudaStream_t s_, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *d)
+        : p(p_), s(s_), dst(d) {
+        if (p->timing && !capturing(s)) {
+            a = take_event(p);
+            b = take_event(p);
+            if (a && b) cudaEventRecord(a, s);
+        }
+    }
+    void stop() {
+        if (a && b) {
+            cudaEventRecord(b, s);
+            dst->emplace_back(a, b);
+            a = b = nullptr;
+        }
+    }
+};
+
+#define BGS_TRY(x)                 \
+    do {                           \
+        int r_ = (x);              \
+        if (r_ != BGS_OK) return r_; \
+    } while (0)
+
+int check_tile(int tw, int th, bool balanced) {
+    if (tw <= 0 || th <= 0 || tw * th > 1024 || (tw * th) % 32 != 0)
+        return fail(BGS_ERR_INVALID, "tile %dx%d: need 32 <= tile_w*tile_h <= 1024, a multiple of 32", tw, th);
+    if (balanced && (tw % 8 != 0 || th % 4 != 0))
+        return fail(BGS_ERR_INVALID, "tile %dx%d: the persistent kernels need tile_w %% 8 == 0 and tile_h %% 4 == 0",
+                    tw, th);
+    return BGS_OK;
+}
+
+int check_image(int W, int H) {
+    if (W <= 0 || H <= 0 || (long long)W * H > (1ll << 31) - 1)
+        return fail(BGS_ERR_INVALID, "image %dx%d: need 0 < W*H < 2^31", W, H);
+    return BGS_OK;
+}
+
+int grid_for(const bgs_plan *p, const void *kernel, int threads) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    if (p->desc.blocks_per_sm > 0) per_sm = std::min(per_sm, (int)p->desc.blocks_per_sm);
+    return p->num_sms * per_sm;
+}
+
+// Builds the work list of the persistent kernels for one image (a3).
+int build_worklist(bgs_plan *p, const uint32_t *ranges, int W, int H, int tw, int th, int mode, cudaStream_t s) {
+    const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
+    const int T = tiles_x * tiles_y;
+    const int P = p->desc.gw_pixels;
+    const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+    const long long per_tile = std::max<long long>(((tw + 7) / 8) * ((th + 3) / 4), (tw * th + P - 1) / P);
+    const long long max_items = (long long)T * per_tile;
+    if (max_items >= (1ll << 31)) return fail(BGS_ERR_INVALID, "too many work items (%lld)", max_items);
+    BGS_TRY(ensure(p, p->tile_key, sizeof(uint32_t) * T, s, "tile_key"));
+    BGS_TRY(ensure(p, p->tile_idx, sizeof(uint32_t) * T, s, "tile_idx"));
+    BGS_TRY(ensure(p, p->counts, sizeof(uint32_t) * T, s, "counts"));
+    BGS_TRY(ensure(p, p->item_off, sizeof(uint32_t) * T, s, "item_off"));
+    BGS_TRY(ensure(p, p->items, sizeof(uint2) * max_items, s, "items"));
+    uint32_t *key = (uint32_t *)p->tile_key.p, *idx = (uint32_t *)p->tile_idx.p;
+    BGS_CUDA(bgs::launch_tile_counts(rg, T, W, H, tw, th, tiles_x, mode, p->desc.heavy_threshold, P, key, idx, s),
+             "tile_counts");
+    const uint32_t *order = idx;
+    if (p->desc.lpt_order) {
+        BGS_TRY(ensure(p, p->tile_key2, sizeof(uint32_t) * T, s, "tile_key2"));
+        BGS_TRY(ensure(p, p->tile_idx2, sizeof(uint32_t) * T, s, "tile_idx2"));
+        size_t tmp = 0;
+        BGS_CUDA(cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp, key, (uint32_t *)p->tile_key2.p, idx,
+                                                           (uint32_t *)p->tile_idx2.p, T, 0, 32, s),
+                 "sort tiles (size)");
+        BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
+        tmp = p->cub_tmp.bytes;
+        BGS_CUDA(cub::DeviceRadixSort::SortPairsDescending(p->cub_tmp.p, tmp, key, (uint32_t *)p->tile_key2.p, idx,
+                                                           (uint32_t *)p->tile_idx2.p, T, 0, 32, s),
+                 "sort tiles");
+        order = (const uint32_t *)p->tile_idx2.p;
+    }
+    uint32_t *counts = (uint32_t *)p->counts.p, *off = (uint32_t *)p->item_off.p;
+    BGS_CUDA(bgs::launch_gather_counts(order, T, rg, W, H, tw, th, tiles_x, mode, p->desc.heavy_threshold, P, counts, s),
+             "gather_counts");
+    size_t tmp = 0;
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, counts, off, T, s), "scan items (size)");
+    BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
+    tmp = p->cub_tmp.bytes;
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, counts, off, T, s), "scan items");
+    BGS_CUDA(bgs::launch_emit_items(order, counts, off, T, rg, mode, p->desc.heavy_threshold, (uint2 *)p->items.p,
+                                    p->ctrl, s),
+             "emit_items");
+    p->host_launches += 3;  // tile_counts, gather_counts, emit_items
+    return BGS_OK;
+}
+
+bool valid_desc(const bgs_plan_desc *d) {
+    return d->heavy_threshold >= 0 && (d->gw_pixels == 1 || d->gw_pixels == 2 || d->gw_pixels == 4 ||
+                                       d->gw_pixels == 8) &&
+           d->queue_chunk >= 1 && d->queue_chunk <= 1024 && d->blocks_per_sm >= 0 && d->blocks_per_sm <= 64;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bgs_last_error(void) { return g_last_error.c_str(); }
+
+void bgs_plan_desc_default(bgs_plan_desc *d) {
+    if (!d) return;
+    d->heavy_threshold = 512;
+    d->gw_pixels = 4;
+    d->queue_chunk = 1;
+    d->blocks_per_sm = 0;
+    d->lpt_order = 1;
+    d->device = -1;
+}
+
+int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out) {
+    if (!out) return fail(BGS_ERR_INVALID, "bgs_plan_create: out is NULL");
+    *out = nullptr;
+    bgs_plan_desc d;
+    bgs_plan_desc_default(&d);
+    if (desc) d = *desc;
+    if (!valid_desc(&d)) return fail(BGS_ERR_INVALID, "bgs_plan_create: invalid tuning knobs");
+    int dev = d.device;
+    if (dev < 0) BGS_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    int ndev = 0;
+    BGS_CUDA(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (dev >= ndev) return fail(BGS_ERR_INVALID, "device %d of %d", dev, ndev);
+    DeviceGuard g(dev);
+    bgs_plan *p = new bgs_plan();
+    p->desc = d;
+    p->desc.device = dev;
+    p->device = dev;
+    cudaError_t e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&p->ctrl, sizeof(bgs::DevCtrl));
+    if (e == cudaSuccess) e = cudaMemset(p->ctrl, 0, sizeof(bgs::DevCtrl));
+    if (e != cudaSuccess) {
+        if (p->ctrl) cudaFree(p->ctrl);
+        delete p;
+        return cuda_fail(e, "bgs_plan_create");
+    }
+    *out = p;
+    return BGS_OK;
+}
+
+int bgs_plan_destroy(bgs_plan *p) {
+    if (!p) return BGS_OK;
+    DeviceGuard g(p->device);
+    Buf *bufs[] = {&p->touched, &p->offsets, &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
+                   &p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off, &p->items,
+                   &p->grad_acc};
+    for (Buf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (p->ctrl) cudaFree(p->ctrl);
+    for (auto &e : p->ev_fwd) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    for (auto &e : p->ev_bwd) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    delete p;
+    return BGS_OK;
+}
+
+int bgs_plan_timing(bgs_plan *p, int enable) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_plan_timing: NULL plan");
+    p->timing = enable != 0;
+    return BGS_OK;
+}
+
+int bgs_plan_kernel_ms(bgs_plan *p, double *fwd_ms, int32_t *fwd_n, double *bwd_ms, int32_t *bwd_n) {
+    if (!p || !fwd_ms || !fwd_n || !bwd_ms || !bwd_n) return fail(BGS_ERR_INVALID, "bgs_plan_kernel_ms: NULL argument");
+    DeviceGuard g(p->device);
+    double sums[2] = {0.0, 0.0};
+    int counts[2] = {0, 0};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *lists[2] = {&p->ev_fwd, &p->ev_bwd};
+    for (int k = 0; k < 2; ++k) {
+        for (auto &e : *lists[k]) {
+            BGS_CUDA(cudaEventSynchronize(e.second), "kernel timing sync");
+            float ms = 0.f;
+            BGS_CUDA(cudaEventElapsedTime(&ms, e.first, e.second), "kernel timing");
+            sums[k] += ms;
+            counts[k] += 1;
+            p->ev_pool.push_back(e.first);
+            p->ev_pool.push_back(e.second);
+        }
+        lists[k]->clear();
+    }
+    *fwd_ms = sums[0];
+    *fwd_n = counts[0];
+    *bwd_ms = sums[1];
+    *bwd_n = counts[1];
+    return BGS_OK;
+}
+
+int bgs_plan_set(bgs_plan *p, const bgs_plan_desc *d) {
+    if (!p || !d) return fail(BGS_ERR_INVALID, "bgs_plan_set: NULL argument");
+    if (!valid_desc(d)) return fail(BGS_ERR_INVALID, "bgs_plan_set: invalid tuning knobs");
+    const int dev = p->device;
+    p->desc = *d;
+    p->desc.device = dev;
+    return BGS_OK;
+}
+
+int bgs_plan_get(const bgs_plan *p, bgs_plan_desc *d) {
+    if (!p || !d) return fail(BGS_ERR_INVALID, "bgs_plan_get: NULL argument");
+    *d = p->desc;
+    return BGS_OK;
+}
+
+int bgs_plan_num_sms(const bgs_plan *p) { return p ? p->num_sms : 0; }
+
+size_t bgs_workspace_size(const bgs_plan *p, int64_t N, int64_t K, int64_t T, int64_t /*pixels*/) {
+    if (!p || N < 0 || K < 0 || T < 0) return 0;
+    const int P = p->desc.gw_pixels > 0 ? p->desc.gw_pixels : 1;
+    size_t s = 0;
+    s += 4 * N + 8 * N;                 // touched, offsets
+    s += 8 * K * 2 + 4 * K;             // keys in/out, values in
+    s += 48 * N * 2;                    // packed records, gradient accumulators
+    s += 4 * T * 6;                     // tile keys/indices/counts/offsets
+    s += 8 * T * (size_t)std::max(8, (256 + P - 1) / P);  // work items (16x16 tiles)
+    s += 64 << 20;                      // CUB temporaries (upper estimate)
+    return s;
+}
+
+int bgs_plan_reserve(bgs_plan *p, int64_t N, int64_t K, int64_t T, int64_t pixels) {
+    if (!p || N < 0 || K < 0 || T < 0 || pixels < 0) return fail(BGS_ERR_INVALID, "bgs_plan_reserve: bad sizes");
+    DeviceGuard g(p->device);
+    cudaStream_t s = 0;
+    BGS_TRY(ensure(p, p->touched, 4 * N, s, "touched"));
+    BGS_TRY(ensure(p, p->offsets, 8 * N, s, "offsets"));
+    BGS_TRY(ensure(p, p->keys_in, 8 * K, s, "keys_in"));
+    BGS_TRY(ensure(p, p->keys_out, 8 * K, s, "keys_out"));
+    BGS_TRY(ensure(p, p->vals_in, 4 * K, s, "vals_in"));
+    BGS_TRY(ensure(p, p->recs, sizeof(bgs::Rec) * N, s, "recs"));
+    BGS_TRY(ensure(p, p->grad_acc, sizeof(bgs::Rec) * N, s, "grad_acc"));
+    const int P = p->desc.gw_pixels;
+    BGS_TRY(ensure(p, p->tile_key, 4 * T, s, "tile_key"));
+    BGS_TRY(ensure(p, p->tile_key2, 4 * T, s, "tile_key2"));
+    BGS_TRY(ensure(p, p->tile_idx, 4 * T, s, "tile_idx"));
+    BGS_TRY(ensure(p, p->tile_idx2, 4 * T, s, "tile_idx2"));
+    BGS_TRY(ensure(p, p->counts, 4 * T, s, "counts"));
+    BGS_TRY(ensure(p, p->item_off, 4 * T, s, "item_off"));
+    BGS_TRY(ensure(p, p->items, 8 * T * (size_t)std::max(8, (256 + P - 1) / P), s, "items"));
+    // CUB temporaries: the largest of the entry sort, the N-scan and the tile sort / scan
+    size_t t1 = 0, t2 = 0, t3 = 0, t4 = 0;
+    BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, t1, (unsigned long long *)nullptr,
+                                             (unsigned long long *)nullptr, (uint32_t *)nullptr, (uint32_t *)nullptr,
+                                             (int64_t)std::max<int64_t>(K, 1), 0, 64, s),
+             "sort size");
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, t2, (uint32_t *)nullptr, (unsigned long long *)nullptr,
+                                           (int64_t)std::max<int64_t>(N, 1), s),
+             "scan size");
+    BGS_CUDA(cub::DeviceRadixSort::SortPairsDescending(nullptr, t3, (uint32_t *)nullptr, (uint32_t *)nullptr,
+                                                       (uint32_t *)nullptr, (uint32_t *)nullptr,
+                                                       (int)std::max<int64_t>(T, 1), 0, 32, s),
+             "tile sort size");
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, t4, (uint32_t *)nullptr, (uint32_t *)nullptr,
+                                           (int)std::max<int64_t>(T, 1), s),
+             "tile scan size");
+    BGS_TRY(ensure(p, p->cub_tmp, std::max(std::max(t1, t2), std::max(t3, t4)), s, "cub_tmp"));
+    return BGS_OK;
+}
+
+int bgs_check(bgs_plan *p, void *stream) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_check: NULL plan");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int bits = 0;
+    BGS_CUDA(cudaMemcpyAsync(&bits, &p->ctrl->check_bits, sizeof bits, cudaMemcpyDeviceToHost, s), "bgs_check copy");
+    BGS_CUDA(cudaStreamSynchronize(s), "bgs_check sync");
+    if (bits) {
+        BGS_CUDA(cudaMemsetAsync(&p->ctrl->check_bits, 0, sizeof bits, s), "bgs_check clear");
+        BGS_CUDA(cudaStreamSynchronize(s), "bgs_check sync");
+        return fail(BGS_ERR_DEVICE_CHECK, "device check tripped: bits 0x%x (%s%s%s%s)", bits,
+                    (bits & BGS_CHECK_INDEX) ? "index " : "", (bits & BGS_CHECK_RANGE) ? "range " : "",
+                    (bits & BGS_CHECK_OVERFLOW) ? "overflow " : "", (bits & BGS_CHECK_QUEUE) ? "queue" : "");
+    }
+    return BGS_OK;
+}
+
+int bgs_plan_stats(bgs_plan *p, bgs_stats *out, void *stream) {
+    if (!p || !out) return fail(BGS_ERR_INVALID, "bgs_plan_stats: NULL argument");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    bgs::DevCtrl c;
+    BGS_CUDA(cudaMemcpyAsync(&c, p->ctrl, sizeof c, cudaMemcpyDeviceToHost, s), "stats copy");
+    BGS_CUDA(cudaStreamSynchronize(s), "stats sync");
+    out->eval_pairs = c.eval_pairs;
+    out->contrib_pairs = c.contrib_pairs;
+    out->items = c.items_done;
+    out->check_bits = c.check_bits;
+    out->last_num_items = c.num_items;
+    out->host_launches = p->host_launches;
+    return BGS_OK;
+}
+
+int bgs_plan_reset_stats(bgs_plan *p, void *stream) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_plan_reset_stats: NULL plan");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    BGS_CUDA(cudaMemsetAsync(&p->ctrl->eval_pairs, 0, 3 * sizeof(unsigned long long), s), "reset stats");
+    return BGS_OK;
+}
+
+int bgs_preprocess(bgs_plan *p, int64_t N, const float *means3D, const float *log_scales, const float *quats,
+                   const float *opacities, const bgs_camera *cam, int32_t tw, int32_t th, float *means2D,
+                   float *conic_opacity, float *depths, int32_t *radii, uint32_t *tiles_touched, void *stream) {
+    if (!p || !cam) return fail(BGS_ERR_INVALID, "bgs_preprocess: NULL plan or camera");
+    if (N < 0 || N >= (1ll << 32)) return fail(BGS_ERR_INVALID, "bgs_preprocess: N=%lld out of range", (long long)N);
+    if (N > 0 && (!means3D || !log_scales || !quats || !opacities || !means2D || !conic_opacity || !depths || !radii ||
+                  !tiles_touched))
+        return fail(BGS_ERR_INVALID, "bgs_preprocess: NULL array");
+    BGS_TRY(check_image(cam->width, cam->height));
+    BGS_TRY(check_tile(tw, th, false));
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(BGS_ERR_INVALID, "bgs_preprocess: focal lengths must be > 0");
+    DeviceGuard g(p->device);
+    BGS_CUDA(bgs::launch_preprocess(N, means3D, log_scales, quats, opacities, *cam, tw, th, means2D, conic_opacity,
+                                    depths, radii, tiles_touched, (cudaStream_t)stream),
+             "preprocess");
+    if (N > 0) p->host_launches += 1;
+    return BGS_OK;
+}
+
+int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t *radii, const float *depths,
+                     int32_t W, int32_t H, int32_t tw, int32_t th, uint32_t *point_list, int64_t capacity,
+                     uint32_t *ranges, int64_t *num_rendered, int64_t *needed, void *stream) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: NULL plan");
+    if (N < 0 || N >= (1ll << 32)) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: N out of range");
+    if (capacity < 0) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: negative capacity");
+    BGS_TRY(check_image(W, H));
+    BGS_TRY(check_tile(tw, th, false));
+    if (!ranges || (N > 0 && (!means2D || !radii || !depths)) || (capacity > 0 && !point_list))
+        return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: NULL array");
+    const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
+    const long long T = (long long)tiles_x * tiles_y;
+    if (T >= (1ll << 31)) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: too many tiles");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    BGS_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * T, s), "clear ranges");
+    if (num_rendered) *num_rendered = 0;
+    if (N == 0) return BGS_OK;
+    BGS_TRY(ensure(p, p->touched, 4 * N, s, "touched"));
+    BGS_TRY(ensure(p, p->offsets, 8 * N, s, "offsets"));
+    uint32_t *touched = (uint32_t *)p->touched.p;
+    unsigned long long *off = (unsigned long long *)p->offsets.p;
+    BGS_CUDA(bgs::launch_touched(N, means2D, radii, W, H, tw, th, touched, s), "touched");
+    size_t tmp = 0;
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, touched, off, (int64_t)N, s), "scan (size)");
+    BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
+    tmp = p->cub_tmp.bytes;
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, touched, off, (int64_t)N, s), "scan");
+    BGS_CUDA(bgs::launch_count_total(N, touched, off, p->ctrl, s), "count_total");
+    p->host_launches += 2;  // touched, count_total
+    unsigned long long K = 0;
+    BGS_CUDA(cudaMemcpyAsync(&K, &p->ctrl->num_entries, sizeof K, cudaMemcpyDeviceToHost, s), "read K");
+    BGS_CUDA(cudaStreamSynchronize(s), "sync K");
+    if (needed) *needed = (int64_t)K;
+    if ((long long)K > capacity)
+        return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort: %llu entries exceed capacity %lld", K, (long long)capacity);
+    if (K >= (1ull << 32) - 1) return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort: %llu entries exceed 2^32", K);
+    if (num_rendered) *num_rendered = (int64_t)K;
+    if (K == 0) return BGS_OK;
+    BGS_TRY(ensure(p, p->keys_in, 8 * K, s, "keys_in"));
+    BGS_TRY(ensure(p, p->keys_out, 8 * K, s, "keys_out"));
+    BGS_TRY(ensure(p, p->vals_in, 4 * K, s, "vals_in"));
+    unsigned long long *kin = (unsigned long long *)p->keys_in.p, *kout = (unsigned long long *)p->keys_out.p;
+    uint32_t *vin = (uint32_t *)p->vals_in.p;
+    BGS_CUDA(bgs::launch_duplicate(N, means2D, radii, depths, off, W, H, tw, th, kin, vin, (long long)K, s),
+             "duplicate");
+    const int end_bit = 32 + bits_for(T);
+    tmp = 0;
+    BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, kin, kout, vin, point_list, (int64_t)K, 0, end_bit, s),
+             "sort (size)");
+    BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
+    tmp = p->cub_tmp.bytes;
+    BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, kin, kout, vin, point_list, (int64_t)K, 0, end_bit, s),
+             "sort");
+    BGS_CUDA(bgs::launch_ranges(kout, (long long)K, reinterpret_cast<uint2 *>(ranges), s), "ranges");
+    p->host_launches += 2;  // duplicate, ranges
+    return BGS_OK;
+}
+
+static int render_common_checks(bgs_plan *p, int64_t N, const float *means2D, const float *conic_opacity,
+                                const float *colors, const float *depths, const uint32_t *point_list,
+                                int64_t num_entries, const uint32_t *ranges, int W, int H, int tw, int th,
+                                const float *bg, int mode, const char *who) {
+    if (!p) return fail(BGS_ERR_INVALID, "%s: NULL plan", who);
+    if (N < 0 || N >= (1ll << 32)) return fail(BGS_ERR_INVALID, "%s: N out of range", who);
+    if (num_entries < 0 || num_entries >= (1ll << 32)) return fail(BGS_ERR_INVALID, "%s: num_entries out of range", who);
+    if (mode < BGS_MODE_AUTO || mode > BGS_MODE_STATIC) return fail(BGS_ERR_INVALID, "%s: unknown mode %d", who, mode);
+    BGS_TRY(check_image(W, H));
+    BGS_TRY(check_tile(tw, th, mode != BGS_MODE_STATIC));
+    if (!ranges || !bg || (num_entries > 0 && !point_list) ||
+        (N > 0 && (!means2D || !conic_opacity || !colors || !depths)))
+        return fail(BGS_ERR_INVALID, "%s: NULL array", who);
+    if ((((uintptr_t)means2D) & 7) || (((uintptr_t)conic_opacity) & 15) || (((uintptr_t)ranges) & 7))
+        return fail(BGS_ERR_INVALID, "%s: means2D must be 8-byte, conic_opacity 16-byte aligned", who);
+    return BGS_OK;
+}
+
+int bgs_render_forward(bgs_plan *p, int64_t N, const float *means2D, const float *conic_opacity, const float *colors,
+                       const float *depths, const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
+                       int32_t W, int32_t H, int32_t tw, int32_t th, const float *bg, int32_t mode, float *out_color,
+                       float *out_depth, float *out_alpha, float *final_T, int32_t *n_contrib, int32_t *n_eval,
+                       void *stream) {
+    BGS_TRY(render_common_checks(p, N, means2D, conic_opacity, colors, depths, point_list, num_entries, ranges, W, H,
+                                 tw, th, bg, mode, "bgs_render_forward"));
+    if (!out_color || !out_depth || !out_alpha || !final_T || !n_contrib)
+        return fail(BGS_ERR_INVALID, "bgs_render_forward: NULL output");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    bgs::FwdArgs a;
+    memset(&a, 0, sizeof a);
+    a.means2D = means2D;
+    a.conic_opacity = conic_opacity;
+    a.colors = colors;
+    a.depths = depths;
+    a.point_list = point_list;
+    a.ranges = reinterpret_cast<const uint2 *>(ranges);
+    a.N = N;
+    a.num_entries = num_entries;
+    a.W = W;
+    a.H = H;
+    a.tile_w = tw;
+    a.tile_h = th;
+    a.tiles_x = (W + tw - 1) / tw;
+    a.tiles_y = (H + th - 1) / th;
+    a.bg[0] = bg[0];
+    a.bg[1] = bg[1];
+    a.bg[2] = bg[2];
+    a.out_color = out_color;
+    a.out_depth = out_depth;
+    a.out_alpha = out_alpha;
+    a.final_T = final_T;
+    a.n_contrib = n_contrib;
+    a.n_eval = n_eval;
+    a.ctrl = p->ctrl;
+    a.gw_pixels = p->desc.gw_pixels;
+    a.chunk = p->desc.queue_chunk;
+    if (mode == BGS_MODE_STATIC) {
+        KernelTimer kt(p, s, &p->ev_fwd);
+        BGS_CUDA(bgs::launch_forward_static(a, s), "forward_static");
+        kt.stop();
+        p->host_launches += 1;
+        return BGS_OK;
+    }
+    BGS_TRY(ensure(p, p->recs, sizeof(bgs::Rec) * std::max<int64_t>(N, 1), s, "recs"));
+    BGS_CUDA(bgs::launch_pack(N, means2D, conic_opacity, colors, depths, (bgs::Rec *)p->recs.p, s), "pack");
+    p->host_launches += 1;
+    a.recs = (const bgs::Rec *)p->recs.p;
+    BGS_TRY(build_worklist(p, ranges, W, H, tw, th, mode, s));
+    a.items = (const uint2 *)p->items.p;
+    const int grid = grid_for(p, bgs::forward_balanced_kernel(a.gw_pixels), bgs::forward_balanced_block_threads());
+    KernelTimer kt(p, s, &p->ev_fwd);
+    BGS_CUDA(bgs::launch_forward_balanced(a, grid, s), "forward_balanced");
+    kt.stop();
+    p->host_launches += 1;
+    return BGS_OK;
+}
+
+int bgs_render_backward(bgs_plan *p, int64_t N, const float *means2D, const float *conic_opacity, const float *colors,
+                        const float *depths, const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
+                        int32_t W, int32_t H, int32_t tw, int32_t th, const float *bg, int32_t mode,
+                        const float *final_T, const int32_t *n_contrib, const float *dL_dcolor, const float *dL_ddepth,
+                        const float *dL_dalpha, float *dL_dmeans2D, float *dL_dconic, float *dL_dopacity,
+                        float *dL_dcolors, float *dL_ddepths, void *stream) {
+    BGS_TRY(render_common_checks(p, N, means2D, conic_opacity, colors, depths, point_list, num_entries, ranges, W, H,
+                                 tw, th, bg, mode, "bgs_render_backward"));
+    if (!final_T || !n_contrib || !dL_dcolor)
+        return fail(BGS_ERR_INVALID, "bgs_render_backward: NULL final_T / n_contrib / dL_dcolor");
+    if (N > 0 && (!dL_dmeans2D || !dL_dconic || !dL_dopacity || !dL_dcolors))
+        return fail(BGS_ERR_INVALID, "bgs_render_backward: NULL gradient output");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (N == 0) return BGS_OK;
+    BGS_TRY(ensure(p, p->grad_acc, sizeof(bgs::Rec) * N, s, "grad_acc"));
+    BGS_CUDA(cudaMemsetAsync(p->grad_acc.p, 0, sizeof(bgs::Rec) * N, s), "clear grad_acc");
+    bgs::BwdArgs a;
+    memset(&a, 0, sizeof a);
+    a.means2D = means2D;
+    a.conic_opacity = conic_opacity;
+    a.colors = colors;
+    a.depths = depths;
+    a.point_list = point_list;
+    a.ranges = reinterpret_cast<const uint2 *>(ranges);
+    a.N = N;
+    a.num_entries = num_entries;
+    a.W = W;
+    a.H = H;
+    a.tile_w = tw;
+    a.tile_h = th;
+    a.tiles_x = (W + tw - 1) / tw;
+    a.tiles_y = (H + th - 1) / th;
+    a.bg[0] = bg[0];
+    a.bg[1] = bg[1];
+    a.bg[2] = bg[2];
+    a.final_T = final_T;
+    a.n_contrib = n_contrib;
+    a.dL_dcolor = dL_dcolor;
+    a.dL_ddepth = dL_ddepth;
+    a.dL_dalpha = dL_dalpha;
+    a.grad_acc = (float4 *)p->grad_acc.p;
+    a.ctrl = p->ctrl;
+    a.chunk = p->desc.queue_chunk;
+    if (mode == BGS_MODE_STATIC) {
+        KernelTimer kt(p, s, &p->ev_bwd);
+        BGS_CUDA(bgs::launch_backward_static(a, s), "backward_static");
+        kt.stop();
+        p->host_launches += 1;
+    } else {
+        BGS_TRY(ensure(p, p->recs, sizeof(bgs::Rec) * N, s, "recs"));
+        BGS_CUDA(bgs::launch_pack(N, means2D, conic_opacity, colors, depths, (bgs::Rec *)p->recs.p, s), "pack");
+        a.recs = (const bgs::Rec *)p->recs.p;
+        BGS_TRY(build_worklist(p, ranges, W, H, tw, th, BGS_MODE_PIXEL, s));
+        a.items = (const uint2 *)p->items.p;
+        const int grid = grid_for(p, bgs::backward_balanced_kernel(), bgs::backward_balanced_block_threads());
+        KernelTimer kt(p, s, &p->ev_bwd);
+        BGS_CUDA(bgs::launch_backward_balanced(a, grid, s), "backward_balanced");
+        kt.stop();
+        p->host_launches += 2;  // pack + kernel
+    }
+    p->host_launches += 1;      // finalize
+    BGS_CUDA(bgs::launch_grad_finalize(N, (const float4 *)p->grad_acc.p, dL_dmeans2D, dL_dconic, dL_dopacity,
+                                       dL_dcolors, dL_ddepths, s),
+             "grad_finalize");
+    return BGS_OK;
+}
+
+}  // extern "C"

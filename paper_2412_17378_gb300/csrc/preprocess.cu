@@ -1,0 +1,246 @@
+// preprocess.cu -- a1: per-Gaussian projection (Eq. 1-3 of the paper, Sec. 2.1).
+//
+// One thread per Gaussian.  The work is ~80 bytes of HBM traffic and ~150 FP32
+// operations per Gaussian: a few microseconds per million Gaussians, far below the
+// render kernels, so the kernel is written for clarity with coalesced scalar loads.
+#include "bgs_internal.cuh"
+
+namespace bgs {
+
+struct CamDev {
+    float V[12];  // rows 0..2 of the world->camera matrix
+    float fx, fy, cx, cy, near_plane, lowpass, lim_x, lim_y;
+    int W, H, tile_w, tile_h, tiles_x, tiles_y;
+};
+
+// Tile rectangle of a Gaussian: x in [floor((u-r)/tw), floor((u+(r+tw-1))/tw)), clamped.
+// Float32 with one IEEE rounding per operation (no contraction), the same operations the
+// binning kernel and the host-side checks use.
+__device__ __forceinline__ void tile_rect(float u, float v, int r, int tw, int th, int tx, int ty, int &x0,
+                                          int &x1, int &y0, int &y1) {
+    x0 = (int)floorf(__fdiv_rn(__fsub_rn(u, (float)r), (float)tw));
+    x1 = (int)floorf(__fdiv_rn(__fadd_rn(u, (float)(r + tw - 1)), (float)tw));
+    y0 = (int)floorf(__fdiv_rn(__fsub_rn(v, (float)r), (float)th));
+    y1 = (int)floorf(__fdiv_rn(__fadd_rn(v, (float)(r + th - 1)), (float)th));
+    x0 = min(max(x0, 0), tx);
+    x1 = min(max(x1, 0), tx);
+    y0 = min(max(y0, 0), ty);
+    y1 = min(max(y1, 0), ty);
+}
+
+__global__ void __launch_bounds__(256) k_preprocess(long long N, const float *__restrict__ means3D,
+                                                    const float *__restrict__ log_scales,
+                                                    const float *__restrict__ quats,
+                                                    const float *__restrict__ opacities, CamDev cam,
+                                                    float2 *__restrict__ means2D, float4 *__restrict__ conic_opacity,
+                                                    float *__restrict__ depths, int *__restrict__ radii,
+                                                    uint32_t *__restrict__ tiles_touched) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float px = means3D[3 * i], py = means3D[3 * i + 1], pz = means3D[3 * i + 2];
+    const float *V = cam.V;
+    const float tx = V[0] * px + V[1] * py + V[2] * pz + V[3];
+    const float ty = V[4] * px + V[5] * py + V[6] * pz + V[7];
+    const float tz = V[8] * px + V[9] * py + V[10] * pz + V[11];
+    float2 m2 = make_float2(0.f, 0.f);
+    float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
+    int radius = 0;
+    uint32_t touched = 0;
+    depths[i] = tz;
+    if (tz > cam.near_plane) {
+        // R from the normalised quaternion (w, x, y, z)
+        float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+        const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        qw /= qn; qx /= qn; qy /= qn; qz /= qn;
+        const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
+        const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
+        const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
+        const float s0 = expf(log_scales[3 * i]), s1 = expf(log_scales[3 * i + 1]), s2 = expf(log_scales[3 * i + 2]);
+        // M = R S ; Sigma = M M^T (symmetric, 6 entries)
+        const float M00 = R00 * s0, M01 = R01 * s1, M02 = R02 * s2;
+        const float M10 = R10 * s0, M11 = R11 * s1, M12 = R12 * s2;
+        const float M20 = R20 * s0, M21 = R21 * s1, M22 = R22 * s2;
+        const float S00 = M00 * M00 + M01 * M01 + M02 * M02;
+        const float S01 = M00 * M10 + M01 * M11 + M02 * M12;
+        const float S02 = M00 * M20 + M01 * M21 + M02 * M22;
+        const float S11 = M10 * M10 + M11 * M11 + M12 * M12;
+        const float S12 = M10 * M20 + M11 * M21 + M12 * M22;
+        const float S22 = M20 * M20 + M21 * M21 + M22 * M22;
+        // Jacobian of the pinhole map at the tangent-clamped point
+        const float iz = 1.f / tz;
+        const float xc = fminf(cam.lim_x, fmaxf(-cam.lim_x, tx * iz)) * tz;
+        const float yc = fminf(cam.lim_y, fmaxf(-cam.lim_y, ty * iz)) * tz;
+        const float J00 = cam.fx * iz, J02 = -cam.fx * xc * iz * iz;
+        const float J11 = cam.fy * iz, J12 = -cam.fy * yc * iz * iz;
+        // T = J W (2x3)
+        const float T00 = J00 * V[0] + J02 * V[8], T01 = J00 * V[1] + J02 * V[9], T02 = J00 * V[2] + J02 * V[10];
+        const float T10 = J11 * V[4] + J12 * V[8], T11 = J11 * V[5] + J12 * V[9], T12 = J11 * V[6] + J12 * V[10];
+        // Sigma' = T Sigma T^T
+        const float U00 = S00 * T00 + S01 * T01 + S02 * T02;  // (Sigma T^T) column 0
+        const float U10 = S01 * T00 + S11 * T01 + S12 * T02;
+        const float U20 = S02 * T00 + S12 * T01 + S22 * T02;
+        const float U01 = S00 * T10 + S01 * T11 + S02 * T12;  // column 1
+        const float U11 = S01 * T10 + S11 * T11 + S12 * T12;
+        const float U21 = S02 * T10 + S12 * T11 + S22 * T12;
+        const float c00 = T00 * U00 + T01 * U10 + T02 * U20 + cam.lowpass;
+        const float c01 = T00 * U01 + T01 * U11 + T02 * U21;
+        const float c11 = T10 * U01 + T11 * U11 + T12 * U21 + cam.lowpass;
+        const float det = c00 * c11 - c01 * c01;
+        if (det > 0.f) {
+            const float mid = 0.5f * (c00 + c11);
+            const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+            const int r = (int)ceilf(3.f * sqrtf(lam));
+            const float idet = 1.f / det;
+            const float u = cam.fx * tx * iz + cam.cx, v = cam.fy * ty * iz + cam.cy;
+            m2 = make_float2(u, v);
+            co = make_float4(c11 * idet, -c01 * idet, c00 * idet, opacities[i]);
+            int x0, x1, y0, y1;
+            tile_rect(u, v, r, cam.tile_w, cam.tile_h, cam.tiles_x, cam.tiles_y, x0, x1, y0, y1);
+            const long long area = (long long)(x1 - x0) * (long long)(y1 - y0);
+            if (area > 0) {
+                radius = r;
+                touched = (uint32_t)area;
+            }
+        }
+    }
+    means2D[i] = m2;
+    conic_opacity[i] = co;
+    radii[i] = radius;
+    tiles_touched[i] = touched;
+}
+
+cudaError_t launch_preprocess(long long N, const float *means3D, const float *log_scales, const float *quats,
+                              const float *opacities, const bgs_camera &c, int tile_w, int tile_h,
+                              float *means2D, float *conic_opacity, float *depths, int *radii,
+                              uint32_t *tiles_touched, cudaStream_t s) {
+    CamDev cam;
+    for (int k = 0; k < 12; ++k) cam.V[k] = c.viewmat[k];
+    cam.fx = c.fx; cam.fy = c.fy; cam.cx = c.cx; cam.cy = c.cy;
+    cam.near_plane = c.near_plane;
+    cam.lowpass = c.lowpass;
+    cam.lim_x = 1.3f * (float)((double)c.width / (2.0 * (double)c.fx));
+    cam.lim_y = 1.3f * (float)((double)c.height / (2.0 * (double)c.fy));
+    cam.W = c.width; cam.H = c.height;
+    cam.tile_w = tile_w; cam.tile_h = tile_h;
+    cam.tiles_x = (c.width + tile_w - 1) / tile_w;
+    cam.tiles_y = (c.height + tile_h - 1) / tile_h;
+    if (N == 0) return cudaSuccess;
+    const int threads = 256;
+    const long long blocks = (N + threads - 1) / threads;
+    k_preprocess<<<(unsigned)blocks, threads, 0, s>>>(N, means3D, log_scales, quats, opacities, cam,
+                                                       reinterpret_cast<float2 *>(means2D),
+                                                       reinterpret_cast<float4 *>(conic_opacity), depths, radii,
+                                                       tiles_touched);
+    return cudaGetLastError();
+}
+
+// ---- a2 helpers: duplicated keys, totals and ranges ------------------------------------
+
+// Each Gaussian writes one (key, value) entry per covered tile at offsets[i] (an exclusive
+// scan of tiles_touched).  The rectangle is recomputed with the same float32 operations.
+__global__ void __launch_bounds__(256) k_duplicate(long long N, const float2 *__restrict__ means2D,
+                                                   const int *__restrict__ radii, const float *__restrict__ depths,
+                                                   const unsigned long long *__restrict__ offsets, int tw, int th, int tx,
+                                                   int ty, unsigned long long *__restrict__ keys,
+                                                   uint32_t *__restrict__ vals, long long capacity) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int r = radii[i];
+    if (r <= 0) return;
+    const float2 m = means2D[i];
+    int x0, x1, y0, y1;
+    tile_rect(m.x, m.y, r, tw, th, tx, ty, x0, x1, y0, y1);
+    long long off = offsets[i];
+    const unsigned long long dbits = (unsigned long long)__float_as_uint(depths[i]);
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) {
+            if (off < capacity) {
+                keys[off] = ((unsigned long long)(y * tx + x) << 32) | dbits;
+                vals[off] = (uint32_t)i;
+            }
+            ++off;
+        }
+}
+
+cudaError_t launch_duplicate(long long N, const float *means2D, const int *radii, const float *depths,
+                             const unsigned long long *offsets, int W, int H, int tile_w, int tile_h,
+                             unsigned long long *keys, uint32_t *vals, long long capacity, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    const int tx = (W + tile_w - 1) / tile_w, ty = (H + tile_h - 1) / tile_h;
+    const long long blocks = (N + 255) / 256;
+    k_duplicate<<<(unsigned)blocks, 256, 0, s>>>(N, reinterpret_cast<const float2 *>(means2D), radii, depths,
+                                                 offsets, tile_w, tile_h, tx, ty, keys, vals, capacity);
+    return cudaGetLastError();
+}
+
+__global__ void k_count_total(long long N, const uint32_t *touched, const unsigned long long *offsets,
+                              DevCtrl *ctrl) {
+    ctrl->num_entries = N > 0 ? offsets[N - 1] + touched[N - 1] : 0ull;
+}
+
+cudaError_t launch_count_total(long long N, const uint32_t *touched, const unsigned long long *offsets, DevCtrl *ctrl,
+                               cudaStream_t s) {
+    k_count_total<<<1, 1, 0, s>>>(N, touched, offsets, ctrl);
+    return cudaGetLastError();
+}
+
+// Entry count of each Gaussian (area of its tile rectangle, 0 if radius <= 0).
+__global__ void __launch_bounds__(256) k_touched(long long N, const float2 *__restrict__ means2D,
+                                                 const int *__restrict__ radii, int tw, int th, int tx, int ty,
+                                                 uint32_t *__restrict__ touched) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int r = radii[i];
+    uint32_t c = 0;
+    if (r > 0) {
+        const float2 m = means2D[i];
+        int x0, x1, y0, y1;
+        tile_rect(m.x, m.y, r, tw, th, tx, ty, x0, x1, y0, y1);
+        if (x1 > x0 && y1 > y0) c = (uint32_t)((x1 - x0) * (y1 - y0));
+    }
+    touched[i] = c;
+}
+
+cudaError_t launch_touched(long long N, const float *means2D, const int *radii, int W, int H, int tile_w,
+                           int tile_h, uint32_t *touched, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    const int tx = (W + tile_w - 1) / tile_w, ty = (H + tile_h - 1) / tile_h;
+    k_touched<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, reinterpret_cast<const float2 *>(means2D), radii,
+                                                          tile_w, tile_h, tx, ty, touched);
+    return cudaGetLastError();
+}
+
+// ranges[t] = [first, last+1) of tile t in the sorted keys (ranges zeroed beforehand).
+__global__ void __launch_bounds__(256) k_ranges(const unsigned long long *__restrict__ keys, long long K,
+                                                uint2 *__restrict__ ranges) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= K) return;
+    const uint32_t t = (uint32_t)(keys[j] >> 32);
+    if (j == 0 || (uint32_t)(keys[j - 1] >> 32) != t) ranges[t].x = (uint32_t)j;
+    if (j == K - 1 || (uint32_t)(keys[j + 1] >> 32) != t) ranges[t].y = (uint32_t)(j + 1);
+}
+
+cudaError_t launch_ranges(const unsigned long long *keys, long long K, uint2 *ranges, cudaStream_t s) {
+    if (K == 0) return cudaSuccess;
+    k_ranges<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(keys, K, ranges);
+    return cudaGetLastError();
+}
+
+// ---- render input packing ------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_pack(long long N, const float *__restrict__ means2D,
+                                              const float *__restrict__ conic_opacity,
+                                              const float *__restrict__ colors, const float *__restrict__ depths,
+                                              Rec *__restrict__ recs) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    recs[i] = make_rec(means2D, conic_opacity, colors, depths, (unsigned int)i);
+}
+
+cudaError_t launch_pack(long long N, const float *means2D, const float *conic_opacity, const float *colors,
+                        const float *depths, Rec *recs, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    k_pack<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, means2D, conic_opacity, colors, depths, recs);
+    return cudaGetLastError();
+}
+
+}  // namespace bgs

@@ -1,0 +1,290 @@
+// render_bwd.cu -- a6: backward render kernels.
+//
+// The paper describes only the forward kernel; its backward (Sec. 3 cites the L2
+// atomic bottleneck of 3DGS gradients) is derived here from Eq. 4.  With
+// T_i = prod_{j<i}(1 - alpha_j), R_i the colour accumulated behind entry i normalised by
+// T_{i+1} (R starts at the background), and T_f the final transmittance:
+//   dL/dc_i      = alpha_i T_i dL/dC
+//   dL/dalpha_i  = T_i [ (c_i - R_i) . dL/dC + (d_i - Rd_i) dL/dD ] + T_f/(1-alpha_i) dL/dA
+//   R_{i-1}      = alpha_i c_i + (1 - alpha_i) R_i       (same for depth, Rd starts at 0)
+// and alpha = min(0.99, o G), G = exp(power): dL/do = G dL/dalpha and dL/dpower =
+// o G dL/dalpha where the clamp is inactive (both 0 where o G > 0.99).
+// Each pixel walks its tile's list from its last contributor back to the front,
+// recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final T (no per-pair state is
+// kept by the forward).  All lanes of a warp visit the same list entry at the same step,
+// so the per-Gaussian contributions of the warp's 32 pixels are summed with shuffles and
+// added to a packed accumulator by one lane (warp-aggregated atomics, three 16-byte
+// vector atomics per Gaussian and warp).  A final pass scales and scatters the
+// accumulator into the ABI's gradient arrays.
+#include "bgs_internal.cuh"
+
+namespace bgs {
+
+constexpr unsigned kFullB = 0xffffffffu;
+constexpr int kBwdWarps = 8;
+
+struct PixState {
+    float T, Tf, g0, g1, g2, gD, gA, R0, R1, R2, Rd;
+    int nc;
+};
+
+__device__ __forceinline__ PixState load_pixel(const BwdArgs &a, int px, int py, bool inside) {
+    PixState s;
+    if (inside) {
+        const long long HW = (long long)a.W * a.H;
+        const long long pid = (long long)py * a.W + px;
+        s.T = a.final_T[pid];
+        s.nc = a.n_contrib[pid];
+        s.g0 = a.dL_dcolor[pid];
+        s.g1 = a.dL_dcolor[HW + pid];
+        s.g2 = a.dL_dcolor[2 * HW + pid];
+        s.gD = a.dL_ddepth ? a.dL_ddepth[pid] : 0.f;
+        s.gA = a.dL_dalpha ? a.dL_dalpha[pid] : 0.f;
+    } else {
+        s.T = 1.f;
+        s.nc = 0;
+        s.g0 = s.g1 = s.g2 = s.gD = s.gA = 0.f;
+    }
+    s.Tf = s.T;
+    s.R0 = a.bg[0];
+    s.R1 = a.bg[1];
+    s.R2 = a.bg[2];
+    s.Rd = 0.f;
+    return s;
+}
+
+// One (pixel, entry) step of the backward walk.  Returns the 10 gradient contributions
+// (zero when the pair is skipped) in v[]:
+//   v0 = dL/dpower (2 qa dx + qb dy), v1 = dL/dpower (2 qc dy + qb dx),
+//   v2 = dL/dpower dx^2, v3 = dL/dpower dx dy, v4 = dL/dpower dy^2,
+//   v5 = dL/do, v6..8 = dL/dc, v9 = dL/d(depth)
+__device__ __forceinline__ bool pair_backward(const Rec &r, float pxf, float pyf, bool active, PixState &s,
+                                              float v[10]) {
+    float dx, dy, G;
+    const float p2 = pair_power2(r.a, r.b.x, pxf, pyf, dx, dy);
+    const float al = pair_alpha(p2, r.b.y, G);
+    const bool valid = active && p2 <= 0.f && al >= kAlphaMin;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) v[k] = 0.f;
+    if (valid) {
+        const float om = 1.f - al;
+        const float io = 1.f / om;
+        s.T = s.T * io;  // T_i
+        const float w = al * s.T;
+        v[6] = w * s.g0;
+        v[7] = w * s.g1;
+        v[8] = w * s.g2;
+        v[9] = w * s.gD;
+        const float dLda = s.T * ((r.c.x - s.R0) * s.g0 + (r.c.y - s.R1) * s.g1 + (r.c.z - s.R2) * s.g2 +
+                                  (r.b.z - s.Rd) * s.gD) +
+                           s.Tf * io * s.gA;
+        s.R0 = al * r.c.x + om * s.R0;
+        s.R1 = al * r.c.y + om * s.R1;
+        s.R2 = al * r.c.z + om * s.R2;
+        s.Rd = al * r.b.z + om * s.Rd;
+        const float o = r.b.y;
+        if (o * G <= kAlphaMax) {
+            const float gp = o * G * dLda;  // dL/dpower
+            v[0] = gp * (2.f * r.a.z * dx + r.a.w * dy);
+            v[1] = gp * (2.f * r.b.x * dy + r.a.w * dx);
+            v[2] = gp * dx * dx;
+            v[3] = gp * dx * dy;
+            v[4] = gp * dy * dy;
+            v[5] = G * dLda;
+        }
+    }
+    return valid;
+}
+
+__device__ __forceinline__ void warp_accumulate(float v[10], float4 *acc, uint32_t g, int lane) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFullB, v[k], o);
+    }
+    if (lane == 0) {
+        float4 *dst = acc + 3ull * g;
+        atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
+        atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
+        atomicAdd(dst + 2, make_float4(v[8], v[9], 0.f, 0.f));
+    }
+}
+
+__device__ __forceinline__ Rec load_rec_bwd(const BwdArgs &a, uint32_t j) {
+    const uint32_t g = a.point_list[j];
+    Rec r;
+    if ((long long)g >= a.N) {
+        raise_check(a.ctrl, BGS_CHECK_INDEX);
+        r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+        r.b = r.a;
+        r.c = make_float4(0.f, 0.f, 0.f, __uint_as_float(0u));
+        return r;
+    }
+    r = a.recs[g];
+    r.c.w = __uint_as_float(g);
+    return r;
+}
+
+__device__ __forceinline__ uint2 load_range_bwd(const BwdArgs &a, int tile) {
+    uint2 rg = a.ranges[tile];
+    if (rg.y < rg.x || (long long)rg.y > a.num_entries) {
+        raise_check(a.ctrl, BGS_CHECK_RANGE);
+        rg = make_uint2(0, 0);
+    }
+    return rg;
+}
+
+// =====================================================================================
+// plain pixel-wise static backward: one block per tile, block-wide staging
+// =====================================================================================
+__global__ void __launch_bounds__(1024) k_backward_static(BwdArgs a) {
+    extern __shared__ Rec srec[];
+    __shared__ int s_max;
+    const int nthreads = blockDim.x, tid = threadIdx.x, lane = tid & 31;
+    const int tile = blockIdx.x;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int px = tx * a.tile_w + tid % a.tile_w, py = ty * a.tile_h + tid / a.tile_w;
+    const bool inside = px < a.W && py < a.H;
+    uint2 rg = a.ranges[tile];
+    if (rg.y < rg.x || (long long)rg.y > a.num_entries) {
+        if (tid == 0) raise_check(a.ctrl, BGS_CHECK_RANGE);
+        rg = make_uint2(0, 0);
+    }
+    PixState s = load_pixel(a, px, py, inside);
+    if (s.nc > (int)(rg.y - rg.x)) s.nc = (int)(rg.y - rg.x);
+    if (tid == 0) s_max = 0;
+    __syncthreads();
+    atomicMax(&s_max, s.nc);
+    __syncthreads();
+    const uint32_t hi = rg.x + (uint32_t)s_max;
+    const float pxf = (float)px, pyf = (float)py;
+    for (uint32_t top = hi; top > rg.x; top -= min((uint32_t)nthreads, top - rg.x)) {
+        const uint32_t lo = top - min((uint32_t)nthreads, top - rg.x);
+        const int cnt = (int)(top - lo);
+        __syncthreads();
+        if (tid < cnt) {
+            const uint32_t j = top - 1 - tid;
+            const uint32_t g = a.point_list[j];
+            Rec r;
+            if ((long long)g < a.N) {
+                r = make_rec(a.means2D, a.conic_opacity, a.colors, a.depths, g);
+                r.c.w = __uint_as_float(g);
+            } else {
+                raise_check(a.ctrl, BGS_CHECK_INDEX);
+                r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+                r.b = r.a;
+                r.c = r.a;
+            }
+            srec[tid] = r;
+        }
+        __syncthreads();
+        for (int k = 0; k < cnt; ++k) {
+            const Rec r = srec[k];
+            const int pos = (int)(top - 1 - k - rg.x);
+            float v[10];
+            const bool valid = pair_backward(r, pxf, pyf, pos < s.nc, s, v);
+            if (__any_sync(kFullB, valid)) warp_accumulate(v, a.grad_acc, __float_as_uint(r.c.w), lane);
+        }
+    }
+}
+
+cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s) {
+    const int threads = a.tile_w * a.tile_h;
+    const int tiles = a.tiles_x * a.tiles_y;
+    if (tiles == 0) return cudaSuccess;
+    k_backward_static<<<tiles, threads, sizeof(Rec) * threads, s>>>(a);
+    return cudaGetLastError();
+}
+
+// =====================================================================================
+// balanced persistent backward: warps pull pixel-wise items (8x4 sub-blocks)
+// =====================================================================================
+__device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int sub, Rec *buf, int lane) {
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int x0 = tx * a.tile_w, y0 = ty * a.tile_h;
+    const int vw = min(a.tile_w, a.W - x0), vh = min(a.tile_h, a.H - y0);
+    const int cxs = (vw + 7) >> 3;
+    const int sx = sub % cxs, sy = sub / cxs;
+    const int px = x0 + sx * 8 + (lane & 7), py = y0 + sy * 4 + (lane >> 3);
+    const bool inside = px < x0 + vw && py < y0 + vh;
+    const uint2 rg = load_range_bwd(a, tile);
+    PixState s = load_pixel(a, px, py, inside);
+    if (s.nc > (int)(rg.y - rg.x)) s.nc = (int)(rg.y - rg.x);
+    const int maxnc = __reduce_max_sync(kFullB, s.nc);
+    const uint32_t hi = rg.x + (uint32_t)maxnc;
+    const float pxf = (float)px, pyf = (float)py;
+    for (uint32_t top = hi; top > rg.x;) {
+        const uint32_t lo = top - min(32u, top - rg.x);
+        const int cnt = (int)(top - lo);
+        __syncwarp();
+        if (lane < cnt) buf[lane] = load_rec_bwd(a, top - 1 - lane);
+        __syncwarp();
+        for (int k = 0; k < cnt; ++k) {
+            const Rec r = buf[k];
+            const int pos = (int)(top - 1 - k - rg.x);
+            float v[10];
+            const bool valid = pair_backward(r, pxf, pyf, pos < s.nc, s, v);
+            if (__any_sync(kFullB, valid)) warp_accumulate(v, a.grad_acc, __float_as_uint(r.c.w), lane);
+        }
+        top = lo;
+    }
+}
+
+__global__ void __launch_bounds__(kBwdWarps * 32) k_backward_balanced(BwdArgs a) {
+    __shared__ Rec sbuf[kBwdWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Rec *buf = sbuf[warp];
+    const unsigned num_items = a.ctrl->num_items;
+    const unsigned chunk = (unsigned)a.chunk;
+    while (true) {
+        unsigned first = 0;
+        if (lane == 0) first = atomicAdd(&a.ctrl->queue_head, chunk);
+        first = __shfl_sync(kFullB, first, 0);
+        if (first >= num_items) break;
+        const unsigned end = min(first + chunk, num_items);
+        for (unsigned it = first; it < end; ++it) {
+            const uint2 item = a.items[it];
+            bwd_pixel_item(a, (int)item.x, (int)(item.y & ~kKindGauss), buf, lane);
+        }
+    }
+}
+
+int backward_balanced_block_threads() { return kBwdWarps * 32; }
+const void *backward_balanced_kernel() { return (const void *)k_backward_balanced; }
+
+cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s) {
+    k_backward_balanced<<<grid, kBwdWarps * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---- accumulator -> ABI gradient arrays ----------------------------------------------
+__global__ void __launch_bounds__(256) k_grad_finalize(long long N, const float4 *__restrict__ acc,
+                                                       float *__restrict__ dL_dmeans2D, float *__restrict__ dL_dconic,
+                                                       float *__restrict__ dL_dopacity, float *__restrict__ dL_dcolors,
+                                                       float *__restrict__ dL_ddepths) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 a0 = acc[3 * i], a1 = acc[3 * i + 1], a2 = acc[3 * i + 2];
+    // power = ln2 * power2; d power / d mean = ln2 (2 qa dx + qb dy, 2 qc dy + qb dx);
+    // d power / d(a, b, c) = (-dx^2 / 2, -dx dy, -dy^2 / 2)
+    dL_dmeans2D[2 * i] = kLn2 * a0.x;
+    dL_dmeans2D[2 * i + 1] = kLn2 * a0.y;
+    dL_dconic[3 * i] = -0.5f * a0.z;
+    dL_dconic[3 * i + 1] = -a0.w;
+    dL_dconic[3 * i + 2] = -0.5f * a1.x;
+    dL_dopacity[i] = a1.y;
+    dL_dcolors[3 * i] = a1.z;
+    dL_dcolors[3 * i + 1] = a1.w;
+    dL_dcolors[3 * i + 2] = a2.x;
+    if (dL_ddepths) dL_ddepths[i] = a2.y;
+}
+
+cudaError_t launch_grad_finalize(long long N, const float4 *acc, float *dL_dmeans2D, float *dL_dconic,
+                                 float *dL_dopacity, float *dL_dcolors, float *dL_ddepths, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    k_grad_finalize<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, acc, dL_dmeans2D, dL_dconic, dL_dopacity,
+                                                                 dL_dcolors, dL_ddepths);
+    return cudaGetLastError();
+}
+
+}  // namespace bgs

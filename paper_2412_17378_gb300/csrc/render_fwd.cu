@@ -1,0 +1,389 @@
+// render_fwd.cu -- a4/a5: forward render kernels.
+//
+//  k_forward_static    plain pixel-wise kernel on a static grid (one block per tile, one
+//                      thread per pixel, block-wide staging of the tile's records in
+//                      shared memory) -- the paper's "naive renderCUDA" (Algorithm 4)
+//                      with the shared-memory staging of features and depths of
+//                      Sec. 5.2.2.  It is the baseline the balanced kernel is timed against.
+//  k_forward_balanced  persistent kernel (Sec. 4.1's inter-block dynamic distribution,
+//                      taken down to warp granularity): every warp pulls work items from
+//                      a device atomic queue.  An item is either
+//                        - pixel-wise: 32 pixels (an 8x4 sub-block of a tile), one per
+//                          lane, walking the tile's list through a warp-private shared
+//                          memory window of 32 records; or
+//                        - Gaussian-wise (Sec. 4.2, Algorithm 6, fine-grained per
+//                          Sec. 4.3): P pixels of a tile processed one after another by
+//                          the whole warp, lanes splitting the list 32 entries at a time
+//                          and combining transmittance with a shuffle prefix product.
+//
+// Both evaluate each (pixel, entry) pair with the same code (pair_power2 / pair_alpha),
+// so skip and stop decisions of the forward and backward kernels agree bit for bit.
+// Results of all kernels equal the sequential rule of Algorithm 5 up to float32
+// reassociation of the transmittance product (Sec. 4: "without any precision loss").
+#include "bgs_internal.cuh"
+
+namespace bgs {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void write_pixel(const FwdArgs &a, int px, int py, float T, float c0, float c1, float c2,
+                                            float D, float A, int last, int neval) {
+    const long long HW = (long long)a.W * a.H;
+    const long long pid = (long long)py * a.W + px;
+    a.out_color[pid] = c0 + T * a.bg[0];
+    a.out_color[HW + pid] = c1 + T * a.bg[1];
+    a.out_color[2 * HW + pid] = c2 + T * a.bg[2];
+    a.out_depth[pid] = D;
+    a.out_alpha[pid] = A;
+    a.final_T[pid] = T;
+    a.n_contrib[pid] = last;
+    if (a.n_eval) a.n_eval[pid] = neval;
+}
+
+// Validated tile range: an out-of-bounds span raises BGS_CHECK_RANGE and renders empty.
+__device__ __forceinline__ uint2 load_range(const FwdArgs &a, int tile) {
+    uint2 rg = a.ranges[tile];
+    if (rg.y < rg.x || (long long)rg.y > a.num_entries) {
+        raise_check(a.ctrl, BGS_CHECK_RANGE);
+        rg = make_uint2(0, 0);
+    }
+    return rg;
+}
+
+// Record of list entry j; an index >= N raises BGS_CHECK_INDEX and yields a transparent record.
+__device__ __forceinline__ Rec load_rec(const FwdArgs &a, uint32_t j) {
+    const uint32_t g = a.point_list[j];
+    if ((long long)g >= a.N) {
+        raise_check(a.ctrl, BGS_CHECK_INDEX);
+        Rec r;
+        r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+        r.b = make_float4(0.f, 0.f, 0.f, 0.f);
+        r.c = r.b;
+        return r;
+    }
+    return a.recs[g];
+}
+
+// =====================================================================================
+// plain pixel-wise static kernel
+// =====================================================================================
+__global__ void __launch_bounds__(1024) k_forward_static(FwdArgs a) {
+    extern __shared__ Rec srec[];
+    const int nthreads = blockDim.x;
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int px = tx * a.tile_w + tid % a.tile_w, py = ty * a.tile_h + tid / a.tile_w;
+    const bool inside = px < a.W && py < a.H;
+    uint2 rg = a.ranges[tile];
+    if (rg.y < rg.x || (long long)rg.y > a.num_entries) {
+        if (tid == 0) raise_check(a.ctrl, BGS_CHECK_RANGE);
+        rg = make_uint2(0, 0);
+    }
+    const float pxf = (float)px, pyf = (float)py;
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, D = 0.f, A = 0.f;
+    int last = 0, neval = (int)(rg.y - rg.x), nacc = 0;
+    bool done = !inside;
+    for (uint32_t base = rg.x; base < rg.y; base += nthreads) {
+        if (__syncthreads_count(done) == nthreads) break;
+        const uint32_t j = base + tid;
+        if (j < rg.y) {
+            const uint32_t g = a.point_list[j];
+            if ((long long)g < a.N) {
+                srec[tid] = make_rec(a.means2D, a.conic_opacity, a.colors, a.depths, g);
+            } else {
+                raise_check(a.ctrl, BGS_CHECK_INDEX);
+                srec[tid].b = make_float4(0.f, 0.f, 0.f, 0.f);
+                srec[tid].a = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        const int cnt = min(nthreads, (int)(rg.y - base));
+        for (int k = 0; !done && k < cnt; ++k) {
+            const float4 ra = srec[k].a;
+            const float4 rb = srec[k].b;
+            float dx, dy, G;
+            const float p2 = pair_power2(ra, rb.x, pxf, pyf, dx, dy);
+            const float al = pair_alpha(p2, rb.y, G);
+            if (p2 > 0.f || al < kAlphaMin) continue;
+            const float tt = T * (1.f - al);
+            if (tt < kTMin) {
+                done = true;
+                neval = (int)(base + k + 1 - rg.x);
+                break;
+            }
+            const float4 rc = srec[k].c;
+            const float w = al * T;
+            c0 += w * rc.x;
+            c1 += w * rc.y;
+            c2 += w * rc.z;
+            D += w * rb.z;
+            A += w;
+            T = tt;
+            last = (int)(base + k + 1 - rg.x);
+            ++nacc;
+        }
+    }
+    if (inside) write_pixel(a, px, py, T, c0, c1, c2, D, A, last, neval);
+    // evaluated / contributing pair counters
+    unsigned long long e = inside ? (unsigned long long)neval : 0ull, c = inside ? (unsigned long long)nacc : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(kFull, e, o);
+        c += __shfl_xor_sync(kFull, c, o);
+    }
+    if ((tid & 31) == 0) {
+        atomicAdd(&a.ctrl->eval_pairs, e);
+        atomicAdd(&a.ctrl->contrib_pairs, c);
+    }
+}
+
+cudaError_t launch_forward_static(const FwdArgs &a, cudaStream_t s) {
+    const int threads = a.tile_w * a.tile_h;
+    const int tiles = a.tiles_x * a.tiles_y;
+    if (tiles == 0) return cudaSuccess;
+    const size_t smem = sizeof(Rec) * threads;
+    k_forward_static<<<tiles, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// =====================================================================================
+// balanced persistent kernel
+// =====================================================================================
+constexpr int kWarpsPerBlock = 8;
+
+struct TileGeom {
+    int x0, y0, vw, vh;  // tile origin and the part of it inside the image
+};
+
+__device__ __forceinline__ TileGeom tile_geom(const FwdArgs &a, int tile) {
+    TileGeom t;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    t.x0 = tx * a.tile_w;
+    t.y0 = ty * a.tile_h;
+    t.vw = min(a.tile_w, a.W - t.x0);
+    t.vh = min(a.tile_h, a.H - t.y0);
+    return t;
+}
+
+// Pixel-wise item: 32 pixels of an 8x4 sub-block, lane = pixel.
+__device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, Rec *buf, int lane,
+                                           unsigned long long &st_eval, unsigned long long &st_acc) {
+    const TileGeom tg = tile_geom(a, tile);
+    const int cxs = (tg.vw + 7) >> 3;
+    const int sx = sub % cxs, sy = sub / cxs;
+    const int px = tg.x0 + sx * 8 + (lane & 7), py = tg.y0 + sy * 4 + (lane >> 3);
+    const bool inside = px < tg.x0 + tg.vw && py < tg.y0 + tg.vh;
+    const uint2 rg = load_range(a, tile);
+    const float pxf = (float)px, pyf = (float)py;
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, D = 0.f, A = 0.f;
+    int last = 0, neval = (int)(rg.y - rg.x), nacc = 0;
+    bool done = !inside;
+    for (uint32_t base = rg.x; base < rg.y; base += 32) {
+        if (__all_sync(kFull, done)) break;
+        const uint32_t j = base + lane;
+        __syncwarp();
+        if (j < rg.y) buf[lane] = load_rec(a, j);
+        __syncwarp();
+        const int cnt = min(32, (int)(rg.y - base));
+        for (int k = 0; k < cnt; ++k) {
+            const float4 ra = buf[k].a;
+            const float4 rb = buf[k].b;
+            float dx, dy, G;
+            const float p2 = pair_power2(ra, rb.x, pxf, pyf, dx, dy);
+            const float al = pair_alpha(p2, rb.y, G);
+            if (!done && p2 <= 0.f && al >= kAlphaMin) {
+                const float tt = T * (1.f - al);
+                if (tt < kTMin) {
+                    done = true;
+                    neval = (int)(base + k + 1 - rg.x);
+                } else {
+                    const float4 rc = buf[k].c;
+                    const float w = al * T;
+                    c0 += w * rc.x;
+                    c1 += w * rc.y;
+                    c2 += w * rc.z;
+                    D += w * rb.z;
+                    A += w;
+                    T = tt;
+                    last = (int)(base + k + 1 - rg.x);
+                    ++nacc;
+                }
+            }
+        }
+    }
+    if (inside) {
+        write_pixel(a, px, py, T, c0, c1, c2, D, A, last, neval);
+        st_eval += (unsigned long long)neval;
+        st_acc += (unsigned long long)nacc;
+    }
+}
+
+// Gaussian-wise item: P pixels, lanes split the list 32 entries at a time.
+template <int P>
+__device__ __forceinline__ void gauss_item(const FwdArgs &a, int tile, int sub, int lane,
+                                           unsigned long long &st_eval, unsigned long long &st_acc) {
+    const TileGeom tg = tile_geom(a, tile);
+    const int npix = tg.vw * tg.vh;
+    const uint2 rg = load_range(a, tile);
+    const int n = (int)(rg.y - rg.x);
+    float pxf[P], pyf[P], T[P], c0[P], c1[P], c2[P], D[P], A[P];
+    int last[P], neval[P], nacc[P];
+    bool done[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int q = sub * P + p;
+        const bool ok = q < npix;
+        const int qq = ok ? q : 0;
+        pxf[p] = (float)(tg.x0 + qq % tg.vw);
+        pyf[p] = (float)(tg.y0 + qq / tg.vw);
+        T[p] = 1.f;
+        c0[p] = c1[p] = c2[p] = D[p] = A[p] = 0.f;
+        last[p] = 0;
+        neval[p] = n;
+        nacc[p] = 0;
+        done[p] = !ok;
+    }
+    for (uint32_t base = rg.x; base < rg.y; base += 32) {
+        bool all_done = true;
+#pragma unroll
+        for (int p = 0; p < P; ++p) all_done = all_done && done[p];
+        if (all_done) break;
+        const uint32_t j = base + lane;
+        const bool inb = j < rg.y;
+        Rec r;
+        if (inb) {
+            r = load_rec(a, j);
+        } else {
+            r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+            r.b = r.a;
+            r.c = r.a;
+        }
+        const int pos0 = (int)(base - rg.x);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (done[p]) continue;  // warp-uniform
+            float dx, dy, G;
+            const float p2 = pair_power2(r.a, r.b.x, pxf[p], pyf[p], dx, dy);
+            const float al = pair_alpha(p2, r.b.y, G);
+            const bool valid = inb && p2 <= 0.f && al >= kAlphaMin;
+            const unsigned vmask = __ballot_sync(kFull, valid);
+            if (vmask == 0u) continue;  // no lane contributes: skip the scan (Algorithm 6's all-invalid test)
+            // inclusive prefix product of (1 - alpha) over the lanes (skipped lanes contribute 1)
+            float incl = valid ? 1.f - al : 1.f;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const float v = __shfl_up_sync(kFull, incl, off);
+                if (lane >= off) incl *= v;
+            }
+            float excl = __shfl_up_sync(kFull, incl, 1);
+            if (lane == 0) excl = 1.f;
+            const float Tp = T[p];
+            const float tt = Tp * incl;  // transmittance after this lane's entry
+            // exact early stop: the first valid lane whose T' falls below 1e-4 stops the pixel
+            // and is not accumulated; the lanes before it are.
+            const unsigned smask = __ballot_sync(kFull, valid && tt < kTMin);
+            const int kstop = smask ? __ffs(smask) - 1 : 32;
+            const unsigned below = kstop >= 32 ? kFull : ((1u << kstop) - 1u);
+            const unsigned amask = vmask & below;
+            if (valid && lane < kstop) {
+                const float w = al * (Tp * excl);
+                c0[p] += w * r.c.x;
+                c1[p] += w * r.c.y;
+                c2[p] += w * r.c.z;
+                D[p] += w * r.b.z;
+                A[p] += w;
+            }
+            const float tnew = __shfl_sync(kFull, tt, kstop > 0 ? kstop - 1 : 0);
+            if (kstop > 0) T[p] = tnew;
+            if (amask) {
+                last[p] = pos0 + (32 - __clz(amask));
+                nacc[p] += __popc(amask);
+            }
+            if (smask) {
+                done[p] = true;
+                neval[p] = pos0 + kstop + 1;
+            }
+        }
+    }
+    // combine the lanes' partial sums and write the P pixels
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c0[p] += __shfl_xor_sync(kFull, c0[p], o);
+            c1[p] += __shfl_xor_sync(kFull, c1[p], o);
+            c2[p] += __shfl_xor_sync(kFull, c2[p], o);
+            D[p] += __shfl_xor_sync(kFull, D[p], o);
+            A[p] += __shfl_xor_sync(kFull, A[p], o);
+        }
+        const int q = sub * P + p;
+        if (q < npix) {
+            if (lane == p) write_pixel(a, (int)pxf[p], (int)pyf[p], T[p], c0[p], c1[p], c2[p], D[p], A[p], last[p], neval[p]);
+            if (lane == 0) {
+                st_eval += (unsigned long long)neval[p];
+                st_acc += (unsigned long long)nacc[p];
+            }
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_balanced(FwdArgs a) {
+    __shared__ Rec sbuf[kWarpsPerBlock][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Rec *buf = sbuf[warp];
+    const unsigned num_items = a.ctrl->num_items;
+    const unsigned chunk = (unsigned)a.chunk;
+    unsigned long long st_eval = 0, st_acc = 0, st_items = 0;
+    while (true) {
+        unsigned first = 0;
+        if (lane == 0) first = atomicAdd(&a.ctrl->queue_head, chunk);
+        first = __shfl_sync(kFull, first, 0);
+        if (first >= num_items) break;
+        const unsigned end = min(first + chunk, num_items);
+        for (unsigned it = first; it < end; ++it) {
+            const uint2 item = a.items[it];
+            const int sub = (int)(item.y & ~kKindGauss);
+            if (item.y & kKindGauss)
+                gauss_item<P>(a, (int)item.x, sub, lane, st_eval, st_acc);
+            else
+                pixel_item(a, (int)item.x, sub, buf, lane, st_eval, st_acc);
+            ++st_items;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        st_eval += __shfl_xor_sync(kFull, st_eval, o);
+        st_acc += __shfl_xor_sync(kFull, st_acc, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&a.ctrl->eval_pairs, st_eval);
+        atomicAdd(&a.ctrl->contrib_pairs, st_acc);
+        atomicAdd(&a.ctrl->items_done, st_items);
+    }
+}
+
+int forward_balanced_block_threads() { return kWarpsPerBlock * 32; }
+const void *forward_balanced_kernel(int gw_pixels) {
+    switch (gw_pixels) {
+        case 1: return (const void *)k_forward_balanced<1>;
+        case 2: return (const void *)k_forward_balanced<2>;
+        case 4: return (const void *)k_forward_balanced<4>;
+        case 8: return (const void *)k_forward_balanced<8>;
+        default: return nullptr;
+    }
+}
+
+cudaError_t launch_forward_balanced(const FwdArgs &a, int grid, cudaStream_t s) {
+    const int threads = kWarpsPerBlock * 32;
+    switch (a.gw_pixels) {
+        case 1: k_forward_balanced<1><<<grid, threads, 0, s>>>(a); break;
+        case 2: k_forward_balanced<2><<<grid, threads, 0, s>>>(a); break;
+        case 4: k_forward_balanced<4><<<grid, threads, 0, s>>>(a); break;
+        case 8: k_forward_balanced<8><<<grid, threads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace bgs

@@ -1,0 +1,94 @@
+// worklist.cu -- a3: per-tile load statistics and the work list of the persistent kernels.
+//
+// The paper's task pool (Sec. 4.1) holds whole tiles; its fine-grained variant
+// (Sec. 4.3) splits each tile into 4-pixel tasks, and its selector (Sec. 4.4) chooses
+// between the Gaussian-wise and the pixel-wise kernel.  Here the choice is made per
+// tile from its list length n (the paper names "the Gaussians of a tile" as the key
+// load-balance metric, Sec. 4.4):
+//   n >  heavy_threshold -> Gaussian-wise items of P pixels (one warp each),
+//   n <= heavy_threshold -> pixel-wise items of 32 pixels (an 8x4 sub-block, one warp).
+// Items of heavier tiles are queued first (longest-processing-time order) so the long
+// items start early and the light ones fill the tail.
+#include "bgs_internal.cuh"
+
+namespace bgs {
+
+__device__ __forceinline__ bool tile_is_gauss(int mode, int heavy_threshold, uint32_t n) {
+    return mode == BGS_MODE_GAUSSIAN || (mode == BGS_MODE_AUTO && n > (uint32_t)heavy_threshold);
+}
+
+__device__ __forceinline__ uint32_t tile_item_count(int t, uint32_t n, int W, int H, int tile_w, int tile_h,
+                                                    int tiles_x, int mode, int heavy_threshold, int gw_pixels) {
+    const int tx = t % tiles_x, ty = t / tiles_x;
+    const int vw = min(tile_w, W - tx * tile_w), vh = min(tile_h, H - ty * tile_h);
+    if (tile_is_gauss(mode, heavy_threshold, n)) return (uint32_t)((vw * vh + gw_pixels - 1) / gw_pixels);
+    return (uint32_t)(((vw + 7) >> 3) * ((vh + 3) >> 2));
+}
+
+__global__ void k_tile_counts(const uint2 *__restrict__ ranges, int num_tiles, uint32_t *__restrict__ tile_key,
+                              uint32_t *__restrict__ tile_idx) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= num_tiles) return;
+    const uint2 rg = ranges[t];
+    tile_key[t] = rg.y >= rg.x ? rg.y - rg.x : 0u;
+    tile_idx[t] = (uint32_t)t;
+}
+
+cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int, int, int, int, int, int, int, int,
+                               uint32_t *tile_key, uint32_t *tile_idx, cudaStream_t s) {
+    if (num_tiles == 0) return cudaSuccess;
+    k_tile_counts<<<(num_tiles + 255) / 256, 256, 0, s>>>(ranges, num_tiles, tile_key, tile_idx);
+    return cudaGetLastError();
+}
+
+__global__ void k_gather_counts(const uint32_t *__restrict__ order, int num_tiles, const uint2 *__restrict__ ranges,
+                                int W, int H, int tile_w, int tile_h, int tiles_x, int mode, int heavy_threshold,
+                                int gw_pixels, uint32_t *__restrict__ counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= num_tiles) return;
+    const int t = (int)order[i];
+    const uint2 rg = ranges[t];
+    const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
+    counts[i] = tile_item_count(t, n, W, H, tile_w, tile_h, tiles_x, mode, heavy_threshold, gw_pixels);
+}
+
+cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, int W, int H, int tile_w,
+                                 int tile_h, int tiles_x, int mode, int heavy_threshold, int gw_pixels,
+                                 uint32_t *counts, cudaStream_t s) {
+    if (num_tiles == 0) return cudaSuccess;
+    k_gather_counts<<<(num_tiles + 255) / 256, 256, 0, s>>>(order, num_tiles, ranges, W, H, tile_w, tile_h, tiles_x,
+                                                            mode, heavy_threshold, gw_pixels, counts);
+    return cudaGetLastError();
+}
+
+// One warp per tile writes the tile's items at its offset; the last tile also publishes
+// the total and resets the queue cursor.
+__global__ void k_emit_items(const uint32_t *__restrict__ order, const uint32_t *__restrict__ counts,
+                             const uint32_t *__restrict__ offsets, int num_tiles, const uint2 *__restrict__ ranges,
+                             int mode, int heavy_threshold, uint2 *__restrict__ items, DevCtrl *ctrl) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= num_tiles) return;
+    const uint32_t t = order[i];
+    const uint2 rg = ranges[t];
+    const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
+    const uint32_t kind = tile_is_gauss(mode, heavy_threshold, n) ? kKindGauss : 0u;
+    const uint32_t c = counts[i], off = offsets[i];
+    for (uint32_t q = lane; q < c; q += 32) items[off + q] = make_uint2(t, kind | q);
+    if (i == num_tiles - 1 && lane == 0) {
+        ctrl->num_items = off + c;
+        ctrl->queue_head = 0u;
+    }
+}
+
+cudaError_t launch_emit_items(const uint32_t *order, const uint32_t *counts, const uint32_t *offsets, int num_tiles,
+                              const uint2 *ranges, int mode, int heavy_threshold, uint2 *items, DevCtrl *ctrl,
+                              cudaStream_t s) {
+    if (num_tiles == 0) return cudaSuccess;
+    const long long threads = (long long)num_tiles * 32;
+    k_emit_items<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(order, counts, offsets, num_tiles, ranges, mode,
+                                                                   heavy_threshold, items, ctrl);
+    return cudaGetLastError();
+}
+
+}  // namespace bgs

@@ -1,0 +1,282 @@
+"""Thin Python binding of the C ABI (include/bgs.h) plus a torch.autograd.Function.
+
+Every function here only checks and marshals arguments (device pointers of CUDA
+tensors, the current CUDA stream) and calls the library; every step of the render path
+runs in the library's kernels.  PyTorch provides device memory and streams.  The names
+follow the C entry points: ``preprocess`` -> bgs_preprocess, ``bin_and_sort`` ->
+bgs_bin_and_sort, ``render_forward`` / ``render_backward`` -> bgs_render_forward /
+bgs_render_backward.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import MODES, BgsError, check
+
+__all__ = ["Plan", "camera_struct", "preprocess", "bin_and_sort", "render_forward", "render_backward",
+           "RenderFunction", "render", "probe_pipe_rates", "debug_exp2", "BgsError", "MODES"]
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _req(t: torch.Tensor, name: str, dtype, shape=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (there is no CPU path)")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+class Plan:
+    """Owns a bgs_plan: tuning knobs and the library-managed workspace."""
+
+    def __init__(self, heavy_threshold: int = 512, gw_pixels: int = 4, queue_chunk: int = 1,
+                 blocks_per_sm: int = 0, lpt_order: bool = True, device=None):
+        self._lib = _lib.load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = torch.device("cuda", device if isinstance(device, int) else torch.device(device).index or 0)
+        d = _lib.PlanDesc()
+        self._lib.bgs_plan_desc_default(ctypes.byref(d))
+        d.heavy_threshold, d.gw_pixels, d.queue_chunk = heavy_threshold, gw_pixels, queue_chunk
+        d.blocks_per_sm, d.lpt_order, d.device = blocks_per_sm, int(bool(lpt_order)), self.device.index
+        h = ctypes.c_void_p()
+        check(self._lib.bgs_plan_create(ctypes.byref(d), ctypes.byref(h)), "bgs_plan_create")
+        self.handle = h
+
+    def desc(self) -> dict:
+        d = _lib.PlanDesc()
+        check(self._lib.bgs_plan_get(self.handle, ctypes.byref(d)), "bgs_plan_get")
+        return {k: getattr(d, k) for k, _ in _lib.PlanDesc._fields_}
+
+    def set(self, **kw):
+        d = _lib.PlanDesc()
+        check(self._lib.bgs_plan_get(self.handle, ctypes.byref(d)), "bgs_plan_get")
+        for k, v in kw.items():
+            setattr(d, k, int(v))
+        check(self._lib.bgs_plan_set(self.handle, ctypes.byref(d)), "bgs_plan_set")
+
+    @property
+    def num_sms(self) -> int:
+        return self._lib.bgs_plan_num_sms(self.handle)
+
+    def reserve(self, max_gaussians: int, max_entries: int, max_tiles: int, max_pixels: int):
+        check(self._lib.bgs_plan_reserve(self.handle, max_gaussians, max_entries, max_tiles, max_pixels),
+              "bgs_plan_reserve")
+
+    def check(self):
+        """Raises BgsError if a device-side check tripped (synchronises the stream)."""
+        check(self._lib.bgs_check(self.handle, _stream(self.device)), "bgs_check")
+
+    def stats(self) -> dict:
+        s = _lib.Stats()
+        check(self._lib.bgs_plan_stats(self.handle, ctypes.byref(s), _stream(self.device)), "bgs_plan_stats")
+        return {k: getattr(s, k) for k, _ in _lib.Stats._fields_}
+
+    def timing(self, enable: bool):
+        """Turns CUDA-event timing of the render kernels on / off."""
+        check(self._lib.bgs_plan_timing(self.handle, int(bool(enable))), "bgs_plan_timing")
+
+    def kernel_ms(self):
+        """(forward ms, forward launches, backward ms, backward launches) recorded since the last call."""
+        f, b = ctypes.c_double(0), ctypes.c_double(0)
+        nf, nb = ctypes.c_int32(0), ctypes.c_int32(0)
+        check(self._lib.bgs_plan_kernel_ms(self.handle, ctypes.byref(f), ctypes.byref(nf), ctypes.byref(b),
+                                           ctypes.byref(nb)), "bgs_plan_kernel_ms")
+        return f.value, nf.value, b.value, nb.value
+
+    def reset_stats(self):
+        check(self._lib.bgs_plan_reset_stats(self.handle, _stream(self.device)), "bgs_plan_reset_stats")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self._lib.bgs_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def camera_struct(cam: dict) -> _lib.Camera:
+    c = _lib.Camera()
+    c.width, c.height = int(cam["W"]), int(cam["H"])
+    c.fx, c.fy, c.cx, c.cy = float(cam["fx"]), float(cam["fy"]), float(cam["cx"]), float(cam["cy"])
+    V = np.asarray(cam["viewmat"], np.float64).reshape(16)
+    for k in range(16):
+        c.viewmat[k] = float(V[k])
+    c.near_plane = float(cam.get("near", 0.2))
+    c.lowpass = float(cam.get("lowpass", 0.3))
+    return c
+
+
+def preprocess(plan: Plan, means3D, log_scales, quats, opacities, cam: dict, tile=(16, 16), out=None):
+    """bgs_preprocess: returns dict(means2D [N,2], conic_opacity [N,4], depths [N], radii [N] int32,
+    tiles_touched [N] int32 holding uint32)."""
+    N = means3D.shape[0]
+    _req(means3D, "means3D", torch.float32, (N, 3))
+    _req(log_scales, "log_scales", torch.float32, (N, 3))
+    _req(quats, "quats", torch.float32, (N, 4))
+    _req(opacities, "opacities", torch.float32, (N,))
+    dev = means3D.device
+    if out is None:
+        out = dict(means2D=torch.empty((N, 2), device=dev), conic_opacity=torch.empty((N, 4), device=dev),
+                   depths=torch.empty(N, device=dev), radii=torch.empty(N, dtype=torch.int32, device=dev),
+                   tiles_touched=torch.empty(N, dtype=torch.int32, device=dev))
+    c = camera_struct(cam)
+    check(plan._lib.bgs_preprocess(plan.handle, N, _ptr(means3D), _ptr(log_scales), _ptr(quats), _ptr(opacities),
+                                   ctypes.byref(c), tile[0], tile[1], _ptr(out["means2D"]),
+                                   _ptr(out["conic_opacity"]), _ptr(out["depths"]), _ptr(out["radii"]),
+                                   _ptr(out["tiles_touched"]), _stream(dev)), "bgs_preprocess")
+    return out
+
+
+def bin_and_sort(plan: Plan, means2D, radii, depths, W: int, H: int, tile=(16, 16), point_list=None):
+    """bgs_bin_and_sort: returns (point_list int32 [>=K] holding uint32, ranges int32 [T,2], K).
+    Grows ``point_list`` (a torch buffer) when the entry count exceeds its capacity."""
+    N = means2D.shape[0]
+    _req(means2D, "means2D", torch.float32, (N, 2))
+    _req(radii, "radii", torch.int32, (N,))
+    _req(depths, "depths", torch.float32, (N,))
+    dev = means2D.device
+    tx, ty = (W + tile[0] - 1) // tile[0], (H + tile[1] - 1) // tile[1]
+    ranges = torch.empty((tx * ty, 2), dtype=torch.int32, device=dev)
+    if point_list is None:
+        point_list = torch.empty(max(4 * N, 1024), dtype=torch.int32, device=dev)
+    K = ctypes.c_int64(0)
+    need = ctypes.c_int64(0)
+    for _ in range(2):
+        code = plan._lib.bgs_bin_and_sort(plan.handle, N, _ptr(means2D), _ptr(radii), _ptr(depths), W, H, tile[0],
+                                          tile[1], _ptr(point_list), point_list.numel(), _ptr(ranges),
+                                          ctypes.byref(K), ctypes.byref(need), _stream(dev))
+        if code == _lib.BGS_ERR_CAPACITY and need.value > point_list.numel():
+            point_list = torch.empty(int(need.value * 1.1) + 1024, dtype=torch.int32, device=dev)
+            continue
+        check(code, "bgs_bin_and_sort")
+        break
+    return point_list, ranges, int(K.value)
+
+
+def render_forward(plan: Plan, means2D, conic_opacity, colors, depths, point_list, num_entries: int, ranges,
+                   W: int, H: int, tile=(16, 16), bg=(0.0, 0.0, 0.0), mode="auto", n_eval: bool = False, out=None):
+    """bgs_render_forward: returns dict(color [3,H,W], depth, alpha, final_T, n_contrib[, n_eval])."""
+    N = means2D.shape[0]
+    _req(means2D, "means2D", torch.float32, (N, 2))
+    _req(conic_opacity, "conic_opacity", torch.float32, (N, 4))
+    _req(colors, "colors", torch.float32, (N, 3))
+    _req(depths, "depths", torch.float32, (N,))
+    _req(point_list, "point_list", torch.int32)
+    _req(ranges, "ranges", torch.int32)
+    dev = means2D.device
+    if out is None:
+        out = dict(color=torch.empty((3, H, W), device=dev), depth=torch.empty((H, W), device=dev),
+                   alpha=torch.empty((H, W), device=dev), final_T=torch.empty((H, W), device=dev),
+                   n_contrib=torch.empty((H, W), dtype=torch.int32, device=dev))
+        if n_eval:
+            out["n_eval"] = torch.empty((H, W), dtype=torch.int32, device=dev)
+    bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    check(plan._lib.bgs_render_forward(plan.handle, N, _ptr(means2D), _ptr(conic_opacity), _ptr(colors),
+                                       _ptr(depths), _ptr(point_list), int(num_entries), _ptr(ranges), W, H, tile[0],
+                                       tile[1], bgv, m, _ptr(out["color"]), _ptr(out["depth"]), _ptr(out["alpha"]),
+                                       _ptr(out["final_T"]), _ptr(out["n_contrib"]), _ptr(out.get("n_eval")),
+                                       _stream(dev)), "bgs_render_forward")
+    return out
+
+
+def render_backward(plan: Plan, means2D, conic_opacity, colors, depths, point_list, num_entries: int, ranges,
+                    W: int, H: int, final_T, n_contrib, dL_dcolor, dL_ddepth=None, dL_dalpha=None, tile=(16, 16),
+                    bg=(0.0, 0.0, 0.0), mode="auto", out=None):
+    """bgs_render_backward: returns dict(means2D [N,2], conic [N,3], opacity [N], colors [N,3], depths [N])."""
+    N = means2D.shape[0]
+    _req(final_T, "final_T", torch.float32, (H, W))
+    _req(n_contrib, "n_contrib", torch.int32, (H, W))
+    _req(dL_dcolor, "dL_dcolor", torch.float32, (3, H, W))
+    if dL_ddepth is not None:
+        _req(dL_ddepth, "dL_ddepth", torch.float32, (H, W))
+    if dL_dalpha is not None:
+        _req(dL_dalpha, "dL_dalpha", torch.float32, (H, W))
+    dev = means2D.device
+    if out is None:
+        out = dict(means2D=torch.empty((N, 2), device=dev), conic=torch.empty((N, 3), device=dev),
+                   opacity=torch.empty(N, device=dev), colors=torch.empty((N, 3), device=dev),
+                   depths=torch.empty(N, device=dev))
+    bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    check(plan._lib.bgs_render_backward(plan.handle, N, _ptr(means2D), _ptr(conic_opacity), _ptr(colors),
+                                        _ptr(depths), _ptr(point_list), int(num_entries), _ptr(ranges), W, H,
+                                        tile[0], tile[1], bgv, m, _ptr(final_T), _ptr(n_contrib), _ptr(dL_dcolor),
+                                        _ptr(dL_ddepth), _ptr(dL_dalpha), _ptr(out["means2D"]), _ptr(out["conic"]),
+                                        _ptr(out["opacity"]), _ptr(out["colors"]), _ptr(out.get("depths")),
+                                        _stream(dev)), "bgs_render_backward")
+    return out
+
+
+class RenderFunction(torch.autograd.Function):
+    """Differentiable render of projected Gaussians: (means2D, conic_opacity, colors, depths)
+    -> (color [3,H,W], depth [H,W], alpha [H,W]).  The backward calls bgs_render_backward,
+    which recomputes the blend from the stored final T and last-contributor index."""
+
+    @staticmethod
+    def forward(ctx, means2D, conic_opacity, colors, depths, binning, plan, W, H, tile, bg, mode):
+        point_list, ranges, K = binning
+        out = render_forward(plan, means2D.contiguous(), conic_opacity.contiguous(), colors.contiguous(),
+                             depths.contiguous(), point_list, K, ranges, W, H, tile, bg, mode)
+        ctx.plan, ctx.W, ctx.H, ctx.tile, ctx.bg, ctx.mode, ctx.K = plan, W, H, tile, bg, mode, K
+        ctx.save_for_backward(means2D, conic_opacity, colors, depths, point_list, ranges, out["final_T"],
+                              out["n_contrib"])
+        ctx.mark_non_differentiable(out["final_T"], out["n_contrib"])
+        return out["color"], out["depth"], out["alpha"], out["final_T"], out["n_contrib"]
+
+    @staticmethod
+    def backward(ctx, g_color, g_depth, g_alpha, _g_T, _g_n):
+        means2D, conic_opacity, colors, depths, point_list, ranges, final_T, n_contrib = ctx.saved_tensors
+        g = render_backward(ctx.plan, means2D, conic_opacity, colors, depths, point_list, ctx.K, ranges, ctx.W,
+                            ctx.H, final_T, n_contrib,
+                            g_color.contiguous() if g_color is not None else torch.zeros_like(final_T).expand(3, -1, -1).contiguous(),
+                            None if g_depth is None else g_depth.contiguous(),
+                            None if g_alpha is None else g_alpha.contiguous(),
+                            ctx.tile, ctx.bg, ctx.mode)
+        d_conic = torch.cat([g["conic"], g["opacity"][:, None]], 1)
+        return g["means2D"], d_conic, g["colors"], g["depths"], None, None, None, None, None, None, None
+
+
+def render(plan: Plan, means2D, conic_opacity, colors, depths, binning, W, H, tile=(16, 16), bg=(0.0, 0.0, 0.0),
+           mode="auto"):
+    """Differentiable render; returns (color, depth, alpha)."""
+    color, depth, alpha, _, _ = RenderFunction.apply(means2D, conic_opacity, colors, depths, binning, plan, W, H,
+                                                     tuple(tile), tuple(bg), mode)
+    return color, depth, alpha
+
+
+def probe_pipe_rates(plan: Plan):
+    """Measured (FP32 FMA, MUFU ex2) operations per SM per clock on the plan's device."""
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    check(plan._lib.bgs_probe_pipe_rates(plan.handle, ctypes.byref(a), ctypes.byref(b), _stream(plan.device)),
+          "bgs_probe_pipe_rates")
+    return a.value, b.value
+
+
+def debug_exp2(x: torch.Tensor) -> torch.Tensor:
+    _req(x, "x", torch.float32)
+    y = torch.empty_like(x)
+    check(_lib.load().bgs_debug_exp2(_ptr(x), _ptr(y), x.numel(), _stream(x.device)), "bgs_debug_exp2")
+    return y
