@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
+    ap.add_argument("--mode", default="auto", choices=["auto", "pixel", "gaussian", "static"],
+                    help="render mode of the timed steps")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the timed steps (no tuning, baselines, e2e or oracle): for profiler runs")
     return ap.parse_args()
 
 
@@ -255,6 +259,8 @@ def main():
 
     # ---- autotune: heavy-tile threshold and pixels per Gaussian-wise item ----
     tuned = {}
+    if args.quick:
+        args.no_tune = args.no_cpu_baseline = True
     if not args.no_tune:
         best = None
         for thr in (256, 1024, 4096, 1 << 30):
@@ -279,7 +285,7 @@ def main():
 
     # ---- warmup + timed region ----
     for _ in range(args.warmup):
-        step("auto")
+        step(args.mode)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -293,7 +299,7 @@ def main():
     torch.cuda.synchronize()
     e0.record()
     for _ in range(args.steps):
-        step("auto")
+        step(args.mode)
     e1.record()
     torch.cuda.synchronize()
     ms_total = e0.elapsed_time(e1)
@@ -309,6 +315,13 @@ def main():
     ms_step = ms_total / args.steps
     fwd_ms, bwd_ms = f_ms / max(nf, 1), b_ms / max(nb, 1)
     value = eval_pairs * world / (ms_step / 1e3)
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "pairs/s", "ms_per_step": ms_step,
+                              "render_ms_per_frame": {"forward": fwd_ms, "backward": bwd_ms},
+                              "note": "--quick profiling run"}), flush=True)
+        plan.close()
+        return
 
     # ---- plain pixel-wise 16x16 static grid on the same inputs (render kernels only) ----
     plan.timing(True)

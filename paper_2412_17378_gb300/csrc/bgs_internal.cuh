@@ -119,14 +119,17 @@ cudaError_t launch_preprocess(long long N, const float *means3D, const float *lo
                               float *means2D, float *conic_opacity, float *depths, int *radii,
                               uint32_t *tiles_touched, cudaStream_t s);
 
-cudaError_t launch_touched(long long N, const float *means2D, const int *radii, int W, int H, int tile_w,
-                           int tile_h, uint32_t *touched, cudaStream_t s);
-cudaError_t launch_duplicate(long long N, const float *means2D, const int *radii, const float *depths,
-                             const unsigned long long *offsets, int W, int H, int tile_w, int tile_h,
-                             unsigned long long *keys, uint32_t *vals, long long capacity, cudaStream_t s);
+cudaError_t launch_touched(long long N, const float *means2D, const int *radii, const float *depths, int W, int H,
+                           int tile_w, int tile_h, uint32_t *touched, uint32_t *dkey, uint32_t *idx, cudaStream_t s);
+cudaError_t launch_gather_u32(long long N, const uint32_t *src, const uint32_t *order, uint32_t *dst, cudaStream_t s);
+template <typename KeyT>
+cudaError_t launch_duplicate(long long N, const uint32_t *order, const float *means2D, const int *radii,
+                             const unsigned long long *offsets, int W, int H, int tile_w, int tile_h, KeyT *keys,
+                             uint32_t *vals, long long capacity, cudaStream_t s);
 cudaError_t launch_count_total(long long N, const uint32_t *touched, const unsigned long long *offsets,
                                DevCtrl *ctrl, cudaStream_t s);
-cudaError_t launch_ranges(const unsigned long long *keys, long long K, uint2 *ranges, cudaStream_t s);
+template <typename KeyT>
+cudaError_t launch_ranges(const KeyT *keys, long long K, uint2 *ranges, cudaStream_t s);
 
 cudaError_t launch_pack(long long N, const float *means2D, const float *conic_opacity, const float *colors,
                         const float *depths, Rec *recs, cudaStream_t s);

@@ -75,7 +75,7 @@ struct bgs_plan {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_fwd, ev_bwd;
     unsigned long long host_launches = 0;
     // binning
-    Buf touched, offsets, keys_in, keys_out, vals_in, cub_tmp;
+    Buf touched, touched_sorted, dkey, dkey_sorted, gidx, order, offsets, keys_in, keys_out, vals_in, cub_tmp;
     // render
     Buf recs, tile_key, tile_key2, tile_idx, tile_idx2, counts, item_off, items, grad_acc;
 };
@@ -275,7 +275,8 @@ int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out) {
 int bgs_plan_destroy(bgs_plan *p) {
     if (!p) return BGS_OK;
     DeviceGuard g(p->device);
-    Buf *bufs[] = {&p->touched, &p->offsets, &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
+    Buf *bufs[] = {&p->touched, &p->touched_sorted, &p->dkey, &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
+                   &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off, &p->items,
                    &p->grad_acc};
     for (Buf *b : bufs)
@@ -359,38 +360,30 @@ int bgs_plan_reserve(bgs_plan *p, int64_t N, int64_t K, int64_t T, int64_t pixel
     if (!p || N < 0 || K < 0 || T < 0 || pixels < 0) return fail(BGS_ERR_INVALID, "bgs_plan_reserve: bad sizes");
     DeviceGuard g(p->device);
     cudaStream_t s = 0;
-    BGS_TRY(ensure(p, p->touched, 4 * N, s, "touched"));
+    Buf *n4[] = {&p->touched, &p->touched_sorted, &p->dkey, &p->dkey_sorted, &p->gidx, &p->order};
+    for (Buf *b : n4) BGS_TRY(ensure(p, *b, 4 * N, s, "per-Gaussian"));
     BGS_TRY(ensure(p, p->offsets, 8 * N, s, "offsets"));
-    BGS_TRY(ensure(p, p->keys_in, 8 * K, s, "keys_in"));
-    BGS_TRY(ensure(p, p->keys_out, 8 * K, s, "keys_out"));
+    BGS_TRY(ensure(p, p->keys_in, 4 * K, s, "keys_in"));
+    BGS_TRY(ensure(p, p->keys_out, 4 * K, s, "keys_out"));
     BGS_TRY(ensure(p, p->vals_in, 4 * K, s, "vals_in"));
     BGS_TRY(ensure(p, p->recs, sizeof(bgs::Rec) * N, s, "recs"));
     BGS_TRY(ensure(p, p->grad_acc, sizeof(bgs::Rec) * N, s, "grad_acc"));
     const int P = p->desc.gw_pixels;
-    BGS_TRY(ensure(p, p->tile_key, 4 * T, s, "tile_key"));
-    BGS_TRY(ensure(p, p->tile_key2, 4 * T, s, "tile_key2"));
-    BGS_TRY(ensure(p, p->tile_idx, 4 * T, s, "tile_idx"));
-    BGS_TRY(ensure(p, p->tile_idx2, 4 * T, s, "tile_idx2"));
-    BGS_TRY(ensure(p, p->counts, 4 * T, s, "counts"));
-    BGS_TRY(ensure(p, p->item_off, 4 * T, s, "item_off"));
+    Buf *t4[] = {&p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off};
+    for (Buf *b : t4) BGS_TRY(ensure(p, *b, 4 * T, s, "per-tile"));
     BGS_TRY(ensure(p, p->items, 8 * T * (size_t)std::max(8, (256 + P - 1) / P), s, "items"));
-    // CUB temporaries: the largest of the entry sort, the N-scan and the tile sort / scan
-    size_t t1 = 0, t2 = 0, t3 = 0, t4 = 0;
-    BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, t1, (unsigned long long *)nullptr,
-                                             (unsigned long long *)nullptr, (uint32_t *)nullptr, (uint32_t *)nullptr,
-                                             (int64_t)std::max<int64_t>(K, 1), 0, 64, s),
-             "sort size");
-    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, t2, (uint32_t *)nullptr, (unsigned long long *)nullptr,
-                                           (int64_t)std::max<int64_t>(N, 1), s),
-             "scan size");
-    BGS_CUDA(cub::DeviceRadixSort::SortPairsDescending(nullptr, t3, (uint32_t *)nullptr, (uint32_t *)nullptr,
-                                                       (uint32_t *)nullptr, (uint32_t *)nullptr,
-                                                       (int)std::max<int64_t>(T, 1), 0, 32, s),
-             "tile sort size");
-    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, t4, (uint32_t *)nullptr, (uint32_t *)nullptr,
-                                           (int)std::max<int64_t>(T, 1), s),
-             "tile scan size");
-    BGS_TRY(ensure(p, p->cub_tmp, std::max(std::max(t1, t2), std::max(t3, t4)), s, "cub_tmp"));
+    // CUB temporaries: the largest of the depth sort, the N-scan, the tile sort and the work-list sort / scan
+    size_t t[5] = {0, 0, 0, 0, 0};
+    const int64_t n1 = std::max<int64_t>(N, 1), k1 = std::max<int64_t>(K, 1);
+    const int tt = (int)std::max<int64_t>(T, 1);
+    uint32_t *u = nullptr;
+    unsigned long long *ul = nullptr;
+    BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, t[0], u, u, u, u, n1, 0, 32, s), "sort size");
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, t[1], u, ul, n1, s), "scan size");
+    BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, t[2], u, u, u, u, k1, 0, 32, s), "tile sort size");
+    BGS_CUDA(cub::DeviceRadixSort::SortPairsDescending(nullptr, t[3], u, u, u, u, tt, 0, 32, s), "tile order size");
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, t[4], u, u, tt, s), "tile scan size");
+    BGS_TRY(ensure(p, p->cub_tmp, *std::max_element(t, t + 5), s, "cub_tmp"));
     return BGS_OK;
 }
 
@@ -454,6 +447,38 @@ int bgs_preprocess(bgs_plan *p, int64_t N, const float *means3D, const float *lo
     return BGS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+template <typename KeyT>
+int sort_and_range(bgs_plan *p, long long N, const float *means2D, const int32_t *radii, int W, int H, int tw,
+                   int th, long long K, long long T, uint32_t *point_list, uint32_t *ranges, cudaStream_t s) {
+    const uint32_t *order = (const uint32_t *)p->order.p;
+    const unsigned long long *off = (const unsigned long long *)p->offsets.p;
+    BGS_TRY(ensure(p, p->keys_in, sizeof(KeyT) * K, s, "keys_in"));
+    BGS_TRY(ensure(p, p->keys_out, sizeof(KeyT) * K, s, "keys_out"));
+    BGS_TRY(ensure(p, p->vals_in, 4 * K, s, "vals_in"));
+    KeyT *kin = (KeyT *)p->keys_in.p, *kout = (KeyT *)p->keys_out.p;
+    uint32_t *vin = (uint32_t *)p->vals_in.p;
+    BGS_CUDA(bgs::launch_duplicate<KeyT>(N, order, means2D, radii, off, W, H, tw, th, kin, vin, K, s), "duplicate");
+    const int end_bit = bits_for(T);
+    size_t tmp = 0;
+    BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, kin, kout, vin, point_list, (int64_t)K, 0, end_bit, s),
+             "tile sort (size)");
+    BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
+    tmp = p->cub_tmp.bytes;
+    BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, kin, kout, vin, point_list, (int64_t)K, 0, end_bit, s),
+             "tile sort");
+    BGS_CUDA(bgs::launch_ranges<KeyT>(kout, K, reinterpret_cast<uint2 *>(ranges), s), "ranges");
+    p->host_launches += 2;  // duplicate, ranges
+    return BGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t *radii, const float *depths,
                      int32_t W, int32_t H, int32_t tw, int32_t th, uint32_t *point_list, int64_t capacity,
                      uint32_t *ranges, int64_t *num_rendered, int64_t *needed, void *stream) {
@@ -471,19 +496,37 @@ int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t
     cudaStream_t s = (cudaStream_t)stream;
     BGS_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * T, s), "clear ranges");
     if (num_rendered) *num_rendered = 0;
+    if (needed) *needed = 0;
     if (N == 0) return BGS_OK;
+    // (1) entry counts and the depth order of the Gaussians (stable: ties keep index order)
     BGS_TRY(ensure(p, p->touched, 4 * N, s, "touched"));
+    BGS_TRY(ensure(p, p->touched_sorted, 4 * N, s, "touched_sorted"));
+    BGS_TRY(ensure(p, p->dkey, 4 * N, s, "dkey"));
+    BGS_TRY(ensure(p, p->dkey_sorted, 4 * N, s, "dkey_sorted"));
+    BGS_TRY(ensure(p, p->gidx, 4 * N, s, "gidx"));
+    BGS_TRY(ensure(p, p->order, 4 * N, s, "order"));
     BGS_TRY(ensure(p, p->offsets, 8 * N, s, "offsets"));
-    uint32_t *touched = (uint32_t *)p->touched.p;
+    uint32_t *touched = (uint32_t *)p->touched.p, *tsorted = (uint32_t *)p->touched_sorted.p;
+    uint32_t *dkey = (uint32_t *)p->dkey.p, *dkey2 = (uint32_t *)p->dkey_sorted.p;
+    uint32_t *gidx = (uint32_t *)p->gidx.p, *order = (uint32_t *)p->order.p;
     unsigned long long *off = (unsigned long long *)p->offsets.p;
-    BGS_CUDA(bgs::launch_touched(N, means2D, radii, W, H, tw, th, touched, s), "touched");
+    BGS_CUDA(bgs::launch_touched(N, means2D, radii, depths, W, H, tw, th, touched, dkey, gidx, s), "touched");
     size_t tmp = 0;
-    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, touched, off, (int64_t)N, s), "scan (size)");
+    BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, dkey, dkey2, gidx, order, (int64_t)N, 0, 32, s),
+             "depth sort (size)");
     BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
     tmp = p->cub_tmp.bytes;
-    BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, touched, off, (int64_t)N, s), "scan");
-    BGS_CUDA(bgs::launch_count_total(N, touched, off, p->ctrl, s), "count_total");
-    p->host_launches += 2;  // touched, count_total
+    BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, dkey, dkey2, gidx, order, (int64_t)N, 0, 32, s),
+             "depth sort");
+    // (2) entry offsets in depth order
+    BGS_CUDA(bgs::launch_gather_u32(N, touched, order, tsorted, s), "gather counts");
+    tmp = 0;
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tsorted, off, (int64_t)N, s), "scan (size)");
+    BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
+    tmp = p->cub_tmp.bytes;
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, tsorted, off, (int64_t)N, s), "scan");
+    BGS_CUDA(bgs::launch_count_total(N, tsorted, off, p->ctrl, s), "count_total");
+    p->host_launches += 3;  // touched, gather, count_total
     unsigned long long K = 0;
     BGS_CUDA(cudaMemcpyAsync(&K, &p->ctrl->num_entries, sizeof K, cudaMemcpyDeviceToHost, s), "read K");
     BGS_CUDA(cudaStreamSynchronize(s), "sync K");
@@ -493,24 +536,10 @@ int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t
     if (K >= (1ull << 32) - 1) return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort: %llu entries exceed 2^32", K);
     if (num_rendered) *num_rendered = (int64_t)K;
     if (K == 0) return BGS_OK;
-    BGS_TRY(ensure(p, p->keys_in, 8 * K, s, "keys_in"));
-    BGS_TRY(ensure(p, p->keys_out, 8 * K, s, "keys_out"));
-    BGS_TRY(ensure(p, p->vals_in, 4 * K, s, "vals_in"));
-    unsigned long long *kin = (unsigned long long *)p->keys_in.p, *kout = (unsigned long long *)p->keys_out.p;
-    uint32_t *vin = (uint32_t *)p->vals_in.p;
-    BGS_CUDA(bgs::launch_duplicate(N, means2D, radii, depths, off, W, H, tw, th, kin, vin, (long long)K, s),
-             "duplicate");
-    const int end_bit = 32 + bits_for(T);
-    tmp = 0;
-    BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, kin, kout, vin, point_list, (int64_t)K, 0, end_bit, s),
-             "sort (size)");
-    BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
-    tmp = p->cub_tmp.bytes;
-    BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, kin, kout, vin, point_list, (int64_t)K, 0, end_bit, s),
-             "sort");
-    BGS_CUDA(bgs::launch_ranges(kout, (long long)K, reinterpret_cast<uint2 *>(ranges), s), "ranges");
-    p->host_launches += 2;  // duplicate, ranges
-    return BGS_OK;
+    // (3) emit entries in depth order and group them per tile with a stable sort on the tile id
+    if (T <= 65536)
+        return sort_and_range<uint16_t>(p, N, means2D, radii, W, H, tw, th, (long long)K, T, point_list, ranges, s);
+    return sort_and_range<uint32_t>(p, N, means2D, radii, W, H, tw, th, (long long)K, T, point_list, ranges, s);
 }
 
 static int render_common_checks(bgs_plan *p, int64_t N, const float *means2D, const float *conic_opacity,

@@ -134,44 +134,99 @@ cudaError_t launch_preprocess(long long N, const float *means3D, const float *lo
     return cudaGetLastError();
 }
 
-// ---- a2 helpers: duplicated keys, totals and ranges ------------------------------------
+// ---- a2: binning -----------------------------------------------------------------------
+// The per-tile lists must be ordered by (float32 depth, Gaussian index).  Instead of one
+// radix sort of 64-bit (tile, depth) keys over all K duplicated entries, the Gaussians are
+// first sorted by depth (N keys of 32 bits), the entries are then emitted in that order,
+// and a stable radix sort on the tile id alone (13-17 bits) groups them per tile while
+// keeping the depth order.  This moves the multi-pass work from K 12-byte records over
+// 45 key bits to K 6- or 8-byte records over the tile bits only.
 
-// Each Gaussian writes one (key, value) entry per covered tile at offsets[i] (an exclusive
-// scan of tiles_touched).  The rectangle is recomputed with the same float32 operations.
-__global__ void __launch_bounds__(256) k_duplicate(long long N, const float2 *__restrict__ means2D,
-                                                   const int *__restrict__ radii, const float *__restrict__ depths,
-                                                   const unsigned long long *__restrict__ offsets, int tw, int th, int tx,
-                                                   int ty, unsigned long long *__restrict__ keys,
-                                                   uint32_t *__restrict__ vals, long long capacity) {
+// Entry count (rectangle area) and depth sort key of each Gaussian.
+__global__ void __launch_bounds__(256) k_touched(long long N, const float2 *__restrict__ means2D,
+                                                 const int *__restrict__ radii, const float *__restrict__ depths,
+                                                 int tw, int th, int tx, int ty, uint32_t *__restrict__ touched,
+                                                 uint32_t *__restrict__ dkey, uint32_t *__restrict__ idx) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const int r = radii[i];
+    uint32_t c = 0;
+    if (r > 0) {
+        const float2 m = means2D[i];
+        int x0, x1, y0, y1;
+        tile_rect(m.x, m.y, r, tw, th, tx, ty, x0, x1, y0, y1);
+        if (x1 > x0 && y1 > y0) c = (uint32_t)((x1 - x0) * (y1 - y0));
+    }
+    touched[i] = c;
+    dkey[i] = __float_as_uint(depths[i]);
+    idx[i] = (uint32_t)i;
+}
+
+cudaError_t launch_touched(long long N, const float *means2D, const int *radii, const float *depths, int W, int H,
+                           int tile_w, int tile_h, uint32_t *touched, uint32_t *dkey, uint32_t *idx, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    const int tx = (W + tile_w - 1) / tile_w, ty = (H + tile_h - 1) / tile_h;
+    k_touched<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, reinterpret_cast<const float2 *>(means2D), radii, depths,
+                                                          tile_w, tile_h, tx, ty, touched, dkey, idx);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_gather_u32(long long N, const uint32_t *__restrict__ src,
+                                                    const uint32_t *__restrict__ order, uint32_t *__restrict__ dst) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) dst[i] = src[order[i]];
+}
+
+cudaError_t launch_gather_u32(long long N, const uint32_t *src, const uint32_t *order, uint32_t *dst, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    k_gather_u32<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, src, order, dst);
+    return cudaGetLastError();
+}
+
+// Emits the entries of the depth-ordered Gaussians: position s of the depth order writes
+// one (tile id, Gaussian index) pair per covered tile at offsets[s].
+template <typename KeyT>
+__global__ void __launch_bounds__(256) k_duplicate(long long N, const uint32_t *__restrict__ order,
+                                                   const float2 *__restrict__ means2D, const int *__restrict__ radii,
+                                                   const unsigned long long *__restrict__ offsets, int tw, int th,
+                                                   int tx, int ty, KeyT *__restrict__ keys, uint32_t *__restrict__ vals,
+                                                   long long capacity) {
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const uint32_t i = order[s];
     const int r = radii[i];
     if (r <= 0) return;
     const float2 m = means2D[i];
     int x0, x1, y0, y1;
     tile_rect(m.x, m.y, r, tw, th, tx, ty, x0, x1, y0, y1);
-    long long off = offsets[i];
-    const unsigned long long dbits = (unsigned long long)__float_as_uint(depths[i]);
+    long long off = (long long)offsets[s];
     for (int y = y0; y < y1; ++y)
         for (int x = x0; x < x1; ++x) {
             if (off < capacity) {
-                keys[off] = ((unsigned long long)(y * tx + x) << 32) | dbits;
-                vals[off] = (uint32_t)i;
+                keys[off] = (KeyT)(y * tx + x);
+                vals[off] = i;
             }
             ++off;
         }
 }
 
-cudaError_t launch_duplicate(long long N, const float *means2D, const int *radii, const float *depths,
-                             const unsigned long long *offsets, int W, int H, int tile_w, int tile_h,
-                             unsigned long long *keys, uint32_t *vals, long long capacity, cudaStream_t s) {
+template <typename KeyT>
+cudaError_t launch_duplicate(long long N, const uint32_t *order, const float *means2D, const int *radii,
+                             const unsigned long long *offsets, int W, int H, int tile_w, int tile_h, KeyT *keys,
+                             uint32_t *vals, long long capacity, cudaStream_t s) {
     if (N == 0) return cudaSuccess;
     const int tx = (W + tile_w - 1) / tile_w, ty = (H + tile_h - 1) / tile_h;
-    const long long blocks = (N + 255) / 256;
-    k_duplicate<<<(unsigned)blocks, 256, 0, s>>>(N, reinterpret_cast<const float2 *>(means2D), radii, depths,
-                                                 offsets, tile_w, tile_h, tx, ty, keys, vals, capacity);
+    k_duplicate<KeyT><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, order, reinterpret_cast<const float2 *>(means2D),
+                                                                  radii, offsets, tile_w, tile_h, tx, ty, keys, vals,
+                                                                  capacity);
     return cudaGetLastError();
 }
+template cudaError_t launch_duplicate<uint16_t>(long long, const uint32_t *, const float *, const int *,
+                                                const unsigned long long *, int, int, int, int, uint16_t *, uint32_t *,
+                                                long long, cudaStream_t);
+template cudaError_t launch_duplicate<uint32_t>(long long, const uint32_t *, const float *, const int *,
+                                                const unsigned long long *, int, int, int, int, uint32_t *, uint32_t *,
+                                                long long, cudaStream_t);
 
 __global__ void k_count_total(long long N, const uint32_t *touched, const unsigned long long *offsets,
                               DevCtrl *ctrl) {
@@ -184,47 +239,24 @@ cudaError_t launch_count_total(long long N, const uint32_t *touched, const unsig
     return cudaGetLastError();
 }
 
-// Entry count of each Gaussian (area of its tile rectangle, 0 if radius <= 0).
-__global__ void __launch_bounds__(256) k_touched(long long N, const float2 *__restrict__ means2D,
-                                                 const int *__restrict__ radii, int tw, int th, int tx, int ty,
-                                                 uint32_t *__restrict__ touched) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int r = radii[i];
-    uint32_t c = 0;
-    if (r > 0) {
-        const float2 m = means2D[i];
-        int x0, x1, y0, y1;
-        tile_rect(m.x, m.y, r, tw, th, tx, ty, x0, x1, y0, y1);
-        if (x1 > x0 && y1 > y0) c = (uint32_t)((x1 - x0) * (y1 - y0));
-    }
-    touched[i] = c;
-}
-
-cudaError_t launch_touched(long long N, const float *means2D, const int *radii, int W, int H, int tile_w,
-                           int tile_h, uint32_t *touched, cudaStream_t s) {
-    if (N == 0) return cudaSuccess;
-    const int tx = (W + tile_w - 1) / tile_w, ty = (H + tile_h - 1) / tile_h;
-    k_touched<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, reinterpret_cast<const float2 *>(means2D), radii,
-                                                          tile_w, tile_h, tx, ty, touched);
-    return cudaGetLastError();
-}
-
-// ranges[t] = [first, last+1) of tile t in the sorted keys (ranges zeroed beforehand).
-__global__ void __launch_bounds__(256) k_ranges(const unsigned long long *__restrict__ keys, long long K,
-                                                uint2 *__restrict__ ranges) {
+// ranges[t] = [first, last+1) of tile t in the sorted tile keys (ranges zeroed beforehand).
+template <typename KeyT>
+__global__ void __launch_bounds__(256) k_ranges(const KeyT *__restrict__ keys, long long K, uint2 *__restrict__ ranges) {
     long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= K) return;
-    const uint32_t t = (uint32_t)(keys[j] >> 32);
-    if (j == 0 || (uint32_t)(keys[j - 1] >> 32) != t) ranges[t].x = (uint32_t)j;
-    if (j == K - 1 || (uint32_t)(keys[j + 1] >> 32) != t) ranges[t].y = (uint32_t)(j + 1);
+    const uint32_t t = keys[j];
+    if (j == 0 || (uint32_t)keys[j - 1] != t) ranges[t].x = (uint32_t)j;
+    if (j == K - 1 || (uint32_t)keys[j + 1] != t) ranges[t].y = (uint32_t)(j + 1);
 }
 
-cudaError_t launch_ranges(const unsigned long long *keys, long long K, uint2 *ranges, cudaStream_t s) {
+template <typename KeyT>
+cudaError_t launch_ranges(const KeyT *keys, long long K, uint2 *ranges, cudaStream_t s) {
     if (K == 0) return cudaSuccess;
-    k_ranges<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(keys, K, ranges);
+    k_ranges<KeyT><<<(unsigned)((K + 255) / 256), 256, 0, s>>>(keys, K, ranges);
     return cudaGetLastError();
 }
+template cudaError_t launch_ranges<uint16_t>(const uint16_t *, long long, uint2 *, cudaStream_t);
+template cudaError_t launch_ranges<uint32_t>(const uint32_t *, long long, uint2 *, cudaStream_t);
 
 // ---- render input packing ------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_pack(long long N, const float *__restrict__ means2D,

@@ -11,7 +11,13 @@ namespace {
 constexpr int kProbeThreads = 512;
 constexpr int kProbeIters = 4096;
 
-// 8 independent FMA chains per thread; records the SM-clock duration of the block.
+__device__ __forceinline__ unsigned smid() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
+// 8 independent FMA chains per thread; records (SM id, start clock, end clock) per block.
 __global__ void __launch_bounds__(kProbeThreads) k_probe_fma(float seed, float *sink, long long *cycles) {
     float v[8];
 #pragma unroll
@@ -20,7 +26,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_fma(float seed, float *
     const long long t0 = clock64();
     for (int i = 0; i < kProbeIters; ++i) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = fmaf(v[k], 0.999f, 1e-3f);
+        for (int k = 0; k < 8; ++k) asm volatile("fma.rn.f32 %0, %0, 0f3F7FBE77, 0f3A83126F;" : "+f"(v[k]));
     }
     __syncthreads();
     const long long t1 = clock64();
@@ -28,7 +34,11 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_fma(float seed, float *
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += v[k];
     if (s == 12345.f) sink[threadIdx.x] = s;
-    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+    if (threadIdx.x == 0) {
+        cycles[3 * blockIdx.x] = smid();
+        cycles[3 * blockIdx.x + 1] = t0;
+        cycles[3 * blockIdx.x + 2] = t1;
+    }
 }
 
 // 8 independent ex2 chains per thread (the value is kept in a bounded range).
@@ -40,7 +50,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_ex2(float seed, float *
     const long long t0 = clock64();
     for (int i = 0; i < kProbeIters; ++i) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = -bgs::ex2_approx(v[k]);
+        for (int k = 0; k < 8; ++k) asm volatile("ex2.approx.ftz.f32 %0, %0;" : "+f"(v[k]));
     }
     __syncthreads();
     const long long t1 = clock64();
@@ -48,7 +58,11 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_ex2(float seed, float *
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += v[k];
     if (s == 12345.f) sink[threadIdx.x] = s;
-    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+    if (threadIdx.x == 0) {
+        cycles[3 * blockIdx.x] = smid();
+        cycles[3 * blockIdx.x + 1] = t0;
+        cycles[3 * blockIdx.x + 2] = t1;
+    }
 }
 
 __global__ void k_exp2(const float *x, float *y, long long n) {
@@ -70,11 +84,11 @@ extern "C" int bgs_probe_pipe_rates(bgs_plan *plan, double *fp32_per_sm_clk, dou
     float *sink = nullptr;
     long long *cyc = nullptr;
     if (cudaMalloc(&sink, sizeof(float) * kProbeThreads) != cudaSuccess) return BGS_ERR_CUDA;
-    if (cudaMalloc(&cyc, sizeof(long long) * blocks) != cudaSuccess) {
+    if (cudaMalloc(&cyc, sizeof(long long) * 3 * blocks) != cudaSuccess) {
         cudaFree(sink);
         return BGS_ERR_CUDA;
     }
-    std::vector<long long> h(blocks);
+    std::vector<long long> h(3 * blocks);
     double rates[2] = {0, 0};
     for (int which = 0; which < 2; ++which) {
         for (int rep = 0; rep < 2; ++rep) {  // first repetition warms up
@@ -83,16 +97,33 @@ extern "C" int bgs_probe_pipe_rates(bgs_plan *plan, double *fp32_per_sm_clk, dou
             else
                 k_probe_ex2<<<blocks, kProbeThreads, 0, s>>>(0.5f, sink, cyc);
         }
-        if (cudaMemcpyAsync(h.data(), cyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        if (cudaMemcpyAsync(h.data(), cyc, sizeof(long long) * 3 * blocks, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             cudaFree(sink);
             cudaFree(cyc);
             return BGS_ERR_CUDA;
         }
-        std::sort(h.begin(), h.end());
-        const double med = (double)h[blocks / 2];
+        // per SM: operations of the blocks it ran / (last end - first start) on its clock
+        const int max_sm = 1024;
+        std::vector<long long> first(max_sm, -1), last(max_sm, -1), nblk(max_sm, 0);
+        for (int b = 0; b < blocks; ++b) {
+            const int id = (int)h[3 * b];
+            if (id < 0 || id >= max_sm) continue;
+            if (first[id] < 0 || h[3 * b + 1] < first[id]) first[id] = h[3 * b + 1];
+            if (last[id] < 0 || h[3 * b + 2] > last[id]) last[id] = h[3 * b + 2];
+            nblk[id] += 1;
+        }
+        std::vector<double> r;
         const double ops_per_block = (double)kProbeThreads * kProbeIters * 8;
-        rates[which] = ops_per_block * per_sm / med;  // blocks of one SM run concurrently
+        for (int id = 0; id < max_sm; ++id)
+            if (nblk[id] > 0 && last[id] > first[id]) r.push_back(ops_per_block * nblk[id] / (double)(last[id] - first[id]));
+        if (r.empty()) {
+            cudaFree(sink);
+            cudaFree(cyc);
+            return BGS_ERR_CUDA;
+        }
+        std::sort(r.begin(), r.end());
+        rates[which] = r[r.size() / 2];  // median over SMs
     }
     cudaFree(sink);
     cudaFree(cyc);
