@@ -18,15 +18,23 @@ constexpr float kLn2 = 0.6931471805599453f;    // ln(2)
 
 // ---- device control block (one per plan) --------------------------------------------
 struct DevCtrl {
-    unsigned int queue_head;    // persistent-kernel work queue cursor
+    unsigned int queue_head;    // pixel-wise queue cursor (starts at num_gauss)
     unsigned int num_items;     // work items in the current list
     unsigned int check_bits;    // BGS_CHECK_* raised by device checks
-    unsigned int pad0;
+    unsigned int num_gauss;     // items [0, num_gauss) are Gaussian-wise, the rest pixel-wise
     unsigned long long num_entries;  // K written by binning
     unsigned long long eval_pairs;
     unsigned long long contrib_pairs;
     unsigned long long items_done;
+    unsigned int queue_head_g;  // Gaussian-wise queue cursor (starts at 0)
+    unsigned int pad0;
 };
+
+// Pixel-wise items cover 8 x (4 * kPixPerLane) pixels of a tile: lane l owns the pixels
+// (l % 8, l / 8 + 4 q), q < kPixPerLane.
+constexpr int kPixPerLane = 2;
+constexpr int kPixItemW = 8;
+constexpr int kPixItemH = 4 * kPixPerLane;
 
 // ---- packed per-Gaussian record used by the render kernels (48 bytes) ---------------
 //   a = (mx, my, qa, qb), b = (qc, o, depth, 0), c = (r, g, b, 0)
@@ -64,17 +72,37 @@ __device__ __forceinline__ Rec make_rec(const float *__restrict__ means2D, const
     return r;
 }
 
-// power2 = log2(e) * power of the pair (pixel px, py) -- identical code in every kernel,
-// forward and backward, so that skip / stop decisions agree bit for bit.
+// power2 = log2(e) * power of the pair (pixel px, py) = qa dx^2 + qb dx dy + qc dy^2,
+// evaluated as hx + dy (bx + qc dy) with hx = qa dx^2 and bx = qb dx (shared by pixels of
+// one column).  Written with explicit round-to-nearest intrinsics so that no kernel's
+// compilation can contract or reorder it: every kernel, forward and backward, takes the
+// same skip / stop decisions bit for bit.
+struct PairX {
+    float dx, hx, bx;
+};
+
+__device__ __forceinline__ PairX pair_x(float4 a, float px) {
+    PairX r;
+    r.dx = __fsub_rn(a.x, px);
+    r.hx = __fmul_rn(__fmul_rn(a.z, r.dx), r.dx);
+    r.bx = __fmul_rn(a.w, r.dx);
+    return r;
+}
+
+__device__ __forceinline__ float pair_power2_y(const PairX &x, float ay, float qc, float py, float &dy) {
+    dy = __fsub_rn(ay, py);
+    return __fmaf_rn(dy, __fmaf_rn(qc, dy, x.bx), x.hx);
+}
+
 __device__ __forceinline__ float pair_power2(float4 a, float qc, float px, float py, float &dx, float &dy) {
-    dx = a.x - px;
-    dy = a.y - py;
-    return (a.z * dx + a.w * dy) * dx + qc * dy * dy;
+    const PairX x = pair_x(a, px);
+    dx = x.dx;
+    return pair_power2_y(x, a.y, qc, py, dy);
 }
 
 __device__ __forceinline__ float pair_alpha(float power2, float o, float &G) {
     G = ex2_approx(power2);
-    return fminf(kAlphaMax, o * G);
+    return fminf(kAlphaMax, __fmul_rn(o, G));
 }
 
 // ---- launch parameter blocks -----------------------------------------------------------
@@ -107,7 +135,7 @@ struct BwdArgs {
     const float *final_T;
     const int *n_contrib;
     const float *dL_dcolor, *dL_ddepth, *dL_dalpha;
-    float4 *grad_acc;            // [N][3] float4 accumulators (10 used of 12)
+    float *grad_acc;             // [N][12] accumulators (10 used)
     DevCtrl *ctrl;
     const uint2 *items;
     int chunk;
@@ -131,13 +159,24 @@ cudaError_t launch_count_total(long long N, const uint32_t *touched, const unsig
 template <typename KeyT>
 cudaError_t launch_ranges(const KeyT *keys, long long K, uint2 *ranges, cudaStream_t s);
 
+// counting-sort binning (binning.cu)
+size_t bin_count_smem(int T);
+cudaError_t setup_bin_kernels(size_t smem);
+cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
+                             int W, int H, int tw, int th, uint32_t *Hm, cudaStream_t s);
+cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, uint32_t *total, cudaStream_t s);
+cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *total, uint2 *ranges, DevCtrl *ctrl,
+                              cudaStream_t s);
+cudaError_t launch_bin_scatter(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
+                               int W, int H, int tw, int th, const uint32_t *Hm, const uint32_t *start,
+                               uint32_t *point_list, long long capacity, cudaStream_t s);
+
 cudaError_t launch_pack(long long N, const float *means2D, const float *conic_opacity, const float *colors,
                         const float *depths, Rec *recs, cudaStream_t s);
 
 // work list: per-tile keys/counts, then emission in (optionally sorted) tile order
-cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int W, int H, int tile_w, int tile_h,
-                               int tiles_x, int mode, int heavy_threshold, int gw_pixels, uint32_t *tile_key,
-                               uint32_t *tile_idx, cudaStream_t s);
+cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int mode, int heavy_threshold, int lpt,
+                               uint32_t *tile_key, uint32_t *tile_idx, cudaStream_t s);
 cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, int W, int H,
                                  int tile_w, int tile_h, int tiles_x, int mode, int heavy_threshold,
                                  int gw_pixels, uint32_t *counts, cudaStream_t s);
@@ -146,9 +185,11 @@ cudaError_t launch_emit_items(const uint32_t *order, const uint32_t *counts, con
                               DevCtrl *ctrl, cudaStream_t s);
 
 cudaError_t launch_forward_static(const FwdArgs &a, cudaStream_t s);
-cudaError_t launch_forward_balanced(const FwdArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_forward_gauss(const FwdArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_forward_pixel(const FwdArgs &a, int grid, cudaStream_t s);
 int forward_balanced_block_threads();
-const void *forward_balanced_kernel(int gw_pixels);
+const void *forward_gauss_kernel(int gw_pixels);
+const void *forward_pixel_kernel();
 
 cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s);

@@ -76,6 +76,8 @@ struct bgs_plan {
     unsigned long long host_launches = 0;
     // binning
     Buf touched, touched_sorted, dkey, dkey_sorted, gidx, order, offsets, keys_in, keys_out, vals_in, cub_tmp;
+    Buf bin_h, bin_total, bin_start;  // counting-sort binning
+    int smem_optin = 0;
     // render
     Buf recs, tile_key, tile_key2, tile_idx, tile_idx2, counts, item_off, items, grad_acc;
 };
@@ -180,7 +182,9 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, int W, int H, int tw, in
     const int T = tiles_x * tiles_y;
     const int P = p->desc.gw_pixels;
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-    const long long per_tile = std::max<long long>(((tw + 7) / 8) * ((th + 3) / 4), (tw * th + P - 1) / P);
+    const long long per_tile = std::max<long long>(((tw + bgs::kPixItemW - 1) / bgs::kPixItemW) *
+                                                       ((th + bgs::kPixItemH - 1) / bgs::kPixItemH),
+                                                   (tw * th + P - 1) / P);
     const long long max_items = (long long)T * per_tile;
     if (max_items >= (1ll << 31)) return fail(BGS_ERR_INVALID, "too many work items (%lld)", max_items);
     BGS_TRY(ensure(p, p->tile_key, sizeof(uint32_t) * T, s, "tile_key"));
@@ -189,23 +193,24 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, int W, int H, int tw, in
     BGS_TRY(ensure(p, p->item_off, sizeof(uint32_t) * T, s, "item_off"));
     BGS_TRY(ensure(p, p->items, sizeof(uint2) * max_items, s, "items"));
     uint32_t *key = (uint32_t *)p->tile_key.p, *idx = (uint32_t *)p->tile_idx.p;
-    BGS_CUDA(bgs::launch_tile_counts(rg, T, W, H, tw, th, tiles_x, mode, p->desc.heavy_threshold, P, key, idx, s),
+    BGS_CUDA(bgs::launch_tile_counts(rg, T, mode, p->desc.heavy_threshold, p->desc.lpt_order, key, idx, s),
              "tile_counts");
-    const uint32_t *order = idx;
-    if (p->desc.lpt_order) {
-        BGS_TRY(ensure(p, p->tile_key2, sizeof(uint32_t) * T, s, "tile_key2"));
-        BGS_TRY(ensure(p, p->tile_idx2, sizeof(uint32_t) * T, s, "tile_idx2"));
+    // stable descending sort: Gaussian-wise tiles first (heaviest first when lpt_order is on)
+    BGS_TRY(ensure(p, p->tile_key2, sizeof(uint32_t) * T, s, "tile_key2"));
+    BGS_TRY(ensure(p, p->tile_idx2, sizeof(uint32_t) * T, s, "tile_idx2"));
+    {
         size_t tmp = 0;
+        const int kbits = p->desc.lpt_order ? 32 : 1;
         BGS_CUDA(cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp, key, (uint32_t *)p->tile_key2.p, idx,
-                                                           (uint32_t *)p->tile_idx2.p, T, 0, 32, s),
+                                                           (uint32_t *)p->tile_idx2.p, T, 0, kbits, s),
                  "sort tiles (size)");
         BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
         tmp = p->cub_tmp.bytes;
         BGS_CUDA(cub::DeviceRadixSort::SortPairsDescending(p->cub_tmp.p, tmp, key, (uint32_t *)p->tile_key2.p, idx,
-                                                           (uint32_t *)p->tile_idx2.p, T, 0, 32, s),
+                                                           (uint32_t *)p->tile_idx2.p, T, 0, kbits, s),
                  "sort tiles");
-        order = (const uint32_t *)p->tile_idx2.p;
     }
+    const uint32_t *order = (const uint32_t *)p->tile_idx2.p;
     uint32_t *counts = (uint32_t *)p->counts.p, *off = (uint32_t *)p->item_off.p;
     BGS_CUDA(bgs::launch_gather_counts(order, T, rg, W, H, tw, th, tiles_x, mode, p->desc.heavy_threshold, P, counts, s),
              "gather_counts");
@@ -261,6 +266,7 @@ int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out) {
     p->desc.device = dev;
     p->device = dev;
     cudaError_t e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess) e = cudaMalloc((void **)&p->ctrl, sizeof(bgs::DevCtrl));
     if (e == cudaSuccess) e = cudaMemset(p->ctrl, 0, sizeof(bgs::DevCtrl));
     if (e != cudaSuccess) {
@@ -275,7 +281,8 @@ int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out) {
 int bgs_plan_destroy(bgs_plan *p) {
     if (!p) return BGS_OK;
     DeviceGuard g(p->device);
-    Buf *bufs[] = {&p->touched, &p->touched_sorted, &p->dkey, &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
+    Buf *bufs[] = {&p->bin_h, &p->bin_total, &p->bin_start, &p->touched, &p->touched_sorted, &p->dkey,
+                   &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off, &p->items,
                    &p->grad_acc};
@@ -518,7 +525,46 @@ int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t
     tmp = p->cub_tmp.bytes;
     BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, dkey, dkey2, gidx, order, (int64_t)N, 0, 32, s),
              "depth sort");
-    // (2) entry offsets in depth order
+    // (2) counting sort over tile rectangles when the per-tile counters fit in shared memory
+    const size_t smem = bgs::bin_count_smem((int)T);
+    if (smem <= (size_t)p->smem_optin) {
+        long long G = std::max<long long>(512, (N * T + (1ll << 24) - 1) >> 24);
+        const long long B = (N + G - 1) / G;
+        if (B * T >= (1ll << 31)) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: tile histogram too large");
+        BGS_TRY(ensure(p, p->bin_h, sizeof(uint32_t) * B * T, s, "bin_h"));
+        BGS_TRY(ensure(p, p->bin_total, sizeof(uint32_t) * T, s, "bin_total"));
+        BGS_TRY(ensure(p, p->bin_start, sizeof(uint32_t) * T, s, "bin_start"));
+        uint32_t *Hm = (uint32_t *)p->bin_h.p, *tot = (uint32_t *)p->bin_total.p, *start = (uint32_t *)p->bin_start.p;
+        if (smem > 48 * 1024) BGS_CUDA(bgs::setup_bin_kernels(smem), "bin smem attribute");
+        BGS_CUDA(bgs::launch_bin_count(N, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, s), "bin_count");
+        BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, tot, s), "bin_colscan");
+        tmp = 0;
+        BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tot, start, (int)T, s), "tile scan (size)");
+        BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
+        tmp = p->cub_tmp.bytes;
+        BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, tot, start, (int)T, s), "tile scan");
+        BGS_CUDA(cudaMemsetAsync(&p->ctrl->num_entries, 0, sizeof(unsigned long long), s), "clear K");
+        BGS_CUDA(bgs::launch_bin_ranges((int)T, start, tot, reinterpret_cast<uint2 *>(ranges), p->ctrl, s),
+                 "bin_ranges");
+        p->host_launches += 4;  // touched, count, colscan, ranges
+        unsigned long long K = 0;
+        BGS_CUDA(cudaMemcpyAsync(&K, &p->ctrl->num_entries, sizeof K, cudaMemcpyDeviceToHost, s), "read K");
+        BGS_CUDA(cudaStreamSynchronize(s), "sync K");
+        if (needed) *needed = (int64_t)K;
+        if ((long long)K > capacity || K >= (1ull << 32) - 1) {
+            BGS_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * T, s), "clear ranges");
+            return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort: %llu entries exceed capacity %lld (or 2^32)", K,
+                        (long long)capacity);
+        }
+        if (num_rendered) *num_rendered = (int64_t)K;
+        if (K == 0) return BGS_OK;
+        BGS_CUDA(bgs::launch_bin_scatter(N, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, start, point_list,
+                                         capacity, s),
+                 "bin_scatter");
+        p->host_launches += 1;
+        return BGS_OK;
+    }
+    // (2') otherwise: entry offsets in depth order, emit, stable radix sort on the tile id
     BGS_CUDA(bgs::launch_gather_u32(N, touched, order, tsorted, s), "gather counts");
     tmp = 0;
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tsorted, off, (int64_t)N, s), "scan (size)");
@@ -536,7 +582,7 @@ int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t
     if (K >= (1ull << 32) - 1) return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort: %llu entries exceed 2^32", K);
     if (num_rendered) *num_rendered = (int64_t)K;
     if (K == 0) return BGS_OK;
-    // (3) emit entries in depth order and group them per tile with a stable sort on the tile id
+    // emit entries in depth order and group them per tile with a stable sort on the tile id
     if (T <= 65536)
         return sort_and_range<uint16_t>(p, N, means2D, radii, W, H, tw, th, (long long)K, T, point_list, ranges, s);
     return sort_and_range<uint32_t>(p, N, means2D, radii, W, H, tw, th, (long long)K, T, point_list, ranges, s);
@@ -612,11 +658,14 @@ int bgs_render_forward(bgs_plan *p, int64_t N, const float *means2D, const float
     a.recs = (const bgs::Rec *)p->recs.p;
     BGS_TRY(build_worklist(p, ranges, W, H, tw, th, mode, s));
     a.items = (const uint2 *)p->items.p;
-    const int grid = grid_for(p, bgs::forward_balanced_kernel(a.gw_pixels), bgs::forward_balanced_block_threads());
+    const int threads = bgs::forward_balanced_block_threads();
+    const int grid_g = grid_for(p, bgs::forward_gauss_kernel(a.gw_pixels), threads);
+    const int grid_p = grid_for(p, bgs::forward_pixel_kernel(), threads);
     KernelTimer kt(p, s, &p->ev_fwd);
-    BGS_CUDA(bgs::launch_forward_balanced(a, grid, s), "forward_balanced");
+    if (mode != BGS_MODE_PIXEL) BGS_CUDA(bgs::launch_forward_gauss(a, grid_g, s), "forward_gauss");
+    if (mode != BGS_MODE_GAUSSIAN) BGS_CUDA(bgs::launch_forward_pixel(a, grid_p, s), "forward_pixel");
     kt.stop();
-    p->host_launches += 1;
+    p->host_launches += (mode == BGS_MODE_AUTO) ? 2 : 1;
     return BGS_OK;
 }
 
@@ -661,7 +710,7 @@ int bgs_render_backward(bgs_plan *p, int64_t N, const float *means2D, const floa
     a.dL_dcolor = dL_dcolor;
     a.dL_ddepth = dL_ddepth;
     a.dL_dalpha = dL_dalpha;
-    a.grad_acc = (float4 *)p->grad_acc.p;
+    a.grad_acc = (float *)p->grad_acc.p;
     a.ctrl = p->ctrl;
     a.chunk = p->desc.queue_chunk;
     if (mode == BGS_MODE_STATIC) {

@@ -184,30 +184,53 @@ cudaError_t launch_gather_u32(long long N, const uint32_t *src, const uint32_t *
 }
 
 // Emits the entries of the depth-ordered Gaussians: position s of the depth order writes
-// one (tile id, Gaussian index) pair per covered tile at offsets[s].
+// one (tile id, Gaussian index) pair per covered tile at offsets[s], row-major over its
+// rectangle.  A warp takes 32 consecutive positions and writes their runs one after the
+// other, the 32 lanes storing consecutive entries of a run (coalesced stores).
 template <typename KeyT>
 __global__ void __launch_bounds__(256) k_duplicate(long long N, const uint32_t *__restrict__ order,
                                                    const float2 *__restrict__ means2D, const int *__restrict__ radii,
                                                    const unsigned long long *__restrict__ offsets, int tw, int th,
                                                    int tx, int ty, KeyT *__restrict__ keys, uint32_t *__restrict__ vals,
                                                    long long capacity) {
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    const uint32_t i = order[s];
-    const int r = radii[i];
-    if (r <= 0) return;
-    const float2 m = means2D[i];
-    int x0, x1, y0, y1;
-    tile_rect(m.x, m.y, r, tw, th, tx, ty, x0, x1, y0, y1);
-    long long off = (long long)offsets[s];
-    for (int y = y0; y < y1; ++y)
-        for (int x = x0; x < x1; ++x) {
-            if (off < capacity) {
-                keys[off] = (KeyT)(y * tx + x);
-                vals[off] = i;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    uint32_t i = 0;
+    int x0 = 0, y0 = 0, w = 1, cnt = 0;
+    long long off = 0;
+    if (s < N) {
+        i = order[s];
+        const int r = radii[i];
+        if (r > 0) {
+            const float2 m = means2D[i];
+            int x1, y1;
+            tile_rect(m.x, m.y, r, tw, th, tx, ty, x0, x1, y0, y1);
+            if (x1 > x0 && y1 > y0) {
+                w = x1 - x0;
+                cnt = w * (y1 - y0);
+                off = (long long)offsets[s];
             }
-            ++off;
         }
+    }
+    unsigned pending = __ballot_sync(0xffffffffu, cnt > 0);
+    while (pending) {
+        const int q = __ffs(pending) - 1;
+        pending &= pending - 1;
+        const int cq = __shfl_sync(0xffffffffu, cnt, q);
+        const int wq = __shfl_sync(0xffffffffu, w, q);
+        const int xq = __shfl_sync(0xffffffffu, x0, q);
+        const int yq = __shfl_sync(0xffffffffu, y0, q);
+        const uint32_t iq = __shfl_sync(0xffffffffu, i, q);
+        const long long oq = __shfl_sync(0xffffffffu, off, q);
+        for (int k = lane; k < cq; k += 32) {
+            const long long o = oq + k;
+            if (o < capacity) {
+                const int dy = k / wq;
+                keys[o] = (KeyT)((yq + dy) * tx + xq + (k - dy * wq));
+                vals[o] = iq;
+            }
+        }
+    }
 }
 
 template <typename KeyT>
@@ -240,19 +263,34 @@ cudaError_t launch_count_total(long long N, const uint32_t *touched, const unsig
 }
 
 // ranges[t] = [first, last+1) of tile t in the sorted tile keys (ranges zeroed beforehand).
+// Each thread inspects 8 consecutive keys and their right neighbour.
 template <typename KeyT>
 __global__ void __launch_bounds__(256) k_ranges(const KeyT *__restrict__ keys, long long K, uint2 *__restrict__ ranges) {
-    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= K) return;
-    const uint32_t t = keys[j];
-    if (j == 0 || (uint32_t)keys[j - 1] != t) ranges[t].x = (uint32_t)j;
-    if (j == K - 1 || (uint32_t)keys[j + 1] != t) ranges[t].y = (uint32_t)(j + 1);
+    const long long j0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 8;
+    if (j0 >= K) return;
+    const int n = (int)min(8ll, K - j0);
+    uint32_t k[9];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) k[q] = q < n ? (uint32_t)keys[j0 + q] : 0u;
+    k[8] = (j0 + 8 < K) ? (uint32_t)keys[j0 + 8] : 0xffffffffu;
+    const uint32_t prev = j0 > 0 ? (uint32_t)keys[j0 - 1] : 0xffffffffu;
+    if (prev != k[0]) ranges[k[0]].x = (uint32_t)j0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (q >= n) break;
+        const uint32_t nxt = (q + 1 < n) ? k[q + 1] : k[8];
+        if (nxt != k[q]) {
+            ranges[k[q]].y = (uint32_t)(j0 + q + 1);
+            if (q + 1 < n) ranges[k[q + 1]].x = (uint32_t)(j0 + q + 1);
+        }
+    }
 }
 
 template <typename KeyT>
 cudaError_t launch_ranges(const KeyT *keys, long long K, uint2 *ranges, cudaStream_t s) {
     if (K == 0) return cudaSuccess;
-    k_ranges<KeyT><<<(unsigned)((K + 255) / 256), 256, 0, s>>>(keys, K, ranges);
+    const long long threads = (K + 7) / 8;
+    k_ranges<KeyT><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(keys, K, ranges);
     return cudaGetLastError();
 }
 template cudaError_t launch_ranges<uint16_t>(const uint16_t *, long long, uint2 *, cudaStream_t);

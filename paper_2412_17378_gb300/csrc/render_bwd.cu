@@ -12,10 +12,9 @@
 // Each pixel walks its tile's list from its last contributor back to the front,
 // recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final T (no per-pair state is
 // kept by the forward).  All lanes of a warp visit the same list entry at the same step,
-// so the per-Gaussian contributions of the warp's 32 pixels are summed with shuffles and
-// added to a packed accumulator by one lane (warp-aggregated atomics, three 16-byte
-// vector atomics per Gaussian and warp).  A final pass scales and scatters the
-// accumulator into the ABI's gradient arrays.
+// so the per-Gaussian contributions of the warp's pixels are summed with shuffles and added
+// to a packed accumulator [N][12] with one red.add instruction (warp-aggregated atomics).
+// A final pass scales and scatters the accumulator into the ABI's gradient arrays.
 #include "bgs_internal.cuh"
 
 namespace bgs {
@@ -53,28 +52,27 @@ __device__ __forceinline__ PixState load_pixel(const BwdArgs &a, int px, int py,
     return s;
 }
 
-// One (pixel, entry) step of the backward walk.  Returns the 10 gradient contributions
-// (zero when the pair is skipped) in v[]:
+// One (pixel, entry) step of the backward walk.  Adds the pair's 10 gradient
+// contributions (nothing when the pair is skipped) to v[]:
 //   v0 = dL/dpower (2 qa dx + qb dy), v1 = dL/dpower (2 qc dy + qb dx),
 //   v2 = dL/dpower dx^2, v3 = dL/dpower dx dy, v4 = dL/dpower dy^2,
 //   v5 = dL/do, v6..8 = dL/dc, v9 = dL/d(depth)
+// (power is the natural-log exponent; the final pass applies the ln2 and -1/2 factors).
 __device__ __forceinline__ bool pair_backward(const Rec &r, float pxf, float pyf, bool active, PixState &s,
                                               float v[10]) {
     float dx, dy, G;
     const float p2 = pair_power2(r.a, r.b.x, pxf, pyf, dx, dy);
     const float al = pair_alpha(p2, r.b.y, G);
     const bool valid = active && p2 <= 0.f && al >= kAlphaMin;
-#pragma unroll
-    for (int k = 0; k < 10; ++k) v[k] = 0.f;
     if (valid) {
         const float om = 1.f - al;
         const float io = 1.f / om;
         s.T = s.T * io;  // T_i
         const float w = al * s.T;
-        v[6] = w * s.g0;
-        v[7] = w * s.g1;
-        v[8] = w * s.g2;
-        v[9] = w * s.gD;
+        v[6] += w * s.g0;
+        v[7] += w * s.g1;
+        v[8] += w * s.g2;
+        v[9] += w * s.gD;
         const float dLda = s.T * ((r.c.x - s.R0) * s.g0 + (r.c.y - s.R1) * s.g1 + (r.c.z - s.R2) * s.g2 +
                                   (r.b.z - s.Rd) * s.gD) +
                            s.Tf * io * s.gA;
@@ -85,29 +83,42 @@ __device__ __forceinline__ bool pair_backward(const Rec &r, float pxf, float pyf
         const float o = r.b.y;
         if (o * G <= kAlphaMax) {
             const float gp = o * G * dLda;  // dL/dpower
-            v[0] = gp * (2.f * r.a.z * dx + r.a.w * dy);
-            v[1] = gp * (2.f * r.b.x * dy + r.a.w * dx);
-            v[2] = gp * dx * dx;
-            v[3] = gp * dx * dy;
-            v[4] = gp * dy * dy;
-            v[5] = G * dLda;
+            v[0] += gp * (2.f * r.a.z * dx + r.a.w * dy);
+            v[1] += gp * (2.f * r.b.x * dy + r.a.w * dx);
+            v[2] += gp * dx * dx;
+            v[3] += gp * dx * dy;
+            v[4] += gp * dy * dy;
+            v[5] += G * dLda;
         }
     }
     return valid;
 }
 
-__device__ __forceinline__ void warp_accumulate(float v[10], float4 *acc, uint32_t g, int lane) {
+// Sums v[0..9] over the warp's 32 lanes and adds the 10 totals to acc[0..9].  Recursive
+// halving (reduce-scatter): at each of 4 stages a lane keeps one half of its remaining
+// values and adds the partner's copy of that half (16 -> 8 -> 4 -> 2 -> 1 values, the
+// vector padded to 16), then one butterfly step completes the sum.  Lane l ends with
+// element (l >> 1) & 15; the even lanes holding elements 0..9 issue one red.add each, all
+// in the same instruction.
+__device__ __forceinline__ void warp_reduce_red10(const float v[10], float *acc, int lane) {
+    float a[16];
 #pragma unroll
-    for (int k = 0; k < 10; ++k) {
+    for (int j = 0; j < 16; ++j) a[j] = j < 10 ? v[j] : 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFullB, v[k], o);
+    for (int stage = 0; stage < 4; ++stage) {
+        const int off = 16 >> stage;  // 16, 8, 4, 2
+        const int half = 8 >> stage;  // 8, 4, 2, 1
+        const bool hi = (lane & off) != 0;
+#pragma unroll
+        for (int j = 0; j < half; ++j) {
+            const float send = hi ? a[j] : a[j + half];
+            const float keep = hi ? a[j + half] : a[j];
+            a[j] = keep + __shfl_xor_sync(kFullB, send, off);
+        }
     }
-    if (lane == 0) {
-        float4 *dst = acc + 3ull * g;
-        atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
-        atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
-        atomicAdd(dst + 2, make_float4(v[8], v[9], 0.f, 0.f));
-    }
+    const float tot = a[0] + __shfl_xor_sync(kFullB, a[0], 1);
+    const int idx = (lane >> 1) & 15;
+    if ((lane & 1) == 0 && idx < 10 && tot != 0.f) atomicAdd(acc + idx, tot);
 }
 
 __device__ __forceinline__ Rec load_rec_bwd(const BwdArgs &a, uint32_t j) {
@@ -181,9 +192,10 @@ __global__ void __launch_bounds__(1024) k_backward_static(BwdArgs a) {
         for (int k = 0; k < cnt; ++k) {
             const Rec r = srec[k];
             const int pos = (int)(top - 1 - k - rg.x);
-            float v[10];
+            float v[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const bool valid = pair_backward(r, pxf, pyf, pos < s.nc, s, v);
-            if (__any_sync(kFullB, valid)) warp_accumulate(v, a.grad_acc, __float_as_uint(r.c.w), lane);
+            if (__any_sync(kFullB, valid))
+                warp_reduce_red10(v, a.grad_acc + 12ull * __float_as_uint(r.c.w), lane);
         }
     }
 }
@@ -199,20 +211,34 @@ cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s) {
 // =====================================================================================
 // balanced persistent backward: warps pull pixel-wise items (8x4 sub-blocks)
 // =====================================================================================
+// Pixel-wise item: the 8 x (4 kPixPerLane) sub-block of the forward's items; lane l owns
+// the pixels (l % 8, l / 8 + 4 q).  The lane adds its pixels' contributions before the
+// warp-wide reduction, so one reduction serves 8 x 4 kPixPerLane pixels.
 __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int sub, Rec *buf, int lane) {
+    constexpr int Q = kPixPerLane;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int x0 = tx * a.tile_w, y0 = ty * a.tile_h;
     const int vw = min(a.tile_w, a.W - x0), vh = min(a.tile_h, a.H - y0);
-    const int cxs = (vw + 7) >> 3;
+    const int cxs = (vw + kPixItemW - 1) / kPixItemW;
     const int sx = sub % cxs, sy = sub / cxs;
-    const int px = x0 + sx * 8 + (lane & 7), py = y0 + sy * 4 + (lane >> 3);
-    const bool inside = px < x0 + vw && py < y0 + vh;
+    const int px = x0 + sx * kPixItemW + (lane & 7);
+    const int py0 = y0 + sy * kPixItemH + (lane >> 3);
     const uint2 rg = load_range_bwd(a, tile);
-    PixState s = load_pixel(a, px, py, inside);
-    if (s.nc > (int)(rg.y - rg.x)) s.nc = (int)(rg.y - rg.x);
-    const int maxnc = __reduce_max_sync(kFullB, s.nc);
+    const int n = (int)(rg.y - rg.x);
+    PixState s[Q];
+    float pyf[Q];
+    int maxnc = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int py = py0 + 4 * q;
+        s[q] = load_pixel(a, px, py, px < x0 + vw && py < y0 + vh);
+        if (s[q].nc > n) s[q].nc = n;
+        maxnc = max(maxnc, s[q].nc);
+        pyf[q] = (float)py;
+    }
+    maxnc = __reduce_max_sync(kFullB, maxnc);
     const uint32_t hi = rg.x + (uint32_t)maxnc;
-    const float pxf = (float)px, pyf = (float)py;
+    const float pxf = (float)px;
     for (uint32_t top = hi; top > rg.x;) {
         const uint32_t lo = top - min(32u, top - rg.x);
         const int cnt = (int)(top - lo);
@@ -222,9 +248,11 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
         for (int k = 0; k < cnt; ++k) {
             const Rec r = buf[k];
             const int pos = (int)(top - 1 - k - rg.x);
-            float v[10];
-            const bool valid = pair_backward(r, pxf, pyf, pos < s.nc, s, v);
-            if (__any_sync(kFullB, valid)) warp_accumulate(v, a.grad_acc, __float_as_uint(r.c.w), lane);
+            float v[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) any |= pair_backward(r, pxf, pyf[q], pos < s[q].nc, s[q], v);
+            if (__any_sync(kFullB, any)) warp_reduce_red10(v, a.grad_acc + 12ull * __float_as_uint(r.c.w), lane);
         }
         top = lo;
     }

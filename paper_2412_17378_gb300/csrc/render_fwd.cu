@@ -5,16 +5,19 @@
 //                      shared memory) -- the paper's "naive renderCUDA" (Algorithm 4)
 //                      with the shared-memory staging of features and depths of
 //                      Sec. 5.2.2.  It is the baseline the balanced kernel is timed against.
-//  k_forward_balanced  persistent kernel (Sec. 4.1's inter-block dynamic distribution,
+//  k_forward_gauss / k_forward_pixel
+//                      persistent kernels (Sec. 4.1's inter-block dynamic distribution,
 //                      taken down to warp granularity): every warp pulls work items from
-//                      a device atomic queue.  An item is either
-//                        - pixel-wise: 32 pixels (an 8x4 sub-block of a tile), one per
-//                          lane, walking the tile's list through a warp-private shared
-//                          memory window of 32 records; or
+//                      a device atomic queue.  The work list holds the Gaussian-wise items
+//                      first, then the pixel-wise ones; each kind has its own kernel (and
+//                      register budget) and its own queue cursor:
 //                        - Gaussian-wise (Sec. 4.2, Algorithm 6, fine-grained per
 //                          Sec. 4.3): P pixels of a tile processed one after another by
 //                          the whole warp, lanes splitting the list 32 entries at a time
-//                          and combining transmittance with a shuffle prefix product.
+//                          and combining transmittance with a shuffle prefix product;
+//                        - pixel-wise: an 8x8 sub-block of a tile, two pixels per lane,
+//                          walking the tile's list through a warp-private shared memory
+//                          window of 32 records.
 //
 // Both evaluate each (pixel, entry) pair with the same code (pair_power2 / pair_alpha),
 // so skip and stop decisions of the forward and backward kernels agree bit for bit.
@@ -165,56 +168,83 @@ __device__ __forceinline__ TileGeom tile_geom(const FwdArgs &a, int tile) {
     return t;
 }
 
-// Pixel-wise item: 32 pixels of an 8x4 sub-block, lane = pixel.
+// Pixel-wise item: an 8 x (4 kPixPerLane) sub-block of a tile; lane l owns the pixels
+// (l % 8, l / 8 + 4 q).  The warp walks the tile's list through a warp-private window of
+// 32 records in shared memory; each record is read once per lane (broadcast) and applied
+// to the lane's kPixPerLane pixels, which share dx.
 __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, Rec *buf, int lane,
                                            unsigned long long &st_eval, unsigned long long &st_acc) {
+    constexpr int Q = kPixPerLane;
     const TileGeom tg = tile_geom(a, tile);
-    const int cxs = (tg.vw + 7) >> 3;
+    const int cxs = (tg.vw + kPixItemW - 1) / kPixItemW;
     const int sx = sub % cxs, sy = sub / cxs;
-    const int px = tg.x0 + sx * 8 + (lane & 7), py = tg.y0 + sy * 4 + (lane >> 3);
-    const bool inside = px < tg.x0 + tg.vw && py < tg.y0 + tg.vh;
+    const int px = tg.x0 + sx * kPixItemW + (lane & 7);
+    const int py0 = tg.y0 + sy * kPixItemH + (lane >> 3);
     const uint2 rg = load_range(a, tile);
-    const float pxf = (float)px, pyf = (float)py;
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, D = 0.f, A = 0.f;
-    int last = 0, neval = (int)(rg.y - rg.x), nacc = 0;
-    bool done = !inside;
+    const float pxf = (float)px;
+    float pyf[Q], T[Q], c0[Q], c1[Q], c2[Q], D[Q], A[Q];
+    int last[Q], neval[Q], nacc[Q];
+    bool done[Q], inside[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int py = py0 + 4 * q;
+        inside[q] = px < tg.x0 + tg.vw && py < tg.y0 + tg.vh;
+        pyf[q] = (float)py;
+        T[q] = 1.f;
+        c0[q] = c1[q] = c2[q] = D[q] = A[q] = 0.f;
+        last[q] = 0;
+        neval[q] = (int)(rg.y - rg.x);
+        nacc[q] = 0;
+        done[q] = !inside[q];
+    }
     for (uint32_t base = rg.x; base < rg.y; base += 32) {
-        if (__all_sync(kFull, done)) break;
+        bool lane_done = true;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) lane_done = lane_done && done[q];
+        if (__all_sync(kFull, lane_done)) break;
         const uint32_t j = base + lane;
         __syncwarp();
         if (j < rg.y) buf[lane] = load_rec(a, j);
         __syncwarp();
         const int cnt = min(32, (int)(rg.y - base));
+        const int pos0 = (int)(base - rg.x);
         for (int k = 0; k < cnt; ++k) {
             const float4 ra = buf[k].a;
-            const float4 rb = buf[k].b;
-            float dx, dy, G;
-            const float p2 = pair_power2(ra, rb.x, pxf, pyf, dx, dy);
-            const float al = pair_alpha(p2, rb.y, G);
-            if (!done && p2 <= 0.f && al >= kAlphaMin) {
-                const float tt = T * (1.f - al);
-                if (tt < kTMin) {
-                    done = true;
-                    neval = (int)(base + k + 1 - rg.x);
-                } else {
-                    const float4 rc = buf[k].c;
-                    const float w = al * T;
-                    c0 += w * rc.x;
-                    c1 += w * rc.y;
-                    c2 += w * rc.z;
-                    D += w * rb.z;
-                    A += w;
-                    T = tt;
-                    last = (int)(base + k + 1 - rg.x);
-                    ++nacc;
+            const float2 rb = *reinterpret_cast<const float2 *>(&buf[k].b);
+            const PairX px2 = pair_x(ra, pxf);  // shared by the lane's pixels (same column)
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                float dy, G;
+                const float p2 = pair_power2_y(px2, ra.y, rb.x, pyf[q], dy);
+                const float al = pair_alpha(p2, rb.y, G);
+                if (!done[q] && p2 <= 0.f && al >= kAlphaMin) {
+                    const float tt = T[q] * (1.f - al);
+                    if (tt < kTMin) {
+                        done[q] = true;
+                        neval[q] = pos0 + k + 1;
+                    } else {
+                        const float4 rc = buf[k].c;
+                        const float w = al * T[q];
+                        c0[q] += w * rc.x;
+                        c1[q] += w * rc.y;
+                        c2[q] += w * rc.z;
+                        D[q] += w * buf[k].b.z;
+                        A[q] += w;
+                        T[q] = tt;
+                        last[q] = pos0 + k + 1;
+                        ++nacc[q];
+                    }
                 }
             }
         }
     }
-    if (inside) {
-        write_pixel(a, px, py, T, c0, c1, c2, D, A, last, neval);
-        st_eval += (unsigned long long)neval;
-        st_acc += (unsigned long long)nacc;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (inside[q]) {
+            write_pixel(a, px, py0 + 4 * q, T[q], c0[q], c1[q], c2[q], D[q], A[q], last[q], neval[q]);
+            st_eval += (unsigned long long)neval[q];
+            st_acc += (unsigned long long)nacc[q];
+        }
     }
 }
 
@@ -327,8 +357,47 @@ __device__ __forceinline__ void gauss_item(const FwdArgs &a, int tile, int sub, 
     }
 }
 
+__device__ __forceinline__ void flush_stats(const FwdArgs &a, int lane, unsigned long long st_eval,
+                                            unsigned long long st_acc, unsigned long long st_items) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        st_eval += __shfl_xor_sync(kFull, st_eval, o);
+        st_acc += __shfl_xor_sync(kFull, st_acc, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&a.ctrl->eval_pairs, st_eval);
+        atomicAdd(&a.ctrl->contrib_pairs, st_acc);
+        atomicAdd(&a.ctrl->items_done, st_items);
+    }
+}
+
+// Gaussian-wise items [0, num_gauss) of the work list.  Launched first; lets the pixel-wise
+// kernel launch as soon as all its blocks are resident (programmatic dependent launch),
+// so that pixel-wise blocks take over SMs as Gaussian-wise blocks run out of items.
 template <int P>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_balanced(FwdArgs a) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_gauss(FwdArgs a) {
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int lane = threadIdx.x & 31;
+    const unsigned num_items = a.ctrl->num_gauss;
+    const unsigned chunk = (unsigned)a.chunk;
+    unsigned long long st_eval = 0, st_acc = 0, st_items = 0;
+    while (true) {
+        unsigned first = 0;
+        if (lane == 0) first = atomicAdd(&a.ctrl->queue_head_g, chunk);
+        first = __shfl_sync(kFull, first, 0);
+        if (first >= num_items) break;
+        const unsigned end = min(first + chunk, num_items);
+        for (unsigned it = first; it < end; ++it) {
+            const uint2 item = a.items[it];
+            gauss_item<P>(a, (int)item.x, (int)(item.y & ~kKindGauss), lane, st_eval, st_acc);
+            ++st_items;
+        }
+    }
+    flush_stats(a, lane, st_eval, st_acc, st_items);
+}
+
+// Pixel-wise items [num_gauss, num_items) of the work list.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_pixel(FwdArgs a) {
     __shared__ Rec sbuf[kWarpsPerBlock][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Rec *buf = sbuf[warp];
@@ -343,47 +412,53 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_balanced(FwdArg
         const unsigned end = min(first + chunk, num_items);
         for (unsigned it = first; it < end; ++it) {
             const uint2 item = a.items[it];
-            const int sub = (int)(item.y & ~kKindGauss);
-            if (item.y & kKindGauss)
-                gauss_item<P>(a, (int)item.x, sub, lane, st_eval, st_acc);
-            else
-                pixel_item(a, (int)item.x, sub, buf, lane, st_eval, st_acc);
+            pixel_item(a, (int)item.x, (int)(item.y & ~kKindGauss), buf, lane, st_eval, st_acc);
             ++st_items;
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        st_eval += __shfl_xor_sync(kFull, st_eval, o);
-        st_acc += __shfl_xor_sync(kFull, st_acc, o);
-    }
-    if (lane == 0) {
-        atomicAdd(&a.ctrl->eval_pairs, st_eval);
-        atomicAdd(&a.ctrl->contrib_pairs, st_acc);
-        atomicAdd(&a.ctrl->items_done, st_items);
-    }
+    flush_stats(a, lane, st_eval, st_acc, st_items);
 }
 
 int forward_balanced_block_threads() { return kWarpsPerBlock * 32; }
-const void *forward_balanced_kernel(int gw_pixels) {
+
+const void *forward_gauss_kernel(int gw_pixels) {
     switch (gw_pixels) {
-        case 1: return (const void *)k_forward_balanced<1>;
-        case 2: return (const void *)k_forward_balanced<2>;
-        case 4: return (const void *)k_forward_balanced<4>;
-        case 8: return (const void *)k_forward_balanced<8>;
+        case 1: return (const void *)k_forward_gauss<1>;
+        case 2: return (const void *)k_forward_gauss<2>;
+        case 4: return (const void *)k_forward_gauss<4>;
+        case 8: return (const void *)k_forward_gauss<8>;
         default: return nullptr;
     }
 }
 
-cudaError_t launch_forward_balanced(const FwdArgs &a, int grid, cudaStream_t s) {
+const void *forward_pixel_kernel() { return (const void *)k_forward_pixel; }
+
+cudaError_t launch_forward_gauss(const FwdArgs &a, int grid, cudaStream_t s) {
     const int threads = kWarpsPerBlock * 32;
     switch (a.gw_pixels) {
-        case 1: k_forward_balanced<1><<<grid, threads, 0, s>>>(a); break;
-        case 2: k_forward_balanced<2><<<grid, threads, 0, s>>>(a); break;
-        case 4: k_forward_balanced<4><<<grid, threads, 0, s>>>(a); break;
-        case 8: k_forward_balanced<8><<<grid, threads, 0, s>>>(a); break;
+        case 1: k_forward_gauss<1><<<grid, threads, 0, s>>>(a); break;
+        case 2: k_forward_gauss<2><<<grid, threads, 0, s>>>(a); break;
+        case 4: k_forward_gauss<4><<<grid, threads, 0, s>>>(a); break;
+        case 8: k_forward_gauss<8><<<grid, threads, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// Launched right after k_forward_gauss on the same stream with programmatic stream
+// serialisation: the two kernels touch disjoint pixels, so no wait is needed.
+cudaError_t launch_forward_pixel(const FwdArgs &a, int grid, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kWarpsPerBlock * 32);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_forward_pixel, a);
 }
 
 }  // namespace bgs

@@ -22,22 +22,26 @@ __device__ __forceinline__ uint32_t tile_item_count(int t, uint32_t n, int W, in
     const int tx = t % tiles_x, ty = t / tiles_x;
     const int vw = min(tile_w, W - tx * tile_w), vh = min(tile_h, H - ty * tile_h);
     if (tile_is_gauss(mode, heavy_threshold, n)) return (uint32_t)((vw * vh + gw_pixels - 1) / gw_pixels);
-    return (uint32_t)(((vw + 7) >> 3) * ((vh + 3) >> 2));
+    return (uint32_t)(((vw + kPixItemW - 1) / kPixItemW) * ((vh + kPixItemH - 1) / kPixItemH));
 }
 
-__global__ void k_tile_counts(const uint2 *__restrict__ ranges, int num_tiles, uint32_t *__restrict__ tile_key,
-                              uint32_t *__restrict__ tile_idx) {
+// Sort key of each tile: its list length (heaviest first) when lpt is on, else only its
+// kind, so that the descending stable sort always puts Gaussian-wise tiles first.
+__global__ void k_tile_counts(const uint2 *__restrict__ ranges, int num_tiles, int mode, int heavy_threshold, int lpt,
+                              uint32_t *__restrict__ tile_key, uint32_t *__restrict__ tile_idx) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= num_tiles) return;
     const uint2 rg = ranges[t];
-    tile_key[t] = rg.y >= rg.x ? rg.y - rg.x : 0u;
+    const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
+    tile_key[t] = lpt ? n : (tile_is_gauss(mode, heavy_threshold, n) ? 1u : 0u);
     tile_idx[t] = (uint32_t)t;
 }
 
-cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int, int, int, int, int, int, int, int,
+cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int mode, int heavy_threshold, int lpt,
                                uint32_t *tile_key, uint32_t *tile_idx, cudaStream_t s) {
     if (num_tiles == 0) return cudaSuccess;
-    k_tile_counts<<<(num_tiles + 255) / 256, 256, 0, s>>>(ranges, num_tiles, tile_key, tile_idx);
+    k_tile_counts<<<(num_tiles + 255) / 256, 256, 0, s>>>(ranges, num_tiles, mode, heavy_threshold, lpt, tile_key,
+                                                         tile_idx);
     return cudaGetLastError();
 }
 
@@ -75,9 +79,22 @@ __global__ void k_emit_items(const uint32_t *__restrict__ order, const uint32_t 
     const uint32_t kind = tile_is_gauss(mode, heavy_threshold, n) ? kKindGauss : 0u;
     const uint32_t c = counts[i], off = offsets[i];
     for (uint32_t q = lane; q < c; q += 32) items[off + q] = make_uint2(t, kind | q);
-    if (i == num_tiles - 1 && lane == 0) {
-        ctrl->num_items = off + c;
-        ctrl->queue_head = 0u;
+    if (lane == 0) {
+        // Gaussian-wise tiles come first: the boundary between the kinds sets num_gauss
+        bool next_gauss = false;
+        if (i + 1 < num_tiles) {
+            const uint2 rn = ranges[order[i + 1]];
+            next_gauss = tile_is_gauss(mode, heavy_threshold, rn.y >= rn.x ? rn.y - rn.x : 0u);
+        }
+        uint32_t ng = 0xffffffffu;
+        if (i == 0 && !kind) ng = 0u;
+        if (kind && !next_gauss) ng = off + c;
+        if (ng != 0xffffffffu) {
+            ctrl->num_gauss = ng;
+            ctrl->queue_head = ng;
+            ctrl->queue_head_g = 0u;
+        }
+        if (i == num_tiles - 1) ctrl->num_items = off + c;
     }
 }
 

@@ -73,7 +73,9 @@ def test_preprocess_matches_oracle(R, plan):
 
 
 @pytest.mark.parametrize("name,scale,tile,W_H", [("cfg1", 1.0, (16, 16), None), ("cfg2", 0.02, (16, 8), None),
-                                                 ("cfg1", 1.0, (16, 16), (250, 130))])
+                                                 ("cfg1", 1.0, (16, 16), (250, 130)),
+                                                 # 65536 tiles: counters exceed shared memory -> radix-sort path
+                                                 ("cfg1", 0.1, (8, 4), (2048, 1024))])
 def test_binning_bit_exact(R, plan, name, scale, tile, W_H):
     s = scene(name, scale)
     if W_H is not None:
