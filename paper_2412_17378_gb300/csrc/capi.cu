@@ -469,7 +469,9 @@ int sort_and_range(bgs_plan *p, long long N, const float *means2D, const int32_t
     KeyT *kin = (KeyT *)p->keys_in.p, *kout = (KeyT *)p->keys_out.p;
     uint32_t *vin = (uint32_t *)p->vals_in.p;
     BGS_CUDA(bgs::launch_duplicate<KeyT>(N, order, means2D, radii, off, W, H, tw, th, kin, vin, K, s), "duplicate");
-    const int end_bit = bits_for(T);
+    // tile ids are < T: sort on the bits of T - 1 only (never more than the key type holds)
+    const int end_bit = bits_for(T - 1);
+    if (end_bit > (int)(8 * sizeof(KeyT))) return fail(BGS_ERR_INVALID, "tile id does not fit the sort key");
     size_t tmp = 0;
     BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, kin, kout, vin, point_list, (int64_t)K, 0, end_bit, s),
              "tile sort (size)");
