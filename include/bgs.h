@@ -187,6 +187,29 @@ int bgs_render_backward(bgs_plan *plan, int64_t N, const float *means2D, const f
                         const float *dL_dalpha, float *dL_dmeans2D, float *dL_dconic, float *dL_dopacity,
                         float *dL_dcolors, float *dL_ddepths, void *stream);
 
+/* ---- allocation-free forward ----------------------------------------------------------
+   The paper has no counterpart to this entry point; it serves callers that cannot let
+   the library allocate device memory -- a host application that owns all device memory
+   under a fixed budget (a game engine, an inference server), a plugin loaded into such a
+   process, or a runtime that forbids allocations after start-up.  It computes the same
+   outputs as bgs_render_forward (persistent pixel-wise kernel, heaviest tiles first) from
+   the same caller-owned inputs and outputs, needs no plan, and calls no cudaMalloc,
+   cudaFree or other allocating routine.  Its scratch (work-queue counters and the tile
+   order) lives in one fixed array of about 256 KiB in this library's device memory,
+   present on every GPU that loads the library until the process exits; it holds at most
+   65536 tiles, and larger tile grids are rejected with BGS_ERR_CAPACITY.  It runs on the
+   caller's current device; the first call on a device looks up the array's device
+   address (no allocation) and should come before any stream capture.  All calls share
+   the array: each call resets what must start at zero, consecutive calls on one stream
+   are independent, and calls that overlap on the GPU race.  Entries whose index is >= N
+   or whose tile span passes num_entries are rendered transparent.  tile_w must be a
+   multiple of 8 and tile_h of 4. */
+int bgs_render_forward_noalloc(int64_t N, const float *means2D, const float *conic_opacity, const float *colors,
+                               const float *depths, const uint32_t *point_list, int64_t num_entries,
+                               const uint32_t *ranges, int32_t W, int32_t H, int32_t tile_w, int32_t tile_h,
+                               const float *bg, float *out_color, float *out_depth, float *out_alpha, float *final_T,
+                               int32_t *n_contrib, int32_t *n_eval, void *stream);
+
 /* ---- diagnostics -------------------------------------------------------------------
    Measures sustained per-SM issue rates of the FP32 pipe (FFMA) and of the MUFU ex2
    unit with dependent-chain-free loops on every SM; writes operations per SM per clock

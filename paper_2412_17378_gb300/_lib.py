@@ -32,6 +32,7 @@ EXPORTS = [
     "bgs_plan_reserve", "bgs_workspace_size", "bgs_check", "bgs_plan_stats", "bgs_plan_reset_stats",
     "bgs_plan_num_sms", "bgs_last_error", "bgs_preprocess", "bgs_bin_and_sort", "bgs_render_forward",
     "bgs_render_backward", "bgs_probe_pipe_rates", "bgs_debug_exp2", "bgs_plan_timing", "bgs_plan_kernel_ms",
+    "bgs_render_forward_noalloc",
 ]
 
 
@@ -103,6 +104,8 @@ def load(build_if_needed: bool = True):
                                             P, P, P, P, P, P, P, P, P, P, P]
         lib.bgs_probe_pipe_rates.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P]
         lib.bgs_debug_exp2.argtypes = [P, P, i64, P]
+        lib.bgs_render_forward_noalloc.argtypes = [i64, P, P, P, P, P, i64, P, i32, i32, i32, i32, P,
+                                                   P, P, P, P, P, P, P]
         _lib = lib
         return lib
 

@@ -141,6 +141,9 @@ struct BwdArgs {
     int chunk;
 };
 
+// Records a message for bgs_last_error() and returns code.
+int set_error(int code, const char *msg);
+
 // ---- launchers (each returns cudaGetLastError() of its launch) ------------------------
 cudaError_t launch_preprocess(long long N, const float *means3D, const float *log_scales, const float *quats,
                               const float *opacities, const bgs_camera &cam, int tile_w, int tile_h,

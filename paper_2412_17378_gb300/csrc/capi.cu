@@ -64,6 +64,11 @@ int bits_for(long long v) {
 
 }  // namespace
 
+namespace bgs {
+// Records a message for bgs_last_error() (used by entry points defined in other files).
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace bgs
+
 struct bgs_plan {
     bgs_plan_desc desc;
     int device = 0;

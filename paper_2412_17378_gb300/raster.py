@@ -18,6 +18,7 @@ from . import _lib
 from ._lib import MODES, BgsError, check
 
 __all__ = ["Plan", "camera_struct", "preprocess", "bin_and_sort", "render_forward", "render_backward",
+           "render_forward_noalloc",
            "RenderFunction", "render", "probe_pipe_rates", "debug_exp2", "BgsError", "MODES"]
 
 
@@ -227,6 +228,32 @@ def render_backward(plan: Plan, means2D, conic_opacity, colors, depths, point_li
                                         _ptr(dL_ddepth), _ptr(dL_dalpha), _ptr(out["means2D"]), _ptr(out["conic"]),
                                         _ptr(out["opacity"]), _ptr(out["colors"]), _ptr(out.get("depths")),
                                         _stream(dev)), "bgs_render_backward")
+    return out
+
+
+def render_forward_noalloc(means2D, conic_opacity, colors, depths, point_list, num_entries: int, ranges, W: int,
+                           H: int, tile=(16, 16), bg=(0.0, 0.0, 0.0), n_eval: bool = False, out=None):
+    """bgs_render_forward_noalloc: the allocation-free forward (no plan; the library keeps
+    its scratch in a fixed device array).  ``out`` may pass preallocated output tensors."""
+    N = means2D.shape[0]
+    _req(means2D, "means2D", torch.float32, (N, 2))
+    _req(conic_opacity, "conic_opacity", torch.float32, (N, 4))
+    _req(colors, "colors", torch.float32, (N, 3))
+    _req(depths, "depths", torch.float32, (N,))
+    dev = means2D.device
+    if out is None:
+        out = dict(color=torch.empty((3, H, W), device=dev), depth=torch.empty((H, W), device=dev),
+                   alpha=torch.empty((H, W), device=dev), final_T=torch.empty((H, W), device=dev),
+                   n_contrib=torch.empty((H, W), dtype=torch.int32, device=dev))
+        if n_eval:
+            out["n_eval"] = torch.empty((H, W), dtype=torch.int32, device=dev)
+    bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    with torch.cuda.device(dev):
+        check(_lib.load().bgs_render_forward_noalloc(
+            N, _ptr(means2D), _ptr(conic_opacity), _ptr(colors), _ptr(depths), _ptr(point_list), int(num_entries),
+            _ptr(ranges), W, H, tile[0], tile[1], bgv, _ptr(out["color"]), _ptr(out["depth"]), _ptr(out["alpha"]),
+            _ptr(out["final_T"]), _ptr(out["n_contrib"]), _ptr(out.get("n_eval")), _stream(dev)),
+            "bgs_render_forward_noalloc")
     return out
 
 
