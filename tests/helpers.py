@@ -1,7 +1,7 @@
 """Shared helpers of the parity tests: build oracle-side inputs from a seeded scene,
 move them to the GPU, and compare images / gradients with the stated tolerances.
 
-Tolerances (spec parity bar, derived in the design doc):
+Tolerances of the parity bar:
   * images: max |GPU - oracle| <= 2e-3 per channel over pixels the oracle does not flag
     as decision-ambiguous, and >= 99.9% of all pixels within 1e-4;
   * integer outputs (n_contrib, n_eval, binning) bit-exact outside flagged pixels;
