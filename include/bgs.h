@@ -149,9 +149,10 @@ int bgs_preprocess(bgs_plan *plan, int64_t N, const float *means3D, const float 
    depth, value = i) is emitted; entries are radix-sorted by key, stably, so ties in
    depth keep ascending i.  point_list [capacity] receives the sorted values and
    ranges [T,2] (T = tiles_x * tiles_y) the half-open span of each tile (0,0 if empty).
-   If the entry count K exceeds `capacity`, nothing is written to point_list, *needed
-   (host, nullable) receives K and BGS_ERR_CAPACITY is returned.  *num_rendered (host,
-   nullable) receives K.  This call synchronises the stream once to read K. */
+   If the entry count K exceeds `capacity`, *needed (host, nullable) receives K,
+   BGS_ERR_CAPACITY is returned and point_list / ranges are unspecified (nothing is
+   written past capacity).  *num_rendered (host, nullable) receives K.  This call
+   synchronises the stream once, at its end, to read K. */
 int bgs_bin_and_sort(bgs_plan *plan, int64_t N, const float *means2D, const int32_t *radii,
                      const float *depths, int32_t W, int32_t H, int32_t tile_w, int32_t tile_h,
                      uint32_t *point_list, int64_t capacity, uint32_t *ranges, int64_t *num_rendered,
@@ -186,6 +187,68 @@ int bgs_render_backward(bgs_plan *plan, int64_t N, const float *means2D, const f
                         const int32_t *n_contrib, const float *dL_dcolor, const float *dL_ddepth,
                         const float *dL_dalpha, float *dL_dmeans2D, float *dL_dconic, float *dL_dopacity,
                         float *dL_dcolors, float *dL_ddepths, void *stream);
+
+/* ---- a7: batched views (many cameras of one Gaussian set) and graph capture ----------
+   A batched call renders V <= 32 views of N Gaussians in one persistent launch (the task
+   pool of Sec. 4.1 spans all views).  Record v * N + g is Gaussian g seen from view v:
+   per-record arrays (means2D, conic_opacity, depths, radii and their gradients) are
+   [V * N, ...], view-major; colors [N, 3] are shared by the views.  The views' tiles form
+   one global tile space, view v owning tile ids [sum_{u<v} T_u, sum_{u<=v} T_u) with
+   T_u its tiles_x * tiles_y; ranges is [sum T_u, 2] and point_list holds record indices. */
+typedef struct bgs_view {
+    bgs_camera cam;                           /* host: camera and image size of the view     */
+    float *out_color, *out_depth, *out_alpha; /* forward outputs [3,H,W], [H,W], [H,W]        */
+    float *final_T;                           /* forward output [H,W], backward input         */
+    int32_t *n_contrib;                       /* forward output [H,W], backward input         */
+    int32_t *n_eval;                          /* forward output [H,W], nullable                */
+    const float *dL_dcolor;                   /* backward input [3,H,W]                       */
+    const float *dL_ddepth, *dL_dalpha;       /* backward inputs [H,W], nullable              */
+} bgs_view;
+
+#define BGS_BIN_NO_SYNC 1 /* bin_and_sort_batched: no host synchronisation (graph capture); an
+                             entry count past capacity raises BGS_CHECK_OVERFLOW instead */
+
+/* Projection (as bgs_preprocess) of N Gaussians into V views; views[] is a host array (only
+   cam is read).  Outputs are [V * N, ...]. */
+int bgs_preprocess_batched(bgs_plan *plan, int32_t V, const bgs_view *views, int64_t N, const float *means3D,
+                           const float *log_scales, const float *quats, const float *opacities, int32_t tile_w,
+                           int32_t tile_h, float *means2D, float *conic_opacity, float *depths, int32_t *radii,
+                           uint32_t *tiles_touched, void *stream);
+/* Binning (as bgs_bin_and_sort) of the V * N records into the global tile space: each
+   view's lists are built in its own tile range, in view order, and point_list values are
+   record indices.  Without BGS_BIN_NO_SYNC the call synchronises once at its end, returns
+   BGS_ERR_CAPACITY if the entry count K exceeds capacity (*needed = K) and sets
+   *num_rendered = K (both host, nullable).  With BGS_BIN_NO_SYNC it only enqueues work:
+   lists are written up to capacity and an overflow raises BGS_CHECK_OVERFLOW.  Each view
+   may have at most (opt-in shared memory per block / 4) tiles. */
+int bgs_bin_and_sort_batched(bgs_plan *plan, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                             const int32_t *radii, const float *depths, int32_t tile_w, int32_t tile_h,
+                             uint32_t *point_list, int64_t capacity, uint32_t *ranges, int32_t flags,
+                             int64_t *num_rendered, int64_t *needed, void *stream);
+/* Forward (as bgs_render_forward) of all views in one persistent launch; outputs go to
+   views[v].out_*.  mode: AUTO, PIXEL or GAUSSIAN. */
+int bgs_render_forward_batched(bgs_plan *plan, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                               const float *conic_opacity, const float *colors, const float *depths,
+                               const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
+                               int32_t tile_w, int32_t tile_h, const float *bg, int32_t mode, void *stream);
+/* Backward (as bgs_render_backward) of all views in one launch, reading views[v].final_T,
+   n_contrib and dL_d*.  dL_dmeans2D, dL_dconic, dL_dopacity, dL_ddepths are per record
+   ([V * N, ...]); dL_dcolors [N, 3] is summed over the views (colours are shared). */
+int bgs_render_backward_batched(bgs_plan *plan, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                                const float *conic_opacity, const float *colors, const float *depths,
+                                const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
+                                int32_t tile_w, int32_t tile_h, const float *bg, int32_t mode, float *dL_dmeans2D,
+                                float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,
+                                void *stream);
+/* Graph capture of a whole step: bgs_graph_begin starts capturing `stream` (thread-local
+   mode), the caller enqueues its bgs_* calls (and its own work), bgs_graph_end ends the
+   capture and instantiates the graph (kept by the plan, replacing an earlier one), and
+   bgs_graph_launch replays it on `stream`.  Inside a capture the plan allocates nothing:
+   run the step once before capturing (or call bgs_plan_reserve) so that its workspace is
+   large enough, use BGS_BIN_NO_SYNC, and pass num_entries = the point_list capacity. */
+int bgs_graph_begin(bgs_plan *plan, void *stream);
+int bgs_graph_end(bgs_plan *plan, void *stream);
+int bgs_graph_launch(bgs_plan *plan, void *stream);
 
 /* ---- allocation-free forward ----------------------------------------------------------
    The paper has no counterpart to this entry point; it serves callers that cannot let

@@ -32,7 +32,9 @@ EXPORTS = [
     "bgs_plan_reserve", "bgs_workspace_size", "bgs_check", "bgs_plan_stats", "bgs_plan_reset_stats",
     "bgs_plan_num_sms", "bgs_last_error", "bgs_preprocess", "bgs_bin_and_sort", "bgs_render_forward",
     "bgs_render_backward", "bgs_probe_pipe_rates", "bgs_debug_exp2", "bgs_plan_timing", "bgs_plan_kernel_ms",
-    "bgs_render_forward_noalloc",
+    "bgs_render_forward_noalloc", "bgs_preprocess_batched", "bgs_bin_and_sort_batched",
+    "bgs_render_forward_batched", "bgs_render_backward_batched", "bgs_graph_begin", "bgs_graph_end",
+    "bgs_graph_launch",
 ]
 
 
@@ -52,6 +54,16 @@ class Camera(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float),
                 ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
                 ("viewmat", ctypes.c_float * 16), ("near_plane", ctypes.c_float), ("lowpass", ctypes.c_float)]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("cam", Camera), ("out_color", ctypes.c_void_p), ("out_depth", ctypes.c_void_p),
+                ("out_alpha", ctypes.c_void_p), ("final_T", ctypes.c_void_p), ("n_contrib", ctypes.c_void_p),
+                ("n_eval", ctypes.c_void_p), ("dL_dcolor", ctypes.c_void_p), ("dL_ddepth", ctypes.c_void_p),
+                ("dL_dalpha", ctypes.c_void_p)]
+
+
+BIN_NO_SYNC = 1
 
 
 class Stats(ctypes.Structure):
@@ -104,6 +116,16 @@ def load(build_if_needed: bool = True):
                                             P, P, P, P, P, P, P, P, P, P, P]
         lib.bgs_probe_pipe_rates.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P]
         lib.bgs_debug_exp2.argtypes = [P, P, i64, P]
+        VP = ctypes.POINTER(View)
+        lib.bgs_preprocess_batched.argtypes = [P, i32, VP, i64, P, P, P, P, i32, i32, P, P, P, P, P, P]
+        lib.bgs_bin_and_sort_batched.argtypes = [P, i32, VP, i64, P, P, P, i32, i32, P, i64, P, i32,
+                                                 ctypes.POINTER(i64), ctypes.POINTER(i64), P]
+        lib.bgs_render_forward_batched.argtypes = [P, i32, VP, i64, P, P, P, P, P, i64, P, i32, i32, P, i32, P]
+        lib.bgs_render_backward_batched.argtypes = [P, i32, VP, i64, P, P, P, P, P, i64, P, i32, i32, P, i32,
+                                                    P, P, P, P, P, P]
+        lib.bgs_graph_begin.argtypes = [P, P]
+        lib.bgs_graph_end.argtypes = [P, P]
+        lib.bgs_graph_launch.argtypes = [P, P]
         lib.bgs_render_forward_noalloc.argtypes = [i64, P, P, P, P, P, i64, P, i32, i32, i32, i32, P,
                                                    P, P, P, P, P, P, P]
         _lib = lib

@@ -28,6 +28,7 @@ struct DevCtrl {
     unsigned long long items_done;
     unsigned int queue_head_g;  // Gaussian-wise queue cursor (starts at 0)
     unsigned int pad0;
+    unsigned long long bin_base;  // binning: first point_list slot of the view being binned
 };
 
 // Pixel-wise items cover 8 x (4 * kPixPerLane) pixels of a tile: lane l owns the pixels
@@ -59,17 +60,24 @@ __device__ __forceinline__ void raise_check(DevCtrl *ctrl, unsigned int bit) {
     atomicOr(&ctrl->check_bits, bit);
 }
 
-// Packs one Gaussian's render inputs into a Rec (the conic is pre-scaled by -log2(e)/2).
+// Packs record g into a Rec (the conic is pre-scaled by -log2(e)/2); its colour is
+// colour row cg (views of a batched call share the colours of their Gaussians).
 __device__ __forceinline__ Rec make_rec(const float *__restrict__ means2D, const float *__restrict__ conic_opacity,
                                         const float *__restrict__ colors, const float *__restrict__ depths,
-                                        unsigned int g) {
+                                        unsigned int g, unsigned int cg) {
     Rec r;
     const float2 m = reinterpret_cast<const float2 *>(means2D)[g];
     const float4 co = reinterpret_cast<const float4 *>(conic_opacity)[g];
     r.a = make_float4(m.x, m.y, -0.5f * kLog2e * co.x, -kLog2e * co.y);
     r.b = make_float4(-0.5f * kLog2e * co.z, co.w, depths[g], 0.f);
-    r.c = make_float4(colors[3 * g], colors[3 * g + 1], colors[3 * g + 2], 0.f);
+    r.c = make_float4(colors[3 * cg], colors[3 * cg + 1], colors[3 * cg + 2], 0.f);
     return r;
+}
+
+__device__ __forceinline__ Rec make_rec(const float *__restrict__ means2D, const float *__restrict__ conic_opacity,
+                                        const float *__restrict__ colors, const float *__restrict__ depths,
+                                        unsigned int g) {
+    return make_rec(means2D, conic_opacity, colors, depths, g, g);
 }
 
 // power2 = log2(e) * power of the pair (pixel px, py) = qa dx^2 + qb dx dy + qc dy^2,
@@ -105,18 +113,52 @@ __device__ __forceinline__ float pair_alpha(float power2, float o, float &G) {
     return fminf(kAlphaMax, __fmul_rn(o, G));
 }
 
+// ---- views ---------------------------------------------------------------------------
+// A render call covers V views (1 for the single-view entry points).  Their tiles form
+// one global tile space: view v owns tile ids [tile_base[v], tile_base[v+1]).  Record
+// (and gradient) index v * n_per_view + g belongs to Gaussian g seen from view v.
+constexpr int kMaxViews = 32;
+
+struct ViewTable {
+    int V;
+    int W[kMaxViews], H[kMaxViews], tiles_x[kMaxViews], tiles_y[kMaxViews];
+    int tile_base[kMaxViews + 1];
+};
+
+// view owning a global tile id (binary search over tile_base)
+__device__ __forceinline__ int view_of(const ViewTable &vt, int tile) {
+    int lo = 0, hi = vt.V - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (vt.tile_base[mid] <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct ViewOut {  // forward outputs, per view
+    float *out_color[kMaxViews], *out_depth[kMaxViews], *out_alpha[kMaxViews], *final_T[kMaxViews];
+    int *n_contrib[kMaxViews], *n_eval[kMaxViews];
+};
+
+struct ViewGradIn {  // backward inputs, per view
+    const float *final_T[kMaxViews];
+    const int *n_contrib[kMaxViews];
+    const float *dL_dcolor[kMaxViews], *dL_ddepth[kMaxViews], *dL_dalpha[kMaxViews];
+};
+
 // ---- launch parameter blocks -----------------------------------------------------------
 struct FwdArgs {
-    const Rec *recs;             // packed records [N]
+    const Rec *recs;             // packed records [V * n_per_view]
     const float *means2D, *conic_opacity, *colors, *depths;  // ABI arrays (static kernel)
     const uint32_t *point_list;
-    const uint2 *ranges;
-    long long N;
+    const uint2 *ranges;         // [total tiles]
+    long long N;                 // number of records (V * n_per_view)
     long long num_entries;
-    int W, H, tile_w, tile_h, tiles_x, tiles_y;
+    int tile_w, tile_h, num_tiles;
     float bg[3];
-    float *out_color, *out_depth, *out_alpha, *final_T;
-    int *n_contrib, *n_eval;
+    ViewTable vt;
+    ViewOut io;
     DevCtrl *ctrl;
     const uint2 *items;          // work list (persistent kernels)
     int gw_pixels;
@@ -130,11 +172,10 @@ struct BwdArgs {
     const uint2 *ranges;
     long long N;
     long long num_entries;
-    int W, H, tile_w, tile_h, tiles_x, tiles_y;
+    int tile_w, tile_h, num_tiles;
     float bg[3];
-    const float *final_T;
-    const int *n_contrib;
-    const float *dL_dcolor, *dL_ddepth, *dL_dalpha;
+    ViewTable vt;
+    ViewGradIn gi;
     float *grad_acc;             // [N][12] accumulators (10 used)
     DevCtrl *ctrl;
     const uint2 *items;
@@ -145,10 +186,13 @@ struct BwdArgs {
 int set_error(int code, const char *msg);
 
 // ---- launchers (each returns cudaGetLastError() of its launch) ------------------------
-cudaError_t launch_preprocess(long long N, const float *means3D, const float *log_scales, const float *quats,
-                              const float *opacities, const bgs_camera &cam, int tile_w, int tile_h,
+// N Gaussians seen from V cameras: record v * N + g (V = 1 for a single view)
+cudaError_t launch_preprocess(long long N, int V, const float *means3D, const float *log_scales, const float *quats,
+                              const float *opacities, const bgs_camera *cams, int tile_w, int tile_h,
                               float *means2D, float *conic_opacity, float *depths, int *radii,
                               uint32_t *tiles_touched, cudaStream_t s);
+cudaError_t launch_depth_keys64(long long N, int V, const float *depths, unsigned long long *keys, uint32_t *idx,
+                                cudaStream_t s);
 
 cudaError_t launch_touched(long long N, const float *means2D, const int *radii, const float *depths, int W, int H,
                            int tile_w, int tile_h, uint32_t *touched, uint32_t *dkey, uint32_t *idx, cudaStream_t s);
@@ -168,21 +212,26 @@ cudaError_t setup_bin_kernels(size_t smem);
 cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
                              int W, int H, int tw, int th, uint32_t *Hm, cudaStream_t s);
 cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, uint32_t *total, cudaStream_t s);
+// ranges of one view's tiles, offset by ctrl->bin_base (the view's first point_list slot)
 cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *total, uint2 *ranges, DevCtrl *ctrl,
                               cudaStream_t s);
 cudaError_t launch_bin_scatter(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
                                int W, int H, int tw, int th, const uint32_t *Hm, const uint32_t *start,
-                               uint32_t *point_list, long long capacity, cudaStream_t s);
+                               uint32_t *point_list, long long capacity, const DevCtrl *ctrl, cudaStream_t s);
+// bin_base += this view's entry count; num_entries = bin_base; raises BGS_CHECK_OVERFLOW past capacity
+cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *total, long long capacity, DevCtrl *ctrl,
+                               cudaStream_t s);
 
+// recs[i] from means2D[i], conic_opacity[i], depths[i] and colors[i % n_colors]
 cudaError_t launch_pack(long long N, const float *means2D, const float *conic_opacity, const float *colors,
-                        const float *depths, Rec *recs, cudaStream_t s);
+                        long long n_colors, const float *depths, Rec *recs, cudaStream_t s);
 
 // work list: per-tile keys/counts, then emission in (optionally sorted) tile order
 cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int mode, int heavy_threshold, int lpt,
                                uint32_t *tile_key, uint32_t *tile_idx, cudaStream_t s);
-cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, int W, int H,
-                                 int tile_w, int tile_h, int tiles_x, int mode, int heavy_threshold,
-                                 int gw_pixels, uint32_t *counts, cudaStream_t s);
+cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, const ViewTable &vt,
+                                 int tile_w, int tile_h, int mode, int heavy_threshold, int gw_pixels,
+                                 uint32_t *counts, cudaStream_t s);
 cudaError_t launch_emit_items(const uint32_t *order, const uint32_t *counts, const uint32_t *offsets,
                               int num_tiles, const uint2 *ranges, int mode, int heavy_threshold, uint2 *items,
                               DevCtrl *ctrl, cudaStream_t s);
@@ -198,7 +247,9 @@ cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s);
 int backward_balanced_block_threads();
 const void *backward_balanced_kernel();
-cudaError_t launch_grad_finalize(long long N, const float4 *acc, float *dL_dmeans2D, float *dL_dconic,
-                                 float *dL_dopacity, float *dL_dcolors, float *dL_ddepths, cudaStream_t s);
+// gradients of N records; colours have n_colors rows (n_colors < N: summed over views)
+cudaError_t launch_grad_finalize(long long N, long long n_colors, const float4 *acc, float *dL_dmeans2D,
+                                 float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,
+                                 cudaStream_t s);
 
 }  // namespace bgs

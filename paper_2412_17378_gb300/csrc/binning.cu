@@ -106,19 +106,33 @@ __global__ void __launch_bounds__(1024) k_bin_colscan(int B, int T, uint32_t *__
     }
 }
 
-// ranges[t] = [start[t], start[t] + n[t]); K accumulates in 64 bits (ctrl->num_entries is
-// zeroed beforehand) so that an entry count beyond 32 bits is detected by the host.
+// ranges[t] = bin_base + [start[t], start[t] + n[t]) for the tiles of one view ((0,0) for
+// an empty tile).
 __global__ void k_bin_ranges(int T, const uint32_t *__restrict__ start, const uint32_t *__restrict__ total,
-                             uint2 *__restrict__ ranges, DevCtrl *ctrl) {
+                             uint2 *__restrict__ ranges, const DevCtrl *ctrl) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const uint32_t base = (uint32_t)ctrl->bin_base;
+    const uint32_t a = base + start[t], n = total[t];
+    ranges[t] = n ? make_uint2(a, a + n) : make_uint2(0u, 0u);
+}
+
+// Adds the view's entry count (computed in 64 bits from the per-tile totals) to bin_base.
+__global__ void k_bin_advance(int T, const uint32_t *__restrict__ total, long long capacity, DevCtrl *ctrl) {
+    __shared__ unsigned long long part[32];
     unsigned long long n = 0;
-    if (t < T) {
-        const uint32_t a = start[t];
-        n = total[t];
-        ranges[t] = n ? make_uint2(a, a + (uint32_t)n) : make_uint2(0u, 0u);  // (0,0) for an empty tile
-    }
+    for (int t = threadIdx.x; t < T; t += blockDim.x) n += total[t];
     for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-    if ((threadIdx.x & 31) == 0 && n) atomicAdd(&ctrl->num_entries, n);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long k = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) k += part[w];
+        const unsigned long long next = ctrl->bin_base + k;
+        ctrl->bin_base = next;
+        ctrl->num_entries = next;
+        if ((long long)next > capacity || next >= 0xffffffffull) atomicOr(&ctrl->check_bits, (unsigned)BGS_CHECK_OVERFLOW);
+    }
 }
 
 // One warp per block of the depth order: walks its Gaussians in order and writes each
@@ -127,12 +141,13 @@ __global__ void __launch_bounds__(32) k_bin_scatter(long long N, int G, const ui
                                                     const float2 *__restrict__ means2D, const int *__restrict__ radii,
                                                     int tw, int th, int tx, int ty, const uint32_t *__restrict__ H,
                                                     const uint32_t *__restrict__ start, uint32_t *__restrict__ point_list,
-                                                    long long capacity) {
+                                                    long long capacity, const DevCtrl *ctrl) {
     extern __shared__ uint32_t pos_s[];
     const int T = tx * ty;
     const int b = blockIdx.x, lane = threadIdx.x;
     const uint32_t *row = H + (size_t)b * T;
-    for (int t = lane; t < T; t += 32) pos_s[t] = start[t] + row[t];
+    const uint32_t base = (uint32_t)ctrl->bin_base;
+    for (int t = lane; t < T; t += 32) pos_s[t] = base + start[t] + row[t];
     __syncwarp();
     const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
     for (long long base = s0; base < s1; base += 32) {
@@ -190,12 +205,19 @@ cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *tota
     return cudaGetLastError();
 }
 
+cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *total, long long capacity, DevCtrl *ctrl,
+                               cudaStream_t s) {
+    (void)start;
+    k_bin_advance<<<1, 1024, 0, s>>>(T, total, capacity, ctrl);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bin_scatter(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
                                int W, int H, int tw, int th, const uint32_t *Hm, const uint32_t *start,
-                               uint32_t *point_list, long long capacity, cudaStream_t s) {
+                               uint32_t *point_list, long long capacity, const DevCtrl *ctrl, cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
     k_bin_scatter<<<B, 32, bin_count_smem(tx * ty), s>>>(N, G, order, reinterpret_cast<const float2 *>(means2D), radii,
-                                                          tw, th, tx, ty, Hm, start, point_list, capacity);
+                                                          tw, th, tx, ty, Hm, start, point_list, capacity, ctrl);
     return cudaGetLastError();
 }
 

@@ -85,6 +85,11 @@ struct bgs_plan {
     int smem_optin = 0;
     // render
     Buf recs, tile_key, tile_key2, tile_idx, tile_idx2, counts, item_off, items, grad_acc;
+    // batched binning (64-bit depth keys)
+    Buf dkey64, dkey64_sorted;
+    // captured CUDA graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
 };
 
 namespace {
@@ -181,10 +186,10 @@ int grid_for(const bgs_plan *p, const void *kernel, int threads) {
     return p->num_sms * per_sm;
 }
 
-// Builds the work list of the persistent kernels for one image (a3).
-int build_worklist(bgs_plan *p, const uint32_t *ranges, int W, int H, int tw, int th, int mode, cudaStream_t s) {
-    const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
-    const int T = tiles_x * tiles_y;
+// Builds the work list of the persistent kernels over the global tile space of the views (a3).
+int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt, int tw, int th, int mode,
+                   cudaStream_t s) {
+    const int T = vt.tile_base[vt.V];
     const int P = p->desc.gw_pixels;
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
     const long long per_tile = std::max<long long>(((tw + bgs::kPixItemW - 1) / bgs::kPixItemW) *
@@ -217,7 +222,7 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, int W, int H, int tw, in
     }
     const uint32_t *order = (const uint32_t *)p->tile_idx2.p;
     uint32_t *counts = (uint32_t *)p->counts.p, *off = (uint32_t *)p->item_off.p;
-    BGS_CUDA(bgs::launch_gather_counts(order, T, rg, W, H, tw, th, tiles_x, mode, p->desc.heavy_threshold, P, counts, s),
+    BGS_CUDA(bgs::launch_gather_counts(order, T, rg, vt, tw, th, mode, p->desc.heavy_threshold, P, counts, s),
              "gather_counts");
     size_t tmp = 0;
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, counts, off, T, s), "scan items (size)");
@@ -286,7 +291,9 @@ int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out) {
 int bgs_plan_destroy(bgs_plan *p) {
     if (!p) return BGS_OK;
     DeviceGuard g(p->device);
-    Buf *bufs[] = {&p->bin_h, &p->bin_total, &p->bin_start, &p->touched, &p->touched_sorted, &p->dkey,
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    Buf *bufs[] = {&p->dkey64, &p->dkey64_sorted, &p->bin_h, &p->bin_total, &p->bin_start, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off, &p->items,
@@ -452,7 +459,7 @@ int bgs_preprocess(bgs_plan *p, int64_t N, const float *means3D, const float *lo
     BGS_TRY(check_tile(tw, th, false));
     if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(BGS_ERR_INVALID, "bgs_preprocess: focal lengths must be > 0");
     DeviceGuard g(p->device);
-    BGS_CUDA(bgs::launch_preprocess(N, means3D, log_scales, quats, opacities, *cam, tw, th, means2D, conic_opacity,
+    BGS_CUDA(bgs::launch_preprocess(N, 1, means3D, log_scales, quats, opacities, cam, tw, th, means2D, conic_opacity,
                                     depths, radii, tiles_touched, (cudaStream_t)stream),
              "preprocess");
     if (N > 0) p->host_launches += 1;
@@ -462,6 +469,43 @@ int bgs_preprocess(bgs_plan *p, int64_t N, const float *means3D, const float *lo
 }  // extern "C"
 
 namespace {
+
+// Counting-sort binning of one view (binning.cu): order holds the view's records in depth
+// order (global record indices); ranges points at the view's first tile.  Writes its lists
+// from point_list slot ctrl->bin_base on and advances bin_base.  No host synchronisation.
+// With flag_overflow, an entry count past capacity raises BGS_CHECK_OVERFLOW on the device
+// (graph-safe callers check it with bgs_check); otherwise the host checks the count.
+int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const float *means2D, const int32_t *radii,
+                      int W, int H, int tw, int th, uint32_t *point_list, long long capacity, uint32_t *ranges,
+                      bool flag_overflow, cudaStream_t s) {
+    const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
+    const long long T = (long long)tiles_x * tiles_y;
+    const size_t smem = bgs::bin_count_smem((int)T);
+    if (smem > (size_t)p->smem_optin) return fail(BGS_ERR_INVALID, "tile grid too large for counting-sort binning");
+    const long long G = std::max<long long>(512, (n * T + (1ll << 24) - 1) >> 24);
+    const long long B = std::max<long long>(1, (n + G - 1) / G);
+    if (B * T >= (1ll << 31)) return fail(BGS_ERR_INVALID, "tile histogram too large");
+    BGS_TRY(ensure(p, p->bin_h, sizeof(uint32_t) * B * T, s, "bin_h"));
+    BGS_TRY(ensure(p, p->bin_total, sizeof(uint32_t) * T, s, "bin_total"));
+    BGS_TRY(ensure(p, p->bin_start, sizeof(uint32_t) * T, s, "bin_start"));
+    uint32_t *Hm = (uint32_t *)p->bin_h.p, *tot = (uint32_t *)p->bin_total.p, *start = (uint32_t *)p->bin_start.p;
+    if (smem > 48 * 1024) BGS_CUDA(bgs::setup_bin_kernels(smem), "bin smem attribute");
+    BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, s), "bin_count");
+    BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, tot, s), "bin_colscan");
+    size_t tmp = 0;
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tot, start, (int)T, s), "tile scan (size)");
+    BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
+    tmp = p->cub_tmp.bytes;
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, tot, start, (int)T, s), "tile scan");
+    BGS_CUDA(bgs::launch_bin_ranges((int)T, start, tot, reinterpret_cast<uint2 *>(ranges), p->ctrl, s), "bin_ranges");
+    BGS_CUDA(bgs::launch_bin_scatter(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, start, point_list,
+                                     capacity, p->ctrl, s),
+             "bin_scatter");
+    BGS_CUDA(bgs::launch_bin_advance((int)T, start, tot, flag_overflow ? capacity : (1ll << 62), p->ctrl, s),
+             "bin_advance");
+    p->host_launches += 5;  // count, colscan, ranges, scatter, advance
+    return BGS_OK;
+}
 
 template <typename KeyT>
 int sort_and_range(bgs_plan *p, long long N, const float *means2D, const int32_t *radii, int W, int H, int tw,
@@ -533,42 +577,17 @@ int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t
     BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, dkey, dkey2, gidx, order, (int64_t)N, 0, 32, s),
              "depth sort");
     // (2) counting sort over tile rectangles when the per-tile counters fit in shared memory
-    const size_t smem = bgs::bin_count_smem((int)T);
-    if (smem <= (size_t)p->smem_optin) {
-        long long G = std::max<long long>(512, (N * T + (1ll << 24) - 1) >> 24);
-        const long long B = (N + G - 1) / G;
-        if (B * T >= (1ll << 31)) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: tile histogram too large");
-        BGS_TRY(ensure(p, p->bin_h, sizeof(uint32_t) * B * T, s, "bin_h"));
-        BGS_TRY(ensure(p, p->bin_total, sizeof(uint32_t) * T, s, "bin_total"));
-        BGS_TRY(ensure(p, p->bin_start, sizeof(uint32_t) * T, s, "bin_start"));
-        uint32_t *Hm = (uint32_t *)p->bin_h.p, *tot = (uint32_t *)p->bin_total.p, *start = (uint32_t *)p->bin_start.p;
-        if (smem > 48 * 1024) BGS_CUDA(bgs::setup_bin_kernels(smem), "bin smem attribute");
-        BGS_CUDA(bgs::launch_bin_count(N, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, s), "bin_count");
-        BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, tot, s), "bin_colscan");
-        tmp = 0;
-        BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tot, start, (int)T, s), "tile scan (size)");
-        BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
-        tmp = p->cub_tmp.bytes;
-        BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, tot, start, (int)T, s), "tile scan");
-        BGS_CUDA(cudaMemsetAsync(&p->ctrl->num_entries, 0, sizeof(unsigned long long), s), "clear K");
-        BGS_CUDA(bgs::launch_bin_ranges((int)T, start, tot, reinterpret_cast<uint2 *>(ranges), p->ctrl, s),
-                 "bin_ranges");
-        p->host_launches += 4;  // touched, count, colscan, ranges
+    if (bgs::bin_count_smem((int)T) <= (size_t)p->smem_optin) {
+        BGS_CUDA(cudaMemsetAsync(&p->ctrl->bin_base, 0, sizeof(unsigned long long), s), "clear bin base");
+        BGS_TRY(bin_view_counting(p, N, order, means2D, radii, W, H, tw, th, point_list, capacity, ranges, false, s));
         unsigned long long K = 0;
         BGS_CUDA(cudaMemcpyAsync(&K, &p->ctrl->num_entries, sizeof K, cudaMemcpyDeviceToHost, s), "read K");
         BGS_CUDA(cudaStreamSynchronize(s), "sync K");
         if (needed) *needed = (int64_t)K;
-        if ((long long)K > capacity || K >= (1ull << 32) - 1) {
-            BGS_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * T, s), "clear ranges");
+        if ((long long)K > capacity || K >= (1ull << 32) - 1)
             return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort: %llu entries exceed capacity %lld (or 2^32)", K,
                         (long long)capacity);
-        }
         if (num_rendered) *num_rendered = (int64_t)K;
-        if (K == 0) return BGS_OK;
-        BGS_CUDA(bgs::launch_bin_scatter(N, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, start, point_list,
-                                         capacity, s),
-                 "bin_scatter");
-        p->host_launches += 1;
         return BGS_OK;
     }
     // (2') otherwise: entry offsets in depth order, emit, stable radix sort on the tile id
@@ -595,15 +614,16 @@ int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t
     return sort_and_range<uint32_t>(p, N, means2D, radii, W, H, tw, th, (long long)K, T, point_list, ranges, s);
 }
 
-static int render_common_checks(bgs_plan *p, int64_t N, const float *means2D, const float *conic_opacity,
-                                const float *colors, const float *depths, const uint32_t *point_list,
-                                int64_t num_entries, const uint32_t *ranges, int W, int H, int tw, int th,
-                                const float *bg, int mode, const char *who) {
-    if (!p) return fail(BGS_ERR_INVALID, "%s: NULL plan", who);
+}  // extern "C"
+
+namespace {
+
+int check_render_arrays(int64_t N, const float *means2D, const float *conic_opacity, const float *colors,
+                        const float *depths, const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
+                        int tw, int th, const float *bg, int mode, const char *who) {
     if (N < 0 || N >= (1ll << 32)) return fail(BGS_ERR_INVALID, "%s: N out of range", who);
     if (num_entries < 0 || num_entries >= (1ll << 32)) return fail(BGS_ERR_INVALID, "%s: num_entries out of range", who);
     if (mode < BGS_MODE_AUTO || mode > BGS_MODE_STATIC) return fail(BGS_ERR_INVALID, "%s: unknown mode %d", who, mode);
-    BGS_TRY(check_image(W, H));
     BGS_TRY(check_tile(tw, th, mode != BGS_MODE_STATIC));
     if (!ranges || !bg || (num_entries > 0 && !point_list) ||
         (N > 0 && (!means2D || !conic_opacity || !colors || !depths)))
@@ -613,17 +633,31 @@ static int render_common_checks(bgs_plan *p, int64_t N, const float *means2D, co
     return BGS_OK;
 }
 
-int bgs_render_forward(bgs_plan *p, int64_t N, const float *means2D, const float *conic_opacity, const float *colors,
-                       const float *depths, const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
-                       int32_t W, int32_t H, int32_t tw, int32_t th, const float *bg, int32_t mode, float *out_color,
-                       float *out_depth, float *out_alpha, float *final_T, int32_t *n_contrib, int32_t *n_eval,
-                       void *stream) {
-    BGS_TRY(render_common_checks(p, N, means2D, conic_opacity, colors, depths, point_list, num_entries, ranges, W, H,
-                                 tw, th, bg, mode, "bgs_render_forward"));
-    if (!out_color || !out_depth || !out_alpha || !final_T || !n_contrib)
-        return fail(BGS_ERR_INVALID, "bgs_render_forward: NULL output");
-    DeviceGuard g(p->device);
-    cudaStream_t s = (cudaStream_t)stream;
+// View table of V views of the given sizes (tile grids laid out one after the other).
+int make_view_table(int V, const int *W, const int *H, int tw, int th, bgs::ViewTable &vt) {
+    if (V < 1 || V > bgs::kMaxViews) return fail(BGS_ERR_INVALID, "number of views %d outside [1, %d]", V, bgs::kMaxViews);
+    memset(&vt, 0, sizeof vt);
+    vt.V = V;
+    long long base = 0;
+    for (int v = 0; v < V; ++v) {
+        BGS_TRY(check_image(W[v], H[v]));
+        vt.W[v] = W[v];
+        vt.H[v] = H[v];
+        vt.tiles_x[v] = (W[v] + tw - 1) / tw;
+        vt.tiles_y[v] = (H[v] + th - 1) / th;
+        vt.tile_base[v] = (int)base;
+        base += (long long)vt.tiles_x[v] * vt.tiles_y[v];
+        if (base >= (1ll << 30)) return fail(BGS_ERR_INVALID, "too many tiles over the views");
+    }
+    vt.tile_base[V] = (int)base;
+    return BGS_OK;
+}
+
+// Forward over the views of vt; records are n_records = V * n_per_view, colours n_colors rows.
+int render_forward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewOut &io, int64_t n_records,
+                        int64_t n_colors, const float *means2D, const float *conic_opacity, const float *colors,
+                        const float *depths, const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
+                        int tw, int th, const float *bg, int mode, cudaStream_t s) {
     bgs::FwdArgs a;
     memset(&a, 0, sizeof a);
     a.means2D = means2D;
@@ -632,38 +666,33 @@ int bgs_render_forward(bgs_plan *p, int64_t N, const float *means2D, const float
     a.depths = depths;
     a.point_list = point_list;
     a.ranges = reinterpret_cast<const uint2 *>(ranges);
-    a.N = N;
+    a.N = n_records;
     a.num_entries = num_entries;
-    a.W = W;
-    a.H = H;
     a.tile_w = tw;
     a.tile_h = th;
-    a.tiles_x = (W + tw - 1) / tw;
-    a.tiles_y = (H + th - 1) / th;
+    a.num_tiles = vt.tile_base[vt.V];
     a.bg[0] = bg[0];
     a.bg[1] = bg[1];
     a.bg[2] = bg[2];
-    a.out_color = out_color;
-    a.out_depth = out_depth;
-    a.out_alpha = out_alpha;
-    a.final_T = final_T;
-    a.n_contrib = n_contrib;
-    a.n_eval = n_eval;
+    a.vt = vt;
+    a.io = io;
     a.ctrl = p->ctrl;
     a.gw_pixels = p->desc.gw_pixels;
     a.chunk = p->desc.queue_chunk;
     if (mode == BGS_MODE_STATIC) {
+        if (vt.V != 1) return fail(BGS_ERR_INVALID, "the static kernel renders one view");
         KernelTimer kt(p, s, &p->ev_fwd);
         BGS_CUDA(bgs::launch_forward_static(a, s), "forward_static");
         kt.stop();
         p->host_launches += 1;
         return BGS_OK;
     }
-    BGS_TRY(ensure(p, p->recs, sizeof(bgs::Rec) * std::max<int64_t>(N, 1), s, "recs"));
-    BGS_CUDA(bgs::launch_pack(N, means2D, conic_opacity, colors, depths, (bgs::Rec *)p->recs.p, s), "pack");
+    BGS_TRY(ensure(p, p->recs, sizeof(bgs::Rec) * std::max<int64_t>(n_records, 1), s, "recs"));
+    BGS_CUDA(bgs::launch_pack(n_records, means2D, conic_opacity, colors, n_colors, depths, (bgs::Rec *)p->recs.p, s),
+             "pack");
     p->host_launches += 1;
     a.recs = (const bgs::Rec *)p->recs.p;
-    BGS_TRY(build_worklist(p, ranges, W, H, tw, th, mode, s));
+    BGS_TRY(build_worklist(p, ranges, vt, tw, th, mode, s));
     a.items = (const uint2 *)p->items.p;
     const int threads = bgs::forward_balanced_block_threads();
     const int grid_g = grid_for(p, bgs::forward_gauss_kernel(a.gw_pixels), threads);
@@ -676,23 +705,14 @@ int bgs_render_forward(bgs_plan *p, int64_t N, const float *means2D, const float
     return BGS_OK;
 }
 
-int bgs_render_backward(bgs_plan *p, int64_t N, const float *means2D, const float *conic_opacity, const float *colors,
-                        const float *depths, const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
-                        int32_t W, int32_t H, int32_t tw, int32_t th, const float *bg, int32_t mode,
-                        const float *final_T, const int32_t *n_contrib, const float *dL_dcolor, const float *dL_ddepth,
-                        const float *dL_dalpha, float *dL_dmeans2D, float *dL_dconic, float *dL_dopacity,
-                        float *dL_dcolors, float *dL_ddepths, void *stream) {
-    BGS_TRY(render_common_checks(p, N, means2D, conic_opacity, colors, depths, point_list, num_entries, ranges, W, H,
-                                 tw, th, bg, mode, "bgs_render_backward"));
-    if (!final_T || !n_contrib || !dL_dcolor)
-        return fail(BGS_ERR_INVALID, "bgs_render_backward: NULL final_T / n_contrib / dL_dcolor");
-    if (N > 0 && (!dL_dmeans2D || !dL_dconic || !dL_dopacity || !dL_dcolors))
-        return fail(BGS_ERR_INVALID, "bgs_render_backward: NULL gradient output");
-    DeviceGuard g(p->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (N == 0) return BGS_OK;
-    BGS_TRY(ensure(p, p->grad_acc, sizeof(bgs::Rec) * N, s, "grad_acc"));
-    BGS_CUDA(cudaMemsetAsync(p->grad_acc.p, 0, sizeof(bgs::Rec) * N, s), "clear grad_acc");
+int render_backward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewGradIn &gi, int64_t n_records,
+                         int64_t n_colors, const float *means2D, const float *conic_opacity, const float *colors,
+                         const float *depths, const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
+                         int tw, int th, const float *bg, int mode, float *dL_dmeans2D, float *dL_dconic,
+                         float *dL_dopacity, float *dL_dcolors, float *dL_ddepths, cudaStream_t s) {
+    if (n_records == 0) return BGS_OK;
+    BGS_TRY(ensure(p, p->grad_acc, sizeof(bgs::Rec) * n_records, s, "grad_acc"));
+    BGS_CUDA(cudaMemsetAsync(p->grad_acc.p, 0, sizeof(bgs::Rec) * n_records, s), "clear grad_acc");
     bgs::BwdArgs a;
     memset(&a, 0, sizeof a);
     a.means2D = means2D;
@@ -701,35 +721,32 @@ int bgs_render_backward(bgs_plan *p, int64_t N, const float *means2D, const floa
     a.depths = depths;
     a.point_list = point_list;
     a.ranges = reinterpret_cast<const uint2 *>(ranges);
-    a.N = N;
+    a.N = n_records;
     a.num_entries = num_entries;
-    a.W = W;
-    a.H = H;
     a.tile_w = tw;
     a.tile_h = th;
-    a.tiles_x = (W + tw - 1) / tw;
-    a.tiles_y = (H + th - 1) / th;
+    a.num_tiles = vt.tile_base[vt.V];
     a.bg[0] = bg[0];
     a.bg[1] = bg[1];
     a.bg[2] = bg[2];
-    a.final_T = final_T;
-    a.n_contrib = n_contrib;
-    a.dL_dcolor = dL_dcolor;
-    a.dL_ddepth = dL_ddepth;
-    a.dL_dalpha = dL_dalpha;
+    a.vt = vt;
+    a.gi = gi;
     a.grad_acc = (float *)p->grad_acc.p;
     a.ctrl = p->ctrl;
     a.chunk = p->desc.queue_chunk;
     if (mode == BGS_MODE_STATIC) {
+        if (vt.V != 1) return fail(BGS_ERR_INVALID, "the static kernel renders one view");
         KernelTimer kt(p, s, &p->ev_bwd);
         BGS_CUDA(bgs::launch_backward_static(a, s), "backward_static");
         kt.stop();
         p->host_launches += 1;
     } else {
-        BGS_TRY(ensure(p, p->recs, sizeof(bgs::Rec) * N, s, "recs"));
-        BGS_CUDA(bgs::launch_pack(N, means2D, conic_opacity, colors, depths, (bgs::Rec *)p->recs.p, s), "pack");
+        BGS_TRY(ensure(p, p->recs, sizeof(bgs::Rec) * n_records, s, "recs"));
+        BGS_CUDA(bgs::launch_pack(n_records, means2D, conic_opacity, colors, n_colors, depths, (bgs::Rec *)p->recs.p,
+                                  s),
+                 "pack");
         a.recs = (const bgs::Rec *)p->recs.p;
-        BGS_TRY(build_worklist(p, ranges, W, H, tw, th, BGS_MODE_PIXEL, s));
+        BGS_TRY(build_worklist(p, ranges, vt, tw, th, BGS_MODE_PIXEL, s));
         a.items = (const uint2 *)p->items.p;
         const int grid = grid_for(p, bgs::backward_balanced_kernel(), bgs::backward_balanced_block_threads());
         KernelTimer kt(p, s, &p->ev_bwd);
@@ -737,10 +754,267 @@ int bgs_render_backward(bgs_plan *p, int64_t N, const float *means2D, const floa
         kt.stop();
         p->host_launches += 2;  // pack + kernel
     }
-    p->host_launches += 1;      // finalize
-    BGS_CUDA(bgs::launch_grad_finalize(N, (const float4 *)p->grad_acc.p, dL_dmeans2D, dL_dconic, dL_dopacity,
-                                       dL_dcolors, dL_ddepths, s),
+    BGS_CUDA(bgs::launch_grad_finalize(n_records, n_colors, (const float4 *)p->grad_acc.p, dL_dmeans2D, dL_dconic,
+                                       dL_dopacity, dL_dcolors, dL_ddepths, s),
              "grad_finalize");
+    p->host_launches += 1;  // finalize
+    return BGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bgs_render_forward(bgs_plan *p, int64_t N, const float *means2D, const float *conic_opacity, const float *colors,
+                       const float *depths, const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
+                       int32_t W, int32_t H, int32_t tw, int32_t th, const float *bg, int32_t mode, float *out_color,
+                       float *out_depth, float *out_alpha, float *final_T, int32_t *n_contrib, int32_t *n_eval,
+                       void *stream) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_render_forward: NULL plan");
+    BGS_TRY(check_render_arrays(N, means2D, conic_opacity, colors, depths, point_list, num_entries, ranges, tw, th, bg,
+                                mode, "bgs_render_forward"));
+    if (!out_color || !out_depth || !out_alpha || !final_T || !n_contrib)
+        return fail(BGS_ERR_INVALID, "bgs_render_forward: NULL output");
+    bgs::ViewTable vt;
+    BGS_TRY(make_view_table(1, &W, &H, tw, th, vt));
+    bgs::ViewOut io;
+    memset(&io, 0, sizeof io);
+    io.out_color[0] = out_color;
+    io.out_depth[0] = out_depth;
+    io.out_alpha[0] = out_alpha;
+    io.final_T[0] = final_T;
+    io.n_contrib[0] = n_contrib;
+    io.n_eval[0] = n_eval;
+    DeviceGuard g(p->device);
+    return render_forward_impl(p, vt, io, N, N, means2D, conic_opacity, colors, depths, point_list, num_entries, ranges,
+                               tw, th, bg, mode, (cudaStream_t)stream);
+}
+
+int bgs_render_backward(bgs_plan *p, int64_t N, const float *means2D, const float *conic_opacity, const float *colors,
+                        const float *depths, const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
+                        int32_t W, int32_t H, int32_t tw, int32_t th, const float *bg, int32_t mode,
+                        const float *final_T, const int32_t *n_contrib, const float *dL_dcolor, const float *dL_ddepth,
+                        const float *dL_dalpha, float *dL_dmeans2D, float *dL_dconic, float *dL_dopacity,
+                        float *dL_dcolors, float *dL_ddepths, void *stream) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_render_backward: NULL plan");
+    BGS_TRY(check_render_arrays(N, means2D, conic_opacity, colors, depths, point_list, num_entries, ranges, tw, th, bg,
+                                mode, "bgs_render_backward"));
+    if (!final_T || !n_contrib || !dL_dcolor)
+        return fail(BGS_ERR_INVALID, "bgs_render_backward: NULL final_T / n_contrib / dL_dcolor");
+    if (N > 0 && (!dL_dmeans2D || !dL_dconic || !dL_dopacity || !dL_dcolors))
+        return fail(BGS_ERR_INVALID, "bgs_render_backward: NULL gradient output");
+    bgs::ViewTable vt;
+    BGS_TRY(make_view_table(1, &W, &H, tw, th, vt));
+    bgs::ViewGradIn gi;
+    memset(&gi, 0, sizeof gi);
+    gi.final_T[0] = final_T;
+    gi.n_contrib[0] = n_contrib;
+    gi.dL_dcolor[0] = dL_dcolor;
+    gi.dL_ddepth[0] = dL_ddepth;
+    gi.dL_dalpha[0] = dL_dalpha;
+    DeviceGuard g(p->device);
+    return render_backward_impl(p, vt, gi, N, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
+                                ranges, tw, th, bg, mode, dL_dmeans2D, dL_dconic, dL_dopacity, dL_dcolors, dL_ddepths,
+                                (cudaStream_t)stream);
+}
+
+
+// ---- a7: batched views and graph capture ----------------------------------------------
+
+int bgs_preprocess_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means3D,
+                           const float *log_scales, const float *quats, const float *opacities, int32_t tw, int32_t th,
+                           float *means2D, float *conic_opacity, float *depths, int32_t *radii,
+                           uint32_t *tiles_touched, void *stream) {
+    if (!p || !views) return fail(BGS_ERR_INVALID, "bgs_preprocess_batched: NULL plan or views");
+    if (V < 1 || V > bgs::kMaxViews) return fail(BGS_ERR_INVALID, "bgs_preprocess_batched: V=%d", V);
+    if (N < 0 || N * V >= (1ll << 32)) return fail(BGS_ERR_INVALID, "bgs_preprocess_batched: N out of range");
+    if (N > 0 && (!means3D || !log_scales || !quats || !opacities || !means2D || !conic_opacity || !depths || !radii ||
+                  !tiles_touched))
+        return fail(BGS_ERR_INVALID, "bgs_preprocess_batched: NULL array");
+    BGS_TRY(check_tile(tw, th, false));
+    bgs_camera cams[bgs::kMaxViews];
+    for (int v = 0; v < V; ++v) {
+        BGS_TRY(check_image(views[v].cam.width, views[v].cam.height));
+        if (!(views[v].cam.fx > 0.f) || !(views[v].cam.fy > 0.f))
+            return fail(BGS_ERR_INVALID, "bgs_preprocess_batched: focal lengths must be > 0");
+        cams[v] = views[v].cam;
+    }
+    DeviceGuard g(p->device);
+    BGS_CUDA(bgs::launch_preprocess(N, V, means3D, log_scales, quats, opacities, cams, tw, th, means2D, conic_opacity,
+                                    depths, radii, tiles_touched, (cudaStream_t)stream),
+             "preprocess_batched");
+    if (N > 0) p->host_launches += 1;
+    return BGS_OK;
+}
+
+int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                             const int32_t *radii, const float *depths, int32_t tw, int32_t th, uint32_t *point_list,
+                             int64_t capacity, uint32_t *ranges, int32_t flags, int64_t *num_rendered,
+                             int64_t *needed, void *stream) {
+    if (!p || !views) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: NULL plan or views");
+    if (V < 1 || V > bgs::kMaxViews) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: V=%d", V);
+    if (N < 0 || N * V >= (1ll << 32)) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: N out of range");
+    if (capacity < 0) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: negative capacity");
+    if (!ranges || (N > 0 && (!means2D || !radii || !depths)) || (capacity > 0 && !point_list))
+        return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: NULL array");
+    BGS_TRY(check_tile(tw, th, false));
+    int Ws[bgs::kMaxViews], Hs[bgs::kMaxViews];
+    for (int v = 0; v < V; ++v) {
+        Ws[v] = views[v].cam.width;
+        Hs[v] = views[v].cam.height;
+    }
+    bgs::ViewTable vt;
+    BGS_TRY(make_view_table(V, Ws, Hs, tw, th, vt));
+    for (int v = 0; v < V; ++v)
+        if (bgs::bin_count_smem(vt.tiles_x[v] * vt.tiles_y[v]) > (size_t)p->smem_optin)
+            return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: view %d has too many tiles", v);
+    const bool sync = (flags & BGS_BIN_NO_SYNC) == 0;
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long T = vt.tile_base[V];
+    BGS_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * T, s), "clear ranges");
+    BGS_CUDA(cudaMemsetAsync(&p->ctrl->bin_base, 0, sizeof(unsigned long long), s), "clear bin base");
+    if (num_rendered) *num_rendered = 0;
+    if (needed) *needed = 0;
+    const long long R = N * V;
+    if (R > 0) {
+        // depth order of every view's records, views kept apart: sort on (view << 32 | depth bits)
+        BGS_TRY(ensure(p, p->dkey64, 8 * R, s, "dkey64"));
+        BGS_TRY(ensure(p, p->dkey64_sorted, 8 * R, s, "dkey64_sorted"));
+        BGS_TRY(ensure(p, p->gidx, 4 * R, s, "gidx"));
+        BGS_TRY(ensure(p, p->order, 4 * R, s, "order"));
+        unsigned long long *k0 = (unsigned long long *)p->dkey64.p, *k1 = (unsigned long long *)p->dkey64_sorted.p;
+        uint32_t *gidx = (uint32_t *)p->gidx.p, *order = (uint32_t *)p->order.p;
+        BGS_CUDA(bgs::launch_depth_keys64(N, V, depths, k0, gidx, s), "depth keys");
+        const int end_bit = 32 + bits_for(V - 1);
+        size_t tmp = 0;
+        BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, k0, k1, gidx, order, (int64_t)R, 0, end_bit, s),
+                 "view/depth sort (size)");
+        BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
+        tmp = p->cub_tmp.bytes;
+        BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, k0, k1, gidx, order, (int64_t)R, 0, end_bit, s),
+                 "view/depth sort");
+        p->host_launches += 1;
+        for (int v = 0; v < V; ++v)  // view v's records are positions [v N, (v+1) N) of the order
+            BGS_TRY(bin_view_counting(p, N, order + (size_t)v * N, means2D, radii, Ws[v], Hs[v], tw, th, point_list,
+                                      capacity, ranges + 2ull * vt.tile_base[v], !sync, s));
+    }
+    if (!sync) return BGS_OK;
+    unsigned long long K = 0;
+    if (R > 0) {
+        BGS_CUDA(cudaMemcpyAsync(&K, &p->ctrl->num_entries, sizeof K, cudaMemcpyDeviceToHost, s), "read K");
+        BGS_CUDA(cudaStreamSynchronize(s), "sync K");
+    }
+    if (needed) *needed = (int64_t)K;
+    if ((long long)K > capacity || K >= (1ull << 32) - 1)
+        return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort_batched: %llu entries exceed capacity %lld (or 2^32)", K,
+                    (long long)capacity);
+    if (num_rendered) *num_rendered = (int64_t)K;
+    return BGS_OK;
+}
+
+static int batched_tables(int V, const bgs_view *views, int tw, int th, bgs::ViewTable &vt) {
+    if (!views) return fail(BGS_ERR_INVALID, "NULL views");
+    if (V < 1 || V > bgs::kMaxViews) return fail(BGS_ERR_INVALID, "V=%d outside [1, %d]", V, bgs::kMaxViews);
+    int Ws[bgs::kMaxViews], Hs[bgs::kMaxViews];
+    for (int v = 0; v < V; ++v) {
+        Ws[v] = views[v].cam.width;
+        Hs[v] = views[v].cam.height;
+    }
+    return make_view_table(V, Ws, Hs, tw, th, vt);
+}
+
+int bgs_render_forward_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                               const float *conic_opacity, const float *colors, const float *depths,
+                               const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges, int32_t tw,
+                               int32_t th, const float *bg, int32_t mode, void *stream) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_render_forward_batched: NULL plan");
+    if (mode == BGS_MODE_STATIC) return fail(BGS_ERR_INVALID, "bgs_render_forward_batched: the static kernel is single-view");
+    bgs::ViewTable vt;
+    BGS_TRY(batched_tables(V, views, tw, th, vt));
+    if (N < 0 || N * V >= (1ll << 32)) return fail(BGS_ERR_INVALID, "bgs_render_forward_batched: N out of range");
+    BGS_TRY(check_render_arrays(N * V, means2D, conic_opacity, colors, depths, point_list, num_entries, ranges, tw, th,
+                                bg, mode, "bgs_render_forward_batched"));
+    bgs::ViewOut io;
+    memset(&io, 0, sizeof io);
+    for (int v = 0; v < V; ++v) {
+        const bgs_view &w = views[v];
+        if (!w.out_color || !w.out_depth || !w.out_alpha || !w.final_T || !w.n_contrib)
+            return fail(BGS_ERR_INVALID, "bgs_render_forward_batched: NULL output of view %d", v);
+        io.out_color[v] = w.out_color;
+        io.out_depth[v] = w.out_depth;
+        io.out_alpha[v] = w.out_alpha;
+        io.final_T[v] = w.final_T;
+        io.n_contrib[v] = w.n_contrib;
+        io.n_eval[v] = w.n_eval;
+    }
+    DeviceGuard g(p->device);
+    return render_forward_impl(p, vt, io, N * V, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
+                               ranges, tw, th, bg, mode, (cudaStream_t)stream);
+}
+
+int bgs_render_backward_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                                const float *conic_opacity, const float *colors, const float *depths,
+                                const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges, int32_t tw,
+                                int32_t th, const float *bg, int32_t mode, float *dL_dmeans2D, float *dL_dconic,
+                                float *dL_dopacity, float *dL_dcolors, float *dL_ddepths, void *stream) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_render_backward_batched: NULL plan");
+    if (mode == BGS_MODE_STATIC) return fail(BGS_ERR_INVALID, "bgs_render_backward_batched: the static kernel is single-view");
+    bgs::ViewTable vt;
+    BGS_TRY(batched_tables(V, views, tw, th, vt));
+    if (N < 0 || N * V >= (1ll << 32)) return fail(BGS_ERR_INVALID, "bgs_render_backward_batched: N out of range");
+    BGS_TRY(check_render_arrays(N * V, means2D, conic_opacity, colors, depths, point_list, num_entries, ranges, tw, th,
+                                bg, mode, "bgs_render_backward_batched"));
+    if (N > 0 && (!dL_dmeans2D || !dL_dconic || !dL_dopacity || !dL_dcolors))
+        return fail(BGS_ERR_INVALID, "bgs_render_backward_batched: NULL gradient output");
+    bgs::ViewGradIn gi;
+    memset(&gi, 0, sizeof gi);
+    for (int v = 0; v < V; ++v) {
+        const bgs_view &w = views[v];
+        if (!w.final_T || !w.n_contrib || !w.dL_dcolor)
+            return fail(BGS_ERR_INVALID, "bgs_render_backward_batched: NULL final_T / n_contrib / dL_dcolor of view %d", v);
+        gi.final_T[v] = w.final_T;
+        gi.n_contrib[v] = w.n_contrib;
+        gi.dL_dcolor[v] = w.dL_dcolor;
+        gi.dL_ddepth[v] = w.dL_ddepth;
+        gi.dL_dalpha[v] = w.dL_dalpha;
+    }
+    DeviceGuard g(p->device);
+    return render_backward_impl(p, vt, gi, N * V, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
+                                ranges, tw, th, bg, mode, dL_dmeans2D, dL_dconic, dL_dopacity, dL_dcolors, dL_ddepths,
+                                (cudaStream_t)stream);
+}
+
+int bgs_graph_begin(bgs_plan *p, void *stream) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_graph_begin: NULL plan");
+    DeviceGuard g(p->device);
+    BGS_CUDA(cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    return BGS_OK;
+}
+
+int bgs_graph_end(bgs_plan *p, void *stream) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_graph_end: NULL plan");
+    DeviceGuard g(p->device);
+    cudaGraph_t graph = nullptr;
+    BGS_CUDA(cudaStreamEndCapture((cudaStream_t)stream, &graph), "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->graph = graph;
+    p->graph_exec = exec;
+    return BGS_OK;
+}
+
+int bgs_graph_launch(bgs_plan *p, void *stream) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_graph_launch: NULL plan");
+    if (!p->graph_exec) return fail(BGS_ERR_INVALID, "bgs_graph_launch: no captured graph");
+    DeviceGuard g(p->device);
+    BGS_CUDA(cudaGraphLaunch(p->graph_exec, (cudaStream_t)stream), "cudaGraphLaunch");
     return BGS_OK;
 }
 

@@ -13,6 +13,11 @@ struct CamDev {
     int W, H, tile_w, tile_h, tiles_x, tiles_y;
 };
 
+struct CamTable {
+    int V;
+    CamDev cam[kMaxViews];
+};
+
 // Tile rectangle of a Gaussian: x in [floor((u-r)/tw), floor((u+(r+tw-1))/tw)), clamped.
 // Float32 with one IEEE rounding per operation (no contraction), the same operations the
 // binning kernel and the host-side checks use.
@@ -28,16 +33,20 @@ __device__ __forceinline__ void tile_rect(float u, float v, int r, int tw, int t
     y1 = min(max(y1, 0), ty);
 }
 
+// Record i = v * N + g projects Gaussian g into view v (one view for the single-view call).
 __global__ void __launch_bounds__(256) k_preprocess(long long N, const float *__restrict__ means3D,
                                                     const float *__restrict__ log_scales,
                                                     const float *__restrict__ quats,
-                                                    const float *__restrict__ opacities, CamDev cam,
+                                                    const float *__restrict__ opacities, const CamTable ct,
                                                     float2 *__restrict__ means2D, float4 *__restrict__ conic_opacity,
                                                     float *__restrict__ depths, int *__restrict__ radii,
                                                     uint32_t *__restrict__ tiles_touched) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const float px = means3D[3 * i], py = means3D[3 * i + 1], pz = means3D[3 * i + 2];
+    const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (rec >= N * ct.V) return;
+    const int view = (int)(rec / N);
+    const long long g = rec - (long long)view * N;
+    const CamDev &cam = ct.cam[view];
+    const float px = means3D[3 * g], py = means3D[3 * g + 1], pz = means3D[3 * g + 2];
     const float *V = cam.V;
     const float tx = V[0] * px + V[1] * py + V[2] * pz + V[3];
     const float ty = V[4] * px + V[5] * py + V[6] * pz + V[7];
@@ -46,16 +55,16 @@ __global__ void __launch_bounds__(256) k_preprocess(long long N, const float *__
     float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
     int radius = 0;
     uint32_t touched = 0;
-    depths[i] = tz;
+    depths[rec] = tz;
     if (tz > cam.near_plane) {
         // R from the normalised quaternion (w, x, y, z)
-        float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+        float qw = quats[4 * g], qx = quats[4 * g + 1], qy = quats[4 * g + 2], qz = quats[4 * g + 3];
         const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
         qw /= qn; qx /= qn; qy /= qn; qz /= qn;
         const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
         const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
         const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
-        const float s0 = expf(log_scales[3 * i]), s1 = expf(log_scales[3 * i + 1]), s2 = expf(log_scales[3 * i + 2]);
+        const float s0 = expf(log_scales[3 * g]), s1 = expf(log_scales[3 * g + 1]), s2 = expf(log_scales[3 * g + 2]);
         // M = R S ; Sigma = M M^T (symmetric, 6 entries)
         const float M00 = R00 * s0, M01 = R01 * s1, M02 = R02 * s2;
         const float M10 = R10 * s0, M11 = R11 * s1, M12 = R12 * s2;
@@ -93,7 +102,7 @@ __global__ void __launch_bounds__(256) k_preprocess(long long N, const float *__
             const float idet = 1.f / det;
             const float u = cam.fx * tx * iz + cam.cx, v = cam.fy * ty * iz + cam.cy;
             m2 = make_float2(u, v);
-            co = make_float4(c11 * idet, -c01 * idet, c00 * idet, opacities[i]);
+            co = make_float4(c11 * idet, -c01 * idet, c00 * idet, opacities[g]);
             int x0, x1, y0, y1;
             tile_rect(u, v, r, cam.tile_w, cam.tile_h, cam.tiles_x, cam.tiles_y, x0, x1, y0, y1);
             const long long area = (long long)(x1 - x0) * (long long)(y1 - y0);
@@ -103,16 +112,13 @@ __global__ void __launch_bounds__(256) k_preprocess(long long N, const float *__
             }
         }
     }
-    means2D[i] = m2;
-    conic_opacity[i] = co;
-    radii[i] = radius;
-    tiles_touched[i] = touched;
+    means2D[rec] = m2;
+    conic_opacity[rec] = co;
+    radii[rec] = radius;
+    tiles_touched[rec] = touched;
 }
 
-cudaError_t launch_preprocess(long long N, const float *means3D, const float *log_scales, const float *quats,
-                              const float *opacities, const bgs_camera &c, int tile_w, int tile_h,
-                              float *means2D, float *conic_opacity, float *depths, int *radii,
-                              uint32_t *tiles_touched, cudaStream_t s) {
+static CamDev cam_dev(const bgs_camera &c, int tile_w, int tile_h) {
     CamDev cam;
     for (int k = 0; k < 12; ++k) cam.V[k] = c.viewmat[k];
     cam.fx = c.fx; cam.fy = c.fy; cam.cx = c.cx; cam.cy = c.cy;
@@ -124,13 +130,41 @@ cudaError_t launch_preprocess(long long N, const float *means3D, const float *lo
     cam.tile_w = tile_w; cam.tile_h = tile_h;
     cam.tiles_x = (c.width + tile_w - 1) / tile_w;
     cam.tiles_y = (c.height + tile_h - 1) / tile_h;
+    return cam;
+}
+
+cudaError_t launch_preprocess(long long N, int V, const float *means3D, const float *log_scales, const float *quats,
+                              const float *opacities, const bgs_camera *cams, int tile_w, int tile_h,
+                              float *means2D, float *conic_opacity, float *depths, int *radii,
+                              uint32_t *tiles_touched, cudaStream_t s) {
+    if (V < 1 || V > kMaxViews) return cudaErrorInvalidValue;
+    CamTable ct;
+    ct.V = V;
+    for (int v = 0; v < V; ++v) ct.cam[v] = cam_dev(cams[v], tile_w, tile_h);
     if (N == 0) return cudaSuccess;
     const int threads = 256;
-    const long long blocks = (N + threads - 1) / threads;
-    k_preprocess<<<(unsigned)blocks, threads, 0, s>>>(N, means3D, log_scales, quats, opacities, cam,
+    const long long blocks = (N * V + threads - 1) / threads;
+    k_preprocess<<<(unsigned)blocks, threads, 0, s>>>(N, means3D, log_scales, quats, opacities, ct,
                                                        reinterpret_cast<float2 *>(means2D),
                                                        reinterpret_cast<float4 *>(conic_opacity), depths, radii,
                                                        tiles_touched);
+    return cudaGetLastError();
+}
+
+// Depth sort keys of a batched binning: (view << 32 | float bits of depth), value = record.
+__global__ void __launch_bounds__(256) k_depth_keys64(long long N, int V, const float *__restrict__ depths,
+                                                      unsigned long long *__restrict__ keys, uint32_t *__restrict__ idx) {
+    const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (rec >= N * V) return;
+    const unsigned long long view = (unsigned long long)(rec / N);
+    keys[rec] = (view << 32) | (unsigned long long)__float_as_uint(depths[rec]);
+    idx[rec] = (uint32_t)rec;
+}
+
+cudaError_t launch_depth_keys64(long long N, int V, const float *depths, unsigned long long *keys, uint32_t *idx,
+                                cudaStream_t s) {
+    if (N * V == 0) return cudaSuccess;
+    k_depth_keys64<<<(unsigned)((N * V + 255) / 256), 256, 0, s>>>(N, V, depths, keys, idx);
     return cudaGetLastError();
 }
 
@@ -297,19 +331,21 @@ template cudaError_t launch_ranges<uint16_t>(const uint16_t *, long long, uint2 
 template cudaError_t launch_ranges<uint32_t>(const uint32_t *, long long, uint2 *, cudaStream_t);
 
 // ---- render input packing ------------------------------------------------------------------
+// recs[i] packs record i; the colour comes from Gaussian i % n_colors (views share colours).
 __global__ void __launch_bounds__(256) k_pack(long long N, const float *__restrict__ means2D,
                                               const float *__restrict__ conic_opacity,
-                                              const float *__restrict__ colors, const float *__restrict__ depths,
-                                              Rec *__restrict__ recs) {
+                                              const float *__restrict__ colors, long long n_colors,
+                                              const float *__restrict__ depths, Rec *__restrict__ recs) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    recs[i] = make_rec(means2D, conic_opacity, colors, depths, (unsigned int)i);
+    const long long c = (n_colors == N) ? i : i % n_colors;
+    recs[i] = make_rec(means2D, conic_opacity, colors, depths, (unsigned int)i, (unsigned int)c);
 }
 
 cudaError_t launch_pack(long long N, const float *means2D, const float *conic_opacity, const float *colors,
-                        const float *depths, Rec *recs, cudaStream_t s) {
+                        long long n_colors, const float *depths, Rec *recs, cudaStream_t s) {
     if (N == 0) return cudaSuccess;
-    k_pack<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, means2D, conic_opacity, colors, depths, recs);
+    k_pack<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, means2D, conic_opacity, colors, n_colors, depths, recs);
     return cudaGetLastError();
 }
 

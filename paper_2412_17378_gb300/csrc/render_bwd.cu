@@ -27,18 +27,20 @@ struct PixState {
     int nc;
 };
 
-__device__ __forceinline__ PixState load_pixel(const BwdArgs &a, int px, int py, bool inside) {
+__device__ __forceinline__ PixState load_pixel(const BwdArgs &a, int v, int px, int py, bool inside) {
     PixState s;
     if (inside) {
-        const long long HW = (long long)a.W * a.H;
-        const long long pid = (long long)py * a.W + px;
-        s.T = a.final_T[pid];
-        s.nc = a.n_contrib[pid];
-        s.g0 = a.dL_dcolor[pid];
-        s.g1 = a.dL_dcolor[HW + pid];
-        s.g2 = a.dL_dcolor[2 * HW + pid];
-        s.gD = a.dL_ddepth ? a.dL_ddepth[pid] : 0.f;
-        s.gA = a.dL_dalpha ? a.dL_dalpha[pid] : 0.f;
+        const int W = a.vt.W[v];
+        const long long HW = (long long)W * a.vt.H[v];
+        const long long pid = (long long)py * W + px;
+        s.T = a.gi.final_T[v][pid];
+        s.nc = a.gi.n_contrib[v][pid];
+        const float *gc = a.gi.dL_dcolor[v];
+        s.g0 = gc[pid];
+        s.g1 = gc[HW + pid];
+        s.g2 = gc[2 * HW + pid];
+        s.gD = a.gi.dL_ddepth[v] ? a.gi.dL_ddepth[v][pid] : 0.f;
+        s.gA = a.gi.dL_dalpha[v] ? a.gi.dL_dalpha[v][pid] : 0.f;
     } else {
         s.T = 1.f;
         s.nc = 0;
@@ -152,16 +154,16 @@ __global__ void __launch_bounds__(1024) k_backward_static(BwdArgs a) {
     extern __shared__ Rec srec[];
     __shared__ int s_max;
     const int nthreads = blockDim.x, tid = threadIdx.x, lane = tid & 31;
-    const int tile = blockIdx.x;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int tile = blockIdx.x;  // single view
+    const int tx = tile % a.vt.tiles_x[0], ty = tile / a.vt.tiles_x[0];
     const int px = tx * a.tile_w + tid % a.tile_w, py = ty * a.tile_h + tid / a.tile_w;
-    const bool inside = px < a.W && py < a.H;
+    const bool inside = px < a.vt.W[0] && py < a.vt.H[0];
     uint2 rg = a.ranges[tile];
     if (rg.y < rg.x || (long long)rg.y > a.num_entries) {
         if (tid == 0) raise_check(a.ctrl, BGS_CHECK_RANGE);
         rg = make_uint2(0, 0);
     }
-    PixState s = load_pixel(a, px, py, inside);
+    PixState s = load_pixel(a, 0, px, py, inside);
     if (s.nc > (int)(rg.y - rg.x)) s.nc = (int)(rg.y - rg.x);
     if (tid == 0) s_max = 0;
     __syncthreads();
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(1024) k_backward_static(BwdArgs a) {
 
 cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s) {
     const int threads = a.tile_w * a.tile_h;
-    const int tiles = a.tiles_x * a.tiles_y;
+    const int tiles = a.vt.tiles_x[0] * a.vt.tiles_y[0];
     if (tiles == 0) return cudaSuccess;
     k_backward_static<<<tiles, threads, sizeof(Rec) * threads, s>>>(a);
     return cudaGetLastError();
@@ -216,9 +218,11 @@ cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s) {
 // warp-wide reduction, so one reduction serves 8 x 4 kPixPerLane pixels.
 __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int sub, Rec *buf, int lane) {
     constexpr int Q = kPixPerLane;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int v = view_of(a.vt, tile);
+    const int lt = tile - a.vt.tile_base[v];
+    const int tx = lt % a.vt.tiles_x[v], ty = lt / a.vt.tiles_x[v];
     const int x0 = tx * a.tile_w, y0 = ty * a.tile_h;
-    const int vw = min(a.tile_w, a.W - x0), vh = min(a.tile_h, a.H - y0);
+    const int vw = min(a.tile_w, a.vt.W[v] - x0), vh = min(a.tile_h, a.vt.H[v] - y0);
     const int cxs = (vw + kPixItemW - 1) / kPixItemW;
     const int sx = sub % cxs, sy = sub / cxs;
     const int px = x0 + sx * kPixItemW + (lane & 7);
@@ -231,7 +235,7 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int py = py0 + 4 * q;
-        s[q] = load_pixel(a, px, py, px < x0 + vw && py < y0 + vh);
+        s[q] = load_pixel(a, v, px, py, px < x0 + vw && py < y0 + vh);
         if (s[q].nc > n) s[q].nc = n;
         maxnc = max(maxnc, s[q].nc);
         pyf[q] = (float)py;
@@ -286,7 +290,10 @@ cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s)
 }
 
 // ---- accumulator -> ABI gradient arrays ----------------------------------------------
-__global__ void __launch_bounds__(256) k_grad_finalize(long long N, const float4 *__restrict__ acc,
+// Record i's accumulator row -> its gradients.  Colours are shared by the views of a
+// batched call: when n_colors < N, the colour gradient of Gaussian g sums the rows
+// g, g + n_colors, ... (one per view) in k_grad_colors instead.
+__global__ void __launch_bounds__(256) k_grad_finalize(long long N, long long n_colors, const float4 *__restrict__ acc,
                                                        float *__restrict__ dL_dmeans2D, float *__restrict__ dL_dconic,
                                                        float *__restrict__ dL_dopacity, float *__restrict__ dL_dcolors,
                                                        float *__restrict__ dL_ddepths) {
@@ -301,17 +308,38 @@ __global__ void __launch_bounds__(256) k_grad_finalize(long long N, const float4
     dL_dconic[3 * i + 1] = -a0.w;
     dL_dconic[3 * i + 2] = -0.5f * a1.x;
     dL_dopacity[i] = a1.y;
-    dL_dcolors[3 * i] = a1.z;
-    dL_dcolors[3 * i + 1] = a1.w;
-    dL_dcolors[3 * i + 2] = a2.x;
+    if (n_colors == N) {
+        dL_dcolors[3 * i] = a1.z;
+        dL_dcolors[3 * i + 1] = a1.w;
+        dL_dcolors[3 * i + 2] = a2.x;
+    }
     if (dL_ddepths) dL_ddepths[i] = a2.y;
 }
 
-cudaError_t launch_grad_finalize(long long N, const float4 *acc, float *dL_dmeans2D, float *dL_dconic,
-                                 float *dL_dopacity, float *dL_dcolors, float *dL_ddepths, cudaStream_t s) {
+__global__ void __launch_bounds__(256) k_grad_colors(long long N, long long n_colors, const float4 *__restrict__ acc,
+                                                     float *__restrict__ dL_dcolors) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_colors) return;
+    float r = 0.f, gg = 0.f, b = 0.f;
+    for (long long i = g; i < N; i += n_colors) {
+        const float4 a1 = acc[3 * i + 1], a2 = acc[3 * i + 2];
+        r += a1.z;
+        gg += a1.w;
+        b += a2.x;
+    }
+    dL_dcolors[3 * g] = r;
+    dL_dcolors[3 * g + 1] = gg;
+    dL_dcolors[3 * g + 2] = b;
+}
+
+cudaError_t launch_grad_finalize(long long N, long long n_colors, const float4 *acc, float *dL_dmeans2D,
+                                 float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,
+                                 cudaStream_t s) {
     if (N == 0) return cudaSuccess;
-    k_grad_finalize<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, acc, dL_dmeans2D, dL_dconic, dL_dopacity,
+    k_grad_finalize<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, n_colors, acc, dL_dmeans2D, dL_dconic, dL_dopacity,
                                                                  dL_dcolors, dL_ddepths);
+    if (n_colors != N && n_colors > 0)
+        k_grad_colors<<<(unsigned)((n_colors + 255) / 256), 256, 0, s>>>(N, n_colors, acc, dL_dcolors);
     return cudaGetLastError();
 }
 

@@ -29,18 +29,20 @@ namespace bgs {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ void write_pixel(const FwdArgs &a, int px, int py, float T, float c0, float c1, float c2,
-                                            float D, float A, int last, int neval) {
-    const long long HW = (long long)a.W * a.H;
-    const long long pid = (long long)py * a.W + px;
-    a.out_color[pid] = c0 + T * a.bg[0];
-    a.out_color[HW + pid] = c1 + T * a.bg[1];
-    a.out_color[2 * HW + pid] = c2 + T * a.bg[2];
-    a.out_depth[pid] = D;
-    a.out_alpha[pid] = A;
-    a.final_T[pid] = T;
-    a.n_contrib[pid] = last;
-    if (a.n_eval) a.n_eval[pid] = neval;
+__device__ __forceinline__ void write_pixel(const FwdArgs &a, int v, int px, int py, float T, float c0, float c1,
+                                            float c2, float D, float A, int last, int neval) {
+    const int W = a.vt.W[v];
+    const long long HW = (long long)W * a.vt.H[v];
+    const long long pid = (long long)py * W + px;
+    float *oc = a.io.out_color[v];
+    oc[pid] = c0 + T * a.bg[0];
+    oc[HW + pid] = c1 + T * a.bg[1];
+    oc[2 * HW + pid] = c2 + T * a.bg[2];
+    a.io.out_depth[v][pid] = D;
+    a.io.out_alpha[v][pid] = A;
+    a.io.final_T[v][pid] = T;
+    a.io.n_contrib[v][pid] = last;
+    if (a.io.n_eval[v]) a.io.n_eval[v][pid] = neval;
 }
 
 // Validated tile range: an out-of-bounds span raises BGS_CHECK_RANGE and renders empty.
@@ -74,10 +76,10 @@ __global__ void __launch_bounds__(1024) k_forward_static(FwdArgs a) {
     extern __shared__ Rec srec[];
     const int nthreads = blockDim.x;
     const int tid = threadIdx.x;
-    const int tile = blockIdx.x;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int tile = blockIdx.x;  // single view: global tile id = tile of view 0
+    const int tx = tile % a.vt.tiles_x[0], ty = tile / a.vt.tiles_x[0];
     const int px = tx * a.tile_w + tid % a.tile_w, py = ty * a.tile_h + tid / a.tile_w;
-    const bool inside = px < a.W && py < a.H;
+    const bool inside = px < a.vt.W[0] && py < a.vt.H[0];
     uint2 rg = a.ranges[tile];
     if (rg.y < rg.x || (long long)rg.y > a.num_entries) {
         if (tid == 0) raise_check(a.ctrl, BGS_CHECK_RANGE);
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(1024) k_forward_static(FwdArgs a) {
             ++nacc;
         }
     }
-    if (inside) write_pixel(a, px, py, T, c0, c1, c2, D, A, last, neval);
+    if (inside) write_pixel(a, 0, px, py, T, c0, c1, c2, D, A, last, neval);
     // evaluated / contributing pair counters
     unsigned long long e = inside ? (unsigned long long)neval : 0ull, c = inside ? (unsigned long long)nacc : 0ull;
     for (int o = 16; o > 0; o >>= 1) {
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(1024) k_forward_static(FwdArgs a) {
 
 cudaError_t launch_forward_static(const FwdArgs &a, cudaStream_t s) {
     const int threads = a.tile_w * a.tile_h;
-    const int tiles = a.tiles_x * a.tiles_y;
+    const int tiles = a.vt.tiles_x[0] * a.vt.tiles_y[0];
     if (tiles == 0) return cudaSuccess;
     const size_t smem = sizeof(Rec) * threads;
     k_forward_static<<<tiles, threads, smem, s>>>(a);
@@ -155,16 +157,19 @@ cudaError_t launch_forward_static(const FwdArgs &a, cudaStream_t s) {
 constexpr int kWarpsPerBlock = 8;
 
 struct TileGeom {
-    int x0, y0, vw, vh;  // tile origin and the part of it inside the image
+    int v;               // view
+    int x0, y0, vw, vh;  // tile origin and the part of it inside the view's image
 };
 
 __device__ __forceinline__ TileGeom tile_geom(const FwdArgs &a, int tile) {
     TileGeom t;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    t.v = view_of(a.vt, tile);
+    const int lt = tile - a.vt.tile_base[t.v];
+    const int tx = lt % a.vt.tiles_x[t.v], ty = lt / a.vt.tiles_x[t.v];
     t.x0 = tx * a.tile_w;
     t.y0 = ty * a.tile_h;
-    t.vw = min(a.tile_w, a.W - t.x0);
-    t.vh = min(a.tile_h, a.H - t.y0);
+    t.vw = min(a.tile_w, a.vt.W[t.v] - t.x0);
+    t.vh = min(a.tile_h, a.vt.H[t.v] - t.y0);
     return t;
 }
 
@@ -241,7 +246,7 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (inside[q]) {
-            write_pixel(a, px, py0 + 4 * q, T[q], c0[q], c1[q], c2[q], D[q], A[q], last[q], neval[q]);
+            write_pixel(a, tg.v, px, py0 + 4 * q, T[q], c0[q], c1[q], c2[q], D[q], A[q], last[q], neval[q]);
             st_eval += (unsigned long long)neval[q];
             st_acc += (unsigned long long)nacc[q];
         }
@@ -348,7 +353,9 @@ __device__ __forceinline__ void gauss_item(const FwdArgs &a, int tile, int sub, 
         }
         const int q = sub * P + p;
         if (q < npix) {
-            if (lane == p) write_pixel(a, (int)pxf[p], (int)pyf[p], T[p], c0[p], c1[p], c2[p], D[p], A[p], last[p], neval[p]);
+            if (lane == p)
+                write_pixel(a, tg.v, (int)pxf[p], (int)pyf[p], T[p], c0[p], c1[p], c2[p], D[p], A[p], last[p],
+                            neval[p]);
             if (lane == 0) {
                 st_eval += (unsigned long long)neval[p];
                 st_acc += (unsigned long long)nacc[p];

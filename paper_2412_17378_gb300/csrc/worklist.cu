@@ -6,7 +6,8 @@
 // tile from its list length n (the paper names "the Gaussians of a tile" as the key
 // load-balance metric, Sec. 4.4):
 //   n >  heavy_threshold -> Gaussian-wise items of P pixels (one warp each),
-//   n <= heavy_threshold -> pixel-wise items of 32 pixels (an 8x4 sub-block, one warp).
+//   n <= heavy_threshold -> pixel-wise items of 8 x 8 pixels (one warp, two pixels per lane).
+// Tiles of all views of a batched call share one global tile space.
 // Items of heavier tiles are queued first (longest-processing-time order) so the long
 // items start early and the light ones fill the tail.
 #include "bgs_internal.cuh"
@@ -17,10 +18,12 @@ __device__ __forceinline__ bool tile_is_gauss(int mode, int heavy_threshold, uin
     return mode == BGS_MODE_GAUSSIAN || (mode == BGS_MODE_AUTO && n > (uint32_t)heavy_threshold);
 }
 
-__device__ __forceinline__ uint32_t tile_item_count(int t, uint32_t n, int W, int H, int tile_w, int tile_h,
-                                                    int tiles_x, int mode, int heavy_threshold, int gw_pixels) {
-    const int tx = t % tiles_x, ty = t / tiles_x;
-    const int vw = min(tile_w, W - tx * tile_w), vh = min(tile_h, H - ty * tile_h);
+__device__ __forceinline__ uint32_t tile_item_count(int t, uint32_t n, const ViewTable &vt, int tile_w, int tile_h,
+                                                    int mode, int heavy_threshold, int gw_pixels) {
+    const int v = view_of(vt, t);
+    const int lt = t - vt.tile_base[v];
+    const int tx = lt % vt.tiles_x[v], ty = lt / vt.tiles_x[v];
+    const int vw = min(tile_w, vt.W[v] - tx * tile_w), vh = min(tile_h, vt.H[v] - ty * tile_h);
     if (tile_is_gauss(mode, heavy_threshold, n)) return (uint32_t)((vw * vh + gw_pixels - 1) / gw_pixels);
     return (uint32_t)(((vw + kPixItemW - 1) / kPixItemW) * ((vh + kPixItemH - 1) / kPixItemH));
 }
@@ -46,22 +49,22 @@ cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int mode, int
 }
 
 __global__ void k_gather_counts(const uint32_t *__restrict__ order, int num_tiles, const uint2 *__restrict__ ranges,
-                                int W, int H, int tile_w, int tile_h, int tiles_x, int mode, int heavy_threshold,
+                                const ViewTable vt, int tile_w, int tile_h, int mode, int heavy_threshold,
                                 int gw_pixels, uint32_t *__restrict__ counts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= num_tiles) return;
     const int t = (int)order[i];
     const uint2 rg = ranges[t];
     const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
-    counts[i] = tile_item_count(t, n, W, H, tile_w, tile_h, tiles_x, mode, heavy_threshold, gw_pixels);
+    counts[i] = tile_item_count(t, n, vt, tile_w, tile_h, mode, heavy_threshold, gw_pixels);
 }
 
-cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, int W, int H, int tile_w,
-                                 int tile_h, int tiles_x, int mode, int heavy_threshold, int gw_pixels,
+cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, const ViewTable &vt,
+                                 int tile_w, int tile_h, int mode, int heavy_threshold, int gw_pixels,
                                  uint32_t *counts, cudaStream_t s) {
     if (num_tiles == 0) return cudaSuccess;
-    k_gather_counts<<<(num_tiles + 255) / 256, 256, 0, s>>>(order, num_tiles, ranges, W, H, tile_w, tile_h, tiles_x,
-                                                            mode, heavy_threshold, gw_pixels, counts);
+    k_gather_counts<<<(num_tiles + 255) / 256, 256, 0, s>>>(order, num_tiles, ranges, vt, tile_w, tile_h, mode,
+                                                            heavy_threshold, gw_pixels, counts);
     return cudaGetLastError();
 }
 

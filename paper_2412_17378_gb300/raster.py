@@ -294,6 +294,155 @@ def render(plan: Plan, means2D, conic_opacity, colors, depths, binning, W, H, ti
     return color, depth, alpha
 
 
+# ---- batched views (many cameras, one Gaussian set) and graph capture --------------------
+
+def _views(cams, outs=None, grads=None, fw=None):
+    arr = (_lib.View * len(cams))()
+    for v, cam in enumerate(cams):
+        arr[v].cam = camera_struct(cam)
+        if outs is not None:
+            o = outs[v]
+            arr[v].out_color, arr[v].out_depth = o["color"].data_ptr(), o["depth"].data_ptr()
+            arr[v].out_alpha, arr[v].final_T = o["alpha"].data_ptr(), o["final_T"].data_ptr()
+            arr[v].n_contrib = o["n_contrib"].data_ptr()
+            arr[v].n_eval = o["n_eval"].data_ptr() if "n_eval" in o else None
+        if fw is not None:
+            arr[v].final_T, arr[v].n_contrib = fw[v]["final_T"].data_ptr(), fw[v]["n_contrib"].data_ptr()
+        if grads is not None:
+            gv = grads[v]
+            arr[v].dL_dcolor = gv["color"].data_ptr()
+            arr[v].dL_ddepth = gv["depth"].data_ptr() if gv.get("depth") is not None else None
+            arr[v].dL_dalpha = gv["alpha"].data_ptr() if gv.get("alpha") is not None else None
+    return arr
+
+
+def tile_counts(cams, tile=(16, 16)):
+    """Tiles per view and the total of the global tile space."""
+    per = [((c["W"] + tile[0] - 1) // tile[0]) * ((c["H"] + tile[1] - 1) // tile[1]) for c in cams]
+    return per, sum(per)
+
+
+def preprocess_batched(plan: Plan, means3D, log_scales, quats, opacities, cams, tile=(16, 16), out=None):
+    """bgs_preprocess_batched: records v * N + g; returns dict of [V*N, ...] tensors."""
+    N, V = means3D.shape[0], len(cams)
+    _req(means3D, "means3D", torch.float32, (N, 3))
+    _req(log_scales, "log_scales", torch.float32, (N, 3))
+    _req(quats, "quats", torch.float32, (N, 4))
+    _req(opacities, "opacities", torch.float32, (N,))
+    dev, R = means3D.device, N * V
+    if out is None:
+        out = dict(means2D=torch.empty((R, 2), device=dev), conic_opacity=torch.empty((R, 4), device=dev),
+                   depths=torch.empty(R, device=dev), radii=torch.empty(R, dtype=torch.int32, device=dev),
+                   tiles_touched=torch.empty(R, dtype=torch.int32, device=dev))
+    vw = _views(cams)
+    check(plan._lib.bgs_preprocess_batched(plan.handle, V, vw, N, _ptr(means3D), _ptr(log_scales), _ptr(quats),
+                                           _ptr(opacities), tile[0], tile[1], _ptr(out["means2D"]),
+                                           _ptr(out["conic_opacity"]), _ptr(out["depths"]), _ptr(out["radii"]),
+                                           _ptr(out["tiles_touched"]), _stream(dev)), "bgs_preprocess_batched")
+    return out
+
+
+def bin_and_sort_batched(plan: Plan, means2D, radii, depths, cams, tile=(16, 16), point_list=None, ranges=None,
+                         no_sync: bool = False):
+    """bgs_bin_and_sort_batched: returns (point_list, ranges [sum T_v, 2], K).  With no_sync the call
+    only enqueues work (graph capture): K is returned as -1 and an overflow raises a device check."""
+    R = means2D.shape[0]
+    V = len(cams)
+    assert R % V == 0
+    N = R // V
+    _req(means2D, "means2D", torch.float32, (R, 2))
+    _req(radii, "radii", torch.int32, (R,))
+    _req(depths, "depths", torch.float32, (R,))
+    dev = means2D.device
+    _, T = tile_counts(cams, tile)
+    if ranges is None:
+        ranges = torch.empty((T, 2), dtype=torch.int32, device=dev)
+    if point_list is None:
+        point_list = torch.empty(max(4 * R, 1024), dtype=torch.int32, device=dev)
+    vw = _views(cams)
+    K, need = ctypes.c_int64(0), ctypes.c_int64(0)
+    flags = _lib.BIN_NO_SYNC if no_sync else 0
+    for _ in range(2):
+        code = plan._lib.bgs_bin_and_sort_batched(plan.handle, V, vw, N, _ptr(means2D), _ptr(radii), _ptr(depths),
+                                                  tile[0], tile[1], _ptr(point_list), point_list.numel(),
+                                                  _ptr(ranges), flags, ctypes.byref(K), ctypes.byref(need),
+                                                  _stream(dev))
+        if code == _lib.BGS_ERR_CAPACITY and not no_sync and need.value > point_list.numel():
+            point_list = torch.empty(int(need.value * 1.1) + 1024, dtype=torch.int32, device=dev)
+            continue
+        check(code, "bgs_bin_and_sort_batched")
+        break
+    return point_list, ranges, (-1 if no_sync else int(K.value))
+
+
+def alloc_view_outputs(cams, device, n_eval=False):
+    outs = []
+    for c in cams:
+        H, W = c["H"], c["W"]
+        o = dict(color=torch.empty((3, H, W), device=device), depth=torch.empty((H, W), device=device),
+                 alpha=torch.empty((H, W), device=device), final_T=torch.empty((H, W), device=device),
+                 n_contrib=torch.empty((H, W), dtype=torch.int32, device=device))
+        if n_eval:
+            o["n_eval"] = torch.empty((H, W), dtype=torch.int32, device=device)
+        outs.append(o)
+    return outs
+
+
+def render_forward_batched(plan: Plan, means2D, conic_opacity, colors, depths, point_list, num_entries: int, ranges,
+                           cams, tile=(16, 16), bg=(0.0, 0.0, 0.0), mode="auto", outs=None, n_eval=False):
+    """bgs_render_forward_batched: returns the list of per-view output dicts."""
+    R, N, V = means2D.shape[0], colors.shape[0], len(cams)
+    assert R == N * V
+    _req(means2D, "means2D", torch.float32, (R, 2))
+    _req(conic_opacity, "conic_opacity", torch.float32, (R, 4))
+    _req(colors, "colors", torch.float32, (N, 3))
+    _req(depths, "depths", torch.float32, (R,))
+    dev = means2D.device
+    if outs is None:
+        outs = alloc_view_outputs(cams, dev, n_eval)
+    vw = _views(cams, outs=outs)
+    bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    check(plan._lib.bgs_render_forward_batched(plan.handle, V, vw, N, _ptr(means2D), _ptr(conic_opacity),
+                                               _ptr(colors), _ptr(depths), _ptr(point_list), int(num_entries),
+                                               _ptr(ranges), tile[0], tile[1], bgv, m, _stream(dev)),
+          "bgs_render_forward_batched")
+    return outs
+
+
+def render_backward_batched(plan: Plan, means2D, conic_opacity, colors, depths, point_list, num_entries: int, ranges,
+                            cams, fw_outs, grads_in, tile=(16, 16), bg=(0.0, 0.0, 0.0), mode="auto", out=None):
+    """bgs_render_backward_batched: grads_in[v] = dict(color=[3,H,W], depth=None|[H,W], alpha=None|[H,W]).
+    Returns dict(means2D [V*N,2], conic [V*N,3], opacity [V*N], colors [N,3] (summed over views), depths [V*N])."""
+    R, N, V = means2D.shape[0], colors.shape[0], len(cams)
+    dev = means2D.device
+    if out is None:
+        out = dict(means2D=torch.empty((R, 2), device=dev), conic=torch.empty((R, 3), device=dev),
+                   opacity=torch.empty(R, device=dev), colors=torch.empty((N, 3), device=dev),
+                   depths=torch.empty(R, device=dev))
+    vw = _views(cams, fw=fw_outs, grads=grads_in)
+    bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    check(plan._lib.bgs_render_backward_batched(plan.handle, V, vw, N, _ptr(means2D), _ptr(conic_opacity),
+                                                _ptr(colors), _ptr(depths), _ptr(point_list), int(num_entries),
+                                                _ptr(ranges), tile[0], tile[1], bgv, m, _ptr(out["means2D"]),
+                                                _ptr(out["conic"]), _ptr(out["opacity"]), _ptr(out["colors"]),
+                                                _ptr(out.get("depths")), _stream(dev)), "bgs_render_backward_batched")
+    return out
+
+
+def graph_begin(plan: Plan):
+    check(plan._lib.bgs_graph_begin(plan.handle, _stream(plan.device)), "bgs_graph_begin")
+
+
+def graph_end(plan: Plan):
+    check(plan._lib.bgs_graph_end(plan.handle, _stream(plan.device)), "bgs_graph_end")
+
+
+def graph_launch(plan: Plan):
+    check(plan._lib.bgs_graph_launch(plan.handle, _stream(plan.device)), "bgs_graph_launch")
+
+
 def probe_pipe_rates(plan: Plan):
     """Measured (FP32 FMA, MUFU ex2) operations per SM per clock on the plan's device."""
     a, b = ctypes.c_double(0), ctypes.c_double(0)
