@@ -223,6 +223,8 @@ def main():
     from paper_2412_17378_gb300 import raster, scenes
 
     scene = scenes.scene_config(args.config, args.scale)
+    if len(scene["cameras"]) > 1:
+        return main_batched(args, scene, rank, world, local)
     g, cam = scene["gaussians"], scene["cameras"][0]
     W, H = cam["W"], cam["H"]
     dev = torch.device("cuda", local)
@@ -421,6 +423,159 @@ def main():
     plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def roofline_obj(dom, eval_pairs, contrib_pairs, bwd_pairs, fwd_ms, bwd_ms, sms, fp32_rate, ex2_rate, clk_meas_mhz):
+    """Roofline of the dominant render kernel (see the module docstring for the op counts)."""
+    peaks, peak_src = load_peaks()
+    clk_peak = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+
+    def t_min(fp32_ops, mufu_ops, clk):
+        return max(fp32_ops / (sms * FP32_LANES_PER_SM_CLK * clk), mufu_ops / (sms * ex2_rate * clk))
+
+    fwd_ops = (FWD_EVAL_FP32 * eval_pairs + FWD_ACC_FP32 * contrib_pairs, FWD_EVAL_MUFU * eval_pairs)
+    bwd_ops = (BWD_EVAL_FP32 * bwd_pairs + BWD_ACC_FP32 * contrib_pairs,
+               BWD_EVAL_MUFU * bwd_pairs + BWD_ACC_MUFU * contrib_pairs)
+    ops, dur = (fwd_ops, fwd_ms) if dom == "forward" else (bwd_ops, bwd_ms)
+    achieved = eval_pairs / (dur / 1e3)
+    peak = eval_pairs / t_min(*ops, clk_peak)
+    clk_meas = (clk_meas_mhz or 0) * 1e6
+    return {"bound": "alu", "kernel": f"k_{dom}_balanced", "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
+            "model": "max(FP32-pipe ops / (SMs*128*clk), MUFU ops / (SMs*ex2_rate*clk)) at the max SM clock",
+            "peak_source": f"derived from unit counts; SM clock {clk_peak/1e6:.0f} MHz ({peak_src}); "
+                           f"probed ex2 {ex2_rate:.1f}/SM/clk, fp32 {fp32_rate:.1f}/SM/clk",
+            "frac_at_measured_clock": (achieved / (eval_pairs / t_min(*ops, clk_meas))) if clk_meas else None}
+
+
+def main_batched(args, scene, rank, world, local):
+    """Batched views (one Gaussian set, many cameras): the whole step -- projection of all
+    views, binning without host synchronisation, one persistent forward launch, the L2 loss
+    gradients and one persistent backward launch -- captured once as a CUDA graph and
+    replayed.  pairs = evaluated pairs summed over the views."""
+    import torch
+    from paper_2412_17378_gb300 import raster, scenes
+    g, cams = scene["gaussians"], scene["cameras"]
+    V = len(cams)
+    dev = torch.device("cuda", local)
+    host = {k: torch.from_numpy(v).pin_memory() for k, v in g.items()}
+    d = {k: v.to(dev) for k, v in host.items()}
+    targets_h = [torch.from_numpy(scenes.target_image(4 + v, c["W"], c["H"])).pin_memory() for v, c in enumerate(cams)]
+    targets = [t.to(dev) for t in targets_h]
+    N = d["means3D"].shape[0]
+    plan = raster.Plan(device=local)
+    side = torch.cuda.Stream(device=dev)
+    state = {}
+
+    def step(no_sync=True, mode="auto"):
+        pre = raster.preprocess_batched(plan, d["means3D"], d["log_scales"], d["quats"], d["opacities"], cams,
+                                        out=state.get("pre"))
+        state["pre"] = pre
+        pl, rg, K = raster.bin_and_sort_batched(plan, pre["means2D"], pre["radii"], pre["depths"], cams,
+                                                point_list=state.get("pl"), ranges=state.get("rg"), no_sync=no_sync)
+        state["pl"], state["rg"] = pl, rg
+        ne = pl.numel() if no_sync else K
+        outs = raster.render_forward_batched(plan, pre["means2D"], pre["conic_opacity"], d["colors"], pre["depths"],
+                                             pl, ne, rg, cams, mode=mode, outs=state.get("outs"))
+        state["outs"] = outs
+        if "gin" not in state:
+            state["gin"] = [dict(color=torch.empty_like(o["color"])) for o in outs]
+        for o, gi, t in zip(outs, state["gin"], targets):
+            torch.sub(o["color"], t, out=gi["color"])
+        gr = raster.render_backward_batched(plan, pre["means2D"], pre["conic_opacity"], d["colors"], pre["depths"],
+                                            pl, ne, rg, cams, outs, state["gin"], mode=mode, out=state.get("gr"))
+        state["gr"] = gr
+        return K
+
+    with torch.cuda.stream(side):
+        K = step(no_sync=False)  # sizes the point_list and every workspace
+        state["pl"] = torch.empty(int(K * 1.15) + 1024, dtype=torch.int32, device=dev)
+        plan.reset_stats()
+        l0 = plan.stats()["host_launches"]
+        step(no_sync=False)
+        st = plan.stats()
+        eval_pairs, contrib_pairs = st["eval_pairs"], st["contrib_pairs"]
+        launches_per_step = st["host_launches"] - l0
+        bwd_pairs = int(sum(o["n_contrib"].sum().item() for o in state["outs"]))
+        # eager timing of the render kernels
+        plan.timing(True)
+        for _ in range(3):
+            step()
+        side.synchronize()
+        plan.kernel_ms()
+        for _ in range(3):
+            step()
+        f_ms, nf, b_ms, nb = plan.kernel_ms()
+        plan.timing(False)
+        fwd_ms, bwd_ms = f_ms / max(nf, 1), b_ms / max(nb, 1)
+        # capture the step
+        raster.graph_begin(plan)
+        step()
+        raster.graph_end(plan)
+        for _ in range(args.warmup):
+            raster.graph_launch(plan)
+        side.synchronize()
+        plan.check()
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        for _ in range(args.steps):
+            raster.graph_launch(plan)
+        e1.record(side)
+        side.synchronize()
+        ms_total = e0.elapsed_time(e1)
+        clk = clocks.stop()
+        plan.check()
+        # end to end: inputs from pinned host memory, graph replay, loss read back
+        loss_h = torch.empty(1, pin_memory=True)
+        h2d = sum(v.numel() * v.element_size() for v in host.values()) + sum(
+            t.numel() * t.element_size() for t in targets_h)
+
+        def e2e_step():
+            for k in host:
+                d[k].copy_(host[k], non_blocking=True)
+            for t, th in zip(targets, targets_h):
+                t.copy_(th, non_blocking=True)
+            raster.graph_launch(plan)
+            loss = sum((gi["color"] * gi["color"]).sum() for gi in state["gin"]) * 0.5
+            loss_h.copy_(loss.reshape(1), non_blocking=True)
+            side.synchronize()
+
+        for _ in range(3):
+            e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+    ms_step = ms_total / args.steps
+    fp32_rate, ex2_rate = raster.probe_pipe_rates(plan)
+    dom = "forward" if fwd_ms >= bwd_ms else "backward"
+    roof = roofline_obj(dom, eval_pairs, contrib_pairs, bwd_pairs, fwd_ms, bwd_ms, plan.num_sms, fp32_rate, ex2_rate,
+                        clk.get("sm_mhz"))
+    sizes = sorted(set(f"{c['W']}x{c['H']}" for c in cams))
+    line = {
+        "metric": METRIC, "value": eval_pairs * world / (ms_step / 1e3), "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; stands in for the paper's internal dataset)",
+        "config": {"workload": f"{V} views ({', '.join(sizes)}) of {N} Gaussians, fwd+bwd, one persistent launch "
+                               f"per pass, captured CUDA graph", "gaussians": N, "views": V, "tile": "16x16",
+                   "l2": "working set per step > L2, no flush", "parallelism": "single GPU"},
+        "ms_per_frame": ms_step / V,
+        "render_ms_per_step": {"forward": fwd_ms, "backward": bwd_ms, "total": fwd_ms + bwd_ms},
+        "frame": {"eval_pairs": eval_pairs, "contrib_pairs": contrib_pairs, "bwd_pairs": bwd_pairs, "entries": K},
+        "roofline": roof, "cpu_baseline": None,
+        "e2e": {"value": eval_pairs * world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches_per_step * args.steps), "gpu_launches_per_step": int(launches_per_step),
+        "gpu_launches_note": "libbgs kernels per graph replay, not counting CUB sort/scan kernels",
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
 
 
 if __name__ == "__main__":
