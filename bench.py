@@ -30,7 +30,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd render ms/frame & Gaussian-pixel pairs/s vs pixel-wise kernel, 1 GB300"
-WORKLOAD = "imbalanced single view 1920x1080, 1M Gaussians (80% clustered), fwd+bwd"
+WORKLOADS = {
+    "cfg1": "single view 256x256, 10k Gaussians uniform in a box, fwd+bwd",
+    "cfg2": "imbalanced single view 1920x1080, 1M Gaussians (80% clustered), fwd+bwd",
+    "cfg3early": "training-stage sweep, early: 1280x720, 100k large low-opacity Gaussians, fwd+bwd",
+    "cfg3late": "training-stage sweep, late: 1280x720, 3M small opaque Gaussians, fwd+bwd",
+    "cfg4": "16 uneven views (4x640x360, 8x1280x720, 4x1920x1080) of 2M clustered Gaussians, fwd+bwd",
+    "cfg5": "3840x2160 + 8x1920x1080 views of 4M Gaussians in 3 clusters, fwd+bwd",
+}
+WORKLOAD = WORKLOADS["cfg2"]
 
 # Algorithmic per-pair operation counts of the sequential rule (Algorithm 5 and its
 # derivative), counted at source level as the minimum a kernel must issue:
@@ -202,7 +210,7 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded; stands in for the paper's internal dataset)",
-            "config": {"workload": WORKLOAD, "sample": desc},
+            "config": {"workload": WORKLOADS.get(args.config, args.config), "sample": desc},
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -259,31 +267,16 @@ def main():
     rgh = binning[1].cpu().numpy()
     lens = rgh[:, 1] - rgh[:, 0]
 
-    # ---- autotune: heavy-tile threshold and pixels per Gaussian-wise item ----
+    # ---- autotune (bgs_autotune_render): sub-tile, heavy-tile threshold, Gaussian-wise pixels, chunk ----
     tuned = {}
     if args.quick:
         args.no_tune = args.no_cpu_baseline = True
     if not args.no_tune:
-        best = None
-        for thr in (256, 1024, 4096, 1 << 30):
-            for P in (2, 4):
-                if thr == (1 << 30) and P != 4:
-                    continue
-                plan.set(heavy_threshold=thr, gw_pixels=P)
-                plan.timing(True)
-                for _ in range(2):
-                    step("auto")
-                torch.cuda.synchronize()
-                plan.kernel_ms()
-                for _ in range(2):
-                    step("auto")
-                f_ms, nf, b_ms, nb = plan.kernel_ms()
-                plan.timing(False)
-                t = f_ms / max(nf, 1) + b_ms / max(nb, 1)
-                if best is None or t < best[0]:
-                    best = (t, thr, P)
-        plan.set(heavy_threshold=best[1], gw_pixels=best[2])
-        tuned = {"heavy_threshold": best[1], "gw_pixels": best[2], "render_ms": round(best[0], 4)}
+        pl, rg, K = binning
+        best_ms, knobs = raster.autotune_render(plan, pre["means2D"], pre["conic_opacity"], d["colors"],
+                                                pre["depths"], pl, K, rg, [cam])
+        tuned = {k: knobs[k] for k in ("pixel_rows", "heavy_threshold", "gw_pixels", "queue_chunk")}
+        tuned["render_ms"] = round(best_ms, 4)
 
     # ---- warmup + timed region ----
     for _ in range(args.warmup):
@@ -398,7 +391,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; stands in for the paper's internal dataset)",
-        "config": {"workload": WORKLOAD, "gaussians": N, "width": W, "height": H, "tile": "16x16",
+        "config": {"workload": WORKLOADS.get(args.config, args.config), "gaussians": N, "width": W, "height": H,
+                   "tile": "16x16",
                    "l2": "working set per step > L2 (sort buffers of K entries), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU", "tuned": tuned},
         "ms_per_frame": ms_step,
@@ -490,6 +484,13 @@ def main_batched(args, scene, rank, world, local):
     with torch.cuda.stream(side):
         K = step(no_sync=False)  # sizes the point_list and every workspace
         state["pl"] = torch.empty(int(K * 1.15) + 1024, dtype=torch.int32, device=dev)
+        step(no_sync=False)
+        pre = state["pre"]
+        best_ms, knobs = raster.autotune_render(plan, pre["means2D"], pre["conic_opacity"], d["colors"],
+                                                pre["depths"], state["pl"], K, state["rg"], cams, outs=state["outs"],
+                                                grads_in=state["gin"], out=state["gr"])
+        tuned = {k: knobs[k] for k in ("pixel_rows", "heavy_threshold", "gw_pixels", "queue_chunk")}
+        tuned["render_ms"] = round(best_ms, 4)
         plan.reset_stats()
         l0 = plan.stats()["host_launches"]
         step(no_sync=False)
@@ -560,9 +561,10 @@ def main_batched(args, scene, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; stands in for the paper's internal dataset)",
-        "config": {"workload": f"{V} views ({', '.join(sizes)}) of {N} Gaussians, fwd+bwd, one persistent launch "
-                               f"per pass, captured CUDA graph", "gaussians": N, "views": V, "tile": "16x16",
-                   "l2": "working set per step > L2, no flush", "parallelism": "single GPU"},
+        "config": {"workload": WORKLOADS.get(args.config, f"{V} views ({', '.join(sizes)}) of {N} Gaussians") +
+                               ", one persistent launch per pass, captured CUDA graph", "gaussians": N, "views": V,
+                   "tile": "16x16",
+                   "l2": "working set per step > L2, no flush", "parallelism": "single GPU", "tuned": tuned},
         "ms_per_frame": ms_step / V,
         "render_ms_per_step": {"forward": fwd_ms, "backward": bwd_ms, "total": fwd_ms + bwd_ms},
         "frame": {"eval_pairs": eval_pairs, "contrib_pairs": contrib_pairs, "bwd_pairs": bwd_pairs, "entries": K},

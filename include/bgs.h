@@ -78,6 +78,8 @@ typedef struct bgs_plan_desc {
     int32_t blocks_per_sm;   /* persistent grid = SMs x blocks_per_sm; 0 = max resident     */
     int32_t lpt_order;       /* 1: work items ordered heaviest tile first; 0: tile order    */
     int32_t device;          /* CUDA device ordinal; -1 = the current device at creation    */
+    int32_t pixel_rows;      /* sub-tile of a pixel-wise item: 8 x (4 pixel_rows) pixels, one
+                                warp, pixel_rows pixels per lane (1, 2 or 4)                 */
 } bgs_plan_desc;
 
 typedef struct bgs_plan bgs_plan;
@@ -94,7 +96,7 @@ typedef struct bgs_stats {
 } bgs_stats;
 
 /* Fills *desc with defaults (threshold 512, 4 px per Gaussian-wise item, chunk 1,
-   max resident blocks, LPT order on, current device). */
+   max resident blocks, LPT order on, current device, 2 pixel rows per lane). */
 void bgs_plan_desc_default(bgs_plan_desc *desc);
 /* Creates a plan bound to desc->device.  Allocates a small device control block. */
 int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out);
@@ -240,6 +242,19 @@ int bgs_render_backward_batched(bgs_plan *plan, int32_t V, const bgs_view *views
                                 int32_t tile_w, int32_t tile_h, const float *bg, int32_t mode, float *dL_dmeans2D,
                                 float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,
                                 void *stream);
+/* Autotuner: times forward (+ backward when `backward` is 1) passes of this frame under
+   candidate plan knobs -- pixel_rows (sub-tile of pixel-wise items), heavy_threshold (the
+   per-tile selector between pixel-wise and Gaussian-wise items), gw_pixels and
+   queue_chunk -- and keeps the fastest in the plan (*best_ms, host, nullable, gets its
+   time).  Arguments as bgs_render_forward_batched / bgs_render_backward_batched (the
+   views' outputs and dL_dcolor buffers are used as scratch; dL_ddepths is not written).
+   Synchronises the stream after every candidate; not for use inside a graph capture. */
+int bgs_autotune_render(bgs_plan *plan, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                        const float *conic_opacity, const float *colors, const float *depths,
+                        const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges, int32_t tile_w,
+                        int32_t tile_h, const float *bg, int32_t backward, float *dL_dmeans2D, float *dL_dconic,
+                        float *dL_dopacity, float *dL_dcolors, double *best_ms, void *stream);
+
 /* Graph capture of a whole step: bgs_graph_begin starts capturing `stream` (thread-local
    mode), the caller enqueues its bgs_* calls (and its own work), bgs_graph_end ends the
    capture and instantiates the graph (kept by the plan, replacing an earlier one), and

@@ -34,7 +34,7 @@ EXPORTS = [
     "bgs_render_backward", "bgs_probe_pipe_rates", "bgs_debug_exp2", "bgs_plan_timing", "bgs_plan_kernel_ms",
     "bgs_render_forward_noalloc", "bgs_preprocess_batched", "bgs_bin_and_sort_batched",
     "bgs_render_forward_batched", "bgs_render_backward_batched", "bgs_graph_begin", "bgs_graph_end",
-    "bgs_graph_launch",
+    "bgs_graph_launch", "bgs_autotune_render",
 ]
 
 
@@ -47,7 +47,7 @@ class BgsError(RuntimeError):
 class PlanDesc(ctypes.Structure):
     _fields_ = [("heavy_threshold", ctypes.c_int32), ("gw_pixels", ctypes.c_int32),
                 ("queue_chunk", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("lpt_order", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("lpt_order", ctypes.c_int32), ("device", ctypes.c_int32), ("pixel_rows", ctypes.c_int32)]
 
 
 class Camera(ctypes.Structure):
@@ -123,6 +123,8 @@ def load(build_if_needed: bool = True):
         lib.bgs_render_forward_batched.argtypes = [P, i32, VP, i64, P, P, P, P, P, i64, P, i32, i32, P, i32, P]
         lib.bgs_render_backward_batched.argtypes = [P, i32, VP, i64, P, P, P, P, P, i64, P, i32, i32, P, i32,
                                                     P, P, P, P, P, P]
+        lib.bgs_autotune_render.argtypes = [P, i32, VP, i64, P, P, P, P, P, i64, P, i32, i32, P, i32,
+                                            P, P, P, P, ctypes.POINTER(ctypes.c_double), P]
         lib.bgs_graph_begin.argtypes = [P, P]
         lib.bgs_graph_end.argtypes = [P, P]
         lib.bgs_graph_launch.argtypes = [P, P]

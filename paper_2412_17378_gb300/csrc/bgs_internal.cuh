@@ -31,11 +31,9 @@ struct DevCtrl {
     unsigned long long bin_base;  // binning: first point_list slot of the view being binned
 };
 
-// Pixel-wise items cover 8 x (4 * kPixPerLane) pixels of a tile: lane l owns the pixels
-// (l % 8, l / 8 + 4 q), q < kPixPerLane.
-constexpr int kPixPerLane = 2;
+// Pixel-wise items cover 8 x (4 Q) pixels of a tile, Q = pixel rows per lane (1, 2 or 4,
+// the plan's sub-tile knob): lane l owns the pixels (l % 8, l / 8 + 4 q), q < Q.
 constexpr int kPixItemW = 8;
-constexpr int kPixItemH = 4 * kPixPerLane;
 
 // ---- packed per-Gaussian record used by the render kernels (48 bytes) ---------------
 //   a = (mx, my, qa, qb), b = (qc, o, depth, 0), c = (r, g, b, 0)
@@ -162,6 +160,7 @@ struct FwdArgs {
     DevCtrl *ctrl;
     const uint2 *items;          // work list (persistent kernels)
     int gw_pixels;
+    int pixel_rows;              // Q of the pixel-wise items
     int chunk;
 };
 
@@ -179,6 +178,7 @@ struct BwdArgs {
     float *grad_acc;             // [N][12] accumulators (10 used)
     DevCtrl *ctrl;
     const uint2 *items;
+    int pixel_rows;
     int chunk;
 };
 
@@ -231,7 +231,7 @@ cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int mode, int
                                uint32_t *tile_key, uint32_t *tile_idx, cudaStream_t s);
 cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, const ViewTable &vt,
                                  int tile_w, int tile_h, int mode, int heavy_threshold, int gw_pixels,
-                                 uint32_t *counts, cudaStream_t s);
+                                 int pixel_rows, uint32_t *counts, cudaStream_t s);
 cudaError_t launch_emit_items(const uint32_t *order, const uint32_t *counts, const uint32_t *offsets,
                               int num_tiles, const uint2 *ranges, int mode, int heavy_threshold, uint2 *items,
                               DevCtrl *ctrl, cudaStream_t s);
@@ -241,12 +241,12 @@ cudaError_t launch_forward_gauss(const FwdArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_forward_pixel(const FwdArgs &a, int grid, cudaStream_t s);
 int forward_balanced_block_threads();
 const void *forward_gauss_kernel(int gw_pixels);
-const void *forward_pixel_kernel();
+const void *forward_pixel_kernel(int pixel_rows);
 
 cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s);
 int backward_balanced_block_threads();
-const void *backward_balanced_kernel();
+const void *backward_balanced_kernel(int pixel_rows);
 // gradients of N records; colours have n_colors rows (n_colors < N: summed over views)
 cudaError_t launch_grad_finalize(long long N, long long n_colors, const float4 *acc, float *dL_dmeans2D,
                                  float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,

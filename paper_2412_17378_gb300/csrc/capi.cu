@@ -192,8 +192,9 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
     const int T = vt.tile_base[vt.V];
     const int P = p->desc.gw_pixels;
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+    const int item_h = 4 * p->desc.pixel_rows;
     const long long per_tile = std::max<long long>(((tw + bgs::kPixItemW - 1) / bgs::kPixItemW) *
-                                                       ((th + bgs::kPixItemH - 1) / bgs::kPixItemH),
+                                                       ((th + item_h - 1) / item_h),
                                                    (tw * th + P - 1) / P);
     const long long max_items = (long long)T * per_tile;
     if (max_items >= (1ll << 31)) return fail(BGS_ERR_INVALID, "too many work items (%lld)", max_items);
@@ -222,7 +223,8 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
     }
     const uint32_t *order = (const uint32_t *)p->tile_idx2.p;
     uint32_t *counts = (uint32_t *)p->counts.p, *off = (uint32_t *)p->item_off.p;
-    BGS_CUDA(bgs::launch_gather_counts(order, T, rg, vt, tw, th, mode, p->desc.heavy_threshold, P, counts, s),
+    BGS_CUDA(bgs::launch_gather_counts(order, T, rg, vt, tw, th, mode, p->desc.heavy_threshold, P,
+                                       p->desc.pixel_rows, counts, s),
              "gather_counts");
     size_t tmp = 0;
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, counts, off, T, s), "scan items (size)");
@@ -239,7 +241,8 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
 bool valid_desc(const bgs_plan_desc *d) {
     return d->heavy_threshold >= 0 && (d->gw_pixels == 1 || d->gw_pixels == 2 || d->gw_pixels == 4 ||
                                        d->gw_pixels == 8) &&
-           d->queue_chunk >= 1 && d->queue_chunk <= 1024 && d->blocks_per_sm >= 0 && d->blocks_per_sm <= 64;
+           d->queue_chunk >= 1 && d->queue_chunk <= 1024 && d->blocks_per_sm >= 0 && d->blocks_per_sm <= 64 &&
+           (d->pixel_rows == 1 || d->pixel_rows == 2 || d->pixel_rows == 4);
 }
 
 }  // namespace
@@ -256,6 +259,7 @@ void bgs_plan_desc_default(bgs_plan_desc *d) {
     d->blocks_per_sm = 0;
     d->lpt_order = 1;
     d->device = -1;
+    d->pixel_rows = 2;
 }
 
 int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out) {
@@ -678,6 +682,7 @@ int render_forward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewOu
     a.io = io;
     a.ctrl = p->ctrl;
     a.gw_pixels = p->desc.gw_pixels;
+    a.pixel_rows = p->desc.pixel_rows;
     a.chunk = p->desc.queue_chunk;
     if (mode == BGS_MODE_STATIC) {
         if (vt.V != 1) return fail(BGS_ERR_INVALID, "the static kernel renders one view");
@@ -696,7 +701,7 @@ int render_forward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewOu
     a.items = (const uint2 *)p->items.p;
     const int threads = bgs::forward_balanced_block_threads();
     const int grid_g = grid_for(p, bgs::forward_gauss_kernel(a.gw_pixels), threads);
-    const int grid_p = grid_for(p, bgs::forward_pixel_kernel(), threads);
+    const int grid_p = grid_for(p, bgs::forward_pixel_kernel(a.pixel_rows), threads);
     KernelTimer kt(p, s, &p->ev_fwd);
     if (mode != BGS_MODE_PIXEL) BGS_CUDA(bgs::launch_forward_gauss(a, grid_g, s), "forward_gauss");
     if (mode != BGS_MODE_GAUSSIAN) BGS_CUDA(bgs::launch_forward_pixel(a, grid_p, s), "forward_pixel");
@@ -733,6 +738,7 @@ int render_backward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewG
     a.gi = gi;
     a.grad_acc = (float *)p->grad_acc.p;
     a.ctrl = p->ctrl;
+    a.pixel_rows = p->desc.pixel_rows;
     a.chunk = p->desc.queue_chunk;
     if (mode == BGS_MODE_STATIC) {
         if (vt.V != 1) return fail(BGS_ERR_INVALID, "the static kernel renders one view");
@@ -748,7 +754,8 @@ int render_backward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewG
         a.recs = (const bgs::Rec *)p->recs.p;
         BGS_TRY(build_worklist(p, ranges, vt, tw, th, BGS_MODE_PIXEL, s));
         a.items = (const uint2 *)p->items.p;
-        const int grid = grid_for(p, bgs::backward_balanced_kernel(), bgs::backward_balanced_block_threads());
+        const int grid = grid_for(p, bgs::backward_balanced_kernel(a.pixel_rows),
+                                  bgs::backward_balanced_block_threads());
         KernelTimer kt(p, s, &p->ev_bwd);
         BGS_CUDA(bgs::launch_backward_balanced(a, grid, s), "backward_balanced");
         kt.stop();
@@ -1016,6 +1023,83 @@ int bgs_graph_launch(bgs_plan *p, void *stream) {
     DeviceGuard g(p->device);
     BGS_CUDA(cudaGraphLaunch(p->graph_exec, (cudaStream_t)stream), "cudaGraphLaunch");
     return BGS_OK;
+}
+
+
+int bgs_autotune_render(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                        const float *conic_opacity, const float *colors, const float *depths,
+                        const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges, int32_t tw, int32_t th,
+                        const float *bg, int32_t backward, float *dL_dmeans2D, float *dL_dconic, float *dL_dopacity,
+                        float *dL_dcolors, double *best_ms, void *stream) {
+    if (!p || !views) return fail(BGS_ERR_INVALID, "bgs_autotune_render: NULL plan or views");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BGS_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate");
+    }
+    const bgs_plan_desc start = p->desc;
+    const bool was_timing = p->timing;
+    p->timing = false;
+    // one candidate: 1 untimed + 2 timed passes of forward (+ backward); best of the two
+    auto run = [&](const bgs_plan_desc &d, double &ms) -> int {
+        p->desc = d;
+        ms = 1e30;
+        for (int rep = 0; rep < 3; ++rep) {
+            BGS_CUDA(cudaEventRecord(e0, s), "event");
+            BGS_TRY(bgs_render_forward_batched(p, V, views, N, means2D, conic_opacity, colors, depths, point_list,
+                                               num_entries, ranges, tw, th, bg, BGS_MODE_AUTO, stream));
+            if (backward)
+                BGS_TRY(bgs_render_backward_batched(p, V, views, N, means2D, conic_opacity, colors, depths,
+                                                    point_list, num_entries, ranges, tw, th, bg, BGS_MODE_AUTO,
+                                                    dL_dmeans2D, dL_dconic, dL_dopacity, dL_dcolors, nullptr, stream));
+            BGS_CUDA(cudaEventRecord(e1, s), "event");
+            BGS_CUDA(cudaEventSynchronize(e1), "event sync");
+            float t = 0.f;
+            BGS_CUDA(cudaEventElapsedTime(&t, e0, e1), "elapsed");
+            if (rep > 0) ms = std::min(ms, (double)t);
+        }
+        return BGS_OK;
+    };
+    bgs_plan_desc best = start, d = start;
+    double best_t = 1e30, t = 0.0;
+    int rc = BGS_OK;
+    // stage 1: sub-tile (pixel rows per lane) with pixel-wise items only
+    d.heavy_threshold = 0x7fffffff;
+    d.queue_chunk = 1;
+    for (int q : {1, 2, 4}) {
+        d.pixel_rows = q;
+        if ((rc = run(d, t)) != BGS_OK) break;
+        if (t < best_t) best_t = t, best = d;
+    }
+    // stage 2: heavy-tile threshold and pixels per Gaussian-wise item
+    for (int thr : {256, 1024, 4096, 16384}) {
+        if (rc != BGS_OK) break;
+        for (int P : {2, 4}) {
+            d = best;
+            d.heavy_threshold = thr;
+            d.gw_pixels = P;
+            if ((rc = run(d, t)) != BGS_OK) break;
+            if (t < best_t) best_t = t, best = d;
+        }
+    }
+    // stage 3: queue granularity
+    for (int c : {2, 4}) {
+        if (rc != BGS_OK) break;
+        d = best;
+        d.queue_chunk = c;
+        if ((rc = run(d, t)) != BGS_OK) break;
+        if (t < best_t) best_t = t, best = d;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->timing = was_timing;
+    p->desc = (rc == BGS_OK) ? best : start;
+    if (best_ms) *best_ms = best_t;
+    return rc;
 }
 
 }  // extern "C"

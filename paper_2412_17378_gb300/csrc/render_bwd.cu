@@ -213,11 +213,12 @@ cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s) {
 // =====================================================================================
 // balanced persistent backward: warps pull pixel-wise items (8x4 sub-blocks)
 // =====================================================================================
-// Pixel-wise item: the 8 x (4 kPixPerLane) sub-block of the forward's items; lane l owns
-// the pixels (l % 8, l / 8 + 4 q).  The lane adds its pixels' contributions before the
-// warp-wide reduction, so one reduction serves 8 x 4 kPixPerLane pixels.
+// Pixel-wise item: an 8 x 4Q sub-block; lane l owns the pixels (l % 8, l / 8 + 4 q).  The
+// lane adds its pixels' contributions before the warp-wide reduction, so one reduction
+// serves 32 Q pixels.
+template <int Q>
 __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int sub, Rec *buf, int lane) {
-    constexpr int Q = kPixPerLane;
+    constexpr int kItemH = 4 * Q;
     const int v = view_of(a.vt, tile);
     const int lt = tile - a.vt.tile_base[v];
     const int tx = lt % a.vt.tiles_x[v], ty = lt / a.vt.tiles_x[v];
@@ -226,7 +227,7 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
     const int cxs = (vw + kPixItemW - 1) / kPixItemW;
     const int sx = sub % cxs, sy = sub / cxs;
     const int px = x0 + sx * kPixItemW + (lane & 7);
-    const int py0 = y0 + sy * kPixItemH + (lane >> 3);
+    const int py0 = y0 + sy * kItemH + (lane >> 3);
     const uint2 rg = load_range_bwd(a, tile);
     const int n = (int)(rg.y - rg.x);
     PixState s[Q];
@@ -262,6 +263,7 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
     }
 }
 
+template <int Q>
 __global__ void __launch_bounds__(kBwdWarps * 32) k_backward_balanced(BwdArgs a) {
     __shared__ Rec sbuf[kBwdWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -276,16 +278,28 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_backward_balanced(BwdArgs a)
         const unsigned end = min(first + chunk, num_items);
         for (unsigned it = first; it < end; ++it) {
             const uint2 item = a.items[it];
-            bwd_pixel_item(a, (int)item.x, (int)(item.y & ~kKindGauss), buf, lane);
+            bwd_pixel_item<Q>(a, (int)item.x, (int)(item.y & ~kKindGauss), buf, lane);
         }
     }
 }
 
 int backward_balanced_block_threads() { return kBwdWarps * 32; }
-const void *backward_balanced_kernel() { return (const void *)k_backward_balanced; }
+const void *backward_balanced_kernel(int pixel_rows) {
+    switch (pixel_rows) {
+        case 1: return (const void *)k_backward_balanced<1>;
+        case 2: return (const void *)k_backward_balanced<2>;
+        case 4: return (const void *)k_backward_balanced<4>;
+        default: return nullptr;
+    }
+}
 
 cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s) {
-    k_backward_balanced<<<grid, kBwdWarps * 32, 0, s>>>(a);
+    switch (a.pixel_rows) {
+        case 1: k_backward_balanced<1><<<grid, kBwdWarps * 32, 0, s>>>(a); break;
+        case 2: k_backward_balanced<2><<<grid, kBwdWarps * 32, 0, s>>>(a); break;
+        case 4: k_backward_balanced<4><<<grid, kBwdWarps * 32, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

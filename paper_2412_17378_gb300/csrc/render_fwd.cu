@@ -173,18 +173,19 @@ __device__ __forceinline__ TileGeom tile_geom(const FwdArgs &a, int tile) {
     return t;
 }
 
-// Pixel-wise item: an 8 x (4 kPixPerLane) sub-block of a tile; lane l owns the pixels
-// (l % 8, l / 8 + 4 q).  The warp walks the tile's list through a warp-private window of
-// 32 records in shared memory; each record is read once per lane (broadcast) and applied
-// to the lane's kPixPerLane pixels, which share dx.
+// Pixel-wise item: an 8 x 4Q sub-block of a tile; lane l owns the pixels (l % 8, l / 8 + 4 q).
+// The warp walks the tile's list through a warp-private window of 32 records in shared
+// memory; each record is read once per lane (broadcast) and applied to the lane's Q
+// pixels, which share dx.
+template <int Q>
 __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, Rec *buf, int lane,
                                            unsigned long long &st_eval, unsigned long long &st_acc) {
-    constexpr int Q = kPixPerLane;
+    constexpr int kItemH = 4 * Q;
     const TileGeom tg = tile_geom(a, tile);
     const int cxs = (tg.vw + kPixItemW - 1) / kPixItemW;
     const int sx = sub % cxs, sy = sub / cxs;
     const int px = tg.x0 + sx * kPixItemW + (lane & 7);
-    const int py0 = tg.y0 + sy * kPixItemH + (lane >> 3);
+    const int py0 = tg.y0 + sy * kItemH + (lane >> 3);
     const uint2 rg = load_range(a, tile);
     const float pxf = (float)px;
     float pyf[Q], T[Q], c0[Q], c1[Q], c2[Q], D[Q], A[Q];
@@ -404,6 +405,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_gauss(FwdArgs a
 }
 
 // Pixel-wise items [num_gauss, num_items) of the work list.
+template <int Q>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_pixel(FwdArgs a) {
     __shared__ Rec sbuf[kWarpsPerBlock][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -419,7 +421,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_pixel(FwdArgs a
         const unsigned end = min(first + chunk, num_items);
         for (unsigned it = first; it < end; ++it) {
             const uint2 item = a.items[it];
-            pixel_item(a, (int)item.x, (int)(item.y & ~kKindGauss), buf, lane, st_eval, st_acc);
+            pixel_item<Q>(a, (int)item.x, (int)(item.y & ~kKindGauss), buf, lane, st_eval, st_acc);
             ++st_items;
         }
     }
@@ -438,7 +440,14 @@ const void *forward_gauss_kernel(int gw_pixels) {
     }
 }
 
-const void *forward_pixel_kernel() { return (const void *)k_forward_pixel; }
+const void *forward_pixel_kernel(int pixel_rows) {
+    switch (pixel_rows) {
+        case 1: return (const void *)k_forward_pixel<1>;
+        case 2: return (const void *)k_forward_pixel<2>;
+        case 4: return (const void *)k_forward_pixel<4>;
+        default: return nullptr;
+    }
+}
 
 cudaError_t launch_forward_gauss(const FwdArgs &a, int grid, cudaStream_t s) {
     const int threads = kWarpsPerBlock * 32;
@@ -465,7 +474,12 @@ cudaError_t launch_forward_pixel(const FwdArgs &a, int grid, cudaStream_t s) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_forward_pixel, a);
+    switch (a.pixel_rows) {
+        case 1: return cudaLaunchKernelEx(&cfg, k_forward_pixel<1>, a);
+        case 2: return cudaLaunchKernelEx(&cfg, k_forward_pixel<2>, a);
+        case 4: return cudaLaunchKernelEx(&cfg, k_forward_pixel<4>, a);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace bgs

@@ -6,7 +6,7 @@
 // tile from its list length n (the paper names "the Gaussians of a tile" as the key
 // load-balance metric, Sec. 4.4):
 //   n >  heavy_threshold -> Gaussian-wise items of P pixels (one warp each),
-//   n <= heavy_threshold -> pixel-wise items of 8 x 8 pixels (one warp, two pixels per lane).
+//   n <= heavy_threshold -> pixel-wise items of 8 x 4Q pixels (one warp, Q pixels per lane).
 // Tiles of all views of a batched call share one global tile space.
 // Items of heavier tiles are queued first (longest-processing-time order) so the long
 // items start early and the light ones fill the tail.
@@ -19,13 +19,14 @@ __device__ __forceinline__ bool tile_is_gauss(int mode, int heavy_threshold, uin
 }
 
 __device__ __forceinline__ uint32_t tile_item_count(int t, uint32_t n, const ViewTable &vt, int tile_w, int tile_h,
-                                                    int mode, int heavy_threshold, int gw_pixels) {
+                                                    int mode, int heavy_threshold, int gw_pixels, int pixel_rows) {
     const int v = view_of(vt, t);
     const int lt = t - vt.tile_base[v];
     const int tx = lt % vt.tiles_x[v], ty = lt / vt.tiles_x[v];
     const int vw = min(tile_w, vt.W[v] - tx * tile_w), vh = min(tile_h, vt.H[v] - ty * tile_h);
     if (tile_is_gauss(mode, heavy_threshold, n)) return (uint32_t)((vw * vh + gw_pixels - 1) / gw_pixels);
-    return (uint32_t)(((vw + kPixItemW - 1) / kPixItemW) * ((vh + kPixItemH - 1) / kPixItemH));
+    const int item_h = 4 * pixel_rows;
+    return (uint32_t)(((vw + kPixItemW - 1) / kPixItemW) * ((vh + item_h - 1) / item_h));
 }
 
 // Sort key of each tile: its list length (heaviest first) when lpt is on, else only its
@@ -50,21 +51,21 @@ cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int mode, int
 
 __global__ void k_gather_counts(const uint32_t *__restrict__ order, int num_tiles, const uint2 *__restrict__ ranges,
                                 const ViewTable vt, int tile_w, int tile_h, int mode, int heavy_threshold,
-                                int gw_pixels, uint32_t *__restrict__ counts) {
+                                int gw_pixels, int pixel_rows, uint32_t *__restrict__ counts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= num_tiles) return;
     const int t = (int)order[i];
     const uint2 rg = ranges[t];
     const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
-    counts[i] = tile_item_count(t, n, vt, tile_w, tile_h, mode, heavy_threshold, gw_pixels);
+    counts[i] = tile_item_count(t, n, vt, tile_w, tile_h, mode, heavy_threshold, gw_pixels, pixel_rows);
 }
 
 cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, const ViewTable &vt,
                                  int tile_w, int tile_h, int mode, int heavy_threshold, int gw_pixels,
-                                 uint32_t *counts, cudaStream_t s) {
+                                 int pixel_rows, uint32_t *counts, cudaStream_t s) {
     if (num_tiles == 0) return cudaSuccess;
     k_gather_counts<<<(num_tiles + 255) / 256, 256, 0, s>>>(order, num_tiles, ranges, vt, tile_w, tile_h, mode,
-                                                            heavy_threshold, gw_pixels, counts);
+                                                            heavy_threshold, gw_pixels, pixel_rows, counts);
     return cudaGetLastError();
 }
 

@@ -48,7 +48,7 @@ class Plan:
     """Owns a bgs_plan: tuning knobs and the library-managed workspace."""
 
     def __init__(self, heavy_threshold: int = 512, gw_pixels: int = 4, queue_chunk: int = 1,
-                 blocks_per_sm: int = 0, lpt_order: bool = True, device=None):
+                 blocks_per_sm: int = 0, lpt_order: bool = True, device=None, pixel_rows: int = 2):
         self._lib = _lib.load()
         if device is None:
             device = torch.cuda.current_device()
@@ -57,6 +57,7 @@ class Plan:
         self._lib.bgs_plan_desc_default(ctypes.byref(d))
         d.heavy_threshold, d.gw_pixels, d.queue_chunk = heavy_threshold, gw_pixels, queue_chunk
         d.blocks_per_sm, d.lpt_order, d.device = blocks_per_sm, int(bool(lpt_order)), self.device.index
+        d.pixel_rows = pixel_rows
         h = ctypes.c_void_p()
         check(self._lib.bgs_plan_create(ctypes.byref(d), ctypes.byref(h)), "bgs_plan_create")
         self.handle = h
@@ -429,6 +430,32 @@ def render_backward_batched(plan: Plan, means2D, conic_opacity, colors, depths, 
                                                 _ptr(out["conic"]), _ptr(out["opacity"]), _ptr(out["colors"]),
                                                 _ptr(out.get("depths")), _stream(dev)), "bgs_render_backward_batched")
     return out
+
+
+def autotune_render(plan: Plan, means2D, conic_opacity, colors, depths, point_list, num_entries: int, ranges, cams,
+                    tile=(16, 16), bg=(0.0, 0.0, 0.0), backward: bool = True, outs=None, grads_in=None, out=None):
+    """bgs_autotune_render: times candidate plan knobs (pixel rows per lane, heavy-tile threshold,
+    pixels per Gaussian-wise item, queue chunk) on this frame and keeps the fastest in the plan.
+    Works for one view (cams of length 1) or several.  Returns (best ms, chosen knobs)."""
+    R, N, V = means2D.shape[0], colors.shape[0], len(cams)
+    dev = means2D.device
+    if outs is None:
+        outs = alloc_view_outputs(cams, dev)
+    if backward and grads_in is None:
+        grads_in = [dict(color=torch.zeros((3, c["H"], c["W"]), device=dev)) for c in cams]
+    if backward and out is None:
+        out = dict(means2D=torch.empty((R, 2), device=dev), conic=torch.empty((R, 3), device=dev),
+                   opacity=torch.empty(R, device=dev), colors=torch.empty((N, 3), device=dev))
+    vw = _views(cams, outs=outs, grads=grads_in if backward else None)
+    bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    best = ctypes.c_double(0)
+    g = out or {}
+    check(plan._lib.bgs_autotune_render(plan.handle, V, vw, N, _ptr(means2D), _ptr(conic_opacity), _ptr(colors),
+                                        _ptr(depths), _ptr(point_list), int(num_entries), _ptr(ranges), tile[0],
+                                        tile[1], bgv, int(bool(backward)), _ptr(g.get("means2D")),
+                                        _ptr(g.get("conic")), _ptr(g.get("opacity")), _ptr(g.get("colors")),
+                                        ctypes.byref(best), _stream(dev)), "bgs_autotune_render")
+    return best.value, plan.desc()
 
 
 def graph_begin(plan: Plan):

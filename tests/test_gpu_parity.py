@@ -248,3 +248,32 @@ def test_exp2_accuracy(R):
     ref = np.exp2(x.astype(np.float64))
     rel = np.abs(y - ref) / ref
     assert rel.max() < 2.0 ** -21, rel.max()
+
+
+@pytest.mark.parametrize("rows", [1, 2, 4])
+def test_pixel_rows_sub_tiles(R, cfg1, rows):
+    """Every sub-tile size of the pixel-wise items (8 x 4, 8 x 8, 8 x 16) gives the oracle's
+    image and gradients."""
+    p = R.Plan(heavy_threshold=1 << 30, pixel_rows=rows)
+    ref = oracle.render(cfg1["means2D"], cfg1["conic_opacity"], cfg1["colors"], cfg1["depths"], cfg1["point_list"],
+                        cfg1["ranges"], cfg1["W"], cfg1["H"])
+    out, _ = _render_gpu(R, p, cfg1, "auto")
+    compare_images(out["color"], ref, what=f"rows {rows}")
+    got, gref = _backward_case(R, p, cfg1, "pixel", seed=rows)
+    for k in ("means2D", "conic", "opacity", "colors"):
+        assert rel_l2(got[k], gref[k]) <= GRAD_REL_L2, k
+    p.close()
+
+
+def test_autotuner_choice_keeps_parity(R, cfg1):
+    p = R.Plan()
+    g = to_gpu(cfg1)
+    cam = dict(W=cfg1["W"], H=cfg1["H"], fx=256.0, fy=256.0, cx=127.5, cy=127.5, viewmat=np.eye(4))
+    best_ms, knobs = R.autotune_render(p, g["means2D"], g["conic_opacity"], g["colors"], g["depths"],
+                                       g["point_list"], g["K"], g["ranges"], [cam])
+    assert best_ms > 0 and knobs["pixel_rows"] in (1, 2, 4) and knobs["queue_chunk"] in (1, 2, 4)
+    ref = oracle.render(cfg1["means2D"], cfg1["conic_opacity"], cfg1["colors"], cfg1["depths"], cfg1["point_list"],
+                        cfg1["ranges"], cfg1["W"], cfg1["H"])
+    out, _ = _render_gpu(R, p, cfg1, "auto")
+    compare_images(out["color"], ref, what="tuned")
+    p.close()
