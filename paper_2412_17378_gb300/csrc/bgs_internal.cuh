@@ -17,6 +17,7 @@ constexpr float kLog2e = 1.4426950408889634f;  // log2(e): exp(x) = 2^(x log2 e)
 constexpr float kLn2 = 0.6931471805599453f;    // ln(2)
 
 // ---- device control block (one per plan) --------------------------------------------
+constexpr int kMaxViewsCtrl = 32;
 struct DevCtrl {
     unsigned int queue_head;    // pixel-wise queue cursor (starts at num_gauss)
     unsigned int num_items;     // work items in the current list
@@ -29,6 +30,7 @@ struct DevCtrl {
     unsigned int queue_head_g;  // Gaussian-wise queue cursor (starts at 0)
     unsigned int pad0;
     unsigned long long bin_base;  // binning: first point_list slot of the view being binned
+    unsigned long long view_entries[kMaxViewsCtrl];  // binning: entries of each view
 };
 
 // Pixel-wise items cover 8 x (4 Q) pixels of a tile, Q = pixel rows per lane (1, 2 or 4,
@@ -191,8 +193,16 @@ cudaError_t launch_preprocess(long long N, int V, const float *means3D, const fl
                               const float *opacities, const bgs_camera *cams, int tile_w, int tile_h,
                               float *means2D, float *conic_opacity, float *depths, int *radii,
                               uint32_t *tiles_touched, cudaStream_t s);
-cudaError_t launch_depth_keys64(long long N, int V, const float *depths, unsigned long long *keys, uint32_t *idx,
-                                cudaStream_t s);
+// batched binning: per record its entry count and its (view << 32 | depth bits) sort key
+struct TileGrids {
+    int tx[kMaxViews], ty[kMaxViews];
+};
+cudaError_t launch_depth_keys64(long long N, int V, const float *means2D, const int *radii, const float *depths,
+                                int tw, int th, const TileGrids &tg, uint32_t *touched, unsigned long long *keys,
+                                uint32_t *idx, cudaStream_t s);
+// view_entries[v] = offsets[v N + N - 1] + counts[v N + N - 1]
+cudaError_t launch_view_totals(int V, long long N, const unsigned long long *offsets, const uint32_t *counts,
+                               DevCtrl *ctrl, cudaStream_t s);
 
 cudaError_t launch_touched(long long N, const float *means2D, const int *radii, const float *depths, int W, int H,
                            int tile_w, int tile_h, uint32_t *touched, uint32_t *dkey, uint32_t *idx, cudaStream_t s);
@@ -206,21 +216,29 @@ cudaError_t launch_count_total(long long N, const uint32_t *touched, const unsig
 template <typename KeyT>
 cudaError_t launch_ranges(const KeyT *keys, long long K, uint2 *ranges, cudaStream_t s);
 
-// counting-sort binning (binning.cu)
+// one-pass binning over entry chunks (binning.cu)
+constexpr int kChunk = 16384;  // entries per chunk of the binning sort
 size_t bin_count_smem(int T);
+size_t bin_sort_smem();
 cudaError_t setup_bin_kernels(size_t smem);
-cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
-                             int W, int H, int tw, int th, uint32_t *Hm, cudaStream_t s);
+cudaError_t launch_chunk_first(long long N, const unsigned long long *offsets, const uint32_t *counts, long long B,
+                               uint32_t *first, cudaStream_t s);
+cudaError_t launch_bin_count(long long N, int B, const uint32_t *order, const unsigned long long *offsets,
+                             const uint32_t *first, const unsigned long long *view_entries, const float *means2D,
+                             const int *radii, int W, int H, int tw, int th, uint32_t *Hm, cudaStream_t s);
 cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, uint32_t *total, cudaStream_t s);
 // ranges of one view's tiles, offset by ctrl->bin_base (the view's first point_list slot)
 cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *total, uint2 *ranges, DevCtrl *ctrl,
                               cudaStream_t s);
-cudaError_t launch_bin_scatter(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
-                               int W, int H, int tw, int th, const uint32_t *Hm, const uint32_t *start,
-                               uint32_t *point_list, long long capacity, const DevCtrl *ctrl, cudaStream_t s);
-// bin_base += this view's entry count; num_entries = bin_base; raises BGS_CHECK_OVERFLOW past capacity
-cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *total, long long capacity, DevCtrl *ctrl,
-                               cudaStream_t s);
+cudaError_t launch_bin_sort_scatter(long long N, int B, const uint32_t *order, const unsigned long long *offsets,
+                                    const uint32_t *first, const unsigned long long *view_entries, const DevCtrl *ctrl,
+                                    const float *means2D, const int *radii, int W, int H, int tw, int th,
+                                    const uint32_t *Hm, const uint32_t *start, uint32_t *point_list, long long capacity,
+                                    int end_bit, cudaStream_t s);
+// bin_base += this view's entry count; num_entries = bin_base; raises BGS_CHECK_OVERFLOW past
+// capacity or when the view's entries exceed its chunk capacity
+cudaError_t launch_bin_advance(int T, const uint32_t *total, long long capacity, int view, long long chunk_capacity,
+                               DevCtrl *ctrl, cudaStream_t s);
 
 // recs[i] from means2D[i], conic_opacity[i], depths[i] and colors[i % n_colors]
 cudaError_t launch_pack(long long N, const float *means2D, const float *conic_opacity, const float *colors,
