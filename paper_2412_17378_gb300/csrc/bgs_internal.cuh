@@ -17,7 +17,6 @@ constexpr float kLog2e = 1.4426950408889634f;  // log2(e): exp(x) = 2^(x log2 e)
 constexpr float kLn2 = 0.6931471805599453f;    // ln(2)
 
 // ---- device control block (one per plan) --------------------------------------------
-constexpr int kMaxViewsCtrl = 32;
 struct DevCtrl {
     unsigned int queue_head;    // pixel-wise queue cursor (starts at num_gauss)
     unsigned int num_items;     // work items in the current list
@@ -30,7 +29,6 @@ struct DevCtrl {
     unsigned int queue_head_g;  // Gaussian-wise queue cursor (starts at 0)
     unsigned int pad0;
     unsigned long long bin_base;  // binning: first point_list slot of the view being binned
-    unsigned long long view_entries[kMaxViewsCtrl];  // binning: entries of each view
 };
 
 // Pixel-wise items cover 8 x (4 Q) pixels of a tile, Q = pixel rows per lane (1, 2 or 4,
@@ -38,9 +36,12 @@ struct DevCtrl {
 constexpr int kPixItemW = 8;
 
 // ---- packed per-Gaussian record used by the render kernels (48 bytes) ---------------
-//   a = (mx, my, qa, qb), b = (qc, o, depth, 0), c = (r, g, b, 0)
+//   a = (mx, my, qa, qb), b = (qc, o, hx, hy), c = (r, g, b, depth)
 //   with (qa, qb, qc) = -log2(e) (a/2, b, c/2), so that the natural-log power of the
 //   pair is ln2 * (qa dx^2 + qb dx dy + qc dy^2) and exp(power) = 2^(qa dx^2 + ...).
+//   (hx, hy) are half-extents of a box around the mean outside which no pixel can reach
+//   alpha >= 1/255 (negative: no pixel can); kernels use it to skip whole records for a
+//   block of pixels.
 struct __align__(16) Rec {
     float4 a, b, c;
 };
@@ -60,6 +61,19 @@ __device__ __forceinline__ void raise_check(DevCtrl *ctrl, unsigned int bit) {
     atomicOr(&ctrl->check_bits, bit);
 }
 
+// Half-extents of the region where alpha = min(0.99, o G) can reach 1/255: alpha >= 1/255
+// needs o G >= 1/255, i.e. d^T Q d <= r^2 = 2 ln(255 o), whose bounding box has half-widths
+// r sqrt((Q^-1)_xx) = r sqrt(c / det) and r sqrt(a / det) for Q = (a b; b c).  Widened by
+// 0.1% and 0.01 px so that float32 evaluation of a pair never decides "valid" outside it.
+__device__ __forceinline__ float2 alpha_box(float a, float b, float c, float o) {
+    const float det = a * c - b * b;
+    const float lo = 255.f * o;
+    if (!(lo > 1.f)) return make_float2(-1.f, -1.f);  // alpha <= o < 1/255 everywhere
+    if (!(det > 0.f)) return make_float2(3.0e38f, 3.0e38f);
+    const float r2 = 2.f * logf(lo);
+    return make_float2(sqrtf(r2 * c / det) * 1.001f + 0.01f, sqrtf(r2 * a / det) * 1.001f + 0.01f);
+}
+
 // Packs record g into a Rec (the conic is pre-scaled by -log2(e)/2); its colour is
 // colour row cg (views of a batched call share the colours of their Gaussians).
 __device__ __forceinline__ Rec make_rec(const float *__restrict__ means2D, const float *__restrict__ conic_opacity,
@@ -68,10 +82,17 @@ __device__ __forceinline__ Rec make_rec(const float *__restrict__ means2D, const
     Rec r;
     const float2 m = reinterpret_cast<const float2 *>(means2D)[g];
     const float4 co = reinterpret_cast<const float4 *>(conic_opacity)[g];
+    const float2 box = alpha_box(co.x, co.y, co.z, co.w);
     r.a = make_float4(m.x, m.y, -0.5f * kLog2e * co.x, -kLog2e * co.y);
-    r.b = make_float4(-0.5f * kLog2e * co.z, co.w, depths[g], 0.f);
-    r.c = make_float4(colors[3 * cg], colors[3 * cg + 1], colors[3 * cg + 2], 0.f);
+    r.b = make_float4(-0.5f * kLog2e * co.z, co.w, box.x, box.y);
+    r.c = make_float4(colors[3 * cg], colors[3 * cg + 1], colors[3 * cg + 2], depths[g]);
     return r;
+}
+
+// true when the record cannot reach alpha >= 1/255 at any pixel whose centre lies within
+// (hw, hh) of (cx, cy)
+__device__ __forceinline__ bool box_misses(const float4 &a, const float4 &b, float cx, float cy, float hw, float hh) {
+    return fabsf(a.x - cx) > b.z + hw || fabsf(a.y - cy) > b.w + hh;
 }
 
 __device__ __forceinline__ Rec make_rec(const float *__restrict__ means2D, const float *__restrict__ conic_opacity,
@@ -193,16 +214,8 @@ cudaError_t launch_preprocess(long long N, int V, const float *means3D, const fl
                               const float *opacities, const bgs_camera *cams, int tile_w, int tile_h,
                               float *means2D, float *conic_opacity, float *depths, int *radii,
                               uint32_t *tiles_touched, cudaStream_t s);
-// batched binning: per record its entry count and its (view << 32 | depth bits) sort key
-struct TileGrids {
-    int tx[kMaxViews], ty[kMaxViews];
-};
-cudaError_t launch_depth_keys64(long long N, int V, const float *means2D, const int *radii, const float *depths,
-                                int tw, int th, const TileGrids &tg, uint32_t *touched, unsigned long long *keys,
-                                uint32_t *idx, cudaStream_t s);
-// view_entries[v] = offsets[v N + N - 1] + counts[v N + N - 1]
-cudaError_t launch_view_totals(int V, long long N, const unsigned long long *offsets, const uint32_t *counts,
-                               DevCtrl *ctrl, cudaStream_t s);
+cudaError_t launch_depth_keys64(long long N, int V, const float *depths, unsigned long long *keys, uint32_t *idx,
+                                cudaStream_t s);
 
 cudaError_t launch_touched(long long N, const float *means2D, const int *radii, const float *depths, int W, int H,
                            int tile_w, int tile_h, uint32_t *touched, uint32_t *dkey, uint32_t *idx, cudaStream_t s);
@@ -216,29 +229,21 @@ cudaError_t launch_count_total(long long N, const uint32_t *touched, const unsig
 template <typename KeyT>
 cudaError_t launch_ranges(const KeyT *keys, long long K, uint2 *ranges, cudaStream_t s);
 
-// one-pass binning over entry chunks (binning.cu)
-constexpr int kChunk = 16384;  // entries per chunk of the binning sort
+// counting-sort binning (binning.cu)
 size_t bin_count_smem(int T);
-size_t bin_sort_smem();
 cudaError_t setup_bin_kernels(size_t smem);
-cudaError_t launch_chunk_first(long long N, const unsigned long long *offsets, const uint32_t *counts, long long B,
-                               uint32_t *first, cudaStream_t s);
-cudaError_t launch_bin_count(long long N, int B, const uint32_t *order, const unsigned long long *offsets,
-                             const uint32_t *first, const unsigned long long *view_entries, const float *means2D,
-                             const int *radii, int W, int H, int tw, int th, uint32_t *Hm, cudaStream_t s);
+cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
+                             int W, int H, int tw, int th, uint32_t *Hm, cudaStream_t s);
 cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, uint32_t *total, cudaStream_t s);
 // ranges of one view's tiles, offset by ctrl->bin_base (the view's first point_list slot)
 cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *total, uint2 *ranges, DevCtrl *ctrl,
                               cudaStream_t s);
-cudaError_t launch_bin_sort_scatter(long long N, int B, const uint32_t *order, const unsigned long long *offsets,
-                                    const uint32_t *first, const unsigned long long *view_entries, const DevCtrl *ctrl,
-                                    const float *means2D, const int *radii, int W, int H, int tw, int th,
-                                    const uint32_t *Hm, const uint32_t *start, uint32_t *point_list, long long capacity,
-                                    int end_bit, cudaStream_t s);
-// bin_base += this view's entry count; num_entries = bin_base; raises BGS_CHECK_OVERFLOW past
-// capacity or when the view's entries exceed its chunk capacity
-cudaError_t launch_bin_advance(int T, const uint32_t *total, long long capacity, int view, long long chunk_capacity,
-                               DevCtrl *ctrl, cudaStream_t s);
+cudaError_t launch_bin_scatter(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
+                               int W, int H, int tw, int th, const uint32_t *Hm, const uint32_t *start,
+                               uint32_t *point_list, long long capacity, const DevCtrl *ctrl, cudaStream_t s);
+// bin_base += this view's entry count; num_entries = bin_base; raises BGS_CHECK_OVERFLOW past capacity
+cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *total, long long capacity, DevCtrl *ctrl,
+                               cudaStream_t s);
 
 // recs[i] from means2D[i], conic_opacity[i], depths[i] and colors[i % n_colors]
 cudaError_t launch_pack(long long N, const float *means2D, const float *conic_opacity, const float *colors,
@@ -264,7 +269,7 @@ const void *forward_pixel_kernel(int pixel_rows);
 cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s);
 int backward_balanced_block_threads();
-const void *backward_balanced_kernel(int pixel_rows);
+const void *backward_balanced_kernel(const BwdArgs &a);  // the instantiation a would launch
 // gradients of N records; colours have n_colors rows (n_colors < N: summed over views)
 cudaError_t launch_grad_finalize(long long N, long long n_colors, const float4 *acc, float *dL_dmeans2D,
                                  float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,

@@ -1,25 +1,19 @@
-// binning.cu -- a2: per-tile depth-ordered lists in one pass over the duplicated entries.
+// binning.cu -- a2: per-tile depth-ordered lists by a counting sort over tile rectangles.
 //
 // After the Gaussians are sorted by depth (ties by index), every per-tile list is the
-// subsequence of that order whose rectangles cover the tile.  Conceptually every Gaussian
-// emits one (tile, index) entry per covered tile in depth order (entry e of the stream
-// belongs to the Gaussian whose exclusive entry offset is the last one <= e) and the
-// entries are stably partitioned by tile.  The stream is cut into chunks of kChunk
-// consecutive entries, regenerated from the Gaussians' rectangles whenever needed:
-//   1. k_chunk_first - first Gaussian of every chunk.
-//   2. k_bin_count   - chunk b counts its entries per tile in shared memory: H[b][t].
-//   3. k_bin_colscan - exclusive scan of every column of H over b (in place) and the tile
-//                      totals n[t]; (CUB) exclusive scan of n -> tile starts; ranges.
-//   4. k_bin_sort_scatter - chunk b regenerates its entries, sorts them by tile in shared
-//                      memory with a stable block radix sort, ranks each entry inside its
-//                      tile's run and writes its Gaussian index to
-//                      start[t] + H[b][t] + rank, the runs coalesced.
-// The result is the stable (depth, index) order per tile; the K entries are written once
-// and never sorted in global memory.
-#include <cub/block/block_exchange.cuh>
-#include <cub/block/block_radix_sort.cuh>
-#include <cub/block/block_scan.cuh>
-
+// subsequence of that order whose rectangles cover the tile.  The lists are built without
+// materialising and sorting the K duplicated entries:
+//   1. k_bin_count   - the depth order is cut into B blocks of G consecutive Gaussians;
+//                      block b counts, in shared memory, how many of its Gaussians cover
+//                      each tile: H[b][t].
+//   2. k_bin_colscan - exclusive scan of every column of H over b (in place) and the tile
+//                      totals n[t].
+//   3. (CUB) exclusive scan of n -> tile start; k_bin_ranges writes ranges and K.
+//   4. k_bin_scatter - one warp per block walks its Gaussians in depth order and writes
+//                      each one's index at start[t] + H[b][t] + (running count of the tile
+//                      inside the block), for every tile t of its rectangle.
+// The result is the stable (depth, index) order per tile.  Traffic is O(B T + K) words
+// instead of the ~26 bytes per entry of a two-pass radix sort of (tile, index) pairs.
 #include "bgs_internal.cuh"
 
 namespace bgs {
@@ -48,77 +42,31 @@ __device__ __forceinline__ void rect_of(const float2 *__restrict__ means2D, cons
     }
 }
 
-// first Gaussian (depth position) of every chunk of kChunk entries
-__global__ void __launch_bounds__(256) k_chunk_first(long long N, const unsigned long long *__restrict__ offsets,
-                                                     const uint32_t *__restrict__ counts, long long chunk,
-                                                     long long num_chunks, uint32_t *__restrict__ first) {
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    const unsigned long long c = counts[s];
-    if (c == 0) return;
-    const unsigned long long off = offsets[s];
-    for (unsigned long long b = (off + chunk - 1) / chunk; b * chunk < off + c && (long long)b < num_chunks; ++b)
-        first[b] = (uint32_t)s;
-}
-
-// Visits the entries [e0, e1) of the depth-ordered entry stream: fn(local position, tile, Gaussian index).
-// Warps take 32 consecutive Gaussians at a time (strided over the block) starting at
-// s_first; each one's entries are spread over the warp's lanes.
-template <typename Fn>
-__device__ __forceinline__ void for_chunk_entries(long long N, const uint32_t *__restrict__ order,
-                                                  const unsigned long long *__restrict__ offsets,
-                                                  const float2 *__restrict__ means2D, const int *__restrict__ radii,
-                                                  int tw, int th, int tx, int ty, long long s_first,
-                                                  unsigned long long e0, unsigned long long e1, Fn fn) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (long long base = s_first + 32ll * warp;; base += 32ll * nwarps) {
+__global__ void __launch_bounds__(256) k_bin_count(long long N, int G, const uint32_t *__restrict__ order,
+                                                   const float2 *__restrict__ means2D, const int *__restrict__ radii,
+                                                   int tw, int th, int tx, int ty, uint32_t *__restrict__ H) {
+    extern __shared__ uint32_t cnt_s[];
+    const int T = tx * ty;
+    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) cnt_s[t] = 0u;
+    __syncthreads();
+    const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
+    for (long long base = s0 + 32ll * warp; base < s1; base += 32ll * nwarps) {
         const long long s = base + lane;
         int x0 = 0, y0 = 0, w = 1, c = 0;
-        uint32_t g = 0;
-        unsigned long long off = e1;
-        if (s < N) {
-            off = offsets[s];
-            if (off < e1) {
-                g = order[s];
-                rect_of(means2D, radii, g, tw, th, tx, ty, x0, y0, w, c);
-            }
-        }
-        // the warp's first Gaussian starts past the chunk: every later one does too
-        if (__shfl_sync(0xffffffffu, off, 0) >= e1 || base >= N) break;
-        unsigned pending = __ballot_sync(0xffffffffu, c > 0 && off < e1 && off + (unsigned long long)c > e0);
+        if (s < s1) rect_of(means2D, radii, order[s], tw, th, tx, ty, x0, y0, w, c);
+        unsigned pending = __ballot_sync(0xffffffffu, c > 0);
         while (pending) {
             const int q = __ffs(pending) - 1;
             pending &= pending - 1;
             const int cq = __shfl_sync(0xffffffffu, c, q), wq = __shfl_sync(0xffffffffu, w, q);
             const int xq = __shfl_sync(0xffffffffu, x0, q), yq = __shfl_sync(0xffffffffu, y0, q);
-            const uint32_t gq = __shfl_sync(0xffffffffu, g, q);
-            const unsigned long long oq = __shfl_sync(0xffffffffu, off, q);
-            const int k0 = oq < e0 ? (int)(e0 - oq) : 0;
-            const int k1 = (int)min((unsigned long long)cq, e1 - oq);
-            for (int k = k0 + lane; k < k1; k += 32) {
+            for (int k = lane; k < cq; k += 32) {
                 const int dy = k / wq;
-                fn((int)(oq + k - e0), (yq + dy) * tx + xq + (k - dy * wq), gq);
+                atomicAdd(&cnt_s[(yq + dy) * tx + xq + (k - dy * wq)], 1u);
             }
         }
     }
-}
-
-__global__ void __launch_bounds__(512) k_bin_count(long long N, const uint32_t *__restrict__ order,
-                                                   const unsigned long long *__restrict__ offsets,
-                                                   const uint32_t *__restrict__ first,
-                                                   const unsigned long long *view_entries,
-                                                   const float2 *__restrict__ means2D, const int *__restrict__ radii,
-                                                   int tw, int th, int tx, int ty, uint32_t *__restrict__ H) {
-    extern __shared__ uint32_t cnt_s[];
-    const int T = tx * ty;
-    const int b = blockIdx.x;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) cnt_s[t] = 0u;
-    __syncthreads();
-    const unsigned long long K = *view_entries;
-    const unsigned long long e0 = (unsigned long long)b * kChunk, e1 = min(K, e0 + kChunk);
-    if (e0 < e1)
-        for_chunk_entries(N, order, offsets, means2D, radii, tw, th, tx, ty, first[b], e0, e1,
-                          [&](int, int t, uint32_t) { atomicAdd(&cnt_s[t], 1u); });
     __syncthreads();
     uint32_t *row = H + (size_t)b * T;
     for (int t = threadIdx.x; t < T; t += blockDim.x) row[t] = cnt_s[t];
@@ -169,10 +117,8 @@ __global__ void k_bin_ranges(int T, const uint32_t *__restrict__ start, const ui
     ranges[t] = n ? make_uint2(a, a + n) : make_uint2(0u, 0u);
 }
 
-// Adds the view's entry count (computed in 64 bits from the per-tile totals) to bin_base;
-// flags an overflow past the point_list capacity or past the view's chunk capacity.
-__global__ void k_bin_advance(int T, const uint32_t *__restrict__ total, long long capacity, int view,
-                              long long chunk_capacity, DevCtrl *ctrl) {
+// Adds the view's entry count (computed in 64 bits from the per-tile totals) to bin_base.
+__global__ void k_bin_advance(int T, const uint32_t *__restrict__ total, long long capacity, DevCtrl *ctrl) {
     __shared__ unsigned long long part[32];
     unsigned long long n = 0;
     for (int t = threadIdx.x; t < T; t += blockDim.x) n += total[t];
@@ -185,102 +131,50 @@ __global__ void k_bin_advance(int T, const uint32_t *__restrict__ total, long lo
         const unsigned long long next = ctrl->bin_base + k;
         ctrl->bin_base = next;
         ctrl->num_entries = next;
-        if ((long long)next > capacity || next >= 0xffffffffull ||
-            (long long)ctrl->view_entries[view] > chunk_capacity)
-            atomicOr(&ctrl->check_bits, (unsigned)BGS_CHECK_OVERFLOW);
+        if ((long long)next > capacity || next >= 0xffffffffull) atomicOr(&ctrl->check_bits, (unsigned)BGS_CHECK_OVERFLOW);
     }
 }
 
-// Chunk b: regenerate its entries, stable block radix sort by tile, rank inside each
-// tile's run, write index g to bin_base + start[t] + H[b][t] + rank.
-constexpr int kSortThreads = 512;
-constexpr int kSortItems = kChunk / kSortThreads;
-using SortKey = uint16_t;  // tile ids of a view are < 65536
-using BlockSortT = cub::BlockRadixSort<SortKey, kSortThreads, kSortItems, uint32_t>;
-using BlockScanT = cub::BlockScan<int, kSortThreads>;
-using BlockExchangeT = cub::BlockExchange<uint32_t, kSortThreads, kSortItems>;
-
-struct SortSmem {
-    union {
-        struct {
-            SortKey key[kChunk];
-            uint32_t val[kChunk];
-        } stage;
-        typename BlockSortT::TempStorage sort;
-        SortKey sorted_key[kChunk];
-        typename BlockExchangeT::TempStorage exchange;
-    } u;
-    typename BlockScanT::TempStorage scan;
-};
-
-size_t bin_sort_smem() { return sizeof(SortSmem); }
-
-__global__ void __launch_bounds__(kSortThreads) k_bin_sort_scatter(
-    long long N, const uint32_t *__restrict__ order, const unsigned long long *__restrict__ offsets,
-    const uint32_t *__restrict__ first, const unsigned long long *view_entries, const DevCtrl *ctrl,
-    const float2 *__restrict__ means2D, const int *__restrict__ radii, int tw, int th, int tx, int ty,
-    const uint32_t *__restrict__ H, const uint32_t *__restrict__ start, uint32_t *__restrict__ point_list,
-    long long capacity, int end_bit) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SortSmem &sm = *reinterpret_cast<SortSmem *>(smem_raw);
+// One warp per block of the depth order: walks its Gaussians in order and writes each
+// Gaussian index into the lists of the tiles its rectangle covers.
+__global__ void __launch_bounds__(32) k_bin_scatter(long long N, int G, const uint32_t *__restrict__ order,
+                                                    const float2 *__restrict__ means2D, const int *__restrict__ radii,
+                                                    int tw, int th, int tx, int ty, const uint32_t *__restrict__ H,
+                                                    const uint32_t *__restrict__ start, uint32_t *__restrict__ point_list,
+                                                    long long capacity, const DevCtrl *ctrl) {
+    extern __shared__ uint32_t pos_s[];
     const int T = tx * ty;
-    const int b = blockIdx.x;
-    const unsigned long long K = *view_entries;
-    const unsigned long long e0 = (unsigned long long)b * kChunk, e1 = min(K, e0 + kChunk);
-    if (e0 >= e1) return;  // uniform over the block
-    const int n = (int)(e1 - e0);
-    // 1. the chunk's entries in stream order (padding sorts last and is never written)
-    for (int i = threadIdx.x; i < kChunk; i += kSortThreads) {
-        if (i >= n) {
-            sm.u.stage.key[i] = (SortKey)0xffffu;
-            sm.u.stage.val[i] = 0xffffffffu;
+    const int b = blockIdx.x, lane = threadIdx.x;
+    const uint32_t *row = H + (size_t)b * T;
+    const uint32_t base = (uint32_t)ctrl->bin_base;
+    for (int t = lane; t < T; t += 32) pos_s[t] = base + start[t] + row[t];
+    __syncwarp();
+    const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
+    for (long long base = s0; base < s1; base += 32) {
+        const long long s = base + lane;
+        uint32_t g = 0;
+        int x0 = 0, y0 = 0, w = 1, c = 0;
+        if (s < s1) {
+            g = order[s];
+            rect_of(means2D, radii, g, tw, th, tx, ty, x0, y0, w, c);
+        }
+        unsigned pending = __ballot_sync(0xffffffffu, c > 0);
+        while (pending) {  // in depth order: lowest lane first
+            const int q = __ffs(pending) - 1;
+            pending &= pending - 1;
+            const int cq = __shfl_sync(0xffffffffu, c, q), wq = __shfl_sync(0xffffffffu, w, q);
+            const int xq = __shfl_sync(0xffffffffu, x0, q), yq = __shfl_sync(0xffffffffu, y0, q);
+            const uint32_t gq = __shfl_sync(0xffffffffu, g, q);
+            for (int k = lane; k < cq; k += 32) {  // distinct tiles: no two lanes share a counter
+                const int dy = k / wq;
+                const int t = (yq + dy) * tx + xq + (k - dy * wq);
+                const uint32_t p = pos_s[t];
+                pos_s[t] = p + 1u;
+                if ((long long)p < capacity) point_list[p] = gq;
+            }
+            __syncwarp();
         }
     }
-    for_chunk_entries(N, order, offsets, means2D, radii, tw, th, tx, ty, first[b], e0, e1,
-                      [&](int i, int t, uint32_t g) {
-                          sm.u.stage.key[i] = (SortKey)t;
-                          sm.u.stage.val[i] = g;
-                      });
-    __syncthreads();
-    SortKey keys[kSortItems];
-    uint32_t vals[kSortItems];
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        keys[j] = sm.u.stage.key[threadIdx.x * kSortItems + j];
-        vals[j] = sm.u.stage.val[threadIdx.x * kSortItems + j];
-    }
-    __syncthreads();
-    // 2. stable sort by tile (blocked arrangement in, blocked out)
-    BlockSortT(sm.u.sort).Sort(keys, vals, 0, end_bit);
-    __syncthreads();
-    // 3. rank inside the tile's run: position minus the run's first position (max-scan of heads)
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) sm.u.sorted_key[threadIdx.x * kSortItems + j] = keys[j];
-    __syncthreads();
-    int heads[kSortItems];
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const int p = threadIdx.x * kSortItems + j;
-        heads[j] = (p == 0 || sm.u.sorted_key[p - 1] != keys[j]) ? p : 0;
-    }
-    __syncthreads();
-    BlockScanT(sm.scan).InclusiveScan(heads, heads, [](int a, int b) { return a > b ? a : b; });
-    // 4. global slots, then write in striped order (consecutive threads, consecutive slots)
-    const uint32_t base = (uint32_t)ctrl->bin_base;
-    const uint32_t *row = H + (size_t)b * T;
-    uint32_t pos[kSortItems];
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const int p = threadIdx.x * kSortItems + j;
-        const int t = (int)keys[j];
-        pos[j] = (p < n && t < T) ? base + start[t] + row[t] + (uint32_t)(p - heads[j]) : 0xffffffffu;
-    }
-    BlockExchangeT(sm.u.exchange).BlockedToStriped(pos);
-    __syncthreads();
-    BlockExchangeT(sm.u.exchange).BlockedToStriped(vals);
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j)
-        if (pos[j] != 0xffffffffu && (long long)pos[j] < capacity) point_list[pos[j]] = vals[j];
 }
 
 size_t bin_count_smem(int T) { return sizeof(uint32_t) * (size_t)T; }
@@ -288,25 +182,15 @@ size_t bin_count_smem(int T) { return sizeof(uint32_t) * (size_t)T; }
 cudaError_t setup_bin_kernels(size_t smem) {
     cudaError_t e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_bin_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bin_sort_smem());
+        e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return e;
 }
 
-cudaError_t launch_chunk_first(long long N, const unsigned long long *offsets, const uint32_t *counts, long long B,
-                               uint32_t *first, cudaStream_t s) {
-    if (N == 0) return cudaSuccess;
-    k_chunk_first<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, offsets, counts, kChunk, B, first);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bin_count(long long N, int B, const uint32_t *order, const unsigned long long *offsets,
-                             const uint32_t *first, const unsigned long long *view_entries, const float *means2D,
-                             const int *radii, int W, int H, int tw, int th, uint32_t *Hm, cudaStream_t s) {
+cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
+                             int W, int H, int tw, int th, uint32_t *Hm, cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
-    k_bin_count<<<B, 512, bin_count_smem(tx * ty), s>>>(N, order, offsets, first, view_entries,
-                                                         reinterpret_cast<const float2 *>(means2D), radii, tw, th, tx,
-                                                         ty, Hm);
+    k_bin_count<<<B, 256, bin_count_smem(tx * ty), s>>>(N, G, order, reinterpret_cast<const float2 *>(means2D), radii,
+                                                         tw, th, tx, ty, Hm);
     return cudaGetLastError();
 }
 
@@ -321,21 +205,19 @@ cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *tota
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_advance(int T, const uint32_t *total, long long capacity, int view, long long chunk_capacity,
-                               DevCtrl *ctrl, cudaStream_t s) {
-    k_bin_advance<<<1, 1024, 0, s>>>(T, total, capacity, view, chunk_capacity, ctrl);
+cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *total, long long capacity, DevCtrl *ctrl,
+                               cudaStream_t s) {
+    (void)start;
+    k_bin_advance<<<1, 1024, 0, s>>>(T, total, capacity, ctrl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_sort_scatter(long long N, int B, const uint32_t *order, const unsigned long long *offsets,
-                                    const uint32_t *first, const unsigned long long *view_entries, const DevCtrl *ctrl,
-                                    const float *means2D, const int *radii, int W, int H, int tw, int th,
-                                    const uint32_t *Hm, const uint32_t *start, uint32_t *point_list, long long capacity,
-                                    int end_bit, cudaStream_t s) {
+cudaError_t launch_bin_scatter(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
+                               int W, int H, int tw, int th, const uint32_t *Hm, const uint32_t *start,
+                               uint32_t *point_list, long long capacity, const DevCtrl *ctrl, cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
-    k_bin_sort_scatter<<<B, kSortThreads, bin_sort_smem(), s>>>(N, order, offsets, first, view_entries, ctrl,
-                                                                 reinterpret_cast<const float2 *>(means2D), radii, tw,
-                                                                 th, tx, ty, Hm, start, point_list, capacity, end_bit);
+    k_bin_scatter<<<B, 32, bin_count_smem(tx * ty), s>>>(N, G, order, reinterpret_cast<const float2 *>(means2D), radii,
+                                                          tw, th, tx, ty, Hm, start, point_list, capacity, ctrl);
     return cudaGetLastError();
 }
 

@@ -81,11 +81,8 @@ struct bgs_plan {
     unsigned long long host_launches = 0;
     // binning
     Buf touched, touched_sorted, dkey, dkey_sorted, gidx, order, offsets, keys_in, keys_out, vals_in, cub_tmp;
-    Buf bin_h, bin_total, bin_start, bin_first;  // one-pass binning
+    Buf bin_h, bin_total, bin_start;  // counting-sort binning
     int smem_optin = 0;
-    // chunk grid of each view, sized by the last synchronising binning call
-    std::vector<long long> bin_chunks;
-    std::vector<long long> bin_sig;
     // render
     Buf recs, tile_key, tile_key2, tile_idx, tile_idx2, counts, item_off, items, grad_acc;
     // batched binning (64-bit depth keys)
@@ -300,7 +297,7 @@ int bgs_plan_destroy(bgs_plan *p) {
     DeviceGuard g(p->device);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     if (p->graph) cudaGraphDestroy(p->graph);
-    Buf *bufs[] = {&p->dkey64, &p->dkey64_sorted, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_first, &p->touched, &p->touched_sorted, &p->dkey,
+    Buf *bufs[] = {&p->dkey64, &p->dkey64_sorted, &p->bin_h, &p->bin_total, &p->bin_start, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off, &p->items,
@@ -477,104 +474,40 @@ int bgs_preprocess(bgs_plan *p, int64_t N, const float *means3D, const float *lo
 
 namespace {
 
-// Binning of V views (binning.cu).  order holds, for view v at positions [v N, (v+1) N),
-// the view's records in depth order (global record indices); touched [V N] is the entry
-// count of each record.  View v's lists follow those of views < v in point_list and its
-// tiles start at tile_base[v] in ranges.  With sync, the views' entry counts are read once
-// (one synchronisation) to size the chunk grids, *K_total receives their sum and nothing is
-// written when it exceeds capacity; without sync, the grids of the last synchronising call
-// with the same shapes are reused and overflows raise BGS_CHECK_OVERFLOW on the device.
-int bin_views(bgs_plan *p, int V, const int *Ws, const int *Hs, long long N, const uint32_t *order,
-              const uint32_t *touched, const float *means2D, const int32_t *radii, int tw, int th, uint32_t *point_list,
-              long long capacity, uint32_t *ranges, const int *tile_base, bool sync, unsigned long long *K_total,
-              cudaStream_t s) {
-    const long long R = (long long)V * N;
-    std::vector<long long> sig = {V, N, tw, th};
-    for (int v = 0; v < V; ++v) {
-        sig.push_back(Ws[v]);
-        sig.push_back(Hs[v]);
-        const long long T = (long long)((Ws[v] + tw - 1) / tw) * ((Hs[v] + th - 1) / th);
-        if (bgs::bin_count_smem((int)T) > (size_t)p->smem_optin || T > 65536)
-            return fail(BGS_ERR_INVALID, "view %d: tile grid too large for one-pass binning", v);
-    }
-    BGS_TRY(ensure(p, p->touched_sorted, 4 * R, s, "touched_sorted"));
-    BGS_TRY(ensure(p, p->offsets, 8 * R, s, "offsets"));
-    uint32_t *tsorted = (uint32_t *)p->touched_sorted.p;
-    unsigned long long *off = (unsigned long long *)p->offsets.p;
-    // (a) entry counts in depth order and their exclusive scan, per view
-    BGS_CUDA(bgs::launch_gather_u32(R, touched, order, tsorted, s), "gather counts");
-    for (int v = 0; v < V; ++v) {
-        size_t tmp = 0;
-        BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tsorted + (size_t)v * N, off + (size_t)v * N,
-                                               (int64_t)N, s),
-                 "entry scan (size)");
-        BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
-        tmp = p->cub_tmp.bytes;
-        BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, tsorted + (size_t)v * N, off + (size_t)v * N,
-                                               (int64_t)N, s),
-                 "entry scan");
-    }
-    BGS_CUDA(bgs::launch_view_totals(V, N, off, tsorted, p->ctrl, s), "view totals");
-    BGS_CUDA(cudaMemsetAsync(&p->ctrl->bin_base, 0, sizeof(unsigned long long), s), "clear bin base");
-    p->host_launches += 2;
-    // (b) chunk grids
-    std::vector<long long> chunks(V, 1);
-    if (sync) {
-        unsigned long long ke[bgs::kMaxViewsCtrl] = {0};
-        BGS_CUDA(cudaMemcpyAsync(ke, p->ctrl->view_entries, sizeof(unsigned long long) * V, cudaMemcpyDeviceToHost, s),
-                 "read view entries");
-        BGS_CUDA(cudaStreamSynchronize(s), "sync view entries");
-        unsigned long long k = 0;
-        for (int v = 0; v < V; ++v) {
-            k += ke[v];
-            chunks[v] = std::max<long long>(1, (long long)((ke[v] + bgs::kChunk - 1) / bgs::kChunk));
-        }
-        *K_total = k;
-        p->bin_chunks = chunks;
-        p->bin_sig = sig;
-        if ((long long)k > capacity || k >= (1ull << 32) - 1) return BGS_ERR_CAPACITY;  // caller reports
-    } else {
-        if (p->bin_sig != sig)
-            return fail(BGS_ERR_INVALID, "binning without synchronisation needs an earlier synchronising call with "
-                                         "the same views and Gaussian count (it sizes the chunk grids)");
-        chunks = p->bin_chunks;
-        *K_total = 0;
-    }
-    // (c) per view: chunk starts, per-chunk tile counts, column scan, tile starts, ranges, sort + scatter
-    for (int v = 0; v < V; ++v) {
-        const int W = Ws[v], H = Hs[v];
-        const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
-        const long long T = (long long)tiles_x * tiles_y;
-        const long long B = chunks[v];
-        if (B * T >= (1ll << 31)) return fail(BGS_ERR_INVALID, "tile histogram too large");
-        BGS_TRY(ensure(p, p->bin_h, sizeof(uint32_t) * B * T, s, "bin_h"));
-        BGS_TRY(ensure(p, p->bin_first, sizeof(uint32_t) * B, s, "bin_first"));
-        BGS_TRY(ensure(p, p->bin_total, sizeof(uint32_t) * T, s, "bin_total"));
-        BGS_TRY(ensure(p, p->bin_start, sizeof(uint32_t) * T, s, "bin_start"));
-        uint32_t *Hm = (uint32_t *)p->bin_h.p, *tot = (uint32_t *)p->bin_total.p, *start = (uint32_t *)p->bin_start.p;
-        uint32_t *first = (uint32_t *)p->bin_first.p;
-        BGS_CUDA(bgs::setup_bin_kernels(bgs::bin_count_smem((int)T)), "bin smem attribute");
-        const uint32_t *ord = order + (size_t)v * N;
-        const unsigned long long *offv = off + (size_t)v * N;
-        const unsigned long long *ke = &p->ctrl->view_entries[v];
-        BGS_CUDA(bgs::launch_chunk_first(N, offv, tsorted + (size_t)v * N, B, first, s), "chunk_first");
-        BGS_CUDA(bgs::launch_bin_count(N, (int)B, ord, offv, first, ke, means2D, radii, W, H, tw, th, Hm, s),
-                 "bin_count");
-        BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, tot, s), "bin_colscan");
-        size_t tmp = 0;
-        BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tot, start, (int)T, s), "tile scan (size)");
-        BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
-        tmp = p->cub_tmp.bytes;
-        BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, tot, start, (int)T, s), "tile scan");
-        uint32_t *rg = ranges + 2ull * tile_base[v];
-        BGS_CUDA(bgs::launch_bin_ranges((int)T, start, tot, reinterpret_cast<uint2 *>(rg), p->ctrl, s), "bin_ranges");
-        BGS_CUDA(bgs::launch_bin_sort_scatter(N, (int)B, ord, offv, first, ke, p->ctrl, means2D, radii, W, H, tw, th,
-                                              Hm, start, point_list, capacity, bits_for(T - 1), s),
-                 "bin_sort_scatter");
-        BGS_CUDA(bgs::launch_bin_advance((int)T, tot, sync ? (1ll << 62) : capacity, v, B * bgs::kChunk, p->ctrl, s),
-                 "bin_advance");
-        p->host_launches += 6;  // chunk_first, count, colscan, ranges, sort_scatter, advance
-    }
+// Counting-sort binning of one view (binning.cu): order holds the view's records in depth
+// order (global record indices); ranges points at the view's first tile.  Writes its lists
+// from point_list slot ctrl->bin_base on and advances bin_base.  No host synchronisation.
+// With flag_overflow, an entry count past capacity raises BGS_CHECK_OVERFLOW on the device
+// (graph-safe callers check it with bgs_check); otherwise the host checks the count.
+int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const float *means2D, const int32_t *radii,
+                      int W, int H, int tw, int th, uint32_t *point_list, long long capacity, uint32_t *ranges,
+                      bool flag_overflow, cudaStream_t s) {
+    const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
+    const long long T = (long long)tiles_x * tiles_y;
+    const size_t smem = bgs::bin_count_smem((int)T);
+    if (smem > (size_t)p->smem_optin) return fail(BGS_ERR_INVALID, "tile grid too large for counting-sort binning");
+    const long long G = std::max<long long>(512, (n * T + (1ll << 24) - 1) >> 24);
+    const long long B = std::max<long long>(1, (n + G - 1) / G);
+    if (B * T >= (1ll << 31)) return fail(BGS_ERR_INVALID, "tile histogram too large");
+    BGS_TRY(ensure(p, p->bin_h, sizeof(uint32_t) * B * T, s, "bin_h"));
+    BGS_TRY(ensure(p, p->bin_total, sizeof(uint32_t) * T, s, "bin_total"));
+    BGS_TRY(ensure(p, p->bin_start, sizeof(uint32_t) * T, s, "bin_start"));
+    uint32_t *Hm = (uint32_t *)p->bin_h.p, *tot = (uint32_t *)p->bin_total.p, *start = (uint32_t *)p->bin_start.p;
+    if (smem > 48 * 1024) BGS_CUDA(bgs::setup_bin_kernels(smem), "bin smem attribute");
+    BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, s), "bin_count");
+    BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, tot, s), "bin_colscan");
+    size_t tmp = 0;
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tot, start, (int)T, s), "tile scan (size)");
+    BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
+    tmp = p->cub_tmp.bytes;
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, tot, start, (int)T, s), "tile scan");
+    BGS_CUDA(bgs::launch_bin_ranges((int)T, start, tot, reinterpret_cast<uint2 *>(ranges), p->ctrl, s), "bin_ranges");
+    BGS_CUDA(bgs::launch_bin_scatter(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, start, point_list,
+                                     capacity, p->ctrl, s),
+             "bin_scatter");
+    BGS_CUDA(bgs::launch_bin_advance((int)T, start, tot, flag_overflow ? capacity : (1ll << 62), p->ctrl, s),
+             "bin_advance");
+    p->host_launches += 5;  // count, colscan, ranges, scatter, advance
     return BGS_OK;
 }
 
@@ -647,17 +580,17 @@ int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t
     tmp = p->cub_tmp.bytes;
     BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, dkey, dkey2, gidx, order, (int64_t)N, 0, 32, s),
              "depth sort");
-    // (2) one-pass binning when the per-tile counters fit in shared memory
-    if (bgs::bin_count_smem((int)T) <= (size_t)p->smem_optin && T <= 65536) {
-        const int base0 = 0;
+    // (2) counting sort over tile rectangles when the per-tile counters fit in shared memory
+    if (bgs::bin_count_smem((int)T) <= (size_t)p->smem_optin) {
+        BGS_CUDA(cudaMemsetAsync(&p->ctrl->bin_base, 0, sizeof(unsigned long long), s), "clear bin base");
+        BGS_TRY(bin_view_counting(p, N, order, means2D, radii, W, H, tw, th, point_list, capacity, ranges, false, s));
         unsigned long long K = 0;
-        const int rc = bin_views(p, 1, &W, &H, N, order, touched, means2D, radii, tw, th, point_list, capacity, ranges,
-                                 &base0, true, &K, s);
+        BGS_CUDA(cudaMemcpyAsync(&K, &p->ctrl->num_entries, sizeof K, cudaMemcpyDeviceToHost, s), "read K");
+        BGS_CUDA(cudaStreamSynchronize(s), "sync K");
         if (needed) *needed = (int64_t)K;
-        if (rc == BGS_ERR_CAPACITY)
+        if ((long long)K > capacity || K >= (1ull << 32) - 1)
             return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort: %llu entries exceed capacity %lld (or 2^32)", K,
                         (long long)capacity);
-        BGS_TRY(rc);
         if (num_rendered) *num_rendered = (int64_t)K;
         return BGS_OK;
     }
@@ -821,8 +754,7 @@ int render_backward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewG
         a.recs = (const bgs::Rec *)p->recs.p;
         BGS_TRY(build_worklist(p, ranges, vt, tw, th, BGS_MODE_PIXEL, s));
         a.items = (const uint2 *)p->items.p;
-        const int grid = grid_for(p, bgs::backward_balanced_kernel(a.pixel_rows),
-                                  bgs::backward_balanced_block_threads());
+        const int grid = grid_for(p, bgs::backward_balanced_kernel(a), bgs::backward_balanced_block_threads());
         KernelTimer kt(p, s, &p->ev_bwd);
         BGS_CUDA(bgs::launch_backward_balanced(a, grid, s), "backward_balanced");
         kt.stop();
@@ -957,16 +889,9 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
         BGS_TRY(ensure(p, p->dkey64_sorted, 8 * R, s, "dkey64_sorted"));
         BGS_TRY(ensure(p, p->gidx, 4 * R, s, "gidx"));
         BGS_TRY(ensure(p, p->order, 4 * R, s, "order"));
-        BGS_TRY(ensure(p, p->touched, 4 * R, s, "touched"));
         unsigned long long *k0 = (unsigned long long *)p->dkey64.p, *k1 = (unsigned long long *)p->dkey64_sorted.p;
-        uint32_t *gidx = (uint32_t *)p->gidx.p, *order = (uint32_t *)p->order.p, *touched = (uint32_t *)p->touched.p;
-        bgs::TileGrids tg;
-        for (int v = 0; v < V; ++v) {
-            tg.tx[v] = vt.tiles_x[v];
-            tg.ty[v] = vt.tiles_y[v];
-        }
-        BGS_CUDA(bgs::launch_depth_keys64(N, V, means2D, radii, depths, tw, th, tg, touched, k0, gidx, s),
-                 "depth keys");
+        uint32_t *gidx = (uint32_t *)p->gidx.p, *order = (uint32_t *)p->order.p;
+        BGS_CUDA(bgs::launch_depth_keys64(N, V, depths, k0, gidx, s), "depth keys");
         const int end_bit = 32 + bits_for(V - 1);
         size_t tmp = 0;
         BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, k0, k1, gidx, order, (int64_t)R, 0, end_bit, s),
@@ -976,18 +901,24 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
         BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, k0, k1, gidx, order, (int64_t)R, 0, end_bit, s),
                  "view/depth sort");
         p->host_launches += 1;
-        unsigned long long K = 0;
-        const int rc = bin_views(p, V, Ws, Hs, N, order, touched, means2D, radii, tw, th, point_list, capacity, ranges,
-                                 vt.tile_base, sync, &K, s);
-        if (needed) *needed = (int64_t)K;
-        if (rc == BGS_ERR_CAPACITY)
-            return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort_batched: %llu entries exceed capacity %lld (or 2^32)", K,
-                        (long long)capacity);
-        BGS_TRY(rc);
-        if (num_rendered) *num_rendered = (int64_t)K;
+        for (int v = 0; v < V; ++v)  // view v's records are positions [v N, (v+1) N) of the order
+            BGS_TRY(bin_view_counting(p, N, order + (size_t)v * N, means2D, radii, Ws[v], Hs[v], tw, th, point_list,
+                                      capacity, ranges + 2ull * vt.tile_base[v], !sync, s));
     }
+    if (!sync) return BGS_OK;
+    unsigned long long K = 0;
+    if (R > 0) {
+        BGS_CUDA(cudaMemcpyAsync(&K, &p->ctrl->num_entries, sizeof K, cudaMemcpyDeviceToHost, s), "read K");
+        BGS_CUDA(cudaStreamSynchronize(s), "sync K");
+    }
+    if (needed) *needed = (int64_t)K;
+    if ((long long)K > capacity || K >= (1ull << 32) - 1)
+        return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort_batched: %llu entries exceed capacity %lld (or 2^32)", K,
+                    (long long)capacity);
+    if (num_rendered) *num_rendered = (int64_t)K;
     return BGS_OK;
 }
+
 static int batched_tables(int V, const bgs_view *views, int tw, int th, bgs::ViewTable &vt) {
     if (!views) return fail(BGS_ERR_INVALID, "NULL views");
     if (V < 1 || V > bgs::kMaxViews) return fail(BGS_ERR_INVALID, "V=%d outside [1, %d]", V, bgs::kMaxViews);

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kNaWarps * 32) k_na_forward(NaArgs a, NaScratc
                         c0 += w * rc.x;
                         c1 += w * rc.y;
                         c2 += w * rc.z;
-                        D += w * rb.z;
+                        D += w * rc.w;
                         A += w;
                         T = tt;
                         last = (int)(base + k + 1 - rg.x);

@@ -151,46 +151,20 @@ cudaError_t launch_preprocess(long long N, int V, const float *means3D, const fl
     return cudaGetLastError();
 }
 
-// Batched binning: entry count of each record (its rectangle's area in its view's tile
-// grid) and its sort key (view << 32 | float bits of depth); value = record index.
-__global__ void __launch_bounds__(256) k_depth_keys64(long long N, int V, const float2 *__restrict__ means2D,
-                                                      const int *__restrict__ radii, const float *__restrict__ depths,
-                                                      int tw, int th, const TileGrids tg, uint32_t *__restrict__ touched,
+// Depth sort keys of a batched binning: (view << 32 | float bits of depth), value = record.
+__global__ void __launch_bounds__(256) k_depth_keys64(long long N, int V, const float *__restrict__ depths,
                                                       unsigned long long *__restrict__ keys, uint32_t *__restrict__ idx) {
     const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (rec >= N * V) return;
-    const int view = (int)(rec / N);
-    uint32_t c = 0;
-    const int r = radii[rec];
-    if (r > 0) {
-        const float2 m = means2D[rec];
-        int x0, x1, y0, y1;
-        tile_rect(m.x, m.y, r, tw, th, tg.tx[view], tg.ty[view], x0, x1, y0, y1);
-        if (x1 > x0 && y1 > y0) c = (uint32_t)((x1 - x0) * (y1 - y0));
-    }
-    touched[rec] = c;
-    keys[rec] = ((unsigned long long)view << 32) | (unsigned long long)__float_as_uint(depths[rec]);
+    const unsigned long long view = (unsigned long long)(rec / N);
+    keys[rec] = (view << 32) | (unsigned long long)__float_as_uint(depths[rec]);
     idx[rec] = (uint32_t)rec;
 }
 
-cudaError_t launch_depth_keys64(long long N, int V, const float *means2D, const int *radii, const float *depths,
-                                int tw, int th, const TileGrids &tg, uint32_t *touched, unsigned long long *keys,
-                                uint32_t *idx, cudaStream_t s) {
+cudaError_t launch_depth_keys64(long long N, int V, const float *depths, unsigned long long *keys, uint32_t *idx,
+                                cudaStream_t s) {
     if (N * V == 0) return cudaSuccess;
-    k_depth_keys64<<<(unsigned)((N * V + 255) / 256), 256, 0, s>>>(N, V, reinterpret_cast<const float2 *>(means2D),
-                                                                   radii, depths, tw, th, tg, touched, keys, idx);
-    return cudaGetLastError();
-}
-
-__global__ void k_view_totals(int V, long long N, const unsigned long long *__restrict__ offsets,
-                              const uint32_t *__restrict__ counts, DevCtrl *ctrl) {
-    const int v = threadIdx.x;
-    if (v < V && N > 0) ctrl->view_entries[v] = offsets[v * N + N - 1] + counts[v * N + N - 1];
-}
-
-cudaError_t launch_view_totals(int V, long long N, const unsigned long long *offsets, const uint32_t *counts,
-                               DevCtrl *ctrl, cudaStream_t s) {
-    k_view_totals<<<1, 32, 0, s>>>(V, N, offsets, counts, ctrl);
+    k_depth_keys64<<<(unsigned)((N * V + 255) / 256), 256, 0, s>>>(N, V, depths, keys, idx);
     return cudaGetLastError();
 }
 

@@ -60,6 +60,9 @@ __device__ __forceinline__ PixState load_pixel(const BwdArgs &a, int v, int px, 
 //   v2 = dL/dpower dx^2, v3 = dL/dpower dx dy, v4 = dL/dpower dy^2,
 //   v5 = dL/do, v6..8 = dL/dc, v9 = dL/d(depth)
 // (power is the natural-log exponent; the final pass applies the ln2 and -1/2 factors).
+// Extra = false: no depth / alpha output gradients (dL/dD = dL/dA = 0), their terms are
+// compiled out.
+template <bool Extra>
 __device__ __forceinline__ bool pair_backward(const Rec &r, float pxf, float pyf, bool active, PixState &s,
                                               float v[10]) {
     float dx, dy, G;
@@ -74,14 +77,15 @@ __device__ __forceinline__ bool pair_backward(const Rec &r, float pxf, float pyf
         v[6] += w * s.g0;
         v[7] += w * s.g1;
         v[8] += w * s.g2;
-        v[9] += w * s.gD;
-        const float dLda = s.T * ((r.c.x - s.R0) * s.g0 + (r.c.y - s.R1) * s.g1 + (r.c.z - s.R2) * s.g2 +
-                                  (r.b.z - s.Rd) * s.gD) +
-                           s.Tf * io * s.gA;
+        float dLda = s.T * ((r.c.x - s.R0) * s.g0 + (r.c.y - s.R1) * s.g1 + (r.c.z - s.R2) * s.g2);
+        if (Extra) {
+            v[9] += w * s.gD;
+            dLda += s.T * (r.c.w - s.Rd) * s.gD + s.Tf * io * s.gA;
+            s.Rd = al * r.c.w + om * s.Rd;
+        }
         s.R0 = al * r.c.x + om * s.R0;
         s.R1 = al * r.c.y + om * s.R1;
         s.R2 = al * r.c.z + om * s.R2;
-        s.Rd = al * r.b.z + om * s.Rd;
         const float o = r.b.y;
         if (o * G <= kAlphaMax) {
             const float gp = o * G * dLda;  // dL/dpower
@@ -123,19 +127,20 @@ __device__ __forceinline__ void warp_reduce_red10(const float v[10], float *acc,
     if ((lane & 1) == 0 && idx < 10 && tot != 0.f) atomicAdd(acc + idx, tot);
 }
 
-__device__ __forceinline__ Rec load_rec_bwd(const BwdArgs &a, uint32_t j) {
-    const uint32_t g = a.point_list[j];
+// Record of list entry j and its index g; an index >= N raises BGS_CHECK_INDEX and yields a
+// transparent record (its box misses every pixel) with index 0.
+__device__ __forceinline__ Rec load_rec_bwd(const BwdArgs &a, uint32_t j, uint32_t &g) {
+    g = a.point_list[j];
     Rec r;
     if ((long long)g >= a.N) {
         raise_check(a.ctrl, BGS_CHECK_INDEX);
+        g = 0;
         r.a = make_float4(0.f, 0.f, 0.f, 0.f);
-        r.b = r.a;
-        r.c = make_float4(0.f, 0.f, 0.f, __uint_as_float(0u));
+        r.b = make_float4(0.f, 0.f, -1.f, -1.f);
+        r.c = make_float4(0.f, 0.f, 0.f, 0.f);
         return r;
     }
-    r = a.recs[g];
-    r.c.w = __uint_as_float(g);
-    return r;
+    return a.recs[g];
 }
 
 __device__ __forceinline__ uint2 load_range_bwd(const BwdArgs &a, int tile) {
@@ -151,7 +156,7 @@ __device__ __forceinline__ uint2 load_range_bwd(const BwdArgs &a, int tile) {
 // plain pixel-wise static backward: one block per tile, block-wide staging
 // =====================================================================================
 __global__ void __launch_bounds__(1024) k_backward_static(BwdArgs a) {
-    extern __shared__ Rec srec[];
+    extern __shared__ Rec srec[];  // [nthreads] records, then [nthreads] indices
     __shared__ int s_max;
     const int nthreads = blockDim.x, tid = threadIdx.x, lane = tid & 31;
     const int tile = blockIdx.x;  // single view
@@ -171,6 +176,7 @@ __global__ void __launch_bounds__(1024) k_backward_static(BwdArgs a) {
     __syncthreads();
     const uint32_t hi = rg.x + (uint32_t)s_max;
     const float pxf = (float)px, pyf = (float)py;
+    uint32_t *sidx = reinterpret_cast<uint32_t *>(srec + nthreads);
     for (uint32_t top = hi; top > rg.x; top -= min((uint32_t)nthreads, top - rg.x)) {
         const uint32_t lo = top - min((uint32_t)nthreads, top - rg.x);
         const int cnt = (int)(top - lo);
@@ -181,7 +187,6 @@ __global__ void __launch_bounds__(1024) k_backward_static(BwdArgs a) {
             Rec r;
             if ((long long)g < a.N) {
                 r = make_rec(a.means2D, a.conic_opacity, a.colors, a.depths, g);
-                r.c.w = __uint_as_float(g);
             } else {
                 raise_check(a.ctrl, BGS_CHECK_INDEX);
                 r.a = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -189,15 +194,15 @@ __global__ void __launch_bounds__(1024) k_backward_static(BwdArgs a) {
                 r.c = r.a;
             }
             srec[tid] = r;
+            sidx[tid] = (long long)g < a.N ? g : 0u;
         }
         __syncthreads();
         for (int k = 0; k < cnt; ++k) {
             const Rec r = srec[k];
             const int pos = (int)(top - 1 - k - rg.x);
             float v[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const bool valid = pair_backward(r, pxf, pyf, pos < s.nc, s, v);
-            if (__any_sync(kFullB, valid))
-                warp_reduce_red10(v, a.grad_acc + 12ull * __float_as_uint(r.c.w), lane);
+            const bool valid = pair_backward<true>(r, pxf, pyf, pos < s.nc, s, v);
+            if (__any_sync(kFullB, valid)) warp_reduce_red10(v, a.grad_acc + 12ull * sidx[k], lane);
         }
     }
 }
@@ -206,7 +211,7 @@ cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s) {
     const int threads = a.tile_w * a.tile_h;
     const int tiles = a.vt.tiles_x[0] * a.vt.tiles_y[0];
     if (tiles == 0) return cudaSuccess;
-    k_backward_static<<<tiles, threads, sizeof(Rec) * threads, s>>>(a);
+    k_backward_static<<<tiles, threads, (sizeof(Rec) + sizeof(uint32_t)) * threads, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -216,8 +221,9 @@ cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s) {
 // Pixel-wise item: an 8 x 4Q sub-block; lane l owns the pixels (l % 8, l / 8 + 4 q).  The
 // lane adds its pixels' contributions before the warp-wide reduction, so one reduction
 // serves 32 Q pixels.
-template <int Q>
-__device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int sub, Rec *buf, int lane) {
+template <int Q, bool Extra>
+__device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int sub, Rec *buf, uint32_t *gbuf,
+                                               int lane) {
     constexpr int kItemH = 4 * Q;
     const int v = view_of(a.vt, tile);
     const int lt = tile - a.vt.tile_base[v];
@@ -244,30 +250,40 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
     maxnc = __reduce_max_sync(kFullB, maxnc);
     const uint32_t hi = rg.x + (uint32_t)maxnc;
     const float pxf = (float)px;
+    const float bcx = (float)(x0 + sx * kPixItemW) + 3.5f;
+    const float bcy = (float)(y0 + sy * kItemH) + 0.5f * (kItemH - 1);
     for (uint32_t top = hi; top > rg.x;) {
         const uint32_t lo = top - min(32u, top - rg.x);
         const int cnt = (int)(top - lo);
         __syncwarp();
-        if (lane < cnt) buf[lane] = load_rec_bwd(a, top - 1 - lane);
+        if (lane < cnt) {
+            uint32_t g;
+            buf[lane] = load_rec_bwd(a, top - 1 - lane, g);
+            gbuf[lane] = g;
+        }
         __syncwarp();
         for (int k = 0; k < cnt; ++k) {
+            const float4 ra = buf[k].a, rb = buf[k].b;
+            if (box_misses(ra, rb, bcx, bcy, 3.5f, 0.5f * (kItemH - 1))) continue;  // warp-uniform
             const Rec r = buf[k];
             const int pos = (int)(top - 1 - k - rg.x);
             float v[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool any = false;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) any |= pair_backward(r, pxf, pyf[q], pos < s[q].nc, s[q], v);
-            if (__any_sync(kFullB, any)) warp_reduce_red10(v, a.grad_acc + 12ull * __float_as_uint(r.c.w), lane);
+            for (int q = 0; q < Q; ++q) any |= pair_backward<Extra>(r, pxf, pyf[q], pos < s[q].nc, s[q], v);
+            if (__any_sync(kFullB, any)) warp_reduce_red10(v, a.grad_acc + 12ull * gbuf[k], lane);
         }
         top = lo;
     }
 }
 
-template <int Q>
+template <int Q, bool Extra>
 __global__ void __launch_bounds__(kBwdWarps * 32) k_backward_balanced(BwdArgs a) {
     __shared__ Rec sbuf[kBwdWarps][32];
+    __shared__ uint32_t sidx[kBwdWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Rec *buf = sbuf[warp];
+    uint32_t *gbuf = sidx[warp];
     const unsigned num_items = a.ctrl->num_items;
     const unsigned chunk = (unsigned)a.chunk;
     while (true) {
@@ -278,29 +294,34 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_backward_balanced(BwdArgs a)
         const unsigned end = min(first + chunk, num_items);
         for (unsigned it = first; it < end; ++it) {
             const uint2 item = a.items[it];
-            bwd_pixel_item<Q>(a, (int)item.x, (int)(item.y & ~kKindGauss), buf, lane);
+            bwd_pixel_item<Q, Extra>(a, (int)item.x, (int)(item.y & ~kKindGauss), buf, gbuf, lane);
         }
     }
 }
 
 int backward_balanced_block_threads() { return kBwdWarps * 32; }
-const void *backward_balanced_kernel(int pixel_rows) {
-    switch (pixel_rows) {
-        case 1: return (const void *)k_backward_balanced<1>;
-        case 2: return (const void *)k_backward_balanced<2>;
-        case 4: return (const void *)k_backward_balanced<4>;
+static bool has_extra(const BwdArgs &a) {
+    for (int v = 0; v < a.vt.V; ++v)
+        if (a.gi.dL_ddepth[v] || a.gi.dL_dalpha[v]) return true;
+    return false;
+}
+
+const void *backward_balanced_kernel(const BwdArgs &a) {
+    const bool e = has_extra(a);
+    switch (a.pixel_rows) {
+        case 1: return e ? (const void *)k_backward_balanced<1, true> : (const void *)k_backward_balanced<1, false>;
+        case 2: return e ? (const void *)k_backward_balanced<2, true> : (const void *)k_backward_balanced<2, false>;
+        case 4: return e ? (const void *)k_backward_balanced<4, true> : (const void *)k_backward_balanced<4, false>;
         default: return nullptr;
     }
 }
 
 cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s) {
-    switch (a.pixel_rows) {
-        case 1: k_backward_balanced<1><<<grid, kBwdWarps * 32, 0, s>>>(a); break;
-        case 2: k_backward_balanced<2><<<grid, kBwdWarps * 32, 0, s>>>(a); break;
-        case 4: k_backward_balanced<4><<<grid, kBwdWarps * 32, 0, s>>>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    const void *k = backward_balanced_kernel(a);
+    if (!k) return cudaErrorInvalidValue;
+    BwdArgs arg = a;
+    void *params[] = {&arg};
+    return cudaLaunchKernel(k, dim3(grid), dim3(kBwdWarps * 32), params, 0, s);
 }
 
 // ---- accumulator -> ABI gradient arrays ----------------------------------------------

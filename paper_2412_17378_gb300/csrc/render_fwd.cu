@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(1024) k_forward_static(FwdArgs a) {
             c0 += w * rc.x;
             c1 += w * rc.y;
             c2 += w * rc.z;
-            D += w * rb.z;
+            D += w * rc.w;
             A += w;
             T = tt;
             last = (int)(base + k + 1 - rg.x);
@@ -188,6 +188,9 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
     const int py0 = tg.y0 + sy * kItemH + (lane >> 3);
     const uint2 rg = load_range(a, tile);
     const float pxf = (float)px;
+    // centre and half-extent of the item's pixel block (for skipping records that miss it)
+    const float bcx = (float)(tg.x0 + sx * kPixItemW) + 3.5f;
+    const float bcy = (float)(tg.y0 + sy * kItemH) + 0.5f * (kItemH - 1);
     float pyf[Q], T[Q], c0[Q], c1[Q], c2[Q], D[Q], A[Q];
     int last[Q], neval[Q], nacc[Q];
     bool done[Q], inside[Q];
@@ -216,7 +219,8 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
         const int pos0 = (int)(base - rg.x);
         for (int k = 0; k < cnt; ++k) {
             const float4 ra = buf[k].a;
-            const float2 rb = *reinterpret_cast<const float2 *>(&buf[k].b);
+            const float4 rb = buf[k].b;
+            if (box_misses(ra, rb, bcx, bcy, 3.5f, 0.5f * (kItemH - 1))) continue;  // warp-uniform
             const PairX px2 = pair_x(ra, pxf);  // shared by the lane's pixels (same column)
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
@@ -234,7 +238,7 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
                         c0[q] += w * rc.x;
                         c1[q] += w * rc.y;
                         c2[q] += w * rc.z;
-                        D[q] += w * buf[k].b.z;
+                        D[q] += w * rc.w;
                         A[q] += w;
                         T[q] = tt;
                         last[q] = pos0 + k + 1;
@@ -326,7 +330,7 @@ __device__ __forceinline__ void gauss_item(const FwdArgs &a, int tile, int sub, 
                 c0[p] += w * r.c.x;
                 c1[p] += w * r.c.y;
                 c2[p] += w * r.c.z;
-                D[p] += w * r.b.z;
+                D[p] += w * r.c.w;
                 A[p] += w;
             }
             const float tnew = __shfl_sync(kFull, tt, kstop > 0 ? kstop - 1 : 0);

@@ -176,9 +176,9 @@ def test_graph_capture_replays_the_step(R, batch):
 def test_no_sync_binning_flags_overflow(R, batch):
     plan = R.Plan()
     cams = batch["cams"]
+    m2, rd, dp = _stack(batch, "means2D"), _stack(batch, "radii"), _stack(batch, "depths")
     pl = torch.empty(100, dtype=torch.int32, device="cuda")  # far too small
-    R.bin_and_sort_batched(plan, _stack(batch, "means2D"), _stack(batch, "radii"), _stack(batch, "depths"), cams,
-                           point_list=pl, no_sync=True)
+    R.bin_and_sort_batched(plan, m2, rd, dp, cams, point_list=pl, no_sync=True)
     with pytest.raises(R.BgsError) as e:
         plan.check()
     assert e.value.code == -4 and "overflow" in str(e.value)
