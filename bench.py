@@ -1,10 +1,12 @@
 """Benchmark of the balanced splat render path on one GB300 (or N replicas).
 
-A step is one pass of the whole hot path over one synthetic frame:
+A step is one pass of the whole hot path over one synthetic frame (every view of the
+workload):
   a1 projection -> a2 binning + sort -> a3 work list -> a5 balanced forward
-  -> L2 loss gradient (torch) -> a6 balanced backward.
-Workload: 1920x1080, 1M Gaussians, 80% in one cluster covering ~5% of the image (the
-imbalanced single-view configuration), forward + backward.
+  -> L2 loss gradient (torch) -> a6 balanced backward,
+enqueued without host synchronisation, captured once as a CUDA graph and replayed.
+Default workload: 1920x1080, 1M Gaussians, 80% in one cluster covering ~5% of the image
+(the imbalanced single-view configuration), forward + backward.
 
 The metric is Gaussian-pixel pairs per second: pairs = (pixel, list entry) pairs the
 sequential rule visits (sum of n_eval over the frame), divided by the step time.  The
@@ -12,7 +14,7 @@ JSON line also carries ms/frame, the plain pixel-wise 16x16 static-grid kernel o
 same inputs, the roofline of the dominant render kernel and the FP64 CPU oracle timed on
 a bounded sample of the same frame.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py [--gpus N --steps K --warmup W] [--config cfg2] [--impl reference]
 """
 from __future__ import annotations
 
@@ -64,9 +66,22 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
     ap.add_argument("--mode", default="auto", choices=["auto", "pixel", "gaussian", "static"],
                     help="render mode of the timed steps")
+    ap.add_argument("--knobs", default="",
+                    help="plan knobs for the timed steps when not tuning, e.g. pixel_rows=4,heavy_threshold=2147483647")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed steps (no tuning, baselines, e2e or oracle): for profiler runs")
     return ap.parse_args()
+
+
+def apply_knobs(plan, spec):
+    """Sets plan knobs given as 'name=value,...' (the tuner's knob names)."""
+    kw = {}
+    for item in filter(None, spec.split(",")):
+        k, v = item.split("=")
+        kw[k.strip()] = int(v)
+    if kw:
+        plan.set(**kw)
+    return kw
 
 
 def dist_init(args):
@@ -222,231 +237,26 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.mode == "static":
+        raise SystemExit("--mode static: the static kernel is timed as the baseline of every full run")
     import torch
     rank, world, local = dist_init(args)
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_2412_17378_gb300 import raster, scenes
-
+    from paper_2412_17378_gb300 import scenes
     scene = scenes.scene_config(args.config, args.scale)
-    if len(scene["cameras"]) > 1:
-        return main_batched(args, scene, rank, world, local)
-    g, cam = scene["gaussians"], scene["cameras"][0]
-    W, H = cam["W"], cam["H"]
-    dev = torch.device("cuda", local)
-    host = {k: torch.from_numpy(v).pin_memory() for k, v in g.items()}
-    target_h = torch.from_numpy(scenes.target_image(2, W, H)).pin_memory()
-    d = {k: v.to(dev) for k, v in host.items()}
-    target = target_h.to(dev)
-    N = d["means3D"].shape[0]
-    plan = raster.Plan(device=local)
-    tile = (16, 16)
-    pl_buf = [None]
-
-    def step(mode="auto", gin=d, tgt=target):
-        pre = raster.preprocess(plan, gin["means3D"], gin["log_scales"], gin["quats"], gin["opacities"], cam, tile)
-        pl, rg, K = raster.bin_and_sort(plan, pre["means2D"], pre["radii"], pre["depths"], W, H, tile, pl_buf[0])
-        pl_buf[0] = pl
-        fw = raster.render_forward(plan, pre["means2D"], pre["conic_opacity"], gin["colors"], pre["depths"], pl, K, rg,
-                                   W, H, tile, (0.0, 0.0, 0.0), mode)
-        dL = torch.sub(fw["color"], tgt)
-        gr = raster.render_backward(plan, pre["means2D"], pre["conic_opacity"], gin["colors"], pre["depths"], pl, K,
-                                    rg, W, H, fw["final_T"], fw["n_contrib"], dL, None, None, tile, (0.0, 0.0, 0.0),
-                                    mode)
-        return pre, (pl, rg, K), fw, gr, dL
-
-    # ---- frame statistics (evaluated / contributing pairs, backward pairs) ----
-    plan.reset_stats()
-    pre, binning, fw, _, _ = step("auto")
-    st = plan.stats()
-    eval_pairs, contrib_pairs = st["eval_pairs"], st["contrib_pairs"]
-    bwd_pairs = int(fw["n_contrib"].sum().item())
-    K = binning[2]
-    rgh = binning[1].cpu().numpy()
-    lens = rgh[:, 1] - rgh[:, 0]
-
-    # ---- autotune (bgs_autotune_render): sub-tile, heavy-tile threshold, Gaussian-wise pixels, chunk ----
-    tuned = {}
-    if args.quick:
-        args.no_tune = args.no_cpu_baseline = True
-    if not args.no_tune:
-        pl, rg, K = binning
-        best_ms, knobs = raster.autotune_render(plan, pre["means2D"], pre["conic_opacity"], d["colors"],
-                                                pre["depths"], pl, K, rg, [cam])
-        tuned = {k: knobs[k] for k in ("pixel_rows", "heavy_threshold", "gw_pixels", "queue_chunk")}
-        tuned["render_ms"] = round(best_ms, 4)
-
-    # ---- warmup + timed region ----
-    for _ in range(args.warmup):
-        step(args.mode)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    plan.reset_stats()
-    launches0 = plan.stats()["host_launches"]
-    plan.timing(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(args.steps):
-        step(args.mode)
-    e1.record()
-    torch.cuda.synchronize()
-    ms_total = e0.elapsed_time(e1)
-    f_ms, nf, b_ms, nb = plan.kernel_ms()
-    plan.timing(False)
-    clk = clocks.stop()
-    st_t = plan.stats()
-    launches = st_t["host_launches"] - launches0
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
-    fwd_ms, bwd_ms = f_ms / max(nf, 1), b_ms / max(nb, 1)
-    value = eval_pairs * world / (ms_step / 1e3)
-    if args.quick:
-        if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": "pairs/s", "ms_per_step": ms_step,
-                              "render_ms_per_frame": {"forward": fwd_ms, "backward": bwd_ms},
-                              "note": "--quick profiling run"}), flush=True)
-        plan.close()
-        return
-
-    # ---- plain pixel-wise 16x16 static grid on the same inputs (render kernels only) ----
-    plan.timing(True)
-    for _ in range(2):
-        step("static")
-    torch.cuda.synchronize()
-    plan.kernel_ms()
-    for _ in range(max(3, args.steps // 2)):
-        step("static")
-    sf_ms, snf, sb_ms, snb = plan.kernel_ms()
-    plan.timing(False)
-    static_fwd, static_bwd = sf_ms / max(snf, 1), sb_ms / max(snb, 1)
-
-    # ---- end to end through the public API with host buffers ----
-    # every step copies its inputs from pinned host memory and reads the loss back
-    h2d = sum(v.numel() * v.element_size() for v in host.values()) + target_h.numel() * target_h.element_size()
-    dbuf = {k: torch.empty_like(v) for k, v in d.items()}
-    tbuf = torch.empty_like(target)
-    loss_h = torch.empty(1, pin_memory=True)
-
-    for _ in range(3):  # same loop as the timed one (first use of torch's reduction kernel included)
-        for k in host:
-            dbuf[k].copy_(host[k], non_blocking=True)
-        tbuf.copy_(target_h, non_blocking=True)
-        _, _, _, _, dL = step("auto", dbuf, tbuf)
-        loss_h.copy_((0.5 * (dL * dL).sum()).reshape(1), non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for k in host:
-            dbuf[k].copy_(host[k], non_blocking=True)
-        tbuf.copy_(target_h, non_blocking=True)
-        _, _, _, _, dL = step("auto", dbuf, tbuf)
-        loss_h.copy_((0.5 * (dL * dL).sum()).reshape(1), non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e_value = eval_pairs * world / e2e_s
-
-    # ---- roofline of the dominant render kernel ----
-    sms = plan.num_sms
-    fp32_rate, ex2_rate = raster.probe_pipe_rates(plan)
-    peaks, peak_src = load_peaks()
-    clk_peak = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-
-    def t_min(fp32_ops, mufu_ops, clk):
-        return max(fp32_ops / (sms * FP32_LANES_PER_SM_CLK * clk), mufu_ops / (sms * ex2_rate * clk))
-
-    fwd_ops = (FWD_EVAL_FP32 * eval_pairs + FWD_ACC_FP32 * contrib_pairs, FWD_EVAL_MUFU * eval_pairs)
-    bwd_ops = (BWD_EVAL_FP32 * bwd_pairs + BWD_ACC_FP32 * contrib_pairs,
-               BWD_EVAL_MUFU * bwd_pairs + BWD_ACC_MUFU * contrib_pairs)
-    dom = "forward" if fwd_ms >= bwd_ms else "backward"
-    ops, dur = (fwd_ops, fwd_ms) if dom == "forward" else (bwd_ops, bwd_ms)
-    tmin = t_min(*ops, clk_peak)
-    achieved = eval_pairs / (dur / 1e3)
-    peak = eval_pairs / tmin
-    clk_meas = (clk.get("sm_mhz") or 0) * 1e6
-    roof = {"bound": "alu", "kernel": f"k_{dom}_balanced", "achieved": achieved / 1e9, "peak": peak / 1e9,
-            "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
-            "model": "max(FP32-pipe ops / (SMs*128*clk), MUFU ops / (SMs*ex2_rate*clk)) at the max SM clock",
-            "peak_source": f"derived from unit counts; SM clock {clk_peak/1e6:.0f} MHz ({peak_src}); "
-                           f"probed ex2 {ex2_rate:.1f}/SM/clk, fp32 {fp32_rate:.1f}/SM/clk",
-            "frac_at_measured_clock": (achieved / (eval_pairs / t_min(*ops, clk_meas))) if clk_meas else None}
-
-    # ---- FP64 CPU oracle on a bounded sample (rank 0, one GPU only) ----
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, desc, _, _ = oracle_sample_run(scene, args.cpu_seconds)
-        cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc}
-
-    line = {
-        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded; stands in for the paper's internal dataset)",
-        "config": {"workload": WORKLOADS.get(args.config, args.config), "gaussians": N, "width": W, "height": H,
-                   "tile": "16x16",
-                   "l2": "working set per step > L2 (sort buffers of K entries), no flush",
-                   "parallelism": "replicas" if world > 1 else "single GPU", "tuned": tuned},
-        "ms_per_frame": ms_step,
-        "render_ms_per_frame": {"forward": fwd_ms, "backward": bwd_ms, "total": fwd_ms + bwd_ms},
-        "pixelwise_static": {"forward_ms": static_fwd, "backward_ms": static_bwd,
-                             "total_ms": static_fwd + static_bwd,
-                             "pairs_per_s_render": eval_pairs / ((static_fwd + static_bwd) / 1e3),
-                             "speedup_render": (static_fwd + static_bwd) / (fwd_ms + bwd_ms)},
-        "frame": {"eval_pairs": eval_pairs, "contrib_pairs": contrib_pairs, "bwd_pairs": bwd_pairs,
-                  "entries": K, "tile_list_max": int(lens.max()), "tile_list_mean": float(lens.mean()),
-                  "tile_list_p99": float(np.percentile(lens, 99))},
-        "roofline": roof,
-        "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4},
-        "gpu_launches": int(launches),
-        "gpu_launches_per_step": int(launches) // args.steps,
-        "gpu_launches_note": "libbgs kernels launched in the timed region, not counting CUB sort/scan kernels",
-        "clocks": clk,
-    }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    plan.close()
+    main_views(args, scene, rank, world, local)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def roofline_obj(dom, eval_pairs, contrib_pairs, bwd_pairs, fwd_ms, bwd_ms, sms, fp32_rate, ex2_rate, clk_meas_mhz):
-    """Roofline of the dominant render kernel (see the module docstring for the op counts)."""
-    peaks, peak_src = load_peaks()
-    clk_peak = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-
-    def t_min(fp32_ops, mufu_ops, clk):
-        return max(fp32_ops / (sms * FP32_LANES_PER_SM_CLK * clk), mufu_ops / (sms * ex2_rate * clk))
-
-    fwd_ops = (FWD_EVAL_FP32 * eval_pairs + FWD_ACC_FP32 * contrib_pairs, FWD_EVAL_MUFU * eval_pairs)
-    bwd_ops = (BWD_EVAL_FP32 * bwd_pairs + BWD_ACC_FP32 * contrib_pairs,
-               BWD_EVAL_MUFU * bwd_pairs + BWD_ACC_MUFU * contrib_pairs)
-    ops, dur = (fwd_ops, fwd_ms) if dom == "forward" else (bwd_ops, bwd_ms)
-    achieved = eval_pairs / (dur / 1e3)
-    peak = eval_pairs / t_min(*ops, clk_peak)
-    clk_meas = (clk_meas_mhz or 0) * 1e6
-    return {"bound": "alu", "kernel": f"k_{dom}_balanced", "achieved": achieved / 1e9, "peak": peak / 1e9,
-            "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
-            "model": "max(FP32-pipe ops / (SMs*128*clk), MUFU ops / (SMs*ex2_rate*clk)) at the max SM clock",
-            "peak_source": f"derived from unit counts; SM clock {clk_peak/1e6:.0f} MHz ({peak_src}); "
-                           f"probed ex2 {ex2_rate:.1f}/SM/clk, fp32 {fp32_rate:.1f}/SM/clk",
-            "frac_at_measured_clock": (achieved / (eval_pairs / t_min(*ops, clk_meas))) if clk_meas else None}
-
-
-def main_batched(args, scene, rank, world, local):
-    """Batched views (one Gaussian set, many cameras): the whole step -- projection of all
-    views, binning without host synchronisation, one persistent forward launch, the L2 loss
-    gradients and one persistent backward launch -- captured once as a CUDA graph and
-    replayed.  pairs = evaluated pairs summed over the views."""
+def main_views(args, scene, rank, world, local):
+    """One step = the whole path for every camera of the workload: projection of all views,
+    binning without host synchronisation, one persistent forward launch, the L2 loss
+    gradients and one persistent backward launch, captured once as a CUDA graph and
+    replayed K times.  pairs = evaluated (pixel, entry) pairs summed over the views."""
     import torch
     from paper_2412_17378_gb300 import raster, scenes
     g, cams = scene["gaussians"], scene["cameras"]
@@ -454,14 +264,17 @@ def main_batched(args, scene, rank, world, local):
     dev = torch.device("cuda", local)
     host = {k: torch.from_numpy(v).pin_memory() for k, v in g.items()}
     d = {k: v.to(dev) for k, v in host.items()}
-    targets_h = [torch.from_numpy(scenes.target_image(4 + v, c["W"], c["H"])).pin_memory() for v, c in enumerate(cams)]
+    seeds = [2] if V == 1 else [4 + v for v in range(V)]
+    targets_h = [torch.from_numpy(scenes.target_image(sd, c["W"], c["H"])).pin_memory() for sd, c in zip(seeds, cams)]
     targets = [t.to(dev) for t in targets_h]
     N = d["means3D"].shape[0]
     plan = raster.Plan(device=local)
     side = torch.cuda.Stream(device=dev)
     state = {}
+    if args.quick:
+        args.no_tune = args.no_cpu_baseline = True
 
-    def step(no_sync=True, mode="auto"):
+    def step(no_sync=True, mode=args.mode):
         pre = raster.preprocess_batched(plan, d["means3D"], d["log_scales"], d["quats"], d["opacities"], cams,
                                         out=state.get("pre"))
         state["pre"] = pre
@@ -486,30 +299,38 @@ def main_batched(args, scene, rank, world, local):
         state["pl"] = torch.empty(int(K * 1.15) + 1024, dtype=torch.int32, device=dev)
         step(no_sync=False)
         pre = state["pre"]
-        best_ms, knobs = raster.autotune_render(plan, pre["means2D"], pre["conic_opacity"], d["colors"],
-                                                pre["depths"], state["pl"], K, state["rg"], cams, outs=state["outs"],
-                                                grads_in=state["gin"], out=state["gr"])
-        tuned = {k: knobs[k] for k in ("pixel_rows", "heavy_threshold", "gw_pixels", "queue_chunk")}
-        tuned["render_ms"] = round(best_ms, 4)
+        # ---- knobs: autotuner (bgs_autotune_render), --knobs, or the plan defaults ----
+        tuned = {}
+        if args.knobs:
+            tuned = dict(apply_knobs(plan, args.knobs), source="--knobs")
+        elif not args.no_tune:
+            best_ms, knobs = raster.autotune_render(plan, pre["means2D"], pre["conic_opacity"], d["colors"],
+                                                    pre["depths"], state["pl"], K, state["rg"], cams,
+                                                    outs=state["outs"], grads_in=state["gin"], out=state["gr"])
+            tuned = {k: knobs[k] for k in ("pixel_rows", "heavy_threshold", "gw_pixels", "queue_chunk")}
+            tuned["render_ms"] = round(best_ms, 4)
+        # ---- frame statistics (evaluated / contributing pairs, backward pairs) ----
         plan.reset_stats()
         l0 = plan.stats()["host_launches"]
-        step(no_sync=False)
+        K = step(no_sync=False)
         st = plan.stats()
         eval_pairs, contrib_pairs = st["eval_pairs"], st["contrib_pairs"]
         launches_per_step = st["host_launches"] - l0
         bwd_pairs = int(sum(o["n_contrib"].sum().item() for o in state["outs"]))
-        # eager timing of the render kernels
+        rgh = state["rg"].cpu().numpy().reshape(-1, 2)
+        lens = rgh[:, 1].astype(np.int64) - rgh[:, 0]
+        # ---- render kernels alone (CUDA events around the persistent launches) ----
         plan.timing(True)
         for _ in range(3):
             step()
         side.synchronize()
         plan.kernel_ms()
-        for _ in range(3):
+        for _ in range(max(3, args.steps // 2)):
             step()
         f_ms, nf, b_ms, nb = plan.kernel_ms()
         plan.timing(False)
         fwd_ms, bwd_ms = f_ms / max(nf, 1), b_ms / max(nb, 1)
-        # capture the step
+        # ---- the timed region: graph replays of the whole step ----
         raster.graph_begin(plan)
         step()
         raster.graph_end(plan)
@@ -517,10 +338,13 @@ def main_batched(args, scene, rank, world, local):
             raster.graph_launch(plan)
         side.synchronize()
         plan.check()
+        if world > 1:
+            torch.distributed.barrier()
         clocks = ClockSampler(local)
         clocks.start()
         time.sleep(0.3)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        side.synchronize()
         e0.record(side)
         for _ in range(args.steps):
             raster.graph_launch(plan)
@@ -529,7 +353,20 @@ def main_batched(args, scene, rank, world, local):
         ms_total = e0.elapsed_time(e1)
         clk = clocks.stop()
         plan.check()
-        # end to end: inputs from pinned host memory, graph replay, loss read back
+        if world > 1:
+            t = torch.tensor([ms_total], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms_total = float(t.item())
+        ms_step = ms_total / args.steps
+        value = eval_pairs * world / (ms_step / 1e3)
+        if args.quick:
+            if rank == 0:
+                print(json.dumps({"metric": METRIC, "value": value, "unit": "pairs/s", "ms_per_step": ms_step,
+                                  "render_ms_per_step": {"forward": fwd_ms, "backward": bwd_ms},
+                                  "tuned": tuned, "note": "--quick profiling run"}), flush=True)
+            plan.close()
+            return
+        # ---- end to end: inputs from pinned host memory, graph replay, loss read back ----
         loss_h = torch.empty(1, pin_memory=True)
         h2d = sum(v.numel() * v.element_size() for v in host.values()) + sum(
             t.numel() * t.element_size() for t in targets_h)
@@ -550,25 +387,61 @@ def main_batched(args, scene, rank, world, local):
         for _ in range(args.steps):
             e2e_step()
         e2e_s = (time.perf_counter() - t0) / args.steps
-    ms_step = ms_total / args.steps
+        # ---- plain pixel-wise 16x16 static grid on the same inputs (single view) ----
+        static = None
+        if V == 1:
+            W, H = cams[0]["W"], cams[0]["H"]
+            pl, rg = state["pl"], state["rg"]
+
+            def static_pass():
+                fw = raster.render_forward(plan, pre["means2D"], pre["conic_opacity"], d["colors"], pre["depths"], pl,
+                                           K, rg, W, H, (16, 16), (0.0, 0.0, 0.0), "static")
+                raster.render_backward(plan, pre["means2D"], pre["conic_opacity"], d["colors"], pre["depths"], pl, K,
+                                       rg, W, H, fw["final_T"], fw["n_contrib"], state["gin"][0]["color"], None, None,
+                                       (16, 16), (0.0, 0.0, 0.0), "static")
+
+            plan.timing(True)
+            for _ in range(2):
+                static_pass()
+            side.synchronize()
+            plan.kernel_ms()
+            for _ in range(max(3, args.steps // 2)):
+                static_pass()
+            sf_ms, snf, sb_ms, snb = plan.kernel_ms()
+            plan.timing(False)
+            sf, sb = sf_ms / max(snf, 1), sb_ms / max(snb, 1)
+            static = {"forward_ms": sf, "backward_ms": sb, "total_ms": sf + sb,
+                      "pairs_per_s_render": eval_pairs / ((sf + sb) / 1e3),
+                      "speedup_render": (sf + sb) / (fwd_ms + bwd_ms)}
     fp32_rate, ex2_rate = raster.probe_pipe_rates(plan)
     dom = "forward" if fwd_ms >= bwd_ms else "backward"
     roof = roofline_obj(dom, eval_pairs, contrib_pairs, bwd_pairs, fwd_ms, bwd_ms, plan.num_sms, fp32_rate, ex2_rate,
                         clk.get("sm_mhz"))
+    # ---- FP64 CPU oracle on a bounded sample (rank 0, one GPU, single view) ----
+    cpu = None
+    if rank == 0 and world == 1 and V == 1 and not args.no_cpu_baseline:
+        rate, cores, desc, _, _ = oracle_sample_run(scene, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc}
     sizes = sorted(set(f"{c['W']}x{c['H']}" for c in cams))
+    config = {"workload": WORKLOADS.get(args.config, f"{V} views ({', '.join(sizes)}) of {N} Gaussians"),
+              "gaussians": N, "views": V, "image": sizes[0] if V == 1 else sizes, "tile": "16x16",
+              "step": "projection, binning, forward, L2 loss gradient, backward; one CUDA graph replay",
+              "l2": "working set per step > L2 (point list and tile histogram), no flush",
+              "parallelism": "replicas" if world > 1 else "single GPU", "tuned": tuned}
     line = {
-        "metric": METRIC, "value": eval_pairs * world / (ms_step / 1e3), "unit": "pairs/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; stands in for the paper's internal dataset)",
-        "config": {"workload": WORKLOADS.get(args.config, f"{V} views ({', '.join(sizes)}) of {N} Gaussians") +
-                               ", one persistent launch per pass, captured CUDA graph", "gaussians": N, "views": V,
-                   "tile": "16x16",
-                   "l2": "working set per step > L2, no flush", "parallelism": "single GPU", "tuned": tuned},
+        "config": config,
         "ms_per_frame": ms_step / V,
         "render_ms_per_step": {"forward": fwd_ms, "backward": bwd_ms, "total": fwd_ms + bwd_ms},
-        "frame": {"eval_pairs": eval_pairs, "contrib_pairs": contrib_pairs, "bwd_pairs": bwd_pairs, "entries": K},
-        "roofline": roof, "cpu_baseline": None,
+        "pixelwise_static": static,
+        "frame": {"eval_pairs": eval_pairs, "contrib_pairs": contrib_pairs, "bwd_pairs": bwd_pairs, "entries": K,
+                  "tile_list_max": int(lens.max()), "tile_list_mean": float(lens.mean()),
+                  "tile_list_p99": float(np.percentile(lens, 99))},
+        "roofline": roof,
+        "cpu_baseline": cpu,
         "e2e": {"value": eval_pairs * world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": 4},
         "gpu_launches": int(launches_per_step * args.steps), "gpu_launches_per_step": int(launches_per_step),
@@ -578,6 +451,30 @@ def main_batched(args, scene, rank, world, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
+
+
+def roofline_obj(dom, eval_pairs, contrib_pairs, bwd_pairs, fwd_ms, bwd_ms, sms, fp32_rate, ex2_rate, clk_meas_mhz):
+    """Roofline of the dominant render kernel (see the module docstring for the op counts)."""
+    peaks, peak_src = load_peaks()
+    clk_peak = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+
+    def t_min(fp32_ops, mufu_ops, clk):
+        return max(fp32_ops / (sms * FP32_LANES_PER_SM_CLK * clk), mufu_ops / (sms * ex2_rate * clk))
+
+    fwd_ops = (FWD_EVAL_FP32 * eval_pairs + FWD_ACC_FP32 * contrib_pairs, FWD_EVAL_MUFU * eval_pairs)
+    bwd_ops = (BWD_EVAL_FP32 * bwd_pairs + BWD_ACC_FP32 * contrib_pairs,
+               BWD_EVAL_MUFU * bwd_pairs + BWD_ACC_MUFU * contrib_pairs)
+    ops, dur = (fwd_ops, fwd_ms) if dom == "forward" else (bwd_ops, bwd_ms)
+    achieved = eval_pairs / (dur / 1e3)
+    peak = eval_pairs / t_min(*ops, clk_peak)
+    clk_meas = (clk_meas_mhz or 0) * 1e6
+    return {"bound": "alu", "kernel": f"k_{dom}_balanced", "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
+            "model": "max(FP32-pipe ops / (SMs*128*clk), MUFU ops / (SMs*ex2_rate*clk)) at the max SM clock",
+            "peak_source": f"derived from unit counts; SM clock {clk_peak/1e6:.0f} MHz ({peak_src}); "
+                           f"probed ex2 {ex2_rate:.1f}/SM/clk, fp32 {fp32_rate:.1f}/SM/clk",
+            "frac_at_measured_clock": (achieved / (eval_pairs / t_min(*ops, clk_meas))) if clk_meas else None}
+
 
 
 if __name__ == "__main__":

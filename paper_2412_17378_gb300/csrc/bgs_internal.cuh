@@ -57,6 +57,13 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// hardware reciprocal approximation (a few ulp; used where the backward recovers T_i)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ void raise_check(DevCtrl *ctrl, unsigned int bit) {
     atomicOr(&ctrl->check_bits, bit);
 }
@@ -231,16 +238,20 @@ cudaError_t launch_ranges(const KeyT *keys, long long K, uint2 *ranges, cudaStre
 
 // counting-sort binning (binning.cu)
 size_t bin_count_smem(int T);
-cudaError_t setup_bin_kernels(size_t smem);
+cudaError_t setup_bin_kernels(int tx, int ty);
+// also writes each sorted position's packed tile rectangle: rect_x = x0 | w << 16,
+// rect_y = y0 | h << 16 (0 when empty)
 cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
-                             int W, int H, int tw, int th, uint32_t *Hm, cudaStream_t s);
+                             int W, int H, int tw, int th, uint32_t *Hm, uint32_t *rect_x, uint32_t *rect_y,
+                             cudaStream_t s);
 cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, uint32_t *total, cudaStream_t s);
 // ranges of one view's tiles, offset by ctrl->bin_base (the view's first point_list slot)
 cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *total, uint2 *ranges, DevCtrl *ctrl,
                               cudaStream_t s);
-cudaError_t launch_bin_scatter(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
-                               int W, int H, int tw, int th, const uint32_t *Hm, const uint32_t *start,
-                               uint32_t *point_list, long long capacity, const DevCtrl *ctrl, cudaStream_t s);
+cudaError_t launch_bin_scatter(long long N, int G, int B, const uint32_t *order, const uint32_t *rect_x,
+                               const uint32_t *rect_y, int W, int H, int tw, int th, const uint32_t *Hm,
+                               const uint32_t *start, uint32_t *point_list, long long capacity, const DevCtrl *ctrl,
+                               cudaStream_t s);
 // bin_base += this view's entry count; num_entries = bin_base; raises BGS_CHECK_OVERFLOW past capacity
 cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *total, long long capacity, DevCtrl *ctrl,
                                cudaStream_t s);

@@ -4,14 +4,20 @@
 // subsequence of that order whose rectangles cover the tile.  The lists are built without
 // materialising and sorting the K duplicated entries:
 //   1. k_bin_count   - the depth order is cut into B blocks of G consecutive Gaussians;
-//                      block b counts, in shared memory, how many of its Gaussians cover
-//                      each tile: H[b][t].
+//                      block b counts how many of its Gaussians cover each tile, H[b][t],
+//                      as a 2D difference array in shared memory (4 updates per
+//                      rectangle) followed by a prefix sum along x then y.  It also stores
+//                      every sorted position's packed rectangle for step 4.
 //   2. k_bin_colscan - exclusive scan of every column of H over b (in place) and the tile
 //                      totals n[t].
 //   3. (CUB) exclusive scan of n -> tile start; k_bin_ranges writes ranges and K.
-//   4. k_bin_scatter - one warp per block walks its Gaussians in depth order and writes
-//                      each one's index at start[t] + H[b][t] + (running count of the tile
-//                      inside the block), for every tile t of its rectangle.
+//   4. k_bin_scatter - block (b, tile row), one warp, the row's write positions
+//                      start[t] + H[b][t] in shared memory.  The warp visits the block's
+//                      Gaussians that cover its row in depth order; lane l appends the
+//                      Gaussian's index to the l-th tile of its x-range.  Blocks run row
+//                      after row in launch order, so the slice of the point list being
+//                      written (a few tile rows) stays resident in L2 while its sectors fill
+//                      up from many blocks.
 // The result is the stable (depth, index) order per tile.  Traffic is O(B T + K) words
 // instead of the ~26 bytes per entry of a two-pass radix sort of (tile, index) pairs.
 #include "bgs_internal.cuh"
@@ -44,32 +50,59 @@ __device__ __forceinline__ void rect_of(const float2 *__restrict__ means2D, cons
 
 __global__ void __launch_bounds__(256) k_bin_count(long long N, int G, const uint32_t *__restrict__ order,
                                                    const float2 *__restrict__ means2D, const int *__restrict__ radii,
-                                                   int tw, int th, int tx, int ty, uint32_t *__restrict__ H) {
-    extern __shared__ uint32_t cnt_s[];
+                                                   int tw, int th, int tx, int ty, uint32_t *__restrict__ H,
+                                                   uint32_t *__restrict__ rect_x, uint32_t *__restrict__ rect_y) {
+    extern __shared__ uint32_t d_s[];
     const int T = tx * ty;
     const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) cnt_s[t] = 0u;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) d_s[t] = 0u;
     __syncthreads();
+    // 2D difference array: +1 at (x0, y0) and (x1, y1), -1 at (x1, y0) and (x0, y1)
+    // (modulo 2^32; the prefix sums below give the exact non-negative counts)
     const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
-    for (long long base = s0 + 32ll * warp; base < s1; base += 32ll * nwarps) {
-        const long long s = base + lane;
-        int x0 = 0, y0 = 0, w = 1, c = 0;
-        if (s < s1) rect_of(means2D, radii, order[s], tw, th, tx, ty, x0, y0, w, c);
-        unsigned pending = __ballot_sync(0xffffffffu, c > 0);
-        while (pending) {
-            const int q = __ffs(pending) - 1;
-            pending &= pending - 1;
-            const int cq = __shfl_sync(0xffffffffu, c, q), wq = __shfl_sync(0xffffffffu, w, q);
-            const int xq = __shfl_sync(0xffffffffu, x0, q), yq = __shfl_sync(0xffffffffu, y0, q);
-            for (int k = lane; k < cq; k += 32) {
-                const int dy = k / wq;
-                atomicAdd(&cnt_s[(yq + dy) * tx + xq + (k - dy * wq)], 1u);
+    for (long long s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        int x0, y0, w, c;
+        rect_of(means2D, radii, order[s], tw, th, tx, ty, x0, y0, w, c);
+        uint32_t px = 0u, py = 0u;  // packed (x0 | w << 16, y0 | h << 16); h = 0 if empty
+        if (c > 0) {
+            const int h = c / w, x1 = x0 + w, y1 = y0 + h;
+            px = (uint32_t)x0 | ((uint32_t)w << 16);
+            py = (uint32_t)y0 | ((uint32_t)h << 16);
+            atomicAdd(&d_s[y0 * tx + x0], 1u);
+            if (x1 < tx) atomicAdd(&d_s[y0 * tx + x1], 0xffffffffu);
+            if (y1 < ty) {
+                atomicAdd(&d_s[y1 * tx + x0], 0xffffffffu);
+                if (x1 < tx) atomicAdd(&d_s[y1 * tx + x1], 1u);
             }
+        }
+        rect_x[s] = px;
+        rect_y[s] = py;
+    }
+    __syncthreads();
+    // prefix along x: one warp per tile row, 32 columns per step
+    for (int y = warp; y < ty; y += nwarps) {
+        uint32_t carry = 0u;
+        for (int xb = 0; xb < tx; xb += 32) {
+            const int x = xb + lane;
+            uint32_t v = x < tx ? d_s[y * tx + x] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (x < tx) d_s[y * tx + x] = v + carry;
+            carry += __shfl_sync(0xffffffffu, v, 31);
         }
     }
     __syncthreads();
+    // prefix along y: one thread per tile column, written straight to H[b]
     uint32_t *row = H + (size_t)b * T;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) row[t] = cnt_s[t];
+    for (int x = threadIdx.x; x < tx; x += blockDim.x) {
+        uint32_t run = 0u;
+        for (int y = 0; y < ty; ++y) {
+            run += d_s[y * tx + x];
+            row[y * tx + x] = run;
+        }
+    }
 }
 
 // Block (32 tiles) x (32 row groups): per column t, exclusive prefix over b in place, and
@@ -135,62 +168,77 @@ __global__ void k_bin_advance(int T, const uint32_t *__restrict__ total, long lo
     }
 }
 
-// One warp per block of the depth order: walks its Gaussians in order and writes each
-// Gaussian index into the lists of the tiles its rectangle covers.
+// Block (b, row): one warp; the row's write positions start[t] + H[b][t] live in shared
+// memory.  Gaussian by Gaussian in depth order, lane l handles the l-th tile of the
+// Gaussian's x-range (32 at a time), so every append is one shared load / store pair.
 __global__ void __launch_bounds__(32) k_bin_scatter(long long N, int G, const uint32_t *__restrict__ order,
-                                                    const float2 *__restrict__ means2D, const int *__restrict__ radii,
-                                                    int tw, int th, int tx, int ty, const uint32_t *__restrict__ H,
-                                                    const uint32_t *__restrict__ start, uint32_t *__restrict__ point_list,
-                                                    long long capacity, const DevCtrl *ctrl) {
+                                                    const uint32_t *__restrict__ rect_x,
+                                                    const uint32_t *__restrict__ rect_y, int tx, int ty,
+                                                    const uint32_t *__restrict__ H, const uint32_t *__restrict__ start,
+                                                    uint32_t *__restrict__ point_list, long long capacity,
+                                                    const DevCtrl *ctrl) {
     extern __shared__ uint32_t pos_s[];
-    const int T = tx * ty;
-    const int b = blockIdx.x, lane = threadIdx.x;
-    const uint32_t *row = H + (size_t)b * T;
+    const int b = blockIdx.x, r = blockIdx.y, lane = threadIdx.x;
+    const size_t t0 = (size_t)r * tx;
+    const uint32_t *hrow = H + (size_t)b * tx * ty + t0;
     const uint32_t base = (uint32_t)ctrl->bin_base;
-    for (int t = lane; t < T; t += 32) pos_s[t] = base + start[t] + row[t];
+    for (int x = lane; x < tx; x += 32) pos_s[x] = base + start[t0 + x] + hrow[x];
     __syncwarp();
     const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
-    for (long long base = s0; base < s1; base += 32) {
-        const long long s = base + lane;
-        uint32_t g = 0;
-        int x0 = 0, y0 = 0, w = 1, c = 0;
-        if (s < s1) {
-            g = order[s];
-            rect_of(means2D, radii, g, tw, th, tx, ty, x0, y0, w, c);
+    // 512 Gaussians per pass: all rectangle / index loads of the pass are issued before any
+    // is used (two dependent rounds instead of one per 32 Gaussians)
+    constexpr int kPre = 16;
+    for (long long cb = s0; cb < s1; cb += 32 * kPre) {
+        uint32_t py[kPre], span[kPre], g[kPre];
+#pragma unroll
+        for (int i = 0; i < kPre; ++i) {
+            const long long s = cb + 32 * i + lane;
+            py[i] = s < s1 ? rect_y[s] : 0u;
         }
-        unsigned pending = __ballot_sync(0xffffffffu, c > 0);
-        while (pending) {  // in depth order: lowest lane first
-            const int q = __ffs(pending) - 1;
-            pending &= pending - 1;
-            const int cq = __shfl_sync(0xffffffffu, c, q), wq = __shfl_sync(0xffffffffu, w, q);
-            const int xq = __shfl_sync(0xffffffffu, x0, q), yq = __shfl_sync(0xffffffffu, y0, q);
-            const uint32_t gq = __shfl_sync(0xffffffffu, g, q);
-            for (int k = lane; k < cq; k += 32) {  // distinct tiles: no two lanes share a counter
-                const int dy = k / wq;
-                const int t = (yq + dy) * tx + xq + (k - dy * wq);
-                const uint32_t p = pos_s[t];
-                pos_s[t] = p + 1u;
-                if ((long long)p < capacity) point_list[p] = gq;
+#pragma unroll
+        for (int i = 0; i < kPre; ++i) {
+            const long long s = cb + 32 * i + lane;
+            const bool on_row = (uint32_t)(r - (int)(py[i] & 0xffffu)) < (py[i] >> 16);  // y0 <= r < y0 + h
+            span[i] = on_row ? rect_x[s] : 0u;  // x0 | w << 16 (w = 0: not on this row)
+            g[i] = on_row ? order[s] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < kPre; ++i) {
+            unsigned m = __ballot_sync(0xffffffffu, (span[i] >> 16) != 0u);
+            while (m) {  // in depth order: lowest lane first
+                const int q = __ffs(m) - 1;
+                m &= m - 1;
+                const uint32_t sp = __shfl_sync(0xffffffffu, span[i], q);
+                const uint32_t gq = __shfl_sync(0xffffffffu, g[i], q);
+                const int x0 = (int)(sp & 0xffffu), w = (int)(sp >> 16);
+                for (int k = lane; k < w; k += 32) {  // distinct tiles: no two lanes share a counter
+                    const uint32_t p = pos_s[x0 + k];
+                    pos_s[x0 + k] = p + 1u;
+                    if ((long long)p < capacity) point_list[p] = gq;
+                }
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
 }
 
 size_t bin_count_smem(int T) { return sizeof(uint32_t) * (size_t)T; }
 
-cudaError_t setup_bin_kernels(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t setup_bin_kernels(int tx, int ty) {
+    const size_t sc = bin_count_smem(tx * ty), ss = sizeof(uint32_t) * (size_t)tx;
+    cudaError_t e = cudaSuccess;
+    if (sc > 48 * 1024) e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+    if (e == cudaSuccess && ss > 48 * 1024)
+        e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     return e;
 }
 
 cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
-                             int W, int H, int tw, int th, uint32_t *Hm, cudaStream_t s) {
+                             int W, int H, int tw, int th, uint32_t *Hm, uint32_t *rect_x, uint32_t *rect_y,
+                             cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
     k_bin_count<<<B, 256, bin_count_smem(tx * ty), s>>>(N, G, order, reinterpret_cast<const float2 *>(means2D), radii,
-                                                         tw, th, tx, ty, Hm);
+                                                         tw, th, tx, ty, Hm, rect_x, rect_y);
     return cudaGetLastError();
 }
 
@@ -212,12 +260,13 @@ cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *tot
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_scatter(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
-                               int W, int H, int tw, int th, const uint32_t *Hm, const uint32_t *start,
-                               uint32_t *point_list, long long capacity, const DevCtrl *ctrl, cudaStream_t s) {
+cudaError_t launch_bin_scatter(long long N, int G, int B, const uint32_t *order, const uint32_t *rect_x,
+                               const uint32_t *rect_y, int W, int H, int tw, int th, const uint32_t *Hm,
+                               const uint32_t *start, uint32_t *point_list, long long capacity, const DevCtrl *ctrl,
+                               cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
-    k_bin_scatter<<<B, 32, bin_count_smem(tx * ty), s>>>(N, G, order, reinterpret_cast<const float2 *>(means2D), radii,
-                                                          tw, th, tx, ty, Hm, start, point_list, capacity, ctrl);
+    k_bin_scatter<<<dim3(B, ty), 32, sizeof(uint32_t) * tx, s>>>(N, G, order, rect_x, rect_y, tx, ty, Hm, start,
+                                                                 point_list, capacity, ctrl);
     return cudaGetLastError();
 }
 

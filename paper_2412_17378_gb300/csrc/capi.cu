@@ -81,7 +81,7 @@ struct bgs_plan {
     unsigned long long host_launches = 0;
     // binning
     Buf touched, touched_sorted, dkey, dkey_sorted, gidx, order, offsets, keys_in, keys_out, vals_in, cub_tmp;
-    Buf bin_h, bin_total, bin_start;  // counting-sort binning
+    Buf bin_h, bin_total, bin_start, bin_rect;  // counting-sort binning
     int smem_optin = 0;
     // render
     Buf recs, tile_key, tile_key2, tile_idx, tile_idx2, counts, item_off, items, grad_acc;
@@ -297,7 +297,7 @@ int bgs_plan_destroy(bgs_plan *p) {
     DeviceGuard g(p->device);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     if (p->graph) cudaGraphDestroy(p->graph);
-    Buf *bufs[] = {&p->dkey64, &p->dkey64_sorted, &p->bin_h, &p->bin_total, &p->bin_start, &p->touched, &p->touched_sorted, &p->dkey,
+    Buf *bufs[] = {&p->dkey64, &p->dkey64_sorted, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_rect, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off, &p->items,
@@ -492,9 +492,11 @@ int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const flo
     BGS_TRY(ensure(p, p->bin_h, sizeof(uint32_t) * B * T, s, "bin_h"));
     BGS_TRY(ensure(p, p->bin_total, sizeof(uint32_t) * T, s, "bin_total"));
     BGS_TRY(ensure(p, p->bin_start, sizeof(uint32_t) * T, s, "bin_start"));
+    BGS_TRY(ensure(p, p->bin_rect, 2 * sizeof(uint32_t) * n, s, "bin_rect"));
     uint32_t *Hm = (uint32_t *)p->bin_h.p, *tot = (uint32_t *)p->bin_total.p, *start = (uint32_t *)p->bin_start.p;
-    if (smem > 48 * 1024) BGS_CUDA(bgs::setup_bin_kernels(smem), "bin smem attribute");
-    BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, s), "bin_count");
+    uint32_t *rect_x = (uint32_t *)p->bin_rect.p, *rect_y = rect_x + n;
+    if (smem > 48 * 1024) BGS_CUDA(bgs::setup_bin_kernels(tiles_x, tiles_y), "bin smem attribute");
+    BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, rect_x, rect_y, s), "bin_count");
     BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, tot, s), "bin_colscan");
     size_t tmp = 0;
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tot, start, (int)T, s), "tile scan (size)");
@@ -502,7 +504,7 @@ int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const flo
     tmp = p->cub_tmp.bytes;
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, tot, start, (int)T, s), "tile scan");
     BGS_CUDA(bgs::launch_bin_ranges((int)T, start, tot, reinterpret_cast<uint2 *>(ranges), p->ctrl, s), "bin_ranges");
-    BGS_CUDA(bgs::launch_bin_scatter(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, start, point_list,
+    BGS_CUDA(bgs::launch_bin_scatter(n, (int)G, (int)B, order, rect_x, rect_y, W, H, tw, th, Hm, start, point_list,
                                      capacity, p->ctrl, s),
              "bin_scatter");
     BGS_CUDA(bgs::launch_bin_advance((int)T, start, tot, flag_overflow ? capacity : (1ll << 62), p->ctrl, s),

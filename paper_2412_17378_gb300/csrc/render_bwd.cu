@@ -63,15 +63,16 @@ __device__ __forceinline__ PixState load_pixel(const BwdArgs &a, int v, int px, 
 // Extra = false: no depth / alpha output gradients (dL/dD = dL/dA = 0), their terms are
 // compiled out.
 template <bool Extra>
-__device__ __forceinline__ bool pair_backward(const Rec &r, float pxf, float pyf, bool active, PixState &s,
+__device__ __forceinline__ bool pair_backward(const Rec &r, const PairX &x, float pyf, bool active, PixState &s,
                                               float v[10]) {
-    float dx, dy, G;
-    const float p2 = pair_power2(r.a, r.b.x, pxf, pyf, dx, dy);
+    float dy, G;
+    const float dx = x.dx;
+    const float p2 = pair_power2_y(x, r.a.y, r.b.x, pyf, dy);
     const float al = pair_alpha(p2, r.b.y, G);
     const bool valid = active && p2 <= 0.f && al >= kAlphaMin;
     if (valid) {
         const float om = 1.f - al;
-        const float io = 1.f / om;
+        const float io = rcp_approx(om);  // om in [0.01, 1]
         s.T = s.T * io;  // T_i
         const float w = al * s.T;
         v[6] += w * s.g0;
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(1024) k_backward_static(BwdArgs a) {
             const Rec r = srec[k];
             const int pos = (int)(top - 1 - k - rg.x);
             float v[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const bool valid = pair_backward<true>(r, pxf, pyf, pos < s.nc, s, v);
+            const bool valid = pair_backward<true>(r, pair_x(r.a, pxf), pyf, pos < s.nc, s, v);
             if (__any_sync(kFullB, valid)) warp_reduce_red10(v, a.grad_acc + 12ull * sidx[k], lane);
         }
     }
@@ -255,22 +256,28 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
     for (uint32_t top = hi; top > rg.x;) {
         const uint32_t lo = top - min(32u, top - rg.x);
         const int cnt = (int)(top - lo);
+        bool hit = false;
         __syncwarp();
         if (lane < cnt) {
             uint32_t g;
-            buf[lane] = load_rec_bwd(a, top - 1 - lane, g);
+            const Rec r = load_rec_bwd(a, top - 1 - lane, g);
+            buf[lane] = r;
             gbuf[lane] = g;
+            hit = !box_misses(r.a, r.b, bcx, bcy, 3.5f, 0.5f * (kItemH - 1));
         }
+        // back to front over the records whose alpha box reaches the pixel block
+        unsigned live = __ballot_sync(kFullB, hit);
         __syncwarp();
-        for (int k = 0; k < cnt; ++k) {
-            const float4 ra = buf[k].a, rb = buf[k].b;
-            if (box_misses(ra, rb, bcx, bcy, 3.5f, 0.5f * (kItemH - 1))) continue;  // warp-uniform
+        while (live) {
+            const int k = __ffs(live) - 1;
+            live &= live - 1;
             const Rec r = buf[k];
             const int pos = (int)(top - 1 - k - rg.x);
+            const PairX px2 = pair_x(r.a, pxf);  // shared by the lane's pixels (same column)
             float v[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool any = false;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) any |= pair_backward<Extra>(r, pxf, pyf[q], pos < s[q].nc, s[q], v);
+            for (int q = 0; q < Q; ++q) any |= pair_backward<Extra>(r, px2, pyf[q], pos < s[q].nc, s[q], v);
             if (__any_sync(kFullB, any)) warp_reduce_red10(v, a.grad_acc + 12ull * gbuf[k], lane);
         }
         top = lo;

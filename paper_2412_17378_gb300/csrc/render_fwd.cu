@@ -212,15 +212,22 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
         for (int q = 0; q < Q; ++q) lane_done = lane_done && done[q];
         if (__all_sync(kFull, lane_done)) break;
         const uint32_t j = base + lane;
+        bool hit = false;
         __syncwarp();
-        if (j < rg.y) buf[lane] = load_rec(a, j);
+        if (j < rg.y) {
+            const Rec r = load_rec(a, j);
+            buf[lane] = r;
+            hit = !box_misses(r.a, r.b, bcx, bcy, 3.5f, 0.5f * (kItemH - 1));
+        }
+        // records whose alpha box reaches the item's pixel block; the others are skipped
+        unsigned live = __ballot_sync(kFull, hit);
         __syncwarp();
-        const int cnt = min(32, (int)(rg.y - base));
         const int pos0 = (int)(base - rg.x);
-        for (int k = 0; k < cnt; ++k) {
+        while (live) {
+            const int k = __ffs(live) - 1;
+            live &= live - 1;
             const float4 ra = buf[k].a;
             const float4 rb = buf[k].b;
-            if (box_misses(ra, rb, bcx, bcy, 3.5f, 0.5f * (kItemH - 1))) continue;  // warp-uniform
             const PairX px2 = pair_x(ra, pxf);  // shared by the lane's pixels (same column)
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
