@@ -169,52 +169,66 @@ __global__ void k_bin_advance(int T, const uint32_t *__restrict__ total, long lo
 }
 
 // Block (b, row): one warp; the row's write positions start[t] + H[b][t] live in shared
-// memory.  Gaussian by Gaussian in depth order, lane l handles the l-th tile of the
-// Gaussian's x-range (32 at a time), so every append is one shared load / store pair.
-__global__ void __launch_bounds__(32) k_bin_scatter(long long N, int G, const uint32_t *__restrict__ order,
+// memory.  The block's Gaussians that cover the row are compacted (depth order kept) 32 at
+// a time into a shared list and visited in order; for each, lane l appends the Gaussian's
+// index to the l-th tile of its x-range.
+__global__ void __launch_bounds__(32) k_bin_scatter(uint32_t N, uint32_t G, const uint32_t *__restrict__ order,
                                                     const uint32_t *__restrict__ rect_x,
                                                     const uint32_t *__restrict__ rect_y, int tx, int ty,
                                                     const uint32_t *__restrict__ H, const uint32_t *__restrict__ start,
-                                                    uint32_t *__restrict__ point_list, long long capacity,
+                                                    uint32_t *__restrict__ point_list, uint32_t capacity,
                                                     const DevCtrl *ctrl) {
     extern __shared__ uint32_t pos_s[];
+    __shared__ uint2 hit_s[32];  // (x0 | w << 16, index) of the group's Gaussians on the row
     const int b = blockIdx.x, r = blockIdx.y, lane = threadIdx.x;
+    const unsigned lt = (1u << lane) - 1u;
     const size_t t0 = (size_t)r * tx;
     const uint32_t *hrow = H + (size_t)b * tx * ty + t0;
     const uint32_t base = (uint32_t)ctrl->bin_base;
     for (int x = lane; x < tx; x += 32) pos_s[x] = base + start[t0 + x] + hrow[x];
     __syncwarp();
-    const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
+    const uint32_t s0 = (uint32_t)b * G, s1 = min(N, s0 + G);
     // 512 Gaussians per pass: all rectangle / index loads of the pass are issued before any
     // is used (two dependent rounds instead of one per 32 Gaussians)
     constexpr int kPre = 16;
-    for (long long cb = s0; cb < s1; cb += 32 * kPre) {
+    for (uint32_t cb = s0; cb < s1; cb += 32 * kPre) {
         uint32_t py[kPre], span[kPre], g[kPre];
 #pragma unroll
         for (int i = 0; i < kPre; ++i) {
-            const long long s = cb + 32 * i + lane;
+            const uint32_t s = cb + 32 * i + lane;
             py[i] = s < s1 ? rect_y[s] : 0u;
         }
 #pragma unroll
         for (int i = 0; i < kPre; ++i) {
-            const long long s = cb + 32 * i + lane;
+            const uint32_t s = cb + 32 * i + lane;
             const bool on_row = (uint32_t)(r - (int)(py[i] & 0xffffu)) < (py[i] >> 16);  // y0 <= r < y0 + h
             span[i] = on_row ? rect_x[s] : 0u;  // x0 | w << 16 (w = 0: not on this row)
             g[i] = on_row ? order[s] : 0u;
         }
-#pragma unroll
         for (int i = 0; i < kPre; ++i) {
-            unsigned m = __ballot_sync(0xffffffffu, (span[i] >> 16) != 0u);
-            while (m) {  // in depth order: lowest lane first
-                const int q = __ffs(m) - 1;
-                m &= m - 1;
-                const uint32_t sp = __shfl_sync(0xffffffffu, span[i], q);
-                const uint32_t gq = __shfl_sync(0xffffffffu, g[i], q);
-                const int x0 = (int)(sp & 0xffffu), w = (int)(sp >> 16);
-                for (int k = lane; k < w; k += 32) {  // distinct tiles: no two lanes share a counter
-                    const uint32_t p = pos_s[x0 + k];
-                    pos_s[x0 + k] = p + 1u;
-                    if ((long long)p < capacity) point_list[p] = gq;
+            const bool hit = (span[i] >> 16) != 0u;
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (m == 0u) continue;
+            if (hit) hit_s[__popc(m & lt)] = make_uint2(span[i], g[i]);
+            __syncwarp();
+            const int nh = __popc(m);
+#pragma unroll 1
+            for (int c = 0; c < nh; ++c) {  // depth order
+                const uint2 e = hit_s[c];
+                const int x0 = (int)(e.x & 0xffffu), w = (int)(e.x >> 16);
+                // distinct tiles: no two lanes share a counter
+                if (lane < w) {
+                    const uint32_t pp = pos_s[x0 + lane];
+                    pos_s[x0 + lane] = pp + 1u;
+                    if (pp < capacity) point_list[pp] = e.y;
+                }
+                if (w > 32) {  // rare: ranges wider than the warp
+#pragma unroll 1
+                    for (int k = lane + 32; k < w; k += 32) {
+                        const uint32_t pp = pos_s[x0 + k];
+                        pos_s[x0 + k] = pp + 1u;
+                        if (pp < capacity) point_list[pp] = e.y;
+                    }
                 }
                 __syncwarp();
             }
@@ -265,8 +279,10 @@ cudaError_t launch_bin_scatter(long long N, int G, int B, const uint32_t *order,
                                const uint32_t *start, uint32_t *point_list, long long capacity, const DevCtrl *ctrl,
                                cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
-    k_bin_scatter<<<dim3(B, ty), 32, sizeof(uint32_t) * tx, s>>>(N, G, order, rect_x, rect_y, tx, ty, Hm, start,
-                                                                 point_list, capacity, ctrl);
+    // indices, sorted positions and list slots are < 2^32 (checked by the callers)
+    const uint32_t cap = capacity >= 0xffffffffll ? 0xffffffffu : (uint32_t)capacity;
+    k_bin_scatter<<<dim3(B, ty), 32, sizeof(uint32_t) * tx, s>>>((uint32_t)N, (uint32_t)G, order, rect_x, rect_y, tx,
+                                                                 ty, Hm, start, point_list, cap, ctrl);
     return cudaGetLastError();
 }
 

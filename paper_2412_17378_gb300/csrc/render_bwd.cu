@@ -14,7 +14,11 @@
 // kept by the forward).  All lanes of a warp visit the same list entry at the same step,
 // so the per-Gaussian contributions of the warp's pixels are summed with shuffles and added
 // to a packed accumulator [N][12] with one red.add instruction (warp-aggregated atomics).
-// A final pass scales and scatters the accumulator into the ABI's gradient arrays.
+// With gp = dL/dpower2 of a pair, the mean and conic gradients of a Gaussian are sums of
+// gp times (dx, dy, dx^2, dx dy, dy^2) combined with the Gaussian's (constant) conic, so a
+// lane only sums gp, gp dy and gp dy^2 over its pixels (which share dx), forms the five
+// moments once, and the conic is applied after the warp sum.  A final pass scales and
+// scatters the accumulator into the ABI's gradient arrays.
 #include "bgs_internal.cuh"
 
 namespace bgs {
@@ -54,78 +58,128 @@ __device__ __forceinline__ PixState load_pixel(const BwdArgs &a, int v, int px, 
     return s;
 }
 
-// One (pixel, entry) step of the backward walk.  Adds the pair's 10 gradient
-// contributions (nothing when the pair is skipped) to v[]:
-//   v0 = dL/dpower (2 qa dx + qb dy), v1 = dL/dpower (2 qc dy + qb dx),
-//   v2 = dL/dpower dx^2, v3 = dL/dpower dx dy, v4 = dL/dpower dy^2,
-//   v5 = dL/do, v6..8 = dL/dc, v9 = dL/d(depth)
-// (power is the natural-log exponent; the final pass applies the ln2 and -1/2 factors).
-// Extra = false: no depth / alpha output gradients (dL/dD = dL/dA = 0), their terms are
-// compiled out.
+// Per-lane sums of one record's pair contributions over the lane's pixels.
+struct PairSums {
+    float g, gy, gyy;  // sum of gp, gp dy, gp dy^2 (gp = dL/dpower2, power2 the log2 exponent)
+    float o;           // sum of G dL/dalpha            (-> dL/dopacity)
+    float c0, c1, c2;  // sum of alpha T dL/dC           (-> dL/dcolour)
+    float d;           // sum of alpha T dL/dD           (-> dL/ddepth)
+};
+
+__device__ __forceinline__ PairSums zero_sums() {
+    PairSums a;
+    a.g = a.gy = a.gyy = a.o = a.c0 = a.c1 = a.c2 = a.d = 0.f;
+    return a;
+}
+
+// One (pixel, entry) step of the backward walk: adds the pair's contributions to a
+// (nothing when the pair is skipped).  dL/dalpha_i = T_i [(c_i - R_i) . dL/dC + (d_i - Rd_i)
+// dL/dD] + T_f / (1 - alpha_i) dL/dA; then R_{i-1} = R_i + alpha_i (c_i - R_i).  Extra =
+// false: no depth / alpha output gradients (dL/dD = dL/dA = 0), their terms are compiled out.
 template <bool Extra>
 __device__ __forceinline__ bool pair_backward(const Rec &r, const PairX &x, float pyf, bool active, PixState &s,
-                                              float v[10]) {
+                                              PairSums &a) {
     float dy, G;
-    const float dx = x.dx;
     const float p2 = pair_power2_y(x, r.a.y, r.b.x, pyf, dy);
     const float al = pair_alpha(p2, r.b.y, G);
     const bool valid = active && p2 <= 0.f && al >= kAlphaMin;
     if (valid) {
         const float om = 1.f - al;
         const float io = rcp_approx(om);  // om in [0.01, 1]
-        s.T = s.T * io;  // T_i
+        s.T = s.T * io;                   // T_i
         const float w = al * s.T;
-        v[6] += w * s.g0;
-        v[7] += w * s.g1;
-        v[8] += w * s.g2;
-        float dLda = s.T * ((r.c.x - s.R0) * s.g0 + (r.c.y - s.R1) * s.g1 + (r.c.z - s.R2) * s.g2);
+        a.c0 += w * s.g0;
+        a.c1 += w * s.g1;
+        a.c2 += w * s.g2;
+        const float d0 = r.c.x - s.R0, d1 = r.c.y - s.R1, d2 = r.c.z - s.R2;
+        float dLda = s.T * (d0 * s.g0 + d1 * s.g1 + d2 * s.g2);
         if (Extra) {
-            v[9] += w * s.gD;
-            dLda += s.T * (r.c.w - s.Rd) * s.gD + s.Tf * io * s.gA;
-            s.Rd = al * r.c.w + om * s.Rd;
+            a.d += w * s.gD;
+            const float dd = r.c.w - s.Rd;
+            dLda += s.T * dd * s.gD + s.Tf * io * s.gA;
+            s.Rd += al * dd;
         }
-        s.R0 = al * r.c.x + om * s.R0;
-        s.R1 = al * r.c.y + om * s.R1;
-        s.R2 = al * r.c.z + om * s.R2;
-        const float o = r.b.y;
-        if (o * G <= kAlphaMax) {
-            const float gp = o * G * dLda;  // dL/dpower
-            v[0] += gp * (2.f * r.a.z * dx + r.a.w * dy);
-            v[1] += gp * (2.f * r.b.x * dy + r.a.w * dx);
-            v[2] += gp * dx * dx;
-            v[3] += gp * dx * dy;
-            v[4] += gp * dy * dy;
-            v[5] += G * dLda;
+        s.R0 += al * d0;
+        s.R1 += al * d1;
+        s.R2 += al * d2;
+        const float oG = r.b.y * G;
+        if (oG <= kAlphaMax) {  // alpha = min(0.99, o G): no gradient through the clamp
+            const float gp = oG * dLda;
+            const float gpy = gp * dy;
+            a.g += gp;
+            a.gy += gpy;
+            a.gyy += gpy * dy;
+            a.o += G * dLda;
         }
     }
     return valid;
 }
 
-// Sums v[0..9] over the warp's 32 lanes and adds the 10 totals to acc[0..9].  Recursive
-// halving (reduce-scatter): at each of 4 stages a lane keeps one half of its remaining
-// values and adds the partner's copy of that half (16 -> 8 -> 4 -> 2 -> 1 values, the
-// vector padded to 16), then one butterfly step completes the sum.  Lane l ends with
-// element (l >> 1) & 15; the even lanes holding elements 0..9 issue one red.add each, all
-// in the same instruction.
-__device__ __forceinline__ void warp_reduce_red10(const float v[10], float *acc, int lane) {
-    float a[16];
+// Sums the lane sums of one record over the warp's 32 lanes and adds them to the record's
+// accumulator row acc[0..9]:
+//   acc0 = sum gp (2 qa dx + qb dy), acc1 = sum gp (2 qc dy + qb dx), acc2..4 = sum gp
+//   (dx^2, dx dy, dy^2), acc5 = sum G dL/dalpha, acc6..8 = colour sums, acc9 = depth sum
+// (qa, qb, qc: the record's pre-scaled conic; dx = mean_x - px is shared by the lane's
+// pixels).  The eight values (sum gp dx, sum gp dy, the three second moments, opacity, two
+// colour channels) are reduced by recursive halving over lane bits 4, 3, 2 (4 + 2 + 1
+// shuffles) and two butterfly steps, leaving element (l >> 2) & 7 in lane l; the third
+// colour channel and the depth sum take one more halving step and four butterflies.  The
+// lanes 0, 4, ..., 28, 1 (and 17) then issue one red.add each, in one instruction.
+template <bool Extra>
+__device__ __forceinline__ void warp_reduce_red(const PairSums &s, float dx, const Rec &r, float *acc, int lane) {
+    const float sdx = dx * s.g;
+    float v[8] = {sdx, s.gy, dx * sdx, dx * s.gy, s.gyy, s.o, s.c0, s.c1};
+    float h4[4], h2[2];
+    {
+        const bool hi = (lane & 16) != 0;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) a[j] = j < 10 ? v[j] : 0.f;
-#pragma unroll
-    for (int stage = 0; stage < 4; ++stage) {
-        const int off = 16 >> stage;  // 16, 8, 4, 2
-        const int half = 8 >> stage;  // 8, 4, 2, 1
-        const bool hi = (lane & off) != 0;
-#pragma unroll
-        for (int j = 0; j < half; ++j) {
-            const float send = hi ? a[j] : a[j + half];
-            const float keep = hi ? a[j + half] : a[j];
-            a[j] = keep + __shfl_xor_sync(kFullB, send, off);
+        for (int j = 0; j < 4; ++j) {
+            const float send = hi ? v[j] : v[j + 4];
+            h4[j] = (hi ? v[j + 4] : v[j]) + __shfl_xor_sync(kFullB, send, 16);
         }
     }
-    const float tot = a[0] + __shfl_xor_sync(kFullB, a[0], 1);
-    const int idx = (lane >> 1) & 15;
-    if ((lane & 1) == 0 && idx < 10 && tot != 0.f) atomicAdd(acc + idx, tot);
+    {
+        const bool hi = (lane & 8) != 0;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float send = hi ? h4[j] : h4[j + 2];
+            h2[j] = (hi ? h4[j + 2] : h4[j]) + __shfl_xor_sync(kFullB, send, 8);
+        }
+    }
+    float t;
+    {
+        const bool hi = (lane & 4) != 0;
+        t = (hi ? h2[1] : h2[0]) + __shfl_xor_sync(kFullB, hi ? h2[0] : h2[1], 4);
+    }
+    t += __shfl_xor_sync(kFullB, t, 2);
+    t += __shfl_xor_sync(kFullB, t, 1);
+    float u;  // colour channel 2 (lanes with bit 4 clear) / depth (bit 4 set) when Extra
+    if (Extra) {
+        const bool hi = (lane & 16) != 0;
+        u = (hi ? s.d : s.c2) + __shfl_xor_sync(kFullB, hi ? s.c2 : s.d, 16);
+    } else {
+        u = s.c2 + __shfl_xor_sync(kFullB, s.c2, 16);
+    }
+    u += __shfl_xor_sync(kFullB, u, 8);
+    u += __shfl_xor_sync(kFullB, u, 4);
+    u += __shfl_xor_sync(kFullB, u, 2);
+    u += __shfl_xor_sync(kFullB, u, 1);
+    // mean terms: lane 0 holds sum gp dx, lane 4 sum gp dy; they swap
+    const float other = __shfl_xor_sync(kFullB, t, 4);
+    const int e = (lane >> 2) & 7;
+    int idx = -1;
+    float val = 0.f;
+    if ((lane & 3) == 0) {
+        idx = e;
+        val = e == 0 ? 2.f * r.a.z * t + r.a.w * other : e == 1 ? 2.f * r.b.x * t + r.a.w * other : t;
+    } else if (lane == 1) {
+        idx = 8;
+        val = u;
+    } else if (Extra && lane == 17) {
+        idx = 9;
+        val = u;
+    }
+    if (idx >= 0 && val != 0.f) atomicAdd(acc + idx, val);
 }
 
 // Record of list entry j and its index g; an index >= N raises BGS_CHECK_INDEX and yields a
@@ -201,9 +255,10 @@ __global__ void __launch_bounds__(1024) k_backward_static(BwdArgs a) {
         for (int k = 0; k < cnt; ++k) {
             const Rec r = srec[k];
             const int pos = (int)(top - 1 - k - rg.x);
-            float v[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const bool valid = pair_backward<true>(r, pair_x(r.a, pxf), pyf, pos < s.nc, s, v);
-            if (__any_sync(kFullB, valid)) warp_reduce_red10(v, a.grad_acc + 12ull * sidx[k], lane);
+            const PairX x = pair_x(r.a, pxf);
+            PairSums sums = zero_sums();
+            const bool valid = pair_backward<true>(r, x, pyf, pos < s.nc, s, sums);
+            if (__any_sync(kFullB, valid)) warp_reduce_red<true>(sums, x.dx, r, a.grad_acc + 12ull * sidx[k], lane);
         }
     }
 }
@@ -274,11 +329,11 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
             const Rec r = buf[k];
             const int pos = (int)(top - 1 - k - rg.x);
             const PairX px2 = pair_x(r.a, pxf);  // shared by the lane's pixels (same column)
-            float v[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            PairSums sums = zero_sums();
             bool any = false;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) any |= pair_backward<Extra>(r, px2, pyf[q], pos < s[q].nc, s[q], v);
-            if (__any_sync(kFullB, any)) warp_reduce_red10(v, a.grad_acc + 12ull * gbuf[k], lane);
+            for (int q = 0; q < Q; ++q) any |= pair_backward<Extra>(r, px2, pyf[q], pos < s[q].nc, s[q], sums);
+            if (__any_sync(kFullB, any)) warp_reduce_red<Extra>(sums, px2.dx, r, a.grad_acc + 12ull * gbuf[k], lane);
         }
         top = lo;
     }
