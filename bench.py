@@ -43,13 +43,19 @@ WORKLOADS = {
 WORKLOAD = WORKLOADS["cfg2"]
 
 # Algorithmic per-pair operation counts of the sequential rule (Algorithm 5 and its
-# derivative), counted at source level as the minimum a kernel must issue:
-#  forward, every evaluated pair: dx, dy (2), power (5), o*G and min (2), two tests (2) = 11
-#          FP32-pipe ops + 1 MUFU ex2; every accumulated pair: 1-alpha, T', test, w, 5 FMA = 9;
-#  backward, every pair before the last contributor: 11 + 1 ex2 (recompute);
-#          every accumulated pair: 45 FP32-pipe ops + 1 MUFU rcp.
-FWD_EVAL_FP32, FWD_EVAL_MUFU, FWD_ACC_FP32 = 11, 1, 9
-BWD_EVAL_FP32, BWD_EVAL_MUFU, BWD_ACC_FP32, BWD_ACC_MUFU = 11, 1, 45, 1
+# derivative), counted at source level for the formulation the kernels implement, as the
+# minimum a kernel must issue (the dx terms of a pixel column -- dx, qa dx^2, qb dx -- are
+# shared by the 4 pixels of a lane: 1 op per pair):
+#  forward, every evaluated pair: shared dx terms (1), dy (1), power (2 FMA), o*G and the
+#          0.99 clamp (2), the power <= 0 and alpha >= 1/255 tests (2) = 8 FP32-pipe ops
+#          + 1 MUFU ex2; every accumulated pair: 1-alpha, T', the T test, w, 5 FMA = 9;
+#  backward, every pair before the last contributor: the forward's 8 + the n_contrib test
+#          = 9, + 1 ex2 (recompute); every accumulated pair: 1-alpha, T/(1-alpha), w,
+#          3 colour FMA, 3 (c - R), dL/dalpha (4), 3 R updates, o G, clamp test, dL/dpower,
+#          its dy product and 4 sums = 24 FP32-pipe ops + 1 MUFU rcp.
+# (The warp reductions and atomics of the backward are aggregation overhead, not counted.)
+FWD_EVAL_FP32, FWD_EVAL_MUFU, FWD_ACC_FP32 = 8, 1, 9
+BWD_EVAL_FP32, BWD_EVAL_MUFU, BWD_ACC_FP32, BWD_ACC_MUFU = 9, 1, 24, 1
 FP32_LANES_PER_SM_CLK = 128
 
 
@@ -140,6 +146,43 @@ class ClockSampler:
         os.unlink(self.path)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), for the oracle's timing line."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def tile_eval_histogram(outs, cams, tile=16):
+    """Per-tile evaluated pairs (sum of n_eval over the tile's pixels), all views: summary
+    statistics and a log2 histogram (bin k counts tiles with 2^k <= pairs < 2^(k+1); bin
+    "0" the empty tiles)."""
+    per = []
+    for o, c in zip(outs, cams):
+        ne = o["n_eval"].double()
+        H, W = ne.shape
+        ty, tx = (H + tile - 1) // tile, (W + tile - 1) // tile
+        pad = ne.new_zeros(ty * tile, tx * tile)
+        pad[:H, :W] = ne
+        per.append(pad.reshape(ty, tile, tx, tile).sum(dim=(1, 3)).reshape(-1).cpu().numpy())
+    per = np.concatenate(per)
+    hist = {}
+    nz = per[per > 0]
+    hist["0"] = int((per == 0).sum())
+    if nz.size:
+        k = np.floor(np.log2(nz)).astype(int)
+        for b in range(int(k.max()) + 1):
+            hist[f"2^{b}"] = int((k == b).sum())
+    return {"tiles": int(per.size), "max": float(per.max()), "mean": float(per.mean()),
+            "p99": float(np.percentile(per, 99)), "max_over_mean": float(per.max() / max(per.mean(), 1e-9)),
+            "log2_hist": hist}
 
 
 def load_peaks():
@@ -319,6 +362,27 @@ def main_views(args, scene, rank, world, local):
         bwd_pairs = int(sum(o["n_contrib"].sum().item() for o in state["outs"]))
         rgh = state["rg"].cpu().numpy().reshape(-1, 2)
         lens = rgh[:, 1].astype(np.int64) - rgh[:, 0]
+        # per-tile evaluated pairs (the imbalance the balanced kernels address)
+        outs_ne = raster.render_forward_batched(plan, pre["means2D"], pre["conic_opacity"], d["colors"],
+                                                pre["depths"], state["pl"], K, state["rg"], cams, n_eval=True)
+        tile_hist = tile_eval_histogram(outs_ne, cams)
+        del outs_ne
+        # ---- binning alone (a2: depth sort + per-tile lists), CUDA events, no host sync ----
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        bin_ms = []
+        for it in range(6):
+            b0.record(side)
+            raster.bin_and_sort_batched(plan, pre["means2D"], pre["radii"], pre["depths"], cams,
+                                        point_list=state["pl"], ranges=state["rg"], no_sync=True)
+            b1.record(side)
+            side.synchronize()
+            if it >= 2:
+                bin_ms.append(b0.elapsed_time(b1))
+        bin_ms = float(np.median(bin_ms))
+        n_tiles = int(rgh.shape[0])
+        # algorithmic bytes: read means2D, radii, depths once (16 B per record), write the
+        # point list (4 B per entry) and the ranges (8 B per tile)
+        bin_bytes = 16 * N * V + 4 * K + 8 * n_tiles
         # ---- render kernels alone (CUDA events around the persistent launches) ----
         plan.timing(True)
         for _ in range(3):
@@ -387,32 +451,41 @@ def main_views(args, scene, rank, world, local):
         for _ in range(args.steps):
             e2e_step()
         e2e_s = (time.perf_counter() - t0) / args.steps
-        # ---- plain pixel-wise 16x16 static grid on the same inputs (single view) ----
-        static = None
-        if V == 1:
-            W, H = cams[0]["W"], cams[0]["H"]
-            pl, rg = state["pl"], state["rg"]
+        # ---- plain pixel-wise 16x16 static grid on the same inputs ----
+        # (single-view kernel: a view at a time, each with its own binning; render kernels
+        # only, summed over the views)
+        sf = sb = 0.0
+        for v, c in enumerate(cams):
+            W, H = c["W"], c["H"]
+            sl = slice(v * N, (v + 1) * N)
+            m2, co, dp = pre["means2D"][sl], pre["conic_opacity"][sl], pre["depths"][sl]
+            if V == 1:
+                pl, rg, Kv = state["pl"], state["rg"], K
+            else:
+                pl, rg, Kv = raster.bin_and_sort(plan, m2, pre["radii"][sl], dp, W, H)
 
             def static_pass():
-                fw = raster.render_forward(plan, pre["means2D"], pre["conic_opacity"], d["colors"], pre["depths"], pl,
-                                           K, rg, W, H, (16, 16), (0.0, 0.0, 0.0), "static")
-                raster.render_backward(plan, pre["means2D"], pre["conic_opacity"], d["colors"], pre["depths"], pl, K,
-                                       rg, W, H, fw["final_T"], fw["n_contrib"], state["gin"][0]["color"], None, None,
-                                       (16, 16), (0.0, 0.0, 0.0), "static")
+                fw = raster.render_forward(plan, m2, co, d["colors"], dp, pl, Kv, rg, W, H, (16, 16),
+                                           (0.0, 0.0, 0.0), "static")
+                raster.render_backward(plan, m2, co, d["colors"], dp, pl, Kv, rg, W, H, fw["final_T"],
+                                       fw["n_contrib"], state["gin"][v]["color"], None, None, (16, 16),
+                                       (0.0, 0.0, 0.0), "static")
 
             plan.timing(True)
-            for _ in range(2):
-                static_pass()
+            static_pass()
             side.synchronize()
             plan.kernel_ms()
-            for _ in range(max(3, args.steps // 2)):
+            reps = max(2, args.steps // 2) if V == 1 else 2
+            for _ in range(reps):
                 static_pass()
             sf_ms, snf, sb_ms, snb = plan.kernel_ms()
             plan.timing(False)
-            sf, sb = sf_ms / max(snf, 1), sb_ms / max(snb, 1)
-            static = {"forward_ms": sf, "backward_ms": sb, "total_ms": sf + sb,
-                      "pairs_per_s_render": eval_pairs / ((sf + sb) / 1e3),
-                      "speedup_render": (sf + sb) / (fwd_ms + bwd_ms)}
+            sf += sf_ms / max(snf, 1)
+            sb += sb_ms / max(snb, 1)
+            del pl, rg
+        static = {"forward_ms": sf, "backward_ms": sb, "total_ms": sf + sb,
+                  "pairs_per_s_render": eval_pairs / ((sf + sb) / 1e3),
+                  "speedup_render": (sf + sb) / (fwd_ms + bwd_ms)}
     fp32_rate, ex2_rate = raster.probe_pipe_rates(plan)
     dom = "forward" if fwd_ms >= bwd_ms else "backward"
     roof = roofline_obj(dom, eval_pairs, contrib_pairs, bwd_pairs, fwd_ms, bwd_ms, plan.num_sms, fp32_rate, ex2_rate,
@@ -421,7 +494,14 @@ def main_views(args, scene, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and V == 1 and not args.no_cpu_baseline:
         rate, cores, desc, _, _ = oracle_sample_run(scene, args.cpu_seconds)
-        cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc}
+        cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc,
+               "cpu_model": cpu_model()}
+    peaks, _ = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    binning = {"ms": bin_ms, "algorithmic_bytes": int(bin_bytes), "GB_s": bin_bytes / (bin_ms / 1e3) / 1e9,
+               "hbm_peak_GB_s": hbm, "frac_of_hbm": bin_bytes / (bin_ms / 1e3) / 1e9 / hbm,
+               "note": "depth sort + counting-sort binning of K entries; algorithmic bytes = 16 B per "
+                       "projected record read + 4 B per entry + 8 B per tile written"}
     sizes = sorted(set(f"{c['W']}x{c['H']}" for c in cams))
     config = {"workload": WORKLOADS.get(args.config, f"{V} views ({', '.join(sizes)}) of {N} Gaussians"),
               "gaussians": N, "views": V, "image": sizes[0] if V == 1 else sizes, "tile": "16x16",
@@ -439,7 +519,8 @@ def main_views(args, scene, rank, world, local):
         "pixelwise_static": static,
         "frame": {"eval_pairs": eval_pairs, "contrib_pairs": contrib_pairs, "bwd_pairs": bwd_pairs, "entries": K,
                   "tile_list_max": int(lens.max()), "tile_list_mean": float(lens.mean()),
-                  "tile_list_p99": float(np.percentile(lens, 99))},
+                  "tile_list_p99": float(np.percentile(lens, 99)), "tile_eval_pairs": tile_hist},
+        "binning": binning,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": eval_pairs * world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
