@@ -7,22 +7,25 @@
 //                      block b counts how many of its Gaussians cover each tile, H[b][t],
 //                      as a 2D difference array in shared memory (4 updates per
 //                      rectangle) followed by a prefix sum along x then y.  It also stores
-//                      every sorted position's packed rectangle for step 4.
+//                      every sorted position's packed rectangle and, per group of 8 x 4
+//                      tiles C, a bit mask of the block's Gaussians whose rectangle meets C.
 //   2. k_bin_colscan - exclusive scan of every column of H over b (in place) and the tile
 //                      totals n[t].
 //   3. (CUB) exclusive scan of n -> tile start; k_bin_ranges writes ranges and K.
-//   4. k_bin_scatter - block (b, tile row), one warp, the row's write positions
-//                      start[t] + H[b][t] in shared memory.  The warp visits the block's
-//                      Gaussians that cover its row in depth order; lane l appends the
-//                      Gaussian's index to the l-th tile of its x-range.  Blocks run row
-//                      after row in launch order, so the slice of the point list being
-//                      written (a few tile rows) stays resident in L2 while its sectors fill
-//                      up from many blocks.
+//   4. k_bin_scatter - block (b, C), one warp, lane l owns tile l of C and keeps its write
+//                      position start[t] + H[b][t] in a register.  The warp visits the
+//                      Gaussians flagged in the (b, C) mask in depth order; every lane whose
+//                      tile the rectangle covers appends the Gaussian's index.  A lane stages
+//                      its appends in a 16-word ring in shared memory and writes each
+//                      completed 32-byte sector of its run with two 16-byte stores, so the
+//                      point list is written in whole sectors (not one word per request).
 // The result is the stable (depth, index) order per tile.  Traffic is O(B T + K) words
 // instead of the ~26 bytes per entry of a two-pass radix sort of (tile, index) pairs.
 #include "bgs_internal.cuh"
 
 namespace bgs {
+
+constexpr int kCbW = 8, kCbH = 4;  // tile group of one scatter warp (a tile per lane)
 
 __device__ __forceinline__ void rect_of(const float2 *__restrict__ means2D, const int *__restrict__ radii, uint32_t g,
                                         int tw, int th, int tx, int ty, int &x0, int &y0, int &w, int &cnt) {
@@ -51,34 +54,52 @@ __device__ __forceinline__ void rect_of(const float2 *__restrict__ means2D, cons
 __global__ void __launch_bounds__(256) k_bin_count(long long N, int G, const uint32_t *__restrict__ order,
                                                    const float2 *__restrict__ means2D, const int *__restrict__ radii,
                                                    int tw, int th, int tx, int ty, uint32_t *__restrict__ H,
-                                                   uint32_t *__restrict__ rect_x, uint32_t *__restrict__ rect_y) {
-    extern __shared__ uint32_t d_s[];
+                                                   uint32_t *__restrict__ rect_x, uint32_t *__restrict__ rect_y,
+                                                   uint32_t *__restrict__ masks, int W32) {
+    extern __shared__ uint32_t d_s[];  // [T] tile counters, then [nC][16] mask words
     const int T = tx * ty;
+    const int ncx = (tx + kCbW - 1) / kCbW, nC = ncx * ((ty + kCbH - 1) / kCbH);
+    uint32_t *m_s = d_s + T;
     const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) d_s[t] = 0u;
+    for (int t = threadIdx.x; t < T + 16 * nC; t += blockDim.x) d_s[t] = 0u;
     __syncthreads();
-    // 2D difference array: +1 at (x0, y0) and (x1, y1), -1 at (x1, y0) and (x0, y1)
-    // (modulo 2^32; the prefix sums below give the exact non-negative counts)
     const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
-    for (long long s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-        int x0, y0, w, c;
-        rect_of(means2D, radii, order[s], tw, th, tx, ty, x0, y0, w, c);
-        uint32_t px = 0u, py = 0u;  // packed (x0 | w << 16, y0 | h << 16); h = 0 if empty
-        if (c > 0) {
-            const int h = c / w, x1 = x0 + w, y1 = y0 + h;
-            px = (uint32_t)x0 | ((uint32_t)w << 16);
-            py = (uint32_t)y0 | ((uint32_t)h << 16);
-            atomicAdd(&d_s[y0 * tx + x0], 1u);
-            if (x1 < tx) atomicAdd(&d_s[y0 * tx + x1], 0xffffffffu);
-            if (y1 < ty) {
-                atomicAdd(&d_s[y1 * tx + x0], 0xffffffffu);
-                if (x1 < tx) atomicAdd(&d_s[y1 * tx + x1], 1u);
+    // 512 Gaussians (16 mask words per C) at a time
+    for (int sub = 0; sub < W32 / 16; ++sub) {
+        const long long c0 = s0 + 512ll * sub, c1 = min(s1, c0 + 512);
+        for (long long s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
+            int x0, y0, w, c;
+            rect_of(means2D, radii, order[s], tw, th, tx, ty, x0, y0, w, c);
+            uint32_t px = 0u, py = 0u;  // packed (x0 | w << 16, y0 | h << 16); h = 0 if empty
+            if (c > 0) {
+                const int h = c / w, x1 = x0 + w, y1 = y0 + h;
+                px = (uint32_t)x0 | ((uint32_t)w << 16);
+                py = (uint32_t)y0 | ((uint32_t)h << 16);
+                // 2D difference array: +1 at (x0, y0) and (x1, y1), -1 at (x1, y0) and
+                // (x0, y1) (modulo 2^32; the prefix sums below give the exact counts)
+                atomicAdd(&d_s[y0 * tx + x0], 1u);
+                if (x1 < tx) atomicAdd(&d_s[y0 * tx + x1], 0xffffffffu);
+                if (y1 < ty) {
+                    atomicAdd(&d_s[y1 * tx + x0], 0xffffffffu);
+                    if (x1 < tx) atomicAdd(&d_s[y1 * tx + x1], 1u);
+                }
+                const int li = (int)(s - c0);
+                const uint32_t bit = 1u << (li & 31);
+                for (int cy = y0 / kCbH; cy <= (y1 - 1) / kCbH; ++cy)
+                    for (int cx = x0 / kCbW; cx <= (x1 - 1) / kCbW; ++cx)
+                        atomicOr(&m_s[(cy * ncx + cx) * 16 + (li >> 5)], bit);
             }
+            rect_x[s] = px;
+            rect_y[s] = py;
         }
-        rect_x[s] = px;
-        rect_y[s] = py;
+        __syncthreads();
+        // the sub-block's mask words: (b, C) words [16 sub, 16 sub + 16)
+        for (int k = threadIdx.x; k < 16 * nC; k += blockDim.x) {
+            masks[((size_t)b * nC + (k >> 4)) * W32 + 16 * sub + (k & 15)] = m_s[k];
+            m_s[k] = 0u;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     // prefix along x: one warp per tile row, 32 columns per step
     for (int y = warp; y < ty; y += nwarps) {
         uint32_t carry = 0u;
@@ -168,91 +189,126 @@ __global__ void k_bin_advance(int T, const uint32_t *__restrict__ total, long lo
     }
 }
 
-// Block (b, row): one warp; the row's write positions start[t] + H[b][t] live in shared
-// memory.  The block's Gaussians that cover the row are compacted (depth order kept) 32 at
-// a time into a shared list and visited in order; for each, lane l appends the Gaussian's
-// index to the l-th tile of its x-range.
-__global__ void __launch_bounds__(32) k_bin_scatter(uint32_t N, uint32_t G, const uint32_t *__restrict__ order,
-                                                    const uint32_t *__restrict__ rect_x,
-                                                    const uint32_t *__restrict__ rect_y, int tx, int ty,
-                                                    const uint32_t *__restrict__ H, const uint32_t *__restrict__ start,
-                                                    uint32_t *__restrict__ point_list, uint32_t capacity,
-                                                    const DevCtrl *ctrl) {
-    extern __shared__ uint32_t pos_s[];
-    __shared__ uint2 hit_s[32];  // (x0 | w << 16, index) of the group's Gaussians on the row
-    const int b = blockIdx.x, r = blockIdx.y, lane = threadIdx.x;
-    const unsigned lt = (1u << lane) - 1u;
-    const size_t t0 = (size_t)r * tx;
-    const uint32_t *hrow = H + (size_t)b * tx * ty + t0;
-    const uint32_t base = (uint32_t)ctrl->bin_base;
-    for (int x = lane; x < tx; x += 32) pos_s[x] = base + start[t0 + x] + hrow[x];
-    __syncwarp();
-    const uint32_t s0 = (uint32_t)b * G, s1 = min(N, s0 + G);
-    // 512 Gaussians per pass: all rectangle / index loads of the pass are issued before any
-    // is used (two dependent rounds instead of one per 32 Gaussians)
-    constexpr int kPre = 16;
-    for (uint32_t cb = s0; cb < s1; cb += 32 * kPre) {
-        uint32_t py[kPre], span[kPre], g[kPre];
+// Writes the completed sector [done, done + 8) of a lane's run from its ring (words below
+// run0 belong to the previous block's run of the tile and are left alone).
+__device__ __forceinline__ void flush_sector(const uint32_t *ring, int rot, uint32_t done, uint32_t run0,
+                                             uint32_t *__restrict__ point_list, uint32_t capacity, bool vec_ok) {
+    uint32_t v[8];
 #pragma unroll
-        for (int i = 0; i < kPre; ++i) {
-            const uint32_t s = cb + 32 * i + lane;
-            py[i] = s < s1 ? rect_y[s] : 0u;
-        }
+    for (int j = 0; j < 8; ++j) v[j] = ring[(done + j + rot) & 15u];
+    if (vec_ok && done >= run0 && done + 8u <= capacity) {
+        uint4 *dst = reinterpret_cast<uint4 *>(point_list + done);  // 32-byte aligned
+        dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_uint4(v[4], v[5], v[6], v[7]);
+    } else {
 #pragma unroll
-        for (int i = 0; i < kPre; ++i) {
-            const uint32_t s = cb + 32 * i + lane;
-            const bool on_row = (uint32_t)(r - (int)(py[i] & 0xffffu)) < (py[i] >> 16);  // y0 <= r < y0 + h
-            span[i] = on_row ? rect_x[s] : 0u;  // x0 | w << 16 (w = 0: not on this row)
-            g[i] = on_row ? order[s] : 0u;
-        }
-        for (int i = 0; i < kPre; ++i) {
-            const bool hit = (span[i] >> 16) != 0u;
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (m == 0u) continue;
-            if (hit) hit_s[__popc(m & lt)] = make_uint2(span[i], g[i]);
-            __syncwarp();
-            const int nh = __popc(m);
-#pragma unroll 1
-            for (int c = 0; c < nh; ++c) {  // depth order
-                const uint2 e = hit_s[c];
-                const int x0 = (int)(e.x & 0xffffu), w = (int)(e.x >> 16);
-                // distinct tiles: no two lanes share a counter
-                if (lane < w) {
-                    const uint32_t pp = pos_s[x0 + lane];
-                    pos_s[x0 + lane] = pp + 1u;
-                    if (pp < capacity) point_list[pp] = e.y;
-                }
-                if (w > 32) {  // rare: ranges wider than the warp
-#pragma unroll 1
-                    for (int k = lane + 32; k < w; k += 32) {
-                        const uint32_t pp = pos_s[x0 + k];
-                        pos_s[x0 + k] = pp + 1u;
-                        if (pp < capacity) point_list[pp] = e.y;
-                    }
-                }
-                __syncwarp();
-            }
-        }
+        for (int j = 0; j < 8; ++j)
+            if (done + j >= run0 && done + j < capacity) point_list[done + j] = v[j];
     }
 }
 
-size_t bin_count_smem(int T) { return sizeof(uint32_t) * (size_t)T; }
+// Block (b, cx, cy): one warp, lane l owns tile (8 cx + l % 8, 4 cy + l / 8) of the group.
+__global__ void __launch_bounds__(32) k_bin_scatter(uint32_t N, uint32_t G, int W32, const uint32_t *__restrict__ order,
+                                                    const uint32_t *__restrict__ rect_x,
+                                                    const uint32_t *__restrict__ rect_y, int tx, int ty,
+                                                    const uint32_t *__restrict__ H, const uint32_t *__restrict__ start,
+                                                    const uint32_t *__restrict__ masks,
+                                                    uint32_t *__restrict__ point_list, uint32_t capacity, int vec_ok,
+                                                    const DevCtrl *ctrl) {
+    __shared__ uint32_t idx_s[512];  // sorted positions of the pass's flagged Gaussians
+    __shared__ uint2 hit_s[512];     // (lanes whose tile the rectangle covers, Gaussian index)
+    __shared__ uint32_t ring_s[32 * 16];
+    const int b = blockIdx.x, cx = blockIdx.y, cy = blockIdx.z, lane = threadIdx.x;
+    const int gx0 = cx * kCbW, gy0 = cy * kCbH;
+    const int ltx = gx0 + (lane % kCbW), lty = gy0 + (lane / kCbW);
+    const bool own = ltx < tx && lty < ty;
+    const unsigned own_mask = __ballot_sync(0xffffffffu, own);
+    const size_t t = (size_t)lty * tx + ltx;
+    const uint32_t base = (uint32_t)ctrl->bin_base;
+    uint32_t pos = own ? base + start[t] + H[(size_t)b * tx * ty + t] : 0u;
+    const uint32_t run0 = pos;
+    uint32_t done = pos & ~7u;  // positions below done are written (or precede the run)
+    uint32_t *ring = ring_s + 16 * lane;
+    const int rot = lane >> 1;  // ring rotation: lanes appending at one slot hit distinct banks
+    const int nC = ((tx + kCbW - 1) / kCbW) * ((ty + kCbH - 1) / kCbH);
+    const uint32_t *mk = masks + ((size_t)b * nC + cy * ((tx + kCbW - 1) / kCbW) + cx) * W32;
+    const uint32_t s0 = (uint32_t)b * G;
+    for (int wb = 0; wb < W32; wb += 16) {  // 512 Gaussians per pass
+        uint32_t word = lane < 16 ? mk[wb + lane] : 0u;
+        const uint32_t cnt = (uint32_t)__popc(word);
+        uint32_t incl = cnt;
+        for (int o = 1; o < 16; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const int total = (int)__shfl_sync(0xffffffffu, incl, 15);
+        if (total == 0) continue;
+        // compact the flagged positions in depth order (word by word, bit by bit)
+        uint32_t off = incl - cnt;
+        while (word) {
+            const int bit = __ffs(word) - 1;
+            word &= word - 1u;
+            idx_s[off++] = s0 + 32u * (uint32_t)(wb + lane) + (uint32_t)bit;
+        }
+        __syncwarp();
+        // per flagged Gaussian: the lanes whose tile its rectangle covers (a nonempty
+        // rectangle meeting the group: the masks flag no other)
+        for (int k = lane; k < total; k += 32) {
+            const uint32_t s = idx_s[k];
+            const uint32_t px = rect_x[s], py = rect_y[s];
+            const int x0 = (int)(px & 0xffffu) - gx0, x1 = x0 + (int)(px >> 16);
+            const int y0 = (int)(py & 0xffffu) - gy0, y1 = y0 + (int)(py >> 16);
+            const uint32_t lx0 = (uint32_t)max(x0, 0), lx1 = (uint32_t)min(x1, kCbW);
+            const uint32_t ly0 = (uint32_t)max(y0, 0), ly1 = (uint32_t)min(y1, kCbH);
+            const uint32_t cols = ((1u << lx1) - 1u) ^ ((1u << lx0) - 1u);
+            const uint32_t rows = (ly1 >= 4u ? 0xffffffffu : (1u << (8u * ly1)) - 1u) ^ ((1u << (8u * ly0)) - 1u);
+            hit_s[k] = make_uint2(rows & (cols * 0x01010101u) & own_mask, order[s]);
+        }
+        __syncwarp();
+        for (int k0 = 0; k0 < total; k0 += 8) {  // depth order, 8 visits at a time
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (k0 + j < total) {
+                    const uint2 e = hit_s[k0 + j];
+                    if ((e.x >> lane) & 1u) {
+                        ring[(pos + rot) & 15u] = e.y;
+                        ++pos;
+                    }
+                }
+            }
+            // at most 8 appends since the last check: at most one newly completed sector,
+            // and no ring slot overwritten before it is written out
+            if (done + 8u <= pos) {
+                flush_sector(ring, rot, done, run0, point_list, capacity, vec_ok != 0);
+                done += 8u;
+            }
+        }
+        __syncwarp();
+    }
+    // the last, partial sector
+    for (uint32_t p = done; p < pos; ++p)
+        if (p >= run0 && p < capacity) point_list[p] = ring[(p + rot) & 15u];
+}
+
+size_t bin_count_smem(int tx, int ty) {
+    const size_t nC = (size_t)((tx + kCbW - 1) / kCbW) * ((ty + kCbH - 1) / kCbH);
+    return sizeof(uint32_t) * ((size_t)tx * ty + 16 * nC);
+}
+
+int bin_mask_groups(int tx, int ty) { return ((tx + kCbW - 1) / kCbW) * ((ty + kCbH - 1) / kCbH); }
 
 cudaError_t setup_bin_kernels(int tx, int ty) {
-    const size_t sc = bin_count_smem(tx * ty), ss = sizeof(uint32_t) * (size_t)tx;
-    cudaError_t e = cudaSuccess;
-    if (sc > 48 * 1024) e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
-    if (e == cudaSuccess && ss > 48 * 1024)
-        e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    return e;
+    const size_t sc = bin_count_smem(tx, ty);
+    if (sc <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
 }
 
 cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
                              int W, int H, int tw, int th, uint32_t *Hm, uint32_t *rect_x, uint32_t *rect_y,
-                             cudaStream_t s) {
+                             uint32_t *masks, int W32, cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
-    k_bin_count<<<B, 256, bin_count_smem(tx * ty), s>>>(N, G, order, reinterpret_cast<const float2 *>(means2D), radii,
-                                                         tw, th, tx, ty, Hm, rect_x, rect_y);
+    k_bin_count<<<B, 256, bin_count_smem(tx, ty), s>>>(N, G, order, reinterpret_cast<const float2 *>(means2D), radii,
+                                                        tw, th, tx, ty, Hm, rect_x, rect_y, masks, W32);
     return cudaGetLastError();
 }
 
@@ -274,15 +330,17 @@ cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *tot
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_scatter(long long N, int G, int B, const uint32_t *order, const uint32_t *rect_x,
+cudaError_t launch_bin_scatter(long long N, int G, int B, int W32, const uint32_t *order, const uint32_t *rect_x,
                                const uint32_t *rect_y, int W, int H, int tw, int th, const uint32_t *Hm,
-                               const uint32_t *start, uint32_t *point_list, long long capacity, const DevCtrl *ctrl,
-                               cudaStream_t s) {
+                               const uint32_t *start, const uint32_t *masks, uint32_t *point_list, long long capacity,
+                               const DevCtrl *ctrl, cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
     // indices, sorted positions and list slots are < 2^32 (checked by the callers)
     const uint32_t cap = capacity >= 0xffffffffll ? 0xffffffffu : (uint32_t)capacity;
-    k_bin_scatter<<<dim3(B, ty), 32, sizeof(uint32_t) * tx, s>>>((uint32_t)N, (uint32_t)G, order, rect_x, rect_y, tx,
-                                                                 ty, Hm, start, point_list, cap, ctrl);
+    const int vec_ok = (reinterpret_cast<uintptr_t>(point_list) & 31u) == 0u;
+    const dim3 grid(B, (tx + kCbW - 1) / kCbW, (ty + kCbH - 1) / kCbH);
+    k_bin_scatter<<<grid, 32, 0, s>>>((uint32_t)N, (uint32_t)G, W32, order, rect_x, rect_y, tx, ty, Hm, start, masks,
+                                      point_list, cap, vec_ok, ctrl);
     return cudaGetLastError();
 }
 

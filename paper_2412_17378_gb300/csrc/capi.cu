@@ -81,7 +81,7 @@ struct bgs_plan {
     unsigned long long host_launches = 0;
     // binning
     Buf touched, touched_sorted, dkey, dkey_sorted, gidx, order, offsets, keys_in, keys_out, vals_in, cub_tmp;
-    Buf bin_h, bin_total, bin_start, bin_rect;  // counting-sort binning
+    Buf bin_h, bin_total, bin_start, bin_rect, bin_mask;  // counting-sort binning
     int smem_optin = 0;
     // render
     Buf recs, tile_key, tile_key2, tile_idx, tile_idx2, counts, item_off, items, grad_acc;
@@ -297,7 +297,7 @@ int bgs_plan_destroy(bgs_plan *p) {
     DeviceGuard g(p->device);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     if (p->graph) cudaGraphDestroy(p->graph);
-    Buf *bufs[] = {&p->dkey64, &p->dkey64_sorted, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_rect, &p->touched, &p->touched_sorted, &p->dkey,
+    Buf *bufs[] = {&p->dkey64, &p->dkey64_sorted, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_rect, &p->bin_mask, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off, &p->items,
@@ -484,19 +484,26 @@ int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const flo
                       bool flag_overflow, cudaStream_t s) {
     const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
     const long long T = (long long)tiles_x * tiles_y;
-    const size_t smem = bgs::bin_count_smem((int)T);
+    const size_t smem = bgs::bin_count_smem(tiles_x, tiles_y);
     if (smem > (size_t)p->smem_optin) return fail(BGS_ERR_INVALID, "tile grid too large for counting-sort binning");
-    const long long G = std::max<long long>(512, (n * T + (1ll << 24) - 1) >> 24);
+    // G: a multiple of 32, at least 2048, and large enough that B T stays below 2^24
+    long long G = std::max<long long>(2048, (n * T + (1ll << 24) - 1) >> 24);
+    G = (G + 31) & ~31ll;
     const long long B = std::max<long long>(1, (n + G - 1) / G);
-    if (B * T >= (1ll << 31)) return fail(BGS_ERR_INVALID, "tile histogram too large");
+    const long long W32 = ((G + 511) / 512) * 16;  // mask words per (block, tile group)
+    const long long nC = bgs::bin_mask_groups(tiles_x, tiles_y);
+    if (B * T >= (1ll << 31) || B * nC * W32 >= (1ll << 40)) return fail(BGS_ERR_INVALID, "tile histogram too large");
     BGS_TRY(ensure(p, p->bin_h, sizeof(uint32_t) * B * T, s, "bin_h"));
     BGS_TRY(ensure(p, p->bin_total, sizeof(uint32_t) * T, s, "bin_total"));
     BGS_TRY(ensure(p, p->bin_start, sizeof(uint32_t) * T, s, "bin_start"));
     BGS_TRY(ensure(p, p->bin_rect, 2 * sizeof(uint32_t) * n, s, "bin_rect"));
+    BGS_TRY(ensure(p, p->bin_mask, sizeof(uint32_t) * B * nC * W32, s, "bin_mask"));
     uint32_t *Hm = (uint32_t *)p->bin_h.p, *tot = (uint32_t *)p->bin_total.p, *start = (uint32_t *)p->bin_start.p;
-    uint32_t *rect_x = (uint32_t *)p->bin_rect.p, *rect_y = rect_x + n;
+    uint32_t *rect_x = (uint32_t *)p->bin_rect.p, *rect_y = rect_x + n, *masks = (uint32_t *)p->bin_mask.p;
     if (smem > 48 * 1024) BGS_CUDA(bgs::setup_bin_kernels(tiles_x, tiles_y), "bin smem attribute");
-    BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, rect_x, rect_y, s), "bin_count");
+    BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, rect_x, rect_y, masks,
+                                   (int)W32, s),
+             "bin_count");
     BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, tot, s), "bin_colscan");
     size_t tmp = 0;
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tot, start, (int)T, s), "tile scan (size)");
@@ -504,8 +511,8 @@ int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const flo
     tmp = p->cub_tmp.bytes;
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, tot, start, (int)T, s), "tile scan");
     BGS_CUDA(bgs::launch_bin_ranges((int)T, start, tot, reinterpret_cast<uint2 *>(ranges), p->ctrl, s), "bin_ranges");
-    BGS_CUDA(bgs::launch_bin_scatter(n, (int)G, (int)B, order, rect_x, rect_y, W, H, tw, th, Hm, start, point_list,
-                                     capacity, p->ctrl, s),
+    BGS_CUDA(bgs::launch_bin_scatter(n, (int)G, (int)B, (int)W32, order, rect_x, rect_y, W, H, tw, th, Hm, start, masks,
+                                     point_list, capacity, p->ctrl, s),
              "bin_scatter");
     BGS_CUDA(bgs::launch_bin_advance((int)T, start, tot, flag_overflow ? capacity : (1ll << 62), p->ctrl, s),
              "bin_advance");
@@ -583,7 +590,7 @@ int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t
     BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, dkey, dkey2, gidx, order, (int64_t)N, 0, 32, s),
              "depth sort");
     // (2) counting sort over tile rectangles when the per-tile counters fit in shared memory
-    if (bgs::bin_count_smem((int)T) <= (size_t)p->smem_optin) {
+    if (bgs::bin_count_smem(tiles_x, tiles_y) <= (size_t)p->smem_optin) {
         BGS_CUDA(cudaMemsetAsync(&p->ctrl->bin_base, 0, sizeof(unsigned long long), s), "clear bin base");
         BGS_TRY(bin_view_counting(p, N, order, means2D, radii, W, H, tw, th, point_list, capacity, ranges, false, s));
         unsigned long long K = 0;
@@ -874,7 +881,7 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
     bgs::ViewTable vt;
     BGS_TRY(make_view_table(V, Ws, Hs, tw, th, vt));
     for (int v = 0; v < V; ++v)
-        if (bgs::bin_count_smem(vt.tiles_x[v] * vt.tiles_y[v]) > (size_t)p->smem_optin)
+        if (bgs::bin_count_smem(vt.tiles_x[v], vt.tiles_y[v]) > (size_t)p->smem_optin)
             return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: view %d has too many tiles", v);
     const bool sync = (flags & BGS_BIN_NO_SYNC) == 0;
     DeviceGuard g(p->device);
