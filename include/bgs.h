@@ -181,7 +181,11 @@ int bgs_render_forward(bgs_plan *plan, int64_t N, const float *means2D, const fl
    dL_dalpha [H,W] (nullable).  Outputs (overwritten): dL_dmeans2D [N,2],
    dL_dconic [N,3] (w.r.t. a, b, c exactly as used in power), dL_dopacity [N],
    dL_dcolors [N,3], dL_ddepths [N] (nullable).  Where o exp(power) > 0.99 the alpha
-   clamp is active and the pair passes no gradient to o or to the Gaussian's shape. */
+   clamp is active and the pair passes no gradient to o or to the Gaussian's shape.
+   The arrays must hold what the forward read (final_T and n_contrib only describe that
+   blend).  When they are the same arrays (pointers and sizes) as the plan's last forward
+   and that forward queued every tile pixel-wise, the packed records and the work list
+   of that forward are reused instead of being rebuilt. */
 int bgs_render_backward(bgs_plan *plan, int64_t N, const float *means2D, const float *conic_opacity,
                         const float *colors, const float *depths, const uint32_t *point_list,
                         int64_t num_entries, const uint32_t *ranges, int32_t W, int32_t H, int32_t tile_w,

@@ -90,6 +90,18 @@ struct bgs_plan {
     // captured CUDA graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    // what the packed records and the work list currently hold (a backward on the arrays of
+    // the last forward reuses both instead of rebuilding them)
+    struct RecKey {
+        const void *means2D, *conic_opacity, *colors, *depths;
+        int64_t n_records, n_colors;
+    } rec_key;
+    struct WlKey {
+        const void *ranges;
+        bgs::ViewTable vt;
+        int tw, th, mode, heavy_threshold, gw_pixels, pixel_rows, lpt_order;
+    } wl_key;
+    bool rec_valid = false, wl_valid = false;
 };
 
 namespace {
@@ -101,7 +113,8 @@ int ensure(bgs_plan *p, Buf &b, size_t bytes, cudaStream_t s, const char *what) 
     if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone)
         return fail(BGS_ERR_CAPACITY, "workspace '%s' needs %zu bytes while the stream is being captured; "
                                       "call bgs_plan_reserve before capture", what, bytes);
-    (void)p;
+    if (&b == &p->recs) p->rec_valid = false;
+    if (&b == &p->items) p->wl_valid = false;
     if (b.p) {
         cudaError_t e = cudaFree(b.p);
         b.p = nullptr;
@@ -187,8 +200,40 @@ int grid_for(const bgs_plan *p, const void *kernel, int threads) {
 }
 
 // Builds the work list of the persistent kernels over the global tile space of the views (a3).
+bgs_plan::WlKey worklist_key(const bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt, int tw, int th,
+                             int mode) {
+    bgs_plan::WlKey k;
+    memset(&k, 0, sizeof k);  // padding included: keys are compared with memcmp
+    k.ranges = ranges;
+    k.vt = vt;
+    k.tw = tw;
+    k.th = th;
+    k.mode = mode;
+    k.heavy_threshold = p->desc.heavy_threshold;
+    k.gw_pixels = p->desc.gw_pixels;
+    k.pixel_rows = p->desc.pixel_rows;
+    k.lpt_order = p->desc.lpt_order;
+    return k;
+}
+
+bgs_plan::RecKey records_key(const float *means2D, const float *conic_opacity, const float *colors,
+                             const float *depths, int64_t n_records, int64_t n_colors) {
+    bgs_plan::RecKey k;
+    memset(&k, 0, sizeof k);
+    k.means2D = means2D;
+    k.conic_opacity = conic_opacity;
+    k.colors = colors;
+    k.depths = depths;
+    k.n_records = n_records;
+    k.n_colors = n_colors;
+    return k;
+}
+
+// mode: the render mode; AUTO with a threshold no list can exceed queues every tile
+// pixel-wise and builds the same list as PIXEL (so a backward can reuse it).
 int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt, int tw, int th, int mode,
-                   cudaStream_t s) {
+                   int64_t num_entries, cudaStream_t s) {
+    if (mode == BGS_MODE_AUTO && (int64_t)p->desc.heavy_threshold >= num_entries) mode = BGS_MODE_PIXEL;
     const int T = vt.tile_base[vt.V];
     const int P = p->desc.gw_pixels;
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
@@ -211,7 +256,7 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
     BGS_TRY(ensure(p, p->tile_idx2, sizeof(uint32_t) * T, s, "tile_idx2"));
     {
         size_t tmp = 0;
-        const int kbits = p->desc.lpt_order ? 32 : 1;
+        const int kbits = p->desc.lpt_order ? 8 : 1;  // 8-bit key: kind bit + log-length bucket
         BGS_CUDA(cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp, key, (uint32_t *)p->tile_key2.p, idx,
                                                            (uint32_t *)p->tile_idx2.p, T, 0, kbits, s),
                  "sort tiles (size)");
@@ -235,6 +280,8 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
                                     p->ctrl, s),
              "emit_items");
     p->host_launches += 3;  // tile_counts, gather_counts, emit_items
+    p->wl_key = worklist_key(p, ranges, vt, tw, th, mode);
+    p->wl_valid = true;
     return BGS_OK;
 }
 
@@ -705,8 +752,10 @@ int render_forward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewOu
     BGS_CUDA(bgs::launch_pack(n_records, means2D, conic_opacity, colors, n_colors, depths, (bgs::Rec *)p->recs.p, s),
              "pack");
     p->host_launches += 1;
+    p->rec_key = records_key(means2D, conic_opacity, colors, depths, n_records, n_colors);
+    p->rec_valid = true;
     a.recs = (const bgs::Rec *)p->recs.p;
-    BGS_TRY(build_worklist(p, ranges, vt, tw, th, mode, s));
+    BGS_TRY(build_worklist(p, ranges, vt, tw, th, mode, num_entries, s));
     a.items = (const uint2 *)p->items.p;
     const int threads = bgs::forward_balanced_block_threads();
     const int grid_g = grid_for(p, bgs::forward_gauss_kernel(a.gw_pixels), threads);
@@ -756,18 +805,32 @@ int render_backward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewG
         kt.stop();
         p->host_launches += 1;
     } else {
-        BGS_TRY(ensure(p, p->recs, sizeof(bgs::Rec) * n_records, s, "recs"));
-        BGS_CUDA(bgs::launch_pack(n_records, means2D, conic_opacity, colors, n_colors, depths, (bgs::Rec *)p->recs.p,
-                                  s),
-                 "pack");
+        // the packed records and the pixel-wise work list of the last forward, when it ran on
+        // these arrays (the backward needs the forward's inputs unchanged in any case)
+        const bgs_plan::RecKey rk = records_key(means2D, conic_opacity, colors, depths, n_records, n_colors);
+        if (!(p->rec_valid && memcmp(&rk, &p->rec_key, sizeof rk) == 0)) {
+            BGS_TRY(ensure(p, p->recs, sizeof(bgs::Rec) * n_records, s, "recs"));
+            BGS_CUDA(bgs::launch_pack(n_records, means2D, conic_opacity, colors, n_colors, depths,
+                                      (bgs::Rec *)p->recs.p, s),
+                     "pack");
+            p->host_launches += 1;
+            p->rec_key = rk;
+            p->rec_valid = true;
+        }
         a.recs = (const bgs::Rec *)p->recs.p;
-        BGS_TRY(build_worklist(p, ranges, vt, tw, th, BGS_MODE_PIXEL, s));
+        const bgs_plan::WlKey wk = worklist_key(p, ranges, vt, tw, th, BGS_MODE_PIXEL);
+        if (p->wl_valid && memcmp(&wk, &p->wl_key, sizeof wk) == 0) {
+            // same list (no Gaussian-wise items): rewind the pixel-wise queue cursor
+            BGS_CUDA(cudaMemsetAsync(&p->ctrl->queue_head, 0, sizeof(unsigned int), s), "rewind queue");
+        } else {
+            BGS_TRY(build_worklist(p, ranges, vt, tw, th, BGS_MODE_PIXEL, num_entries, s));
+        }
         a.items = (const uint2 *)p->items.p;
         const int grid = grid_for(p, bgs::backward_balanced_kernel(a), bgs::backward_balanced_block_threads());
         KernelTimer kt(p, s, &p->ev_bwd);
         BGS_CUDA(bgs::launch_backward_balanced(a, grid, s), "backward_balanced");
         kt.stop();
-        p->host_launches += 2;  // pack + kernel
+        p->host_launches += 1;  // kernel
     }
     BGS_CUDA(bgs::launch_grad_finalize(n_records, n_colors, (const float4 *)p->grad_acc.p, dL_dmeans2D, dL_dconic,
                                        dL_dopacity, dL_dcolors, dL_ddepths, s),
@@ -901,7 +964,7 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
         unsigned long long *k0 = (unsigned long long *)p->dkey64.p, *k1 = (unsigned long long *)p->dkey64_sorted.p;
         uint32_t *gidx = (uint32_t *)p->gidx.p, *order = (uint32_t *)p->order.p;
         BGS_CUDA(bgs::launch_depth_keys64(N, V, depths, k0, gidx, s), "depth keys");
-        const int end_bit = 32 + bits_for(V - 1);
+        const int end_bit = V > 1 ? 32 + bits_for(V - 1) : 32;  // view bits only when there are views
         size_t tmp = 0;
         BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, k0, k1, gidx, order, (int64_t)R, 0, end_bit, s),
                  "view/depth sort (size)");

@@ -29,15 +29,25 @@ __device__ __forceinline__ uint32_t tile_item_count(int t, uint32_t n, const Vie
     return (uint32_t)(((vw + kPixItemW - 1) / kPixItemW) * ((vh + item_h - 1) / item_h));
 }
 
-// Sort key of each tile: its list length (heaviest first) when lpt is on, else only its
-// kind, so that the descending stable sort always puts Gaussian-wise tiles first.
+// Sort key of each tile for the descending stable sort: its kind in the top bit (Gaussian-
+// wise tiles first) and, when lpt is on, a log-scale bucket of its list length below it
+// (heaviest first; lengths within ~19% share a bucket): bucket = 4 floor(log2 n) + the two
+// bits after the leading one, + 1 (0 for an empty tile).  One 8-bit radix pass sorts it.
+__device__ __forceinline__ uint32_t length_bucket(uint32_t n) {
+    if (n == 0u) return 0u;
+    const int e = 31 - __clz(n);
+    const uint32_t m = e >= 2 ? (n >> (e - 2)) & 3u : (n << (2 - e)) & 3u;
+    return min(127u, 4u * (uint32_t)e + m + 1u);
+}
+
 __global__ void k_tile_counts(const uint2 *__restrict__ ranges, int num_tiles, int mode, int heavy_threshold, int lpt,
                               uint32_t *__restrict__ tile_key, uint32_t *__restrict__ tile_idx) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= num_tiles) return;
     const uint2 rg = ranges[t];
     const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
-    tile_key[t] = lpt ? n : (tile_is_gauss(mode, heavy_threshold, n) ? 1u : 0u);
+    const uint32_t kind = tile_is_gauss(mode, heavy_threshold, n) ? 1u : 0u;
+    tile_key[t] = lpt ? (kind << 7) | length_bucket(n) : kind;
     tile_idx[t] = (uint32_t)t;
 }
 

@@ -218,6 +218,43 @@ def test_backward_fd_crop(R, plan, mode):
         assert e <= GRAD_REL_L2, (k, e)
 
 
+@pytest.mark.parametrize("mode,threshold", [("pixel", 64), ("auto", 1 << 30), ("auto", 64)])
+def test_backward_reuses_or_rebuilds_forward_state(R, cfg1, mode, threshold):
+    """A backward on the arrays of the plan's last forward reuses its packed records and
+    (when every tile was queued pixel-wise) its work list; after a forward on other arrays
+    it rebuilds them; a plan that ran no forward builds them.  All three give the same
+    gradients."""
+    W, H, tile = cfg1["W"], cfg1["H"], cfg1["tile"]
+    rng = np.random.default_rng(4)
+    gC = torch.from_numpy(rng.normal(size=(3, H, W)).astype(np.float32)).cuda()
+    gA, gB = to_gpu(cfg1), to_gpu(cfg1)  # same values, different arrays
+
+    def fwd(pl, g):
+        return R.render_forward(pl, g["means2D"], g["conic_opacity"], g["colors"], g["depths"], g["point_list"],
+                                g["K"], g["ranges"], W, H, tile, (0.0, 0.0, 0.0), mode)
+
+    def bwd(pl, g, out):
+        gr = R.render_backward(pl, g["means2D"], g["conic_opacity"], g["colors"], g["depths"], g["point_list"],
+                               g["K"], g["ranges"], W, H, out["final_T"], out["n_contrib"], gC, None, None, tile,
+                               (0.0, 0.0, 0.0), mode)
+        torch.cuda.synchronize()
+        pl.check()
+        return {k: _np(v) for k, v in gr.items()}
+
+    plans = [R.Plan(heavy_threshold=threshold) for _ in range(3)]
+    out = fwd(plans[0], gA)
+    reused = bwd(plans[0], gA, out)
+    fwd(plans[1], gA)
+    fwd(plans[1], gB)  # the plan now holds gB's records
+    rebuilt = bwd(plans[1], gA, out)
+    fresh = bwd(plans[2], gA, out)
+    for k in ("means2D", "conic", "opacity", "colors"):
+        assert rel_l2(reused[k], fresh[k]) < 1e-6, k
+        assert rel_l2(rebuilt[k], fresh[k]) < 1e-6, k
+    for pl in plans:
+        pl.close()
+
+
 # --------------------------------------------------------------------------------- device checks
 
 def test_device_checks_report_bad_indices_and_ranges(R, plan, cfg1):
