@@ -275,7 +275,7 @@ cudaError_t launch_emit_items(const uint32_t *order, const uint32_t *counts, con
 
 cudaError_t launch_forward_static(const FwdArgs &a, cudaStream_t s);
 cudaError_t launch_forward_gauss(const FwdArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_forward_pixel(const FwdArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_forward_pixel(const FwdArgs &a, int grid, bool after_gauss, cudaStream_t s);
 int forward_balanced_block_threads();
 const void *forward_gauss_kernel(int gw_pixels);
 const void *forward_pixel_kernel(int pixel_rows);

@@ -760,11 +760,14 @@ int render_forward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewOu
     const int threads = bgs::forward_balanced_block_threads();
     const int grid_g = grid_for(p, bgs::forward_gauss_kernel(a.gw_pixels), threads);
     const int grid_p = grid_for(p, bgs::forward_pixel_kernel(a.pixel_rows), threads);
+    // AUTO with a threshold no list can exceed queues no Gaussian-wise item
+    const bool gauss = mode == BGS_MODE_GAUSSIAN ||
+                       (mode == BGS_MODE_AUTO && (int64_t)p->desc.heavy_threshold < num_entries);
     KernelTimer kt(p, s, &p->ev_fwd);
-    if (mode != BGS_MODE_PIXEL) BGS_CUDA(bgs::launch_forward_gauss(a, grid_g, s), "forward_gauss");
-    if (mode != BGS_MODE_GAUSSIAN) BGS_CUDA(bgs::launch_forward_pixel(a, grid_p, s), "forward_pixel");
+    if (gauss) BGS_CUDA(bgs::launch_forward_gauss(a, grid_g, s), "forward_gauss");
+    if (mode != BGS_MODE_GAUSSIAN) BGS_CUDA(bgs::launch_forward_pixel(a, grid_p, gauss, s), "forward_pixel");
     kt.stop();
-    p->host_launches += (mode == BGS_MODE_AUTO) ? 2 : 1;
+    p->host_launches += (gauss && mode != BGS_MODE_GAUSSIAN) ? 2 : 1;
     return BGS_OK;
 }
 

@@ -472,9 +472,12 @@ cudaError_t launch_forward_gauss(const FwdArgs &a, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Launched right after k_forward_gauss on the same stream with programmatic stream
-// serialisation: the two kernels touch disjoint pixels, so no wait is needed.
-cudaError_t launch_forward_pixel(const FwdArgs &a, int grid, cudaStream_t s) {
+// after_gauss: launched right after k_forward_gauss on the same stream, with programmatic
+// stream serialisation (the two kernels touch disjoint pixels and k_forward_gauss started
+// after the work list was complete, so no wait is needed).  Otherwise an ordinary launch:
+// the kernel has no grid-dependency wait, so it must not overlap the kernels that build
+// its work list.
+cudaError_t launch_forward_pixel(const FwdArgs &a, int grid, bool after_gauss, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kWarpsPerBlock * 32);
@@ -484,7 +487,7 @@ cudaError_t launch_forward_pixel(const FwdArgs &a, int grid, cudaStream_t s) {
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = after_gauss ? 1 : 0;
     switch (a.pixel_rows) {
         case 1: return cudaLaunchKernelEx(&cfg, k_forward_pixel<1>, a);
         case 2: return cudaLaunchKernelEx(&cfg, k_forward_pixel<2>, a);
