@@ -13,6 +13,9 @@ Each wrapper cites the passage of the paper it follows:
 * ``render``       -- Eq. 4 under Algorithm 5's per-pair rules (Appendix A).
 * ``render_backward`` -- the analytic gradient of ``render`` (not in the paper, which
   only names the backward pass in Sec. 3; derived from Eq. 4 directly).
+* ``preprocess_backward`` -- the chain rule through the projection of Eq. 2-3 (the
+  paper prints no backward; ``project64`` is the same projection from FP64 inputs, for
+  finite differences).
 
 Parity status: pinned by closed forms, invariants, brute force and FP64 finite
 differences (``tests/test_oracle_pins.py``); the paper prints no numeric example, so
@@ -68,6 +71,9 @@ def _load():
             lib.orc_tile_rect.argtypes = [ctypes.c_float, ctypes.c_float, i32, i32, i32, i32, i32, P]
             lib.orc_preprocess.argtypes = [i64, P, P, P, P, i32, i32, d, d, d, d, P, d, d, i32, i32,
                                            P, P, P, P, P, P]
+            lib.orc_project64.argtypes = [i64, P, P, P, i32, i32, d, d, d, d, P, d, d, P, P, P, P]
+            lib.orc_preprocess_backward.argtypes = [i64, P, P, P, i32, i32, d, d, d, d, P, d, d, P, P, P, P, P, P,
+                                                    P]
             lib.orc_bin.argtypes = [i64, P, P, P, i32, i32, i32, i32, i64, P, P]
             lib.orc_bin.restype = i64
             lib.orc_render.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, i64, P,
@@ -125,6 +131,45 @@ def preprocess(means3D, log_scales, quats, opacities, cam: dict, tile_w=16, tile
                        tile_w, tile_h, _p(out["means2D"]), _p(out["conic_opacity"]),
                        _p(out["depth"]), _p(out["radius"]), _p(out["radius_raw"]),
                        _p(out["tiles_touched"]))
+    return out
+
+
+def _cam_args(cam: dict):
+    V = _f64(np.asarray(cam["viewmat"], np.float64).reshape(16))
+    return V, (int(cam["W"]), int(cam["H"]), float(cam["fx"]), float(cam["fy"]), float(cam["cx"]),
+               float(cam["cy"]))
+
+
+def project64(means3D, log_scales, quats, cam: dict):
+    """The projection of ``preprocess`` (Eq. 1-3) from FP64 inputs: means2D [N,2],
+    conic [N,3] (a, b, c), depth [N] and valid [N] (0 where culled)."""
+    lib = _load()
+    m3, ls, q = _f64(means3D), _f64(log_scales), _f64(quats)
+    N = m3.shape[0]
+    V, (W, H, fx, fy, cx, cy) = _cam_args(cam)
+    out = dict(means2D=np.zeros((N, 2)), conic=np.zeros((N, 3)), depth=np.zeros(N), valid=np.zeros(N, np.int32))
+    lib.orc_project64(N, _p(m3), _p(ls), _p(q), W, H, fx, fy, cx, cy, _p(V), float(cam.get("near", 0.2)),
+                      float(cam.get("lowpass", 0.3)), _p(out["means2D"]), _p(out["conic"]), _p(out["depth"]),
+                      _p(out["valid"]))
+    return out
+
+
+def preprocess_backward(means3D, log_scales, quats, cam: dict, dL_dmeans2D, dL_dconic, dL_ddepth=None,
+                        radius=None):
+    """Chain rule through the projection (Eq. 2-3): dL/d(means2D [N,2], conic [N,3],
+    depth [N]) -> dL/d(means3D [N,3], log_scales [N,3], quats [N,4]) in FP64.  Gaussians
+    with radius 0 (when ``radius`` is given) or culled get zero."""
+    lib = _load()
+    m3, ls, q = _f64(means3D), _f64(log_scales), _f64(quats)
+    N = m3.shape[0]
+    V, (W, H, fx, fy, cx, cy) = _cam_args(cam)
+    gm, gc = _f64(dL_dmeans2D).reshape(N, 2), _f64(dL_dconic).reshape(N, 3)
+    gd = None if dL_ddepth is None else _f64(dL_ddepth).reshape(N)
+    rad = None if radius is None else np.ascontiguousarray(radius, np.int32)
+    out = dict(means3D=np.zeros((N, 3)), log_scales=np.zeros((N, 3)), quats=np.zeros((N, 4)))
+    lib.orc_preprocess_backward(N, _p(m3), _p(ls), _p(q), W, H, fx, fy, cx, cy, _p(V), float(cam.get("near", 0.2)),
+                                float(cam.get("lowpass", 0.3)), _p(rad), _p(gm), _p(gc), _p(gd),
+                                _p(out["means3D"]), _p(out["log_scales"]), _p(out["quats"]))
     return out
 
 

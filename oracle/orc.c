@@ -97,18 +97,100 @@ void orc_tile_rect(float u, float v, int r, int W, int H, int tw, int th, int32_
     out4[0] = a; out4[1] = b; out4[2] = c; out4[3] = d;
 }
 
+/* Camera of the projection: rows 0..2 of the 4x4 row-major world->camera matrix V,
+   intrinsics, near plane, low-pass and the tangent clamp lim = 1.3 tan(fov / 2). */
+typedef struct {
+    const double *V;
+    double fx, fy, cx, cy, near_z, lowpass, lim_x, lim_y;
+} orc_cam;
+
+static orc_cam make_cam(const double *V, int W, int H, double fx, double fy, double cx, double cy, double near_z,
+                        double lowpass) {
+    orc_cam c;
+    c.V = V;
+    c.fx = fx; c.fy = fy; c.cx = cx; c.cy = cy;
+    c.near_z = near_z;
+    c.lowpass = lowpass;
+    c.lim_x = 1.3 * ((double)W / (2.0 * fx));
+    c.lim_y = 1.3 * ((double)H / (2.0 * fy));
+    return c;
+}
+
+/* The intermediate values of one Gaussian's projection (Eq. 1-3).  Returns 0 when the
+   Gaussian is culled (z <= near or a non-positive-definite 2D covariance). */
+typedef struct {
+    double t[3];          /* camera-space centre */
+    double q[4], qn;      /* normalised quaternion (w, x, y, z) and the input's norm */
+    double R[3][3], s[3]; /* rotation, scales */
+    double M[3][3];       /* R S */
+    double Sig[3][3];     /* 3D covariance (R S)(R S)^T */
+    double J[2][3];       /* Jacobian of the pinhole map at the tangent-clamped point */
+    int in_x, in_y;       /* tangent of the centre within the clamp */
+    double Tm[2][3];      /* J W */
+    double C2[2][2];      /* 2D covariance + low-pass */
+    double det;
+    double u, v, conic[3], rr;
+} orc_proj;
+
+static int project_one(const orc_cam *c, const double p[3], const double log_s[3], const double quat[4],
+                       orc_proj *o) {
+    const double *V = c->V;
+    for (int r = 0; r < 3; ++r) o->t[r] = V[4 * r] * p[0] + V[4 * r + 1] * p[1] + V[4 * r + 2] * p[2] + V[4 * r + 3];
+    if (!(o->t[2] > c->near_z)) return 0;
+    o->qn = sqrt(quat[0] * quat[0] + quat[1] * quat[1] + quat[2] * quat[2] + quat[3] * quat[3]);
+    for (int k = 0; k < 4; ++k) o->q[k] = quat[k] / o->qn;
+    const double qw = o->q[0], qx = o->q[1], qy = o->q[2], qz = o->q[3];
+    const double R[3][3] = {
+        {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+        {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+        {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+    memcpy(o->R, R, sizeof R);
+    for (int k = 0; k < 3; ++k) o->s[k] = exp(log_s[k]);
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) o->M[r][k] = R[r][k] * o->s[k];
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k)
+            o->Sig[r][k] = o->M[r][0] * o->M[k][0] + o->M[r][1] * o->M[k][1] + o->M[r][2] * o->M[k][2];
+    const double z = o->t[2];
+    const double txz = o->t[0] / z, tyz = o->t[1] / z;
+    o->in_x = txz >= -c->lim_x && txz <= c->lim_x;
+    o->in_y = tyz >= -c->lim_y && tyz <= c->lim_y;
+    const double xc = (txz < -c->lim_x ? -c->lim_x : (txz > c->lim_x ? c->lim_x : txz)) * z;
+    const double yc = (tyz < -c->lim_y ? -c->lim_y : (tyz > c->lim_y ? c->lim_y : tyz)) * z;
+    const double J[2][3] = {{c->fx / z, 0.0, -c->fx * xc / (z * z)}, {0.0, c->fy / z, -c->fy * yc / (z * z)}};
+    memcpy(o->J, J, sizeof J);
+    for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < 3; ++k) o->Tm[r][k] = J[r][0] * V[k] + J[r][1] * V[4 + k] + J[r][2] * V[8 + k];
+    for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < 2; ++k) {
+            double acc = 0.0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) acc += o->Tm[r][a] * o->Sig[a][b] * o->Tm[k][b];
+            o->C2[r][k] = acc;
+        }
+    o->C2[0][0] += c->lowpass;
+    o->C2[1][1] += c->lowpass;
+    o->det = o->C2[0][0] * o->C2[1][1] - o->C2[0][1] * o->C2[1][0];
+    if (!(o->det > 0.0)) return 0;
+    double mid = 0.5 * (o->C2[0][0] + o->C2[1][1]);
+    double disc = mid * mid - o->det;
+    if (disc < 0.1) disc = 0.1;
+    o->rr = 3.0 * sqrt(mid + sqrt(disc));
+    o->u = c->fx * o->t[0] / z + c->cx;
+    o->v = c->fy * o->t[1] / z + c->cy;
+    o->conic[0] = o->C2[1][1] / o->det;
+    o->conic[1] = -o->C2[0][1] / o->det;
+    o->conic[2] = o->C2[0][0] / o->det;
+    return 1;
+}
+
 /* ------------------------------------------------------------------------- */
-/* Projection (Eq. 1-3).                                                      */
-/*   camera: fx fy cx cy, row-major 4x4 world->camera matrix V, near plane,   */
-/*   lowpass added to the diagonal of Sigma'.                                 */
-/*   Sigma = R S S^T R^T, R from the normalised quaternion (w,x,y,z), S =     */
-/*   diag(exp(log_scale)).  J is the Jacobian of (fx x/z + cx, fy y/z + cy)   */
-/*   at the (tangent-clamped) camera-space point; W is V's rotation block.    */
-/* Outputs: means2D [N,2], conic_opacity [N,4] (a,b,c,o with                   */
-/*   power = -1/2 (a dx^2 + c dy^2) - b dx dy), depth [N], radius [N] (int),   */
-/*   radius_raw [N] = 3 sqrt(lambda_max) before the ceil, tiles_touched [N]    */
-/*   (rectangle area, computed from the float32-rounded mean).                */
-/* A culled Gaussian gets radius 0 and tiles_touched 0.                        */
+/* Projection (Eq. 1-3, Sec. 2.1): camera-space centre t = W p + w, 3D        */
+/* covariance Sigma = R S S^T R^T from the normalised quaternion (w, x, y, z) */
+/* and exp(log_scale), 2D covariance J W Sigma W^T J^T (+ low-pass on the     */
+/* diagonal) with J the pinhole Jacobian at the tangent-clamped centre, conic */
+/* = its inverse (a, b, c), radius = ceil(3 sqrt(lambda_max)) with the        */
+/* discriminant floored at 0.1, means2D = (fx x/z + cx, fy y/z + cy).        */
 /* ------------------------------------------------------------------------- */
 void orc_preprocess(int64_t N, const float *means3D, const float *log_scales, const float *quats,
                     const float *opacities, int W, int H, double fx, double fy, double cx, double cy,
@@ -116,80 +198,154 @@ void orc_preprocess(int64_t N, const float *means3D, const float *log_scales, co
                     double *means2D, double *conic_opacity, double *depth, int32_t *radius,
                     double *radius_raw, int32_t *tiles_touched) {
     const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
-    const double tan_x = (double)W / (2.0 * fx), tan_y = (double)H / (2.0 * fy);
-    const double lim_x = 1.3 * tan_x, lim_y = 1.3 * tan_y;
+    const orc_cam cam = make_cam(V, W, H, fx, fy, cx, cy, near_z, lowpass);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) {
-        double p[3] = {means3D[3 * i], means3D[3 * i + 1], means3D[3 * i + 2]};
-        double t[3];
-        for (int r = 0; r < 3; ++r) t[r] = V[4 * r] * p[0] + V[4 * r + 1] * p[1] + V[4 * r + 2] * p[2] + V[4 * r + 3];
+        const double p[3] = {means3D[3 * i], means3D[3 * i + 1], means3D[3 * i + 2]};
+        const double ls[3] = {log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]};
+        const double q[4] = {quats[4 * i], quats[4 * i + 1], quats[4 * i + 2], quats[4 * i + 3]};
+        orc_proj o;
+        const int ok = project_one(&cam, p, ls, q, &o);
         means2D[2 * i] = means2D[2 * i + 1] = 0.0;
         for (int k = 0; k < 4; ++k) conic_opacity[4 * i + k] = 0.0;
-        depth[i] = t[2];
+        depth[i] = o.t[2];
         radius[i] = 0;
         radius_raw[i] = 0.0;
         tiles_touched[i] = 0;
-        if (!(t[2] > near_z)) continue;
-
-        /* rotation from the normalised quaternion q = (w, x, y, z) */
-        double qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
-        double qn = sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
-        qw /= qn; qx /= qn; qy /= qn; qz /= qn;
-        double R[3][3] = {
-            {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
-            {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
-            {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
-        double s[3] = {exp(log_scales[3 * i]), exp(log_scales[3 * i + 1]), exp(log_scales[3 * i + 2])};
-        /* Sigma = (R S)(R S)^T */
-        double M[3][3], Sig[3][3];
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) M[r][c] = R[r][c] * s[c];
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) Sig[r][c] = M[r][0] * M[c][0] + M[r][1] * M[c][1] + M[r][2] * M[c][2];
-
-        /* Jacobian at the tangent-clamped point */
-        double z = t[2];
-        double txz = t[0] / z, tyz = t[1] / z;
-        double xc = (txz < -lim_x ? -lim_x : (txz > lim_x ? lim_x : txz)) * z;
-        double yc = (tyz < -lim_y ? -lim_y : (tyz > lim_y ? lim_y : tyz)) * z;
-        double J[2][3] = {{fx / z, 0.0, -fx * xc / (z * z)}, {0.0, fy / z, -fy * yc / (z * z)}};
-        /* T = J W (2x3), W = rotation block of V */
-        double Tm[2][3];
-        for (int r = 0; r < 2; ++r)
-            for (int c = 0; c < 3; ++c) Tm[r][c] = J[r][0] * V[c] + J[r][1] * V[4 + c] + J[r][2] * V[8 + c];
-        double C2[2][2];
-        for (int r = 0; r < 2; ++r)
-            for (int c = 0; c < 2; ++c) {
-                double acc = 0.0;
-                for (int k = 0; k < 3; ++k)
-                    for (int l = 0; l < 3; ++l) acc += Tm[r][k] * Sig[k][l] * Tm[c][l];
-                C2[r][c] = acc;
-            }
-        C2[0][0] += lowpass;
-        C2[1][1] += lowpass;
-        double det = C2[0][0] * C2[1][1] - C2[0][1] * C2[1][0];
-        if (!(det > 0.0)) continue;
-        double mid = 0.5 * (C2[0][0] + C2[1][1]);
-        double disc = mid * mid - det;
-        if (disc < 0.1) disc = 0.1;
-        double lam = mid + sqrt(disc);
-        double rr = 3.0 * sqrt(lam);
-        int r = (int)ceil(rr);
-
-        double u = fx * t[0] / z + cx, v = fy * t[1] / z + cy;
-        means2D[2 * i] = u;
-        means2D[2 * i + 1] = v;
-        conic_opacity[4 * i + 0] = C2[1][1] / det;
-        conic_opacity[4 * i + 1] = -C2[0][1] / det;
-        conic_opacity[4 * i + 2] = C2[0][0] / det;
+        if (!ok) continue;
+        const int r = (int)ceil(o.rr);
+        means2D[2 * i] = o.u;
+        means2D[2 * i + 1] = o.v;
+        for (int k = 0; k < 3; ++k) conic_opacity[4 * i + k] = o.conic[k];
         conic_opacity[4 * i + 3] = opacities[i];
-        radius_raw[i] = rr;
+        radius_raw[i] = o.rr;
         int x0, x1, y0, y1;
-        tile_rect((float)u, (float)v, r, tiles_x, tiles_y, tw, th, &x0, &x1, &y0, &y1);
+        tile_rect((float)o.u, (float)o.v, r, tiles_x, tiles_y, tw, th, &x0, &x1, &y0, &y1);
         int64_t area = (int64_t)(x1 - x0) * (int64_t)(y1 - y0);
         if (area <= 0) continue;
         radius[i] = r;
         tiles_touched[i] = (int32_t)area;
+    }
+}
+
+/* The same projection from FP64 inputs (means2D, conic (a, b, c), depth; valid = not
+   culled), for finite differences of the projection backward. */
+void orc_project64(int64_t N, const double *means3D, const double *log_scales, const double *quats, int W, int H,
+                   double fx, double fy, double cx, double cy, const double *V, double near_z, double lowpass,
+                   double *means2D, double *conic, double *depth, int32_t *valid) {
+    const orc_cam cam = make_cam(V, W, H, fx, fy, cx, cy, near_z, lowpass);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        orc_proj o;
+        valid[i] = project_one(&cam, means3D + 3 * i, log_scales + 3 * i, quats + 4 * i, &o);
+        depth[i] = o.t[2];
+        means2D[2 * i] = valid[i] ? o.u : 0.0;
+        means2D[2 * i + 1] = valid[i] ? o.v : 0.0;
+        for (int k = 0; k < 3; ++k) conic[3 * i + k] = valid[i] ? o.conic[k] : 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Projection backward (not printed in the paper; the chain rule through     */
+/* Eq. 2-3 as written above): given dL/d(means2D, conic a b c, depth) of     */
+/* each Gaussian, dL/d(means3D, log_scales, quats).  Gaussians with          */
+/* radius 0 (culled or off-screen) get zero.                                  */
+/*   conic = inv(C2): with A, B, C the entries of C2 and det = AC - B^2,       */
+/*     a = C/det, b = -B/det, c = A/det;                                      */
+/*   C2 = T Sigma T^T + lowpass I, T = J W: dL/dSigma = T^T G T,               */
+/*     dL/dT = 2 G T Sigma (G = dL/dC2 symmetric, off-diagonal = dL/dB / 2);   */
+/*   J from the clamped centre: d/dx of the clamped tangent is 0 outside;     */
+/*   Sigma = M M^T, M = R S: dL/dM = 2 dL/dSigma M; dL/ds = column sums of     */
+/*     dL/dM * R; dL/dR = dL/dM S; R(q) from the normalised quaternion, then  */
+/*     the normalisation's Jacobian; t = W p + w: dL/dp = W^T dL/dt.          */
+/* ------------------------------------------------------------------------- */
+void orc_preprocess_backward(int64_t N, const double *means3D, const double *log_scales, const double *quats,
+                             int W, int H, double fx, double fy, double cx, double cy, const double *V,
+                             double near_z, double lowpass, const int32_t *radius, const double *g_means2D,
+                             const double *g_conic, const double *g_depth, double *g_means3D,
+                             double *g_log_scales, double *g_quats) {
+    const orc_cam cam = make_cam(V, W, H, fx, fy, cx, cy, near_z, lowpass);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        for (int k = 0; k < 3; ++k) g_means3D[3 * i + k] = g_log_scales[3 * i + k] = 0.0;
+        for (int k = 0; k < 4; ++k) g_quats[4 * i + k] = 0.0;
+        if (radius && radius[i] <= 0) continue;
+        orc_proj o;
+        if (!project_one(&cam, means3D + 3 * i, log_scales + 3 * i, quats + 4 * i, &o)) continue;
+        const double z = o.t[2];
+        double gt[3] = {0.0, 0.0, g_depth ? g_depth[i] : 0.0};
+        /* means2D */
+        const double gu = g_means2D[2 * i], gv = g_means2D[2 * i + 1];
+        gt[0] += gu * fx / z;
+        gt[1] += gv * fy / z;
+        gt[2] += -gu * fx * o.t[0] / (z * z) - gv * fy * o.t[1] / (z * z);
+        /* conic -> C2 */
+        const double A = o.C2[0][0], B = o.C2[0][1], C = o.C2[1][1], d2 = o.det * o.det;
+        const double ga = g_conic[3 * i], gb = g_conic[3 * i + 1], gc = g_conic[3 * i + 2];
+        const double dA = ga * (-C * C / d2) + gb * (B * C / d2) + gc * (-B * B / d2);
+        const double dC = ga * (-B * B / d2) + gb * (A * B / d2) + gc * (-A * A / d2);
+        const double dB = ga * (2.0 * B * C / d2) + gb * (-1.0 / o.det - 2.0 * B * B / d2) + gc * (2.0 * A * B / d2);
+        const double G[2][2] = {{dA, 0.5 * dB}, {0.5 * dB, dC}};
+        /* C2 = T Sigma T^T */
+        double gSig[3][3], gT[2][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double acc = 0.0;
+                for (int r = 0; r < 2; ++r)
+                    for (int k = 0; k < 2; ++k) acc += o.Tm[r][a] * G[r][k] * o.Tm[k][b];
+                gSig[a][b] = acc;
+            }
+        for (int r = 0; r < 2; ++r)
+            for (int a = 0; a < 3; ++a) {
+                double acc = 0.0;
+                for (int k = 0; k < 2; ++k)
+                    for (int b = 0; b < 3; ++b) acc += G[r][k] * o.Tm[k][b] * o.Sig[b][a];
+                gT[r][a] = 2.0 * acc;
+            }
+        /* T = J W: dL/dJ[r][k] = sum_c dL/dT[r][c] W[k][c] */
+        double gJ[2][3];
+        for (int r = 0; r < 2; ++r)
+            for (int k = 0; k < 3; ++k) gJ[r][k] = gT[r][0] * V[4 * k] + gT[r][1] * V[4 * k + 1] + gT[r][2] * V[4 * k + 2];
+        /* J(t): J00 = fx/z, J02 = -fx cl(x/z)/z, J11 = fy/z, J12 = -fy cl(y/z)/z */
+        const double clx = -o.J[0][2] * z / fx, cly = -o.J[1][2] * z / fy; /* clamped tangents */
+        gt[2] += gJ[0][0] * (-fx / (z * z)) + gJ[1][1] * (-fy / (z * z));
+        gt[2] += gJ[0][2] * (fx * clx / (z * z)) + gJ[1][2] * (fy * cly / (z * z));
+        if (o.in_x) {
+            gt[0] += gJ[0][2] * (-fx / (z * z));
+            gt[2] += gJ[0][2] * (fx * o.t[0] / (z * z * z));
+        }
+        if (o.in_y) {
+            gt[1] += gJ[1][2] * (-fy / (z * z));
+            gt[2] += gJ[1][2] * (fy * o.t[1] / (z * z * z));
+        }
+        /* t = W p + w */
+        for (int k = 0; k < 3; ++k) g_means3D[3 * i + k] = V[k] * gt[0] + V[4 + k] * gt[1] + V[8 + k] * gt[2];
+        /* Sigma = M M^T, M = R S */
+        double gM[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 3; ++k)
+                gM[r][k] = 2.0 * (gSig[r][0] * o.M[0][k] + gSig[r][1] * o.M[1][k] + gSig[r][2] * o.M[2][k]);
+        double gR[3][3];
+        for (int k = 0; k < 3; ++k) {
+            double gs = 0.0;
+            for (int r = 0; r < 3; ++r) {
+                gs += gM[r][k] * o.R[r][k];
+                gR[r][k] = gM[r][k] * o.s[k];
+            }
+            g_log_scales[3 * i + k] = gs * o.s[k];
+        }
+        /* R(q), q normalised (w, x, y, z) */
+        const double w = o.q[0], x = o.q[1], y = o.q[2], zq = o.q[3];
+        double gq[4];
+        gq[0] = 2.0 * (-zq * gR[0][1] + y * gR[0][2] + zq * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
+        gq[1] = 2.0 * (y * gR[0][1] + zq * gR[0][2] + y * gR[1][0] - 2.0 * x * gR[1][1] - w * gR[1][2] + zq * gR[2][0] +
+                       w * gR[2][1] - 2.0 * x * gR[2][2]);
+        gq[2] = 2.0 * (-2.0 * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] + zq * gR[1][2] - w * gR[2][0] +
+                       zq * gR[2][1] - 2.0 * y * gR[2][2]);
+        gq[3] = 2.0 * (-2.0 * zq * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] - 2.0 * zq * gR[1][1] +
+                       y * gR[1][2] + x * gR[2][0] + y * gR[2][1]);
+        const double dot = o.q[0] * gq[0] + o.q[1] * gq[1] + o.q[2] * gq[2] + o.q[3] * gq[3];
+        for (int k = 0; k < 4; ++k) g_quats[4 * i + k] = (gq[k] - o.q[k] * dot) / o.qn;
     }
 }
 

@@ -450,3 +450,88 @@ def test_oracle_regression_snapshot():
         stored[k] = float(v)
     for k, v in mg.snapshot():
         assert v == pytest.approx(stored[k], rel=1e-12, abs=1e-15), k
+
+
+# --------------------------------------------------------------------- projection backward
+
+def _projection_fd_scene():
+    """40 anisotropic Gaussians seen by a rotated, translated camera: quaternions of
+    non-unit norm, a third of the centres beyond the tangent clamp (|x/z| well above
+    1.3 tan(fov/2)), none within 5 % of the clamp edge."""
+    rng = np.random.default_rng(11)
+    cam = scenes.look_at_camera(96, 64, eye=(0.3, -0.2, -1.0), target=(0.1, 0.05, 3.0))
+    cam["lowpass"] = 0.3
+    n = 40
+    V = cam["viewmat"]
+    lim_x, lim_y = 1.3 * cam["W"] / (2 * cam["fx"]), 1.3 * cam["H"] / (2 * cam["fy"])
+    pts = []
+    while len(pts) < n:
+        z = rng.uniform(1.5, 5.0)
+        tx = rng.uniform(-2.2, 2.2) * lim_x * z if len(pts) % 3 == 0 else rng.uniform(-0.9, 0.9) * lim_x * z
+        ty = rng.uniform(-0.9, 0.9) * lim_y * z
+        if abs(abs(tx / z) - lim_x) < 0.05 * lim_x:
+            continue
+        t = np.array([tx, ty, z])
+        pts.append(np.linalg.solve(V[:3, :3], t - V[:3, 3]))  # world point with camera coords t
+    m3 = np.array(pts)
+    ls = rng.normal(-2.0, 0.6, (n, 3))
+    q = rng.normal(size=(n, 4)) * rng.uniform(0.5, 2.0, (n, 1))
+    return m3, ls, q, cam
+
+
+def test_projection_backward_matches_central_differences():
+    m3, ls, q, cam = _projection_fd_scene()
+    n = m3.shape[0]
+    rng = np.random.default_rng(12)
+    gm, gc, gd = rng.normal(size=(n, 2)), rng.normal(size=(n, 3)) * 100.0, rng.normal(size=n)
+    base = oracle.project64(m3, ls, q, cam)
+    assert base["valid"].all()
+    got = oracle.preprocess_backward(m3, ls, q, cam, gm, gc, gd)
+
+    def loss(m3_, ls_, q_):
+        o = oracle.project64(m3_, ls_, q_, cam)
+        return np.sum(gm * o["means2D"], axis=1) + np.sum(gc * o["conic"], axis=1) + gd * o["depth"]
+
+    for name, arr in (("means3D", m3), ("log_scales", ls), ("quats", q)):
+        fd = np.zeros_like(arr)
+        for k in range(arr.shape[1]):
+            h = 1e-6 * np.maximum(1.0, np.abs(arr[:, k]))
+            a_p, a_m = arr.copy(), arr.copy()
+            a_p[:, k] += h
+            a_m[:, k] -= h
+            args_p = [m3, ls, q]
+            args_m = [m3, ls, q]
+            idx = ("means3D", "log_scales", "quats").index(name)
+            args_p[idx], args_m[idx] = a_p, a_m
+            fd[:, k] = (loss(*args_p) - loss(*args_m)) / (2 * h)  # per-Gaussian losses are independent
+        scale = np.abs(fd).max(axis=1, keepdims=True) + 1e-12
+        err = np.abs(got[name] - fd) / scale
+        assert err.max() < 1e-5, (name, float(err.max()))
+
+
+def test_projection_backward_zero_for_culled_and_radius_zero():
+    m3, ls, q, cam = _projection_fd_scene()
+    n = m3.shape[0]
+    m3 = m3.copy()
+    # Gaussian 0 behind the near plane
+    V = cam["viewmat"]
+    m3[0] = np.linalg.solve(V[:3, :3], np.array([0.0, 0.0, 0.1]) - V[:3, 3])
+    radius = np.ones(n, np.int32)
+    radius[1] = 0  # off-screen: passes no gradient
+    g = oracle.preprocess_backward(m3, ls, q, cam, np.ones((n, 2)), np.ones((n, 3)), np.ones(n), radius=radius)
+    for k in ("means3D", "log_scales", "quats"):
+        assert not g[k][:2].any(), k
+        assert np.abs(g[k][2:]).sum() > 0, k
+
+
+def test_projection_backward_quaternion_gradient_is_tangent():
+    """The projection depends on q only through q / |q|: the gradient is orthogonal to q
+    and scales as 1 / |q|."""
+    m3, ls, q, cam = _projection_fd_scene()
+    n = m3.shape[0]
+    rng = np.random.default_rng(13)
+    gm, gc = rng.normal(size=(n, 2)), rng.normal(size=(n, 3))
+    g1 = oracle.preprocess_backward(m3, ls, q, cam, gm, gc)["quats"]
+    g2 = oracle.preprocess_backward(m3, ls, 2.0 * q, cam, gm, gc)["quats"]
+    np.testing.assert_allclose(np.sum(g1 * q, axis=1), 0.0, atol=1e-9 * np.abs(g1).max())
+    np.testing.assert_allclose(g2, 0.5 * g1, rtol=1e-9, atol=1e-15)
