@@ -144,13 +144,30 @@ int bgs_preprocess(bgs_plan *plan, int64_t N, const float *means3D, const float 
                    int32_t tile_h, float *means2D, float *conic_opacity, float *depths, int32_t *radii,
                    uint32_t *tiles_touched, void *stream);
 
-/* ---- a2: binning with key duplication (point_list of Algorithms 1-6) ---------------
+/* ---- projection backward (the chain rule through Eq. 2-3; the paper prints none) ---
+   Given dL/dmeans2D [N,2] (8-byte aligned), dL/dconic [N,3] (w.r.t. a, b, c as output by
+   bgs_preprocess and consumed by the render; bgs_render_backward's dL_dconic) and
+   dL/ddepths [N] (nullable), writes dL/dmeans3D [N,3], dL/dlog_scales [N,3] and
+   dL/dquats [N,4] (w.r.t. the unnormalised input quaternion), overwriting them.  The
+   projection is recomputed from the same inputs and camera as bgs_preprocess; Gaussians
+   whose radii[i] is 0 (culled, or touching no tile) get zero.  The tangent clamp passes no
+   gradient to the clamped coordinate.  The opacity and colour gradients of the render
+   need no projection step (the render consumes opacities and colours as given). */
+int bgs_preprocess_backward(bgs_plan *plan, int64_t N, const float *means3D, const float *log_scales,
+                            const float *quats, const bgs_camera *cam, const int32_t *radii,
+                            const float *dL_dmeans2D, const float *dL_dconic, const float *dL_ddepths,
+                            float *dL_dmeans3D, float *dL_dlog_scales, float *dL_dquats, void *stream);
+
+/* ---- a2: binning: per-tile depth-ordered lists (point_list of Algorithms 1-6) --------
    Gaussian i with radius r > 0 covers the tiles x in [floor((u-r)/tw),
    floor((u+(r+tw-1))/tw)), y likewise, clamped to the tile grid (float32, one rounding
-   per operation).  For every covered tile one entry (key = tile << 32 | float bits of
-   depth, value = i) is emitted; entries are radix-sorted by key, stably, so ties in
-   depth keep ascending i.  point_list [capacity] receives the sorted values and
-   ranges [T,2] (T = tiles_x * tiles_y) the half-open span of each tile (0,0 if empty).
+   per operation).  Tile t's list holds the Gaussians covering t ordered by (float32
+   depth bits, i) -- what a stable sort of (tile << 32 | depth bits, i) keys over all
+   covered (tile, Gaussian) pairs gives; it is built by a depth sort of the N Gaussians
+   and a counting sort over their tile rectangles (a stable radix sort on the tile id
+   when the tile grid is too large for the counters).  point_list [capacity] receives
+   the lists one after the other and ranges [T,2] (T = tiles_x * tiles_y) the half-open
+   span of each tile (0,0 if empty).
    If the entry count K exceeds `capacity`, *needed (host, nullable) receives K,
    BGS_ERR_CAPACITY is returned and point_list / ranges are unspecified (nothing is
    written past capacity).  *num_rendered (host, nullable) receives K.  This call
@@ -220,6 +237,14 @@ int bgs_preprocess_batched(bgs_plan *plan, int32_t V, const bgs_view *views, int
                            const float *log_scales, const float *quats, const float *opacities, int32_t tile_w,
                            int32_t tile_h, float *means2D, float *conic_opacity, float *depths, int32_t *radii,
                            uint32_t *tiles_touched, void *stream);
+/* Projection backward of the batched projection: records v * N + g (radii, dL_dmeans2D,
+   dL_dconic, dL_ddepths are [V * N, ...]); the gradients of Gaussian g [N, ...] are summed
+   over the views. */
+int bgs_preprocess_backward_batched(bgs_plan *plan, int32_t V, const bgs_view *views, int64_t N,
+                                    const float *means3D, const float *log_scales, const float *quats,
+                                    const int32_t *radii, const float *dL_dmeans2D, const float *dL_dconic,
+                                    const float *dL_ddepths, float *dL_dmeans3D, float *dL_dlog_scales,
+                                    float *dL_dquats, void *stream);
 /* Binning (as bgs_bin_and_sort) of the V * N records into the global tile space: each
    view's lists are built in its own tile range, in view order, and point_list values are
    record indices.  Without BGS_BIN_NO_SYNC the call synchronises once at its end, returns

@@ -33,6 +33,7 @@ EXPORTS = [
     "bgs_plan_num_sms", "bgs_last_error", "bgs_preprocess", "bgs_bin_and_sort", "bgs_render_forward",
     "bgs_render_backward", "bgs_probe_pipe_rates", "bgs_debug_exp2", "bgs_plan_timing", "bgs_plan_kernel_ms",
     "bgs_render_forward_noalloc", "bgs_preprocess_batched", "bgs_bin_and_sort_batched",
+    "bgs_preprocess_backward", "bgs_preprocess_backward_batched",
     "bgs_render_forward_batched", "bgs_render_backward_batched", "bgs_graph_begin", "bgs_graph_end",
     "bgs_graph_launch", "bgs_autotune_render",
 ]
@@ -118,6 +119,8 @@ def load(build_if_needed: bool = True):
         lib.bgs_debug_exp2.argtypes = [P, P, i64, P]
         VP = ctypes.POINTER(View)
         lib.bgs_preprocess_batched.argtypes = [P, i32, VP, i64, P, P, P, P, i32, i32, P, P, P, P, P, P]
+        lib.bgs_preprocess_backward.argtypes = [P, i64, P, P, P, ctypes.POINTER(Camera), P, P, P, P, P, P, P, P]
+        lib.bgs_preprocess_backward_batched.argtypes = [P, i32, VP, i64, P, P, P, P, P, P, P, P, P, P, P]
         lib.bgs_bin_and_sort_batched.argtypes = [P, i32, VP, i64, P, P, P, i32, i32, P, i64, P, i32,
                                                  ctypes.POINTER(i64), ctypes.POINTER(i64), P]
         lib.bgs_render_forward_batched.argtypes = [P, i32, VP, i64, P, P, P, P, P, i64, P, i32, i32, P, i32, P]

@@ -221,6 +221,12 @@ cudaError_t launch_preprocess(long long N, int V, const float *means3D, const fl
                               const float *opacities, const bgs_camera *cams, int tile_w, int tile_h,
                               float *means2D, float *conic_opacity, float *depths, int *radii,
                               uint32_t *tiles_touched, cudaStream_t s);
+// projection backward: dL/d(means2D, conic a b c, depth) of the records [V N] ->
+// dL/d(means3D, log_scales, quats) [N] summed over the views (radius-0 records skipped)
+cudaError_t launch_preprocess_backward(long long N, int V, const float *means3D, const float *log_scales,
+                                       const float *quats, const bgs_camera *cams, const int *radii,
+                                       const float *dL_dmeans2D, const float *dL_dconic, const float *dL_ddepths,
+                                       float *dL_dmeans3D, float *dL_dlog_scales, float *dL_dquats, cudaStream_t s);
 cudaError_t launch_depth_keys64(long long N, int V, const float *depths, unsigned long long *keys, uint32_t *idx,
                                 cudaStream_t s);
 

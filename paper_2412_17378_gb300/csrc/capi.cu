@@ -517,6 +517,27 @@ int bgs_preprocess(bgs_plan *p, int64_t N, const float *means3D, const float *lo
     return BGS_OK;
 }
 
+int bgs_preprocess_backward(bgs_plan *p, int64_t N, const float *means3D, const float *log_scales,
+                            const float *quats, const bgs_camera *cam, const int32_t *radii, const float *dL_dmeans2D,
+                            const float *dL_dconic, const float *dL_ddepths, float *dL_dmeans3D,
+                            float *dL_dlog_scales, float *dL_dquats, void *stream) {
+    if (!p || !cam) return fail(BGS_ERR_INVALID, "bgs_preprocess_backward: NULL plan or camera");
+    if (N < 0 || N >= (1ll << 32)) return fail(BGS_ERR_INVALID, "bgs_preprocess_backward: N out of range");
+    if (N > 0 && (!means3D || !log_scales || !quats || !radii || !dL_dmeans2D || !dL_dconic || !dL_dmeans3D ||
+                  !dL_dlog_scales || !dL_dquats))
+        return fail(BGS_ERR_INVALID, "bgs_preprocess_backward: NULL array");
+    if (((uintptr_t)dL_dmeans2D) & 7) return fail(BGS_ERR_INVALID, "bgs_preprocess_backward: dL_dmeans2D alignment");
+    BGS_TRY(check_image(cam->width, cam->height));
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f))
+        return fail(BGS_ERR_INVALID, "bgs_preprocess_backward: focal lengths must be > 0");
+    DeviceGuard g(p->device);
+    BGS_CUDA(bgs::launch_preprocess_backward(N, 1, means3D, log_scales, quats, cam, radii, dL_dmeans2D, dL_dconic,
+                                             dL_ddepths, dL_dmeans3D, dL_dlog_scales, dL_dquats, (cudaStream_t)stream),
+             "preprocess_backward");
+    if (N > 0) p->host_launches += 1;
+    return BGS_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -924,6 +945,33 @@ int bgs_preprocess_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_
     BGS_CUDA(bgs::launch_preprocess(N, V, means3D, log_scales, quats, opacities, cams, tw, th, means2D, conic_opacity,
                                     depths, radii, tiles_touched, (cudaStream_t)stream),
              "preprocess_batched");
+    if (N > 0) p->host_launches += 1;
+    return BGS_OK;
+}
+
+int bgs_preprocess_backward_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means3D,
+                                    const float *log_scales, const float *quats, const int32_t *radii,
+                                    const float *dL_dmeans2D, const float *dL_dconic, const float *dL_ddepths,
+                                    float *dL_dmeans3D, float *dL_dlog_scales, float *dL_dquats, void *stream) {
+    if (!p || !views) return fail(BGS_ERR_INVALID, "bgs_preprocess_backward_batched: NULL plan or views");
+    if (V < 1 || V > bgs::kMaxViews) return fail(BGS_ERR_INVALID, "bgs_preprocess_backward_batched: V=%d", V);
+    if (N < 0 || N * V >= (1ll << 32)) return fail(BGS_ERR_INVALID, "bgs_preprocess_backward_batched: N out of range");
+    if (N > 0 && (!means3D || !log_scales || !quats || !radii || !dL_dmeans2D || !dL_dconic || !dL_dmeans3D ||
+                  !dL_dlog_scales || !dL_dquats))
+        return fail(BGS_ERR_INVALID, "bgs_preprocess_backward_batched: NULL array");
+    if (((uintptr_t)dL_dmeans2D) & 7)
+        return fail(BGS_ERR_INVALID, "bgs_preprocess_backward_batched: dL_dmeans2D alignment");
+    bgs_camera cams[bgs::kMaxViews];
+    for (int v = 0; v < V; ++v) {
+        BGS_TRY(check_image(views[v].cam.width, views[v].cam.height));
+        if (!(views[v].cam.fx > 0.f) || !(views[v].cam.fy > 0.f))
+            return fail(BGS_ERR_INVALID, "bgs_preprocess_backward_batched: focal lengths must be > 0");
+        cams[v] = views[v].cam;
+    }
+    DeviceGuard g(p->device);
+    BGS_CUDA(bgs::launch_preprocess_backward(N, V, means3D, log_scales, quats, cams, radii, dL_dmeans2D, dL_dconic,
+                                             dL_ddepths, dL_dmeans3D, dL_dlog_scales, dL_dquats, (cudaStream_t)stream),
+             "preprocess_backward_batched");
     if (N > 0) p->host_launches += 1;
     return BGS_OK;
 }

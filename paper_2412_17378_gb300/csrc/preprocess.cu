@@ -33,6 +33,88 @@ __device__ __forceinline__ void tile_rect(float u, float v, int r, int tw, int t
     y1 = min(max(y1, 0), ty);
 }
 
+// FP32 intermediates of one Gaussian's projection into one view (Eq. 1-3): the forward
+// kernel reads the outputs, the backward kernel recomputes them to apply the chain rule.
+struct Proj {
+    float tx, ty, tz, iz;          // camera-space centre, 1 / z
+    float qw, qx, qy, qz, qn;      // normalised quaternion and the input's norm
+    float R[3][3], s[3];           // rotation, scales
+    float M[3][3];                 // R S
+    float S00, S01, S02, S11, S12, S22;  // Sigma = M M^T
+    float clx, cly;                // tangents of the centre, clamped
+    bool in_x, in_y;               // ... and whether the clamp is inactive
+    float J00, J02, J11, J12;      // pinhole Jacobian at the clamped centre
+    float T[2][3];                 // J W
+    float c00, c01, c11, det;      // 2D covariance (+ low-pass) and its determinant
+};
+
+// Returns false when the Gaussian is culled (z <= near or det <= 0); tz is always set.
+__device__ __forceinline__ bool project(const CamDev &cam, const float *__restrict__ means3D,
+                                        const float *__restrict__ log_scales, const float *__restrict__ quats,
+                                        long long g, Proj &o) {
+    const float px = means3D[3 * g], py = means3D[3 * g + 1], pz = means3D[3 * g + 2];
+    const float *V = cam.V;
+    o.tx = V[0] * px + V[1] * py + V[2] * pz + V[3];
+    o.ty = V[4] * px + V[5] * py + V[6] * pz + V[7];
+    o.tz = V[8] * px + V[9] * py + V[10] * pz + V[11];
+    if (!(o.tz > cam.near_plane)) return false;
+    // R from the normalised quaternion (w, x, y, z)
+    float qw = quats[4 * g], qx = quats[4 * g + 1], qy = quats[4 * g + 2], qz = quats[4 * g + 3];
+    o.qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw /= o.qn; qx /= o.qn; qy /= o.qn; qz /= o.qn;
+    o.qw = qw; o.qx = qx; o.qy = qy; o.qz = qz;
+    o.R[0][0] = 1.f - 2.f * (qy * qy + qz * qz); o.R[0][1] = 2.f * (qx * qy - qw * qz); o.R[0][2] = 2.f * (qx * qz + qw * qy);
+    o.R[1][0] = 2.f * (qx * qy + qw * qz); o.R[1][1] = 1.f - 2.f * (qx * qx + qz * qz); o.R[1][2] = 2.f * (qy * qz - qw * qx);
+    o.R[2][0] = 2.f * (qx * qz - qw * qy); o.R[2][1] = 2.f * (qy * qz + qw * qx); o.R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
+    o.s[0] = expf(log_scales[3 * g]);
+    o.s[1] = expf(log_scales[3 * g + 1]);
+    o.s[2] = expf(log_scales[3 * g + 2]);
+    // M = R S ; Sigma = M M^T (symmetric, 6 entries)
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) o.M[r][k] = o.R[r][k] * o.s[k];
+    const float (&M)[3][3] = o.M;
+    o.S00 = M[0][0] * M[0][0] + M[0][1] * M[0][1] + M[0][2] * M[0][2];
+    o.S01 = M[0][0] * M[1][0] + M[0][1] * M[1][1] + M[0][2] * M[1][2];
+    o.S02 = M[0][0] * M[2][0] + M[0][1] * M[2][1] + M[0][2] * M[2][2];
+    o.S11 = M[1][0] * M[1][0] + M[1][1] * M[1][1] + M[1][2] * M[1][2];
+    o.S12 = M[1][0] * M[2][0] + M[1][1] * M[2][1] + M[1][2] * M[2][2];
+    o.S22 = M[2][0] * M[2][0] + M[2][1] * M[2][1] + M[2][2] * M[2][2];
+    // Jacobian of the pinhole map at the tangent-clamped point
+    o.iz = 1.f / o.tz;
+    const float ux = o.tx * o.iz, uy = o.ty * o.iz;
+    o.in_x = ux >= -cam.lim_x && ux <= cam.lim_x;
+    o.in_y = uy >= -cam.lim_y && uy <= cam.lim_y;
+    o.clx = fminf(cam.lim_x, fmaxf(-cam.lim_x, ux));
+    o.cly = fminf(cam.lim_y, fmaxf(-cam.lim_y, uy));
+    const float xc = o.clx * o.tz, yc = o.cly * o.tz;
+    o.J00 = cam.fx * o.iz;
+    o.J02 = -cam.fx * xc * o.iz * o.iz;
+    o.J11 = cam.fy * o.iz;
+    o.J12 = -cam.fy * yc * o.iz * o.iz;
+    // T = J W (2x3)
+    o.T[0][0] = o.J00 * V[0] + o.J02 * V[8];
+    o.T[0][1] = o.J00 * V[1] + o.J02 * V[9];
+    o.T[0][2] = o.J00 * V[2] + o.J02 * V[10];
+    o.T[1][0] = o.J11 * V[4] + o.J12 * V[8];
+    o.T[1][1] = o.J11 * V[5] + o.J12 * V[9];
+    o.T[1][2] = o.J11 * V[6] + o.J12 * V[10];
+    const float (&T)[2][3] = o.T;
+    // Sigma' = T Sigma T^T
+    const float U00 = o.S00 * T[0][0] + o.S01 * T[0][1] + o.S02 * T[0][2];  // (Sigma T^T) column 0
+    const float U10 = o.S01 * T[0][0] + o.S11 * T[0][1] + o.S12 * T[0][2];
+    const float U20 = o.S02 * T[0][0] + o.S12 * T[0][1] + o.S22 * T[0][2];
+    const float U01 = o.S00 * T[1][0] + o.S01 * T[1][1] + o.S02 * T[1][2];  // column 1
+    const float U11 = o.S01 * T[1][0] + o.S11 * T[1][1] + o.S12 * T[1][2];
+    const float U21 = o.S02 * T[1][0] + o.S12 * T[1][1] + o.S22 * T[1][2];
+    o.c00 = T[0][0] * U00 + T[0][1] * U10 + T[0][2] * U20 + cam.lowpass;
+    o.c01 = T[0][0] * U01 + T[0][1] * U11 + T[0][2] * U21;
+    o.c11 = T[1][0] * U01 + T[1][1] * U11 + T[1][2] * U21 + cam.lowpass;
+    o.det = o.c00 * o.c11 - o.c01 * o.c01;
+    return o.det > 0.f;
+}
+
 // Record i = v * N + g projects Gaussian g into view v (one view for the single-view call).
 __global__ void __launch_bounds__(256) k_preprocess(long long N, const float *__restrict__ means3D,
                                                     const float *__restrict__ log_scales,
@@ -46,76 +128,151 @@ __global__ void __launch_bounds__(256) k_preprocess(long long N, const float *__
     const int view = (int)(rec / N);
     const long long g = rec - (long long)view * N;
     const CamDev &cam = ct.cam[view];
-    const float px = means3D[3 * g], py = means3D[3 * g + 1], pz = means3D[3 * g + 2];
-    const float *V = cam.V;
-    const float tx = V[0] * px + V[1] * py + V[2] * pz + V[3];
-    const float ty = V[4] * px + V[5] * py + V[6] * pz + V[7];
-    const float tz = V[8] * px + V[9] * py + V[10] * pz + V[11];
+    Proj o;
+    const bool ok = project(cam, means3D, log_scales, quats, g, o);
     float2 m2 = make_float2(0.f, 0.f);
     float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
     int radius = 0;
     uint32_t touched = 0;
-    depths[rec] = tz;
-    if (tz > cam.near_plane) {
-        // R from the normalised quaternion (w, x, y, z)
-        float qw = quats[4 * g], qx = quats[4 * g + 1], qy = quats[4 * g + 2], qz = quats[4 * g + 3];
-        const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-        qw /= qn; qx /= qn; qy /= qn; qz /= qn;
-        const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
-        const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
-        const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
-        const float s0 = expf(log_scales[3 * g]), s1 = expf(log_scales[3 * g + 1]), s2 = expf(log_scales[3 * g + 2]);
-        // M = R S ; Sigma = M M^T (symmetric, 6 entries)
-        const float M00 = R00 * s0, M01 = R01 * s1, M02 = R02 * s2;
-        const float M10 = R10 * s0, M11 = R11 * s1, M12 = R12 * s2;
-        const float M20 = R20 * s0, M21 = R21 * s1, M22 = R22 * s2;
-        const float S00 = M00 * M00 + M01 * M01 + M02 * M02;
-        const float S01 = M00 * M10 + M01 * M11 + M02 * M12;
-        const float S02 = M00 * M20 + M01 * M21 + M02 * M22;
-        const float S11 = M10 * M10 + M11 * M11 + M12 * M12;
-        const float S12 = M10 * M20 + M11 * M21 + M12 * M22;
-        const float S22 = M20 * M20 + M21 * M21 + M22 * M22;
-        // Jacobian of the pinhole map at the tangent-clamped point
-        const float iz = 1.f / tz;
-        const float xc = fminf(cam.lim_x, fmaxf(-cam.lim_x, tx * iz)) * tz;
-        const float yc = fminf(cam.lim_y, fmaxf(-cam.lim_y, ty * iz)) * tz;
-        const float J00 = cam.fx * iz, J02 = -cam.fx * xc * iz * iz;
-        const float J11 = cam.fy * iz, J12 = -cam.fy * yc * iz * iz;
-        // T = J W (2x3)
-        const float T00 = J00 * V[0] + J02 * V[8], T01 = J00 * V[1] + J02 * V[9], T02 = J00 * V[2] + J02 * V[10];
-        const float T10 = J11 * V[4] + J12 * V[8], T11 = J11 * V[5] + J12 * V[9], T12 = J11 * V[6] + J12 * V[10];
-        // Sigma' = T Sigma T^T
-        const float U00 = S00 * T00 + S01 * T01 + S02 * T02;  // (Sigma T^T) column 0
-        const float U10 = S01 * T00 + S11 * T01 + S12 * T02;
-        const float U20 = S02 * T00 + S12 * T01 + S22 * T02;
-        const float U01 = S00 * T10 + S01 * T11 + S02 * T12;  // column 1
-        const float U11 = S01 * T10 + S11 * T11 + S12 * T12;
-        const float U21 = S02 * T10 + S12 * T11 + S22 * T12;
-        const float c00 = T00 * U00 + T01 * U10 + T02 * U20 + cam.lowpass;
-        const float c01 = T00 * U01 + T01 * U11 + T02 * U21;
-        const float c11 = T10 * U01 + T11 * U11 + T12 * U21 + cam.lowpass;
-        const float det = c00 * c11 - c01 * c01;
-        if (det > 0.f) {
-            const float mid = 0.5f * (c00 + c11);
-            const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
-            const int r = (int)ceilf(3.f * sqrtf(lam));
-            const float idet = 1.f / det;
-            const float u = cam.fx * tx * iz + cam.cx, v = cam.fy * ty * iz + cam.cy;
-            m2 = make_float2(u, v);
-            co = make_float4(c11 * idet, -c01 * idet, c00 * idet, opacities[g]);
-            int x0, x1, y0, y1;
-            tile_rect(u, v, r, cam.tile_w, cam.tile_h, cam.tiles_x, cam.tiles_y, x0, x1, y0, y1);
-            const long long area = (long long)(x1 - x0) * (long long)(y1 - y0);
-            if (area > 0) {
-                radius = r;
-                touched = (uint32_t)area;
-            }
+    depths[rec] = o.tz;
+    if (ok) {
+        const float mid = 0.5f * (o.c00 + o.c11);
+        const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - o.det));
+        const int r = (int)ceilf(3.f * sqrtf(lam));
+        const float idet = 1.f / o.det;
+        const float u = cam.fx * o.tx * o.iz + cam.cx, v = cam.fy * o.ty * o.iz + cam.cy;
+        m2 = make_float2(u, v);
+        co = make_float4(o.c11 * idet, -o.c01 * idet, o.c00 * idet, opacities[g]);
+        int x0, x1, y0, y1;
+        tile_rect(u, v, r, cam.tile_w, cam.tile_h, cam.tiles_x, cam.tiles_y, x0, x1, y0, y1);
+        const long long area = (long long)(x1 - x0) * (long long)(y1 - y0);
+        if (area > 0) {
+            radius = r;
+            touched = (uint32_t)area;
         }
     }
     means2D[rec] = m2;
     conic_opacity[rec] = co;
     radii[rec] = radius;
     tiles_touched[rec] = touched;
+}
+
+// Projection backward: thread per Gaussian, summing its records over the views.  Records
+// with radius 0 pass no gradient.  The chain rule through the projection above:
+//   conic = (C, -B, A) / det of C2 = (A B; B C), det = A C - B^2;
+//   C2 = T Sigma T^T + lowpass I with T = J W: dL/dSigma = T^T G T, dL/dT = 2 G T Sigma
+//     (G = dL/dC2, its off-diagonal entry half of dL/dB);
+//   J(t) at the clamped tangent (the clamped coordinate carries no x / y gradient);
+//   means2D = (fx x / z + cx, fy y / z + cy), depth = z, t = W p + w;
+//   Sigma = M M^T, M = R S: dL/dM = 2 dL/dSigma M, dL/dlog s_k = s_k sum_r dL/dM_rk R_rk,
+//   dL/dR = dL/dM S, then R(q) and the Jacobian of q / |q|.
+__global__ void __launch_bounds__(256) k_preprocess_backward(long long N, const float *__restrict__ means3D,
+                                                             const float *__restrict__ log_scales,
+                                                             const float *__restrict__ quats, const CamTable ct,
+                                                             const int *__restrict__ radii,
+                                                             const float2 *__restrict__ dL_dmeans2D,
+                                                             const float *__restrict__ dL_dconic,
+                                                             const float *__restrict__ dL_ddepths,
+                                                             float *__restrict__ dL_dmeans3D,
+                                                             float *__restrict__ dL_dlog_scales,
+                                                             float *__restrict__ dL_dquats) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N) return;
+    float gp[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int view = 0; view < ct.V; ++view) {
+        const long long rec = (long long)view * N + g;
+        if (radii[rec] <= 0) continue;
+        const CamDev &cam = ct.cam[view];
+        Proj o;
+        if (!project(cam, means3D, log_scales, quats, g, o)) continue;
+        const float *V = cam.V;
+        const float2 gm = dL_dmeans2D[rec];
+        const float ga = dL_dconic[3 * rec], gb = dL_dconic[3 * rec + 1], gc = dL_dconic[3 * rec + 2];
+        const float iz2 = o.iz * o.iz;
+        // means2D and depth
+        float gtx = gm.x * cam.fx * o.iz, gty = gm.y * cam.fy * o.iz;
+        float gtz = (dL_ddepths ? dL_ddepths[rec] : 0.f) - (gm.x * cam.fx * o.tx + gm.y * cam.fy * o.ty) * iz2;
+        // conic -> G = dL/dC2
+        const float A = o.c00, B = o.c01, C = o.c11;
+        const float idet = 1.f / o.det, id2 = idet * idet;
+        const float dA = (-C * C * ga + B * C * gb - B * B * gc) * id2;
+        const float dC = (-B * B * ga + A * B * gb - A * A * gc) * id2;
+        const float hB = (B * C * ga - B * B * gb + A * B * gc) * id2 - 0.5f * gb * idet;  // dL/dB / 2
+        // dL/dSigma = T^T G T (symmetric)
+        const float (&T)[2][3] = o.T;
+        float GT[2][3];  // G T
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            GT[0][k] = dA * T[0][k] + hB * T[1][k];
+            GT[1][k] = hB * T[0][k] + dC * T[1][k];
+        }
+        float gS[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) gS[a][b] = T[0][a] * GT[0][b] + T[1][a] * GT[1][b];
+        // dL/dT = 2 G T Sigma
+        const float Sg[3][3] = {{o.S00, o.S01, o.S02}, {o.S01, o.S11, o.S12}, {o.S02, o.S12, o.S22}};
+        float gT[2][3];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gT[r][k] = 2.f * (GT[r][0] * Sg[0][k] + GT[r][1] * Sg[1][k] + GT[r][2] * Sg[2][k]);
+        // T = J W: the four nonzero entries of J
+        const float gJ00 = gT[0][0] * V[0] + gT[0][1] * V[1] + gT[0][2] * V[2];
+        const float gJ02 = gT[0][0] * V[8] + gT[0][1] * V[9] + gT[0][2] * V[10];
+        const float gJ11 = gT[1][0] * V[4] + gT[1][1] * V[5] + gT[1][2] * V[6];
+        const float gJ12 = gT[1][0] * V[8] + gT[1][1] * V[9] + gT[1][2] * V[10];
+        // J00 = fx / z, J02 = -fx cl(x / z) / z, J11 = fy / z, J12 = -fy cl(y / z) / z
+        gtz += (-gJ00 * cam.fx - gJ11 * cam.fy + gJ02 * cam.fx * o.clx + gJ12 * cam.fy * o.cly) * iz2;
+        if (o.in_x) {
+            gtx -= gJ02 * cam.fx * iz2;
+            gtz += gJ02 * cam.fx * o.tx * iz2 * o.iz;
+        }
+        if (o.in_y) {
+            gty -= gJ12 * cam.fy * iz2;
+            gtz += gJ12 * cam.fy * o.ty * iz2 * o.iz;
+        }
+        // t = W p + w
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gp[k] += V[k] * gtx + V[4 + k] * gty + V[8 + k] * gtz;
+        // Sigma = M M^T, M = R S
+        float gR[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float gs = 0.f;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const float gM = 2.f * (gS[r][0] * o.M[0][k] + gS[r][1] * o.M[1][k] + gS[r][2] * o.M[2][k]);
+                gs += gM * o.R[r][k];
+                gR[r][k] = gM * o.s[k];
+            }
+            gls[k] += gs * o.s[k];
+        }
+        // R(q) of the normalised quaternion, then d(q / |q|)
+        const float w = o.qw, x = o.qx, y = o.qy, z = o.qz;
+        float dq[4];
+        dq[0] = 2.f * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
+        dq[1] = 2.f * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2.f * x * gR[1][1] - w * gR[1][2] + z * gR[2][0] +
+                       w * gR[2][1] - 2.f * x * gR[2][2]);
+        dq[2] = 2.f * (-2.f * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] + z * gR[1][2] -
+                       w * gR[2][0] + z * gR[2][1] - 2.f * y * gR[2][2]);
+        dq[3] = 2.f * (-2.f * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] - 2.f * z * gR[1][1] +
+                       y * gR[1][2] + x * gR[2][0] + y * gR[2][1]);
+        const float dot = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
+        const float iqn = 1.f / o.qn;
+        gq[0] += (dq[0] - w * dot) * iqn;
+        gq[1] += (dq[1] - x * dot) * iqn;
+        gq[2] += (dq[2] - y * dot) * iqn;
+        gq[3] += (dq[3] - z * dot) * iqn;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dL_dmeans3D[3 * g + k] = gp[k];
+        dL_dlog_scales[3 * g + k] = gls[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dL_dquats[4 * g + k] = gq[k];
 }
 
 static CamDev cam_dev(const bgs_camera &c, int tile_w, int tile_h) {
@@ -148,6 +305,21 @@ cudaError_t launch_preprocess(long long N, int V, const float *means3D, const fl
                                                        reinterpret_cast<float2 *>(means2D),
                                                        reinterpret_cast<float4 *>(conic_opacity), depths, radii,
                                                        tiles_touched);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_backward(long long N, int V, const float *means3D, const float *log_scales,
+                                       const float *quats, const bgs_camera *cams, const int *radii,
+                                       const float *dL_dmeans2D, const float *dL_dconic, const float *dL_ddepths,
+                                       float *dL_dmeans3D, float *dL_dlog_scales, float *dL_dquats, cudaStream_t s) {
+    if (V < 1 || V > kMaxViews) return cudaErrorInvalidValue;
+    CamTable ct;
+    ct.V = V;
+    for (int v = 0; v < V; ++v) ct.cam[v] = cam_dev(cams[v], 16, 16);
+    if (N == 0) return cudaSuccess;
+    k_preprocess_backward<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
+        N, means3D, log_scales, quats, ct, radii, reinterpret_cast<const float2 *>(dL_dmeans2D), dL_dconic,
+        dL_ddepths, dL_dmeans3D, dL_dlog_scales, dL_dquats);
     return cudaGetLastError();
 }
 

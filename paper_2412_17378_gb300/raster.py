@@ -17,7 +17,8 @@ import torch
 from . import _lib
 from ._lib import MODES, BgsError, check
 
-__all__ = ["Plan", "camera_struct", "preprocess", "bin_and_sort", "render_forward", "render_backward",
+__all__ = ["Plan", "camera_struct", "preprocess", "preprocess_backward", "bin_and_sort", "render_forward",
+           "render_backward", "PreprocessFunction",
            "render_forward_noalloc",
            "RenderFunction", "render", "probe_pipe_rates", "debug_exp2", "BgsError", "MODES"]
 
@@ -148,6 +149,36 @@ def preprocess(plan: Plan, means3D, log_scales, quats, opacities, cam: dict, til
                                    ctypes.byref(c), tile[0], tile[1], _ptr(out["means2D"]),
                                    _ptr(out["conic_opacity"]), _ptr(out["depths"]), _ptr(out["radii"]),
                                    _ptr(out["tiles_touched"]), _stream(dev)), "bgs_preprocess")
+    return out
+
+
+def _grads_out(N, dev, out):
+    if out is None:
+        out = dict(means3D=torch.empty((N, 3), device=dev), log_scales=torch.empty((N, 3), device=dev),
+                   quats=torch.empty((N, 4), device=dev))
+    return out
+
+
+def preprocess_backward(plan: Plan, means3D, log_scales, quats, cam: dict, radii, dL_dmeans2D, dL_dconic,
+                        dL_ddepths=None, out=None):
+    """bgs_preprocess_backward: dL/d(means2D [N,2], conic [N,3], depths [N]) -> dict of
+    dL/d(means3D [N,3], log_scales [N,3], quats [N,4])."""
+    N = means3D.shape[0]
+    _req(means3D, "means3D", torch.float32, (N, 3))
+    _req(log_scales, "log_scales", torch.float32, (N, 3))
+    _req(quats, "quats", torch.float32, (N, 4))
+    _req(radii, "radii", torch.int32, (N,))
+    _req(dL_dmeans2D, "dL_dmeans2D", torch.float32, (N, 2))
+    _req(dL_dconic, "dL_dconic", torch.float32, (N, 3))
+    if dL_ddepths is not None:
+        _req(dL_ddepths, "dL_ddepths", torch.float32, (N,))
+    dev = means3D.device
+    out = _grads_out(N, dev, out)
+    c = camera_struct(cam)
+    check(plan._lib.bgs_preprocess_backward(plan.handle, N, _ptr(means3D), _ptr(log_scales), _ptr(quats),
+                                            ctypes.byref(c), _ptr(radii), _ptr(dL_dmeans2D), _ptr(dL_dconic),
+                                            _ptr(dL_ddepths), _ptr(out["means3D"]), _ptr(out["log_scales"]),
+                                            _ptr(out["quats"]), _stream(dev)), "bgs_preprocess_backward")
     return out
 
 
@@ -287,6 +318,32 @@ class RenderFunction(torch.autograd.Function):
         return g["means2D"], d_conic, g["colors"], g["depths"], None, None, None, None, None, None, None
 
 
+class PreprocessFunction(torch.autograd.Function):
+    """Differentiable projection (Eq. 1-3): (means3D, log_scales, quats, opacities) ->
+    (means2D, conic_opacity, depths, radii).  The backward calls bgs_preprocess_backward;
+    the opacity column of conic_opacity passes its gradient straight to opacities."""
+
+    @staticmethod
+    def forward(ctx, means3D, log_scales, quats, opacities, plan, cam, tile):
+        m3, ls, q = means3D.contiguous(), log_scales.contiguous(), quats.contiguous()
+        out = preprocess(plan, m3, ls, q, opacities.contiguous(), cam, tile)
+        ctx.plan, ctx.cam = plan, cam
+        ctx.save_for_backward(m3, ls, q, out["radii"])
+        ctx.mark_non_differentiable(out["radii"])
+        return out["means2D"], out["conic_opacity"], out["depths"], out["radii"]
+
+    @staticmethod
+    def backward(ctx, g_means2D, g_conic_opacity, g_depths, _g_radii):
+        m3, ls, q, radii = ctx.saved_tensors
+        N = m3.shape[0]
+        z = lambda *shape: torch.zeros(shape, device=m3.device)
+        gm = g_means2D.contiguous() if g_means2D is not None else z(N, 2)
+        gco = g_conic_opacity if g_conic_opacity is not None else z(N, 4)
+        gd = g_depths.contiguous() if g_depths is not None else None
+        g = preprocess_backward(ctx.plan, m3, ls, q, ctx.cam, radii, gm, gco[:, :3].contiguous(), gd)
+        return g["means3D"], g["log_scales"], g["quats"], gco[:, 3].contiguous(), None, None, None
+
+
 def render(plan: Plan, means2D, conic_opacity, colors, depths, binning, W, H, tile=(16, 16), bg=(0.0, 0.0, 0.0),
            mode="auto"):
     """Differentiable render; returns (color, depth, alpha)."""
@@ -340,6 +397,31 @@ def preprocess_batched(plan: Plan, means3D, log_scales, quats, opacities, cams, 
                                            _ptr(opacities), tile[0], tile[1], _ptr(out["means2D"]),
                                            _ptr(out["conic_opacity"]), _ptr(out["depths"]), _ptr(out["radii"]),
                                            _ptr(out["tiles_touched"]), _stream(dev)), "bgs_preprocess_batched")
+    return out
+
+
+def preprocess_backward_batched(plan: Plan, means3D, log_scales, quats, cams, radii, dL_dmeans2D, dL_dconic,
+                                dL_ddepths=None, out=None):
+    """bgs_preprocess_backward_batched: record gradients [V*N, ...] -> Gaussian gradients
+    [N, ...] summed over the views."""
+    N, V = means3D.shape[0], len(cams)
+    R = N * V
+    _req(means3D, "means3D", torch.float32, (N, 3))
+    _req(log_scales, "log_scales", torch.float32, (N, 3))
+    _req(quats, "quats", torch.float32, (N, 4))
+    _req(radii, "radii", torch.int32, (R,))
+    _req(dL_dmeans2D, "dL_dmeans2D", torch.float32, (R, 2))
+    _req(dL_dconic, "dL_dconic", torch.float32, (R, 3))
+    if dL_ddepths is not None:
+        _req(dL_ddepths, "dL_ddepths", torch.float32, (R,))
+    dev = means3D.device
+    out = _grads_out(N, dev, out)
+    vw = _views(cams)
+    check(plan._lib.bgs_preprocess_backward_batched(plan.handle, V, vw, N, _ptr(means3D), _ptr(log_scales),
+                                                    _ptr(quats), _ptr(radii), _ptr(dL_dmeans2D), _ptr(dL_dconic),
+                                                    _ptr(dL_ddepths), _ptr(out["means3D"]), _ptr(out["log_scales"]),
+                                                    _ptr(out["quats"]), _stream(dev)),
+          "bgs_preprocess_backward_batched")
     return out
 
 
