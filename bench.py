@@ -74,6 +74,9 @@ def parse():
                     help="render mode of the timed steps")
     ap.add_argument("--knobs", default="",
                     help="plan knobs for the timed steps when not tuning, e.g. pixel_rows=4,heavy_threshold=2147483647")
+    ap.add_argument("--selector-drift", type=int, default=0, metavar="STAGES",
+                    help="run the Sec. 4.4 selector (mode 'select', a timing every stage) over STAGES scenes "
+                         "drifting from config 3-early to 3-late and print its record as one JSON line")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed steps (no tuning, baselines, e2e or oracle): for profiler runs")
     return ap.parse_args()
@@ -308,10 +311,59 @@ def reference_arm(args):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def selector_drift(args):
+    """The self-adaptive selection of Sec. 4.4 over a synthetic training drift: at every
+    stage the selector times the balanced forward against the static pixel-wise forward
+    (select_period = 1) until the static one wins, then keeps it.  Two balanced kernels
+    are guarded: "combined" = the plan defaults (tiles with lists longer than 512 entries
+    rendered Gaussian-wise, the paper's fine-grained combined kernel), and "tuned" = the
+    knobs bgs_autotune_render picks on the first stage."""
+    import torch
+    from paper_2412_17378_gb300 import raster, scenes
+    torch.cuda.set_device(0)
+    plans = {"combined": raster.Plan(select_period=1), "tuned": raster.Plan(select_period=1)}
+    rows = {k: [] for k in plans}
+    tuned = None
+    for k in range(args.selector_drift):
+        frac = k / max(1, args.selector_drift - 1)
+        sc = scenes.drift_scene(frac)
+        g, cam = sc["gaussians"], sc["cameras"][0]
+        W, H = cam["W"], cam["H"]
+        d = {n: torch.from_numpy(v).cuda() for n, v in g.items()}
+        for name, plan in plans.items():
+            pre = raster.preprocess(plan, d["means3D"], d["log_scales"], d["quats"], d["opacities"], cam)
+            pl, rg, K = raster.bin_and_sort(plan, pre["means2D"], pre["radii"], pre["depths"], W, H)
+            if name == "tuned" and tuned is None:
+                _, knobs = raster.autotune_render(plan, pre["means2D"], pre["conic_opacity"], d["colors"],
+                                                  pre["depths"], pl, K, rg, [cam])
+                tuned = {n: knobs[n] for n in ("pixel_rows", "heavy_threshold", "gw_pixels", "queue_chunk")}
+            for m in ("auto", "static"):  # warm both kernels on this frame
+                raster.render_forward(plan, pre["means2D"], pre["conic_opacity"], d["colors"], pre["depths"], pl, K,
+                                      rg, W, H, mode=m)
+            before = plan.selector()
+            raster.render_forward(plan, pre["means2D"], pre["conic_opacity"], d["colors"], pre["depths"], pl, K, rg,
+                                  W, H, mode="select")
+            torch.cuda.synchronize()
+            st = plan.selector()
+            measured = st["measurements"] > before["measurements"]
+            rows[name].append({"stage": k, "frac": round(frac, 3), "gaussians": int(g["means3D"].shape[0]),
+                               "entries": int(K), "balanced_ms": st["balanced_ms"] if measured else None,
+                               "static_ms": st["static_ms"] if measured else None, "switched": st["switched"]})
+    out = {"rule": "Sec. 4.4: time the balanced forward against the static pixel-wise forward every "
+                   "select_period forward calls; switch once, irreversibly", "tuned_knobs": tuned}
+    for name, r in rows.items():
+        out[name] = {"stages": r, "switched_at_stage": next((x["stage"] for x in r if x["switched"]), None)}
+    print(json.dumps({"selector_drift": out}), flush=True)
+    for plan in plans.values():
+        plan.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.selector_drift:
+        return selector_drift(args)
     if args.mode == "static":
         raise SystemExit("--mode static: the static kernel is timed as the baseline of every full run")
     import torch
@@ -483,6 +535,26 @@ def main_views(args, scene, rank, world, local):
         for _ in range(args.steps):
             e2e_step()
         e2e_s = (time.perf_counter() - t0) / args.steps
+        # ---- projection (a1) and its backward alone, CUDA events ----
+        gr = state["gr"]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        pf, pb = [], []
+        for it in range(6):
+            ev[0].record(side)
+            raster.preprocess_batched(plan, d["means3D"], d["log_scales"], d["quats"], d["opacities"], cams,
+                                      out=state["pre"])
+            ev[1].record(side)
+            raster.preprocess_backward_batched(plan, d["means3D"], d["log_scales"], d["quats"], cams, pre["radii"],
+                                               gr["means2D"], gr["conic"], gr.get("depths"))
+            ev[2].record(side)
+            side.synchronize()
+            if it >= 2:
+                pf.append(ev[0].elapsed_time(ev[1]))
+                pb.append(ev[1].elapsed_time(ev[2]))
+        proj_ms = (float(np.median(pf)), float(np.median(pb)))
+        # algorithmic bytes: forward reads 44 B per Gaussian and writes 36 B per record;
+        # backward reads 40 B per Gaussian + 28 B per record and writes 40 B per Gaussian
+        proj_bytes = (44 * N + 36 * N * V, 80 * N + 28 * N * V)
         # ---- plain pixel-wise 16x16 static grid on the same inputs ----
         # (single-view kernel: a view at a time, each with its own binning; render kernels
         # only, summed over the views)
@@ -537,6 +609,12 @@ def main_views(args, scene, rank, world, local):
                "hbm_peak_GB_s": hbm, "frac_of_hbm": bin_bytes / (bin_ms / 1e3) / 1e9 / hbm,
                "note": "depth sort + counting-sort binning of K entries; algorithmic bytes = 16 B per "
                        "projected record read + 4 B per entry + 8 B per tile written"}
+    projection = {"forward_ms": proj_ms[0], "backward_ms": proj_ms[1],
+                  "forward_GB_s": proj_bytes[0] / (proj_ms[0] / 1e3) / 1e9,
+                  "backward_GB_s": proj_bytes[1] / (proj_ms[1] / 1e3) / 1e9, "hbm_peak_GB_s": hbm,
+                  "note": "a1 projection and its backward (chain rule to means3D, log_scales, quats); "
+                          "algorithmic bytes: forward 44 B per Gaussian + 36 B per record, backward 80 B per "
+                          "Gaussian + 28 B per record"}
     sizes = sorted(set(f"{c['W']}x{c['H']}" for c in cams))
     config = {"workload": WORKLOADS.get(args.config, f"{V} views ({', '.join(sizes)}) of {N} Gaussians"),
               "gaussians": N, "views": V, "image": sizes[0] if V == 1 else sizes, "tile": "16x16",
@@ -556,6 +634,7 @@ def main_views(args, scene, rank, world, local):
                   "tile_list_max": int(lens.max()), "tile_list_mean": float(lens.mean()),
                   "tile_list_p99": float(np.percentile(lens, 99)), "tile_eval_pairs": tile_hist},
         "binning": binning,
+        "projection": projection,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": eval_pairs * world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),

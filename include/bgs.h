@@ -60,6 +60,14 @@ extern "C" {
 #define BGS_MODE_PIXEL 1    /* persistent queue (Sec. 4.1), every item pixel-wise               */
 #define BGS_MODE_GAUSSIAN 2 /* persistent queue, every item Gaussian-wise (Sec. 4.2-4.3)        */
 #define BGS_MODE_STATIC 3   /* plain pixel-wise static grid, one block per tile (Algorithm 4)  */
+#define BGS_MODE_SELECT 4   /* self-adaptive selection (Sec. 4.4), single-view calls: render with
+                               the balanced kernels (AUTO); every plan.select_period forward
+                               calls, starting with the first, time the balanced forward against
+                               the static pixel-wise forward on the call's frame (both run; the
+                               outputs are the same); once the balanced forward is slower, use
+                               the static kernels for every later call (irreversible, until
+                               bgs_plan_selector_reset).  No measurement is taken while the
+                               stream is being captured (timing needs a host synchronisation). */
 
 /* ---- camera (Eq. 2: W = viewmat rotation, J = Jacobian of the pinhole map) ---------- */
 typedef struct bgs_camera {
@@ -80,6 +88,7 @@ typedef struct bgs_plan_desc {
     int32_t device;          /* CUDA device ordinal; -1 = the current device at creation    */
     int32_t pixel_rows;      /* sub-tile of a pixel-wise item: 8 x (4 pixel_rows) pixels, one
                                 warp, pixel_rows pixels per lane (1, 2 or 4)                 */
+    int32_t select_period;   /* BGS_MODE_SELECT: forward calls between two timings (>= 1)   */
 } bgs_plan_desc;
 
 typedef struct bgs_plan bgs_plan;
@@ -96,7 +105,8 @@ typedef struct bgs_stats {
 } bgs_stats;
 
 /* Fills *desc with defaults (threshold 512, 4 px per Gaussian-wise item, chunk 1,
-   max resident blocks, LPT order on, current device, 2 pixel rows per lane). */
+   max resident blocks, LPT order on, current device, 2 pixel rows per lane, selector
+   timing every 1000 forward calls). */
 void bgs_plan_desc_default(bgs_plan_desc *desc);
 /* Creates a plan bound to desc->device.  Allocates a small device control block. */
 int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out);
@@ -126,6 +136,13 @@ int bgs_plan_timing(bgs_plan *plan, int enable);
 int bgs_plan_kernel_ms(bgs_plan *plan, double *fwd_ms, int32_t *fwd_n, double *bwd_ms, int32_t *bwd_n);
 /* Number of SMs of the plan's device (host). */
 int bgs_plan_num_sms(const bgs_plan *plan);
+/* State of the BGS_MODE_SELECT selector (all outputs host, nullable): *switched = 1 once
+   the static kernels were chosen; *calls = forward calls in SELECT mode; *measurements =
+   timings taken; *last_balanced_ms / *last_static_ms = the last timing of each forward. */
+int bgs_plan_selector(const bgs_plan *plan, int32_t *switched, int64_t *calls, int64_t *measurements,
+                      double *last_balanced_ms, double *last_static_ms);
+/* Restarts the selector: balanced kernels, no calls, no measurements. */
+int bgs_plan_selector_reset(bgs_plan *plan);
 const char *bgs_last_error(void);
 
 /* ---- a1: projection (Eq. 1-3) ------------------------------------------------------

@@ -21,8 +21,9 @@ BGS_ERR_CAPACITY = -2
 BGS_ERR_CUDA = -3
 BGS_ERR_DEVICE_CHECK = -4
 
-MODE_AUTO, MODE_PIXEL, MODE_GAUSSIAN, MODE_STATIC = 0, 1, 2, 3
-MODES = {"auto": MODE_AUTO, "pixel": MODE_PIXEL, "gaussian": MODE_GAUSSIAN, "static": MODE_STATIC}
+MODE_AUTO, MODE_PIXEL, MODE_GAUSSIAN, MODE_STATIC, MODE_SELECT = 0, 1, 2, 3, 4
+MODES = {"auto": MODE_AUTO, "pixel": MODE_PIXEL, "gaussian": MODE_GAUSSIAN, "static": MODE_STATIC,
+         "select": MODE_SELECT}
 
 CHECK_INDEX, CHECK_RANGE, CHECK_OVERFLOW, CHECK_QUEUE = 1, 2, 4, 8
 
@@ -33,7 +34,7 @@ EXPORTS = [
     "bgs_plan_num_sms", "bgs_last_error", "bgs_preprocess", "bgs_bin_and_sort", "bgs_render_forward",
     "bgs_render_backward", "bgs_probe_pipe_rates", "bgs_debug_exp2", "bgs_plan_timing", "bgs_plan_kernel_ms",
     "bgs_render_forward_noalloc", "bgs_preprocess_batched", "bgs_bin_and_sort_batched",
-    "bgs_preprocess_backward", "bgs_preprocess_backward_batched",
+    "bgs_preprocess_backward", "bgs_preprocess_backward_batched", "bgs_plan_selector", "bgs_plan_selector_reset",
     "bgs_render_forward_batched", "bgs_render_backward_batched", "bgs_graph_begin", "bgs_graph_end",
     "bgs_graph_launch", "bgs_autotune_render",
 ]
@@ -48,7 +49,8 @@ class BgsError(RuntimeError):
 class PlanDesc(ctypes.Structure):
     _fields_ = [("heavy_threshold", ctypes.c_int32), ("gw_pixels", ctypes.c_int32),
                 ("queue_chunk", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("lpt_order", ctypes.c_int32), ("device", ctypes.c_int32), ("pixel_rows", ctypes.c_int32)]
+                ("lpt_order", ctypes.c_int32), ("device", ctypes.c_int32), ("pixel_rows", ctypes.c_int32),
+                ("select_period", ctypes.c_int32)]
 
 
 class Camera(ctypes.Structure):
@@ -105,6 +107,9 @@ def load(build_if_needed: bool = True):
         lib.bgs_plan_stats.argtypes = [P, ctypes.POINTER(Stats), P]
         lib.bgs_plan_reset_stats.argtypes = [P, P]
         lib.bgs_plan_num_sms.argtypes = [P]
+        lib.bgs_plan_selector.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        lib.bgs_plan_selector_reset.argtypes = [P]
         lib.bgs_plan_timing.argtypes = [P, i32]
         lib.bgs_plan_kernel_ms.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]

@@ -102,6 +102,10 @@ struct bgs_plan {
         int tw, th, mode, heavy_threshold, gw_pixels, pixel_rows, lpt_order;
     } wl_key;
     bool rec_valid = false, wl_valid = false;
+    // BGS_MODE_SELECT (Sec. 4.4)
+    bool sel_switched = false;
+    long long sel_calls = 0, sel_measurements = 0;
+    double sel_last_balanced = 0.0, sel_last_static = 0.0;
 };
 
 namespace {
@@ -289,7 +293,7 @@ bool valid_desc(const bgs_plan_desc *d) {
     return d->heavy_threshold >= 0 && (d->gw_pixels == 1 || d->gw_pixels == 2 || d->gw_pixels == 4 ||
                                        d->gw_pixels == 8) &&
            d->queue_chunk >= 1 && d->queue_chunk <= 1024 && d->blocks_per_sm >= 0 && d->blocks_per_sm <= 64 &&
-           (d->pixel_rows == 1 || d->pixel_rows == 2 || d->pixel_rows == 4);
+           (d->pixel_rows == 1 || d->pixel_rows == 2 || d->pixel_rows == 4) && d->select_period >= 1;
 }
 
 }  // namespace
@@ -307,6 +311,7 @@ void bgs_plan_desc_default(bgs_plan_desc *d) {
     d->lpt_order = 1;
     d->device = -1;
     d->pixel_rows = 2;
+    d->select_period = 1000;
 }
 
 int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out) {
@@ -424,6 +429,25 @@ size_t bgs_workspace_size(const bgs_plan *p, int64_t N, int64_t K, int64_t T, in
     s += 8 * T * (size_t)std::max(8, (256 + P - 1) / P);  // work items (16x16 tiles)
     s += 64 << 20;                      // CUB temporaries (upper estimate)
     return s;
+}
+
+int bgs_plan_selector(const bgs_plan *p, int32_t *switched, int64_t *calls, int64_t *measurements,
+                      double *last_balanced_ms, double *last_static_ms) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_plan_selector: NULL plan");
+    if (switched) *switched = p->sel_switched ? 1 : 0;
+    if (calls) *calls = p->sel_calls;
+    if (measurements) *measurements = p->sel_measurements;
+    if (last_balanced_ms) *last_balanced_ms = p->sel_last_balanced;
+    if (last_static_ms) *last_static_ms = p->sel_last_static;
+    return BGS_OK;
+}
+
+int bgs_plan_selector_reset(bgs_plan *p) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_plan_selector_reset: NULL plan");
+    p->sel_switched = false;
+    p->sel_calls = p->sel_measurements = 0;
+    p->sel_last_balanced = p->sel_last_static = 0.0;
+    return BGS_OK;
 }
 
 int bgs_plan_reserve(bgs_plan *p, int64_t N, int64_t K, int64_t T, int64_t pixels) {
@@ -704,7 +728,7 @@ int check_render_arrays(int64_t N, const float *means2D, const float *conic_opac
                         int tw, int th, const float *bg, int mode, const char *who) {
     if (N < 0 || N >= (1ll << 32)) return fail(BGS_ERR_INVALID, "%s: N out of range", who);
     if (num_entries < 0 || num_entries >= (1ll << 32)) return fail(BGS_ERR_INVALID, "%s: num_entries out of range", who);
-    if (mode < BGS_MODE_AUTO || mode > BGS_MODE_STATIC) return fail(BGS_ERR_INVALID, "%s: unknown mode %d", who, mode);
+    if (mode < BGS_MODE_AUTO || mode > BGS_MODE_SELECT) return fail(BGS_ERR_INVALID, "%s: unknown mode %d", who, mode);
     BGS_TRY(check_tile(tw, th, mode != BGS_MODE_STATIC));
     if (!ranges || !bg || (num_entries > 0 && !point_list) ||
         (N > 0 && (!means2D || !conic_opacity || !colors || !depths)))
@@ -888,8 +912,44 @@ int bgs_render_forward(bgs_plan *p, int64_t N, const float *means2D, const float
     io.n_contrib[0] = n_contrib;
     io.n_eval[0] = n_eval;
     DeviceGuard g(p->device);
-    return render_forward_impl(p, vt, io, N, N, means2D, conic_opacity, colors, depths, point_list, num_entries, ranges,
-                               tw, th, bg, mode, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mode != BGS_MODE_SELECT)
+        return render_forward_impl(p, vt, io, N, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
+                                   ranges, tw, th, bg, mode, s);
+    // Sec. 4.4: balanced kernels until a timing finds the static pixel-wise forward faster
+    const long long call = p->sel_calls++;
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    BGS_CUDA(cudaStreamIsCapturing(s, &cst), "cudaStreamIsCapturing");
+    const bool measure = !p->sel_switched && call % p->desc.select_period == 0 && cst == cudaStreamCaptureStatusNone;
+    if (!measure)
+        return render_forward_impl(p, vt, io, N, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
+                                   ranges, tw, th, bg, p->sel_switched ? BGS_MODE_STATIC : BGS_MODE_AUTO, s);
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    for (auto &e : ev) BGS_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+    int rc = BGS_OK;
+    if (cudaEventRecord(ev[0], s) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "cudaEventRecord");
+    if (rc == BGS_OK)
+        rc = render_forward_impl(p, vt, io, N, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
+                                 ranges, tw, th, bg, BGS_MODE_AUTO, s);
+    if (rc == BGS_OK && cudaEventRecord(ev[1], s) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "cudaEventRecord");
+    if (rc == BGS_OK)
+        rc = render_forward_impl(p, vt, io, N, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
+                                 ranges, tw, th, bg, BGS_MODE_STATIC, s);
+    if (rc == BGS_OK && cudaEventRecord(ev[2], s) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "cudaEventRecord");
+    float t_bal = 0.f, t_sta = 0.f;
+    if (rc == BGS_OK) {
+        cudaError_t e = cudaEventSynchronize(ev[2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t_bal, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t_sta, ev[1], ev[2]);
+        if (e != cudaSuccess) rc = cuda_fail(e, "selector timing");
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (rc != BGS_OK) return rc;
+    p->sel_measurements += 1;
+    p->sel_last_balanced = t_bal;
+    p->sel_last_static = t_sta;
+    if (t_sta < t_bal) p->sel_switched = true;
+    return BGS_OK;
 }
 
 int bgs_render_backward(bgs_plan *p, int64_t N, const float *means2D, const float *conic_opacity, const float *colors,
@@ -915,6 +975,7 @@ int bgs_render_backward(bgs_plan *p, int64_t N, const float *means2D, const floa
     gi.dL_ddepth[0] = dL_ddepth;
     gi.dL_dalpha[0] = dL_dalpha;
     DeviceGuard g(p->device);
+    if (mode == BGS_MODE_SELECT) mode = p->sel_switched ? BGS_MODE_STATIC : BGS_MODE_AUTO;
     return render_backward_impl(p, vt, gi, N, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
                                 ranges, tw, th, bg, mode, dL_dmeans2D, dL_dconic, dL_dopacity, dL_dcolors, dL_ddepths,
                                 (cudaStream_t)stream);
@@ -1058,7 +1119,8 @@ int bgs_render_forward_batched(bgs_plan *p, int32_t V, const bgs_view *views, in
                                const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges, int32_t tw,
                                int32_t th, const float *bg, int32_t mode, void *stream) {
     if (!p) return fail(BGS_ERR_INVALID, "bgs_render_forward_batched: NULL plan");
-    if (mode == BGS_MODE_STATIC) return fail(BGS_ERR_INVALID, "bgs_render_forward_batched: the static kernel is single-view");
+    if (mode == BGS_MODE_STATIC || mode == BGS_MODE_SELECT)
+        return fail(BGS_ERR_INVALID, "bgs_render_forward_batched: the static kernel (and the selector) is single-view");
     bgs::ViewTable vt;
     BGS_TRY(batched_tables(V, views, tw, th, vt));
     if (N < 0 || N * V >= (1ll << 32)) return fail(BGS_ERR_INVALID, "bgs_render_forward_batched: N out of range");
@@ -1088,7 +1150,8 @@ int bgs_render_backward_batched(bgs_plan *p, int32_t V, const bgs_view *views, i
                                 int32_t th, const float *bg, int32_t mode, float *dL_dmeans2D, float *dL_dconic,
                                 float *dL_dopacity, float *dL_dcolors, float *dL_ddepths, void *stream) {
     if (!p) return fail(BGS_ERR_INVALID, "bgs_render_backward_batched: NULL plan");
-    if (mode == BGS_MODE_STATIC) return fail(BGS_ERR_INVALID, "bgs_render_backward_batched: the static kernel is single-view");
+    if (mode == BGS_MODE_STATIC || mode == BGS_MODE_SELECT)
+        return fail(BGS_ERR_INVALID, "bgs_render_backward_batched: the static kernel (and the selector) is single-view");
     bgs::ViewTable vt;
     BGS_TRY(batched_tables(V, views, tw, th, vt));
     if (N < 0 || N * V >= (1ll << 32)) return fail(BGS_ERR_INVALID, "bgs_render_backward_batched: N out of range");

@@ -49,7 +49,8 @@ class Plan:
     """Owns a bgs_plan: tuning knobs and the library-managed workspace."""
 
     def __init__(self, heavy_threshold: int = 512, gw_pixels: int = 4, queue_chunk: int = 1,
-                 blocks_per_sm: int = 0, lpt_order: bool = True, device=None, pixel_rows: int = 2):
+                 blocks_per_sm: int = 0, lpt_order: bool = True, device=None, pixel_rows: int = 2,
+                 select_period: int = 1000):
         self._lib = _lib.load()
         if device is None:
             device = torch.cuda.current_device()
@@ -59,6 +60,7 @@ class Plan:
         d.heavy_threshold, d.gw_pixels, d.queue_chunk = heavy_threshold, gw_pixels, queue_chunk
         d.blocks_per_sm, d.lpt_order, d.device = blocks_per_sm, int(bool(lpt_order)), self.device.index
         d.pixel_rows = pixel_rows
+        d.select_period = select_period
         h = ctypes.c_void_p()
         check(self._lib.bgs_plan_create(ctypes.byref(d), ctypes.byref(h)), "bgs_plan_create")
         self.handle = h
@@ -74,6 +76,19 @@ class Plan:
         for k, v in kw.items():
             setattr(d, k, int(v))
         check(self._lib.bgs_plan_set(self.handle, ctypes.byref(d)), "bgs_plan_set")
+
+    def selector(self) -> dict:
+        """State of the "select" mode (Sec. 4.4): switched, calls, measurements and the last
+        balanced / static forward timings in ms."""
+        sw, calls, meas = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        tb, ts = ctypes.c_double(), ctypes.c_double()
+        check(self._lib.bgs_plan_selector(self.handle, ctypes.byref(sw), ctypes.byref(calls), ctypes.byref(meas),
+                                          ctypes.byref(tb), ctypes.byref(ts)), "bgs_plan_selector")
+        return dict(switched=bool(sw.value), calls=calls.value, measurements=meas.value, balanced_ms=tb.value,
+                    static_ms=ts.value)
+
+    def selector_reset(self):
+        check(self._lib.bgs_plan_selector_reset(self.handle), "bgs_plan_selector_reset")
 
     @property
     def num_sms(self) -> int:

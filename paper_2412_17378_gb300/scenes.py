@@ -155,6 +155,23 @@ def _config3(stage: str, scale=1.0):
     return dict(name=f"cfg3{stage}_{W}x{H}_{N}", gaussians=g, cameras=[camera(W, H)], backward=True)
 
 
+def drift_scene(frac: float, scale=1.0, seed: int = 31) -> dict:
+    """A stage of a synthetic training run between config 3-early (frac = 0: 100k large,
+    faint Gaussians) and config 3-late (frac = 1: 3M small, opaque ones) at 1280x720:
+    the Gaussian count grows geometrically, the mean log-scale falls linearly from -2 to
+    -5 and the opacity range moves from U[0.05, 0.3] to U[0.5, 1] -- the densification /
+    sharpening drift behind the paper's inflection point (Sec. 4.4, Sec. 5.2.2)."""
+    f = min(max(float(frac), 0.0), 1.0)
+    W, H = 1280, 720
+    rng = np.random.default_rng([seed, int(round(1000 * f))])
+    N = max(1, int(100_000 * (30.0 ** f) * scale))
+    ls = rng.normal(-2.0 - 3.0 * f, 0.5, (N, 3))
+    op = rng.uniform(0.05 + 0.45 * f, 0.3 + 0.7 * f, N)
+    means = frustum_uniform(rng, N, W, H)
+    g = _gaussians(means, ls, _quats(rng, N), op, rng.uniform(0, 1, (N, 3)))
+    return dict(name=f"drift{f:.2f}_{W}x{H}_{N}", gaussians=g, cameras=[camera(W, H)], backward=True)
+
+
 def _config4(scale=1.0):
     rng = np.random.default_rng(4)
     N = max(1, int(2_000_000 * scale))

@@ -46,15 +46,21 @@ def test_host_only_calls():
     lib = _lib.load()
     d = _lib.PlanDesc()
     lib.bgs_plan_desc_default(ctypes.byref(d))
-    assert (d.heavy_threshold, d.gw_pixels, d.queue_chunk, d.lpt_order, d.device) == (512, 4, 1, 1, -1)
+    assert (d.heavy_threshold, d.gw_pixels, d.queue_chunk, d.lpt_order, d.device, d.pixel_rows,
+            d.select_period) == (512, 4, 1, 1, -1, 2, 1000)
     assert lib.bgs_workspace_size(None, 10, 10, 10, 10) == 0
     # NULL output pointer is rejected before any CUDA call
     assert lib.bgs_plan_create(ctypes.byref(d), None) == _lib.BGS_ERR_INVALID
     assert b"NULL" in lib.bgs_last_error()
     # invalid knobs are rejected before any CUDA call
-    d.gw_pixels = 3
     h = ctypes.c_void_p()
+    d.select_period = 0
     assert lib.bgs_plan_create(ctypes.byref(d), ctypes.byref(h)) == _lib.BGS_ERR_INVALID
+    d.select_period = 1000
+    d.gw_pixels = 3
+    assert lib.bgs_plan_create(ctypes.byref(d), ctypes.byref(h)) == _lib.BGS_ERR_INVALID
+    # the selector query rejects a NULL plan
+    assert lib.bgs_plan_selector(None, None, None, None, None, None) == _lib.BGS_ERR_INVALID
     # argument checks of the entry points run before any device work
     assert lib.bgs_render_forward(None, 0, None, None, None, None, None, 0, None, 16, 16, 16, 16, None, 0,
                                   None, None, None, None, None, None, None) == _lib.BGS_ERR_INVALID
