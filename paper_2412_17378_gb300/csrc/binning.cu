@@ -190,12 +190,14 @@ __global__ void k_bin_advance(int T, const uint32_t *__restrict__ total, long lo
 }
 
 // Writes the completed sector [done, done + 8) of a lane's run from its ring (words below
-// run0 belong to the previous block's run of the tile and are left alone).
-__device__ __forceinline__ void flush_sector(const uint32_t *ring, int rot, uint32_t done, uint32_t run0,
+// run0 belong to the previous block's run of the tile and are left alone).  The ring is
+// slot-major, ring_s[slot * 32 + lane]: appends and these reads are bank-conflict free.
+__device__ __forceinline__ void flush_sector(const uint32_t *ring_s, int lane, uint32_t done, uint32_t run0,
                                              uint32_t *__restrict__ point_list, uint32_t capacity, bool vec_ok) {
+    const uint32_t *src = ring_s + ((done & 15u) << 5) + lane;
     uint32_t v[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = ring[(done + j + rot) & 15u];
+    for (int j = 0; j < 8; ++j) v[j] = src[32 * j];
     if (vec_ok && done >= run0 && done + 8u <= capacity) {
         uint4 *dst = reinterpret_cast<uint4 *>(point_list + done);  // 32-byte aligned
         dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t N, uint32_t G, int 
                                                     const DevCtrl *ctrl) {
     __shared__ uint32_t idx_s[512];  // sorted positions of the pass's flagged Gaussians
     __shared__ uint2 hit_s[512];     // (lanes whose tile the rectangle covers, Gaussian index)
-    __shared__ uint32_t ring_s[32 * 16];
+    __shared__ uint32_t ring_s[16 * 32];  // per-lane 16-word output rings, slot-major
     const int b = blockIdx.x, cx = blockIdx.y, cy = blockIdx.z, lane = threadIdx.x;
     const int gx0 = cx * kCbW, gy0 = cy * kCbH;
     const int ltx = gx0 + (lane % kCbW), lty = gy0 + (lane / kCbW);
@@ -228,8 +230,7 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t N, uint32_t G, int 
     uint32_t pos = own ? base + start[t] + H[(size_t)b * tx * ty + t] : 0u;
     const uint32_t run0 = pos;
     uint32_t done = pos & ~7u;  // positions below done are written (or precede the run)
-    uint32_t *ring = ring_s + 16 * lane;
-    const int rot = lane >> 1;  // ring rotation: lanes appending at one slot hit distinct banks
+    uint32_t *ring = ring_s + lane;
     const int nC = ((tx + kCbW - 1) / kCbW) * ((ty + kCbH - 1) / kCbH);
     const uint32_t *mk = masks + ((size_t)b * nC + cy * ((tx + kCbW - 1) / kCbW) + cx) * W32;
     const uint32_t s0 = (uint32_t)b * G;
@@ -264,22 +265,23 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t N, uint32_t G, int 
             const uint32_t rows = (ly1 >= 4u ? 0xffffffffu : (1u << (8u * ly1)) - 1u) ^ ((1u << (8u * ly0)) - 1u);
             hit_s[k] = make_uint2(rows & (cols * 0x01010101u) & own_mask, order[s]);
         }
+        // pad to a multiple of 8 with entries that cover no lane
+        const int padded = (total + 7) & ~7;
+        if (lane < padded - total) hit_s[total + lane] = make_uint2(0u, 0u);
         __syncwarp();
-        for (int k0 = 0; k0 < total; k0 += 8) {  // depth order, 8 visits at a time
+        for (int k0 = 0; k0 < padded; k0 += 8) {  // depth order, 8 visits at a time
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                if (k0 + j < total) {
-                    const uint2 e = hit_s[k0 + j];
-                    if ((e.x >> lane) & 1u) {
-                        ring[(pos + rot) & 15u] = e.y;
-                        ++pos;
-                    }
-                }
+                // branch-free: the slot of position pos is free (pos - done < 16), so every
+                // lane writes it and only the lanes whose tile is covered advance past it
+                const uint2 e = hit_s[k0 + j];
+                ring[(pos & 15u) << 5] = e.y;
+                pos += (e.x >> lane) & 1u;
             }
             // at most 8 appends since the last check: at most one newly completed sector,
             // and no ring slot overwritten before it is written out
             if (done + 8u <= pos) {
-                flush_sector(ring, rot, done, run0, point_list, capacity, vec_ok != 0);
+                flush_sector(ring_s, lane, done, run0, point_list, capacity, vec_ok != 0);
                 done += 8u;
             }
         }
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t N, uint32_t G, int 
     }
     // the last, partial sector
     for (uint32_t p = done; p < pos; ++p)
-        if (p >= run0 && p < capacity) point_list[p] = ring[(p + rot) & 15u];
+        if (p >= run0 && p < capacity) point_list[p] = ring[(p & 15u) << 5];
 }
 
 size_t bin_count_smem(int tx, int ty) {
