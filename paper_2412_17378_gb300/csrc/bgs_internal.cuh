@@ -31,9 +31,13 @@ struct DevCtrl {
     unsigned long long bin_base;  // binning: first point_list slot of the view being binned
 };
 
-// Pixel-wise items cover 8 x (4 Q) pixels of a tile, Q = pixel rows per lane (1, 2 or 4,
-// the plan's sub-tile knob): lane l owns the pixels (l % 8, l / 8 + 4 q), q < Q.
-constexpr int kPixItemW = 8;
+// Pixel-wise items: Q = pixel rows per lane (the plan's sub-tile knob, 1, 2, 4 or 8).  For
+// Q <= 4 an item covers 8 x 4Q pixels of a tile and lane l owns the pixels (l % 8, l / 8 +
+// 4 q); for Q = 8 it covers 16 x 16 pixels and lane l owns (l % 16, l / 16 + 2 q), q < Q.
+// Either way a lane's pixels share one column (and so their x-offset to a Gaussian).
+__host__ __device__ constexpr int pix_item_w(int Q) { return Q == 8 ? 16 : 8; }
+__host__ __device__ constexpr int pix_row_step(int Q) { return 32 / pix_item_w(Q); }
+__host__ __device__ constexpr int pix_item_h(int Q) { return pix_row_step(Q) * Q; }
 
 // ---- packed per-Gaussian record used by the render kernels (48 bytes) ---------------
 //   a = (mx, my, qa, qb), b = (qc, o, hx, hy), c = (r, g, b, depth)

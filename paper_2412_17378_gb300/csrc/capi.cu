@@ -241,9 +241,8 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
     const int T = vt.tile_base[vt.V];
     const int P = p->desc.gw_pixels;
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-    const int item_h = 4 * p->desc.pixel_rows;
-    const long long per_tile = std::max<long long>(((tw + bgs::kPixItemW - 1) / bgs::kPixItemW) *
-                                                       ((th + item_h - 1) / item_h),
+    const int item_w = bgs::pix_item_w(p->desc.pixel_rows), item_h = bgs::pix_item_h(p->desc.pixel_rows);
+    const long long per_tile = std::max<long long>(((tw + item_w - 1) / item_w) * ((th + item_h - 1) / item_h),
                                                    (tw * th + P - 1) / P);
     const long long max_items = (long long)T * per_tile;
     if (max_items >= (1ll << 31)) return fail(BGS_ERR_INVALID, "too many work items (%lld)", max_items);
@@ -293,7 +292,8 @@ bool valid_desc(const bgs_plan_desc *d) {
     return d->heavy_threshold >= 0 && (d->gw_pixels == 1 || d->gw_pixels == 2 || d->gw_pixels == 4 ||
                                        d->gw_pixels == 8) &&
            d->queue_chunk >= 1 && d->queue_chunk <= 1024 && d->blocks_per_sm >= 0 && d->blocks_per_sm <= 64 &&
-           (d->pixel_rows == 1 || d->pixel_rows == 2 || d->pixel_rows == 4) && d->select_period >= 1;
+           (d->pixel_rows == 1 || d->pixel_rows == 2 || d->pixel_rows == 4 || d->pixel_rows == 8) &&
+           d->select_period >= 1;
 }
 
 }  // namespace
@@ -1255,7 +1255,7 @@ int bgs_autotune_render(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N
     // stage 1: sub-tile (pixel rows per lane) with pixel-wise items only
     d.heavy_threshold = 0x7fffffff;
     d.queue_chunk = 1;
-    for (int q : {1, 2, 4}) {
+    for (int q : {1, 2, 4, 8}) {
         d.pixel_rows = q;
         if ((rc = run(d, t)) != BGS_OK) break;
         if (t < best_t) best_t = t, best = d;

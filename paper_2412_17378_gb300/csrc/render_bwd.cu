@@ -280,16 +280,16 @@ cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s) {
 template <int Q, bool Extra>
 __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int sub, Rec *buf, uint32_t *gbuf,
                                                int lane) {
-    constexpr int kItemH = 4 * Q;
+    constexpr int kItemW = pix_item_w(Q), kItemH = pix_item_h(Q), kRowStep = pix_row_step(Q);
     const int v = view_of(a.vt, tile);
     const int lt = tile - a.vt.tile_base[v];
     const int tx = lt % a.vt.tiles_x[v], ty = lt / a.vt.tiles_x[v];
     const int x0 = tx * a.tile_w, y0 = ty * a.tile_h;
     const int vw = min(a.tile_w, a.vt.W[v] - x0), vh = min(a.tile_h, a.vt.H[v] - y0);
-    const int cxs = (vw + kPixItemW - 1) / kPixItemW;
+    const int cxs = (vw + kItemW - 1) / kItemW;
     const int sx = sub % cxs, sy = sub / cxs;
-    const int px = x0 + sx * kPixItemW + (lane & 7);
-    const int py0 = y0 + sy * kItemH + (lane >> 3);
+    const int px = x0 + sx * kItemW + (lane % kItemW);
+    const int py0 = y0 + sy * kItemH + (lane / kItemW);
     const uint2 rg = load_range_bwd(a, tile);
     const int n = (int)(rg.y - rg.x);
     PixState s[Q];
@@ -297,7 +297,7 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
     int maxnc = 0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const int py = py0 + 4 * q;
+        const int py = py0 + kRowStep * q;
         s[q] = load_pixel(a, v, px, py, px < x0 + vw && py < y0 + vh);
         if (s[q].nc > n) s[q].nc = n;
         maxnc = max(maxnc, s[q].nc);
@@ -306,7 +306,7 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
     maxnc = __reduce_max_sync(kFullB, maxnc);
     const uint32_t hi = rg.x + (uint32_t)maxnc;
     const float pxf = (float)px;
-    const float bcx = (float)(x0 + sx * kPixItemW) + 3.5f;
+    const float bcx = (float)(x0 + sx * kItemW) + 0.5f * (kItemW - 1);
     const float bcy = (float)(y0 + sy * kItemH) + 0.5f * (kItemH - 1);
     for (uint32_t top = hi; top > rg.x;) {
         const uint32_t lo = top - min(32u, top - rg.x);
@@ -318,7 +318,7 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
             const Rec r = load_rec_bwd(a, top - 1 - lane, g);
             buf[lane] = r;
             gbuf[lane] = g;
-            hit = !box_misses(r.a, r.b, bcx, bcy, 3.5f, 0.5f * (kItemH - 1));
+            hit = !box_misses(r.a, r.b, bcx, bcy, 0.5f * (kItemW - 1), 0.5f * (kItemH - 1));
         }
         // back to front over the records whose alpha box reaches the pixel block
         unsigned live = __ballot_sync(kFullB, hit);
@@ -374,6 +374,7 @@ const void *backward_balanced_kernel(const BwdArgs &a) {
         case 1: return e ? (const void *)k_backward_balanced<1, true> : (const void *)k_backward_balanced<1, false>;
         case 2: return e ? (const void *)k_backward_balanced<2, true> : (const void *)k_backward_balanced<2, false>;
         case 4: return e ? (const void *)k_backward_balanced<4, true> : (const void *)k_backward_balanced<4, false>;
+        case 8: return e ? (const void *)k_backward_balanced<8, true> : (const void *)k_backward_balanced<8, false>;
         default: return nullptr;
     }
 }

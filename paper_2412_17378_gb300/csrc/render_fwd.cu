@@ -180,23 +180,23 @@ __device__ __forceinline__ TileGeom tile_geom(const FwdArgs &a, int tile) {
 template <int Q>
 __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, Rec *buf, int lane,
                                            unsigned long long &st_eval, unsigned long long &st_acc) {
-    constexpr int kItemH = 4 * Q;
+    constexpr int kItemW = pix_item_w(Q), kItemH = pix_item_h(Q), kRowStep = pix_row_step(Q);
     const TileGeom tg = tile_geom(a, tile);
-    const int cxs = (tg.vw + kPixItemW - 1) / kPixItemW;
+    const int cxs = (tg.vw + kItemW - 1) / kItemW;
     const int sx = sub % cxs, sy = sub / cxs;
-    const int px = tg.x0 + sx * kPixItemW + (lane & 7);
-    const int py0 = tg.y0 + sy * kItemH + (lane >> 3);
+    const int px = tg.x0 + sx * kItemW + (lane % kItemW);
+    const int py0 = tg.y0 + sy * kItemH + (lane / kItemW);
     const uint2 rg = load_range(a, tile);
     const float pxf = (float)px;
     // centre and half-extent of the item's pixel block (for skipping records that miss it)
-    const float bcx = (float)(tg.x0 + sx * kPixItemW) + 3.5f;
+    const float bcx = (float)(tg.x0 + sx * kItemW) + 0.5f * (kItemW - 1);
     const float bcy = (float)(tg.y0 + sy * kItemH) + 0.5f * (kItemH - 1);
     float pyf[Q], T[Q], c0[Q], c1[Q], c2[Q], D[Q], A[Q];
     int last[Q], neval[Q], nacc[Q];
     bool done[Q], inside[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const int py = py0 + 4 * q;
+        const int py = py0 + kRowStep * q;
         inside[q] = px < tg.x0 + tg.vw && py < tg.y0 + tg.vh;
         pyf[q] = (float)py;
         T[q] = 1.f;
@@ -217,7 +217,7 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
         if (j < rg.y) {
             const Rec r = load_rec(a, j);
             buf[lane] = r;
-            hit = !box_misses(r.a, r.b, bcx, bcy, 3.5f, 0.5f * (kItemH - 1));
+            hit = !box_misses(r.a, r.b, bcx, bcy, 0.5f * (kItemW - 1), 0.5f * (kItemH - 1));
         }
         // records whose alpha box reaches the item's pixel block; the others are skipped
         unsigned live = __ballot_sync(kFull, hit);
@@ -258,7 +258,7 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (inside[q]) {
-            write_pixel(a, tg.v, px, py0 + 4 * q, T[q], c0[q], c1[q], c2[q], D[q], A[q], last[q], neval[q]);
+            write_pixel(a, tg.v, px, py0 + kRowStep * q, T[q], c0[q], c1[q], c2[q], D[q], A[q], last[q], neval[q]);
             st_eval += (unsigned long long)neval[q];
             st_acc += (unsigned long long)nacc[q];
         }
@@ -456,6 +456,7 @@ const void *forward_pixel_kernel(int pixel_rows) {
         case 1: return (const void *)k_forward_pixel<1>;
         case 2: return (const void *)k_forward_pixel<2>;
         case 4: return (const void *)k_forward_pixel<4>;
+        case 8: return (const void *)k_forward_pixel<8>;
         default: return nullptr;
     }
 }
@@ -492,6 +493,7 @@ cudaError_t launch_forward_pixel(const FwdArgs &a, int grid, bool after_gauss, c
         case 1: return cudaLaunchKernelEx(&cfg, k_forward_pixel<1>, a);
         case 2: return cudaLaunchKernelEx(&cfg, k_forward_pixel<2>, a);
         case 4: return cudaLaunchKernelEx(&cfg, k_forward_pixel<4>, a);
+        case 8: return cudaLaunchKernelEx(&cfg, k_forward_pixel<8>, a);
         default: return cudaErrorInvalidValue;
     }
 }

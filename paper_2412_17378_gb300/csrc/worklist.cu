@@ -25,8 +25,8 @@ __device__ __forceinline__ uint32_t tile_item_count(int t, uint32_t n, const Vie
     const int tx = lt % vt.tiles_x[v], ty = lt / vt.tiles_x[v];
     const int vw = min(tile_w, vt.W[v] - tx * tile_w), vh = min(tile_h, vt.H[v] - ty * tile_h);
     if (tile_is_gauss(mode, heavy_threshold, n)) return (uint32_t)((vw * vh + gw_pixels - 1) / gw_pixels);
-    const int item_h = 4 * pixel_rows;
-    return (uint32_t)(((vw + kPixItemW - 1) / kPixItemW) * ((vh + item_h - 1) / item_h));
+    const int iw = pix_item_w(pixel_rows), ih = pix_item_h(pixel_rows);
+    return (uint32_t)(((vw + iw - 1) / iw) * ((vh + ih - 1) / ih));
 }
 
 // Sort key of each tile for the descending stable sort: its kind in the top bit (Gaussian-

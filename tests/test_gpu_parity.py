@@ -287,10 +287,10 @@ def test_exp2_accuracy(R):
     assert rel.max() < 2.0 ** -21, rel.max()
 
 
-@pytest.mark.parametrize("rows", [1, 2, 4])
+@pytest.mark.parametrize("rows", [1, 2, 4, 8])
 def test_pixel_rows_sub_tiles(R, cfg1, rows):
-    """Every sub-tile size of the pixel-wise items (8 x 4, 8 x 8, 8 x 16) gives the oracle's
-    image and gradients."""
+    """Every sub-tile size of the pixel-wise items (8 x 4, 8 x 8, 8 x 16, 16 x 16) gives the
+    oracle's image and gradients."""
     p = R.Plan(heavy_threshold=1 << 30, pixel_rows=rows)
     ref = oracle.render(cfg1["means2D"], cfg1["conic_opacity"], cfg1["colors"], cfg1["depths"], cfg1["point_list"],
                         cfg1["ranges"], cfg1["W"], cfg1["H"])
@@ -302,13 +302,33 @@ def test_pixel_rows_sub_tiles(R, cfg1, rows):
     p.close()
 
 
+@pytest.mark.parametrize("rows", [4, 8])
+@pytest.mark.parametrize("W,H,tile", [(100, 70, (16, 16)), (67, 33, (16, 8)), (32, 32, (32, 8)), (40, 24, (8, 8))])
+def test_pixel_items_on_ragged_images_and_tiles(R, rows, W, H, tile):
+    """Items larger than the tile or than its part inside the image (16 x 16 items on 16 x 8
+    or 8 x 8 tiles, ragged image edges) render only their in-tile, in-image pixels."""
+    s = scene("cfg1", 0.3)
+    cam = s["cameras"][0]
+    cam.update(W=W, H=H, cx=(W - 1) / 2, cy=(H - 1) / 2, fx=W, fy=W)
+    inp = oracle_render_inputs(s, tile=tile)
+    ref = oracle.render(inp["means2D"], inp["conic_opacity"], inp["colors"], inp["depths"], inp["point_list"],
+                        inp["ranges"], W, H, tile[0], tile[1])
+    p = R.Plan(heavy_threshold=1 << 30, pixel_rows=rows)
+    out, _ = _render_gpu(R, p, inp, "pixel")
+    compare_images(out["color"], ref, what=f"rows {rows} {W}x{H} {tile}")
+    got, gref = _backward_case(R, p, inp, "pixel", seed=7)
+    for k in ("means2D", "conic", "opacity", "colors"):
+        assert rel_l2(got[k], gref[k]) <= GRAD_REL_L2, k
+    p.close()
+
+
 def test_autotuner_choice_keeps_parity(R, cfg1):
     p = R.Plan()
     g = to_gpu(cfg1)
     cam = dict(W=cfg1["W"], H=cfg1["H"], fx=256.0, fy=256.0, cx=127.5, cy=127.5, viewmat=np.eye(4))
     best_ms, knobs = R.autotune_render(p, g["means2D"], g["conic_opacity"], g["colors"], g["depths"],
                                        g["point_list"], g["K"], g["ranges"], [cam])
-    assert best_ms > 0 and knobs["pixel_rows"] in (1, 2, 4) and knobs["queue_chunk"] in (1, 2, 4)
+    assert best_ms > 0 and knobs["pixel_rows"] in (1, 2, 4, 8) and knobs["queue_chunk"] in (1, 2, 4)
     ref = oracle.render(cfg1["means2D"], cfg1["conic_opacity"], cfg1["colors"], cfg1["depths"], cfg1["point_list"],
                         cfg1["ranges"], cfg1["W"], cfg1["H"])
     out, _ = _render_gpu(R, p, cfg1, "auto")
