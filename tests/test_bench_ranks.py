@@ -1,0 +1,67 @@
+"""The multi-rank (replicas) path of bench.py on CPU: two gloo ranks agree on the maximum
+of their timed regions, the whole-job value counts every rank's units, and the reference
+arm runs on rank 0 only."""
+import contextlib
+import io
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = bench.max_over_ranks(10.0 + 3.0 * rank, world, "cpu")
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, ms))
+
+
+def test_two_gloo_ranks_take_the_maximum():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    assert got == {0: 13.0, 1: 13.0}
+
+
+def test_whole_job_value_counts_every_rank():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.whole_job_value(1e6, 1, 2.0) == pytest.approx(5e8)
+    assert bench.whole_job_value(1e6, 4, 2.0) == pytest.approx(2e9)
+    assert bench.max_over_ranks(7.5, 1, "cpu") == 7.5
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+                                      "--warmup", "0"])
+    out = io.StringIO()
+    with contextlib.redirect_stdout(out):
+        bench.main()
+    assert out.getvalue() == ""
