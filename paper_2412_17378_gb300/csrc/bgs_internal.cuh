@@ -231,8 +231,7 @@ cudaError_t launch_preprocess_backward(long long N, int V, const float *means3D,
                                        const float *quats, const bgs_camera *cams, const int *radii,
                                        const float *dL_dmeans2D, const float *dL_dconic, const float *dL_ddepths,
                                        float *dL_dmeans3D, float *dL_dlog_scales, float *dL_dquats, cudaStream_t s);
-cudaError_t launch_depth_keys64(long long N, int V, const float *depths, unsigned long long *keys, uint32_t *idx,
-                                cudaStream_t s);
+cudaError_t launch_depth_keys(long long R, const float *depths, uint32_t *keys, uint32_t *idx, cudaStream_t s);
 
 cudaError_t launch_touched(long long N, const float *means2D, const int *radii, const float *depths, int W, int H,
                            int tile_w, int tile_h, uint32_t *touched, uint32_t *dkey, uint32_t *idx, cudaStream_t s);

@@ -85,8 +85,8 @@ struct bgs_plan {
     int smem_optin = 0;
     // render
     Buf recs, tile_key, tile_key2, tile_idx, tile_idx2, counts, item_off, items, grad_acc;
-    // batched binning (64-bit depth keys)
-    Buf dkey64, dkey64_sorted;
+    // batched binning: depth keys of every view
+    Buf vkey, vkey_sorted;
     // captured CUDA graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -349,7 +349,7 @@ int bgs_plan_destroy(bgs_plan *p) {
     DeviceGuard g(p->device);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     if (p->graph) cudaGraphDestroy(p->graph);
-    Buf *bufs[] = {&p->dkey64, &p->dkey64_sorted, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_rect, &p->bin_mask, &p->touched, &p->touched_sorted, &p->dkey,
+    Buf *bufs[] = {&p->vkey, &p->vkey_sorted, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_rect, &p->bin_mask, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off, &p->items,
@@ -1068,22 +1068,25 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
     if (needed) *needed = 0;
     const long long R = N * V;
     if (R > 0) {
-        // depth order of every view's records, views kept apart: sort on (view << 32 | depth bits)
-        BGS_TRY(ensure(p, p->dkey64, 8 * R, s, "dkey64"));
-        BGS_TRY(ensure(p, p->dkey64_sorted, 8 * R, s, "dkey64_sorted"));
+        // depth order of every view's records: one 32-bit key sort per view slice
+        BGS_TRY(ensure(p, p->vkey, 4 * R, s, "dkey"));
+        BGS_TRY(ensure(p, p->vkey_sorted, 4 * R, s, "dkey_sorted"));
         BGS_TRY(ensure(p, p->gidx, 4 * R, s, "gidx"));
         BGS_TRY(ensure(p, p->order, 4 * R, s, "order"));
-        unsigned long long *k0 = (unsigned long long *)p->dkey64.p, *k1 = (unsigned long long *)p->dkey64_sorted.p;
+        uint32_t *k0 = (uint32_t *)p->vkey.p, *k1 = (uint32_t *)p->vkey_sorted.p;
         uint32_t *gidx = (uint32_t *)p->gidx.p, *order = (uint32_t *)p->order.p;
-        BGS_CUDA(bgs::launch_depth_keys64(N, V, depths, k0, gidx, s), "depth keys");
-        const int end_bit = V > 1 ? 32 + bits_for(V - 1) : 32;  // view bits only when there are views
+        BGS_CUDA(bgs::launch_depth_keys(R, depths, k0, gidx, s), "depth keys");
         size_t tmp = 0;
-        BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, k0, k1, gidx, order, (int64_t)R, 0, end_bit, s),
-                 "view/depth sort (size)");
+        BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, k0, k1, gidx, order, (int64_t)N, 0, 32, s),
+                 "view depth sort (size)");
         BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
         tmp = p->cub_tmp.bytes;
-        BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, k0, k1, gidx, order, (int64_t)R, 0, end_bit, s),
-                 "view/depth sort");
+        for (int v = 0; v < V; ++v) {
+            const size_t o = (size_t)v * N;
+            BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, k0 + o, k1 + o, gidx + o, order + o,
+                                                     (int64_t)N, 0, 32, s),
+                     "view depth sort");
+        }
         p->host_launches += 1;
         for (int v = 0; v < V; ++v)  // view v's records are positions [v N, (v+1) N) of the order
             BGS_TRY(bin_view_counting(p, N, order + (size_t)v * N, means2D, radii, Ws[v], Hs[v], tw, th, point_list,

@@ -323,20 +323,19 @@ cudaError_t launch_preprocess_backward(long long N, int V, const float *means3D,
     return cudaGetLastError();
 }
 
-// Depth sort keys of a batched binning: (view << 32 | float bits of depth), value = record.
-__global__ void __launch_bounds__(256) k_depth_keys64(long long N, int V, const float *__restrict__ depths,
-                                                      unsigned long long *__restrict__ keys, uint32_t *__restrict__ idx) {
+// Depth sort keys of a batched binning: float bits of every record's depth, value = record
+// index (each view's slice [v N, (v + 1) N) is then sorted on its own).
+__global__ void __launch_bounds__(256) k_depth_keys(long long R, const float *__restrict__ depths,
+                                                    uint32_t *__restrict__ keys, uint32_t *__restrict__ idx) {
     const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (rec >= N * V) return;
-    const unsigned long long view = (unsigned long long)(rec / N);
-    keys[rec] = (view << 32) | (unsigned long long)__float_as_uint(depths[rec]);
+    if (rec >= R) return;
+    keys[rec] = __float_as_uint(depths[rec]);
     idx[rec] = (uint32_t)rec;
 }
 
-cudaError_t launch_depth_keys64(long long N, int V, const float *depths, unsigned long long *keys, uint32_t *idx,
-                                cudaStream_t s) {
-    if (N * V == 0) return cudaSuccess;
-    k_depth_keys64<<<(unsigned)((N * V + 255) / 256), 256, 0, s>>>(N, V, depths, keys, idx);
+cudaError_t launch_depth_keys(long long R, const float *depths, uint32_t *keys, uint32_t *idx, cudaStream_t s) {
+    if (R == 0) return cudaSuccess;
+    k_depth_keys<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(R, depths, keys, idx);
     return cudaGetLastError();
 }
 
