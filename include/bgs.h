@@ -89,6 +89,9 @@ typedef struct bgs_plan_desc {
     int32_t pixel_rows;      /* sub-tile of a pixel-wise item: 8 x (4 pixel_rows) pixels, one
                                 warp, pixel_rows pixels per lane (1, 2 or 4)                 */
     int32_t select_period;   /* BGS_MODE_SELECT: forward calls between two timings (>= 1)   */
+    int32_t bin_block;       /* binning: Gaussians per counting block, a multiple of 32, or 0
+                                for automatic (>= 2048, enough to bound the tile histogram);
+                                changes speed only, never the lists                          */
 } bgs_plan_desc;
 
 typedef struct bgs_plan bgs_plan;
@@ -106,7 +109,7 @@ typedef struct bgs_stats {
 
 /* Fills *desc with defaults (threshold 512, 4 px per Gaussian-wise item, chunk 1,
    max resident blocks, LPT order on, current device, 2 pixel rows per lane, selector
-   timing every 1000 forward calls). */
+   timing every 1000 forward calls, automatic binning blocks). */
 void bgs_plan_desc_default(bgs_plan_desc *desc);
 /* Creates a plan bound to desc->device.  Allocates a small device control block. */
 int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out);

@@ -293,7 +293,7 @@ bool valid_desc(const bgs_plan_desc *d) {
                                        d->gw_pixels == 8) &&
            d->queue_chunk >= 1 && d->queue_chunk <= 1024 && d->blocks_per_sm >= 0 && d->blocks_per_sm <= 64 &&
            (d->pixel_rows == 1 || d->pixel_rows == 2 || d->pixel_rows == 4 || d->pixel_rows == 8) &&
-           d->select_period >= 1;
+           d->select_period >= 1 && d->bin_block >= 0 && d->bin_block % 32 == 0;
 }
 
 }  // namespace
@@ -312,6 +312,7 @@ void bgs_plan_desc_default(bgs_plan_desc *d) {
     d->device = -1;
     d->pixel_rows = 2;
     d->select_period = 1000;
+    d->bin_block = 0;
 }
 
 int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out) {
@@ -578,8 +579,9 @@ int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const flo
     const long long T = (long long)tiles_x * tiles_y;
     const size_t smem = bgs::bin_count_smem(tiles_x, tiles_y);
     if (smem > (size_t)p->smem_optin) return fail(BGS_ERR_INVALID, "tile grid too large for counting-sort binning");
-    // G: a multiple of 32, at least 2048, and large enough that B T stays below 2^24
-    long long G = std::max<long long>(2048, (n * T + (1ll << 24) - 1) >> 24);
+    // G: a multiple of 32; automatic: at least 2048 and large enough that B T stays below 2^24
+    long long G = p->desc.bin_block > 0 ? p->desc.bin_block
+                                        : std::max<long long>(2048, (n * T + (1ll << 24) - 1) >> 24);
     G = (G + 31) & ~31ll;
     const long long B = std::max<long long>(1, (n + G - 1) / G);
     const long long W32 = ((G + 511) / 512) * 16;  // mask words per (block, tile group)

@@ -50,7 +50,7 @@ class Plan:
 
     def __init__(self, heavy_threshold: int = 512, gw_pixels: int = 4, queue_chunk: int = 1,
                  blocks_per_sm: int = 0, lpt_order: bool = True, device=None, pixel_rows: int = 2,
-                 select_period: int = 1000):
+                 select_period: int = 1000, bin_block: int = 0):
         self._lib = _lib.load()
         if device is None:
             device = torch.cuda.current_device()
@@ -61,6 +61,7 @@ class Plan:
         d.blocks_per_sm, d.lpt_order, d.device = blocks_per_sm, int(bool(lpt_order)), self.device.index
         d.pixel_rows = pixel_rows
         d.select_period = select_period
+        d.bin_block = bin_block
         h = ctypes.c_void_p()
         check(self._lib.bgs_plan_create(ctypes.byref(d), ctypes.byref(h)), "bgs_plan_create")
         self.handle = h

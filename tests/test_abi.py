@@ -47,7 +47,7 @@ def test_host_only_calls():
     d = _lib.PlanDesc()
     lib.bgs_plan_desc_default(ctypes.byref(d))
     assert (d.heavy_threshold, d.gw_pixels, d.queue_chunk, d.lpt_order, d.device, d.pixel_rows,
-            d.select_period) == (512, 4, 1, 1, -1, 2, 1000)
+            d.select_period, d.bin_block) == (512, 4, 1, 1, -1, 2, 1000, 0)
     assert lib.bgs_workspace_size(None, 10, 10, 10, 10) == 0
     # NULL output pointer is rejected before any CUDA call
     assert lib.bgs_plan_create(ctypes.byref(d), None) == _lib.BGS_ERR_INVALID
@@ -57,6 +57,9 @@ def test_host_only_calls():
     d.select_period = 0
     assert lib.bgs_plan_create(ctypes.byref(d), ctypes.byref(h)) == _lib.BGS_ERR_INVALID
     d.select_period = 1000
+    d.bin_block = 100  # not a multiple of 32
+    assert lib.bgs_plan_create(ctypes.byref(d), ctypes.byref(h)) == _lib.BGS_ERR_INVALID
+    d.bin_block = 0
     d.gw_pixels = 3
     assert lib.bgs_plan_create(ctypes.byref(d), ctypes.byref(h)) == _lib.BGS_ERR_INVALID
     # the selector query rejects a NULL plan

@@ -89,6 +89,46 @@ def test_binning_bit_exact(R, plan, name, scale, tile, W_H):
     np.testing.assert_array_equal(_np(pl)[:K].astype(np.uint32), inp["point_list"])
 
 
+@pytest.mark.parametrize("bin_block", [32, 96, 512, 2560, 4096])
+def test_binning_block_sizes_bit_exact(R, bin_block):
+    """The counting blocks' size changes the work split only: single-word masks (32), a block
+    smaller than one 512-Gaussian pass (96), one pass (512), several passes with a partial
+    last one (2560 = 5 x 512) -- the path large frames take -- and whole passes (4096)."""
+    s = scene("cfg2", 0.02)
+    s["cameras"][0].update(W=700, H=300, cx=349.5, cy=149.5)
+    inp = oracle_render_inputs(s)
+    g = to_gpu(inp)
+    p = R.Plan(bin_block=bin_block)
+    pl, rg, K = R.bin_and_sort(p, g["means2D"], g["radii"], g["depths"], inp["W"], inp["H"])
+    torch.cuda.synchronize()
+    assert K == inp["point_list"].size
+    np.testing.assert_array_equal(_np(rg).astype(np.uint32), inp["ranges"])
+    np.testing.assert_array_equal(_np(pl)[:K].astype(np.uint32), inp["point_list"])
+    p.close()
+
+
+def test_binning_degenerate_inputs(R):
+    """No visible Gaussian, one Gaussian covering every tile, and all Gaussians at one depth."""
+    p = R.Plan(bin_block=64)
+    W, H = 100, 60
+    n = 300
+    rng = np.random.default_rng(8)
+    m2 = np.stack([rng.uniform(0, W, n), rng.uniform(0, H, n)], 1).astype(np.float32)
+    cases = {"none visible": (np.zeros(n, np.int32), rng.uniform(1, 5, n)),
+             "one covers all": (np.where(np.arange(n) == 7, 500, 0).astype(np.int32), rng.uniform(1, 5, n)),
+             "equal depths": (rng.integers(1, 40, n).astype(np.int32), np.full(n, 2.5))}
+    for what, (radii, depth) in cases.items():
+        dp = depth.astype(np.float32)
+        opl, org = oracle.bin_tiles(m2, radii, dp, W, H)
+        pl, rg, K = R.bin_and_sort(p, torch.from_numpy(m2).cuda(), torch.from_numpy(radii).cuda(),
+                                   torch.from_numpy(dp).cuda(), W, H)
+        torch.cuda.synchronize()
+        assert K == opl.size, what
+        np.testing.assert_array_equal(_np(rg).astype(np.uint32), org, err_msg=what)
+        np.testing.assert_array_equal(_np(pl)[:K].astype(np.uint32), opl, err_msg=what)
+    p.close()
+
+
 # --------------------------------------------------------------------------------- a4 / a5
 
 @pytest.mark.parametrize("mode", MODES)
