@@ -90,8 +90,8 @@ typedef struct bgs_plan_desc {
                                 warp, pixel_rows pixels per lane (1, 2 or 4)                 */
     int32_t select_period;   /* BGS_MODE_SELECT: forward calls between two timings (>= 1)   */
     int32_t bin_block;       /* binning: Gaussians per counting block, a multiple of 32, or 0
-                                for automatic (>= 2048, enough to bound the tile histogram);
-                                changes speed only, never the lists                          */
+                                for automatic (>= 2048, about 4 blocks per SM, enough to
+                                bound the tile histogram); changes speed only, not the lists */
 } bgs_plan_desc;
 
 typedef struct bgs_plan bgs_plan;

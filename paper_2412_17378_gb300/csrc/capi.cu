@@ -579,9 +579,14 @@ int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const flo
     const long long T = (long long)tiles_x * tiles_y;
     const size_t smem = bgs::bin_count_smem(tiles_x, tiles_y);
     if (smem > (size_t)p->smem_optin) return fail(BGS_ERR_INVALID, "tile grid too large for counting-sort binning");
-    // G: a multiple of 32; automatic: at least 2048 and large enough that B T stays below 2^24
-    long long G = p->desc.bin_block > 0 ? p->desc.bin_block
-                                        : std::max<long long>(2048, (n * T + (1ll << 24) - 1) >> 24);
+    // G: a multiple of 32.  Automatic: at least 2048, about 4 counting blocks per SM (fewer,
+    // longer blocks keep the scatter's per-(block, tile group) overhead down), and large
+    // enough that B T stays below 2^24
+    long long G = p->desc.bin_block;
+    if (G <= 0) {
+        G = std::max<long long>(2048, (n + 4ll * p->num_sms - 1) / (4ll * std::max(1, p->num_sms)));
+        G = std::max<long long>(G, (n * T + (1ll << 24) - 1) >> 24);
+    }
     G = (G + 31) & ~31ll;
     const long long B = std::max<long long>(1, (n + G - 1) / G);
     const long long W32 = ((G + 511) / 512) * 16;  // mask words per (block, tile group)
