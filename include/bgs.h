@@ -52,7 +52,7 @@ extern "C" {
 #define BGS_CHECK_INDEX 1u        /* point_list held an index >= N                         */
 #define BGS_CHECK_RANGE 2u        /* a tile range pointed past num_entries                 */
 #define BGS_CHECK_OVERFLOW 4u     /* binning produced more entries than the capacity        */
-#define BGS_CHECK_QUEUE 8u        /* the work queue did not drain exactly once              */
+#define BGS_CHECK_QUEUE 8u        /* a persistent pass did not run every queued item once   */
 
 /* ---- render modes (Sec. 4 of the paper and its selector, Sec. 4.4) ------------------ */
 #define BGS_MODE_AUTO 0     /* persistent queue; per-tile choice: Gaussian-wise for tiles whose
@@ -146,6 +146,11 @@ int bgs_plan_selector(const bgs_plan *plan, int32_t *switched, int64_t *calls, i
                       double *last_balanced_ms, double *last_static_ms);
 /* Restarts the selector: balanced kernels, no calls, no measurements. */
 int bgs_plan_selector_reset(bgs_plan *plan);
+/* Fault injection for tests, on the host side (nothing faults on the device): which =
+   BGS_CHECK_QUEUE marks every item of the next persistent pass's queue as already taken,
+   so that pass renders nothing and its drain check raises BGS_CHECK_QUEUE, reported by the
+   next bgs_check.  One-shot. */
+int bgs_plan_inject_fault(bgs_plan *plan, uint32_t which);
 const char *bgs_last_error(void);
 
 /* ---- a1: projection (Eq. 1-3) ------------------------------------------------------

@@ -27,9 +27,30 @@ struct DevCtrl {
     unsigned long long contrib_pairs;
     unsigned long long items_done;
     unsigned int queue_head_g;  // Gaussian-wise queue cursor (starts at 0)
-    unsigned int pad0;
+    unsigned int pass_items;    // items the current persistent pass completed
     unsigned long long bin_base;  // binning: first point_list slot of the view being binned
+    unsigned int warps_done;    // blocks of the current persistent pass that finished
+    unsigned int pad1;
 };
+
+// End of a persistent pass, per warp (lane 0), for a block of `warps_per_block` warps whose
+// shared counters blk[0] (items) and blk[1] (finished warps) start at 0: the block's last
+// warp adds the block's completed items to the pass total, and the pass's last block
+// (`pass_blocks` in all) compares the total with the queued item count and raises
+// BGS_CHECK_QUEUE unless every item ran exactly once.
+__device__ __forceinline__ void finish_pass(DevCtrl *ctrl, unsigned long long items, unsigned int *blk,
+                                            int warps_per_block, int pass_blocks) {
+    atomicAdd(&blk[0], (unsigned int)items);
+    __threadfence_block();
+    if (atomicAdd(&blk[1], 1u) != (unsigned int)warps_per_block - 1u) return;
+    atomicAdd(&ctrl->pass_items, atomicAdd(&blk[0], 0u));
+    __threadfence();
+    if (atomicAdd(&ctrl->warps_done, 1u) == (unsigned int)pass_blocks - 1u) {
+        __threadfence();
+        const unsigned int done = atomicAdd(&ctrl->pass_items, 0u);
+        if (done != *((volatile unsigned int *)&ctrl->num_items)) atomicOr(&ctrl->check_bits, BGS_CHECK_QUEUE);
+    }
+}
 
 // Pixel-wise items: Q = pixel rows per lane (the plan's sub-tile knob, 1, 2, 4 or 8).  For
 // Q <= 4 an item covers 8 x 4Q pixels of a tile and lane l owns the pixels (l % 8, l / 8 +
@@ -192,7 +213,8 @@ struct FwdArgs {
     ViewTable vt;
     ViewOut io;
     DevCtrl *ctrl;
-    const uint2 *items;          // work list (persistent kernels)
+    const uint2 *items;
+    int pass_blocks;  // blocks of the persistent pass (both forward kernels when both run)          // work list (persistent kernels)
     int gw_pixels;
     int pixel_rows;              // Q of the pixel-wise items
     int chunk;
@@ -212,6 +234,7 @@ struct BwdArgs {
     float *grad_acc;             // [N][12] accumulators (10 used)
     DevCtrl *ctrl;
     const uint2 *items;
+    unsigned int *warp_items;  // per warp of the persistent pass: items it completed
     int pixel_rows;
     int chunk;
 };
@@ -278,6 +301,9 @@ cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int mode, int
 cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, const ViewTable &vt,
                                  int tile_w, int tile_h, int mode, int heavy_threshold, int gw_pixels,
                                  int pixel_rows, uint32_t *counts, cudaStream_t s);
+// queue of the current list: rewind for another pass / mark exhausted (fault injection)
+cudaError_t launch_rewind_queue(DevCtrl *ctrl, cudaStream_t s);
+cudaError_t launch_exhaust_queue(DevCtrl *ctrl, cudaStream_t s);
 cudaError_t launch_emit_items(const uint32_t *order, const uint32_t *counts, const uint32_t *offsets,
                               int num_tiles, const uint2 *ranges, int mode, int heavy_threshold, uint2 *items,
                               DevCtrl *ctrl, cudaStream_t s);
@@ -296,6 +322,6 @@ const void *backward_balanced_kernel(const BwdArgs &a);  // the instantiation a 
 // gradients of N records; colours have n_colors rows (n_colors < N: summed over views)
 cudaError_t launch_grad_finalize(long long N, long long n_colors, const float4 *acc, float *dL_dmeans2D,
                                  float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,
-                                 cudaStream_t s);
+                                 const unsigned int *warp_items, int n_warps, DevCtrl *ctrl, cudaStream_t s);
 
 }  // namespace bgs

@@ -84,7 +84,7 @@ struct bgs_plan {
     Buf bin_h, bin_total, bin_start, bin_rect, bin_mask;  // counting-sort binning
     int smem_optin = 0;
     // render
-    Buf recs, tile_key, tile_key2, tile_idx, tile_idx2, counts, item_off, items, grad_acc;
+    Buf recs, tile_key, tile_key2, tile_idx, tile_idx2, counts, item_off, items, grad_acc, warp_items;
     // batched binning: depth keys of every view
     Buf vkey, vkey_sorted;
     // captured CUDA graph
@@ -102,6 +102,7 @@ struct bgs_plan {
         int tw, th, mode, heavy_threshold, gw_pixels, pixel_rows, lpt_order;
     } wl_key;
     bool rec_valid = false, wl_valid = false;
+    unsigned int inject = 0;  // BGS_CHECK_* fault to inject into the next persistent pass
     // BGS_MODE_SELECT (Sec. 4.4)
     bool sel_switched = false;
     long long sel_calls = 0, sel_measurements = 0;
@@ -109,6 +110,13 @@ struct bgs_plan {
 };
 
 namespace {
+
+// A fault requested by bgs_plan_inject_fault, applied once before the next persistent pass.
+int inject_pending_fault(bgs_plan *p, cudaStream_t s) {
+    if (p->inject & BGS_CHECK_QUEUE) BGS_CUDA(bgs::launch_exhaust_queue(p->ctrl, s), "inject queue fault");
+    p->inject = 0;
+    return BGS_OK;
+}
 
 int ensure(bgs_plan *p, Buf &b, size_t bytes, cudaStream_t s, const char *what) {
     if (bytes == 0) bytes = 16;
@@ -353,7 +361,7 @@ int bgs_plan_destroy(bgs_plan *p) {
     Buf *bufs[] = {&p->vkey, &p->vkey_sorted, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_rect, &p->bin_mask, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
-                   &p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off, &p->items,
+                   &p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off, &p->items, &p->warp_items,
                    &p->grad_acc};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -440,6 +448,13 @@ int bgs_plan_selector(const bgs_plan *p, int32_t *switched, int64_t *calls, int6
     if (measurements) *measurements = p->sel_measurements;
     if (last_balanced_ms) *last_balanced_ms = p->sel_last_balanced;
     if (last_static_ms) *last_static_ms = p->sel_last_static;
+    return BGS_OK;
+}
+
+int bgs_plan_inject_fault(bgs_plan *p, uint32_t which) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_plan_inject_fault: NULL plan");
+    if (which & ~(unsigned)BGS_CHECK_QUEUE) return fail(BGS_ERR_INVALID, "bgs_plan_inject_fault: unsupported fault");
+    p->inject |= which;
     return BGS_OK;
 }
 
@@ -815,6 +830,8 @@ int render_forward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewOu
     // AUTO with a threshold no list can exceed queues no Gaussian-wise item
     const bool gauss = mode == BGS_MODE_GAUSSIAN ||
                        (mode == BGS_MODE_AUTO && (int64_t)p->desc.heavy_threshold < num_entries);
+    a.pass_blocks = (gauss ? grid_g : 0) + (mode != BGS_MODE_GAUSSIAN ? grid_p : 0);
+    BGS_TRY(inject_pending_fault(p, s));
     KernelTimer kt(p, s, &p->ev_fwd);
     if (gauss) BGS_CUDA(bgs::launch_forward_gauss(a, grid_g, s), "forward_gauss");
     if (mode != BGS_MODE_GAUSSIAN) BGS_CUDA(bgs::launch_forward_pixel(a, grid_p, gauss, s), "forward_pixel");
@@ -853,6 +870,7 @@ int render_backward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewG
     a.ctrl = p->ctrl;
     a.pixel_rows = p->desc.pixel_rows;
     a.chunk = p->desc.queue_chunk;
+    int n_warps = 0;  // warps of the persistent pass whose item counts finalize checks
     if (mode == BGS_MODE_STATIC) {
         if (vt.V != 1) return fail(BGS_ERR_INVALID, "the static kernel renders one view");
         KernelTimer kt(p, s, &p->ev_bwd);
@@ -875,20 +893,26 @@ int render_backward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewG
         a.recs = (const bgs::Rec *)p->recs.p;
         const bgs_plan::WlKey wk = worklist_key(p, ranges, vt, tw, th, BGS_MODE_PIXEL);
         if (p->wl_valid && memcmp(&wk, &p->wl_key, sizeof wk) == 0) {
-            // same list (no Gaussian-wise items): rewind the pixel-wise queue cursor
-            BGS_CUDA(cudaMemsetAsync(&p->ctrl->queue_head, 0, sizeof(unsigned int), s), "rewind queue");
+            // same list (no Gaussian-wise items): rewind its queue
+            BGS_CUDA(bgs::launch_rewind_queue(p->ctrl, s), "rewind queue");
+            p->host_launches += 1;
         } else {
             BGS_TRY(build_worklist(p, ranges, vt, tw, th, BGS_MODE_PIXEL, num_entries, s));
         }
         a.items = (const uint2 *)p->items.p;
         const int grid = grid_for(p, bgs::backward_balanced_kernel(a), bgs::backward_balanced_block_threads());
+        n_warps = grid * (bgs::backward_balanced_block_threads() / 32);
+        BGS_TRY(ensure(p, p->warp_items, sizeof(unsigned int) * n_warps, s, "warp_items"));
+        a.warp_items = (unsigned int *)p->warp_items.p;
+        BGS_TRY(inject_pending_fault(p, s));
         KernelTimer kt(p, s, &p->ev_bwd);
         BGS_CUDA(bgs::launch_backward_balanced(a, grid, s), "backward_balanced");
         kt.stop();
         p->host_launches += 1;  // kernel
     }
     BGS_CUDA(bgs::launch_grad_finalize(n_records, n_colors, (const float4 *)p->grad_acc.p, dL_dmeans2D, dL_dconic,
-                                       dL_dopacity, dL_dcolors, dL_ddepths, s),
+                                       dL_dopacity, dL_dcolors, dL_ddepths, (const unsigned int *)p->warp_items.p,
+                                       n_warps, p->ctrl, s),
              "grad_finalize");
     p->host_launches += 1;  // finalize
     return BGS_OK;

@@ -19,6 +19,8 @@
 // lane only sums gp, gp dy and gp dy^2 over its pixels (which share dx), forms the five
 // moments once, and the conic is applied after the warp sum.  A final pass scales and
 // scatters the accumulator into the ABI's gradient arrays.
+#include <algorithm>
+
 #include "bgs_internal.cuh"
 
 namespace bgs {
@@ -348,6 +350,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_backward_balanced(BwdArgs a)
     uint32_t *gbuf = sidx[warp];
     const unsigned num_items = a.ctrl->num_items;
     const unsigned chunk = (unsigned)a.chunk;
+    unsigned long long st_items = 0;
     while (true) {
         unsigned first = 0;
         if (lane == 0) first = atomicAdd(&a.ctrl->queue_head, chunk);
@@ -357,8 +360,11 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_backward_balanced(BwdArgs a)
         for (unsigned it = first; it < end; ++it) {
             const uint2 item = a.items[it];
             bwd_pixel_item<Q, Extra>(a, (int)item.x, (int)(item.y & ~kKindGauss), buf, gbuf, lane);
+            ++st_items;
         }
     }
+    // the warp's completed items; k_grad_finalize checks their sum (the queue's drain)
+    if (lane == 0) a.warp_items[blockIdx.x * kBwdWarps + warp] = (unsigned int)st_items;
 }
 
 int backward_balanced_block_threads() { return kBwdWarps * 32; }
@@ -394,7 +400,23 @@ cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s)
 __global__ void __launch_bounds__(256) k_grad_finalize(long long N, long long n_colors, const float4 *__restrict__ acc,
                                                        float *__restrict__ dL_dmeans2D, float *__restrict__ dL_dconic,
                                                        float *__restrict__ dL_dopacity, float *__restrict__ dL_dcolors,
-                                                       float *__restrict__ dL_ddepths) {
+                                                       float *__restrict__ dL_ddepths,
+                                                       const unsigned int *__restrict__ warp_items, int n_warps,
+                                                       DevCtrl *ctrl) {
+    if (blockIdx.x == 0 && n_warps > 0) {
+        // drain check of the persistent backward pass: every queued item ran exactly once
+        __shared__ unsigned int part[8];
+        unsigned int sum = 0;
+        for (int w = threadIdx.x; w < n_warps; w += blockDim.x) sum += warp_items[w];
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned int total = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += part[w];
+            if (total != ctrl->num_items) atomicOr(&ctrl->check_bits, BGS_CHECK_QUEUE);
+        }
+    }
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float4 a0 = acc[3 * i], a1 = acc[3 * i + 1], a2 = acc[3 * i + 2];
@@ -432,10 +454,10 @@ __global__ void __launch_bounds__(256) k_grad_colors(long long N, long long n_co
 
 cudaError_t launch_grad_finalize(long long N, long long n_colors, const float4 *acc, float *dL_dmeans2D,
                                  float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,
-                                 cudaStream_t s) {
-    if (N == 0) return cudaSuccess;
-    k_grad_finalize<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, n_colors, acc, dL_dmeans2D, dL_dconic, dL_dopacity,
-                                                                 dL_dcolors, dL_ddepths);
+                                 const unsigned int *warp_items, int n_warps, DevCtrl *ctrl, cudaStream_t s) {
+    if (N == 0 && n_warps == 0) return cudaSuccess;
+    k_grad_finalize<<<(unsigned)std::max<long long>(1, (N + 255) / 256), 256, 0, s>>>(
+        N, n_colors, acc, dL_dmeans2D, dL_dconic, dL_dopacity, dL_dcolors, dL_ddepths, warp_items, n_warps, ctrl);
     if (n_colors != N && n_colors > 0)
         k_grad_colors<<<(unsigned)((n_colors + 255) / 256), 256, 0, s>>>(N, n_colors, acc, dL_dcolors);
     return cudaGetLastError();

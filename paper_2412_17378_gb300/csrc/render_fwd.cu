@@ -396,6 +396,9 @@ __device__ __forceinline__ void flush_stats(const FwdArgs &a, int lane, unsigned
 template <int P>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_gauss(FwdArgs a) {
     asm volatile("griddepcontrol.launch_dependents;");
+    __shared__ unsigned int blk[2];
+    if (threadIdx.x == 0) blk[0] = blk[1] = 0u;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned num_items = a.ctrl->num_gauss;
     const unsigned chunk = (unsigned)a.chunk;
@@ -413,12 +416,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_gauss(FwdArgs a
         }
     }
     flush_stats(a, lane, st_eval, st_acc, st_items);
+    if (lane == 0) finish_pass(a.ctrl, st_items, blk, kWarpsPerBlock, a.pass_blocks);
 }
 
 // Pixel-wise items [num_gauss, num_items) of the work list.
 template <int Q>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_pixel(FwdArgs a) {
     __shared__ Rec sbuf[kWarpsPerBlock][32];
+    __shared__ unsigned int blk[2];
+    if (threadIdx.x == 0) blk[0] = blk[1] = 0u;
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Rec *buf = sbuf[warp];
     const unsigned num_items = a.ctrl->num_items;
@@ -437,6 +444,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_pixel(FwdArgs a
         }
     }
     flush_stats(a, lane, st_eval, st_acc, st_items);
+    if (lane == 0) finish_pass(a.ctrl, st_items, blk, kWarpsPerBlock, a.pass_blocks);
 }
 
 int forward_balanced_block_threads() { return kWarpsPerBlock * 32; }

@@ -107,6 +107,8 @@ __global__ void k_emit_items(const uint32_t *__restrict__ order, const uint32_t 
             ctrl->num_gauss = ng;
             ctrl->queue_head = ng;
             ctrl->queue_head_g = 0u;
+            ctrl->pass_items = 0u;
+            ctrl->warps_done = 0u;
         }
         if (i == num_tiles - 1) ctrl->num_items = off + c;
     }
@@ -119,6 +121,31 @@ cudaError_t launch_emit_items(const uint32_t *order, const uint32_t *counts, con
     const long long threads = (long long)num_tiles * 32;
     k_emit_items<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(order, counts, offsets, num_tiles, ranges, mode,
                                                                    heavy_threshold, items, ctrl);
+    return cudaGetLastError();
+}
+
+// Rewinds the queue of the current (pixel-wise) list for another persistent pass.
+__global__ void k_rewind_queue(DevCtrl *ctrl) {
+    ctrl->queue_head = ctrl->num_gauss;
+    ctrl->queue_head_g = 0u;
+    ctrl->pass_items = 0u;
+    ctrl->warps_done = 0u;
+}
+
+// Host-requested fault: marks every queued item as taken, so the next pass runs none of
+// them (its drain check must then raise BGS_CHECK_QUEUE).
+__global__ void k_exhaust_queue(DevCtrl *ctrl) {
+    ctrl->queue_head = ctrl->num_items;
+    ctrl->queue_head_g = ctrl->num_gauss;
+}
+
+cudaError_t launch_rewind_queue(DevCtrl *ctrl, cudaStream_t s) {
+    k_rewind_queue<<<1, 1, 0, s>>>(ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exhaust_queue(DevCtrl *ctrl, cudaStream_t s) {
+    k_exhaust_queue<<<1, 1, 0, s>>>(ctrl);
     return cudaGetLastError();
 }
 

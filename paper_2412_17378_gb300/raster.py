@@ -88,6 +88,10 @@ class Plan:
         return dict(switched=bool(sw.value), calls=calls.value, measurements=meas.value, balanced_ms=tb.value,
                     static_ms=ts.value)
 
+    def inject_fault(self, which: int):
+        """bgs_plan_inject_fault: a host-side fault for tests (e.g. _lib.CHECK_QUEUE)."""
+        check(self._lib.bgs_plan_inject_fault(self.handle, int(which)), "bgs_plan_inject_fault")
+
     def selector_reset(self):
         check(self._lib.bgs_plan_selector_reset(self.handle), "bgs_plan_selector_reset")
 

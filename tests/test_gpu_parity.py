@@ -317,6 +317,48 @@ def test_device_checks_report_bad_indices_and_ranges(R, plan, cfg1):
     plan.check()  # bits were cleared
 
 
+def test_queue_drain_check_reports_injected_fault(R, cfg1):
+    """Every persistent pass checks that it ran each queued item exactly once.  A host-side
+    fault (the queue marked exhausted before the pass) must surface as BGS_CHECK_QUEUE;
+    the next, clean passes report nothing."""
+    from paper_2412_17378_gb300 import _lib
+    p = R.Plan(heavy_threshold=64)
+    g = to_gpu(cfg1)
+    W, H = cfg1["W"], cfg1["H"]
+    rng = np.random.default_rng(9)
+    gC = torch.from_numpy(rng.normal(size=(3, H, W)).astype(np.float32)).cuda()
+
+    def fwd(mode):
+        return R.render_forward(p, g["means2D"], g["conic_opacity"], g["colors"], g["depths"], g["point_list"], g["K"],
+                                g["ranges"], W, H, (16, 16), (0, 0, 0), mode)
+
+    def bwd(out, mode):
+        R.render_backward(p, g["means2D"], g["conic_opacity"], g["colors"], g["depths"], g["point_list"], g["K"],
+                          g["ranges"], W, H, out["final_T"], out["n_contrib"], gC, None, None, (16, 16), (0, 0, 0),
+                          mode)
+
+    for mode in ("auto", "pixel", "gaussian"):
+        out = fwd(mode)
+        bwd(out, mode)
+        torch.cuda.synchronize()
+        p.check()  # clean passes
+        p.inject_fault(_lib.CHECK_QUEUE)
+        out = fwd(mode)
+        with pytest.raises(R.BgsError) as e:
+            p.check()
+        assert e.value.code == -4 and "queue" in str(e.value)
+        out = fwd(mode)
+        p.inject_fault(_lib.CHECK_QUEUE)
+        bwd(out, mode)
+        with pytest.raises(R.BgsError) as e:
+            p.check()
+        assert "queue" in str(e.value)
+        bwd(out, mode)
+        torch.cuda.synchronize()
+        p.check()
+    p.close()
+
+
 def test_exp2_accuracy(R):
     """The render kernels' exponential (ex2.approx.ftz) against float64 2^x on the range the
     blend uses (alpha >= 1/255 needs 2^x >= 1/255 with x <= 0)."""
