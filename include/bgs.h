@@ -146,6 +146,10 @@ int bgs_plan_selector(const bgs_plan *plan, int32_t *switched, int64_t *calls, i
                       double *last_balanced_ms, double *last_static_ms);
 /* Restarts the selector: balanced kernels, no calls, no measurements. */
 int bgs_plan_selector_reset(bgs_plan *plan);
+/* Restores a selector state read with bgs_plan_selector (resuming a run from a checkpoint):
+   switched 0 / 1, calls and measurements >= 0, the last timings >= 0. */
+int bgs_plan_selector_restore(bgs_plan *plan, int32_t switched, int64_t calls, int64_t measurements,
+                              double last_balanced_ms, double last_static_ms);
 /* Fault injection for tests, on the host side (nothing faults on the device): which =
    BGS_CHECK_QUEUE marks every item of the next persistent pass's queue as already taken,
    so that pass renders nothing and its drain check raises BGS_CHECK_QUEUE, reported by the

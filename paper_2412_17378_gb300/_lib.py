@@ -35,7 +35,7 @@ EXPORTS = [
     "bgs_render_backward", "bgs_probe_pipe_rates", "bgs_debug_exp2", "bgs_plan_timing", "bgs_plan_kernel_ms",
     "bgs_render_forward_noalloc", "bgs_preprocess_batched", "bgs_bin_and_sort_batched",
     "bgs_preprocess_backward", "bgs_preprocess_backward_batched", "bgs_plan_selector", "bgs_plan_selector_reset",
-    "bgs_plan_inject_fault",
+    "bgs_plan_inject_fault", "bgs_plan_selector_restore",
     "bgs_render_forward_batched", "bgs_render_backward_batched", "bgs_graph_begin", "bgs_graph_end",
     "bgs_graph_launch", "bgs_autotune_render",
 ]
@@ -112,6 +112,7 @@ def load(build_if_needed: bool = True):
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         lib.bgs_plan_selector_reset.argtypes = [P]
         lib.bgs_plan_inject_fault.argtypes = [P, ctypes.c_uint32]
+        lib.bgs_plan_selector_restore.argtypes = [P, i32, i64, i64, ctypes.c_double, ctypes.c_double]
         lib.bgs_plan_timing.argtypes = [P, i32]
         lib.bgs_plan_kernel_ms.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]

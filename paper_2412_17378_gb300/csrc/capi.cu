@@ -451,6 +451,20 @@ int bgs_plan_selector(const bgs_plan *p, int32_t *switched, int64_t *calls, int6
     return BGS_OK;
 }
 
+int bgs_plan_selector_restore(bgs_plan *p, int32_t switched, int64_t calls, int64_t measurements,
+                              double last_balanced_ms, double last_static_ms) {
+    if (!p) return fail(BGS_ERR_INVALID, "bgs_plan_selector_restore: NULL plan");
+    if ((switched != 0 && switched != 1) || calls < 0 || measurements < 0 || measurements > calls ||
+        !(last_balanced_ms >= 0.0) || !(last_static_ms >= 0.0))
+        return fail(BGS_ERR_INVALID, "bgs_plan_selector_restore: inconsistent state");
+    p->sel_switched = switched != 0;
+    p->sel_calls = calls;
+    p->sel_measurements = measurements;
+    p->sel_last_balanced = last_balanced_ms;
+    p->sel_last_static = last_static_ms;
+    return BGS_OK;
+}
+
 int bgs_plan_inject_fault(bgs_plan *p, uint32_t which) {
     if (!p) return fail(BGS_ERR_INVALID, "bgs_plan_inject_fault: NULL plan");
     if (which & ~(unsigned)BGS_CHECK_QUEUE) return fail(BGS_ERR_INVALID, "bgs_plan_inject_fault: unsupported fault");

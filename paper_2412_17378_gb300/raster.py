@@ -88,6 +88,20 @@ class Plan:
         return dict(switched=bool(sw.value), calls=calls.value, measurements=meas.value, balanced_ms=tb.value,
                     static_ms=ts.value)
 
+    def state_dict(self) -> dict:
+        """The plan's resumable state: its knobs (device excluded) and the selector's state --
+        what a training run checkpoints to resume with the same kernels (plain JSON types)."""
+        knobs = {k: int(v) for k, v in self.desc().items() if k != "device"}
+        return {"knobs": knobs, "selector": self.selector()}
+
+    def load_state_dict(self, state: dict):
+        """Restores a state_dict() (knobs, then the selector)."""
+        self.set(**state["knobs"])
+        sel = state["selector"]
+        check(self._lib.bgs_plan_selector_restore(self.handle, int(bool(sel["switched"])), int(sel["calls"]),
+                                                  int(sel["measurements"]), float(sel["balanced_ms"]),
+                                                  float(sel["static_ms"])), "bgs_plan_selector_restore")
+
     def inject_fault(self, which: int):
         """bgs_plan_inject_fault: a host-side fault for tests (e.g. _lib.CHECK_QUEUE)."""
         check(self._lib.bgs_plan_inject_fault(self.handle, int(which)), "bgs_plan_inject_fault")

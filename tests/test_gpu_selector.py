@@ -77,3 +77,20 @@ def test_selector_is_single_view(R):
     with pytest.raises(R.BgsError):
         R.render_forward_batched(plan, m2, co, z((n, 3)).cuda(), dp, pl, 0, rg, cams, mode="select")
     plan.close()
+
+
+def test_plan_state_round_trips_through_json(R):
+    """Checkpoint / resume: the knobs and the selector state survive a JSON round trip."""
+    import json
+    a = R.Plan(heavy_threshold=2048, pixel_rows=4, select_period=7, bin_block=4096)
+    assert a._lib.bgs_plan_selector_restore(a.handle, 1, 1234, 3, 0.5, 0.4) == 0
+    state = json.loads(json.dumps(a.state_dict()))
+    b = R.Plan()
+    b.load_state_dict(state)
+    assert b.state_dict() == a.state_dict()
+    assert b.selector()["switched"] and b.selector()["calls"] == 1234
+    from paper_2412_17378_gb300._lib import check
+    with pytest.raises(R.BgsError):  # more measurements than calls: refused
+        check(b._lib.bgs_plan_selector_restore(b.handle, 0, 1, 5, 0.0, 0.0), "restore")
+    a.close()
+    b.close()
