@@ -105,14 +105,14 @@ __device__ __forceinline__ bool pair_backward(const Rec &r, const PairX &x, floa
         s.R1 += al * d1;
         s.R2 += al * d2;
         const float oG = r.b.y * G;
-        if (oG <= kAlphaMax) {  // alpha = min(0.99, o G): no gradient through the clamp
-            const float gp = oG * dLda;
-            const float gpy = gp * dy;
-            a.g += gp;
-            a.gy += gpy;
-            a.gyy += gpy * dy;
-            a.o += G * dLda;
-        }
+        // alpha = min(0.99, o G): no gradient through the clamp (branch-free)
+        const float gG = oG <= kAlphaMax ? G * dLda : 0.f;  // dL/do
+        const float gp = r.b.y * gG;                          // dL/dpower2
+        const float gpy = gp * dy;
+        a.g += gp;
+        a.gy += gpy;
+        a.gyy += gpy * dy;
+        a.o += gG;
     }
     return valid;
 }
