@@ -506,11 +506,21 @@ def main_views(args, scene, rank, world, local):
         plan.check()
         if world > 1:
             torch.distributed.barrier()
+        # nvidia-smi samples every 200 ms while the GPU replays the step: ~0.6 s of untimed
+        # replays of the same graph right before the timed region (too short on its own to be
+        # sampled), then the timed region
         clocks = ClockSampler(local)
         clocks.start()
-        time.sleep(0.3)
+        if not args.quick:
+            t_load = time.perf_counter()
+            while time.perf_counter() - t_load < 0.6:
+                for _ in range(8):
+                    raster.graph_launch(plan)
+                side.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         side.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         e0.record(side)
         for _ in range(args.steps):
             raster.graph_launch(plan)
@@ -518,6 +528,7 @@ def main_views(args, scene, rank, world, local):
         side.synchronize()
         ms_total = e0.elapsed_time(e1)
         clk = clocks.stop()
+        clk["note"] = "samples taken under ~0.6 s of back-to-back replays of the timed step and the timed region"
         plan.check()
         ms_total = max_over_ranks(ms_total, world, dev)
         ms_step = ms_total / args.steps
