@@ -48,14 +48,16 @@ WORKLOAD = WORKLOADS["cfg2"]
 # shared by the 4 pixels of a lane: 1 op per pair):
 #  forward, every evaluated pair: shared dx terms (1), dy (1), power (2 FMA), o*G and the
 #          0.99 clamp (2), the power <= 0 and alpha >= 1/255 tests (2) = 8 FP32-pipe ops
-#          + 1 MUFU ex2; every accumulated pair: 1-alpha, T', the T test, w, 5 FMA = 9;
+#          + 1 MUFU ex2; every accumulated pair: T' = T - T alpha (1 FMA), the T test, w,
+#          4 FMA (colour, depth) = 7 (the accumulated alpha is 1 - T, written once per pixel);
 #  backward, every pair before the last contributor: the forward's 8 + the n_contrib test
 #          = 9, + 1 ex2 (recompute); every accumulated pair: 1-alpha, T/(1-alpha), w,
-#          3 colour FMA, 3 (c - R), dL/dalpha (4), 3 R updates, o G, clamp test, dL/dpower,
-#          its dy product and 4 sums = 24 FP32-pipe ops + 1 MUFU rcp.
+#          3 colour FMA, c . dL/dC (3), minus R . dL/dC (1), dL/dalpha (1), the R . dL/dC
+#          update (1), clamp test, dL/dpower, its dy product and 3 sums = 18 FP32-pipe ops
+#          + 1 MUFU rcp (dL/dopacity is the dL/dpower sum over o, once per record).
 # (The warp reductions and atomics of the backward are aggregation overhead, not counted.)
-FWD_EVAL_FP32, FWD_EVAL_MUFU, FWD_ACC_FP32 = 8, 1, 9
-BWD_EVAL_FP32, BWD_EVAL_MUFU, BWD_ACC_FP32, BWD_ACC_MUFU = 9, 1, 24, 1
+FWD_EVAL_FP32, FWD_EVAL_MUFU, FWD_ACC_FP32 = 8, 1, 7
+BWD_EVAL_FP32, BWD_EVAL_MUFU, BWD_ACC_FP32, BWD_ACC_MUFU = 9, 1, 18, 1
 FP32_LANES_PER_SM_CLK = 128
 
 

@@ -161,6 +161,10 @@ __device__ __forceinline__ float pair_power2(float4 a, float qc, float px, float
     return pair_power2_y(x, a.y, qc, py, dy);
 }
 
+// Transmittance after a pair, T (1 - alpha), as one fused multiply-add T - T alpha (one
+// rounding); every forward kernel takes its stop decision T' < 1e-4 on this value.
+__device__ __forceinline__ float next_T(float T, float al) { return __fmaf_rn(-T, al, T); }
+
 __device__ __forceinline__ float pair_alpha(float power2, float o, float &G) {
     G = ex2_approx(power2);
     return fminf(kAlphaMax, __fmul_rn(o, G));

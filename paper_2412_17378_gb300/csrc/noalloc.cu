@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kNaWarps * 32) k_na_forward(NaArgs a, NaScratc
             rg = make_uint2(0u, 0u);
         }
         const float pxf = (float)px, pyf = (float)py;
-        float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, D = 0.f, A = 0.f;
+        float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, D = 0.f;
         int last = 0, neval = (int)(rg.y - rg.x);
         bool done = !inside;
         for (uint32_t base = rg.x; base < rg.y; base += 32) {
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kNaWarps * 32) k_na_forward(NaArgs a, NaScratc
                 const float p2 = pair_power2(ra, rb.x, pxf, pyf, dx, dy);
                 const float al = pair_alpha(p2, rb.y, G);
                 if (!done && p2 <= 0.f && al >= kAlphaMin) {
-                    const float tt = T * (1.f - al);
+                    const float tt = next_T(T, al);
                     if (tt < kTMin) {
                         done = true;
                         neval = (int)(base + k + 1 - rg.x);
@@ -146,7 +146,6 @@ __global__ void __launch_bounds__(kNaWarps * 32) k_na_forward(NaArgs a, NaScratc
                         c1 += w * rc.y;
                         c2 += w * rc.z;
                         D += w * rc.w;
-                        A += w;
                         T = tt;
                         last = (int)(base + k + 1 - rg.x);
                     }
@@ -159,7 +158,7 @@ __global__ void __launch_bounds__(kNaWarps * 32) k_na_forward(NaArgs a, NaScratc
             a.out_color[HW + pid] = c1 + T * a.bg[1];
             a.out_color[2 * HW + pid] = c2 + T * a.bg[2];
             a.out_depth[pid] = D;
-            a.out_alpha[pid] = A;
+            a.out_alpha[pid] = 1.f - T;  // sum of alpha_i T_i telescopes to 1 - T
             a.final_T[pid] = T;
             a.n_contrib[pid] = last;
             if (a.n_eval) a.n_eval[pid] = neval;

@@ -17,8 +17,11 @@
 // With gp = dL/dpower2 of a pair, the mean and conic gradients of a Gaussian are sums of
 // gp times (dx, dy, dx^2, dx dy, dy^2) combined with the Gaussian's (constant) conic, so a
 // lane only sums gp, gp dy and gp dy^2 over its pixels (which share dx), forms the five
-// moments once, and the conic is applied after the warp sum.  A final pass scales and
-// scatters the accumulator into the ABI's gradient arrays.
+// moments once, and the conic is applied after the warp sum.  Two identities shorten the
+// per-pair work: R_i enters dL/dalpha only through R_i . dL/dC, so a pixel carries that
+// scalar (updated by the same recurrence) instead of R_i; and dL/do = sum G dL/dalpha =
+// (sum gp) / o, so the opacity gradient is the gp sum divided once by o.  A final pass
+// scales and scatters the accumulator into the ABI's gradient arrays.
 #include <algorithm>
 
 #include "bgs_internal.cuh"
@@ -29,7 +32,8 @@ constexpr unsigned kFullB = 0xffffffffu;
 constexpr int kBwdWarps = 8;
 
 struct PixState {
-    float T, Tf, g0, g1, g2, gD, gA, R0, R1, R2, Rd;
+    float T, Tf, g0, g1, g2, gD, gA;
+    float Rg, Rd;  // R . dL/dC (colour behind the entry, dotted with the pixel's colour gradient), depth behind
     int nc;
 };
 
@@ -53,9 +57,7 @@ __device__ __forceinline__ PixState load_pixel(const BwdArgs &a, int v, int px, 
         s.g0 = s.g1 = s.g2 = s.gD = s.gA = 0.f;
     }
     s.Tf = s.T;
-    s.R0 = a.bg[0];
-    s.R1 = a.bg[1];
-    s.R2 = a.bg[2];
+    s.Rg = a.bg[0] * s.g0 + a.bg[1] * s.g1 + a.bg[2] * s.g2;
     s.Rd = 0.f;
     return s;
 }
@@ -63,27 +65,28 @@ __device__ __forceinline__ PixState load_pixel(const BwdArgs &a, int v, int px, 
 // Per-lane sums of one record's pair contributions over the lane's pixels.
 struct PairSums {
     float g, gy, gyy;  // sum of gp, gp dy, gp dy^2 (gp = dL/dpower2, power2 the log2 exponent)
-    float o;           // sum of G dL/dalpha            (-> dL/dopacity)
     float c0, c1, c2;  // sum of alpha T dL/dC           (-> dL/dcolour)
     float d;           // sum of alpha T dL/dD           (-> dL/ddepth)
 };
 
 __device__ __forceinline__ PairSums zero_sums() {
     PairSums a;
-    a.g = a.gy = a.gyy = a.o = a.c0 = a.c1 = a.c2 = a.d = 0.f;
+    a.g = a.gy = a.gyy = a.c0 = a.c1 = a.c2 = a.d = 0.f;
     return a;
 }
 
 // One (pixel, entry) step of the backward walk: adds the pair's contributions to a
 // (nothing when the pair is skipped).  dL/dalpha_i = T_i [(c_i - R_i) . dL/dC + (d_i - Rd_i)
-// dL/dD] + T_f / (1 - alpha_i) dL/dA; then R_{i-1} = R_i + alpha_i (c_i - R_i).  Extra =
-// false: no depth / alpha output gradients (dL/dD = dL/dA = 0), their terms are compiled out.
+// dL/dD] + T_f / (1 - alpha_i) dL/dA; then R_{i-1} = R_i + alpha_i (c_i - R_i), carried as
+// Rg = R . dL/dC.  Extra = false: no depth / alpha output gradients (dL/dD = dL/dA = 0), their
+// terms are compiled out.
 template <bool Extra>
 __device__ __forceinline__ bool pair_backward(const Rec &r, const PairX &x, float pyf, bool active, PixState &s,
                                               PairSums &a) {
-    float dy, G;
+    float dy;
     const float p2 = pair_power2_y(x, r.a.y, r.b.x, pyf, dy);
-    const float al = pair_alpha(p2, r.b.y, G);
+    const float oG = __fmul_rn(r.b.y, ex2_approx(p2));
+    const float al = fminf(kAlphaMax, oG);
     const bool valid = active && p2 <= 0.f && al >= kAlphaMin;
     if (valid) {
         const float om = 1.f - al;
@@ -93,26 +96,21 @@ __device__ __forceinline__ bool pair_backward(const Rec &r, const PairX &x, floa
         a.c0 += w * s.g0;
         a.c1 += w * s.g1;
         a.c2 += w * s.g2;
-        const float d0 = r.c.x - s.R0, d1 = r.c.y - s.R1, d2 = r.c.z - s.R2;
-        float dLda = s.T * (d0 * s.g0 + d1 * s.g1 + d2 * s.g2);
+        const float diff = (r.c.x * s.g0 + r.c.y * s.g1 + r.c.z * s.g2) - s.Rg;  // (c_i - R_i) . dL/dC
+        float dLda = s.T * diff;
         if (Extra) {
             a.d += w * s.gD;
             const float dd = r.c.w - s.Rd;
             dLda += s.T * dd * s.gD + s.Tf * io * s.gA;
             s.Rd += al * dd;
         }
-        s.R0 += al * d0;
-        s.R1 += al * d1;
-        s.R2 += al * d2;
-        const float oG = r.b.y * G;
+        s.Rg += al * diff;
         // alpha = min(0.99, o G): no gradient through the clamp (branch-free)
-        const float gG = oG <= kAlphaMax ? G * dLda : 0.f;  // dL/do
-        const float gp = r.b.y * gG;                          // dL/dpower2
+        const float gp = oG <= kAlphaMax ? oG * dLda : 0.f;  // dL/dpower2 = o G dL/dalpha
         const float gpy = gp * dy;
         a.g += gp;
         a.gy += gpy;
         a.gyy += gpy * dy;
-        a.o += gG;
     }
     return valid;
 }
@@ -120,9 +118,10 @@ __device__ __forceinline__ bool pair_backward(const Rec &r, const PairX &x, floa
 // Sums the lane sums of one record over the warp's 32 lanes and adds them to the record's
 // accumulator row acc[0..9]:
 //   acc0 = sum gp (2 qa dx + qb dy), acc1 = sum gp (2 qc dy + qb dx), acc2..4 = sum gp
-//   (dx^2, dx dy, dy^2), acc5 = sum G dL/dalpha, acc6..8 = colour sums, acc9 = depth sum
+//   (dx^2, dx dy, dy^2), acc5 = (sum gp) / o = sum G dL/dalpha, acc6..8 = colour sums,
+//   acc9 = depth sum
 // (qa, qb, qc: the record's pre-scaled conic; dx = mean_x - px is shared by the lane's
-// pixels).  The eight values (sum gp dx, sum gp dy, the three second moments, opacity, two
+// pixels).  The eight values (sum gp dx, sum gp dy, the three second moments, sum gp, two
 // colour channels) are reduced by recursive halving over lane bits 4, 3, 2 (4 + 2 + 1
 // shuffles) and two butterfly steps, leaving element (l >> 2) & 7 in lane l; the third
 // colour channel and the depth sum take one more halving step and four butterflies.  The
@@ -130,7 +129,7 @@ __device__ __forceinline__ bool pair_backward(const Rec &r, const PairX &x, floa
 template <bool Extra>
 __device__ __forceinline__ void warp_reduce_red(const PairSums &s, float dx, const Rec &r, float *acc, int lane) {
     const float sdx = dx * s.g;
-    float v[8] = {sdx, s.gy, dx * sdx, dx * s.gy, s.gyy, s.o, s.c0, s.c1};
+    float v[8] = {sdx, s.gy, dx * sdx, dx * s.gy, s.gyy, s.g, s.c0, s.c1};
     float h4[4], h2[2];
     {
         const bool hi = (lane & 16) != 0;
@@ -173,7 +172,10 @@ __device__ __forceinline__ void warp_reduce_red(const PairSums &s, float dx, con
     float val = 0.f;
     if ((lane & 3) == 0) {
         idx = e;
-        val = e == 0 ? 2.f * r.a.z * t + r.a.w * other : e == 1 ? 2.f * r.b.x * t + r.a.w * other : t;
+        val = e == 0   ? 2.f * r.a.z * t + r.a.w * other
+              : e == 1 ? 2.f * r.b.x * t + r.a.w * other
+              : e == 5 ? __fdividef(t, r.b.y)  // o >= 1/255 for any record with a valid pair
+                       : t;
     } else if (lane == 1) {
         idx = 8;
         val = u;
@@ -341,8 +343,11 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
     }
 }
 
+// The walk is latency-bound (dependent FP32 chains, shuffle trees): with colour-only output
+// gradients and up to 4 rows per lane the kernel fits 64 registers, so 4 blocks (32 warps)
+// stay resident per SM instead of 3; the other variants would spill there.
 template <int Q, bool Extra>
-__global__ void __launch_bounds__(kBwdWarps * 32) k_backward_balanced(BwdArgs a) {
+__global__ void __launch_bounds__(kBwdWarps * 32, (Q <= 4 && !Extra) ? 4 : 3) k_backward_balanced(BwdArgs a) {
     __shared__ Rec sbuf[kBwdWarps][32];
     __shared__ uint32_t sidx[kBwdWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

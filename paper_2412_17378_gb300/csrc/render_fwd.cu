@@ -29,8 +29,10 @@ namespace bgs {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// The accumulated alpha sum_i alpha_i T_i telescopes to 1 - T (T_i - T_{i+1} summed), so it is
+// written from the final T instead of being summed per pair.
 __device__ __forceinline__ void write_pixel(const FwdArgs &a, int v, int px, int py, float T, float c0, float c1,
-                                            float c2, float D, float A, int last, int neval) {
+                                            float c2, float D, int last, int neval) {
     const int W = a.vt.W[v];
     const long long HW = (long long)W * a.vt.H[v];
     const long long pid = (long long)py * W + px;
@@ -39,7 +41,7 @@ __device__ __forceinline__ void write_pixel(const FwdArgs &a, int v, int px, int
     oc[HW + pid] = c1 + T * a.bg[1];
     oc[2 * HW + pid] = c2 + T * a.bg[2];
     a.io.out_depth[v][pid] = D;
-    a.io.out_alpha[v][pid] = A;
+    a.io.out_alpha[v][pid] = 1.f - T;
     a.io.final_T[v][pid] = T;
     a.io.n_contrib[v][pid] = last;
     if (a.io.n_eval[v]) a.io.n_eval[v][pid] = neval;
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(1024) k_forward_static(FwdArgs a) {
         rg = make_uint2(0, 0);
     }
     const float pxf = (float)px, pyf = (float)py;
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, D = 0.f, A = 0.f;
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, D = 0.f;
     int last = 0, neval = (int)(rg.y - rg.x), nacc = 0;
     bool done = !inside;
     for (uint32_t base = rg.x; base < rg.y; base += nthreads) {
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(1024) k_forward_static(FwdArgs a) {
             const float p2 = pair_power2(ra, rb.x, pxf, pyf, dx, dy);
             const float al = pair_alpha(p2, rb.y, G);
             if (p2 > 0.f || al < kAlphaMin) continue;
-            const float tt = T * (1.f - al);
+            const float tt = next_T(T, al);
             if (tt < kTMin) {
                 done = true;
                 neval = (int)(base + k + 1 - rg.x);
@@ -123,13 +125,12 @@ __global__ void __launch_bounds__(1024) k_forward_static(FwdArgs a) {
             c1 += w * rc.y;
             c2 += w * rc.z;
             D += w * rc.w;
-            A += w;
             T = tt;
             last = (int)(base + k + 1 - rg.x);
             ++nacc;
         }
     }
-    if (inside) write_pixel(a, 0, px, py, T, c0, c1, c2, D, A, last, neval);
+    if (inside) write_pixel(a, 0, px, py, T, c0, c1, c2, D, last, neval);
     // evaluated / contributing pair counters
     unsigned long long e = inside ? (unsigned long long)neval : 0ull, c = inside ? (unsigned long long)nacc : 0ull;
     for (int o = 16; o > 0; o >>= 1) {
@@ -191,7 +192,7 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
     // centre and half-extent of the item's pixel block (for skipping records that miss it)
     const float bcx = (float)(tg.x0 + sx * kItemW) + 0.5f * (kItemW - 1);
     const float bcy = (float)(tg.y0 + sy * kItemH) + 0.5f * (kItemH - 1);
-    float pyf[Q], T[Q], c0[Q], c1[Q], c2[Q], D[Q], A[Q];
+    float pyf[Q], T[Q], c0[Q], c1[Q], c2[Q], D[Q];
     int last[Q], neval[Q], nacc[Q];
     bool done[Q], inside[Q];
 #pragma unroll
@@ -200,7 +201,7 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
         inside[q] = px < tg.x0 + tg.vw && py < tg.y0 + tg.vh;
         pyf[q] = (float)py;
         T[q] = 1.f;
-        c0[q] = c1[q] = c2[q] = D[q] = A[q] = 0.f;
+        c0[q] = c1[q] = c2[q] = D[q] = 0.f;
         last[q] = 0;
         neval[q] = (int)(rg.y - rg.x);
         nacc[q] = 0;
@@ -235,7 +236,7 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
                 const float p2 = pair_power2_y(px2, ra.y, rb.x, pyf[q], dy);
                 const float al = pair_alpha(p2, rb.y, G);
                 if (!done[q] && p2 <= 0.f && al >= kAlphaMin) {
-                    const float tt = T[q] * (1.f - al);
+                    const float tt = next_T(T[q], al);
                     if (tt < kTMin) {
                         done[q] = true;
                         neval[q] = pos0 + k + 1;
@@ -246,7 +247,6 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
                         c1[q] += w * rc.y;
                         c2[q] += w * rc.z;
                         D[q] += w * rc.w;
-                        A[q] += w;
                         T[q] = tt;
                         last[q] = pos0 + k + 1;
                         ++nacc[q];
@@ -258,7 +258,7 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (inside[q]) {
-            write_pixel(a, tg.v, px, py0 + kRowStep * q, T[q], c0[q], c1[q], c2[q], D[q], A[q], last[q], neval[q]);
+            write_pixel(a, tg.v, px, py0 + kRowStep * q, T[q], c0[q], c1[q], c2[q], D[q], last[q], neval[q]);
             st_eval += (unsigned long long)neval[q];
             st_acc += (unsigned long long)nacc[q];
         }
@@ -273,7 +273,7 @@ __device__ __forceinline__ void gauss_item(const FwdArgs &a, int tile, int sub, 
     const int npix = tg.vw * tg.vh;
     const uint2 rg = load_range(a, tile);
     const int n = (int)(rg.y - rg.x);
-    float pxf[P], pyf[P], T[P], c0[P], c1[P], c2[P], D[P], A[P];
+    float pxf[P], pyf[P], T[P], c0[P], c1[P], c2[P], D[P];
     int last[P], neval[P], nacc[P];
     bool done[P];
 #pragma unroll
@@ -284,7 +284,7 @@ __device__ __forceinline__ void gauss_item(const FwdArgs &a, int tile, int sub, 
         pxf[p] = (float)(tg.x0 + qq % tg.vw);
         pyf[p] = (float)(tg.y0 + qq / tg.vw);
         T[p] = 1.f;
-        c0[p] = c1[p] = c2[p] = D[p] = A[p] = 0.f;
+        c0[p] = c1[p] = c2[p] = D[p] = 0.f;
         last[p] = 0;
         neval[p] = n;
         nacc[p] = 0;
@@ -338,7 +338,6 @@ __device__ __forceinline__ void gauss_item(const FwdArgs &a, int tile, int sub, 
                 c1[p] += w * r.c.y;
                 c2[p] += w * r.c.z;
                 D[p] += w * r.c.w;
-                A[p] += w;
             }
             const float tnew = __shfl_sync(kFull, tt, kstop > 0 ? kstop - 1 : 0);
             if (kstop > 0) T[p] = tnew;
@@ -361,12 +360,11 @@ __device__ __forceinline__ void gauss_item(const FwdArgs &a, int tile, int sub, 
             c1[p] += __shfl_xor_sync(kFull, c1[p], o);
             c2[p] += __shfl_xor_sync(kFull, c2[p], o);
             D[p] += __shfl_xor_sync(kFull, D[p], o);
-            A[p] += __shfl_xor_sync(kFull, A[p], o);
         }
         const int q = sub * P + p;
         if (q < npix) {
             if (lane == p)
-                write_pixel(a, tg.v, (int)pxf[p], (int)pyf[p], T[p], c0[p], c1[p], c2[p], D[p], A[p], last[p],
+                write_pixel(a, tg.v, (int)pxf[p], (int)pyf[p], T[p], c0[p], c1[p], c2[p], D[p], last[p],
                             neval[p]);
             if (lane == 0) {
                 st_eval += (unsigned long long)neval[p];
