@@ -277,20 +277,19 @@ cudaError_t launch_ranges(const KeyT *keys, long long K, uint2 *ranges, cudaStre
 size_t bin_count_smem(int tx, int ty);
 int bin_mask_groups(int tx, int ty);
 cudaError_t setup_bin_kernels(int tx, int ty);
-// also writes each sorted position's packed tile rectangle: rect_x = x0 | w << 16,
-// rect_y = y0 | h << 16 (0 when empty)
-// and the (block, tile group) masks, W32 words each (a multiple of 16)
+// also writes each sorted position's record rect[s] = (x0 | w << 16, y0 | h << 16, Gaussian
+// index, 0) (both rectangle words 0 when empty) and the (block, tile group) masks, W32
+// words each (a multiple of 16)
 cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
-                             int W, int H, int tw, int th, uint32_t *Hm, uint32_t *rect_x, uint32_t *rect_y,
-                             uint32_t *masks, int W32, cudaStream_t s);
+                             int W, int H, int tw, int th, uint32_t *Hm, uint4 *rect, uint32_t *masks, int W32,
+                             cudaStream_t s);
 cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, uint32_t *total, cudaStream_t s);
 // ranges of one view's tiles, offset by ctrl->bin_base (the view's first point_list slot)
 cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *total, uint2 *ranges, DevCtrl *ctrl,
                               cudaStream_t s);
-cudaError_t launch_bin_scatter(long long N, int G, int B, int W32, const uint32_t *order, const uint32_t *rect_x,
-                               const uint32_t *rect_y, int W, int H, int tw, int th, const uint32_t *Hm,
-                               const uint32_t *start, const uint32_t *masks, uint32_t *point_list, long long capacity,
-                               const DevCtrl *ctrl, cudaStream_t s);
+cudaError_t launch_bin_scatter(long long N, int G, int B, int W32, const uint4 *rect, int W, int H, int tw, int th,
+                               const uint32_t *Hm, const uint32_t *start, const uint32_t *masks, uint32_t *point_list,
+                               long long capacity, const DevCtrl *ctrl, cudaStream_t s);
 // bin_base += this view's entry count; num_entries = bin_base; raises BGS_CHECK_OVERFLOW past capacity
 cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *total, long long capacity, DevCtrl *ctrl,
                                cudaStream_t s);

@@ -7,8 +7,9 @@
 //                      block b counts how many of its Gaussians cover each tile, H[b][t],
 //                      as a 2D difference array in shared memory (4 updates per
 //                      rectangle) followed by a prefix sum along x then y.  It also stores
-//                      every sorted position's packed rectangle and, per group of 8 x 4
-//                      tiles C, a bit mask of the block's Gaussians whose rectangle meets C.
+//                      every sorted position's packed rectangle and Gaussian index (one
+//                      16-byte record) and, per group of 8 x 4 tiles C, a bit mask of the
+//                      block's Gaussians whose rectangle meets C.
 //   2. k_bin_colscan - exclusive scan of every column of H over b (in place) and the tile
 //                      totals n[t].
 //   3. (CUB) exclusive scan of n -> tile start; k_bin_ranges writes ranges and K.
@@ -54,8 +55,7 @@ __device__ __forceinline__ void rect_of(const float2 *__restrict__ means2D, cons
 __global__ void __launch_bounds__(256) k_bin_count(long long N, int G, const uint32_t *__restrict__ order,
                                                    const float2 *__restrict__ means2D, const int *__restrict__ radii,
                                                    int tw, int th, int tx, int ty, uint32_t *__restrict__ H,
-                                                   uint32_t *__restrict__ rect_x, uint32_t *__restrict__ rect_y,
-                                                   uint32_t *__restrict__ masks, int W32) {
+                                                   uint4 *__restrict__ rect, uint32_t *__restrict__ masks, int W32) {
     extern __shared__ uint32_t d_s[];  // [T] tile counters, then [nC][16] mask words
     const int T = tx * ty;
     const int ncx = (tx + kCbW - 1) / kCbW, nC = ncx * ((ty + kCbH - 1) / kCbH);
@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(256) k_bin_count(long long N, int G, const uin
         const long long c0 = s0 + 512ll * sub, c1 = min(s1, c0 + 512);
         for (long long s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
             int x0, y0, w, c;
-            rect_of(means2D, radii, order[s], tw, th, tx, ty, x0, y0, w, c);
+            const uint32_t g = order[s];
+            rect_of(means2D, radii, g, tw, th, tx, ty, x0, y0, w, c);
             uint32_t px = 0u, py = 0u;  // packed (x0 | w << 16, y0 | h << 16); h = 0 if empty
             if (c > 0) {
                 const int h = c / w, x1 = x0 + w, y1 = y0 + h;
@@ -89,8 +90,7 @@ __global__ void __launch_bounds__(256) k_bin_count(long long N, int G, const uin
                     for (int cx = x0 / kCbW; cx <= (x1 - 1) / kCbW; ++cx)
                         atomicOr(&m_s[(cy * ncx + cx) * 16 + (li >> 5)], bit);
             }
-            rect_x[s] = px;
-            rect_y[s] = py;
+            rect[s] = make_uint4(px, py, g, 0u);
         }
         __syncthreads();
         // the sub-block's mask words: (b, C) words [16 sub, 16 sub + 16)
@@ -210,17 +210,23 @@ __device__ __forceinline__ void flush_sector(const uint32_t *ring_s, int lane, u
 }
 
 // Block (b, cx, cy): one warp, lane l owns tile (8 cx + l % 8, 4 cy + l / 8) of the group.
-__global__ void __launch_bounds__(32) k_bin_scatter(uint32_t N, uint32_t G, int W32, const uint32_t *__restrict__ order,
-                                                    const uint32_t *__restrict__ rect_x,
-                                                    const uint32_t *__restrict__ rect_y, int tx, int ty,
+// Single-warp blocks: a block's shared memory is released as soon as its warp is done
+// (blocks of several warps hold it until the slowest one finishes, and reached fewer
+// resident warps).
+__global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const uint4 *__restrict__ rect, int tx, int ty,
                                                     const uint32_t *__restrict__ H, const uint32_t *__restrict__ start,
                                                     const uint32_t *__restrict__ masks,
                                                     uint32_t *__restrict__ point_list, uint32_t capacity, int vec_ok,
                                                     const DevCtrl *ctrl) {
-    __shared__ uint32_t idx_s[512];  // sorted positions of the pass's flagged Gaussians
-    __shared__ uint2 hit_s[512];     // (lanes whose tile the rectangle covers, Gaussian index)
-    __shared__ uint32_t ring_s[16 * 32];  // per-lane 16-word output rings, slot-major
+    // per flagged Gaussian of the pass: (lanes whose tile its rectangle covers, Gaussian
+    // index), .y holding its sorted position until the hit is known; and the lanes' 16-word
+    // output rings, slot-major.  7 KB of shared memory a block in all, so that 32 blocks
+    // (the per-SM block limit) fit an SM.
+    __shared__ uint2 hit_s[512];
+    __shared__ uint32_t ring_s[16 * 32];
     const int b = blockIdx.x, cx = blockIdx.y, cy = blockIdx.z, lane = threadIdx.x;
+    const int nC = ((tx + kCbW - 1) / kCbW) * ((ty + kCbH - 1) / kCbH);
+    const int C = cy * ((tx + kCbW - 1) / kCbW) + cx;
     const int gx0 = cx * kCbW, gy0 = cy * kCbH;
     const int ltx = gx0 + (lane % kCbW), lty = gy0 + (lane / kCbW);
     const bool own = ltx < tx && lty < ty;
@@ -231,8 +237,7 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t N, uint32_t G, int 
     const uint32_t run0 = pos;
     uint32_t done = pos & ~7u;  // positions below done are written (or precede the run)
     uint32_t *ring = ring_s + lane;
-    const int nC = ((tx + kCbW - 1) / kCbW) * ((ty + kCbH - 1) / kCbH);
-    const uint32_t *mk = masks + ((size_t)b * nC + cy * ((tx + kCbW - 1) / kCbW) + cx) * W32;
+    const uint32_t *mk = masks + ((size_t)b * nC + C) * W32;
     const uint32_t s0 = (uint32_t)b * G;
     for (int wb = 0; wb < W32; wb += 16) {  // 512 Gaussians per pass
         uint32_t word = lane < 16 ? mk[wb + lane] : 0u;
@@ -249,27 +254,27 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t N, uint32_t G, int 
         while (word) {
             const int bit = __ffs(word) - 1;
             word &= word - 1u;
-            idx_s[off++] = s0 + 32u * (uint32_t)(wb + lane) + (uint32_t)bit;
+            hit_s[off++].y = s0 + 32u * (uint32_t)(wb + lane) + (uint32_t)bit;
         }
         __syncwarp();
         // per flagged Gaussian: the lanes whose tile its rectangle covers (a nonempty
         // rectangle meeting the group: the masks flag no other)
         for (int k = lane; k < total; k += 32) {
-            const uint32_t s = idx_s[k];
-            const uint32_t px = rect_x[s], py = rect_y[s];
-            const int x0 = (int)(px & 0xffffu) - gx0, x1 = x0 + (int)(px >> 16);
-            const int y0 = (int)(py & 0xffffu) - gy0, y1 = y0 + (int)(py >> 16);
+            const uint4 rc = rect[hit_s[k].y];
+            const int x0 = (int)(rc.x & 0xffffu) - gx0, x1 = x0 + (int)(rc.x >> 16);
+            const int y0 = (int)(rc.y & 0xffffu) - gy0, y1 = y0 + (int)(rc.y >> 16);
             const uint32_t lx0 = (uint32_t)max(x0, 0), lx1 = (uint32_t)min(x1, kCbW);
             const uint32_t ly0 = (uint32_t)max(y0, 0), ly1 = (uint32_t)min(y1, kCbH);
             const uint32_t cols = ((1u << lx1) - 1u) ^ ((1u << lx0) - 1u);
             const uint32_t rows = (ly1 >= 4u ? 0xffffffffu : (1u << (8u * ly1)) - 1u) ^ ((1u << (8u * ly0)) - 1u);
-            hit_s[k] = make_uint2(rows & (cols * 0x01010101u) & own_mask, order[s]);
+            hit_s[k] = make_uint2(rows & (cols * 0x01010101u) & own_mask, rc.z);
         }
-        // pad to a multiple of 8 with entries that cover no lane
-        const int padded = (total + 7) & ~7;
-        if (lane < padded - total) hit_s[total + lane] = make_uint2(0u, 0u);
         __syncwarp();
-        for (int k0 = 0; k0 < padded; k0 += 8) {  // depth order, 8 visits at a time
+        // depth order, 8 visits at a time, then the remaining total % 8 one by one; at most 8
+        // appends between two checks: at most one newly completed sector, and no ring slot
+        // overwritten before it is written out
+        const int full = total & ~7;
+        for (int k0 = 0; k0 < full; k0 += 8) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 // branch-free: the slot of position pos is free (pos - done < 16), so every
@@ -278,8 +283,17 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t N, uint32_t G, int 
                 ring[(pos & 15u) << 5] = e.y;
                 pos += (e.x >> lane) & 1u;
             }
-            // at most 8 appends since the last check: at most one newly completed sector,
-            // and no ring slot overwritten before it is written out
+            if (done + 8u <= pos) {
+                flush_sector(ring_s, lane, done, run0, point_list, capacity, vec_ok != 0);
+                done += 8u;
+            }
+        }
+        if (full < total) {
+            for (int k = full; k < total; ++k) {
+                const uint2 e = hit_s[k];
+                ring[(pos & 15u) << 5] = e.y;
+                pos += (e.x >> lane) & 1u;
+            }
             if (done + 8u <= pos) {
                 flush_sector(ring_s, lane, done, run0, point_list, capacity, vec_ok != 0);
                 done += 8u;
@@ -306,11 +320,11 @@ cudaError_t setup_bin_kernels(int tx, int ty) {
 }
 
 cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
-                             int W, int H, int tw, int th, uint32_t *Hm, uint32_t *rect_x, uint32_t *rect_y,
-                             uint32_t *masks, int W32, cudaStream_t s) {
+                             int W, int H, int tw, int th, uint32_t *Hm, uint4 *rect, uint32_t *masks, int W32,
+                             cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
     k_bin_count<<<B, 256, bin_count_smem(tx, ty), s>>>(N, G, order, reinterpret_cast<const float2 *>(means2D), radii,
-                                                        tw, th, tx, ty, Hm, rect_x, rect_y, masks, W32);
+                                                        tw, th, tx, ty, Hm, rect, masks, W32);
     return cudaGetLastError();
 }
 
@@ -332,17 +346,16 @@ cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *tot
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_scatter(long long N, int G, int B, int W32, const uint32_t *order, const uint32_t *rect_x,
-                               const uint32_t *rect_y, int W, int H, int tw, int th, const uint32_t *Hm,
-                               const uint32_t *start, const uint32_t *masks, uint32_t *point_list, long long capacity,
-                               const DevCtrl *ctrl, cudaStream_t s) {
+cudaError_t launch_bin_scatter(long long N, int G, int B, int W32, const uint4 *rect, int W, int H, int tw, int th,
+                               const uint32_t *Hm, const uint32_t *start, const uint32_t *masks, uint32_t *point_list,
+                               long long capacity, const DevCtrl *ctrl, cudaStream_t s) {
+    (void)N;
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
     // indices, sorted positions and list slots are < 2^32 (checked by the callers)
     const uint32_t cap = capacity >= 0xffffffffll ? 0xffffffffu : (uint32_t)capacity;
     const int vec_ok = (reinterpret_cast<uintptr_t>(point_list) & 31u) == 0u;
     const dim3 grid(B, (tx + kCbW - 1) / kCbW, (ty + kCbH - 1) / kCbH);
-    k_bin_scatter<<<grid, 32, 0, s>>>((uint32_t)N, (uint32_t)G, W32, order, rect_x, rect_y, tx, ty, Hm, start, masks,
-                                      point_list, cap, vec_ok, ctrl);
+    k_bin_scatter<<<grid, 32, 0, s>>>((uint32_t)G, W32, rect, tx, ty, Hm, start, masks, point_list, cap, vec_ok, ctrl);
     return cudaGetLastError();
 }
 

@@ -624,13 +624,14 @@ int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const flo
     BGS_TRY(ensure(p, p->bin_h, sizeof(uint32_t) * B * T, s, "bin_h"));
     BGS_TRY(ensure(p, p->bin_total, sizeof(uint32_t) * T, s, "bin_total"));
     BGS_TRY(ensure(p, p->bin_start, sizeof(uint32_t) * T, s, "bin_start"));
-    BGS_TRY(ensure(p, p->bin_rect, 2 * sizeof(uint32_t) * n, s, "bin_rect"));
+    BGS_TRY(ensure(p, p->bin_rect, sizeof(uint4) * n, s, "bin_rect"));
     BGS_TRY(ensure(p, p->bin_mask, sizeof(uint32_t) * B * nC * W32, s, "bin_mask"));
     uint32_t *Hm = (uint32_t *)p->bin_h.p, *tot = (uint32_t *)p->bin_total.p, *start = (uint32_t *)p->bin_start.p;
-    uint32_t *rect_x = (uint32_t *)p->bin_rect.p, *rect_y = rect_x + n, *masks = (uint32_t *)p->bin_mask.p;
+    uint4 *rect = (uint4 *)p->bin_rect.p;
+    uint32_t *masks = (uint32_t *)p->bin_mask.p;
     if (smem > 48 * 1024) BGS_CUDA(bgs::setup_bin_kernels(tiles_x, tiles_y), "bin smem attribute");
-    BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, rect_x, rect_y, masks,
-                                   (int)W32, s),
+    BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, rect, masks, (int)W32,
+                                   s),
              "bin_count");
     BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, tot, s), "bin_colscan");
     size_t tmp = 0;
@@ -639,8 +640,8 @@ int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const flo
     tmp = p->cub_tmp.bytes;
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, tot, start, (int)T, s), "tile scan");
     BGS_CUDA(bgs::launch_bin_ranges((int)T, start, tot, reinterpret_cast<uint2 *>(ranges), p->ctrl, s), "bin_ranges");
-    BGS_CUDA(bgs::launch_bin_scatter(n, (int)G, (int)B, (int)W32, order, rect_x, rect_y, W, H, tw, th, Hm, start, masks,
-                                     point_list, capacity, p->ctrl, s),
+    BGS_CUDA(bgs::launch_bin_scatter(n, (int)G, (int)B, (int)W32, rect, W, H, tw, th, Hm, start, masks, point_list,
+                                     capacity, p->ctrl, s),
              "bin_scatter");
     BGS_CUDA(bgs::launch_bin_advance((int)T, start, tot, flag_overflow ? capacity : (1ll << 62), p->ctrl, s),
              "bin_advance");
