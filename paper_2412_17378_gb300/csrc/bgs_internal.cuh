@@ -323,8 +323,9 @@ cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s)
 int backward_balanced_block_threads();
 const void *backward_balanced_kernel(const BwdArgs &a);  // the instantiation a would launch
 // gradients of N records; colours have n_colors rows (n_colors < N: summed over views)
-cudaError_t launch_grad_finalize(long long N, long long n_colors, const float4 *acc, float *dL_dmeans2D,
-                                 float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,
-                                 const unsigned int *warp_items, int n_warps, DevCtrl *ctrl, cudaStream_t s);
+cudaError_t launch_grad_finalize(long long N, long long n_colors, const float4 *acc, const float *conic_opacity,
+                                 float *dL_dmeans2D, float *dL_dconic, float *dL_dopacity, float *dL_dcolors,
+                                 float *dL_ddepths, const unsigned int *warp_items, int n_warps, DevCtrl *ctrl,
+                                 cudaStream_t s);
 
 }  // namespace bgs

@@ -925,9 +925,9 @@ int render_backward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewG
         kt.stop();
         p->host_launches += 1;  // kernel
     }
-    BGS_CUDA(bgs::launch_grad_finalize(n_records, n_colors, (const float4 *)p->grad_acc.p, dL_dmeans2D, dL_dconic,
-                                       dL_dopacity, dL_dcolors, dL_ddepths, (const unsigned int *)p->warp_items.p,
-                                       n_warps, p->ctrl, s),
+    BGS_CUDA(bgs::launch_grad_finalize(n_records, n_colors, (const float4 *)p->grad_acc.p, conic_opacity, dL_dmeans2D,
+                                       dL_dconic, dL_dopacity, dL_dcolors, dL_ddepths,
+                                       (const unsigned int *)p->warp_items.p, n_warps, p->ctrl, s),
              "grad_finalize");
     p->host_launches += 1;  // finalize
     return BGS_OK;

@@ -20,8 +20,8 @@
 // moments once, and the conic is applied after the warp sum.  Two identities shorten the
 // per-pair work: R_i enters dL/dalpha only through R_i . dL/dC, so a pixel carries that
 // scalar (updated by the same recurrence) instead of R_i; and dL/do = sum G dL/dalpha =
-// (sum gp) / o, so the opacity gradient is the gp sum divided once by o.  A final pass
-// scales and scatters the accumulator into the ABI's gradient arrays.
+// (sum gp) / o, so the opacity gradient is the gp sum, divided by o once per Gaussian in the
+// final pass, which scales and scatters the accumulator into the ABI's gradient arrays.
 #include <algorithm>
 
 #include "bgs_internal.cuh"
@@ -118,7 +118,7 @@ __device__ __forceinline__ bool pair_backward(const Rec &r, const PairX &x, floa
 // Sums the lane sums of one record over the warp's 32 lanes and adds them to the record's
 // accumulator row acc[0..9]:
 //   acc0 = sum gp (2 qa dx + qb dy), acc1 = sum gp (2 qc dy + qb dx), acc2..4 = sum gp
-//   (dx^2, dx dy, dy^2), acc5 = (sum gp) / o = sum G dL/dalpha, acc6..8 = colour sums,
+//   (dx^2, dx dy, dy^2), acc5 = sum gp (= o sum G dL/dalpha), acc6..8 = colour sums,
 //   acc9 = depth sum
 // (qa, qb, qc: the record's pre-scaled conic; dx = mean_x - px is shared by the lane's
 // pixels).  The eight values (sum gp dx, sum gp dy, the three second moments, sum gp, two
@@ -172,10 +172,7 @@ __device__ __forceinline__ void warp_reduce_red(const PairSums &s, float dx, con
     float val = 0.f;
     if ((lane & 3) == 0) {
         idx = e;
-        val = e == 0   ? 2.f * r.a.z * t + r.a.w * other
-              : e == 1 ? 2.f * r.b.x * t + r.a.w * other
-              : e == 5 ? __fdividef(t, r.b.y)  // o >= 1/255 for any record with a valid pair
-                       : t;
+        val = e == 0 ? 2.f * r.a.z * t + r.a.w * other : e == 1 ? 2.f * r.b.x * t + r.a.w * other : t;
     } else if (lane == 1) {
         idx = 8;
         val = u;
@@ -345,9 +342,11 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
 
 // The walk is latency-bound (dependent FP32 chains, shuffle trees): with colour-only output
 // gradients and up to 4 rows per lane the kernel fits 64 registers, so 4 blocks (32 warps)
-// stay resident per SM instead of 3; the other variants would spill there.
+// stay resident per SM instead of 3.  The other variants would spill there: 3 blocks for
+// the depth / alpha gradients at up to 4 rows, no bound at 8 rows.
 template <int Q, bool Extra>
-__global__ void __launch_bounds__(kBwdWarps * 32, (Q <= 4 && !Extra) ? 4 : 3) k_backward_balanced(BwdArgs a) {
+__global__ void __launch_bounds__(kBwdWarps * 32, (Q <= 4 && !Extra) ? 4 : (Q <= 4 ? 3 : 1))
+    k_backward_balanced(BwdArgs a) {
     __shared__ Rec sbuf[kBwdWarps][32];
     __shared__ uint32_t sidx[kBwdWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -403,6 +402,7 @@ cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s)
 // batched call: when n_colors < N, the colour gradient of Gaussian g sums the rows
 // g, g + n_colors, ... (one per view) in k_grad_colors instead.
 __global__ void __launch_bounds__(256) k_grad_finalize(long long N, long long n_colors, const float4 *__restrict__ acc,
+                                                       const float4 *__restrict__ conic_opacity,
                                                        float *__restrict__ dL_dmeans2D, float *__restrict__ dL_dconic,
                                                        float *__restrict__ dL_dopacity, float *__restrict__ dL_dcolors,
                                                        float *__restrict__ dL_ddepths,
@@ -432,7 +432,9 @@ __global__ void __launch_bounds__(256) k_grad_finalize(long long N, long long n_
     dL_dconic[3 * i] = -0.5f * a0.z;
     dL_dconic[3 * i + 1] = -a0.w;
     dL_dconic[3 * i + 2] = -0.5f * a1.x;
-    dL_dopacity[i] = a1.y;
+    // sum gp / o = sum G dL/dalpha (a record with o = 0 has alpha = 0 everywhere: no pair)
+    const float o = conic_opacity[i].w;
+    dL_dopacity[i] = o > 0.f ? a1.y / o : 0.f;
     if (n_colors == N) {
         dL_dcolors[3 * i] = a1.z;
         dL_dcolors[3 * i + 1] = a1.w;
@@ -457,12 +459,14 @@ __global__ void __launch_bounds__(256) k_grad_colors(long long N, long long n_co
     dL_dcolors[3 * g + 2] = b;
 }
 
-cudaError_t launch_grad_finalize(long long N, long long n_colors, const float4 *acc, float *dL_dmeans2D,
-                                 float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,
-                                 const unsigned int *warp_items, int n_warps, DevCtrl *ctrl, cudaStream_t s) {
+cudaError_t launch_grad_finalize(long long N, long long n_colors, const float4 *acc, const float *conic_opacity,
+                                 float *dL_dmeans2D, float *dL_dconic, float *dL_dopacity, float *dL_dcolors,
+                                 float *dL_ddepths, const unsigned int *warp_items, int n_warps, DevCtrl *ctrl,
+                                 cudaStream_t s) {
     if (N == 0 && n_warps == 0) return cudaSuccess;
     k_grad_finalize<<<(unsigned)std::max<long long>(1, (N + 255) / 256), 256, 0, s>>>(
-        N, n_colors, acc, dL_dmeans2D, dL_dconic, dL_dopacity, dL_dcolors, dL_ddepths, warp_items, n_warps, ctrl);
+        N, n_colors, acc, reinterpret_cast<const float4 *>(conic_opacity), dL_dmeans2D, dL_dconic, dL_dopacity,
+        dL_dcolors, dL_ddepths, warp_items, n_warps, ctrl);
     if (n_colors != N && n_colors > 0)
         k_grad_colors<<<(unsigned)((n_colors + 255) / 256), 256, 0, s>>>(N, n_colors, acc, dL_dcolors);
     return cudaGetLastError();

@@ -416,3 +416,37 @@ def test_autotuner_choice_keeps_parity(R, cfg1):
     out, _ = _render_gpu(R, p, cfg1, "auto")
     compare_images(out["color"], ref, what="tuned")
     p.close()
+
+
+_WL_CACHE = {}
+
+
+def _worklist_scene(W, H):
+    if (W, H) not in _WL_CACHE:
+        s = scene("cfg1", 0.3)
+        cam = s["cameras"][0]
+        cam.update(W=W, H=H, cx=(W - 1) / 2, cy=(H - 1) / 2, fx=0.25 * W, fy=0.25 * W)
+        inp = oracle_render_inputs(s)
+        ref = oracle.render(inp["means2D"], inp["conic_opacity"], inp["colors"], inp["depths"], inp["point_list"],
+                            inp["ranges"], W, H)
+        _WL_CACHE[(W, H)] = (inp, ref)
+    return _WL_CACHE[(W, H)]
+
+
+@pytest.mark.parametrize("W,H", [(1000, 700), (4096, 4208)])
+@pytest.mark.parametrize("lpt", [True, False])
+@pytest.mark.parametrize("mode", ["pixel", "gaussian", "auto"])
+def test_worklist_small_and_large_tile_grids(R, W, H, lpt, mode):
+    """The work list of a3 (Sec. 4.1 / 4.3) on 2772 and 67328 tiles, with and without the
+    heaviest-first order and with every tile kind: every item must run exactly once (the
+    drain check) and the image must match the oracle."""
+    inp, ref = _worklist_scene(W, H)
+    p = R.Plan(heavy_threshold=8, gw_pixels=4, lpt_order=lpt)
+    p.reset_stats()
+    out, _ = _render_gpu(R, p, inp, mode)
+    compare_images(out["color"], ref, what=f"worklist {mode} lpt={lpt} {W}x{H}")
+    un = ref["flags"] == 0
+    np.testing.assert_array_equal(out["n_contrib"][un], ref["n_contrib"][un])
+    st = p.stats()
+    assert st["items"] == st["last_num_items"] > 0
+    p.close()
