@@ -117,17 +117,16 @@ __device__ __forceinline__ bool pair_backward(const Rec &r, const PairX &x, floa
 
 // Sums the lane sums of one record over the warp's 32 lanes and adds them to the record's
 // accumulator row acc[0..9]:
-//   acc0 = sum gp (2 qa dx + qb dy), acc1 = sum gp (2 qc dy + qb dx), acc2..4 = sum gp
-//   (dx^2, dx dy, dy^2), acc5 = sum gp (= o sum G dL/dalpha), acc6..8 = colour sums,
-//   acc9 = depth sum
-// (qa, qb, qc: the record's pre-scaled conic; dx = mean_x - px is shared by the lane's
-// pixels).  The eight values (sum gp dx, sum gp dy, the three second moments, sum gp, two
+//   acc0..4 = sum gp (dx, dy, dx^2, dx dy, dy^2), acc5 = sum gp (= o sum G dL/dalpha),
+//   acc6..8 = colour sums, acc9 = depth sum
+// (dx = mean_x - px is shared by the lane's pixels; the final pass applies the Gaussian's
+// conic to the first two moments, once per Gaussian).  The eight values (the five moments, sum gp, two
 // colour channels) are reduced by recursive halving over lane bits 4, 3, 2 (4 + 2 + 1
 // shuffles) and two butterfly steps, leaving element (l >> 2) & 7 in lane l; the third
 // colour channel and the depth sum take one more halving step and four butterflies.  The
 // lanes 0, 4, ..., 28, 1 (and 17) then issue one red.add each, in one instruction.
 template <bool Extra>
-__device__ __forceinline__ void warp_reduce_red(const PairSums &s, float dx, const Rec &r, float *acc, int lane) {
+__device__ __forceinline__ void warp_reduce_red(const PairSums &s, float dx, float *acc, int lane) {
     const float sdx = dx * s.g;
     float v[8] = {sdx, s.gy, dx * sdx, dx * s.gy, s.gyy, s.g, s.c0, s.c1};
     float h4[4], h2[2];
@@ -165,14 +164,12 @@ __device__ __forceinline__ void warp_reduce_red(const PairSums &s, float dx, con
     u += __shfl_xor_sync(kFullB, u, 4);
     u += __shfl_xor_sync(kFullB, u, 2);
     u += __shfl_xor_sync(kFullB, u, 1);
-    // mean terms: lane 0 holds sum gp dx, lane 4 sum gp dy; they swap
-    const float other = __shfl_xor_sync(kFullB, t, 4);
     const int e = (lane >> 2) & 7;
     int idx = -1;
     float val = 0.f;
     if ((lane & 3) == 0) {
         idx = e;
-        val = e == 0 ? 2.f * r.a.z * t + r.a.w * other : e == 1 ? 2.f * r.b.x * t + r.a.w * other : t;
+        val = t;
     } else if (lane == 1) {
         idx = 8;
         val = u;
@@ -259,7 +256,7 @@ __global__ void __launch_bounds__(1024) k_backward_static(BwdArgs a) {
             const PairX x = pair_x(r.a, pxf);
             PairSums sums = zero_sums();
             const bool valid = pair_backward<true>(r, x, pyf, pos < s.nc, s, sums);
-            if (__any_sync(kFullB, valid)) warp_reduce_red<true>(sums, x.dx, r, a.grad_acc + 12ull * sidx[k], lane);
+            if (__any_sync(kFullB, valid)) warp_reduce_red<true>(sums, x.dx, a.grad_acc + 12ull * sidx[k], lane);
         }
     }
 }
@@ -334,7 +331,7 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
             bool any = false;
 #pragma unroll
             for (int q = 0; q < Q; ++q) any |= pair_backward<Extra>(r, px2, pyf[q], pos < s[q].nc, s[q], sums);
-            if (__any_sync(kFullB, any)) warp_reduce_red<Extra>(sums, px2.dx, r, a.grad_acc + 12ull * gbuf[k], lane);
+            if (__any_sync(kFullB, any)) warp_reduce_red<Extra>(sums, px2.dx, a.grad_acc + 12ull * gbuf[k], lane);
         }
         top = lo;
     }
@@ -425,16 +422,19 @@ __global__ void __launch_bounds__(256) k_grad_finalize(long long N, long long n_
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float4 a0 = acc[3 * i], a1 = acc[3 * i + 1], a2 = acc[3 * i + 2];
-    // power = ln2 * power2; d power / d mean = ln2 (2 qa dx + qb dy, 2 qc dy + qb dx);
+    const float4 co = conic_opacity[i];
+    // power = ln2 * power2 with power2 = qa dx^2 + qb dx dy + qc dy^2 and (qa, qb, qc) the
+    // record's pre-scaled conic; d power / d mean = ln2 (2 qa dx + qb dy, 2 qc dy + qb dx),
+    // summed over the pairs from the moments sum gp dx (a0.x) and sum gp dy (a0.y);
     // d power / d(a, b, c) = (-dx^2 / 2, -dx dy, -dy^2 / 2)
-    dL_dmeans2D[2 * i] = kLn2 * a0.x;
-    dL_dmeans2D[2 * i + 1] = kLn2 * a0.y;
+    const float qa = -0.5f * kLog2e * co.x, qb = -kLog2e * co.y, qc = -0.5f * kLog2e * co.z;
+    dL_dmeans2D[2 * i] = kLn2 * (2.f * qa * a0.x + qb * a0.y);
+    dL_dmeans2D[2 * i + 1] = kLn2 * (2.f * qc * a0.y + qb * a0.x);
     dL_dconic[3 * i] = -0.5f * a0.z;
     dL_dconic[3 * i + 1] = -a0.w;
     dL_dconic[3 * i + 2] = -0.5f * a1.x;
     // sum gp / o = sum G dL/dalpha (a record with o = 0 has alpha = 0 everywhere: no pair)
-    const float o = conic_opacity[i].w;
-    dL_dopacity[i] = o > 0.f ? a1.y / o : 0.f;
+    dL_dopacity[i] = co.w > 0.f ? a1.y / co.w : 0.f;
     if (n_colors == N) {
         dL_dcolors[3 * i] = a1.z;
         dL_dcolors[3 * i + 1] = a1.w;
