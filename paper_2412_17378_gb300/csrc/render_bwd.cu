@@ -115,16 +115,20 @@ __device__ __forceinline__ bool pair_backward(const Rec &r, const PairX &x, floa
     return valid;
 }
 
-// Sums the lane sums of one record over the warp's 32 lanes and adds them to the record's
-// accumulator row acc[0..9]:
+// Adds the lane sums of one record, over the warp's 32 lanes, to the record's accumulator
+// row acc[0..9]:
 //   acc0..4 = sum gp (dx, dy, dx^2, dx dy, dy^2), acc5 = sum gp (= o sum G dL/dalpha),
 //   acc6..8 = colour sums, acc9 = depth sum
 // (dx = mean_x - px is shared by the lane's pixels; the final pass applies the Gaussian's
-// conic to the first two moments, once per Gaussian).  The eight values (the five moments, sum gp, two
-// colour channels) are reduced by recursive halving over lane bits 4, 3, 2 (4 + 2 + 1
-// shuffles) and two butterfly steps, leaving element (l >> 2) & 7 in lane l; the third
-// colour channel and the depth sum take one more halving step and four butterflies.  The
-// lanes 0, 4, ..., 28, 1 (and 17) then issue one red.add each, in one instruction.
+// conic to the first two moments, once per Gaussian).  The eight values (the five moments,
+// sum gp, two colour channels) are reduced by recursive halving over lane bits 4, 3, 2
+// (4 + 2 + 1 shuffles), leaving in lane l the sum of element (l >> 2) & 7 over the 8 lanes
+// that share l's bits 1, 0; the third colour channel (and the depth sum, halved against it
+// over bit 4) takes three butterflies.  The four partial sums of every value are then added
+// by the atomics themselves: one red.add instruction from all 32 lanes for the eight
+// values, one from lanes 0-3 (and 16-19) for colour channel 2 (and depth).  Stopping the
+// trees two levels early shortens the per-record dependency chain by two shuffles; L2
+// absorbs the extra atomic operations.
 template <bool Extra>
 __device__ __forceinline__ void warp_reduce_red(const PairSums &s, float dx, float *acc, int lane) {
     const float sdx = dx * s.g;
@@ -151,8 +155,6 @@ __device__ __forceinline__ void warp_reduce_red(const PairSums &s, float dx, flo
         const bool hi = (lane & 4) != 0;
         t = (hi ? h2[1] : h2[0]) + __shfl_xor_sync(kFullB, hi ? h2[0] : h2[1], 4);
     }
-    t += __shfl_xor_sync(kFullB, t, 2);
-    t += __shfl_xor_sync(kFullB, t, 1);
     float u;  // colour channel 2 (lanes with bit 4 clear) / depth (bit 4 set) when Extra
     if (Extra) {
         const bool hi = (lane & 16) != 0;
@@ -162,22 +164,9 @@ __device__ __forceinline__ void warp_reduce_red(const PairSums &s, float dx, flo
     }
     u += __shfl_xor_sync(kFullB, u, 8);
     u += __shfl_xor_sync(kFullB, u, 4);
-    u += __shfl_xor_sync(kFullB, u, 2);
-    u += __shfl_xor_sync(kFullB, u, 1);
-    const int e = (lane >> 2) & 7;
-    int idx = -1;
-    float val = 0.f;
-    if ((lane & 3) == 0) {
-        idx = e;
-        val = t;
-    } else if (lane == 1) {
-        idx = 8;
-        val = u;
-    } else if (Extra && lane == 17) {
-        idx = 9;
-        val = u;
-    }
-    if (idx >= 0 && val != 0.f) atomicAdd(acc + idx, val);
+    if (t != 0.f) atomicAdd(acc + ((lane >> 2) & 7), t);
+    const bool ul = Extra ? (lane & 12) == 0 : lane < 4;  // lanes 0-3 (and 16-19)
+    if (ul && u != 0.f) atomicAdd(acc + ((Extra && (lane & 16)) ? 9 : 8), u);
 }
 
 // Record of list entry j and its index g; an index >= N raises BGS_CHECK_INDEX and yields a
