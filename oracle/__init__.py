@@ -80,6 +80,8 @@ def _load():
                                        P, P, P, P, P, P, P, P]
             lib.orc_render_backward.argtypes = [i32, i32, i32, i32, i64, P, P, P, P, P, P, P,
                                                 P, P, P, i64, P, P, P, P, P, P, P]
+            lib.orc_sh_to_rgb.argtypes = [i64, i32, i32, i32, P, P, P, P, P]
+            lib.orc_sh_to_rgb_backward.argtypes = [i64, i32, i32, i32, P, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -171,6 +173,38 @@ def preprocess_backward(means3D, log_scales, quats, cam: dict, dL_dmeans2D, dL_d
                                 float(cam.get("lowpass", 0.3)), _p(rad), _p(gm), _p(gc), _p(gd),
                                 _p(out["means3D"]), _p(out["log_scales"]), _p(out["quats"]))
     return out
+
+
+def sh_to_rgb(sh, means3D, campos, degree: int):
+    """View-dependent colour of Sec. 2.1 from real orthonormal spherical harmonics of
+    degree <= 3 in FP64: sh [N, K, 3] (K >= (degree+1)^2 coefficient rows), means3D [N,3],
+    campos [V,3] (or [3]).  Returns rgb [V,N,3] and clamped [V,N,3] (uint8, 1 where the
+    channel sum + 1/2 was negative and the colour clamped to 0)."""
+    lib = _load()
+    c = _f64(sh)
+    N, K = c.shape[0], c.shape[1]
+    m3 = _f64(means3D).reshape(N, 3)
+    cp = _f64(campos).reshape(-1, 3)
+    V = cp.shape[0]
+    rgb = np.zeros((V, N, 3))
+    clamped = np.zeros((V, N, 3), np.uint8)
+    lib.orc_sh_to_rgb(N, V, int(degree), K, _p(c), _p(m3), _p(cp), _p(rgb), _p(clamped))
+    return rgb, clamped
+
+
+def sh_to_rgb_backward(sh, means3D, campos, degree: int, dL_drgb):
+    """Gradients of ``sh_to_rgb`` in FP64: dL_drgb [V,N,3] -> dL/dsh [N,K,3] and
+    dL/dmeans3D [N,3] (through the view direction), summed over the V views."""
+    lib = _load()
+    c = _f64(sh)
+    N, K = c.shape[0], c.shape[1]
+    m3 = _f64(means3D).reshape(N, 3)
+    cp = _f64(campos).reshape(-1, 3)
+    V = cp.shape[0]
+    g = _f64(dL_drgb).reshape(V, N, 3)
+    d_sh, d_m = np.zeros((N, K, 3)), np.zeros((N, 3))
+    lib.orc_sh_to_rgb_backward(N, V, int(degree), K, _p(c), _p(m3), _p(cp), _p(g), _p(d_sh), _p(d_m))
+    return d_sh, d_m
 
 
 def bin_tiles(means2D, radius, depth, W, H, tile_w=16, tile_h=16, capacity=None):

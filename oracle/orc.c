@@ -652,3 +652,131 @@ void orc_render_backward(int W, int H, int tw, int th, int64_t N, const double *
         free(suf);
     }
 }
+
+/* ---- view-dependent colour from spherical harmonics (Sec. 2.1) -------------------------
+ * The paper represents a Gaussian's colour by spherical harmonics (Sec. 2.1) and fixes no
+ * basis.  Reading: the real orthonormal spherical harmonics of degree l <= 3 with the
+ * Condon-Shortley phase, written as homogeneous harmonic polynomials of the unit
+ * direction d = (x, y, z) from the camera centre to the Gaussian's mean, in the order
+ * (l, m) = (0,0), (1,-1), (1,0), (1,1), (2,-2), ..., (2,2), (3,-3), ..., (3,3).  Colour
+ * channel c = sum_k Y_k(d) sh[k][c] + 1/2, clamped below at 0; a clamped channel passes no
+ * gradient.  Normalisation constants are the closed forms sqrt((2l+1)/(4 pi) ...) below.
+ *
+ * Y[k] and, when grad is not NULL, the gradient of the polynomial Y_k(x, y, z) (x, y, z
+ * taken as independent variables) in grad[3k .. 3k+2]. */
+static void orc_sh_basis(int degree, double x, double y, double z, double *Y, double *grad) {
+    const double pi = 3.14159265358979323846;
+    const double c0 = 0.5 / sqrt(pi);                  /* Y_00                       */
+    const double c1 = sqrt(3.0 / (4.0 * pi));          /* |Y_1m| / |coordinate|      */
+    const double c2a = 0.5 * sqrt(15.0 / pi);          /* xy, yz, xz terms           */
+    const double c2b = 0.25 * sqrt(5.0 / pi);          /* 2z^2 - x^2 - y^2           */
+    const double c2c = 0.25 * sqrt(15.0 / pi);         /* x^2 - y^2                  */
+    const double c3a = 0.25 * sqrt(35.0 / (2.0 * pi)); /* y(3x^2 - y^2), x(x^2 - 3y^2) */
+    const double c3b = 0.5 * sqrt(105.0 / pi);         /* xyz                        */
+    const double c3c = 0.25 * sqrt(21.0 / (2.0 * pi)); /* y(4z^2 - x^2 - y^2), x(...) */
+    const double c3d = 0.25 * sqrt(7.0 / pi);          /* z(2z^2 - 3x^2 - 3y^2)       */
+    const double c3e = 0.25 * sqrt(105.0 / pi);        /* z(x^2 - y^2)               */
+    double g[16][3];
+    memset(g, 0, sizeof g);
+    Y[0] = c0;
+    if (degree >= 1) {
+        Y[1] = -c1 * y;  g[1][1] = -c1;
+        Y[2] = c1 * z;   g[2][2] = c1;
+        Y[3] = -c1 * x;  g[3][0] = -c1;
+    }
+    if (degree >= 2) {
+        Y[4] = c2a * x * y;
+        g[4][0] = c2a * y; g[4][1] = c2a * x;
+        Y[5] = -c2a * y * z;
+        g[5][1] = -c2a * z; g[5][2] = -c2a * y;
+        Y[6] = c2b * (2.0 * z * z - x * x - y * y);
+        g[6][0] = -2.0 * c2b * x; g[6][1] = -2.0 * c2b * y; g[6][2] = 4.0 * c2b * z;
+        Y[7] = -c2a * x * z;
+        g[7][0] = -c2a * z; g[7][2] = -c2a * x;
+        Y[8] = c2c * (x * x - y * y);
+        g[8][0] = 2.0 * c2c * x; g[8][1] = -2.0 * c2c * y;
+    }
+    if (degree >= 3) {
+        Y[9] = -c3a * y * (3.0 * x * x - y * y);
+        g[9][0] = -6.0 * c3a * x * y; g[9][1] = -c3a * (3.0 * x * x - 3.0 * y * y);
+        Y[10] = c3b * x * y * z;
+        g[10][0] = c3b * y * z; g[10][1] = c3b * x * z; g[10][2] = c3b * x * y;
+        Y[11] = -c3c * y * (4.0 * z * z - x * x - y * y);
+        g[11][0] = 2.0 * c3c * x * y; g[11][1] = -c3c * (4.0 * z * z - x * x - 3.0 * y * y);
+        g[11][2] = -8.0 * c3c * y * z;
+        Y[12] = c3d * z * (2.0 * z * z - 3.0 * x * x - 3.0 * y * y);
+        g[12][0] = -6.0 * c3d * x * z; g[12][1] = -6.0 * c3d * y * z;
+        g[12][2] = c3d * (6.0 * z * z - 3.0 * x * x - 3.0 * y * y);
+        Y[13] = -c3c * x * (4.0 * z * z - x * x - y * y);
+        g[13][0] = -c3c * (4.0 * z * z - 3.0 * x * x - y * y); g[13][1] = 2.0 * c3c * x * y;
+        g[13][2] = -8.0 * c3c * x * z;
+        Y[14] = c3e * z * (x * x - y * y);
+        g[14][0] = 2.0 * c3e * x * z; g[14][1] = -2.0 * c3e * y * z; g[14][2] = c3e * (x * x - y * y);
+        Y[15] = -c3a * x * (x * x - 3.0 * y * y);
+        g[15][0] = -c3a * (3.0 * x * x - 3.0 * y * y); g[15][1] = 6.0 * c3a * x * y;
+    }
+    if (grad) memcpy(grad, g, sizeof(double) * 3 * (degree + 1) * (degree + 1));
+}
+
+/* Unit direction from campos to the mean and its length. */
+static double orc_sh_dir(const double *mean, const double *campos, double *d) {
+    const double v[3] = {mean[0] - campos[0], mean[1] - campos[1], mean[2] - campos[2]};
+    const double len = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int a = 0; a < 3; ++a) d[a] = v[a] / len;
+    return len;
+}
+
+/* rgb [V,N,3] and clamped [V,N,3] (nullable; 1 where the channel was clamped at 0) of N
+ * Gaussians with coefficients sh [N, stride, 3] (stride >= (degree+1)^2 rows) seen from V
+ * camera centres campos [V,3]. */
+void orc_sh_to_rgb(int64_t N, int V, int degree, int stride, const double *sh, const double *means3D,
+                   const double *campos, double *rgb, uint8_t *clamped) {
+    const int nk = (degree + 1) * (degree + 1);
+    for (int v = 0; v < V; ++v)
+        for (int64_t i = 0; i < N; ++i) {
+            double d[3], Y[16];
+            orc_sh_dir(means3D + 3 * i, campos + 3 * v, d);
+            orc_sh_basis(degree, d[0], d[1], d[2], Y, NULL);
+            for (int c = 0; c < 3; ++c) {
+                double s = 0.5;
+                for (int k = 0; k < nk; ++k) s += Y[k] * sh[(i * stride + k) * 3 + c];
+                const int64_t o = ((int64_t)v * N + i) * 3 + c;
+                rgb[o] = s < 0.0 ? 0.0 : s;
+                if (clamped) clamped[o] = s < 0.0 ? 1 : 0;
+            }
+        }
+}
+
+/* Gradients of orc_sh_to_rgb: dL_drgb [V,N,3] -> dL_dsh [N, stride, 3] and dL_dmeans3D
+ * [N,3], summed over the views (overwritten).  With u = mean - campos and d = u / |u|,
+ * dL/du = (dL/dd - (dL/dd . d) d) / |u|, and dL/dd = sum_k (sum_c sh[k][c] g_c) grad Y_k
+ * with g_c = dL/drgb_c for an unclamped channel, 0 for a clamped one. */
+void orc_sh_to_rgb_backward(int64_t N, int V, int degree, int stride, const double *sh, const double *means3D,
+                            const double *campos, const double *dL_drgb, double *dL_dsh, double *dL_dmeans3D) {
+    const int nk = (degree + 1) * (degree + 1);
+    memset(dL_dsh, 0, sizeof(double) * N * stride * 3);
+    memset(dL_dmeans3D, 0, sizeof(double) * N * 3);
+    for (int v = 0; v < V; ++v)
+        for (int64_t i = 0; i < N; ++i) {
+            double d[3], Y[16], gY[48];
+            const double len = orc_sh_dir(means3D + 3 * i, campos + 3 * v, d);
+            orc_sh_basis(degree, d[0], d[1], d[2], Y, gY);
+            double g[3];
+            for (int c = 0; c < 3; ++c) {
+                double s = 0.5;
+                for (int k = 0; k < nk; ++k) s += Y[k] * sh[(i * stride + k) * 3 + c];
+                g[c] = s < 0.0 ? 0.0 : dL_drgb[((int64_t)v * N + i) * 3 + c];
+            }
+            double dd[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < nk; ++k) {
+                double w = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    dL_dsh[(i * stride + k) * 3 + c] += Y[k] * g[c];
+                    w += sh[(i * stride + k) * 3 + c] * g[c];
+                }
+                for (int a = 0; a < 3; ++a) dd[a] += w * gY[3 * k + a];
+            }
+            const double dot = dd[0] * d[0] + dd[1] * d[1] + dd[2] * d[2];
+            for (int a = 0; a < 3; ++a) dL_dmeans3D[3 * i + a] += (dd[a] - dot * d[a]) / len;
+        }
+}

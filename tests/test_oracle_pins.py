@@ -535,3 +535,127 @@ def test_projection_backward_quaternion_gradient_is_tangent():
     g2 = oracle.preprocess_backward(m3, ls, 2.0 * q, cam, gm, gc)["quats"]
     np.testing.assert_allclose(np.sum(g1 * q, axis=1), 0.0, atol=1e-9 * np.abs(g1).max())
     np.testing.assert_allclose(g2, 0.5 * g1, rtol=1e-9, atol=1e-15)
+
+
+# ---- view-dependent colour: spherical harmonics of degree <= 3 (Sec. 2.1) ----------------
+
+def _sh_values(dirs, degree=3):
+    """Y_k(d) for unit directions dirs [M,3], read back through the oracle's colour with one
+    small coefficient at a time (0.1 Y + 1/2 stays positive, so nothing is clamped)."""
+    K = (degree + 1) ** 2
+    M = dirs.shape[0]
+    out = np.zeros((M, K))
+    for k in range(K):
+        sh = np.zeros((M, K, 3))
+        sh[:, k, 0] = 0.1
+        rgb, clamped = oracle.sh_to_rgb(sh, dirs, np.zeros(3), degree)
+        assert not clamped.any()
+        out[:, k] = (rgb[0, :, 0] - 0.5) / 0.1
+    return out
+
+
+def _real_sh_scipy(l, m, dirs):
+    """Real orthonormal SH with the Condon-Shortley phase from scipy's complex ones:
+    sqrt(2) Re Y_l^m (m > 0), sqrt(2) Im Y_l^|m| (m < 0), Y_l^0 (m = 0)."""
+    import scipy.special as sp
+    theta = np.arccos(np.clip(dirs[:, 2], -1, 1))
+    phi = np.arctan2(dirs[:, 1], dirs[:, 0])
+    if hasattr(sp, "sph_harm_y"):
+        Y = sp.sph_harm_y(l, abs(m), theta, phi)
+    else:
+        Y = sp.sph_harm(abs(m), l, phi, theta)
+    if m > 0:
+        return math.sqrt(2) * Y.real
+    if m < 0:
+        return math.sqrt(2) * Y.imag
+    return Y.real
+
+
+def _random_dirs(n, seed):
+    d = np.random.default_rng(seed).normal(size=(n, 3))
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def test_sh_basis_equals_scipy_real_harmonics():
+    dirs = _random_dirs(200, 11)
+    Y = _sh_values(dirs)
+    k = 0
+    for l in range(4):
+        for m in range(-l, l + 1):
+            np.testing.assert_allclose(Y[:, k], _real_sh_scipy(l, m, dirs), rtol=0, atol=1e-12, err_msg=f"l={l} m={m}")
+            k += 1
+
+
+def test_sh_basis_orthonormal_on_the_sphere():
+    """Gauss-Legendre in cos(theta) x uniform phi integrates products of two degree-3
+    harmonics exactly: the Gram matrix must be the identity."""
+    ct, wt = np.polynomial.legendre.leggauss(8)
+    nphi = 16
+    phi = 2 * np.pi * np.arange(nphi) / nphi
+    st = np.sqrt(1 - ct ** 2)
+    dirs = np.stack([np.outer(st, np.cos(phi)).ravel(), np.outer(st, np.sin(phi)).ravel(),
+                     np.repeat(ct, nphi)], axis=1)
+    w = np.repeat(wt, nphi) * (2 * np.pi / nphi)
+    Y = _sh_values(dirs)
+    gram = (Y * w[:, None]).T @ Y
+    np.testing.assert_allclose(gram, np.eye(16), atol=1e-12)
+
+
+def test_sh_addition_theorem():
+    """sum_m Y_lm(d)^2 = (2l + 1) / (4 pi) for every direction and degree."""
+    Y = _sh_values(_random_dirs(64, 12))
+    k = 0
+    for l in range(4):
+        s = (Y[:, k:k + 2 * l + 1] ** 2).sum(axis=1)
+        np.testing.assert_allclose(s, (2 * l + 1) / (4 * np.pi), rtol=1e-13)
+        k += 2 * l + 1
+
+
+def test_sh_degree0_closed_form_and_clamp():
+    rng = np.random.default_rng(13)
+    sh = rng.normal(size=(50, 1, 3))
+    m = rng.normal(size=(50, 3)) * 3
+    rgb, clamped = oracle.sh_to_rgb(sh, m, np.array([0.3, -0.1, 0.2]), 0)
+    s = sh[:, 0, :] / (2 * math.sqrt(math.pi)) + 0.5
+    np.testing.assert_allclose(rgb[0], np.maximum(s, 0), rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(clamped[0], (s < 0).astype(np.uint8))
+    # a clamped channel passes no gradient (to its coefficients or, through it, to the mean)
+    g = np.ones((1, 50, 3))
+    d_sh, d_m = oracle.sh_to_rgb_backward(sh, m, np.array([0.3, -0.1, 0.2]), 0, g)
+    np.testing.assert_allclose(d_sh[:, 0, :], np.where(s < 0, 0.0, 1 / (2 * math.sqrt(math.pi))), atol=1e-15)
+    np.testing.assert_allclose(d_m, 0.0, atol=1e-15)  # degree 0 does not depend on the direction
+    assert clamped.any() and not clamped.all()
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_sh_backward_matches_central_differences(degree):
+    rng = np.random.default_rng(20 + degree)
+    N, K = 6, 16
+    sh = rng.normal(size=(N, K, 3)) * 0.3
+    m = rng.normal(size=(N, 3)) + np.array([0.0, 0.0, 3.0])
+    cp = np.array([[0.0, 0.0, 0.0], [0.4, -0.3, 0.2]])
+    g = rng.normal(size=(2, N, 3))
+    rgb, clamped = oracle.sh_to_rgb(sh, m, cp, degree)
+    assert not clamped.any()
+    d_sh, d_m = oracle.sh_to_rgb_backward(sh, m, cp, degree, g)
+    L = lambda s_, m_: (oracle.sh_to_rgb(s_, m_, cp, degree)[0] * g).sum()
+    h = 1e-6
+    fd_m = np.zeros_like(m)
+    for i in range(N):
+        for a in range(3):
+            mp, mm = m.copy(), m.copy()
+            mp[i, a] += h
+            mm[i, a] -= h
+            fd_m[i, a] = (L(sh, mp) - L(sh, mm)) / (2 * h)
+    np.testing.assert_allclose(d_m, fd_m, rtol=1e-6, atol=1e-8)
+    nk = (degree + 1) ** 2
+    fd_s = np.zeros_like(sh)
+    for i in range(N):
+        for k in range(K):
+            for c in range(3):
+                sp_, sm_ = sh.copy(), sh.copy()
+                sp_[i, k, c] += h
+                sm_[i, k, c] -= h
+                fd_s[i, k, c] = (L(sp_, m) - L(sm_, m)) / (2 * h)
+    np.testing.assert_allclose(d_sh, fd_s, rtol=1e-6, atol=1e-8)
+    assert np.all(d_sh[:, nk:, :] == 0)  # rows past (degree + 1)^2 are not read
