@@ -583,6 +583,28 @@ def main_views(args, scene, rank, world, local):
         # algorithmic bytes: forward reads 44 B per Gaussian and writes 36 B per record;
         # backward reads 40 B per Gaussian + 28 B per record and writes 40 B per Gaussian
         proj_bytes = (44 * N + 36 * N * V, 80 * N + 28 * N * V)
+        # ---- view-dependent colour from degree-3 spherical harmonics (Sec. 2.1) alone ----
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(17)
+        sh_coef = 0.2 * torch.randn((N, 16, 3), device=dev, generator=gen)
+        g_rgb = torch.randn((V * N, 3), device=dev, generator=gen)
+        rgb_sh = torch.empty((V * N, 3), device=dev)
+        shf, shb = [], []
+        for it in range(6):
+            ev[0].record(side)
+            raster.sh_to_rgb(plan, sh_coef, d["means3D"], cams, 3, out=rgb_sh)
+            ev[1].record(side)
+            raster.sh_to_rgb_backward(plan, sh_coef, d["means3D"], cams, 3, g_rgb)
+            ev[2].record(side)
+            side.synchronize()
+            if it >= 2:
+                shf.append(ev[0].elapsed_time(ev[1]))
+                shb.append(ev[1].elapsed_time(ev[2]))
+        sh_ms = (float(np.median(shf)), float(np.median(shb)))
+        # algorithmic bytes: forward reads 192 B of coefficients + 12 B of mean per Gaussian and
+        # writes 12 B per record; backward reads 204 B per Gaussian + 12 B per record and
+        # writes 192 + 12 B per Gaussian
+        sh_bytes = (204 * N + 12 * N * V, 408 * N + 12 * N * V)
         # ---- plain pixel-wise 16x16 static grid on the same inputs ----
         # (single-view kernel: a view at a time, each with its own binning; render kernels
         # only, summed over the views)
@@ -643,6 +665,13 @@ def main_views(args, scene, rank, world, local):
                   "note": "a1 projection and its backward (chain rule to means3D, log_scales, quats); "
                           "algorithmic bytes: forward 44 B per Gaussian + 36 B per record, backward 80 B per "
                           "Gaussian + 28 B per record"}
+    sh_row = {"degree": 3, "forward_ms": sh_ms[0], "backward_ms": sh_ms[1],
+              "forward_GB_s": sh_bytes[0] / (sh_ms[0] / 1e3) / 1e9,
+              "backward_GB_s": sh_bytes[1] / (sh_ms[1] / 1e3) / 1e9, "hbm_peak_GB_s": hbm,
+              "frac_of_hbm": [sh_bytes[0] / (sh_ms[0] / 1e3) / 1e9 / hbm, sh_bytes[1] / (sh_ms[1] / 1e3) / 1e9 / hbm],
+              "note": "view-dependent colour of every record from 16 x 3 coefficients per Gaussian (seeded "
+                      "synthetic) and its backward; algorithmic bytes: forward 204 B per Gaussian + 12 B per "
+                      "record, backward 408 B per Gaussian + 12 B per record"}
     sizes = sorted(set(f"{c['W']}x{c['H']}" for c in cams))
     config = {"workload": WORKLOADS.get(args.config, f"{V} views ({', '.join(sizes)}) of {N} Gaussians"),
               "gaussians": N, "views": V, "image": sizes[0] if V == 1 else sizes, "tile": "16x16",
@@ -663,6 +692,7 @@ def main_views(args, scene, rank, world, local):
                   "tile_list_p99": float(np.percentile(lens, 99)), "tile_eval_pairs": tile_hist},
         "binning": binning,
         "projection": projection,
+        "spherical_harmonics": sh_row,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": whole_job_value(eval_pairs, world, e2e_ms), "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),

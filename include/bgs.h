@@ -300,6 +300,44 @@ int bgs_render_backward_batched(bgs_plan *plan, int32_t V, const bgs_view *views
                                 int32_t tile_w, int32_t tile_h, const float *bg, int32_t mode, float *dL_dmeans2D,
                                 float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,
                                 void *stream);
+/* As bgs_render_forward_batched / bgs_render_backward_batched with view-dependent colours:
+   colors [V * N, 3] holds the colour of every record (view v's colours at rows v * N ..,
+   e.g. from bgs_sh_to_rgb), and dL_dcolors [V * N, 3] receives the per-record colour
+   gradients (no sum over the views). */
+int bgs_render_forward_batched_vc(bgs_plan *plan, int32_t V, const bgs_view *views, int64_t N,
+                                  const float *means2D, const float *conic_opacity, const float *colors,
+                                  const float *depths, const uint32_t *point_list, int64_t num_entries,
+                                  const uint32_t *ranges, int32_t tile_w, int32_t tile_h, const float *bg,
+                                  int32_t mode, void *stream);
+int bgs_render_backward_batched_vc(bgs_plan *plan, int32_t V, const bgs_view *views, int64_t N,
+                                   const float *means2D, const float *conic_opacity, const float *colors,
+                                   const float *depths, const uint32_t *point_list, int64_t num_entries,
+                                   const uint32_t *ranges, int32_t tile_w, int32_t tile_h, const float *bg,
+                                   int32_t mode, float *dL_dmeans2D, float *dL_dconic, float *dL_dopacity,
+                                   float *dL_dcolors, float *dL_ddepths, void *stream);
+
+/* ---- view-dependent colour from spherical harmonics (Sec. 2.1) ----------------------
+   The paper represents a Gaussian's colour by spherical harmonics.  Basis: the real
+   orthonormal spherical harmonics Y_k of degree <= `degree` (0..3) with the Condon-Shortley
+   phase, ordered (l, m) = (0,0), (1,-1), (1,0), (1,1), (2,-2), ..., (3,3) (k = l^2 + l + m),
+   evaluated at the unit direction d from view v's camera centre (solved from its viewmat)
+   to means3D[i]:  rgb[v * N + i][c] = max(0, sum_{k < (degree+1)^2} Y_k(d) sh[i][k][c] + 1/2),
+   clamped[v * N + i][c] = 1 where the sum + 1/2 was negative (0 otherwise).
+   sh [N, stride, 3] f32 (stride >= (degree+1)^2 coefficient rows; rows past (degree+1)^2
+   are not read), means3D [N, 3]; views: host array of V <= 32 (only cam.viewmat is read,
+   which must be invertible); rgb [V * N, 3] (device) and clamped [V * N, 3] u8 (device,
+   nullable).  A mean at a camera centre has no direction (NaN colour).  Errors:
+   BGS_ERR_INVALID for a NULL plan / views / array, V or degree out of range, stride too
+   small or a singular viewmat. */
+int bgs_sh_to_rgb(bgs_plan *plan, int32_t V, const bgs_view *views, int64_t N, int32_t degree, int32_t stride,
+                  const float *sh, const float *means3D, float *rgb, uint8_t *clamped, void *stream);
+/* Gradients of bgs_sh_to_rgb: dL_drgb [V * N, 3] -> dL_dsh [N, stride, 3] (rows past
+   (degree+1)^2 zeroed) and dL_dmeans3D [N, 3] (through the view direction), summed over the
+   views and overwriting the outputs.  A clamped channel passes no gradient; the clamp
+   decisions are recomputed with the forward's arithmetic. */
+int bgs_sh_to_rgb_backward(bgs_plan *plan, int32_t V, const bgs_view *views, int64_t N, int32_t degree,
+                           int32_t stride, const float *sh, const float *means3D, const float *dL_drgb,
+                           float *dL_dsh, float *dL_dmeans3D, void *stream);
 /* Autotuner: times forward (+ backward when `backward` is 1) passes of this frame under
    candidate plan knobs -- pixel_rows (sub-tile of pixel-wise items), heavy_threshold (the
    per-tile selector between pixel-wise and Gaussian-wise items), gw_pixels and

@@ -37,7 +37,8 @@ EXPORTS = [
     "bgs_preprocess_backward", "bgs_preprocess_backward_batched", "bgs_plan_selector", "bgs_plan_selector_reset",
     "bgs_plan_inject_fault", "bgs_plan_selector_restore",
     "bgs_render_forward_batched", "bgs_render_backward_batched", "bgs_graph_begin", "bgs_graph_end",
-    "bgs_graph_launch", "bgs_autotune_render",
+    "bgs_graph_launch", "bgs_autotune_render", "bgs_render_forward_batched_vc", "bgs_render_backward_batched_vc",
+    "bgs_sh_to_rgb", "bgs_sh_to_rgb_backward",
 ]
 
 
@@ -134,6 +135,10 @@ def load(build_if_needed: bool = True):
         lib.bgs_render_forward_batched.argtypes = [P, i32, VP, i64, P, P, P, P, P, i64, P, i32, i32, P, i32, P]
         lib.bgs_render_backward_batched.argtypes = [P, i32, VP, i64, P, P, P, P, P, i64, P, i32, i32, P, i32,
                                                     P, P, P, P, P, P]
+        lib.bgs_render_forward_batched_vc.argtypes = lib.bgs_render_forward_batched.argtypes
+        lib.bgs_render_backward_batched_vc.argtypes = lib.bgs_render_backward_batched.argtypes
+        lib.bgs_sh_to_rgb.argtypes = [P, i32, VP, i64, i32, i32, P, P, P, P, P]
+        lib.bgs_sh_to_rgb_backward.argtypes = [P, i32, VP, i64, i32, i32, P, P, P, P, P, P]
         lib.bgs_autotune_render.argtypes = [P, i32, VP, i64, P, P, P, P, P, i64, P, i32, i32, P, i32,
                                             P, P, P, P, ctypes.POINTER(ctypes.c_double), P]
         lib.bgs_graph_begin.argtypes = [P, P]

@@ -294,6 +294,12 @@ cudaError_t launch_bin_scatter(long long N, int G, int B, int W32, const uint4 *
 cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *total, long long capacity, DevCtrl *ctrl,
                                cudaStream_t s);
 
+// view-dependent colour from spherical harmonics (sh.cu); backward: dL_drgb -> dL_dsh,
+// dL_dmeans3D (summed over the V <= kMaxViews camera centres campos [V,3], host)
+cudaError_t launch_sh(bool backward, long long N, int degree, int stride, const float *sh, const float *means3D,
+                      int V, const float *campos, float *rgb, uint8_t *clamped, const float *dL_drgb, float *dL_dsh,
+                      float *dL_dmeans3D, cudaStream_t s);
+
 // recs[i] from means2D[i], conic_opacity[i], depths[i] and colors[i % n_colors]
 cudaError_t launch_pack(long long N, const float *means2D, const float *conic_opacity, const float *colors,
                         long long n_colors, const float *depths, Rec *recs, cudaStream_t s);

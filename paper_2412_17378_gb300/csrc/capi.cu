@@ -1163,10 +1163,11 @@ static int batched_tables(int V, const bgs_view *views, int tw, int th, bgs::Vie
     return make_view_table(V, Ws, Hs, tw, th, vt);
 }
 
-int bgs_render_forward_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
-                               const float *conic_opacity, const float *colors, const float *depths,
-                               const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges, int32_t tw,
-                               int32_t th, const float *bg, int32_t mode, void *stream) {
+// Batched forward; colours [N,3] shared by the views (per_view false) or [V*N,3] per record.
+static int render_forward_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                                  const float *conic_opacity, const float *colors, const float *depths,
+                                  const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges, int32_t tw,
+                                  int32_t th, const float *bg, int32_t mode, bool per_view, void *stream) {
     if (!p) return fail(BGS_ERR_INVALID, "bgs_render_forward_batched: NULL plan");
     if (mode == BGS_MODE_STATIC || mode == BGS_MODE_SELECT)
         return fail(BGS_ERR_INVALID, "bgs_render_forward_batched: the static kernel (and the selector) is single-view");
@@ -1189,15 +1190,34 @@ int bgs_render_forward_batched(bgs_plan *p, int32_t V, const bgs_view *views, in
         io.n_eval[v] = w.n_eval;
     }
     DeviceGuard g(p->device);
-    return render_forward_impl(p, vt, io, N * V, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
-                               ranges, tw, th, bg, mode, (cudaStream_t)stream);
+    return render_forward_impl(p, vt, io, N * V, per_view ? N * V : N, means2D, conic_opacity, colors, depths,
+                               point_list, num_entries, ranges, tw, th, bg, mode, (cudaStream_t)stream);
 }
 
-int bgs_render_backward_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
-                                const float *conic_opacity, const float *colors, const float *depths,
-                                const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges, int32_t tw,
-                                int32_t th, const float *bg, int32_t mode, float *dL_dmeans2D, float *dL_dconic,
-                                float *dL_dopacity, float *dL_dcolors, float *dL_ddepths, void *stream) {
+int bgs_render_forward_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                               const float *conic_opacity, const float *colors, const float *depths,
+                               const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges, int32_t tw,
+                               int32_t th, const float *bg, int32_t mode, void *stream) {
+    return render_forward_batched(p, V, views, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
+                                  ranges, tw, th, bg, mode, false, stream);
+}
+
+int bgs_render_forward_batched_vc(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                                  const float *conic_opacity, const float *colors, const float *depths,
+                                  const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges, int32_t tw,
+                                  int32_t th, const float *bg, int32_t mode, void *stream) {
+    return render_forward_batched(p, V, views, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
+                                  ranges, tw, th, bg, mode, true, stream);
+}
+
+// Batched backward; colours and dL_dcolors [N,3] shared by the views (per_view false) or
+// [V*N,3] per record.
+static int render_backward_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                                   const float *conic_opacity, const float *colors, const float *depths,
+                                   const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
+                                   int32_t tw, int32_t th, const float *bg, int32_t mode, float *dL_dmeans2D,
+                                   float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,
+                                   bool per_view, void *stream) {
     if (!p) return fail(BGS_ERR_INVALID, "bgs_render_backward_batched: NULL plan");
     if (mode == BGS_MODE_STATIC || mode == BGS_MODE_SELECT)
         return fail(BGS_ERR_INVALID, "bgs_render_backward_batched: the static kernel (and the selector) is single-view");
@@ -1221,9 +1241,90 @@ int bgs_render_backward_batched(bgs_plan *p, int32_t V, const bgs_view *views, i
         gi.dL_dalpha[v] = w.dL_dalpha;
     }
     DeviceGuard g(p->device);
-    return render_backward_impl(p, vt, gi, N * V, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
-                                ranges, tw, th, bg, mode, dL_dmeans2D, dL_dconic, dL_dopacity, dL_dcolors, dL_ddepths,
-                                (cudaStream_t)stream);
+    return render_backward_impl(p, vt, gi, N * V, per_view ? N * V : N, means2D, conic_opacity, colors, depths,
+                                point_list, num_entries, ranges, tw, th, bg, mode, dL_dmeans2D, dL_dconic,
+                                dL_dopacity, dL_dcolors, dL_ddepths, (cudaStream_t)stream);
+}
+
+int bgs_render_backward_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                                const float *conic_opacity, const float *colors, const float *depths,
+                                const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges, int32_t tw,
+                                int32_t th, const float *bg, int32_t mode, float *dL_dmeans2D, float *dL_dconic,
+                                float *dL_dopacity, float *dL_dcolors, float *dL_ddepths, void *stream) {
+    return render_backward_batched(p, V, views, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
+                                   ranges, tw, th, bg, mode, dL_dmeans2D, dL_dconic, dL_dopacity, dL_dcolors,
+                                   dL_ddepths, false, stream);
+}
+
+int bgs_render_backward_batched_vc(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
+                                   const float *conic_opacity, const float *colors, const float *depths,
+                                   const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
+                                   int32_t tw, int32_t th, const float *bg, int32_t mode, float *dL_dmeans2D,
+                                   float *dL_dconic, float *dL_dopacity, float *dL_dcolors, float *dL_ddepths,
+                                   void *stream) {
+    return render_backward_batched(p, V, views, N, means2D, conic_opacity, colors, depths, point_list, num_entries,
+                                   ranges, tw, th, bg, mode, dL_dmeans2D, dL_dconic, dL_dopacity, dL_dcolors,
+                                   dL_ddepths, true, stream);
+}
+
+// Camera centre of a world -> camera viewmat (row-major [A t; 0 1]): A c + t = 0, solved in
+// double by the adjugate of A (A is a rotation for a rigid camera, then c = -A^T t).
+static bool camera_centre(const bgs_camera &cam, float *c) {
+    const float *M = cam.viewmat;
+    const double a[3][3] = {{M[0], M[1], M[2]}, {M[4], M[5], M[6]}, {M[8], M[9], M[10]}};
+    const double t[3] = {M[3], M[7], M[11]};
+    const double co[3][3] = {{a[1][1] * a[2][2] - a[1][2] * a[2][1], a[1][2] * a[2][0] - a[1][0] * a[2][2],
+                              a[1][0] * a[2][1] - a[1][1] * a[2][0]},
+                             {a[0][2] * a[2][1] - a[0][1] * a[2][2], a[0][0] * a[2][2] - a[0][2] * a[2][0],
+                              a[0][1] * a[2][0] - a[0][0] * a[2][1]},
+                             {a[0][1] * a[1][2] - a[0][2] * a[1][1], a[0][2] * a[1][0] - a[0][0] * a[1][2],
+                              a[0][0] * a[1][1] - a[0][1] * a[1][0]}};
+    const double det = a[0][0] * co[0][0] + a[0][1] * co[0][1] + a[0][2] * co[0][2];
+    if (!(fabs(det) > 1e-30)) return false;
+    // inverse = co^T / det; c = -inverse t
+    for (int r = 0; r < 3; ++r) c[r] = (float)(-(co[0][r] * t[0] + co[1][r] * t[1] + co[2][r] * t[2]) / det);
+    return true;
+}
+
+static int sh_args(const char *fn, bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, int32_t degree,
+                   int32_t stride, float *campos) {
+    if (!p || !views) return fail(BGS_ERR_INVALID, "%s: NULL plan or views", fn);
+    if (V < 1 || V > bgs::kMaxViews) return fail(BGS_ERR_INVALID, "%s: V=%d", fn, V);
+    if (N < 0 || N * V >= (1ll << 40)) return fail(BGS_ERR_INVALID, "%s: N out of range", fn);
+    if (degree < 0 || degree > 3) return fail(BGS_ERR_INVALID, "%s: degree %d not in 0..3", fn, degree);
+    if (stride < (degree + 1) * (degree + 1)) return fail(BGS_ERR_INVALID, "%s: stride %d < (degree+1)^2", fn, stride);
+    for (int v = 0; v < V; ++v)
+        if (!camera_centre(views[v].cam, campos + 3 * v))
+            return fail(BGS_ERR_INVALID, "%s: singular viewmat of view %d", fn, v);
+    return BGS_OK;
+}
+
+int bgs_sh_to_rgb(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, int32_t degree, int32_t stride,
+                  const float *sh, const float *means3D, float *rgb, uint8_t *clamped, void *stream) {
+    float campos[3 * bgs::kMaxViews];
+    BGS_TRY(sh_args("bgs_sh_to_rgb", p, V, views, N, degree, stride, campos));
+    if (N > 0 && (!sh || !means3D || !rgb)) return fail(BGS_ERR_INVALID, "bgs_sh_to_rgb: NULL array");
+    DeviceGuard g(p->device);
+    BGS_CUDA(bgs::launch_sh(false, N, degree, stride, sh, means3D, V, campos, rgb, clamped, nullptr, nullptr, nullptr,
+                            (cudaStream_t)stream),
+             "sh_to_rgb");
+    if (N > 0) p->host_launches += 1;
+    return BGS_OK;
+}
+
+int bgs_sh_to_rgb_backward(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, int32_t degree, int32_t stride,
+                           const float *sh, const float *means3D, const float *dL_drgb, float *dL_dsh,
+                           float *dL_dmeans3D, void *stream) {
+    float campos[3 * bgs::kMaxViews];
+    BGS_TRY(sh_args("bgs_sh_to_rgb_backward", p, V, views, N, degree, stride, campos));
+    if (N > 0 && (!sh || !means3D || !dL_drgb || !dL_dsh || !dL_dmeans3D))
+        return fail(BGS_ERR_INVALID, "bgs_sh_to_rgb_backward: NULL array");
+    DeviceGuard g(p->device);
+    BGS_CUDA(bgs::launch_sh(true, N, degree, stride, sh, means3D, V, campos, nullptr, nullptr, dL_drgb, dL_dsh,
+                            dL_dmeans3D, (cudaStream_t)stream),
+             "sh_to_rgb_backward");
+    if (N > 0) p->host_launches += 1;
+    return BGS_OK;
 }
 
 int bgs_graph_begin(bgs_plan *p, void *stream) {

@@ -507,12 +507,16 @@ def alloc_view_outputs(cams, device, n_eval=False):
 
 def render_forward_batched(plan: Plan, means2D, conic_opacity, colors, depths, point_list, num_entries: int, ranges,
                            cams, tile=(16, 16), bg=(0.0, 0.0, 0.0), mode="auto", outs=None, n_eval=False):
-    """bgs_render_forward_batched: returns the list of per-view output dicts."""
-    R, N, V = means2D.shape[0], colors.shape[0], len(cams)
-    assert R == N * V
+    """bgs_render_forward_batched: returns the list of per-view output dicts.  colors is
+    [N, 3] (shared by the views) or, for view-dependent colours, [V*N, 3] (one row per
+    record, e.g. from sh_to_rgb; bgs_render_forward_batched_vc)."""
+    R, V = means2D.shape[0], len(cams)
+    N = R // V
+    assert R == N * V and colors.shape[0] in (N, R)
+    per_view = colors.shape[0] == R and V > 1
     _req(means2D, "means2D", torch.float32, (R, 2))
     _req(conic_opacity, "conic_opacity", torch.float32, (R, 4))
-    _req(colors, "colors", torch.float32, (N, 3))
+    _req(colors, "colors", torch.float32, (colors.shape[0], 3))
     _req(depths, "depths", torch.float32, (R,))
     dev = means2D.device
     if outs is None:
@@ -520,9 +524,9 @@ def render_forward_batched(plan: Plan, means2D, conic_opacity, colors, depths, p
     vw = _views(cams, outs=outs)
     bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
     m = MODES[mode] if isinstance(mode, str) else int(mode)
-    check(plan._lib.bgs_render_forward_batched(plan.handle, V, vw, N, _ptr(means2D), _ptr(conic_opacity),
-                                               _ptr(colors), _ptr(depths), _ptr(point_list), int(num_entries),
-                                               _ptr(ranges), tile[0], tile[1], bgv, m, _stream(dev)),
+    fn = plan._lib.bgs_render_forward_batched_vc if per_view else plan._lib.bgs_render_forward_batched
+    check(fn(plan.handle, V, vw, N, _ptr(means2D), _ptr(conic_opacity), _ptr(colors), _ptr(depths),
+             _ptr(point_list), int(num_entries), _ptr(ranges), tile[0], tile[1], bgv, m, _stream(dev)),
           "bgs_render_forward_batched")
     return outs
 
@@ -530,22 +534,76 @@ def render_forward_batched(plan: Plan, means2D, conic_opacity, colors, depths, p
 def render_backward_batched(plan: Plan, means2D, conic_opacity, colors, depths, point_list, num_entries: int, ranges,
                             cams, fw_outs, grads_in, tile=(16, 16), bg=(0.0, 0.0, 0.0), mode="auto", out=None):
     """bgs_render_backward_batched: grads_in[v] = dict(color=[3,H,W], depth=None|[H,W], alpha=None|[H,W]).
-    Returns dict(means2D [V*N,2], conic [V*N,3], opacity [V*N], colors [N,3] (summed over views), depths [V*N])."""
-    R, N, V = means2D.shape[0], colors.shape[0], len(cams)
+    Returns dict(means2D [V*N,2], conic [V*N,3], opacity [V*N], colors, depths [V*N]) with colors
+    [N,3] summed over the views, or [V*N,3] per record when colors is [V*N,3] (view-dependent)."""
+    R, V = means2D.shape[0], len(cams)
+    N = R // V
+    assert R == N * V and colors.shape[0] in (N, R)
+    per_view = colors.shape[0] == R and V > 1
     dev = means2D.device
     if out is None:
         out = dict(means2D=torch.empty((R, 2), device=dev), conic=torch.empty((R, 3), device=dev),
-                   opacity=torch.empty(R, device=dev), colors=torch.empty((N, 3), device=dev),
+                   opacity=torch.empty(R, device=dev), colors=torch.empty((colors.shape[0], 3), device=dev),
                    depths=torch.empty(R, device=dev))
     vw = _views(cams, fw=fw_outs, grads=grads_in)
     bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
     m = MODES[mode] if isinstance(mode, str) else int(mode)
-    check(plan._lib.bgs_render_backward_batched(plan.handle, V, vw, N, _ptr(means2D), _ptr(conic_opacity),
-                                                _ptr(colors), _ptr(depths), _ptr(point_list), int(num_entries),
-                                                _ptr(ranges), tile[0], tile[1], bgv, m, _ptr(out["means2D"]),
-                                                _ptr(out["conic"]), _ptr(out["opacity"]), _ptr(out["colors"]),
-                                                _ptr(out.get("depths")), _stream(dev)), "bgs_render_backward_batched")
+    fn = plan._lib.bgs_render_backward_batched_vc if per_view else plan._lib.bgs_render_backward_batched
+    check(fn(plan.handle, V, vw, N, _ptr(means2D), _ptr(conic_opacity), _ptr(colors), _ptr(depths),
+             _ptr(point_list), int(num_entries), _ptr(ranges), tile[0], tile[1], bgv, m, _ptr(out["means2D"]),
+             _ptr(out["conic"]), _ptr(out["opacity"]), _ptr(out["colors"]), _ptr(out.get("depths")), _stream(dev)),
+          "bgs_render_backward_batched")
     return out
+
+
+# ---- view-dependent colour from spherical harmonics (Sec. 2.1) ---------------------------
+
+def sh_to_rgb(plan: Plan, sh, means3D, cams, degree: int, clamped: bool = False, out=None):
+    """bgs_sh_to_rgb: sh [N, K, 3] (K >= (degree+1)^2), means3D [N, 3], cams: list of V camera
+    dicts (their viewmats give the camera centres).  Returns rgb [V*N, 3] (and, with
+    clamped=True, the clamp flags [V*N, 3] uint8)."""
+    N, V = means3D.shape[0], len(cams)
+    _req(sh, "sh", torch.float32)
+    assert sh.dim() == 3 and sh.shape[0] == N and sh.shape[2] == 3 and sh.shape[1] >= (degree + 1) ** 2
+    _req(means3D, "means3D", torch.float32, (N, 3))
+    dev = means3D.device
+    rgb = out if out is not None else torch.empty((V * N, 3), device=dev)
+    cl = torch.empty((V * N, 3), dtype=torch.uint8, device=dev) if clamped else None
+    vw = _views(cams)
+    check(plan._lib.bgs_sh_to_rgb(plan.handle, V, vw, N, int(degree), sh.shape[1], _ptr(sh), _ptr(means3D),
+                                  _ptr(rgb), _ptr(cl), _stream(dev)), "bgs_sh_to_rgb")
+    return (rgb, cl) if clamped else rgb
+
+
+def sh_to_rgb_backward(plan: Plan, sh, means3D, cams, degree: int, dL_drgb):
+    """bgs_sh_to_rgb_backward: dL_drgb [V*N, 3] -> (dL/dsh [N, K, 3], dL/dmeans3D [N, 3]),
+    summed over the views."""
+    N, V = means3D.shape[0], len(cams)
+    _req(dL_drgb, "dL_drgb", torch.float32, (V * N, 3))
+    dev = means3D.device
+    d_sh, d_m = torch.empty_like(sh), torch.empty((N, 3), device=dev)
+    vw = _views(cams)
+    check(plan._lib.bgs_sh_to_rgb_backward(plan.handle, V, vw, N, int(degree), sh.shape[1], _ptr(sh),
+                                           _ptr(means3D), _ptr(dL_drgb), _ptr(d_sh), _ptr(d_m), _stream(dev)),
+          "bgs_sh_to_rgb_backward")
+    return d_sh, d_m
+
+
+class SHFunction(torch.autograd.Function):
+    """Differentiable view-dependent colour: (sh [N,K,3], means3D [N,3]) -> rgb [V*N,3]."""
+
+    @staticmethod
+    def forward(ctx, sh, means3D, plan, cams, degree):
+        sh, m3 = sh.contiguous(), means3D.contiguous()
+        ctx.plan, ctx.cams, ctx.degree = plan, cams, degree
+        ctx.save_for_backward(sh, m3)
+        return sh_to_rgb(plan, sh, m3, cams, degree)
+
+    @staticmethod
+    def backward(ctx, g_rgb):
+        sh, m3 = ctx.saved_tensors
+        d_sh, d_m = sh_to_rgb_backward(ctx.plan, sh, m3, ctx.cams, ctx.degree, g_rgb.contiguous())
+        return d_sh, d_m, None, None, None
 
 
 def autotune_render(plan: Plan, means2D, conic_opacity, colors, depths, point_list, num_entries: int, ranges, cams,
