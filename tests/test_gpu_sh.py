@@ -194,3 +194,25 @@ def test_batched_render_with_view_dependent_colours(R):
         e = rel_l2(gr["colors"][v * N:(v + 1) * N].cpu().numpy(), og["colors"])
         assert e <= GRAD_REL_L2, (v, e)
     plan.close()
+
+
+@pytest.mark.parametrize("degree,stride,N", [(1, 4, 1000), (3, 16, 257), (3, 16, 1)])
+def test_sh_staged_rows_single_view(R, degree, stride, N):
+    """Coefficient arrays holding exactly the used rows (degree 1 in rows of 4, degree 3 in
+    rows of 16) take the shared-memory staged kernels; N = 257 and 1 leave partial blocks."""
+    plan = R.Plan()
+    sh, m = _inputs(N, stride, 100 + N)
+    cams = _cams(1)
+    rgb = R.sh_to_rgb(plan, torch.from_numpy(sh).cuda(), torch.from_numpy(m).cuda(), cams, degree)
+    ref, ref_cl, s, cp = _oracle_fwd(sh, m, cams, degree)
+    sure = np.abs(s) > AMBIG
+    np.testing.assert_allclose(rgb.cpu().numpy()[sure], ref[sure], rtol=0, atol=SH_ATOL * 2)
+    g = np.random.default_rng(11).normal(size=(N, 3)).astype(np.float32)
+    g[~sure] = 0.0
+    d_sh, d_m = R.sh_to_rgb_backward(plan, torch.from_numpy(sh).cuda(), torch.from_numpy(m).cuda(), cams, degree,
+                                     torch.from_numpy(g).cuda())
+    r_sh, r_m = oracle.sh_to_rgb_backward(sh.astype(np.float64), m.astype(np.float64), cp, degree,
+                                          g.reshape(1, N, 3).astype(np.float64))
+    assert rel_l2(d_sh.cpu().numpy(), r_sh) <= SH_GRAD_REL
+    assert rel_l2(d_m.cpu().numpy(), r_m) <= SH_GRAD_REL
+    plan.close()
