@@ -214,6 +214,23 @@ PROFILED = {  # dominant-kernel ncu summaries that carry DRAM traffic (workload 
 }
 
 
+def time_enqueued(stream, fns, rounds=6, skip=2):
+    """Median device time of each callable in fns: every round enqueues fns[0], fns[1], ...
+    between CUDA events on `stream`, and the host synchronises only once all rounds are
+    enqueued, so the host-side cost of a call overlaps the device work of the rounds before
+    it instead of landing between its events.  The first `skip` rounds are not counted."""
+    import torch
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)] for _ in range(rounds)]
+    for r in range(rounds):
+        ev[r][0].record(stream)
+        for j, f in enumerate(fns):
+            f()
+            ev[r][j + 1].record(stream)
+    stream.synchronize()
+    return [float(np.median([ev[r][j].elapsed_time(ev[r][j + 1]) for r in range(skip, rounds)]))
+            for j in range(len(fns))]
+
+
 def profiled_traffic(kernel: str, config: str, tuned: dict):
     """DRAM read + write bytes per launch of the kernel from its committed ncu summary,
     when that capture was taken on this workload and knobs and the kernel's source files
@@ -472,17 +489,9 @@ def main_views(args, scene, rank, world, local):
         tile_hist = tile_eval_histogram(outs_ne, cams)
         del outs_ne
         # ---- binning alone (a2: depth sort + per-tile lists), CUDA events, no host sync ----
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        bin_ms = []
-        for it in range(6):
-            b0.record(side)
-            raster.bin_and_sort_batched(plan, pre["means2D"], pre["radii"], pre["depths"], cams,
-                                        point_list=state["pl"], ranges=state["rg"], no_sync=True)
-            b1.record(side)
-            side.synchronize()
-            if it >= 2:
-                bin_ms.append(b0.elapsed_time(b1))
-        bin_ms = float(np.median(bin_ms))
+        bin_ms, = time_enqueued(side, [lambda: raster.bin_and_sort_batched(
+            plan, pre["means2D"], pre["radii"], pre["depths"], cams, point_list=state["pl"], ranges=state["rg"],
+            no_sync=True)])
         n_tiles = int(rgh.shape[0])
         # algorithmic bytes: read means2D, radii, depths once (16 B per record), write the
         # point list (4 B per entry) and the ranges (8 B per tile)
@@ -565,21 +574,11 @@ def main_views(args, scene, rank, world, local):
         e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), world, dev) / args.steps
         # ---- projection (a1) and its backward alone, CUDA events ----
         gr = state["gr"]
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        pf, pb = [], []
-        for it in range(6):
-            ev[0].record(side)
-            raster.preprocess_batched(plan, d["means3D"], d["log_scales"], d["quats"], d["opacities"], cams,
-                                      out=state["pre"])
-            ev[1].record(side)
-            raster.preprocess_backward_batched(plan, d["means3D"], d["log_scales"], d["quats"], cams, pre["radii"],
-                                               gr["means2D"], gr["conic"], gr.get("depths"))
-            ev[2].record(side)
-            side.synchronize()
-            if it >= 2:
-                pf.append(ev[0].elapsed_time(ev[1]))
-                pb.append(ev[1].elapsed_time(ev[2]))
-        proj_ms = (float(np.median(pf)), float(np.median(pb)))
+        proj_ms = tuple(time_enqueued(side, [
+            lambda: raster.preprocess_batched(plan, d["means3D"], d["log_scales"], d["quats"], d["opacities"], cams,
+                                              out=state["pre"]),
+            lambda: raster.preprocess_backward_batched(plan, d["means3D"], d["log_scales"], d["quats"], cams,
+                                                       pre["radii"], gr["means2D"], gr["conic"], gr.get("depths"))]))
         # algorithmic bytes: forward reads 44 B per Gaussian and writes 36 B per record;
         # backward reads 40 B per Gaussian + 28 B per record and writes 40 B per Gaussian
         proj_bytes = (44 * N + 36 * N * V, 80 * N + 28 * N * V)
@@ -589,18 +588,9 @@ def main_views(args, scene, rank, world, local):
         sh_coef = 0.2 * torch.randn((N, 16, 3), device=dev, generator=gen)
         g_rgb = torch.randn((V * N, 3), device=dev, generator=gen)
         rgb_sh = torch.empty((V * N, 3), device=dev)
-        shf, shb = [], []
-        for it in range(6):
-            ev[0].record(side)
-            raster.sh_to_rgb(plan, sh_coef, d["means3D"], cams, 3, out=rgb_sh)
-            ev[1].record(side)
-            raster.sh_to_rgb_backward(plan, sh_coef, d["means3D"], cams, 3, g_rgb)
-            ev[2].record(side)
-            side.synchronize()
-            if it >= 2:
-                shf.append(ev[0].elapsed_time(ev[1]))
-                shb.append(ev[1].elapsed_time(ev[2]))
-        sh_ms = (float(np.median(shf)), float(np.median(shb)))
+        sh_ms = tuple(time_enqueued(side, [
+            lambda: raster.sh_to_rgb(plan, sh_coef, d["means3D"], cams, 3, out=rgb_sh),
+            lambda: raster.sh_to_rgb_backward(plan, sh_coef, d["means3D"], cams, 3, g_rgb)]))
         # algorithmic bytes: forward reads 192 B of coefficients + 12 B of mean per Gaussian and
         # writes 12 B per record; backward reads 204 B per Gaussian + 12 B per record and
         # writes 192 + 12 B per Gaussian
