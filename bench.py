@@ -282,11 +282,19 @@ def oracle_setup(scene):
     return _ORACLE_SETUP[key]
 
 
-def oracle_sample_run(scene, budget_s: float, rng_seed: int = 0):
+def oracle_sample_run(scene, budget_s: float, rng_seed: int = 0, threads: int = 0):
     """Times the FP64 oracle's render forward + backward on a bounded sample of the frame's
-    tiles (chosen uniformly at random), sized to about ``budget_s`` seconds of CPU work.
+    tiles (chosen uniformly at random), sized to about ``budget_s`` seconds of CPU work, on
+    all host cores (threads = 0) or the given number of threads.
     Returns (pairs/s, cores, description, measured pairs, seconds)."""
     import oracle
+    if threads:
+        all_threads = oracle.num_threads()
+        oracle.set_threads(threads)
+        try:
+            return oracle_sample_run(scene, budget_s, rng_seed)
+        finally:
+            oracle.set_threads(all_threads)
     g, cam = scene["gaussians"], scene["cameras"][0]
     W, H = cam["W"], cam["H"]
     m2, co, dp, pl, rg = oracle_setup(scene)
@@ -641,8 +649,10 @@ def main_views(args, scene, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and V == 1 and not args.no_cpu_baseline:
         rate, cores, desc, _, _ = oracle_sample_run(scene, args.cpu_seconds)
+        rate1, _, desc1, _, _ = oracle_sample_run(scene, 2.0, threads=1)
         cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc,
-               "cpu_model": cpu_model()}
+               "cpu_model": cpu_model(),
+               "single_thread": {"value": rate1, "unit": "pairs/s", "cores": 1, "sample": desc1}}
     peaks, _ = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     binning = {"ms": bin_ms, "algorithmic_bytes": int(bin_bytes), "GB_s": bin_bytes / (bin_ms / 1e3) / 1e9,
