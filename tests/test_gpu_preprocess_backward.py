@@ -128,3 +128,49 @@ def test_autograd_chain_projection_then_render(R):
         assert e <= GRAD_REL_L2, (k, e)
     assert rel_l2(colors.grad.cpu().numpy(), ref_r["colors"]) <= GRAD_REL_L2
     plan.close()
+
+
+def test_autograd_chain_with_sh_colours(R):
+    """The documented training step: PreprocessFunction, SHFunction (degree 3), binning and
+    the differentiable render under torch autograd.  Every leaf gradient equals the oracle's
+    render backward composed with its SH backward and projection backward (means3D takes
+    both the projection's and the view direction's terms)."""
+    s = scene("cfg1", 0.3)
+    g, cam = s["gaussians"], s["cameras"][0]
+    W, H = cam["W"], cam["H"]
+    N = g["means3D"].shape[0]
+    plan = R.Plan()
+    p = {k: _gpu(v).requires_grad_(True) for k, v in g.items() if k != "colors"}
+    rng = np.random.default_rng(8)
+    sh_np = (rng.normal(size=(N, 16, 3)) * 0.05).astype(np.float32)  # view-dependent, never clamped
+    sh_np[:, 0, :] += 1.0
+    sh = _gpu(sh_np).requires_grad_(True)
+    m2, co, dp, radii = R.PreprocessFunction.apply(p["means3D"], p["log_scales"], p["quats"], p["opacities"], plan,
+                                                   cam, (16, 16))
+    colors = R.SHFunction.apply(sh, p["means3D"], plan, [cam], 3)
+    binning = R.bin_and_sort(plan, m2.detach(), radii, dp.detach(), W, H)
+    color, _, _ = R.render(plan, m2, co, colors, dp, binning, W, H, mode="pixel")
+    m2n, con, dpn, coln = (t.detach().cpu().numpy() for t in (m2, co, dp, colors))
+    radn = radii.cpu().numpy()
+    opl, org = oracle.bin_tiles(m2n, radn, dpn, W, H)
+    ref_f = oracle.render(m2n, con, coln, dpn, opl, org, W, H)
+    gC = rng.normal(size=(3, H, W)).astype(np.float32)
+    gC[:, ref_f["flags"] != 0] = 0
+    (color * _gpu(gC)).sum().backward()
+    ref_r = oracle.render_backward(m2n, con, coln, dpn, opl, org, W, H, gC)
+    ref_p = oracle.preprocess_backward(g["means3D"].astype(np.float64), g["log_scales"].astype(np.float64),
+                                       g["quats"].astype(np.float64), cam, ref_r["means2D"], ref_r["conic"],
+                                       ref_r.get("depths"), radius=radn)
+    Vm = np.asarray(cam["viewmat"], np.float64)
+    campos = -np.linalg.solve(Vm[:3, :3], Vm[:3, 3])
+    # no colour channel near the clamp at 0, so both sides take the same clamp decisions
+    rgb_ref, _ = oracle.sh_to_rgb(sh_np.astype(np.float64), g["means3D"].astype(np.float64), campos, 3)
+    assert rgb_ref.min() > 1e-3
+    d_sh, d_m_sh = oracle.sh_to_rgb_backward(sh_np.astype(np.float64), g["means3D"].astype(np.float64), campos, 3,
+                                             ref_r["colors"].reshape(1, N, 3))
+    assert rel_l2(sh.grad.cpu().numpy(), d_sh) <= GRAD_REL_L2
+    assert rel_l2(p["means3D"].grad.cpu().numpy(), ref_p["means3D"] + d_m_sh) <= GRAD_REL_L2
+    for k, ref in (("log_scales", ref_p["log_scales"]), ("quats", ref_p["quats"]), ("opacities", ref_r["opacity"])):
+        e = rel_l2(p[k].grad.cpu().numpy(), ref)
+        assert e <= GRAD_REL_L2, (k, e)
+    plan.close()
