@@ -231,11 +231,46 @@ def time_enqueued(stream, fns, rounds=6, skip=2):
             for j in range(len(fns))]
 
 
+def _strip_comments(src: str) -> str:
+    """C/C++/CUDA source without its comments (string and character literals kept)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out)
+
+
+def kernel_code_hash(files) -> str:
+    """First 16 hex digits of the SHA-256 of the named csrc files' code, comments removed and
+    whitespace collapsed: an edit of a comment does not retire a profile capture, an edit of
+    the code does."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        src = open(os.path.join(ROOT, "paper_2412_17378_gb300", "csrc", f)).read()
+        h.update(" ".join(_strip_comments(src).split()).encode())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(kernel: str, config: str, tuned: dict):
     """DRAM read + write bytes per launch of the kernel from its committed ncu summary,
     when that capture was taken on this workload and knobs and the kernel's source files
-    are unchanged since (their hash is recorded in the summary); else (None, reason)."""
-    import hashlib
+    are unchanged since (their code hash is recorded in the summary); else (None, reason)."""
     path = PROFILED.get(kernel)
     if path is None or not os.path.exists(os.path.join(ROOT, path)):
         return None, "no capture for this kernel"
@@ -249,11 +284,8 @@ def profiled_traffic(kernel: str, config: str, tuned: dict):
     if "traffic_bytes_per_launch" not in fields:
         return None, "capture has no traffic line"
     digest, files = fields["kernel_source_sha256_16"].split(" ", 1)
-    h = hashlib.sha256()
-    for f in files.strip("()").split(", "):
-        h.update(open(os.path.join(ROOT, "paper_2412_17378_gb300", "csrc", f), "rb").read())
-    if h.hexdigest()[:16] != digest:
-        return None, "kernel sources changed since the capture"
+    if kernel_code_hash(files.strip("()").split(", ")) != digest:
+        return None, "kernel code changed since the capture"
     return int(fields["traffic_bytes_per_launch"]), path
 
 

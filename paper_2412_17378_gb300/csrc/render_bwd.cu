@@ -13,7 +13,7 @@
 // recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final T (no per-pair state is
 // kept by the forward).  All lanes of a warp visit the same list entry at the same step,
 // so the per-Gaussian contributions of the warp's pixels are summed with shuffles and added
-// to a packed accumulator [N][12] with one red.add instruction (warp-aggregated atomics).
+// to a packed accumulator [N][12] with two red.add instructions (warp-aggregated atomics).
 // With gp = dL/dpower2 of a pair, the mean and conic gradients of a Gaussian are sums of
 // gp times (dx, dy, dx^2, dx dy, dy^2) combined with the Gaussian's (constant) conic, so a
 // lane only sums gp, gp dy and gp dy^2 over its pixels (which share dx), forms the five

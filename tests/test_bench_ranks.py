@@ -65,3 +65,22 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     with contextlib.redirect_stdout(out):
         bench.main()
     assert out.getvalue() == ""
+
+
+def test_kernel_code_hash_ignores_comments_only(tmp_path, monkeypatch):
+    """A profile capture stays valid across comment edits of its kernel's sources and is
+    retired by any code edit (bench.kernel_code_hash)."""
+    import bench
+    csrc = tmp_path / "paper_2412_17378_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    f = csrc / "k.cu"
+    f.write_text('// kernel\n__global__ void k(int *p) { p[0] = 1; /* one */ }\nconst char *s = "a // b";\n')
+    h0 = bench.kernel_code_hash(["k.cu"])
+    f.write_text('// the kernel, reworded\n__global__ void k(int *p) {\n    p[0] = 1;  // one\n}\n'
+                 'const char *s = "a // b";\n')
+    assert bench.kernel_code_hash(["k.cu"]) == h0
+    f.write_text('// kernel\n__global__ void k(int *p) { p[0] = 2; /* one */ }\nconst char *s = "a // b";\n')
+    assert bench.kernel_code_hash(["k.cu"]) != h0
+    f.write_text('// kernel\n__global__ void k(int *p) { p[0] = 1; /* one */ }\nconst char *s = "a // c";\n')
+    assert bench.kernel_code_hash(["k.cu"]) != h0  # string literals are code
