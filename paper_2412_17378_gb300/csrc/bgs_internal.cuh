@@ -310,6 +310,12 @@ cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int mode, int
 cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, const ViewTable &vt,
                                  int tile_w, int tile_h, int mode, int heavy_threshold, int gw_pixels,
                                  int pixel_rows, uint32_t *counts, cudaStream_t s);
+// The same list (items, ctrl counts) in one launch of one block, for up to
+// worklist_one_block_max_tiles() tiles (the chain above serves larger grids).
+int worklist_one_block_max_tiles();
+cudaError_t launch_build_worklist(const uint2 *ranges, int num_tiles, const ViewTable &vt, int tile_w, int tile_h,
+                                  int mode, int heavy_threshold, int lpt, int gw_pixels, int pixel_rows,
+                                  uint2 *items, DevCtrl *ctrl, cudaStream_t s);
 // queue of the current list: rewind for another pass / mark exhausted (fault injection)
 cudaError_t launch_rewind_queue(DevCtrl *ctrl, cudaStream_t s);
 cudaError_t launch_exhaust_queue(DevCtrl *ctrl, cudaStream_t s);

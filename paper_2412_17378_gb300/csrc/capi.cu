@@ -259,6 +259,15 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
     BGS_TRY(ensure(p, p->counts, sizeof(uint32_t) * T, s, "counts"));
     BGS_TRY(ensure(p, p->item_off, sizeof(uint32_t) * T, s, "item_off"));
     BGS_TRY(ensure(p, p->items, sizeof(uint2) * max_items, s, "items"));
+    if (T <= bgs::worklist_one_block_max_tiles()) {
+        BGS_CUDA(bgs::launch_build_worklist(rg, T, vt, tw, th, mode, p->desc.heavy_threshold, p->desc.lpt_order, P,
+                                            p->desc.pixel_rows, (uint2 *)p->items.p, p->ctrl, s),
+                 "build_worklist");
+        p->host_launches += 1;
+        p->wl_key = worklist_key(p, ranges, vt, tw, th, mode);
+        p->wl_valid = true;
+        return BGS_OK;
+    }
     uint32_t *key = (uint32_t *)p->tile_key.p, *idx = (uint32_t *)p->tile_idx.p;
     BGS_CUDA(bgs::launch_tile_counts(rg, T, mode, p->desc.heavy_threshold, p->desc.lpt_order, key, idx, s),
              "tile_counts");
