@@ -481,7 +481,7 @@ def main_views(args, scene, rank, world, local):
     if args.knobs:  # fixed knobs from the first step on (profiler runs)
         tuned = dict(apply_knobs(plan, args.knobs), source="--knobs")
 
-    def step(no_sync=True, mode=args.mode):
+    def step(no_sync=True, mode=args.mode, before_forward=None):
         pre = raster.preprocess_batched(plan, d["means3D"], d["log_scales"], d["quats"], d["opacities"], cams,
                                         out=state.get("pre"))
         state["pre"] = pre
@@ -489,6 +489,8 @@ def main_views(args, scene, rank, world, local):
                                                 point_list=state.get("pl"), ranges=state.get("rg"), no_sync=no_sync)
         state["pl"], state["rg"] = pl, rg
         ne = pl.numel() if no_sync else K
+        if before_forward is not None:
+            before_forward()
         outs = raster.render_forward_batched(plan, pre["means2D"], pre["conic_opacity"], d["colors"], pre["depths"],
                                              pl, ne, rg, cams, mode=mode, outs=state.get("outs"))
         state["outs"] = outs
@@ -591,19 +593,51 @@ def main_views(args, scene, rank, world, local):
                                   "tuned": tuned, "note": "--quick profiling run"}), flush=True)
             plan.close()
             return
-        # ---- end to end: inputs from pinned host memory, graph replay, loss read back ----
+        # ---- end to end: inputs from pinned host memory, loss read back, every step ----
+        # One captured graph per step (torch.cuda.graph, whose private memory pool keeps the
+        # loss reduction's workspace alive for the replays): the Gaussian parameters the
+        # projection reads are copied on the step's stream first; colours and targets, read
+        # from the forward on, are copied on a second stream while projection and binning run.
         loss_h = torch.empty(1, pin_memory=True)
         h2d = sum(v.numel() * v.element_size() for v in host.values()) + sum(
             t.numel() * t.element_size() for t in targets_h)
+        copy_s = torch.cuda.Stream(device=dev)
+        ev_fork, ev_join = torch.cuda.Event(), torch.cuda.Event()
 
-        def e2e_step():
+        def e2e_body():
+            ev_fork.record(side)
+            copy_s.wait_event(ev_fork)
+            with torch.cuda.stream(copy_s):
+                d["colors"].copy_(host["colors"], non_blocking=True)
+                for t, th in zip(targets, targets_h):
+                    t.copy_(th, non_blocking=True)
+                ev_join.record(copy_s)
             for k in host:
-                d[k].copy_(host[k], non_blocking=True)
-            for t, th in zip(targets, targets_h):
-                t.copy_(th, non_blocking=True)
-            raster.graph_launch(plan)
+                if k != "colors":
+                    d[k].copy_(host[k], non_blocking=True)
+            step(before_forward=lambda: side.wait_event(ev_join))
             loss = sum((gi["color"] * gi["color"]).sum() for gi in state["gin"]) * 0.5
             loss_h.copy_(loss.reshape(1), non_blocking=True)
+
+        e2e_graph = None
+        try:
+            for _ in range(2):
+                e2e_body()
+            side.synchronize()
+            e2e_graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(e2e_graph, stream=side, capture_error_mode="thread_local"):
+                e2e_body()
+            side.synchronize()
+        except Exception as exc:  # capture refused: time the same body eagerly
+            e2e_graph = None
+            e2e_capture_error = f"{type(exc).__name__}: {exc}"[:200]
+            side.synchronize()
+
+        def e2e_step():
+            if e2e_graph is not None:
+                e2e_graph.replay()
+            else:
+                e2e_body()
             side.synchronize()
 
         for _ in range(3):
@@ -612,6 +646,9 @@ def main_views(args, scene, rank, world, local):
         for _ in range(args.steps):
             e2e_step()
         e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), world, dev) / args.steps
+        e2e_how = ("one CUDA graph per step: H2D copies (colours and targets on a second stream, "
+                   "overlapping projection and binning), the step, the loss and its D2H read"
+                   if e2e_graph is not None else "eager: " + e2e_capture_error)
         # ---- projection (a1) and its backward alone, CUDA events ----
         gr = state["gr"]
         proj_ms = tuple(time_enqueued(side, [
@@ -728,7 +765,7 @@ def main_views(args, scene, rank, world, local):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": whole_job_value(eval_pairs, world, e2e_ms), "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": 4},
+                "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms, "how": e2e_how},
         "gpu_launches": int(launches_per_step * args.steps), "gpu_launches_per_step": int(launches_per_step),
         "gpu_launches_note": "libbgs kernels per graph replay, not counting CUB sort/scan kernels",
         "clocks": clk,
