@@ -84,3 +84,19 @@ def test_kernel_code_hash_ignores_comments_only(tmp_path, monkeypatch):
     assert bench.kernel_code_hash(["k.cu"]) != h0
     f.write_text('// kernel\n__global__ void k(int *p) { p[0] = 1; /* one */ }\nconst char *s = "a // c";\n')
     assert bench.kernel_code_hash(["k.cu"]) != h0  # string literals are code
+
+
+def test_reference_arm_json_line():
+    """--impl reference (the FP64 oracle on the host cores) prints one line with the keys the
+    ratio is computed from, its own e2e (no device copies) and a cpu_baseline of itself."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--config", "cfg1", "--steps", "1",
+                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    L = json.loads(lines[0])
+    assert L["impl"] == "reference" and L["value"] > 0 and L["unit"] == "pairs/s" and L["higher_is_better"] is True
+    assert L["cpu_baseline"]["kind"] == "oracle" and L["cpu_baseline"]["value"] == L["value"]
+    assert L["e2e"] == {"value": L["value"], "unit": L["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
