@@ -20,7 +20,10 @@ from ._lib import MODES, BgsError, check
 __all__ = ["Plan", "camera_struct", "preprocess", "preprocess_backward", "bin_and_sort", "render_forward",
            "render_backward", "PreprocessFunction",
            "render_forward_noalloc",
-           "RenderFunction", "render", "probe_pipe_rates", "debug_exp2", "BgsError", "MODES"]
+           "RenderFunction", "render", "tile_counts", "preprocess_batched", "preprocess_backward_batched",
+           "bin_and_sort_batched", "alloc_view_outputs", "render_forward_batched", "render_backward_batched",
+           "sh_to_rgb", "sh_to_rgb_backward", "SHFunction", "autotune_render", "graph_begin", "graph_end",
+           "graph_launch", "probe_pipe_rates", "debug_exp2", "BgsError", "MODES"]
 
 
 def _stream(device) -> ctypes.c_void_p:
