@@ -481,8 +481,10 @@ def main_views(args, scene, rank, world, local):
     if args.knobs:  # fixed knobs from the first step on (profiler runs)
         tuned = dict(apply_knobs(plan, args.knobs), source="--knobs")
 
-    def step(no_sync=True, mode=args.mode, before_forward=None):
-        pre = raster.preprocess_batched(plan, d["means3D"], d["log_scales"], d["quats"], d["opacities"], cams,
+    def step(no_sync=True, mode=args.mode, before_forward=None, inp=None):
+        # inp: (device inputs, device targets) to read; the resident set by default
+        dd, tgs = inp if inp is not None else (d, targets)
+        pre = raster.preprocess_batched(plan, dd["means3D"], dd["log_scales"], dd["quats"], dd["opacities"], cams,
                                         out=state.get("pre"))
         state["pre"] = pre
         pl, rg, K = raster.bin_and_sort_batched(plan, pre["means2D"], pre["radii"], pre["depths"], cams,
@@ -491,14 +493,14 @@ def main_views(args, scene, rank, world, local):
         ne = pl.numel() if no_sync else K
         if before_forward is not None:
             before_forward()
-        outs = raster.render_forward_batched(plan, pre["means2D"], pre["conic_opacity"], d["colors"], pre["depths"],
+        outs = raster.render_forward_batched(plan, pre["means2D"], pre["conic_opacity"], dd["colors"], pre["depths"],
                                              pl, ne, rg, cams, mode=mode, outs=state.get("outs"))
         state["outs"] = outs
         if "gin" not in state:
             state["gin"] = [dict(color=torch.empty_like(o["color"])) for o in outs]
-        for o, gi, t in zip(outs, state["gin"], targets):
+        for o, gi, t in zip(outs, state["gin"], tgs):
             torch.sub(o["color"], t, out=gi["color"])
-        gr = raster.render_backward_batched(plan, pre["means2D"], pre["conic_opacity"], d["colors"], pre["depths"],
+        gr = raster.render_backward_batched(plan, pre["means2D"], pre["conic_opacity"], dd["colors"], pre["depths"],
                                             pl, ne, rg, cams, outs, state["gin"], mode=mode, out=state.get("gr"))
         state["gr"] = gr
         return K
@@ -602,9 +604,15 @@ def main_views(args, scene, rank, world, local):
         h2d = sum(v.numel() * v.element_size() for v in host.values()) + sum(
             t.numel() * t.element_size() for t in targets_h)
         copy_s = torch.cuda.Stream(device=dev)
+
+        def loss_to_host():
+            loss = sum((gi["color"] * gi["color"]).sum() for gi in state["gin"]) * 0.5
+            loss_h.copy_(loss.reshape(1), non_blocking=True)
+
+        # (1) serial: a step copies its own inputs, then computes from them
         ev_fork, ev_join = torch.cuda.Event(), torch.cuda.Event()
 
-        def e2e_body():
+        def serial_body(i):
             ev_fork.record(side)
             copy_s.wait_event(ev_fork)
             with torch.cuda.stream(copy_s):
@@ -616,39 +624,80 @@ def main_views(args, scene, rank, world, local):
                 if k != "colors":
                     d[k].copy_(host[k], non_blocking=True)
             step(before_forward=lambda: side.wait_event(ev_join))
-            loss = sum((gi["color"] * gi["color"]).sum() for gi in state["gin"]) * 0.5
-            loss_h.copy_(loss.reshape(1), non_blocking=True)
+            loss_to_host()
 
-        e2e_graph = None
-        try:
-            for _ in range(2):
-                e2e_body()
-            side.synchronize()
-            e2e_graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(e2e_graph, stream=side, capture_error_mode="thread_local"):
-                e2e_body()
-            side.synchronize()
-        except Exception as exc:  # capture refused: time the same body eagerly
-            e2e_graph = None
-            e2e_capture_error = f"{type(exc).__name__}: {exc}"[:200]
-            side.synchronize()
+        # (2) pipelined, as a prefetching loader runs: two device input sets; step i computes
+        # from set i % 2 (filled while step i - 1 ran) while a second stream copies step i + 1's
+        # inputs into the other set.  A set is overwritten only after the step that read it
+        # has ended (the steps run in order on one stream).
+        bufs = [(d, targets), ({k: torch.empty_like(v) for k, v in d.items()}, [torch.empty_like(t) for t in targets])]
+        pev = [(torch.cuda.Event(), torch.cuda.Event()) for _ in range(2)]
 
-        def e2e_step():
-            if e2e_graph is not None:
-                e2e_graph.replay()
-            else:
-                e2e_body()
-            side.synchronize()
+        def pipelined_body(i):
+            k = i % 2
+            ev_f, ev_j = pev[k]
+            ev_f.record(side)
+            copy_s.wait_event(ev_f)
+            with torch.cuda.stream(copy_s):
+                nd, nt = bufs[1 - k]
+                for key in host:
+                    nd[key].copy_(host[key], non_blocking=True)
+                for t, th in zip(nt, targets_h):
+                    t.copy_(th, non_blocking=True)
+                ev_j.record(copy_s)
+            step(inp=bufs[k])
+            loss_to_host()
+            side.wait_event(ev_j)
 
-        for _ in range(3):
-            e2e_step()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
-        e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), world, dev) / args.steps
-        e2e_how = ("one CUDA graph per step: H2D copies (colours and targets on a second stream, "
-                   "overlapping projection and binning), the step, the loss and its D2H read"
-                   if e2e_graph is not None else "eager: " + e2e_capture_error)
+        def capture(body, n):
+            """n CUDA graphs of body(0..n-1) (torch.cuda.graph: its private memory pool keeps
+            the loss reduction's workspace alive for the replays); None if capture fails."""
+            try:
+                for i in range(2):
+                    body(i)
+                side.synchronize()
+                graphs = []
+                for i in range(n):
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+                        body(i)
+                    graphs.append(g)
+                side.synchronize()
+                return graphs, None
+            except Exception as exc:  # capture refused: time the same body eagerly
+                side.synchronize()
+                return None, f"{type(exc).__name__}: {exc}"[:200]
+
+        def run_e2e(graphs, body):
+            """ms per step over the timed steps and the last loss; the host reads the loss
+            after every step."""
+            def one(i):
+                if graphs is not None:
+                    graphs[i % len(graphs)].replay()
+                else:
+                    body(i)
+                side.synchronize()
+                return float(loss_h[0])
+
+            for i in range(4):  # an even count keeps the pipelined input sets in phase
+                one(i)
+            t0 = time.perf_counter()
+            for i in range(args.steps):
+                last = one(i)
+            return max_over_ranks(1e3 * (time.perf_counter() - t0), world, dev) / args.steps, last
+
+        g_serial, err_serial = capture(serial_body, 1)
+        serial_ms, loss_serial = run_e2e(g_serial, serial_body)
+        g_pipe, err_pipe = capture(pipelined_body, 2)
+        e2e_ms, loss_pipe = run_e2e(g_pipe, pipelined_body)
+        del g_serial, g_pipe
+        e2e_how = ("two CUDA graphs alternating over two device input sets: each step copies the next step's "
+                   "inputs (pinned host memory, second stream) while it computes from the set the previous step "
+                   "filled, then reads its loss back" if err_pipe is None else "eager, pipelined: " + err_pipe)
+        serial_how = ("one CUDA graph per step: H2D copies (colours and targets on a second stream, overlapping "
+                      "projection and binning), the step, the loss and its D2H read"
+                      if err_serial is None else "eager: " + err_serial)
+        loss_match = abs(loss_pipe - loss_serial) <= 1e-6 * max(1.0, abs(loss_serial))
         # ---- projection (a1) and its backward alone, CUDA events ----
         gr = state["gr"]
         proj_ms = tuple(time_enqueued(side, [
@@ -765,7 +814,10 @@ def main_views(args, scene, rank, world, local):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": whole_job_value(eval_pairs, world, e2e_ms), "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms, "how": e2e_how},
+                "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms, "how": e2e_how,
+                "serial": {"value": whole_job_value(eval_pairs, world, serial_ms), "ms_per_step": serial_ms,
+                           "how": serial_how},
+                "loss": loss_pipe, "loss_matches_serial": bool(loss_match)},
         "gpu_launches": int(launches_per_step * args.steps), "gpu_launches_per_step": int(launches_per_step),
         "gpu_launches_note": "libbgs kernels per graph replay, not counting CUB sort/scan kernels",
         "clocks": clk,

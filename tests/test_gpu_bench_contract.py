@@ -37,5 +37,7 @@ def test_bench_json_line_contract():
     e2e = L["e2e"]
     assert e2e["value"] > 0 and e2e["unit"] == L["unit"] and e2e["h2d_bytes_per_step"] > 0
     assert e2e["d2h_bytes_per_step"] > 0 and e2e["value"] < L["value"]  # copies are inside its timed region
+    # the pipelined end-to-end loop computes what the serial one does
+    assert e2e["serial"]["ms_per_step"] > 0 and e2e["loss_matches_serial"] is True and e2e["loss"] > 0
     clk = L["clocks"]
     assert clk["sm_mhz"] > 0 and clk["sm_max_mhz"] > 0 and isinstance(clk["reasons"], list)
