@@ -31,6 +31,11 @@ struct DevCtrl {
     unsigned long long bin_base;  // binning: first point_list slot of the view being binned
     unsigned int warps_done;    // blocks of the current persistent pass that finished
     unsigned int pad1;
+    // work-list build: items per sort key, each key's first item, blocks done (the counters
+    // return to zero at the end of every build)
+    unsigned int wl_cnt[256];
+    unsigned int wl_off[256];
+    unsigned int wl_done;
 };
 
 // End of a persistent pass, per warp (lane 0), for a block of `warps_per_block` warps whose
@@ -304,24 +309,17 @@ cudaError_t launch_sh(bool backward, long long N, int degree, int stride, const 
 cudaError_t launch_pack(long long N, const float *means2D, const float *conic_opacity, const float *colors,
                         long long n_colors, const float *depths, Rec *recs, cudaStream_t s);
 
-// work list: per-tile keys/counts, then emission in (optionally sorted) tile order
-cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int mode, int heavy_threshold, int lpt,
-                               uint32_t *tile_key, uint32_t *tile_idx, cudaStream_t s);
-cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, const ViewTable &vt,
-                                 int tile_w, int tile_h, int mode, int heavy_threshold, int gw_pixels,
-                                 int pixel_rows, uint32_t *counts, cudaStream_t s);
-// The same list (items, ctrl counts) in one launch of one block, for up to
-// worklist_one_block_max_tiles() tiles (the chain above serves larger grids).
-int worklist_one_block_max_tiles();
-cudaError_t launch_build_worklist(const uint2 *ranges, int num_tiles, const ViewTable &vt, int tile_w, int tile_h,
-                                  int mode, int heavy_threshold, int lpt, int gw_pixels, int pixel_rows,
-                                  uint2 *items, DevCtrl *ctrl, cudaStream_t s);
+// Work list of the persistent kernels, by bucket counting over the tiles' sort keys:
+// k_wl_count gives every tile its place in its key's bucket and (last block) the buckets'
+// first items and the ctrl counts; k_wl_emit writes the items (positions past `capacity`
+// items raise BGS_CHECK_OVERFLOW and are skipped).  The order of tiles within one key is
+// unspecified.
+cudaError_t launch_worklist_buckets(const uint2 *ranges, int num_tiles, const ViewTable &vt, int tile_w, int tile_h,
+                                    int mode, int heavy_threshold, int lpt, int gw_pixels, int pixel_rows,
+                                    uint32_t *slot, uint2 *items, long long capacity, DevCtrl *ctrl, cudaStream_t s);
 // queue of the current list: rewind for another pass / mark exhausted (fault injection)
 cudaError_t launch_rewind_queue(DevCtrl *ctrl, cudaStream_t s);
 cudaError_t launch_exhaust_queue(DevCtrl *ctrl, cudaStream_t s);
-cudaError_t launch_emit_items(const uint32_t *order, const uint32_t *counts, const uint32_t *offsets,
-                              int num_tiles, const uint2 *ranges, int mode, int heavy_threshold, uint2 *items,
-                              DevCtrl *ctrl, cudaStream_t s);
 
 cudaError_t launch_forward_static(const FwdArgs &a, cudaStream_t s);
 cudaError_t launch_forward_gauss(const FwdArgs &a, int grid, cudaStream_t s);

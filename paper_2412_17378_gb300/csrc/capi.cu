@@ -84,7 +84,7 @@ struct bgs_plan {
     Buf bin_h, bin_total, bin_start, bin_rect, bin_mask;  // counting-sort binning
     int smem_optin = 0;
     // render
-    Buf recs, tile_key, tile_key2, tile_idx, tile_idx2, counts, item_off, items, grad_acc, warp_items;
+    Buf recs, tile_idx, items, grad_acc, warp_items;  // tile_idx: each tile's slot in its work-list bucket
     // batched binning: depth keys of every view
     Buf vkey, vkey_sorted;
     // captured CUDA graph
@@ -254,52 +254,13 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
                                                    (tw * th + P - 1) / P);
     const long long max_items = (long long)T * per_tile;
     if (max_items >= (1ll << 31)) return fail(BGS_ERR_INVALID, "too many work items (%lld)", max_items);
-    BGS_TRY(ensure(p, p->tile_key, sizeof(uint32_t) * T, s, "tile_key"));
     BGS_TRY(ensure(p, p->tile_idx, sizeof(uint32_t) * T, s, "tile_idx"));
-    BGS_TRY(ensure(p, p->counts, sizeof(uint32_t) * T, s, "counts"));
-    BGS_TRY(ensure(p, p->item_off, sizeof(uint32_t) * T, s, "item_off"));
     BGS_TRY(ensure(p, p->items, sizeof(uint2) * max_items, s, "items"));
-    if (T <= bgs::worklist_one_block_max_tiles()) {
-        BGS_CUDA(bgs::launch_build_worklist(rg, T, vt, tw, th, mode, p->desc.heavy_threshold, p->desc.lpt_order, P,
-                                            p->desc.pixel_rows, (uint2 *)p->items.p, p->ctrl, s),
-                 "build_worklist");
-        p->host_launches += 1;
-        p->wl_key = worklist_key(p, ranges, vt, tw, th, mode);
-        p->wl_valid = true;
-        return BGS_OK;
-    }
-    uint32_t *key = (uint32_t *)p->tile_key.p, *idx = (uint32_t *)p->tile_idx.p;
-    BGS_CUDA(bgs::launch_tile_counts(rg, T, mode, p->desc.heavy_threshold, p->desc.lpt_order, key, idx, s),
-             "tile_counts");
-    // stable descending sort: Gaussian-wise tiles first (heaviest first when lpt_order is on)
-    BGS_TRY(ensure(p, p->tile_key2, sizeof(uint32_t) * T, s, "tile_key2"));
-    BGS_TRY(ensure(p, p->tile_idx2, sizeof(uint32_t) * T, s, "tile_idx2"));
-    {
-        size_t tmp = 0;
-        const int kbits = p->desc.lpt_order ? 8 : 1;  // 8-bit key: kind bit + log-length bucket
-        BGS_CUDA(cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp, key, (uint32_t *)p->tile_key2.p, idx,
-                                                           (uint32_t *)p->tile_idx2.p, T, 0, kbits, s),
-                 "sort tiles (size)");
-        BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
-        tmp = p->cub_tmp.bytes;
-        BGS_CUDA(cub::DeviceRadixSort::SortPairsDescending(p->cub_tmp.p, tmp, key, (uint32_t *)p->tile_key2.p, idx,
-                                                           (uint32_t *)p->tile_idx2.p, T, 0, kbits, s),
-                 "sort tiles");
-    }
-    const uint32_t *order = (const uint32_t *)p->tile_idx2.p;
-    uint32_t *counts = (uint32_t *)p->counts.p, *off = (uint32_t *)p->item_off.p;
-    BGS_CUDA(bgs::launch_gather_counts(order, T, rg, vt, tw, th, mode, p->desc.heavy_threshold, P,
-                                       p->desc.pixel_rows, counts, s),
-             "gather_counts");
-    size_t tmp = 0;
-    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, counts, off, T, s), "scan items (size)");
-    BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
-    tmp = p->cub_tmp.bytes;
-    BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, counts, off, T, s), "scan items");
-    BGS_CUDA(bgs::launch_emit_items(order, counts, off, T, rg, mode, p->desc.heavy_threshold, (uint2 *)p->items.p,
-                                    p->ctrl, s),
-             "emit_items");
-    p->host_launches += 3;  // tile_counts, gather_counts, emit_items
+    BGS_CUDA(bgs::launch_worklist_buckets(rg, T, vt, tw, th, mode, p->desc.heavy_threshold, p->desc.lpt_order, P,
+                                          p->desc.pixel_rows, (uint32_t *)p->tile_idx.p, (uint2 *)p->items.p,
+                                          (long long)(p->items.bytes / sizeof(uint2)), p->ctrl, s),
+             "build_worklist");
+    p->host_launches += T > 0 ? 2 : 1;
     p->wl_key = worklist_key(p, ranges, vt, tw, th, mode);
     p->wl_valid = true;
     return BGS_OK;
@@ -370,7 +331,7 @@ int bgs_plan_destroy(bgs_plan *p) {
     Buf *bufs[] = {&p->vkey, &p->vkey_sorted, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_rect, &p->bin_mask, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
-                   &p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off, &p->items, &p->warp_items,
+                   &p->tile_idx, &p->items, &p->warp_items,
                    &p->grad_acc};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -443,7 +404,7 @@ size_t bgs_workspace_size(const bgs_plan *p, int64_t N, int64_t K, int64_t T, in
     s += 4 * N + 8 * N;                 // touched, offsets
     s += 8 * K * 2 + 4 * K;             // keys in/out, values in
     s += 48 * N * 2;                    // packed records, gradient accumulators
-    s += 4 * T * 6;                     // tile keys/indices/counts/offsets
+    s += 4 * T;                         // work-list bucket slots
     s += 8 * T * (size_t)std::max(8, (256 + P - 1) / P);  // work items (16x16 tiles)
     s += 64 << 20;                      // CUB temporaries (upper estimate)
     return s;
@@ -502,11 +463,10 @@ int bgs_plan_reserve(bgs_plan *p, int64_t N, int64_t K, int64_t T, int64_t pixel
     BGS_TRY(ensure(p, p->recs, sizeof(bgs::Rec) * N, s, "recs"));
     BGS_TRY(ensure(p, p->grad_acc, sizeof(bgs::Rec) * N, s, "grad_acc"));
     const int P = p->desc.gw_pixels;
-    Buf *t4[] = {&p->tile_key, &p->tile_key2, &p->tile_idx, &p->tile_idx2, &p->counts, &p->item_off};
-    for (Buf *b : t4) BGS_TRY(ensure(p, *b, 4 * T, s, "per-tile"));
+    BGS_TRY(ensure(p, p->tile_idx, 4 * T, s, "per-tile"));
     BGS_TRY(ensure(p, p->items, 8 * T * (size_t)std::max(8, (256 + P - 1) / P), s, "items"));
-    // CUB temporaries: the largest of the depth sort, the N-scan, the tile sort and the work-list sort / scan
-    size_t t[5] = {0, 0, 0, 0, 0};
+    // CUB temporaries: the largest of the depth sort, the N-scan, the tile sort and the tile scan
+    size_t t[4] = {0, 0, 0, 0};
     const int64_t n1 = std::max<int64_t>(N, 1), k1 = std::max<int64_t>(K, 1);
     const int tt = (int)std::max<int64_t>(T, 1);
     uint32_t *u = nullptr;
@@ -514,9 +474,8 @@ int bgs_plan_reserve(bgs_plan *p, int64_t N, int64_t K, int64_t T, int64_t pixel
     BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, t[0], u, u, u, u, n1, 0, 32, s), "sort size");
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, t[1], u, ul, n1, s), "scan size");
     BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, t[2], u, u, u, u, k1, 0, 32, s), "tile sort size");
-    BGS_CUDA(cub::DeviceRadixSort::SortPairsDescending(nullptr, t[3], u, u, u, u, tt, 0, 32, s), "tile order size");
-    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, t[4], u, u, tt, s), "tile scan size");
-    BGS_TRY(ensure(p, p->cub_tmp, *std::max_element(t, t + 5), s, "cub_tmp"));
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, t[3], u, u, tt, s), "tile scan size");
+    BGS_TRY(ensure(p, p->cub_tmp, *std::max_element(t, t + 4), s, "cub_tmp"));
     return BGS_OK;
 }
 
@@ -542,7 +501,7 @@ int bgs_plan_stats(bgs_plan *p, bgs_stats *out, void *stream) {
     DeviceGuard g(p->device);
     cudaStream_t s = (cudaStream_t)stream;
     bgs::DevCtrl c;
-    BGS_CUDA(cudaMemcpyAsync(&c, p->ctrl, sizeof c, cudaMemcpyDeviceToHost, s), "stats copy");
+    BGS_CUDA(cudaMemcpyAsync(&c, p->ctrl, offsetof(bgs::DevCtrl, wl_cnt), cudaMemcpyDeviceToHost, s), "stats copy");
     BGS_CUDA(cudaStreamSynchronize(s), "stats sync");
     out->eval_pairs = c.eval_pairs;
     out->contrib_pairs = c.contrib_pairs;

@@ -10,7 +10,6 @@
 // Tiles of all views of a batched call share one global tile space.
 // Items of heavier tiles are queued first (longest-processing-time order) so the long
 // items start early and the light ones fill the tail.
-#include <cub/block/block_radix_sort.cuh>
 #include <cub/block/block_scan.cuh>
 
 #include "bgs_internal.cuh"
@@ -33,15 +32,10 @@ __device__ __forceinline__ uint32_t tile_items(int t, bool gauss, const ViewTabl
     return (uint32_t)(((vw + iw - 1) / iw) * ((vh + ih - 1) / ih));
 }
 
-__device__ __forceinline__ uint32_t tile_item_count(int t, uint32_t n, const ViewTable &vt, int tile_w, int tile_h,
-                                                    int mode, int heavy_threshold, int gw_pixels, int pixel_rows) {
-    return tile_items(t, tile_is_gauss(mode, heavy_threshold, n), vt, tile_w, tile_h, gw_pixels, pixel_rows);
-}
-
-// Sort key of each tile for the descending stable sort: its kind in the top bit (Gaussian-
+// The list is ordered by a descending 8-bit key per tile: its kind in the top bit (Gaussian-
 // wise tiles first) and, when lpt is on, a log-scale bucket of its list length below it
 // (heaviest first; lengths within ~19% share a bucket): bucket = 4 floor(log2 n) + the two
-// bits after the leading one, + 1 (0 for an empty tile).  One 8-bit radix pass sorts it.
+// bits after the leading one, + 1 (0 for an empty tile).
 __device__ __forceinline__ uint32_t length_bucket(uint32_t n) {
     if (n == 0u) return 0u;
     const int e = 31 - __clz(n);
@@ -49,169 +43,108 @@ __device__ __forceinline__ uint32_t length_bucket(uint32_t n) {
     return min(127u, 4u * (uint32_t)e + m + 1u);
 }
 
-__global__ void k_tile_counts(const uint2 *__restrict__ ranges, int num_tiles, int mode, int heavy_threshold, int lpt,
-                              uint32_t *__restrict__ tile_key, uint32_t *__restrict__ tile_idx) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= num_tiles) return;
-    const uint2 rg = ranges[t];
-    const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
-    const uint32_t kind = tile_is_gauss(mode, heavy_threshold, n) ? 1u : 0u;
-    tile_key[t] = lpt ? (kind << 7) | length_bucket(n) : kind;
-    tile_idx[t] = (uint32_t)t;
+// ---- bucket-counting build (any grid, two launches) ----------------------------------------
+// The key takes at most 256 values, so no sort is needed: a tile's items go to its key's
+// bucket, the buckets in descending key order.  Within a bucket the order of the tiles
+// follows the atomics (it changes only when items start, never what they compute).  At the
+// grids of a frame (thousands to ~10^5 tiles) this is two short launches, where a block
+// radix sort in one block or a device-wide sort chain is bound by latency.
+constexpr int kWlcThreads = 256;  // one thread per key in the offset pass
+
+__device__ __forceinline__ uint32_t wl_sort_key(uint32_t n, bool gauss, int lpt) {
+    const uint32_t kind = gauss ? 1u : 0u;
+    return lpt ? (kind << 7) | length_bucket(n) : kind;
 }
 
-cudaError_t launch_tile_counts(const uint2 *ranges, int num_tiles, int mode, int heavy_threshold, int lpt,
-                               uint32_t *tile_key, uint32_t *tile_idx, cudaStream_t s) {
-    if (num_tiles == 0) return cudaSuccess;
-    k_tile_counts<<<(num_tiles + 255) / 256, 256, 0, s>>>(ranges, num_tiles, mode, heavy_threshold, lpt, tile_key,
-                                                         tile_idx);
-    return cudaGetLastError();
-}
-
-__global__ void k_gather_counts(const uint32_t *__restrict__ order, int num_tiles, const uint2 *__restrict__ ranges,
-                                const ViewTable vt, int tile_w, int tile_h, int mode, int heavy_threshold,
-                                int gw_pixels, int pixel_rows, uint32_t *__restrict__ counts) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= num_tiles) return;
-    const int t = (int)order[i];
-    const uint2 rg = ranges[t];
-    const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
-    counts[i] = tile_item_count(t, n, vt, tile_w, tile_h, mode, heavy_threshold, gw_pixels, pixel_rows);
-}
-
-cudaError_t launch_gather_counts(const uint32_t *order, int num_tiles, const uint2 *ranges, const ViewTable &vt,
-                                 int tile_w, int tile_h, int mode, int heavy_threshold, int gw_pixels,
-                                 int pixel_rows, uint32_t *counts, cudaStream_t s) {
-    if (num_tiles == 0) return cudaSuccess;
-    k_gather_counts<<<(num_tiles + 255) / 256, 256, 0, s>>>(order, num_tiles, ranges, vt, tile_w, tile_h, mode,
-                                                            heavy_threshold, gw_pixels, pixel_rows, counts);
-    return cudaGetLastError();
-}
-
-// One warp per tile writes the tile's items at its offset; the last tile also publishes
-// the total and resets the queue cursor.
-__global__ void k_emit_items(const uint32_t *__restrict__ order, const uint32_t *__restrict__ counts,
-                             const uint32_t *__restrict__ offsets, int num_tiles, const uint2 *__restrict__ ranges,
-                             int mode, int heavy_threshold, uint2 *__restrict__ items, DevCtrl *ctrl) {
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (i >= num_tiles) return;
-    const uint32_t t = order[i];
-    const uint2 rg = ranges[t];
-    const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
-    const uint32_t kind = tile_is_gauss(mode, heavy_threshold, n) ? kKindGauss : 0u;
-    const uint32_t c = counts[i], off = offsets[i];
-    for (uint32_t q = lane; q < c; q += 32) items[off + q] = make_uint2(t, kind | q);
-    if (lane == 0) {
-        // Gaussian-wise tiles come first: the boundary between the kinds sets num_gauss
-        bool next_gauss = false;
-        if (i + 1 < num_tiles) {
-            const uint2 rn = ranges[order[i + 1]];
-            next_gauss = tile_is_gauss(mode, heavy_threshold, rn.y >= rn.x ? rn.y - rn.x : 0u);
-        }
-        uint32_t ng = 0xffffffffu;
-        if (i == 0 && !kind) ng = 0u;
-        if (kind && !next_gauss) ng = off + c;
-        if (ng != 0xffffffffu) {
-            ctrl->num_gauss = ng;
-            ctrl->queue_head = ng;
-            ctrl->queue_head_g = 0u;
-            ctrl->pass_items = 0u;
-            ctrl->warps_done = 0u;
-        }
-        if (i == num_tiles - 1) ctrl->num_items = off + c;
-    }
-}
-
-cudaError_t launch_emit_items(const uint32_t *order, const uint32_t *counts, const uint32_t *offsets, int num_tiles,
-                              const uint2 *ranges, int mode, int heavy_threshold, uint2 *items, DevCtrl *ctrl,
-                              cudaStream_t s) {
-    if (num_tiles == 0) return cudaSuccess;
-    const long long threads = (long long)num_tiles * 32;
-    k_emit_items<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(order, counts, offsets, num_tiles, ranges, mode,
-                                                                   heavy_threshold, items, ctrl);
-    return cudaGetLastError();
-}
-
-// ---- one-block build for grids of up to kWlMaxTiles tiles ---------------------------------
-// The same list as k_tile_counts + the stable descending key sort + k_gather_counts + the
-// exclusive scan + k_emit_items, in one launch: each of 1024 threads loads 8 tiles' ranges,
-// a block radix sort orders the keys (descending, stable: equal keys keep the tile order;
-// padding entries carry key 0 and indices past T, so they sort after every tile), a block
-// scan of the sorted tiles' item counts gives every tile its first item, and each thread
-// writes its tiles' items.  At a few thousand tiles the multi-kernel chain is dominated by
-// launch latency.
-constexpr int kWlThreads = 1024, kWlPerThread = 8;
-constexpr int kWlMaxTiles = kWlThreads * kWlPerThread;
-
-__global__ void __launch_bounds__(kWlThreads) k_build_worklist(const uint2 *__restrict__ ranges, int T,
-                                                                const ViewTable vt, int tile_w, int tile_h, int mode,
-                                                                int heavy_threshold, int lpt, int gw_pixels,
-                                                                int pixel_rows, uint2 *__restrict__ items,
-                                                                DevCtrl *ctrl) {
-    using Sort = cub::BlockRadixSort<uint32_t, kWlThreads, kWlPerThread, uint32_t>;
-    using Scan = cub::BlockScan<uint32_t, kWlThreads>;
-    __shared__ union {
-        typename Sort::TempStorage sort;
-        typename Scan::TempStorage scan;
-    } tmp;
-    __shared__ uint32_t n_gauss;
-    if (threadIdx.x == 0) n_gauss = 0u;
-    uint32_t key[kWlPerThread], tile[kWlPerThread];
-#pragma unroll
-    for (int j = 0; j < kWlPerThread; ++j) {
-        const int t = threadIdx.x * kWlPerThread + j;
-        key[j] = 0u;
-        tile[j] = (uint32_t)t;
-        if (t < T) {
-            const uint2 rg = ranges[t];
-            const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
-            const uint32_t kind = tile_is_gauss(mode, heavy_threshold, n) ? 1u : 0u;
-            key[j] = lpt ? (kind << 7) | length_bucket(n) : kind;
-        }
-    }
-    Sort(tmp.sort).SortDescending(key, tile, 0, lpt ? 8 : 1);
-    __syncthreads();  // tmp is reused by the scan
-    // this thread now holds sorted positions threadIdx.x * kWlPerThread + j
-    uint32_t cnt[kWlPerThread], sum = 0u, gsum = 0u;
-#pragma unroll
-    for (int j = 0; j < kWlPerThread; ++j) {
-        const int r = threadIdx.x * kWlPerThread + j;
-        const bool gauss = (lpt ? key[j] >> 7 : key[j]) != 0u;
-        cnt[j] = r < T ? tile_items((int)tile[j], gauss, vt, tile_w, tile_h, gw_pixels, pixel_rows) : 0u;
-        sum += cnt[j];
-        if (gauss && r < T) gsum += cnt[j];
-    }
-    uint32_t off, total;
-    Scan(tmp.scan).ExclusiveSum(sum, off, total);
-    if (gsum) atomicAdd(&n_gauss, gsum);
-#pragma unroll
-    for (int j = 0; j < kWlPerThread; ++j) {
-        const uint32_t kindbit = (lpt ? key[j] >> 7 : key[j]) != 0u ? kKindGauss : 0u;
-        for (uint32_t q = 0; q < cnt[j]; ++q) items[off + q] = make_uint2(tile[j], kindbit | q);
-        off += cnt[j];
+// Per block: items per key in shared memory (a tile's slot within its block's share is the
+// atomic's old value), then one global atomic per key gives the block's share its place in
+// the key's bucket.  The last block to finish reads the totals (clearing them for the next
+// build), scans them in descending key order into the buckets' first items and publishes
+// the list's item counts and queue cursors.
+__global__ void __launch_bounds__(kWlcThreads) k_wl_count(const uint2 *__restrict__ ranges, int T, const ViewTable vt,
+                                                           int tile_w, int tile_h, int mode, int heavy_threshold,
+                                                           int lpt, int gw_pixels, int pixel_rows,
+                                                           uint32_t *__restrict__ slot, DevCtrl *ctrl) {
+    using Scan = cub::BlockScan<uint32_t, kWlcThreads>;
+    __shared__ typename Scan::TempStorage scan_tmp;
+    __shared__ uint32_t s_cnt[256], s_base[256];
+    __shared__ bool s_last;
+    s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    const int t = blockIdx.x * kWlcThreads + threadIdx.x;
+    uint32_t key = 0u, local = 0u;
+    if (t < T) {
+        const uint2 rg = ranges[t];
+        const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
+        const bool gauss = tile_is_gauss(mode, heavy_threshold, n);
+        key = wl_sort_key(n, gauss, lpt);
+        local = atomicAdd(&s_cnt[key], tile_items(t, gauss, vt, tile_w, tile_h, gw_pixels, pixel_rows));
     }
     __syncthreads();
+    {
+        const uint32_t c = s_cnt[threadIdx.x];
+        if (c) s_base[threadIdx.x] = atomicAdd(&ctrl->wl_cnt[threadIdx.x], c);
+    }
+    __syncthreads();
+    if (t < T) slot[t] = s_base[key] + local;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctrl->wl_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // thread i takes key 255 - i, so the scan runs in descending key order
+    const int k = kWlcThreads - 1 - (int)threadIdx.x;
+    const uint32_t c = atomicExch(&ctrl->wl_cnt[k], 0u);
+    uint32_t off, total;
+    Scan(scan_tmp).ExclusiveSum(c, off, total);
+    ctrl->wl_off[k] = off;
+    // Gaussian-wise keys (kind bit set) are the largest: the first pixel-wise key's offset
+    // is the number of Gaussian-wise items
+    if (k == (lpt ? 127 : 0)) {
+        ctrl->num_gauss = off;
+        ctrl->queue_head = off;
+    }
     if (threadIdx.x == 0) {
-        // Gaussian-wise tiles sort first (the kind is the key's top bit): items [0, num_gauss)
-        const uint32_t ng = n_gauss;
-        ctrl->num_gauss = ng;
-        ctrl->queue_head = ng;
+        ctrl->num_items = total;
         ctrl->queue_head_g = 0u;
         ctrl->pass_items = 0u;
         ctrl->warps_done = 0u;
-        ctrl->num_items = total;
+        ctrl->wl_done = 0u;
     }
 }
 
-int worklist_one_block_max_tiles() { return kWlMaxTiles; }
+// A thread per tile writes the tile's items at its bucket's first item + its slot.
+__global__ void __launch_bounds__(256) k_wl_emit(const uint2 *__restrict__ ranges, int T, const ViewTable vt,
+                                                 int tile_w, int tile_h, int mode, int heavy_threshold, int lpt,
+                                                 int gw_pixels, int pixel_rows, const uint32_t *__restrict__ slot,
+                                                 uint2 *__restrict__ items, long long capacity, DevCtrl *ctrl) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const uint2 rg = ranges[t];
+    const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
+    const bool gauss = tile_is_gauss(mode, heavy_threshold, n);
+    const uint32_t c = tile_items(t, gauss, vt, tile_w, tile_h, gw_pixels, pixel_rows);
+    const long long pos = (long long)ctrl->wl_off[wl_sort_key(n, gauss, lpt)] + slot[t];
+    if (pos + (long long)c > capacity) {
+        raise_check(ctrl, BGS_CHECK_OVERFLOW);
+        return;
+    }
+    const uint32_t kindbit = gauss ? kKindGauss : 0u;
+    for (uint32_t q = 0; q < c; ++q) items[pos + q] = make_uint2((uint32_t)t, kindbit | q);
+}
 
-cudaError_t launch_build_worklist(const uint2 *ranges, int num_tiles, const ViewTable &vt, int tile_w, int tile_h,
-                                  int mode, int heavy_threshold, int lpt, int gw_pixels, int pixel_rows,
-                                  uint2 *items, DevCtrl *ctrl, cudaStream_t s) {
-    if (num_tiles < 0 || num_tiles > kWlMaxTiles) return cudaErrorInvalidValue;
-    k_build_worklist<<<1, kWlThreads, 0, s>>>(ranges, num_tiles, vt, tile_w, tile_h, mode, heavy_threshold, lpt,
-                                              gw_pixels, pixel_rows, items, ctrl);
+cudaError_t launch_worklist_buckets(const uint2 *ranges, int num_tiles, const ViewTable &vt, int tile_w, int tile_h,
+                                    int mode, int heavy_threshold, int lpt, int gw_pixels, int pixel_rows,
+                                    uint32_t *slot, uint2 *items, long long capacity, DevCtrl *ctrl, cudaStream_t s) {
+    if (num_tiles < 0) return cudaErrorInvalidValue;
+    const int blocks = num_tiles > 0 ? (num_tiles + kWlcThreads - 1) / kWlcThreads : 1;
+    k_wl_count<<<blocks, kWlcThreads, 0, s>>>(ranges, num_tiles, vt, tile_w, tile_h, mode, heavy_threshold, lpt,
+                                              gw_pixels, pixel_rows, slot, ctrl);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || num_tiles == 0) return e;
+    k_wl_emit<<<(num_tiles + 255) / 256, 256, 0, s>>>(ranges, num_tiles, vt, tile_w, tile_h, mode, heavy_threshold,
+                                                      lpt, gw_pixels, pixel_rows, slot, items, capacity, ctrl);
     return cudaGetLastError();
 }
 
