@@ -84,7 +84,9 @@ typedef struct bgs_plan_desc {
     int32_t gw_pixels;       /* pixels one Gaussian-wise warp item covers: 1, 2, 4 or 8     */
     int32_t queue_chunk;     /* work items a warp claims per atomicAdd on the queue (>= 1)  */
     int32_t blocks_per_sm;   /* persistent grid = SMs x blocks_per_sm; 0 = max resident     */
-    int32_t lpt_order;       /* 1: work items ordered heaviest tile first; 0: tile order    */
+    int32_t lpt_order;       /* 1: work items ordered heaviest tile first (lengths in ~19 %
+                                log buckets); 0: by kind only.  Gaussian-wise tiles come
+                                first either way; tiles of one bucket come in no set order */
     int32_t device;          /* CUDA device ordinal; -1 = the current device at creation    */
     int32_t pixel_rows;      /* sub-tile of a pixel-wise item: 8 x (4 pixel_rows) pixels, one
                                 warp, pixel_rows pixels per lane (1, 2 or 4)                 */
