@@ -605,9 +605,11 @@ def main_views(args, scene, rank, world, local):
             t.numel() * t.element_size() for t in targets_h)
         copy_s = torch.cuda.Stream(device=dev)
 
-        def loss_to_host():
+        loss_hp = torch.empty(2, pin_memory=True)  # the pipelined steps' losses, by step parity
+
+        def loss_to_host(dst):
             loss = sum((gi["color"] * gi["color"]).sum() for gi in state["gin"]) * 0.5
-            loss_h.copy_(loss.reshape(1), non_blocking=True)
+            dst.copy_(loss.reshape(1), non_blocking=True)
 
         # (1) serial: a step copies its own inputs, then computes from them
         ev_fork, ev_join = torch.cuda.Event(), torch.cuda.Event()
@@ -624,7 +626,7 @@ def main_views(args, scene, rank, world, local):
                 if k != "colors":
                     d[k].copy_(host[k], non_blocking=True)
             step(before_forward=lambda: side.wait_event(ev_join))
-            loss_to_host()
+            loss_to_host(loss_h)
 
         # (2) pipelined, as a prefetching loader runs: two device input sets; step i computes
         # from set i % 2 (filled while step i - 1 ran) while a second stream copies step i + 1's
@@ -646,7 +648,7 @@ def main_views(args, scene, rank, world, local):
                     t.copy_(th, non_blocking=True)
                 ev_j.record(copy_s)
             step(inp=bufs[k])
-            loss_to_host()
+            loss_to_host(loss_hp[k:k + 1])
             side.wait_event(ev_j)
 
         def capture(body, n):
@@ -668,32 +670,49 @@ def main_views(args, scene, rank, world, local):
                 side.synchronize()
                 return None, f"{type(exc).__name__}: {exc}"[:200]
 
-        def run_e2e(graphs, body):
-            """ms per step over the timed steps and the last loss; the host reads the loss
-            after every step."""
-            def one(i):
+        def run_e2e(graphs, body, lag):
+            """ms per step over the timed steps and the last loss.  lag 0: the host waits for
+            each step and reads its loss before launching the next; lag 1: it launches step i,
+            then waits for step i - 1 and reads that step's loss (one step in flight, every
+            loss read inside the timed region)."""
+            done = [torch.cuda.Event(), torch.cuda.Event()]
+
+            def launch(i):
                 if graphs is not None:
                     graphs[i % len(graphs)].replay()
                 else:
                     body(i)
-                side.synchronize()
-                return float(loss_h[0])
+                done[i % 2].record(side)
 
-            for i in range(4):  # an even count keeps the pipelined input sets in phase
-                one(i)
+            def read(i):
+                done[i % 2].synchronize()
+                return float(loss_hp[i % 2]) if lag else float(loss_h[0])
+
+            def run(n):
+                last = None
+                for i in range(n):
+                    launch(i)
+                    if not lag:
+                        last = read(i)
+                    elif i > 0:
+                        last = read(i - 1)
+                return read(n - 1) if lag else last
+
+            run(4)  # an even count keeps the pipelined input sets in phase
+            side.synchronize()
             t0 = time.perf_counter()
-            for i in range(args.steps):
-                last = one(i)
+            last = run(args.steps)
             return max_over_ranks(1e3 * (time.perf_counter() - t0), world, dev) / args.steps, last
 
         g_serial, err_serial = capture(serial_body, 1)
-        serial_ms, loss_serial = run_e2e(g_serial, serial_body)
+        serial_ms, loss_serial = run_e2e(g_serial, serial_body, 0)
         g_pipe, err_pipe = capture(pipelined_body, 2)
-        e2e_ms, loss_pipe = run_e2e(g_pipe, pipelined_body)
+        e2e_ms, loss_pipe = run_e2e(g_pipe, pipelined_body, 1)
         del g_serial, g_pipe
         e2e_how = ("two CUDA graphs alternating over two device input sets: each step copies the next step's "
                    "inputs (pinned host memory, second stream) while it computes from the set the previous step "
-                   "filled, then reads its loss back" if err_pipe is None else "eager, pipelined: " + err_pipe)
+                   "filled, then copies its loss to pinned host memory; the host reads step i's loss after "
+                   "launching step i + 1" if err_pipe is None else "eager, pipelined: " + err_pipe)
         serial_how = ("one CUDA graph per step: H2D copies (colours and targets on a second stream, overlapping "
                       "projection and binning), the step, the loss and its D2H read"
                       if err_serial is None else "eager: " + err_serial)
