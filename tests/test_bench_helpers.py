@@ -1,6 +1,7 @@
 """Host logic of bench.py that shapes the reported numbers, on CPU: the roofline arithmetic
 of the render kernels (the op-count model against closed forms worked by hand), which ncu
-captures may supply the `traffic` figure, and the knob parser."""
+captures may supply the `traffic` figure, the knob parser and the per-tile evaluated-pair
+histogram."""
 import os
 import sys
 
@@ -90,3 +91,33 @@ def test_apply_knobs_parses_the_profiler_command_line():
     kw = bench.apply_knobs(FakePlan(), "pixel_rows=4,heavy_threshold=2147483647,")
     assert kw == seen == {"pixel_rows": 4, "heavy_threshold": 2147483647}
     assert bench.apply_knobs(FakePlan(), "") == {}
+
+
+def test_tile_eval_histogram_on_ragged_views():
+    """Per-tile sums of n_eval over 16x16 tiles of two views with ragged edges, against a brute
+    force over pixel coordinates; the log2 bins count every nonempty tile once."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    rng = np.random.default_rng(5)
+    shapes = [(35, 20), (16, 50)]  # (H, W): 3x2 and 1x4 tiles
+    outs, cams, expect = [], [], []
+    for H, W in shapes:
+        ne = rng.integers(0, 300, (H, W))
+        ne[:16, :16] = 0  # one empty tile per view
+        outs.append({"n_eval": torch.from_numpy(ne.astype(np.int32))})
+        cams.append({"W": W, "H": H})
+        for ty in range((H + 15) // 16):
+            for tx in range((W + 15) // 16):
+                expect.append(sum(int(ne[y, x]) for y in range(ty * 16, min(H, ty * 16 + 16))
+                                  for x in range(tx * 16, min(W, tx * 16 + 16))))
+    expect = np.array(expect, dtype=np.float64)
+    h = bench.tile_eval_histogram(outs, cams)
+    assert h["tiles"] == expect.size == 10
+    assert h["max"] == expect.max() and h["mean"] == pytest.approx(expect.mean())
+    assert h["max_over_mean"] == pytest.approx(expect.max() / expect.mean())
+    assert h["log2_hist"]["0"] == 2
+    assert sum(h["log2_hist"].values()) == expect.size
+    for b, n in h["log2_hist"].items():
+        if b != "0":
+            k = int(b[2:])
+            assert n == int(((expect >= 2 ** k) & (expect < 2 ** (k + 1))).sum())
