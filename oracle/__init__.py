@@ -9,7 +9,8 @@ Each wrapper cites the passage of the paper it follows:
 
 * ``preprocess``   -- Eq. 1-3 (Sec. 2.1): 3D covariance, EWA projection, conic, radius.
 * ``bin_tiles``    -- the per-tile depth-sorted Gaussian lists (``point_list`` of
-  Algorithms 1-6, the "patch" pre-processing of the Sec. 4.3 footnote).
+  Algorithms 1-6, the "patch" pre-processing of the Sec. 4.3 footnote);
+  ``bin_tiles_subset`` builds the same lists for chosen tiles only.
 * ``render``       -- Eq. 4 under Algorithm 5's per-pair rules (Appendix A).
 * ``render_backward`` -- the analytic gradient of ``render`` (not in the paper, which
   only names the backward pass in Sec. 3; derived from Eq. 4 directly).
@@ -76,10 +77,14 @@ def _load():
                                                     P]
             lib.orc_bin.argtypes = [i64, P, P, P, i32, i32, i32, i32, i64, P, P]
             lib.orc_bin.restype = i64
+            lib.orc_depth_order.argtypes = [i64, P, P, P]
+            lib.orc_depth_order.restype = i64
+            lib.orc_bin_subset.argtypes = [i64, P, P, i32, i32, i32, i32, i64, P, P, i64, i64, P, P]
+            lib.orc_bin_subset.restype = i64
             lib.orc_render.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, i64, P,
                                        P, P, P, P, P, P, P, P]
             lib.orc_render_backward.argtypes = [i32, i32, i32, i32, i64, P, P, P, P, P, P, P,
-                                                P, P, P, i64, P, P, P, P, P, P, P]
+                                                P, P, P, i64, P, P, P, P, P, P, P, P]
             lib.orc_sh_to_rgb.argtypes = [i64, i32, i32, i32, P, P, P, P, P]
             lib.orc_sh_to_rgb_backward.argtypes = [i64, i32, i32, i32, P, P, P, P, P, P]
             _lib = lib
@@ -226,6 +231,39 @@ def bin_tiles(means2D, radius, depth, W, H, tile_w=16, tile_h=16, capacity=None)
     return pl[:K].copy(), ranges
 
 
+def depth_order(radius, depth):
+    """The visible Gaussians (radius > 0) in the stable depth order of the per-tile lists
+    (float32 depth bits, ties by index): uint32 [n_visible]."""
+    lib = _load()
+    r, dep = np.ascontiguousarray(radius, np.int32), _f32(depth)
+    order = np.zeros(max(r.size, 1), np.uint32)
+    n = lib.orc_depth_order(r.size, _p(r), _p(dep), _p(order))
+    return order[:n].copy()
+
+
+def bin_tiles_subset(means2D, radius, depth, W, H, tiles, tile_w=16, tile_h=16, order=None):
+    """The lists of ``bin_tiles`` for the listed tile ids only (distinct), one after the
+    other; ranges [T,2] holds their spans and (0, 0) for every other tile.  ``order`` is
+    ``depth_order(radius, depth)`` (computed when not given).
+
+    Returns (point_list uint32 [K], ranges uint32 [T,2])."""
+    lib = _load()
+    m2, r = _f32(means2D), np.ascontiguousarray(radius, np.int32)
+    sel = np.ascontiguousarray(tiles, np.int64)
+    assert np.unique(sel).size == sel.size, "tile ids must be distinct"
+    od = depth_order(r, depth) if order is None else np.ascontiguousarray(order, np.uint32)
+    N = m2.shape[0]
+    T = ((W + tile_w - 1) // tile_w) * ((H + tile_h - 1) // tile_h)
+    ranges = np.zeros((T, 2), np.uint32)
+    args = (N, _p(m2), _p(r), W, H, tile_w, tile_h, sel.size, _p(sel), _p(od), od.size)
+    K = -lib.orc_bin_subset(*args, -1, None, _p(ranges))
+    pl = np.zeros(max(int(K), 1), np.uint32)
+    K = lib.orc_bin_subset(*args, pl.size, _p(pl), _p(ranges))
+    if K < 0:
+        raise ValueError("bin_tiles_subset: list storage")
+    return pl[:K].copy(), ranges
+
+
 def render(means2D, conic_opacity, colors, depth, point_list, ranges, W, H, tile_w=16, tile_h=16,
            bg=(0.0, 0.0, 0.0), pixels=None):
     """Eq. 4 under Algorithm 5 for every pixel (or for the linear pixel ids in
@@ -256,10 +294,12 @@ def render(means2D, conic_opacity, colors, depth, point_list, ranges, W, H, tile
 
 def render_backward(means2D, conic_opacity, colors, depth, point_list, ranges, W, H, dL_dcolor,
                     dL_ddepth=None, dL_dalpha=None, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0),
-                    tiles=None, mask=None):
+                    tiles=None, mask=None, abs_terms=False):
     """Analytic FP64 gradient of ``render`` w.r.t. means2D, conic (a,b,c), opacity,
     colors and depths, summed over pixels.  ``tiles`` restricts the visited tiles,
-    ``mask`` (uint8 [N]) the Gaussians that receive gradients."""
+    ``mask`` (uint8 [N]) the Gaussians that receive gradients.  With ``abs_terms`` the
+    dict also holds ``abs_<name>``: per element, the sum of the absolute values of the
+    per-pair terms of that gradient sum (its condition; used by test tolerances)."""
     lib = _load()
     m2, co, cl, dp = _f64(means2D), _f64(conic_opacity), _f64(colors), _f64(depth)
     N = m2.shape[0]
@@ -275,8 +315,12 @@ def render_backward(means2D, conic_opacity, colors, depth, point_list, ranges, W
     mk = None if mask is None else np.ascontiguousarray(mask, np.uint8)
     out = dict(means2D=np.zeros((N, 2)), conic=np.zeros((N, 3)), opacity=np.zeros(N),
                colors=np.zeros((N, 3)), depths=np.zeros(N))
+    ab = np.zeros((N, 10)) if abs_terms else None
     lib.orc_render_backward(W, H, tile_w, tile_h, N, _p(m2), _p(co), _p(cl), _p(dp), _p(pl), _p(rg),
                             _p(bgv), _p(gC), _p(gD), _p(gA), 0 if tl is None else tl.shape[0],
                             _p(tl), _p(mk), _p(out["means2D"]), _p(out["conic"]),
-                            _p(out["opacity"]), _p(out["colors"]), _p(out["depths"]))
+                            _p(out["opacity"]), _p(out["colors"]), _p(out["depths"]), _p(ab))
+    if abs_terms:
+        out.update(abs_means2D=ab[:, 0:2].copy(), abs_conic=ab[:, 2:5].copy(), abs_opacity=ab[:, 5].copy(),
+                   abs_colors=ab[:, 6:9].copy(), abs_depths=ab[:, 9].copy())
     return out

@@ -412,6 +412,100 @@ int64_t orc_bin(int64_t N, const float *means2D, const int32_t *radius, const fl
     return K;
 }
 
+/* Visible Gaussians (radius > 0) in the stable depth order of the per-tile lists: by float32
+   depth bits, ties by index.  Writes them to order and returns their count. */
+typedef struct {
+    uint32_t depth_bits, idx;
+} orc_key;
+
+static int cmp_key(const void *pa, const void *pb) {
+    const orc_key *a = (const orc_key *)pa, *b = (const orc_key *)pb;
+    if (a->depth_bits != b->depth_bits) return a->depth_bits < b->depth_bits ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx);
+}
+
+int64_t orc_depth_order(int64_t N, const int32_t *radius, const float *depth, uint32_t *order) {
+    int64_t n = 0;
+    for (int64_t i = 0; i < N; ++i) n += radius[i] > 0;
+    orc_key *k = (orc_key *)malloc((size_t)(n > 0 ? n : 1) * sizeof(orc_key));
+    n = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (radius[i] <= 0) continue;
+        memcpy(&k[n].depth_bits, &depth[i], 4);
+        k[n].idx = (uint32_t)i;
+        ++n;
+    }
+    qsort(k, (size_t)n, sizeof(orc_key), cmp_key);
+    for (int64_t j = 0; j < n; ++j) order[j] = k[j].idx;
+    free(k);
+    return n;
+}
+
+/* The same per-tile lists for a subset of the tiles only: `sel` lists ns distinct tile ids;
+   their lists (same tile rectangles, same stable (depth bits, index) order as orc_bin) are
+   written one after the other to point_list, and ranges [T][2] gets their spans (every
+   other tile empty).  Every tile's list is the subsequence of the depth order of all
+   visible Gaussians whose rectangles cover the tile, so the lists are filled by one walk
+   over that order (`order`, from orc_depth_order, n_order entries).  Returns the entry
+   count, or -count when it exceeds capacity (nothing written).  For sampling large frames
+   without materialising every tile's list. */
+int64_t orc_bin_subset(int64_t N, const float *means2D, const int32_t *radius, int W, int H, int tw, int th,
+                       int64_t ns, const int64_t *sel, const uint32_t *order, int64_t n_order, int64_t capacity,
+                       uint32_t *point_list, uint32_t *ranges) {
+    (void)N;
+    const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
+    const int64_t T = (int64_t)tiles_x * tiles_y;
+    for (int64_t t = 0; t < T; ++t) ranges[2 * t] = ranges[2 * t + 1] = 0;
+    /* the selected tiles of every tile row, and each selected tile's fill position */
+    int64_t *row_start = (int64_t *)calloc((size_t)tiles_y + 1, sizeof(int64_t));
+    int32_t *row_x = (int32_t *)malloc((size_t)(ns > 0 ? ns : 1) * sizeof(int32_t));
+    int64_t *cnt = (int64_t *)calloc((size_t)(ns > 0 ? ns : 1), sizeof(int64_t));
+    for (int64_t q = 0; q < ns; ++q) row_start[sel[q] / tiles_x + 1] += 1;
+    for (int y = 0; y < tiles_y; ++y) row_start[y + 1] += row_start[y];
+    int64_t *fill = (int64_t *)malloc((size_t)(tiles_y + 1) * sizeof(int64_t));
+    memcpy(fill, row_start, (size_t)(tiles_y + 1) * sizeof(int64_t));
+    for (int64_t q = 0; q < ns; ++q) row_x[fill[sel[q] / tiles_x]++] = (int32_t)(sel[q] % tiles_x);
+    free(fill);
+    int64_t K = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int64_t j = 0; j < n_order; ++j) {
+            const uint32_t i = order[j];
+            int x0, x1, y0, y1;
+            tile_rect(means2D[2 * i], means2D[2 * i + 1], radius[i], tiles_x, tiles_y, tw, th, &x0, &x1, &y0, &y1);
+            for (int y = y0; y < y1; ++y)
+                for (int64_t q = row_start[y]; q < row_start[y + 1]; ++q) {
+                    const int x = row_x[q];
+                    if (x < x0 || x >= x1) continue;
+                    if (pass == 1) point_list[cnt[q]] = i;
+                    ++cnt[q];
+                }
+        }
+        if (pass == 0) {
+            K = 0;
+            for (int64_t q = 0; q < ns; ++q) K += cnt[q];
+            if (K > capacity || K == 0) break;
+            /* tiles in sel order, each list contiguous */
+            int64_t run = 0;
+            for (int y = 0; y < tiles_y; ++y)
+                for (int64_t q = row_start[y]; q < row_start[y + 1]; ++q) {
+                    const int64_t t = (int64_t)y * tiles_x + row_x[q];
+                    const int64_t c = cnt[q];
+                    cnt[q] = run;
+                    if (c) {
+                        ranges[2 * t] = (uint32_t)run;
+                        ranges[2 * t + 1] = (uint32_t)(run + c);
+                    }
+                    run += c;
+                }
+        }
+    }
+    free(row_start);
+    free(row_x);
+    free(cnt);
+    if (K > capacity) return -K;
+    return K;
+}
+
 /* ------------------------------------------------------------------------- */
 /* One pixel of the forward (Eq. 4 under Algorithm 5's rules).                */
 /* Walks the tile's depth-sorted list front to back:                           */
@@ -520,7 +614,11 @@ void orc_render(int W, int H, int tw, int th, const double *means2D, const doubl
 /* Gradients are summed over pixels.  Only tiles listed in `tiles` (or all    */
 /* tiles when tiles == NULL) are visited, and only Gaussians with mask[g] != 0 */
 /* (or all when mask == NULL) receive gradients.  dL_ddepth / dL_dalpha may be */
-/* NULL (treated as zero).  Outputs are overwritten.                           */
+/* NULL (treated as zero).  Outputs are overwritten.  When abs_terms is not   */
+/* NULL it receives, per Gaussian, the sum of the absolute values of the same */
+/* per-pair terms ([N][10]: mean x, y, conic a, b, c, opacity, colour r, g, b, */
+/* depth) -- the condition of each gradient sum, which bounds the rounding    */
+/* error any summation order of those terms can make (test tolerances only).  */
 /* ------------------------------------------------------------------------- */
 typedef struct {
     uint32_t g;
@@ -533,7 +631,7 @@ void orc_render_backward(int W, int H, int tw, int th, int64_t N, const double *
                          const uint32_t *ranges, const double *bg, const double *dL_dcolor, const double *dL_ddepth,
                          const double *dL_dalpha, int64_t ntiles_sel, const int64_t *tiles, const uint8_t *mask,
                          double *dL_dmeans2D, double *dL_dconic, double *dL_dopacity, double *dL_dcolors,
-                         double *dL_ddepths) {
+                         double *dL_ddepths, double *abs_terms) {
     const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
     const int64_t HW = (int64_t)W * H;
     memset(dL_dmeans2D, 0, sizeof(double) * 2 * N);
@@ -541,6 +639,7 @@ void orc_render_backward(int W, int H, int tw, int th, int64_t N, const double *
     memset(dL_dopacity, 0, sizeof(double) * N);
     memset(dL_dcolors, 0, sizeof(double) * 3 * N);
     memset(dL_ddepths, 0, sizeof(double) * N);
+    if (abs_terms) memset(abs_terms, 0, sizeof(double) * 10 * N);
     const int64_t TT = tiles ? ntiles_sel : (int64_t)tiles_x * tiles_y;
 #pragma omp parallel
     {
@@ -645,6 +744,14 @@ void orc_render_backward(int W, int H, int tw, int th, int64_t N, const double *
                         dL_dcolors[3 * g + 2] += w * gC[2];
 #pragma omp atomic
                         dL_ddepths[g] += w * gD;
+                        if (abs_terms) {
+                            /* magnitudes of the same per-pair terms (the condition of each sum) */
+                            const double t[10] = {gmx, gmy, ga, gb, gc, dLdo, w * gC[0], w * gC[1], w * gC[2], w * gD};
+                            for (int k = 0; k < 10; ++k) {
+#pragma omp atomic
+                                abs_terms[10 * g + k] += fabs(t[k]);
+                            }
+                        }
                     }
                 }
         }

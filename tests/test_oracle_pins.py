@@ -230,6 +230,39 @@ def test_binning_matches_per_tile_lexsort():
         np.testing.assert_array_equal(pl[rg[t, 0]:rg[t, 1]], expect)
 
 
+def test_subset_binning_matches_per_tile_lexsort():
+    """bin_tiles_subset: the lists of the chosen tiles only, each the Gaussians whose
+    rectangle covers the tile ordered by (float32 depth, index) -- numpy's lexsort per
+    tile -- and empty spans for every other tile."""
+    rng = np.random.default_rng(18)
+    n, W, H, tw, th = 400, 100, 70, 16, 8
+    m2 = rng.uniform(-20, 120, (n, 2)).astype(np.float32)
+    r = rng.integers(0, 30, n).astype(np.int32)
+    dp = rng.choice(np.linspace(1, 2, 50), n).astype(np.float32)  # many ties
+    tx, ty = (W + tw - 1) // tw, (H + th - 1) // th
+    sel = rng.permutation(tx * ty)[:13]
+    pl, rg = oracle.bin_tiles_subset(m2, r, dp, W, H, sel, tw, th)
+    order = oracle.depth_order(r, dp)
+    vis = np.nonzero(r > 0)[0]
+    np.testing.assert_array_equal(order, vis[np.lexsort((vis, dp[vis]))])
+    pl2, rg2 = oracle.bin_tiles_subset(m2, r, dp, W, H, sel, tw, th, order=order)
+    np.testing.assert_array_equal(pl2, pl)
+    np.testing.assert_array_equal(rg2, rg)
+    rects = np.array([oracle.tile_rect(float(m2[i, 0]), float(m2[i, 1]), int(r[i]), W, H, tw, th)
+                      for i in range(n)])
+    total = 0
+    for t in range(tx * ty):
+        if t not in set(sel.tolist()):
+            assert rg[t, 0] == rg[t, 1] == 0
+            continue
+        x, y = t % tx, t // tx
+        inc = np.nonzero((r > 0) & (rects[:, 0] <= x) & (x < rects[:, 1]) & (rects[:, 2] <= y) & (y < rects[:, 3]))[0]
+        expect = inc[np.lexsort((inc, dp[inc]))]
+        np.testing.assert_array_equal(pl[rg[t, 0]:rg[t, 1]], expect)
+        total += expect.size
+    assert pl.size == total > 0
+
+
 def test_tile_rect_is_exact_floor():
     """The rectangle bounds are floor((u - r)/tw) and floor((u + r + tw - 1)/tw),
     clamped: compared with exact rational arithmetic away from rounding ties."""
@@ -432,6 +465,27 @@ def test_backward_tile_subset_and_mask(fd_scene):
                                  tiles=np.arange(16), mask=mask)
     np.testing.assert_allclose(sub["opacity"][mask == 1], full["opacity"][mask == 1], rtol=1e-12, atol=1e-15)
     assert (sub["opacity"][mask == 0] == 0).all()
+
+
+def test_backward_term_magnitudes(fd_scene):
+    """The per-element sums of |term| that the gradient tests use as tolerance scales:
+    never below |gradient| (triangle inequality); equal to it when every term has one sign
+    (colour terms alpha T dL/dC under a positive dL/dC); equal to the gradient of
+    L = <|gC|, C> for the colour terms (their weights are the same); and zero exactly
+    where the gradient receives no term."""
+    s = fd_scene
+    g = oracle.render_backward(s["m2"], s["co"], s["cl"], s["dp"], s["pl"], s["rg"], s["W"], s["H"], s["gC"],
+                               s["gD"], s["gA"], bg=s["bg"], abs_terms=True)
+    for k in ("means2D", "conic", "opacity", "colors", "depths"):
+        assert (g["abs_" + k] >= np.abs(g[k]) * (1 - 1e-12) - 1e-300).all(), k
+    pos = oracle.render_backward(s["m2"], s["co"], s["cl"], s["dp"], s["pl"], s["rg"], s["W"], s["H"],
+                                 np.abs(s["gC"]), bg=s["bg"], abs_terms=True)
+    np.testing.assert_allclose(pos["abs_colors"], pos["colors"], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(g["abs_colors"], pos["colors"], rtol=1e-12, atol=0)
+    touched = np.zeros(s["m2"].shape[0], bool)
+    touched[np.unique(s["pl"])] = True
+    assert (g["abs_opacity"][~touched] == 0).all() and (g["opacity"][~touched] == 0).all()
+    assert (g["abs_means2D"] > np.abs(g["means2D"]) * 1.001).any()  # cancellation does occur
 
 
 def test_oracle_regression_snapshot():
