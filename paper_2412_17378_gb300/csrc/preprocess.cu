@@ -40,11 +40,12 @@ struct Proj {
     float qw, qx, qy, qz, qn;      // normalised quaternion and the input's norm
     float R[3][3], s[3];           // rotation, scales
     float M[3][3];                 // R S
-    float S00, S01, S02, S11, S12, S22;  // Sigma = M M^T
     float clx, cly;                // tangents of the centre, clamped
     bool in_x, in_y;               // ... and whether the clamp is inactive
     float J00, J02, J11, J12;      // pinhole Jacobian at the clamped centre
     float T[2][3];                 // J W
+    float Q[2][3];                 // T R
+    float P[2][3];                 // T R S = Q S: Sigma' (before the low-pass) = P P^T
     float c00, c01, c11, det;      // 2D covariance (+ low-pass) and its determinant
 };
 
@@ -69,18 +70,11 @@ __device__ __forceinline__ bool project(const CamDev &cam, const float *__restri
     o.s[0] = expf(log_scales[3 * g]);
     o.s[1] = expf(log_scales[3 * g + 1]);
     o.s[2] = expf(log_scales[3 * g + 2]);
-    // M = R S ; Sigma = M M^T (symmetric, 6 entries)
+    // M = R S (Sigma = M M^T is never formed: Sigma' = T M (T M)^T below)
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int k = 0; k < 3; ++k) o.M[r][k] = o.R[r][k] * o.s[k];
-    const float (&M)[3][3] = o.M;
-    o.S00 = M[0][0] * M[0][0] + M[0][1] * M[0][1] + M[0][2] * M[0][2];
-    o.S01 = M[0][0] * M[1][0] + M[0][1] * M[1][1] + M[0][2] * M[1][2];
-    o.S02 = M[0][0] * M[2][0] + M[0][1] * M[2][1] + M[0][2] * M[2][2];
-    o.S11 = M[1][0] * M[1][0] + M[1][1] * M[1][1] + M[1][2] * M[1][2];
-    o.S12 = M[1][0] * M[2][0] + M[1][1] * M[2][1] + M[1][2] * M[2][2];
-    o.S22 = M[2][0] * M[2][0] + M[2][1] * M[2][1] + M[2][2] * M[2][2];
     // Jacobian of the pinhole map at the tangent-clamped point
     o.iz = 1.f / o.tz;
     const float ux = o.tx * o.iz, uy = o.ty * o.iz;
@@ -101,17 +95,34 @@ __device__ __forceinline__ bool project(const CamDev &cam, const float *__restri
     o.T[1][1] = o.J11 * V[5] + o.J12 * V[9];
     o.T[1][2] = o.J11 * V[6] + o.J12 * V[10];
     const float (&T)[2][3] = o.T;
-    // Sigma' = T Sigma T^T
-    const float U00 = o.S00 * T[0][0] + o.S01 * T[0][1] + o.S02 * T[0][2];  // (Sigma T^T) column 0
-    const float U10 = o.S01 * T[0][0] + o.S11 * T[0][1] + o.S12 * T[0][2];
-    const float U20 = o.S02 * T[0][0] + o.S12 * T[0][1] + o.S22 * T[0][2];
-    const float U01 = o.S00 * T[1][0] + o.S01 * T[1][1] + o.S02 * T[1][2];  // column 1
-    const float U11 = o.S01 * T[1][0] + o.S11 * T[1][1] + o.S12 * T[1][2];
-    const float U21 = o.S02 * T[1][0] + o.S12 * T[1][1] + o.S22 * T[1][2];
-    o.c00 = T[0][0] * U00 + T[0][1] * U10 + T[0][2] * U20 + cam.lowpass;
-    o.c01 = T[0][0] * U01 + T[0][1] * U11 + T[0][2] * U21;
-    o.c11 = T[1][0] * U01 + T[1][1] * U11 + T[1][2] * U21 + cam.lowpass;
-    o.det = o.c00 * o.c11 - o.c01 * o.c01;
+    // Sigma' = T Sigma T^T = P P^T with P = T R S, written without cancellation: the diagonal
+    // entries are sums of squares, and the determinant comes from the Cauchy-Binet formula
+    // det(P P^T) = sum of the squared 2x2 minors of P.  The minors of P = Q S are s_i s_j
+    // times those of Q = T R, i.e. the components of R^T (t0 x t1) for the rows t0, t1 of
+    // T.  So det(Sigma' + l I) = det(P P^T) + l (A + C) + l^2 is a sum of positive terms,
+    // accurate to a few ulp even for long, thin Gaussians (A C - B^2 computed directly
+    // cancels by a factor of up to ~10^4 there).
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            o.Q[r][k] = T[r][0] * o.R[0][k] + T[r][1] * o.R[1][k] + T[r][2] * o.R[2][k];
+            o.P[r][k] = o.Q[r][k] * o.s[k];
+        }
+    const float (&P)[2][3] = o.P;
+    const float A0 = P[0][0] * P[0][0] + P[0][1] * P[0][1] + P[0][2] * P[0][2];
+    const float C0 = P[1][0] * P[1][0] + P[1][1] * P[1][1] + P[1][2] * P[1][2];
+    o.c01 = P[0][0] * P[1][0] + P[0][1] * P[1][1] + P[0][2] * P[1][2];
+    o.c00 = A0 + cam.lowpass;
+    o.c11 = C0 + cam.lowpass;
+    const float n0 = T[0][1] * T[1][2] - T[0][2] * T[1][1];  // t0 x t1
+    const float n1 = T[0][2] * T[1][0] - T[0][0] * T[1][2];
+    const float n2 = T[0][0] * T[1][1] - T[0][1] * T[1][0];
+    const float m0 = o.R[0][0] * n0 + o.R[1][0] * n1 + o.R[2][0] * n2;  // R^T (t0 x t1)
+    const float m1 = o.R[0][1] * n0 + o.R[1][1] * n1 + o.R[2][1] * n2;
+    const float m2 = o.R[0][2] * n0 + o.R[1][2] * n1 + o.R[2][2] * n2;
+    const float d0 = o.s[1] * o.s[2] * m0, d1 = o.s[0] * o.s[2] * m1, d2 = o.s[0] * o.s[1] * m2;
+    o.det = (d0 * d0 + d1 * d1 + d2 * d2) + cam.lowpass * (A0 + C0) + cam.lowpass * cam.lowpass;
     return o.det > 0.f;
 }
 
@@ -137,7 +148,9 @@ __global__ void __launch_bounds__(256) k_preprocess(long long N, const float *__
     depths[rec] = o.tz;
     if (ok) {
         const float mid = 0.5f * (o.c00 + o.c11);
-        const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - o.det));
+        // mid^2 - det = ((A - C) / 2)^2 + B^2, written without cancellation
+        const float hd = 0.5f * (o.c00 - o.c11);
+        const float lam = mid + sqrtf(fmaxf(0.1f, hd * hd + o.c01 * o.c01));
         const int r = (int)ceilf(3.f * sqrtf(lam));
         const float idet = 1.f / o.det;
         const float u = cam.fx * o.tx * o.iz + cam.cx, v = cam.fy * o.ty * o.iz + cam.cy;
@@ -198,26 +211,25 @@ __global__ void __launch_bounds__(256) k_preprocess_backward(long long N, const 
         const float dA = (-C * C * ga + B * C * gb - B * B * gc) * id2;
         const float dC = (-B * B * ga + A * B * gb - A * A * gc) * id2;
         const float hB = (B * C * ga - B * B * gb + A * B * gc) * id2 - 0.5f * gb * idet;  // dL/dB / 2
-        // dL/dSigma = T^T G T (symmetric)
+        // with G = dL/dC2 and Sigma' = P P^T, P = T R S = Q S (no Sigma formed):
+        //   dL/dT = 2 G T Sigma = 2 (G P) M^T,
+        //   dL/dM = 2 T^T G T M, so dL/dlog s_k = 2 s_k^2 q_k^T G q_k (q_k: column k of Q)
+        //   and dL/dR_rk = 2 s_k^2 (T^T G q_k)_r
         const float (&T)[2][3] = o.T;
-        float GT[2][3];  // G T
+        const float (&P)[2][3] = o.P;
+        const float (&Q)[2][3] = o.Q;
+        float GP[2][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            GT[0][k] = dA * T[0][k] + hB * T[1][k];
-            GT[1][k] = hB * T[0][k] + dC * T[1][k];
+            GP[0][k] = dA * P[0][k] + hB * P[1][k];
+            GP[1][k] = hB * P[0][k] + dC * P[1][k];
         }
-        float gS[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) gS[a][b] = T[0][a] * GT[0][b] + T[1][a] * GT[1][b];
-        // dL/dT = 2 G T Sigma
-        const float Sg[3][3] = {{o.S00, o.S01, o.S02}, {o.S01, o.S11, o.S12}, {o.S02, o.S12, o.S22}};
         float gT[2][3];
 #pragma unroll
         for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) gT[r][k] = 2.f * (GT[r][0] * Sg[0][k] + GT[r][1] * Sg[1][k] + GT[r][2] * Sg[2][k]);
+            for (int k = 0; k < 3; ++k)
+                gT[r][k] = 2.f * (GP[r][0] * o.M[k][0] + GP[r][1] * o.M[k][1] + GP[r][2] * o.M[k][2]);
         // T = J W: the four nonzero entries of J
         const float gJ00 = gT[0][0] * V[0] + gT[0][1] * V[1] + gT[0][2] * V[2];
         const float gJ02 = gT[0][0] * V[8] + gT[0][1] * V[9] + gT[0][2] * V[10];
@@ -240,14 +252,11 @@ __global__ void __launch_bounds__(256) k_preprocess_backward(long long N, const 
         float gR[3][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            float gs = 0.f;
+            const float g0 = dA * Q[0][k] + hB * Q[1][k], g1 = hB * Q[0][k] + dC * Q[1][k];  // G q_k
+            const float s2 = 2.f * o.s[k] * o.s[k];
+            gls[k] += s2 * (Q[0][k] * g0 + Q[1][k] * g1);
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const float gM = 2.f * (gS[r][0] * o.M[0][k] + gS[r][1] * o.M[1][k] + gS[r][2] * o.M[2][k]);
-                gs += gM * o.R[r][k];
-                gR[r][k] = gM * o.s[k];
-            }
-            gls[k] += gs * o.s[k];
+            for (int r = 0; r < 3; ++r) gR[r][k] = s2 * (T[0][r] * g0 + T[1][r] * g1);
         }
         // R(q) of the normalised quaternion, then d(q / |q|)
         const float w = o.qw, x = o.qx, y = o.qy, z = o.qz;
