@@ -48,6 +48,10 @@ extern "C" {
 #define BGS_ERR_CUDA (-3)         /* a CUDA runtime call failed                             */
 #define BGS_ERR_DEVICE_CHECK (-4) /* a device-side check tripped (reported by bgs_check)    */
 
+/* Largest point-list length (num_entries, binning's K) any call accepts: list positions
+   stay below 2^32 with room for the kernels' strides of up to 1024 entries. */
+#define BGS_MAX_ENTRIES 4294963200LL /* 2^32 - 4096 */
+
 /* ---- device-check bits (bgs_check / bgs_plan_stats) -------------------------------- */
 #define BGS_CHECK_INDEX 1u        /* point_list held an index >= N                         */
 #define BGS_CHECK_RANGE 2u        /* a tile range pointed past num_entries                 */
@@ -199,18 +203,30 @@ int bgs_preprocess_backward(bgs_plan *plan, int64_t N, const float *means3D, con
    when the tile grid is too large for the counters).  point_list [capacity] receives
    the lists one after the other and ranges [T,2] (T = tiles_x * tiles_y) the half-open
    span of each tile (0,0 if empty).
+   List truncation: when conic_opacity [N,4] (the render's conics and opacities, 16-byte
+   aligned) is given, each tile's list is cut after the depth block of Gaussians at whose
+   end every pixel of the tile is certified to have stopped (Algorithm 5 stops a pixel at
+   the first pair that takes its transmittance below 1e-4; the entries behind that point
+   are never read by the render, forward or backward).  The certificate is a product of
+   factors 1 - a over the tile's Gaussians whose alpha is at least a at every pixel of the
+   tile, at three opacity-relative levels a, below 1e-5; it never cuts an entry that the
+   render's sequential rule visits, so every render output (images, n_contrib, n_eval,
+   gradients) is the same as with the full lists.  Each kept list is a prefix of the full
+   list.  Without conic_opacity (NULL), or on a tile grid whose counters do not fit in
+   shared memory, the lists are complete.
    If the entry count K exceeds `capacity`, *needed (host, nullable) receives K,
    BGS_ERR_CAPACITY is returned and point_list / ranges are unspecified (nothing is
    written past capacity).  *num_rendered (host, nullable) receives K.  This call
    synchronises the stream once, at its end, to read K. */
 int bgs_bin_and_sort(bgs_plan *plan, int64_t N, const float *means2D, const int32_t *radii,
-                     const float *depths, int32_t W, int32_t H, int32_t tile_w, int32_t tile_h,
-                     uint32_t *point_list, int64_t capacity, uint32_t *ranges, int64_t *num_rendered,
-                     int64_t *needed, void *stream);
+                     const float *depths, const float *conic_opacity, int32_t W, int32_t H, int32_t tile_w,
+                     int32_t tile_h, uint32_t *point_list, int64_t capacity, uint32_t *ranges,
+                     int64_t *num_rendered, int64_t *needed, void *stream);
 
 /* ---- a3-a5: render forward -------------------------------------------------------
    Inputs (the paper's XY, CO, F, D, PL): means2D [N,2], conic_opacity [N,4],
-   colors [N,3], depths [N], point_list [num_entries] (values < N), ranges [T,2].
+   colors [N,3], depths [N], point_list [num_entries] (values < N, num_entries <=
+   BGS_MAX_ENTRIES), ranges [T,2].
    bg: host float[3].  Outputs (OC, OD, OA): out_color [3,H,W], out_depth [H,W],
    out_alpha [H,W] (= sum of weights = 1 - final_T), final_T [H,W], n_contrib [H,W]
    (list position + 1 of the last accumulated pair, 0 if none), n_eval [H,W] (nullable:
@@ -282,11 +298,13 @@ int bgs_preprocess_backward_batched(bgs_plan *plan, int32_t V, const bgs_view *v
    BGS_ERR_CAPACITY if the entry count K exceeds capacity (*needed = K) and sets
    *num_rendered = K (both host, nullable).  With BGS_BIN_NO_SYNC it only enqueues work:
    lists are written up to capacity and an overflow raises BGS_CHECK_OVERFLOW.  Each view
-   may have at most (opt-in shared memory per block / 4) tiles. */
+   may have at most (opt-in shared memory per block / 4) tiles.  conic_opacity [V * N, 4]
+   (nullable) truncates the lists as in bgs_bin_and_sort. */
 int bgs_bin_and_sort_batched(bgs_plan *plan, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
-                             const int32_t *radii, const float *depths, int32_t tile_w, int32_t tile_h,
-                             uint32_t *point_list, int64_t capacity, uint32_t *ranges, int32_t flags,
-                             int64_t *num_rendered, int64_t *needed, void *stream);
+                             const int32_t *radii, const float *depths, const float *conic_opacity,
+                             int32_t tile_w, int32_t tile_h, uint32_t *point_list, int64_t capacity,
+                             uint32_t *ranges, int32_t flags, int64_t *num_rendered, int64_t *needed,
+                             void *stream);
 /* Forward (as bgs_render_forward) of all views in one persistent launch; outputs go to
    views[v].out_*.  mode: AUTO, PIXEL or GAUSSIAN. */
 int bgs_render_forward_batched(bgs_plan *plan, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
@@ -378,13 +396,16 @@ int bgs_graph_launch(bgs_plan *plan, void *stream);
    address (no allocation) and should come before any stream capture.  All calls share
    the array: each call resets what must start at zero, consecutive calls on one stream
    are independent, and calls that overlap on the GPU race.  Entries whose index is >= N
-   or whose tile span passes num_entries are rendered transparent.  tile_w must be a
-   multiple of 8 and tile_h of 4. */
+   or whose tile span passes num_entries are rendered transparent and raise
+   BGS_CHECK_INDEX / BGS_CHECK_RANGE in the array.  check_bits (host, nullable): when
+   given, the call waits for its own work on the stream, writes the bits this call raised
+   and returns BGS_ERR_DEVICE_CHECK if any is set; when NULL it only enqueues work and the
+   bits are not reported.  tile_w must be a multiple of 8 and tile_h of 4. */
 int bgs_render_forward_noalloc(int64_t N, const float *means2D, const float *conic_opacity, const float *colors,
                                const float *depths, const uint32_t *point_list, int64_t num_entries,
                                const uint32_t *ranges, int32_t W, int32_t H, int32_t tile_w, int32_t tile_h,
                                const float *bg, float *out_color, float *out_depth, float *out_alpha, float *final_T,
-                               int32_t *n_contrib, int32_t *n_eval, void *stream);
+                               int32_t *n_contrib, int32_t *n_eval, uint32_t *check_bits, void *stream);
 
 /* ---- diagnostics -------------------------------------------------------------------
    Measures sustained per-SM issue rates of the FP32 pipe (FFMA) and of the MUFU ex2

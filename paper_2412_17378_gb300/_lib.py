@@ -118,7 +118,7 @@ def load(build_if_needed: bool = True):
         lib.bgs_plan_kernel_ms.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
         lib.bgs_preprocess.argtypes = [P, i64, P, P, P, P, ctypes.POINTER(Camera), i32, i32, P, P, P, P, P, P]
-        lib.bgs_bin_and_sort.argtypes = [P, i64, P, P, P, i32, i32, i32, i32, P, i64, P,
+        lib.bgs_bin_and_sort.argtypes = [P, i64, P, P, P, P, i32, i32, i32, i32, P, i64, P,
                                          ctypes.POINTER(i64), ctypes.POINTER(i64), P]
         lib.bgs_render_forward.argtypes = [P, i64, P, P, P, P, P, i64, P, i32, i32, i32, i32, P, i32,
                                            P, P, P, P, P, P, P]
@@ -130,7 +130,7 @@ def load(build_if_needed: bool = True):
         lib.bgs_preprocess_batched.argtypes = [P, i32, VP, i64, P, P, P, P, i32, i32, P, P, P, P, P, P]
         lib.bgs_preprocess_backward.argtypes = [P, i64, P, P, P, ctypes.POINTER(Camera), P, P, P, P, P, P, P, P]
         lib.bgs_preprocess_backward_batched.argtypes = [P, i32, VP, i64, P, P, P, P, P, P, P, P, P, P, P]
-        lib.bgs_bin_and_sort_batched.argtypes = [P, i32, VP, i64, P, P, P, i32, i32, P, i64, P, i32,
+        lib.bgs_bin_and_sort_batched.argtypes = [P, i32, VP, i64, P, P, P, P, i32, i32, P, i64, P, i32,
                                                  ctypes.POINTER(i64), ctypes.POINTER(i64), P]
         lib.bgs_render_forward_batched.argtypes = [P, i32, VP, i64, P, P, P, P, P, i64, P, i32, i32, P, i32, P]
         lib.bgs_render_backward_batched.argtypes = [P, i32, VP, i64, P, P, P, P, P, i64, P, i32, i32, P, i32,
@@ -145,7 +145,7 @@ def load(build_if_needed: bool = True):
         lib.bgs_graph_end.argtypes = [P, P]
         lib.bgs_graph_launch.argtypes = [P, P]
         lib.bgs_render_forward_noalloc.argtypes = [i64, P, P, P, P, P, i64, P, i32, i32, i32, i32, P,
-                                                   P, P, P, P, P, P, P]
+                                                   P, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint32), P]
         _lib = lib
         return lib
 

@@ -167,7 +167,12 @@ __device__ __forceinline__ float pair_power2(float4 a, float qc, float px, float
 }
 
 // Transmittance after a pair, T (1 - alpha), as one fused multiply-add T - T alpha (one
-// rounding); every forward kernel takes its stop decision T' < 1e-4 on this value.
+// rounding); the pixel-wise kernels (static, persistent, allocation-free) and the
+// backward's T recovery take their stop decision T' < 1e-4 on this value.  The
+// Gaussian-wise kernel forms T' as T times a warp prefix product of (1 - alpha), which
+// differs from this sequential chain by float32 rounding (a few ulp per 32-entry window);
+// a decision can only flip where T' lies within that rounding of 1e-4, inside the oracle's
+// |T' - 1e-4| < 1e-9 flag window.
 __device__ __forceinline__ float next_T(float T, float al) { return __fmaf_rn(-T, al, T); }
 
 __device__ __forceinline__ float pair_alpha(float power2, float o, float &G) {
@@ -288,13 +293,22 @@ cudaError_t setup_bin_kernels(int tx, int ty);
 cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
                              int W, int H, int tw, int th, uint32_t *Hm, uint4 *rect, uint32_t *masks, int W32,
                              cudaStream_t s);
-cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, uint32_t *total, cudaStream_t s);
+// per tile column: exclusive prefix of H over the blocks and the total; with the credits D
+// (nullable) the column is cut after the block b_sat[t] at which they certify that every
+// pixel of the tile has stopped (b_sat written when bsat is not null)
+cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, const uint16_t *D, uint32_t *total, uint32_t *bsat,
+                               cudaStream_t s);
+// per block and tile: fixed-point credits toward that certificate (k_bin_credit)
+size_t bin_credit_smem(int tx, int ty);
+cudaError_t launch_bin_credit(long long N, int G, int B, const uint4 *rect, const float *means2D,
+                              const float *conic_opacity, int W, int H, int tw, int th, uint16_t *D, cudaStream_t s);
 // ranges of one view's tiles, offset by ctrl->bin_base (the view's first point_list slot)
 cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *total, uint2 *ranges, DevCtrl *ctrl,
                               cudaStream_t s);
 cudaError_t launch_bin_scatter(long long N, int G, int B, int W32, const uint4 *rect, int W, int H, int tw, int th,
                                const uint32_t *Hm, const uint32_t *start, const uint32_t *masks, uint32_t *point_list,
-                               long long capacity, const DevCtrl *ctrl, cudaStream_t s);
+                               long long capacity, const uint32_t *bsat, uint32_t *item_start, int num_sms,
+                               const DevCtrl *ctrl, cudaStream_t s);
 // bin_base += this view's entry count; num_entries = bin_base; raises BGS_CHECK_OVERFLOW past capacity
 cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *total, long long capacity, DevCtrl *ctrl,
                                cudaStream_t s);

@@ -10,18 +10,24 @@
 //                      every sorted position's packed rectangle and Gaussian index (one
 //                      16-byte record) and, per group of 8 x 4 tiles C, a bit mask of the
 //                      block's Gaussians whose rectangle meets C.
+//   1'. k_bin_credit - (optional, when the conics are given) per block and tile, credits
+//                      that certify where every pixel of a tile has stopped (see below).
 //   2. k_bin_colscan - exclusive scan of every column of H over b (in place) and the tile
-//                      totals n[t].
+//                      totals n[t]; with credits, each tile's list is cut after the block
+//                      at which its pixels are certified to have stopped.
 //   3. (CUB) exclusive scan of n -> tile start; k_bin_ranges writes ranges and K.
-//   4. k_bin_scatter - block (b, C), one warp, lane l owns tile l of C and keeps its write
-//                      position start[t] + H[b][t] in a register.  The warp visits the
-//                      Gaussians flagged in the (b, C) mask in depth order; every lane whose
-//                      tile the rectangle covers appends the Gaussian's index.  A lane stages
+//   4. k_bin_scatter - block (chunk of 8 depth blocks b, C), one warp, lane l owns tile l
+//                      of C and keeps its write position start[t] + H[b][t] in a register.
+//                      For each b of the chunk the warp visits the Gaussians flagged in the
+//                      (b, C) mask in depth order; every lane whose tile the rectangle covers
+//                      (and whose list was not cut before b) appends the index.  A lane stages
 //                      its appends in a 16-word ring in shared memory and writes each
 //                      completed 32-byte sector of its run with two 16-byte stores, so the
 //                      point list is written in whole sectors (not one word per request).
 // The result is the stable (depth, index) order per tile.  Traffic is O(B T + K) words
 // instead of the ~26 bytes per entry of a two-pass radix sort of (tile, index) pairs.
+#include <algorithm>
+
 #include "bgs_internal.cuh"
 
 namespace bgs {
@@ -126,33 +132,256 @@ __global__ void __launch_bounds__(256) k_bin_count(long long N, int G, const uin
     }
 }
 
+// ---- list truncation credits -----------------------------------------------------------
+// A pixel stops (Algorithm 5) at the first pair that would take its transmittance below
+// 1e-4, so the entries of a tile's list past the point where every pixel of the tile has
+// stopped are never read, by the forward or the backward.  A Gaussian whose alpha is at
+// least a at every pixel of a tile lowers the transmittance of each of its pixels by a
+// factor <= 1 - a; once the product of such factors over a prefix of the tile's list is
+// below 1e-5 (ten times under the stop threshold, which absorbs float32 rounding of the
+// blend), every pixel of the tile has stopped within that prefix.
+//
+// k_bin_credit computes, per block b of G depth-ordered Gaussians and per tile, the block's
+// sum of floor(256 ln(1 / (1 - a))) (fixed point, 1/256 nat) over its Gaussians and three
+// levels a = max(f o, 1.01 / 255), f = 0.15, 0.45, 0.8: a Gaussian credits a tile with the
+// highest level whose ellipse {d^T Q d <= 2 ln(o / a')} (a' = a (1 + 2^-9)) holds the
+// tile's whole pixel rectangle (widened by half a pixel).  Alpha is log-concave, so that
+// rectangle lies inside the level set iff its corners do, and per tile row the tiles
+// inside form an interval: the intersection of the ellipse's chords at the row's two edges,
+// shrunk by float32 error margins.  Only tiles of the Gaussian's own tile rectangle (where
+// it has list entries) are credited.  Each row interval is one +/- pair of a per-row
+// difference array in shared memory, so a Gaussian costs O(its tile rows), not O(its
+// tiles).  Near-singular conics (det < 1e-5 a c), whose pairs may round to a positive power
+// and be skipped, earn no credit.
+constexpr uint32_t kCreditThr = 2948;  // ceil(256 ln(1e5))
+constexpr int kCrWarps = 16;           // warps of a k_bin_credit block
+
+// Work units: one per (Gaussian, level, tile row inside that level set's vertical extent).
+// Each warp takes 32 Gaussians at a time and spreads their units evenly over its lanes (a
+// few large Gaussians would otherwise hold the warp for tens of rows); the warps of a block
+// share only the credit counters, so they run without block barriers until the final
+// prefix pass.
+__global__ void __launch_bounds__(kCrWarps * 32) k_bin_credit(long long N, int G, const uint4 *__restrict__ rect,
+                                                              const float2 *__restrict__ means2D,
+                                                              const float4 *__restrict__ conic_opacity, int tw,
+                                                              int th, int tx, int ty, uint16_t *__restrict__ D) {
+    extern __shared__ uint32_t w_s[];  // [T] per-row difference arrays of the credits
+    // per warp, per lane's Gaussian: mx, my, qa, qb, det; per level: qa r^2, credit step,
+    // first row; the rectangle's columns
+    __shared__ float s_g[kCrWarps][32][5];
+    __shared__ float s_ar2[kCrWarps][32][3];
+    __shared__ uint32_t s_dw[kCrWarps][32][3];
+    __shared__ int s_j0[kCrWarps][32][3], s_n[kCrWarps][32][3], s_rx[kCrWarps][32][2];
+    __shared__ int s_scan[kCrWarps][32];
+    const int T = tx * ty;
+    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < T; i += kCrWarps * 32) w_s[i] = 0u;
+    __syncthreads();
+    const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
+    // level set {o G >= a'} of a level a = f o, a' = a (1 + 2^-9): r^2 = 2 ln(o / a') is a
+    // constant of f (0.999 shrinks it against float32 rounding); a level clamped at
+    // 1.01 / 255 computes its logarithm
+    const float fr[3] = {0.15f, 0.45f, 0.8f};
+    // ln(1 / (f (1 + 2^-9))) for f = 0.15, 0.45, 0.8, rounded down
+    const float r2c[3] = {2.f * 1.8951687f * 0.999f, 2.f * 0.7965564f * 0.999f, 2.f * 0.2211923f * 0.999f};
+    for (long long c0 = s0 + 32ll * warp; c0 < s1; c0 += 32ll * kCrWarps) {
+        // (1) per Gaussian: its levels, their credits and the rows their level sets span
+        const long long s = c0 + lane;
+        int n[3] = {0, 0, 0};
+        if (s < s1) {
+            const uint4 rc = rect[s];
+            const int rw = (int)(rc.x >> 16), rh = (int)(rc.y >> 16);
+            if (rw > 0 && rh > 0) {
+                const int rx0 = (int)(rc.x & 0xffffu), ry0 = (int)(rc.y & 0xffffu);
+                const float4 co = conic_opacity[rc.z];
+                const float qa = co.x, qb = co.y, qc = co.z, o = co.w;
+                const float det = qa * qc - qb * qb;
+                // r^2 < 2 ln(255 / 1.01) < 11.1 at every level: a Gaussian whose widest level
+                // set cannot hold half a tile in x or y earns nothing
+                if (qa > 0.f && det >= 1e-5f * qa * qc && 11.1f * qc >= det * (0.25f * tw * tw) &&
+                    11.1f * qa >= det * (0.25f * th * th)) {
+                    const float2 m = means2D[rc.z];
+                    float *gp = s_g[warp][lane];
+                    gp[0] = m.x;
+                    gp[1] = m.y;
+                    gp[2] = qa;
+                    gp[3] = qb;
+                    gp[4] = det;
+                    s_rx[warp][lane][0] = rx0;
+                    s_rx[warp][lane][1] = rx0 + rw;
+                    uint32_t wprev = 0u;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float fo = fr[k] * o;
+                        const bool clamped = fo < 1.01f / 255.f;
+                        const float lv = clamped ? 1.01f / 255.f : fo;
+                        const float lv2 = lv * (1.f + 1.f / 512.f);
+                        if (!(o > lv2)) break;
+                        const float r2 = clamped ? 2.f * logf(o / lv2) * 0.999f : r2c[k];
+                        // the level set's half-extents: no tile fits when below half a tile
+                        if (r2 * qc < det * (0.25f * tw * tw) || r2 * qa < det * (0.25f * th * th)) break;
+                        // floor(256 ln(1 / (1 - a))), shrunk by 0.1% (covers __logf's error)
+                        const uint32_t wk = (uint32_t)floorf(-256.f * __logf(1.f - fminf(lv, 0.99f)) * 0.999f);
+                        if (wk <= wprev) continue;
+                        // tile rows whose band [j th - 0.5, (j + 1) th - 0.5] lies within the level
+                        // set's vertical extent my -+ ey, inside the rectangle
+                        const float ey = fminf(sqrtf(r2 * qa / det), 1e8f);
+                        const int j0 = max(ry0, (int)ceilf((fmaxf(m.y - ey, -1e8f) + 0.5f) / (float)th));
+                        const int j1 = min(ry0 + rh, (int)floorf((fminf(m.y + ey, 1e8f) + 0.5f) / (float)th));
+                        if (j1 <= j0) break;  // the higher levels' sets lie inside this one
+                        s_ar2[warp][lane][k] = qa * r2;
+                        s_dw[warp][lane][k] = wk - wprev;
+                        s_j0[warp][lane][k] = j0;
+                        n[k] = j1 - j0;
+                        wprev = wk;
+                    }
+                }
+            }
+        }
+        s_n[warp][lane][0] = n[0];
+        s_n[warp][lane][1] = n[1];
+        s_n[warp][lane][2] = n[2];
+        // (2) inclusive scan of the lanes' unit counts
+        int v = n[0] + n[1] + n[2];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += u;
+        }
+        s_scan[warp][lane] = v;
+        const int total = __shfl_sync(0xffffffffu, v, 31);
+        __syncwarp();
+        // (3) the units: chords of the level-set ellipse at the row's two edges, their
+        // intersection, and one +/- pair of the row's difference array
+        for (int u = lane; u < total; u += 32) {
+            int lo = 0, hi = 31;  // owner: first lane g with scan[g] > u
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_scan[warp][mid] > u) hi = mid;
+                else lo = mid + 1;
+            }
+            const int g = lo;
+            int r = u - (g > 0 ? s_scan[warp][g - 1] : 0);
+            int k = 0;
+            while (r >= s_n[warp][g][k]) r -= s_n[warp][g][k++];
+            const int j = s_j0[warp][g][k] + r;
+            const float *gp = s_g[warp][g];
+            const float mx = gp[0], my = gp[1], qa = gp[2], qb = gp[3], det = gp[4];
+            const float ar2 = s_ar2[warp][g][k];
+            float lo_x = -1e8f, hi_x = 1e8f;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {  // x in ctr -+ half at height y (empty: half < 0)
+                const float dy = (float)((j + e) * th) - 0.5f - my;
+                const float disc = ar2 - det * dy * dy - 1e-6f * ar2;
+                const float half = disc > 0.f ? sqrtf(disc) / qa * 0.999f - 0.02f : -1e30f;
+                const float ctr = mx - qb * dy / qa;
+                lo_x = fmaxf(lo_x, ctr - half);
+                hi_x = fminf(hi_x, ctr + half);
+            }
+            lo_x = fmaxf(lo_x, -1e8f);
+            hi_x = fminf(hi_x, 1e8f);
+            if (!(hi_x - lo_x >= (float)tw)) continue;
+            // tiles i with [i tw - 0.5, i tw + tw - 0.5] inside [lo, hi], within the rectangle
+            const int i0 = max(s_rx[warp][g][0], (int)ceilf((lo_x + 0.5f) / (float)tw));
+            const int i1 = min(s_rx[warp][g][1], (int)floorf((hi_x + 0.5f) / (float)tw));
+            if (i1 <= i0) continue;
+            const uint32_t dw = s_dw[warp][g][k];
+            atomicAdd(&w_s[j * tx + i0], dw);
+            if (i1 < tx) atomicAdd(&w_s[j * tx + i1], 0u - dw);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // prefix along each tile row (warp per row), saturated to 16 bits on the way out
+    for (int y = warp; y < ty; y += kCrWarps) {
+        uint32_t carry = 0u;
+        for (int xb = 0; xb < tx; xb += 32) {
+            const int x = xb + lane;
+            uint32_t v = x < tx ? w_s[y * tx + x] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (x < tx) D[(size_t)b * T + y * tx + x] = (uint16_t)min(v + carry, 65535u);
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+}
+
 // Block (32 tiles) x (32 row groups): per column t, exclusive prefix over b in place, and
-// the column total n[t].
+// the column total n[t].  With the credits D (nullable): the column is cut after the first
+// block b_sat[t] at whose end the credits summed over blocks 0..b reach thr (every pixel of
+// the tile has stopped there); n[t] then counts blocks 0..b_sat only, and blocks past b_sat
+// keep stale values that the scatter never reads.  b_sat = B - 1 when the credits never
+// reach thr (or without D).
 __global__ void __launch_bounds__(1024) k_bin_colscan(int B, int T, uint32_t *__restrict__ H,
-                                                      uint32_t *__restrict__ total) {
-    __shared__ uint32_t part[32][33];
+                                                      const uint16_t *__restrict__ D, uint32_t thr,
+                                                      uint32_t *__restrict__ total, uint32_t *__restrict__ bsat) {
+    __shared__ uint32_t part[32][33], partD[32][33];
+    __shared__ uint32_t s_gsat[32], s_runD[32], s_bsat[32], s_partH[32];
     const int lx = threadIdx.x, ly = threadIdx.y;
     const int t = blockIdx.x * 32 + lx;
     const int rows = (B + 31) / 32;
     const int b0 = ly * rows, b1 = min(B, b0 + rows);
-    uint32_t sum = 0;
+    uint32_t sum = 0, sumD = 0;
     if (t < T)
-        for (int b = b0; b < b1; ++b) sum += H[(size_t)b * T + t];
+        for (int b = b0; b < b1; ++b) {
+            sum += H[(size_t)b * T + t];
+            if (D) sumD = min(sumD + (uint32_t)D[(size_t)b * T + t], 0x7fffffffu);
+        }
     part[ly][lx] = sum;
+    partD[ly][lx] = sumD;
+    __syncthreads();
+    if (ly == 0) {  // the row group in which the credits reach thr (32: none)
+        uint32_t run = 0;
+        int gsat = 32;
+        if (D)
+            for (int gq = 0; gq < 32; ++gq) {
+                if (run + partD[gq][lx] >= thr) {
+                    gsat = gq;
+                    break;
+                }
+                run += partD[gq][lx];
+            }
+        s_gsat[lx] = (uint32_t)gsat;
+        s_runD[lx] = run;
+        s_bsat[lx] = (uint32_t)(B - 1);
+        s_partH[lx] = 0u;
+    }
+    __syncthreads();
+    const int gsat = (int)s_gsat[lx];
+    if (ly == gsat && t < T) {  // the block inside that group, and the counts up to it
+        uint32_t run = s_runD[lx], ph = 0;
+        int bs = b1 - 1;
+        for (int b = b0; b < b1; ++b) {
+            ph += H[(size_t)b * T + t];
+            run += D[(size_t)b * T + t];
+            if (run >= thr) {
+                bs = b;
+                break;
+            }
+        }
+        s_bsat[lx] = (uint32_t)bs;
+        s_partH[lx] = ph;
+    }
     __syncthreads();
     if (ly == 0) {
         uint32_t run = 0;
-        for (int gq = 0; gq < 32; ++gq) {
+        for (int gq = 0; gq < 32 && gq <= gsat; ++gq) {
             const uint32_t v = part[gq][lx];
             part[gq][lx] = run;
-            run += v;
+            run += (gq == gsat) ? s_partH[lx] : v;
         }
-        if (t < T) total[t] = run;
+        if (t < T) {
+            total[t] = run;
+            if (bsat) bsat[t] = s_bsat[lx];
+        }
     }
     __syncthreads();
-    if (t < T) {
+    if (t < T && ly <= gsat) {
+        const int bend = min(b1, (int)s_bsat[lx] + 1);
         uint32_t off = part[ly][lx];
-        for (int b = b0; b < b1; ++b) {
+        for (int b = b0; b < bend; ++b) {
             const uint32_t h = H[(size_t)b * T + t];
             H[(size_t)b * T + t] = off;
             off += h;
@@ -185,7 +414,8 @@ __global__ void k_bin_advance(int T, const uint32_t *__restrict__ total, long lo
         const unsigned long long next = ctrl->bin_base + k;
         ctrl->bin_base = next;
         ctrl->num_entries = next;
-        if ((long long)next > capacity || next >= 0xffffffffull) atomicOr(&ctrl->check_bits, (unsigned)BGS_CHECK_OVERFLOW);
+        if ((long long)next > capacity || (long long)next > BGS_MAX_ENTRIES)
+            atomicOr(&ctrl->check_bits, (unsigned)BGS_CHECK_OVERFLOW);
     }
 }
 
@@ -213,10 +443,55 @@ __device__ __forceinline__ void flush_sector(const uint32_t *ring_s, int lane, u
 // Single-warp blocks: a block's shared memory is released as soon as its warp is done
 // (blocks of several warps hold it until the slowest one finishes, and reached fewer
 // resident warps).
+// Work items of the scatter: the (depth block b, tile group C) pairs with b at most the last
+// block any tile of C keeps (every pair without truncation), numbered C-major.  One block:
+// item_start[C] = exclusive prefix of min(B, max over C's tiles of b_sat + 1), and
+// item_start[nC] = the item count.
+__global__ void __launch_bounds__(1024) k_bin_items(int nC, int tx, int ty, int B, const uint32_t *__restrict__ bsat,
+                                                    uint32_t *__restrict__ item_start) {
+    __shared__ uint32_t part[1024];
+    const int tid = threadIdx.x;
+    const int per = (nC + 1023) / 1024;
+    const int c0 = min(nC, tid * per), c1 = min(nC, c0 + per);
+    const int ncx = (tx + kCbW - 1) / kCbW;
+    uint32_t local = 0;
+    for (int C = c0; C < c1; ++C) {
+        uint32_t n = (uint32_t)B;
+        if (bsat) {
+            uint32_t gmax = 0;
+            const int gx0 = (C % ncx) * kCbW, gy0 = (C / ncx) * kCbH;
+            for (int y = gy0; y < min(ty, gy0 + kCbH); ++y)
+                for (int x = gx0; x < min(tx, gx0 + kCbW); ++x) gmax = max(gmax, bsat[(size_t)y * tx + x]);
+            n = min((uint32_t)B, gmax + 1u);
+        }
+        item_start[C] = n;  // the count, turned into the offset below
+        local += n;
+    }
+    part[tid] = local;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan of the threads' sums
+        const uint32_t v = tid >= off ? part[tid - off] : 0u;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[tid] - local;
+    for (int C = c0; C < c1; ++C) {
+        const uint32_t n = item_start[C];
+        item_start[C] = run;
+        run += n;
+    }
+    if (tid == 1023) item_start[nC] = part[1023];
+}
+
+// Persistent: the blocks stride over the work items of k_bin_items; item -> (C, b).  Block
+// (b, C): one warp, lane l owns tile l of C; lanes whose list ends before b append nothing.
 __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const uint4 *__restrict__ rect, int tx, int ty,
                                                     const uint32_t *__restrict__ H, const uint32_t *__restrict__ start,
                                                     const uint32_t *__restrict__ masks,
                                                     uint32_t *__restrict__ point_list, uint32_t capacity, int vec_ok,
+                                                    const uint32_t *__restrict__ bsat,
+                                                    const uint32_t *__restrict__ item_start, int nC,
                                                     const DevCtrl *ctrl) {
     // per flagged Gaussian of the pass: (lanes whose tile its rectangle covers, Gaussian
     // index), .y holding its sorted position until the hit is known; and the lanes' 16-word
@@ -224,86 +499,112 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const u
     // (the per-SM block limit) fit an SM.
     __shared__ uint2 hit_s[512];
     __shared__ uint32_t ring_s[16 * 32];
-    const int b = blockIdx.x, cx = blockIdx.y, cy = blockIdx.z, lane = threadIdx.x;
-    const int nC = ((tx + kCbW - 1) / kCbW) * ((ty + kCbH - 1) / kCbH);
-    const int C = cy * ((tx + kCbW - 1) / kCbW) + cx;
-    const int gx0 = cx * kCbW, gy0 = cy * kCbH;
-    const int ltx = gx0 + (lane % kCbW), lty = gy0 + (lane / kCbW);
-    const bool own = ltx < tx && lty < ty;
-    const unsigned own_mask = __ballot_sync(0xffffffffu, own);
-    const size_t t = (size_t)lty * tx + ltx;
+    const int lane = threadIdx.x;
+    const int ncx = (tx + kCbW - 1) / kCbW;
+    const uint32_t n_items = item_start[nC];
     const uint32_t base = (uint32_t)ctrl->bin_base;
-    uint32_t pos = own ? base + start[t] + H[(size_t)b * tx * ty + t] : 0u;
-    const uint32_t run0 = pos;
-    uint32_t done = pos & ~7u;  // positions below done are written (or precede the run)
     uint32_t *ring = ring_s + lane;
-    const uint32_t *mk = masks + ((size_t)b * nC + C) * W32;
-    const uint32_t s0 = (uint32_t)b * G;
-    for (int wb = 0; wb < W32; wb += 16) {  // 512 Gaussians per pass
-        uint32_t word = lane < 16 ? mk[wb + lane] : 0u;
-        const uint32_t cnt = (uint32_t)__popc(word);
-        uint32_t incl = cnt;
-        for (int o = 1; o < 16; o <<= 1) {
-            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
+    for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        int lo = 0, hi = nC - 1;  // C: the last group with item_start[C] <= it
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (item_start[mid] <= it) lo = mid;
+            else hi = mid - 1;
         }
-        const int total = (int)__shfl_sync(0xffffffffu, incl, 15);
-        if (total == 0) continue;
-        // compact the flagged positions in depth order (word by word, bit by bit)
-        uint32_t off = incl - cnt;
-        while (word) {
-            const int bit = __ffs(word) - 1;
-            word &= word - 1u;
-            hit_s[off++].y = s0 + 32u * (uint32_t)(wb + lane) + (uint32_t)bit;
-        }
-        __syncwarp();
-        // per flagged Gaussian: the lanes whose tile its rectangle covers (a nonempty
-        // rectangle meeting the group: the masks flag no other)
-        for (int k = lane; k < total; k += 32) {
-            const uint4 rc = rect[hit_s[k].y];
-            const int x0 = (int)(rc.x & 0xffffu) - gx0, x1 = x0 + (int)(rc.x >> 16);
-            const int y0 = (int)(rc.y & 0xffffu) - gy0, y1 = y0 + (int)(rc.y >> 16);
-            const uint32_t lx0 = (uint32_t)max(x0, 0), lx1 = (uint32_t)min(x1, kCbW);
-            const uint32_t ly0 = (uint32_t)max(y0, 0), ly1 = (uint32_t)min(y1, kCbH);
-            const uint32_t cols = ((1u << lx1) - 1u) ^ ((1u << lx0) - 1u);
-            const uint32_t rows = (ly1 >= 4u ? 0xffffffffu : (1u << (8u * ly1)) - 1u) ^ ((1u << (8u * ly0)) - 1u);
-            hit_s[k] = make_uint2(rows & (cols * 0x01010101u) & own_mask, rc.z);
-        }
-        __syncwarp();
-        // depth order, 8 visits at a time, then the remaining total % 8 one by one; at most 8
-        // appends between two checks: at most one newly completed sector, and no ring slot
-        // overwritten before it is written out
-        const int full = total & ~7;
-        for (int k0 = 0; k0 < full; k0 += 8) {
+        const int C = lo;
+        const int b = (int)(it - item_start[C]);
+        const int gx0 = (C % ncx) * kCbW, gy0 = (C / ncx) * kCbH;
+        const int ltx = gx0 + (lane % kCbW), lty = gy0 + (lane / kCbW);
+        const size_t t = (size_t)lty * tx + ltx;
+        // a lane whose tile's list was cut before block b appends nothing
+        const bool own = ltx < tx && lty < ty && (bsat == nullptr || (uint32_t)b <= bsat[t]);
+        const unsigned own_mask = __ballot_sync(0xffffffffu, own);
+        if (own_mask == 0u) continue;
+        uint32_t pos = own ? base + start[t] + H[(size_t)b * tx * ty + t] : 0u;
+        const uint32_t run0 = pos;
+        uint32_t done = pos & ~7u;  // positions below done are written (or precede the run)
+        const uint32_t *mk = masks + ((size_t)b * nC + C) * W32;
+        const uint32_t s0 = (uint32_t)b * G;
+        for (int wb = 0; wb < W32; wb += 16) {  // 512 Gaussians per pass
+            uint32_t word = lane < 16 ? mk[wb + lane] : 0u;
+            const uint32_t cnt = (uint32_t)__popc(word);
+            uint32_t incl = cnt;
+            for (int o = 1; o < 16; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            int total = (int)__shfl_sync(0xffffffffu, incl, 15);
+            if (total == 0) continue;
+            // compact the flagged positions in depth order (word by word, bit by bit)
+            uint32_t off = incl - cnt;
+            while (word) {
+                const int bit = __ffs(word) - 1;
+                word &= word - 1u;
+                hit_s[off++].y = s0 + 32u * (uint32_t)(wb + lane) + (uint32_t)bit;
+            }
+            __syncwarp();
+            // per flagged Gaussian: the lanes whose tile its rectangle covers (a nonempty
+            // rectangle meeting the group: the masks flag no other), among the lanes whose
+            // list is still open; hits that reach no such lane are dropped (in place: a hit
+            // moves to a slot at or before its own, after the warp has read the round)
+            int kept = 0;
+            for (int k0 = 0; k0 < total; k0 += 32) {
+                const int k = k0 + lane;
+                uint32_t cover = 0u, idx = 0u;
+                if (k < total) {
+                    const uint4 rc = rect[hit_s[k].y];
+                    const int x0 = (int)(rc.x & 0xffffu) - gx0, x1 = x0 + (int)(rc.x >> 16);
+                    const int y0 = (int)(rc.y & 0xffffu) - gy0, y1 = y0 + (int)(rc.y >> 16);
+                    const uint32_t lx0 = (uint32_t)max(x0, 0), lx1 = (uint32_t)min(x1, kCbW);
+                    const uint32_t ly0 = (uint32_t)max(y0, 0), ly1 = (uint32_t)min(y1, kCbH);
+                    const uint32_t cols = ((1u << lx1) - 1u) ^ ((1u << lx0) - 1u);
+                    const uint32_t rows =
+                        (ly1 >= 4u ? 0xffffffffu : (1u << (8u * ly1)) - 1u) ^ ((1u << (8u * ly0)) - 1u);
+                    cover = rows & (cols * 0x01010101u) & own_mask;
+                    idx = rc.z;
+                }
+                const unsigned keep = __ballot_sync(0xffffffffu, cover != 0u);
+                if (cover != 0u) hit_s[kept + __popc(keep & ((1u << lane) - 1u))] = make_uint2(cover, idx);
+                kept += __popc(keep);
+            }
+            __syncwarp();
+            total = kept;
+            // depth order, 8 visits at a time, then the remaining total % 8 one by one; at most 8
+            // appends between two checks: at most one newly completed sector, and no ring slot
+            // overwritten before it is written out
+            const int full = total & ~7;
+            for (int k0 = 0; k0 < full; k0 += 8) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                // branch-free: the slot of position pos is free (pos - done < 16), so every
-                // lane writes it and only the lanes whose tile is covered advance past it
-                const uint2 e = hit_s[k0 + j];
-                ring[(pos & 15u) << 5] = e.y;
-                pos += (e.x >> lane) & 1u;
+                for (int j = 0; j < 8; ++j) {
+                    // branch-free: the slot of position pos is free (pos - done < 16), so every
+                    // lane writes it and only the lanes whose tile is covered advance past it
+                    const uint2 e = hit_s[k0 + j];
+                    ring[(pos & 15u) << 5] = e.y;
+                    pos += (e.x >> lane) & 1u;
+                }
+                if (done + 8u <= pos) {
+                    flush_sector(ring_s, lane, done, run0, point_list, capacity, vec_ok != 0);
+                    done += 8u;
+                }
             }
-            if (done + 8u <= pos) {
-                flush_sector(ring_s, lane, done, run0, point_list, capacity, vec_ok != 0);
-                done += 8u;
+            if (full < total) {
+                for (int k = full; k < total; ++k) {
+                    const uint2 e = hit_s[k];
+                    ring[(pos & 15u) << 5] = e.y;
+                    pos += (e.x >> lane) & 1u;
+                }
+                if (done + 8u <= pos) {
+                    flush_sector(ring_s, lane, done, run0, point_list, capacity, vec_ok != 0);
+                    done += 8u;
+                }
             }
+            __syncwarp();
         }
-        if (full < total) {
-            for (int k = full; k < total; ++k) {
-                const uint2 e = hit_s[k];
-                ring[(pos & 15u) << 5] = e.y;
-                pos += (e.x >> lane) & 1u;
-            }
-            if (done + 8u <= pos) {
-                flush_sector(ring_s, lane, done, run0, point_list, capacity, vec_ok != 0);
-                done += 8u;
-            }
-        }
+        // the last, partial sector
+        for (uint32_t p = done; p < pos; ++p)
+            if (p >= run0 && p < capacity) point_list[p] = ring[(p & 15u) << 5];
         __syncwarp();
     }
-    // the last, partial sector
-    for (uint32_t p = done; p < pos; ++p)
-        if (p >= run0 && p < capacity) point_list[p] = ring[(p & 15u) << 5];
 }
 
 size_t bin_count_smem(int tx, int ty) {
@@ -328,8 +629,27 @@ cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, uint32_t *total, cudaStream_t s) {
-    k_bin_colscan<<<(T + 31) / 32, dim3(32, 32), 0, s>>>(B, T, Hm, total);
+cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, const uint16_t *D, uint32_t *total, uint32_t *bsat,
+                               cudaStream_t s) {
+    k_bin_colscan<<<(T + 31) / 32, dim3(32, 32), 0, s>>>(B, T, Hm, D, kCreditThr, total, bsat);
+    return cudaGetLastError();
+}
+
+// dynamic shared memory of k_bin_credit (one credit counter per tile)
+static size_t bin_credit_dyn_smem(int tx, int ty) { return sizeof(uint32_t) * (size_t)tx * ty; }
+// all of k_bin_credit's shared memory: the counters and ~41 KB of per-warp unit tables
+size_t bin_credit_smem(int tx, int ty) { return bin_credit_dyn_smem(tx, ty) + 44 * 1024; }
+
+cudaError_t launch_bin_credit(long long N, int G, int B, const uint4 *rect, const float *means2D,
+                              const float *conic_opacity, int W, int H, int tw, int th, uint16_t *D, cudaStream_t s) {
+    const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
+    const size_t smem = bin_credit_dyn_smem(tx, ty);
+    if (smem > 24 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_bin_credit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_bin_credit<<<B, kCrWarps * 32, smem, s>>>(N, G, rect, reinterpret_cast<const float2 *>(means2D),
+                                      reinterpret_cast<const float4 *>(conic_opacity), tw, th, tx, ty, D);
     return cudaGetLastError();
 }
 
@@ -348,14 +668,20 @@ cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *tot
 
 cudaError_t launch_bin_scatter(long long N, int G, int B, int W32, const uint4 *rect, int W, int H, int tw, int th,
                                const uint32_t *Hm, const uint32_t *start, const uint32_t *masks, uint32_t *point_list,
-                               long long capacity, const DevCtrl *ctrl, cudaStream_t s) {
+                               long long capacity, const uint32_t *bsat, uint32_t *item_start, int num_sms,
+                               const DevCtrl *ctrl, cudaStream_t s) {
     (void)N;
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
+    const int nC = bin_mask_groups(tx, ty);
     // indices, sorted positions and list slots are < 2^32 (checked by the callers)
-    const uint32_t cap = capacity >= 0xffffffffll ? 0xffffffffu : (uint32_t)capacity;
+    const uint32_t cap = capacity > BGS_MAX_ENTRIES ? (uint32_t)BGS_MAX_ENTRIES : (uint32_t)capacity;
     const int vec_ok = (reinterpret_cast<uintptr_t>(point_list) & 31u) == 0u;
-    const dim3 grid(B, (tx + kCbW - 1) / kCbW, (ty + kCbH - 1) / kCbH);
-    k_bin_scatter<<<grid, 32, 0, s>>>((uint32_t)G, W32, rect, tx, ty, Hm, start, masks, point_list, cap, vec_ok, ctrl);
+    k_bin_items<<<1, 1024, 0, s>>>(nC, tx, ty, B, bsat, item_start);
+    // persistent grid: 32 single-warp blocks per SM (the per-SM block limit), or fewer items
+    const long long grid = std::min<long long>((long long)num_sms * 32, (long long)B * nC);
+    k_bin_scatter<<<(unsigned)std::max<long long>(1, grid), 32, 0, s>>>((uint32_t)G, W32, rect, tx, ty, Hm, start,
+                                                                         masks, point_list, cap, vec_ok, bsat,
+                                                                         item_start, nC, ctrl);
     return cudaGetLastError();
 }
 

@@ -82,6 +82,8 @@ struct bgs_plan {
     // binning
     Buf touched, touched_sorted, dkey, dkey_sorted, gidx, order, offsets, keys_in, keys_out, vals_in, cub_tmp;
     Buf bin_h, bin_total, bin_start, bin_rect, bin_mask;  // counting-sort binning
+    Buf bin_credit, bin_sat;                              // list truncation (credits, last block per tile)
+    Buf bin_items;                                        // the scatter's work items per tile group
     int smem_optin = 0;
     // render
     Buf recs, tile_idx, items, grad_acc, warp_items;  // tile_idx: each tile's slot in its work-list bucket
@@ -328,7 +330,7 @@ int bgs_plan_destroy(bgs_plan *p) {
     DeviceGuard g(p->device);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     if (p->graph) cudaGraphDestroy(p->graph);
-    Buf *bufs[] = {&p->vkey, &p->vkey_sorted, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_rect, &p->bin_mask, &p->touched, &p->touched_sorted, &p->dkey,
+    Buf *bufs[] = {&p->vkey, &p->vkey_sorted, &p->bin_credit, &p->bin_sat, &p->bin_items, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_rect, &p->bin_mask, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_idx, &p->items, &p->warp_items,
@@ -570,8 +572,8 @@ namespace {
 // With flag_overflow, an entry count past capacity raises BGS_CHECK_OVERFLOW on the device
 // (graph-safe callers check it with bgs_check); otherwise the host checks the count.
 int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const float *means2D, const int32_t *radii,
-                      int W, int H, int tw, int th, uint32_t *point_list, long long capacity, uint32_t *ranges,
-                      bool flag_overflow, cudaStream_t s) {
+                      const float *conic_opacity, int W, int H, int tw, int th, uint32_t *point_list,
+                      long long capacity, uint32_t *ranges, bool flag_overflow, cudaStream_t s) {
     const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
     const long long T = (long long)tiles_x * tiles_y;
     const size_t smem = bgs::bin_count_smem(tiles_x, tiles_y);
@@ -601,16 +603,32 @@ int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const flo
     BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, rect, masks, (int)W32,
                                    s),
              "bin_count");
-    BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, tot, s), "bin_colscan");
+    // list truncation: per-block credits toward the certificate that a tile's pixels have all
+    // stopped (needs the conics, and the credit counters of one block in shared memory)
+    const bool trunc = conic_opacity && bgs::bin_credit_smem(tiles_x, tiles_y) <= (size_t)p->smem_optin;  // incl. static
+    uint16_t *credit = nullptr;
+    uint32_t *bsat = nullptr;
+    if (trunc) {
+        BGS_TRY(ensure(p, p->bin_credit, sizeof(uint16_t) * B * T, s, "bin_credit"));
+        BGS_TRY(ensure(p, p->bin_sat, sizeof(uint32_t) * T, s, "bin_sat"));
+        credit = (uint16_t *)p->bin_credit.p;
+        bsat = (uint32_t *)p->bin_sat.p;
+        BGS_CUDA(bgs::launch_bin_credit(n, (int)G, (int)B, rect, means2D, conic_opacity, W, H, tw, th, credit, s),
+                 "bin_credit");
+        p->host_launches += 1;
+    }
+    BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, credit, tot, bsat, s), "bin_colscan");
     size_t tmp = 0;
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tot, start, (int)T, s), "tile scan (size)");
     BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
     tmp = p->cub_tmp.bytes;
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, tot, start, (int)T, s), "tile scan");
     BGS_CUDA(bgs::launch_bin_ranges((int)T, start, tot, reinterpret_cast<uint2 *>(ranges), p->ctrl, s), "bin_ranges");
+    BGS_TRY(ensure(p, p->bin_items, sizeof(uint32_t) * (nC + 1), s, "bin_items"));
     BGS_CUDA(bgs::launch_bin_scatter(n, (int)G, (int)B, (int)W32, rect, W, H, tw, th, Hm, start, masks, point_list,
-                                     capacity, p->ctrl, s),
+                                     capacity, bsat, (uint32_t *)p->bin_items.p, p->num_sms, p->ctrl, s),
              "bin_scatter");
+    p->host_launches += 1;  // the scatter's work list
     BGS_CUDA(bgs::launch_bin_advance((int)T, start, tot, flag_overflow ? capacity : (1ll << 62), p->ctrl, s),
              "bin_advance");
     p->host_launches += 5;  // count, colscan, ranges, scatter, advance
@@ -648,8 +666,8 @@ int sort_and_range(bgs_plan *p, long long N, const float *means2D, const int32_t
 extern "C" {
 
 int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t *radii, const float *depths,
-                     int32_t W, int32_t H, int32_t tw, int32_t th, uint32_t *point_list, int64_t capacity,
-                     uint32_t *ranges, int64_t *num_rendered, int64_t *needed, void *stream) {
+                     const float *conic_opacity, int32_t W, int32_t H, int32_t tw, int32_t th, uint32_t *point_list,
+                     int64_t capacity, uint32_t *ranges, int64_t *num_rendered, int64_t *needed, void *stream) {
     if (!p) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: NULL plan");
     if (N < 0 || N >= (1ll << 32)) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: N out of range");
     if (capacity < 0) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: negative capacity");
@@ -657,6 +675,7 @@ int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t
     BGS_TRY(check_tile(tw, th, false));
     if (!ranges || (N > 0 && (!means2D || !radii || !depths)) || (capacity > 0 && !point_list))
         return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: NULL array");
+    if (((uintptr_t)conic_opacity) & 15) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: conic_opacity alignment");
     const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
     const long long T = (long long)tiles_x * tiles_y;
     if (T >= (1ll << 31)) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort: too many tiles");
@@ -689,14 +708,15 @@ int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t
     // (2) counting sort over tile rectangles when the per-tile counters fit in shared memory
     if (bgs::bin_count_smem(tiles_x, tiles_y) <= (size_t)p->smem_optin) {
         BGS_CUDA(cudaMemsetAsync(&p->ctrl->bin_base, 0, sizeof(unsigned long long), s), "clear bin base");
-        BGS_TRY(bin_view_counting(p, N, order, means2D, radii, W, H, tw, th, point_list, capacity, ranges, false, s));
+        BGS_TRY(bin_view_counting(p, N, order, means2D, radii, conic_opacity, W, H, tw, th, point_list, capacity,
+                                  ranges, false, s));
         unsigned long long K = 0;
         BGS_CUDA(cudaMemcpyAsync(&K, &p->ctrl->num_entries, sizeof K, cudaMemcpyDeviceToHost, s), "read K");
         BGS_CUDA(cudaStreamSynchronize(s), "sync K");
         if (needed) *needed = (int64_t)K;
-        if ((long long)K > capacity || K >= (1ull << 32) - 1)
-            return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort: %llu entries exceed capacity %lld (or 2^32)", K,
-                        (long long)capacity);
+        if ((long long)K > capacity || (long long)K > BGS_MAX_ENTRIES)
+            return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort: %llu entries exceed capacity %lld (or BGS_MAX_ENTRIES)",
+                        K, (long long)capacity);
         if (num_rendered) *num_rendered = (int64_t)K;
         return BGS_OK;
     }
@@ -715,7 +735,8 @@ int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t
     if (needed) *needed = (int64_t)K;
     if ((long long)K > capacity)
         return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort: %llu entries exceed capacity %lld", K, (long long)capacity);
-    if (K >= (1ull << 32) - 1) return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort: %llu entries exceed 2^32", K);
+    if ((long long)K > BGS_MAX_ENTRIES)
+        return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort: %llu entries exceed BGS_MAX_ENTRIES", K);
     if (num_rendered) *num_rendered = (int64_t)K;
     if (K == 0) return BGS_OK;
     // emit entries in depth order and group them per tile with a stable sort on the tile id
@@ -732,7 +753,8 @@ int check_render_arrays(int64_t N, const float *means2D, const float *conic_opac
                         const float *depths, const uint32_t *point_list, int64_t num_entries, const uint32_t *ranges,
                         int tw, int th, const float *bg, int mode, const char *who) {
     if (N < 0 || N >= (1ll << 32)) return fail(BGS_ERR_INVALID, "%s: N out of range", who);
-    if (num_entries < 0 || num_entries >= (1ll << 32)) return fail(BGS_ERR_INVALID, "%s: num_entries out of range", who);
+    if (num_entries < 0 || num_entries > BGS_MAX_ENTRIES)
+        return fail(BGS_ERR_INVALID, "%s: num_entries out of range (<= BGS_MAX_ENTRIES)", who);
     if (mode < BGS_MODE_AUTO || mode > BGS_MODE_SELECT) return fail(BGS_ERR_INVALID, "%s: unknown mode %d", who, mode);
     BGS_TRY(check_tile(tw, th, mode != BGS_MODE_STATIC));
     if (!ranges || !bg || (num_entries > 0 && !point_list) ||
@@ -1052,15 +1074,17 @@ int bgs_preprocess_backward_batched(bgs_plan *p, int32_t V, const bgs_view *view
 }
 
 int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N, const float *means2D,
-                             const int32_t *radii, const float *depths, int32_t tw, int32_t th, uint32_t *point_list,
-                             int64_t capacity, uint32_t *ranges, int32_t flags, int64_t *num_rendered,
-                             int64_t *needed, void *stream) {
+                             const int32_t *radii, const float *depths, const float *conic_opacity, int32_t tw,
+                             int32_t th, uint32_t *point_list, int64_t capacity, uint32_t *ranges, int32_t flags,
+                             int64_t *num_rendered, int64_t *needed, void *stream) {
     if (!p || !views) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: NULL plan or views");
     if (V < 1 || V > bgs::kMaxViews) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: V=%d", V);
     if (N < 0 || N * V >= (1ll << 32)) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: N out of range");
     if (capacity < 0) return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: negative capacity");
     if (!ranges || (N > 0 && (!means2D || !radii || !depths)) || (capacity > 0 && !point_list))
         return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: NULL array");
+    if (((uintptr_t)conic_opacity) & 15)
+        return fail(BGS_ERR_INVALID, "bgs_bin_and_sort_batched: conic_opacity alignment");
     BGS_TRY(check_tile(tw, th, false));
     int Ws[bgs::kMaxViews], Hs[bgs::kMaxViews];
     for (int v = 0; v < V; ++v) {
@@ -1103,8 +1127,8 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
         }
         p->host_launches += 1;
         for (int v = 0; v < V; ++v)  // view v's records are positions [v N, (v+1) N) of the order
-            BGS_TRY(bin_view_counting(p, N, order + (size_t)v * N, means2D, radii, Ws[v], Hs[v], tw, th, point_list,
-                                      capacity, ranges + 2ull * vt.tile_base[v], !sync, s));
+            BGS_TRY(bin_view_counting(p, N, order + (size_t)v * N, means2D, radii, conic_opacity, Ws[v], Hs[v], tw,
+                                      th, point_list, capacity, ranges + 2ull * vt.tile_base[v], !sync, s));
     }
     if (!sync) return BGS_OK;
     unsigned long long K = 0;
@@ -1113,9 +1137,9 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
         BGS_CUDA(cudaStreamSynchronize(s), "sync K");
     }
     if (needed) *needed = (int64_t)K;
-    if ((long long)K > capacity || K >= (1ull << 32) - 1)
-        return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort_batched: %llu entries exceed capacity %lld (or 2^32)", K,
-                    (long long)capacity);
+    if ((long long)K > capacity || (long long)K > BGS_MAX_ENTRIES)
+        return fail(BGS_ERR_CAPACITY, "bgs_bin_and_sort_batched: %llu entries exceed capacity %lld (or "
+                                      "BGS_MAX_ENTRIES)", K, (long long)capacity);
     if (num_rendered) *num_rendered = (int64_t)K;
     return BGS_OK;
 }

@@ -13,8 +13,9 @@
 // The scratch array is shared by all calls: each call first resets the parts that must
 // start at zero, so consecutive calls on one stream are independent, but calls that
 // overlap on the GPU (different streams, or concurrent host threads) race on it.
-// Entries with an out-of-range index or tile span are rendered as transparent (their
-// check bits stay in the scratch array; bgs_render_forward with bgs_check reports them).
+// Entries with an out-of-range index or tile span are rendered as transparent and raise a
+// check bit in the scratch array; a caller that passes a host word for the bits gets them
+// back (the call then waits for its own work), otherwise they are not reported.
 #include <mutex>
 
 #include "bgs_internal.cuh"
@@ -181,8 +182,8 @@ extern "C" int bgs_render_forward_noalloc(int64_t N, const float *means2D, const
                                           int64_t num_entries, const uint32_t *ranges, int32_t W, int32_t H,
                                           int32_t tile_w, int32_t tile_h, const float *bg, float *out_color,
                                           float *out_depth, float *out_alpha, float *final_T, int32_t *n_contrib,
-                                          int32_t *n_eval, void *stream) {
-    if (N < 0 || N >= (1ll << 32) || num_entries < 0 || num_entries >= (1ll << 32))
+                                          int32_t *n_eval, uint32_t *check_bits, void *stream) {
+    if (N < 0 || N >= (1ll << 32) || num_entries < 0 || num_entries > BGS_MAX_ENTRIES)
         return na_fail(BGS_ERR_INVALID, "bgs_render_forward_noalloc: N or num_entries out of range");
     if (W <= 0 || H <= 0 || (long long)W * H > (1ll << 31) - 1)
         return na_fail(BGS_ERR_INVALID, "bgs_render_forward_noalloc: bad image size");
@@ -246,5 +247,14 @@ extern "C" int bgs_render_forward_noalloc(int64_t N, const float *means2D, const
     k_na_prepare<<<1, 1024, 0, s>>>(a, sc);
     k_na_forward<<<blocks, kNaWarps * 32, 0, s>>>(a, sc);
     if (cudaGetLastError() != cudaSuccess) return na_fail(BGS_ERR_CUDA, "bgs_render_forward_noalloc: launch failed");
+    if (check_bits) {
+        // this call's bits, read after its kernels (a copy into the caller's host word)
+        if (cudaMemcpyAsync(check_bits, &sc->check_bits, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return na_fail(BGS_ERR_CUDA, "bgs_render_forward_noalloc: reading the check bits failed");
+        if (*check_bits)
+            return na_fail(BGS_ERR_DEVICE_CHECK, "bgs_render_forward_noalloc: device check tripped (an index >= N "
+                                                 "or a tile span past num_entries was rendered transparent)");
+    }
     return BGS_OK;
 }

@@ -19,8 +19,9 @@
 //                          walking the tile's list through a warp-private shared memory
 //                          window of 32 records.
 //
-// Both evaluate each (pixel, entry) pair with the same code (pair_power2 / pair_alpha),
-// so skip and stop decisions of the forward and backward kernels agree bit for bit.
+// All evaluate each (pixel, entry) pair with the same code (pair_power2 / pair_alpha), so
+// their skip decisions agree bit for bit, and the pixel-wise kernels' stop decisions too;
+// the Gaussian-wise kernel's transmittance product is reassociated (see next_T).
 // Results of all kernels equal the sequential rule of Algorithm 5 up to float32
 // reassociation of the transmittance product (Sec. 4: "without any precision loss").
 #include "bgs_internal.cuh"
@@ -326,8 +327,10 @@ __device__ __forceinline__ void gauss_item(const FwdArgs &a, int tile, int sub, 
             if (lane == 0) excl = 1.f;
             const float Tp = T[p];
             const float tt = Tp * incl;  // transmittance after this lane's entry
-            // exact early stop: the first valid lane whose T' falls below 1e-4 stops the pixel
-            // and is not accumulated; the lanes before it are.
+            // early stop (Algorithm 5's rule on the prefix-product T'): the first valid lane
+            // whose T' falls below 1e-4 stops the pixel and is not accumulated; the lanes
+            // before it are.  T' differs from the sequential FMA chain of the pixel-wise
+            // kernels by rounding only.
             const unsigned smask = __ballot_sync(kFull, valid && tt < kTMin);
             const int kstop = smask ? __ffs(smask) - 1 : 32;
             const unsigned below = kstop >= 32 ? kFull : ((1u << kstop) - 1u);

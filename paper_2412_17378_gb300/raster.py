@@ -219,13 +219,18 @@ def preprocess_backward(plan: Plan, means3D, log_scales, quats, cam: dict, radii
     return out
 
 
-def bin_and_sort(plan: Plan, means2D, radii, depths, W: int, H: int, tile=(16, 16), point_list=None):
+def bin_and_sort(plan: Plan, means2D, radii, depths, W: int, H: int, tile=(16, 16), point_list=None,
+                 conic_opacity=None):
     """bgs_bin_and_sort: returns (point_list int32 [>=K] holding uint32, ranges int32 [T,2], K).
-    Grows ``point_list`` (a torch buffer) when the entry count exceeds its capacity."""
+    Grows ``point_list`` (a torch buffer) when the entry count exceeds its capacity.  With
+    ``conic_opacity`` each tile's list is cut where every pixel of the tile is certified to
+    have stopped (the render's outputs are unchanged)."""
     N = means2D.shape[0]
     _req(means2D, "means2D", torch.float32, (N, 2))
     _req(radii, "radii", torch.int32, (N,))
     _req(depths, "depths", torch.float32, (N,))
+    if conic_opacity is not None:
+        _req(conic_opacity, "conic_opacity", torch.float32, (N, 4))
     dev = means2D.device
     tx, ty = (W + tile[0] - 1) // tile[0], (H + tile[1] - 1) // tile[1]
     ranges = torch.empty((tx * ty, 2), dtype=torch.int32, device=dev)
@@ -234,7 +239,8 @@ def bin_and_sort(plan: Plan, means2D, radii, depths, W: int, H: int, tile=(16, 1
     K = ctypes.c_int64(0)
     need = ctypes.c_int64(0)
     for _ in range(2):
-        code = plan._lib.bgs_bin_and_sort(plan.handle, N, _ptr(means2D), _ptr(radii), _ptr(depths), W, H, tile[0],
+        code = plan._lib.bgs_bin_and_sort(plan.handle, N, _ptr(means2D), _ptr(radii), _ptr(depths),
+                                          _ptr(conic_opacity) if conic_opacity is not None else None, W, H, tile[0],
                                           tile[1], _ptr(point_list), point_list.numel(), _ptr(ranges),
                                           ctypes.byref(K), ctypes.byref(need), _stream(dev))
         if code == _lib.BGS_ERR_CAPACITY and need.value > point_list.numel():
@@ -463,9 +469,10 @@ def preprocess_backward_batched(plan: Plan, means3D, log_scales, quats, cams, ra
 
 
 def bin_and_sort_batched(plan: Plan, means2D, radii, depths, cams, tile=(16, 16), point_list=None, ranges=None,
-                         no_sync: bool = False):
+                         no_sync: bool = False, conic_opacity=None):
     """bgs_bin_and_sort_batched: returns (point_list, ranges [sum T_v, 2], K).  With no_sync the call
-    only enqueues work (graph capture): K is returned as -1 and an overflow raises a device check."""
+    only enqueues work (graph capture): K is returned as -1 and an overflow raises a device check.
+    With ``conic_opacity`` [V*N, 4] the lists are truncated as in ``bin_and_sort``."""
     R = means2D.shape[0]
     V = len(cams)
     assert R % V == 0
@@ -473,6 +480,8 @@ def bin_and_sort_batched(plan: Plan, means2D, radii, depths, cams, tile=(16, 16)
     _req(means2D, "means2D", torch.float32, (R, 2))
     _req(radii, "radii", torch.int32, (R,))
     _req(depths, "depths", torch.float32, (R,))
+    if conic_opacity is not None:
+        _req(conic_opacity, "conic_opacity", torch.float32, (R, 4))
     dev = means2D.device
     _, T = tile_counts(cams, tile)
     if ranges is None:
@@ -484,6 +493,7 @@ def bin_and_sort_batched(plan: Plan, means2D, radii, depths, cams, tile=(16, 16)
     flags = _lib.BIN_NO_SYNC if no_sync else 0
     for _ in range(2):
         code = plan._lib.bgs_bin_and_sort_batched(plan.handle, V, vw, N, _ptr(means2D), _ptr(radii), _ptr(depths),
+                                                  _ptr(conic_opacity) if conic_opacity is not None else None,
                                                   tile[0], tile[1], _ptr(point_list), point_list.numel(),
                                                   _ptr(ranges), flags, ctypes.byref(K), ctypes.byref(need),
                                                   _stream(dev))
