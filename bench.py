@@ -5,8 +5,10 @@ workload):
   a1 projection -> a2 binning + sort -> a3 work list -> a5 balanced forward
   -> L2 loss gradient (torch) -> a6 balanced backward,
 enqueued without host synchronisation, captured once as a CUDA graph and replayed.
-Default workload: 1920x1080, 1M Gaussians, 80% in one cluster covering ~5% of the image
-(the imbalanced single-view configuration), forward + backward.
+Default workload: the large stress configuration -- 4M Gaussians in three dense clusters
+over a sparse background, one 3840x2160 view plus eight 1920x1080 views on an arc, forward
++ backward (the largest configuration that fits one GPU); ``--config cfg2`` selects the
+imbalanced single view (1920x1080, 1M Gaussians, 80% in one cluster).
 
 The metric is Gaussian-pixel pairs per second: pairs = (pixel, list entry) pairs the
 sequential rule visits (sum of n_eval over the frame), divided by the step time.  The
@@ -40,7 +42,7 @@ WORKLOADS = {
     "cfg4": "16 uneven views (4x640x360, 8x1280x720, 4x1920x1080) of 2M clustered Gaussians, fwd+bwd",
     "cfg5": "3840x2160 + 8x1920x1080 views of 4M Gaussians in 3 clusters, fwd+bwd",
 }
-WORKLOAD = WORKLOADS["cfg2"]
+DEFAULT_CONFIG = "cfg5"
 
 # Algorithmic per-pair operation counts of the sequential rule (Algorithm 5 and its
 # derivative), counted at source level for the formulation the kernels implement, as the
@@ -67,7 +69,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cfg2")
+    ap.add_argument("--config", default=DEFAULT_CONFIG)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
@@ -79,6 +81,8 @@ def parse():
     ap.add_argument("--selector-drift", type=int, default=0, metavar="STAGES",
                     help="run the Sec. 4.4 selector (mode 'select', a timing every stage) over STAGES scenes "
                          "drifting from config 3-early to 3-late and print its record as one JSON line")
+    ap.add_argument("--full-lists", action="store_true",
+                    help="bin complete per-tile lists (no truncation where every pixel of a tile has stopped)")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed steps (no tuning, baselines, e2e or oracle): for profiler runs")
     return ap.parse_args()
@@ -121,27 +125,43 @@ def dist_init(args):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle-reason samples taken while the timed region runs."""
+    """nvidia-smi clock / throttle-reason samples (every 50 ms) around the timed region; the
+    summary keeps the samples whose host time falls inside the marked window."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_ms: int = 50):
         self.gpu = gpu_index
+        self.period = period_ms
         self.proc = None
         self.path = None
+        self.window = None
 
     def start(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+            self.t0 = time.time()
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu=timestamp,{self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period)], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def mark(self, t_begin: float, t_end: float):
+        """Host wall-clock bounds (time.time()) of the timed region."""
+        self.window = (t_begin, t_end)
+
+    @staticmethod
+    def _stamp(text: str):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -152,23 +172,27 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                rows.append((self._stamp(parts[0]), float(parts[2]), float(parts[3]),
+                             {n for n, v in zip(names, parts[6:10]) if v.lower() == "active"}))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
         os.unlink(self.path)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        inside = rows
+        if self.window is not None:
+            lo, hi = self.window
+            inside = [r for r in rows if r[0] is not None and lo - 0.05 <= r[0] <= hi + 0.05]
+        use = inside if inside else rows
+        reasons = set().union(*[r[3] for r in use]) if use else set()
+        return {"sm_mhz": float(np.median([r[1] for r in use])) if use else None,
+                "sm_max_mhz": max(r[2] for r in use) if use else None, "reasons": sorted(reasons),
+                "samples": len(rows), "samples_in_timed_region": len(inside), "period_ms": self.period}
 
 
 def cpu_model() -> str:
@@ -302,22 +326,30 @@ _ORACLE_SETUP = {}
 
 
 def oracle_setup(scene):
-    """Oracle projection + binning of the frame (done once, outside any timed region)."""
+    """Oracle projection of every view of the frame (done once, outside any timed region):
+    per view the float32 render inputs the oracle consumes and the view's tile count."""
     key = id(scene)
     if key not in _ORACLE_SETUP:
         import oracle
-        g, cam = scene["gaussians"], scene["cameras"][0]
-        pp = oracle.preprocess(g["means3D"], g["log_scales"], g["quats"], g["opacities"], cam)
-        m2, co, dp = (pp[k].astype(np.float32) for k in ("means2D", "conic_opacity", "depth"))
-        pl, rg = oracle.bin_tiles(m2, pp["radius"], dp, cam["W"], cam["H"])
-        _ORACLE_SETUP[key] = (m2, co, dp, pl, rg)
+        g = scene["gaussians"]
+        views = []
+        for cam in scene["cameras"]:
+            pp = oracle.preprocess(g["means3D"], g["log_scales"], g["quats"], g["opacities"], cam)
+            m2, co, dp = (pp[k].astype(np.float32) for k in ("means2D", "conic_opacity", "depth"))
+            W, H = cam["W"], cam["H"]
+            views.append(dict(m2=m2, co=co, dp=dp, radius=pp["radius"], W=W, H=H,
+                              T=((W + 15) // 16) * ((H + 15) // 16), order=oracle.depth_order(pp["radius"], dp)))
+            del pp
+        _ORACLE_SETUP[key] = views
     return _ORACLE_SETUP[key]
 
 
 def oracle_sample_run(scene, budget_s: float, rng_seed: int = 0, threads: int = 0):
     """Times the FP64 oracle's render forward + backward on a bounded sample of the frame's
-    tiles (chosen uniformly at random), sized to about ``budget_s`` seconds of CPU work, on
-    all host cores (threads = 0) or the given number of threads.
+    tiles (chosen uniformly at random over the tiles of all views), sized to about
+    ``budget_s`` seconds of CPU work, on all host cores (threads = 0) or the given number of
+    threads.  Only the render forward + backward is timed; the sampled tiles' lists are
+    built beforehand by the oracle's own binning (``bin_tiles_subset``).
     Returns (pairs/s, cores, description, measured pairs, seconds)."""
     import oracle
     if threads:
@@ -327,36 +359,43 @@ def oracle_sample_run(scene, budget_s: float, rng_seed: int = 0, threads: int = 
             return oracle_sample_run(scene, budget_s, rng_seed)
         finally:
             oracle.set_threads(all_threads)
-    g, cam = scene["gaussians"], scene["cameras"][0]
-    W, H = cam["W"], cam["H"]
-    m2, co, dp, pl, rg = oracle_setup(scene)
-    tx = (W + 15) // 16
-    T = rg.shape[0]
-    rng = np.random.default_rng(rng_seed)
-    order = rng.permutation(T)
-    cl = g["colors"]
+    views = oracle_setup(scene)
+    cl = scene["gaussians"]["colors"]
+    base = np.cumsum([0] + [v["T"] for v in views])
+    T = int(base[-1])
+    order = np.random.default_rng(rng_seed).permutation(T)
 
-    def run(tiles):
-        pix = []
-        for t in tiles:
-            x0, y0 = (t % tx) * 16, (t // tx) * 16
-            ys, xs = np.mgrid[y0:min(y0 + 16, H), x0:min(x0 + 16, W)]
-            pix.append((ys * W + xs).ravel())
-        pix = np.concatenate(pix)
-        t0 = time.perf_counter()
-        out = oracle.render(m2, co, cl, dp, pl, rg, W, H, pixels=pix)
-        gC = np.zeros((3, H, W))
-        gC.reshape(3, -1)[:, pix] = out["color"]
-        oracle.render_backward(m2, co, cl, dp, pl, rg, W, H, gC, tiles=np.asarray(tiles, np.int64))
-        dt = time.perf_counter() - t0
-        return int(out["n_eval"].sum()), dt
+    def run(tiles_global):
+        pairs, dt = 0, 0.0
+        for vi, v in enumerate(views):
+            sel = np.sort(tiles_global[(tiles_global >= base[vi]) & (tiles_global < base[vi + 1])] - base[vi])
+            if sel.size == 0:
+                continue
+            W, H = v["W"], v["H"]
+            tx = (W + 15) // 16
+            pl, rg = oracle.bin_tiles_subset(v["m2"], v["radius"], v["dp"], W, H, sel, order=v["order"])
+            pix = []
+            for t in sel:
+                x0, y0 = (t % tx) * 16, (t // tx) * 16
+                ys, xs = np.mgrid[y0:min(y0 + 16, H), x0:min(x0 + 16, W)]
+                pix.append((ys * W + xs).ravel())
+            pix = np.concatenate(pix)
+            t0 = time.perf_counter()
+            out = oracle.render(v["m2"], v["co"], cl, v["dp"], pl, rg, W, H, pixels=pix)
+            gC = np.zeros((3, H, W))
+            gC.reshape(3, -1)[:, pix] = out["color"]
+            oracle.render_backward(v["m2"], v["co"], cl, v["dp"], pl, rg, W, H, gC, tiles=sel.astype(np.int64))
+            dt += time.perf_counter() - t0
+            pairs += int(out["n_eval"].sum())
+        return pairs, dt
 
     n = 16
     pairs, dt = run(order[:n])
     while dt < budget_s / 4 and n < T:
         n = min(T, n * 4)
         pairs, dt = run(order[:n])
-    desc = f"{n} random 16x16 tiles of {T} ({100.0 * n / T:.1f}% of the frame), render fwd+bwd"
+    where = f"{len(views)} views" if len(views) > 1 else "the frame"
+    desc = f"{n} random 16x16 tiles of {T} ({100.0 * n / T:.1f}% of {where}), render fwd+bwd"
     return pairs / dt, oracle.num_threads(), desc, pairs, dt
 
 
@@ -473,6 +512,7 @@ def main_views(args, scene, rank, world, local):
     targets = [t.to(dev) for t in targets_h]
     N = d["means3D"].shape[0]
     plan = raster.Plan(device=local)
+    truncate = not args.full_lists
     side = torch.cuda.Stream(device=dev)
     state = {}
     if args.quick:
@@ -481,27 +521,30 @@ def main_views(args, scene, rank, world, local):
     if args.knobs:  # fixed knobs from the first step on (profiler runs)
         tuned = dict(apply_knobs(plan, args.knobs), source="--knobs")
 
-    def step(no_sync=True, mode=args.mode, before_forward=None, inp=None):
-        # inp: (device inputs, device targets) to read; the resident set by default
+    def step(no_sync=True, mode=args.mode, before_forward=None, inp=None, oset=""):
+        # inp: (device inputs, device targets) to read, the resident set by default; oset:
+        # which set of image outputs (and their loss gradients) the step writes
         dd, tgs = inp if inp is not None else (d, targets)
         pre = raster.preprocess_batched(plan, dd["means3D"], dd["log_scales"], dd["quats"], dd["opacities"], cams,
                                         out=state.get("pre"))
         state["pre"] = pre
         pl, rg, K = raster.bin_and_sort_batched(plan, pre["means2D"], pre["radii"], pre["depths"], cams,
-                                                point_list=state.get("pl"), ranges=state.get("rg"), no_sync=no_sync)
+                                                point_list=state.get("pl"), ranges=state.get("rg"), no_sync=no_sync,
+                                                conic_opacity=pre["conic_opacity"] if truncate else None)
         state["pl"], state["rg"] = pl, rg
         ne = pl.numel() if no_sync else K
         if before_forward is not None:
             before_forward()
         outs = raster.render_forward_batched(plan, pre["means2D"], pre["conic_opacity"], dd["colors"], pre["depths"],
-                                             pl, ne, rg, cams, mode=mode, outs=state.get("outs"))
-        state["outs"] = outs
-        if "gin" not in state:
-            state["gin"] = [dict(color=torch.empty_like(o["color"])) for o in outs]
-        for o, gi, t in zip(outs, state["gin"], tgs):
+                                             pl, ne, rg, cams, mode=mode, outs=state.get("outs" + oset))
+        state["outs" + oset] = outs
+        if "gin" + oset not in state:
+            state["gin" + oset] = [dict(color=torch.empty_like(o["color"])) for o in outs]
+        gin = state["gin" + oset]
+        for o, gi, t in zip(outs, gin, tgs):
             torch.sub(o["color"], t, out=gi["color"])
         gr = raster.render_backward_batched(plan, pre["means2D"], pre["conic_opacity"], dd["colors"], pre["depths"],
-                                            pl, ne, rg, cams, outs, state["gin"], mode=mode, out=state.get("gr"))
+                                            pl, ne, rg, cams, outs, gin, mode=mode, out=state.get("gr"))
         state["gr"] = gr
         return K
 
@@ -525,8 +568,8 @@ def main_views(args, scene, rank, world, local):
         eval_pairs, contrib_pairs = st["eval_pairs"], st["contrib_pairs"]
         launches_per_step = st["host_launches"] - l0
         bwd_pairs = int(sum(o["n_contrib"].sum().item() for o in state["outs"]))
-        rgh = state["rg"].cpu().numpy().reshape(-1, 2)
-        lens = rgh[:, 1].astype(np.int64) - rgh[:, 0]
+        rgh = state["rg"].cpu().numpy().reshape(-1, 2).view(np.uint32)  # list positions reach past 2^31
+        lens = rgh[:, 1].astype(np.int64) - rgh[:, 0].astype(np.int64)
         # per-tile evaluated pairs (the imbalance the balanced kernels address)
         outs_ne = raster.render_forward_batched(plan, pre["means2D"], pre["conic_opacity"], d["colors"],
                                                 pre["depths"], state["pl"], K, state["rg"], cams, n_eval=True)
@@ -535,11 +578,19 @@ def main_views(args, scene, rank, world, local):
         # ---- binning alone (a2: depth sort + per-tile lists), CUDA events, no host sync ----
         bin_ms, = time_enqueued(side, [lambda: raster.bin_and_sort_batched(
             plan, pre["means2D"], pre["radii"], pre["depths"], cams, point_list=state["pl"], ranges=state["rg"],
-            no_sync=True)])
+            no_sync=True, conic_opacity=pre["conic_opacity"] if truncate else None)])
         n_tiles = int(rgh.shape[0])
-        # algorithmic bytes: read means2D, radii, depths once (16 B per record), write the
-        # point list (4 B per entry) and the ranges (8 B per tile)
-        bin_bytes = 16 * N * V + 4 * K + 8 * n_tiles
+        # entry count of the complete lists (once, untimed), for the truncation factor
+        K_full = K
+        if truncate:
+            _, _, K_full = raster.bin_and_sort_batched(plan, pre["means2D"], pre["radii"], pre["depths"], cams)
+            raster.bin_and_sort_batched(plan, pre["means2D"], pre["radii"], pre["depths"], cams,
+                                        point_list=state["pl"], ranges=state["rg"],
+                                        conic_opacity=pre["conic_opacity"])
+        # algorithmic bytes: read means2D, radii, depths once (16 B per record; + 16 B of conic
+        # and opacity with list truncation), write the point list (4 B per kept entry) and the
+        # ranges (8 B per tile)
+        bin_bytes = (32 if truncate else 16) * N * V + 4 * K + 8 * n_tiles
         # ---- render kernels alone (CUDA events around the persistent launches) ----
         plan.timing(True)
         for _ in range(3):
@@ -561,29 +612,32 @@ def main_views(args, scene, rank, world, local):
         plan.check()
         if world > 1:
             torch.distributed.barrier()
-        # nvidia-smi samples every 200 ms while the GPU replays the step: ~0.6 s of untimed
-        # replays of the same graph right before the timed region (too short on its own to be
-        # sampled), then the timed region
+        # nvidia-smi samples every 50 ms: ~1 s of untimed replays of the same graph right
+        # before the timed region (the sampler's start-up and the GPU's clock ramp), then the
+        # timed region, whose host-side window selects the samples that are reported
         clocks = ClockSampler(local)
         clocks.start()
         if not args.quick:
             t_load = time.perf_counter()
-            while time.perf_counter() - t_load < 0.6:
-                for _ in range(8):
+            while time.perf_counter() - t_load < 1.0:
+                for _ in range(4):
                     raster.graph_launch(plan)
                 side.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         side.synchronize()
         if world > 1:
             torch.distributed.barrier()
+        t_wall0 = time.time()
         e0.record(side)
         for _ in range(args.steps):
             raster.graph_launch(plan)
         e1.record(side)
         side.synchronize()
+        clocks.mark(t_wall0, time.time())
         ms_total = e0.elapsed_time(e1)
         clk = clocks.stop()
-        clk["note"] = "samples taken under ~0.6 s of back-to-back replays of the timed step and the timed region"
+        clk["note"] = ("median over the samples taken inside the timed region (host wall-clock window); "
+                       "~1 s of untimed replays of the same step precede it")
         plan.check()
         ms_total = max_over_ranks(ms_total, world, dev)
         ms_step = ms_total / args.steps
@@ -595,23 +649,30 @@ def main_views(args, scene, rank, world, local):
                                   "tuned": tuned, "note": "--quick profiling run"}), flush=True)
             plan.close()
             return
-        # ---- end to end: inputs from pinned host memory, loss read back, every step ----
+        # ---- end to end: inputs from pinned host memory, images and loss read back, every step ----
         # One captured graph per step (torch.cuda.graph, whose private memory pool keeps the
-        # loss reduction's workspace alive for the replays): the Gaussian parameters the
-        # projection reads are copied on the step's stream first; colours and targets, read
-        # from the forward on, are copied on a second stream while projection and binning run.
-        loss_h = torch.empty(1, pin_memory=True)
+        # loss reduction's workspace alive for the replays).  Every step copies its inputs in
+        # from pinned host memory and its rendered images (every view's colour planes) and
+        # its loss out to pinned host memory.
         h2d = sum(v.numel() * v.element_size() for v in host.values()) + sum(
             t.numel() * t.element_size() for t in targets_h)
+        img_bytes = sum(3 * c["W"] * c["H"] * 4 for c in cams)
+        d2h = img_bytes + 4
         copy_s = torch.cuda.Stream(device=dev)
-
+        imgs_h = [[torch.empty((3, c["H"], c["W"]), pin_memory=True) for c in cams] for _ in range(2)]
+        loss_h = torch.empty(1, pin_memory=True)
         loss_hp = torch.empty(2, pin_memory=True)  # the pipelined steps' losses, by step parity
 
-        def loss_to_host(dst):
-            loss = sum((gi["color"] * gi["color"]).sum() for gi in state["gin"]) * 0.5
+        def loss_to_host(dst, oset=""):
+            loss = sum((gi["color"] * gi["color"]).sum() for gi in state["gin" + oset]) * 0.5
             dst.copy_(loss.reshape(1), non_blocking=True)
 
-        # (1) serial: a step copies its own inputs, then computes from them
+        def images_to_host(dst, oset=""):
+            for h, o in zip(dst, state["outs" + oset]):
+                h.copy_(o["color"], non_blocking=True)
+
+        # (1) serial: a step copies its own inputs, computes from them, then copies its images
+        # and loss out; the host waits for them before launching the next step
         ev_fork, ev_join = torch.cuda.Event(), torch.cuda.Event()
 
         def serial_body(i):
@@ -626,13 +687,19 @@ def main_views(args, scene, rank, world, local):
                 if k != "colors":
                     d[k].copy_(host[k], non_blocking=True)
             step(before_forward=lambda: side.wait_event(ev_join))
+            images_to_host(imgs_h[0])
             loss_to_host(loss_h)
 
-        # (2) pipelined, as a prefetching loader runs: two device input sets; step i computes
-        # from set i % 2 (filled while step i - 1 ran) while a second stream copies step i + 1's
-        # inputs into the other set.  A set is overwritten only after the step that read it
-        # has ended (the steps run in order on one stream).
+        # (2) pipelined, as a prefetching loader runs: two device input sets and two image
+        # output sets; step i computes from input set i % 2 (filled while step i - 1 ran) into
+        # output set i % 2, while a second stream copies step i + 1's inputs into the other
+        # input set and step i - 1's images (the other output set) to the host.  A set is
+        # overwritten only after the step that read it has ended (the steps run in order on
+        # one stream, and a step's graph ends after its second-stream copies).
         bufs = [(d, targets), ({k: torch.empty_like(v) for k, v in d.items()}, [torch.empty_like(t) for t in targets])]
+        osets = ["", "_b"]
+        step(oset="_b")  # allocates the second output set
+        side.synchronize()
         pev = [(torch.cuda.Event(), torch.cuda.Event()) for _ in range(2)]
 
         def pipelined_body(i):
@@ -646,9 +713,10 @@ def main_views(args, scene, rank, world, local):
                     nd[key].copy_(host[key], non_blocking=True)
                 for t, th in zip(nt, targets_h):
                     t.copy_(th, non_blocking=True)
+                images_to_host(imgs_h[1 - k], osets[1 - k])  # the previous step's images
                 ev_j.record(copy_s)
-            step(inp=bufs[k])
-            loss_to_host(loss_hp[k:k + 1])
+            step(inp=bufs[k], oset=osets[k])
+            loss_to_host(loss_hp[k:k + 1], osets[k])
             side.wait_event(ev_j)
 
         def capture(body, n):
@@ -674,7 +742,8 @@ def main_views(args, scene, rank, world, local):
             """ms per step over the timed steps and the last loss.  lag 0: the host waits for
             each step and reads its loss before launching the next; lag 1: it launches step i,
             then waits for step i - 1 and reads that step's loss (one step in flight, every
-            loss read inside the timed region)."""
+            loss read inside the timed region); the last step's images are copied out after
+            it, inside the timed region."""
             done = [torch.cuda.Event(), torch.cuda.Event()]
 
             def launch(i):
@@ -696,7 +765,12 @@ def main_views(args, scene, rank, world, local):
                         last = read(i)
                     elif i > 0:
                         last = read(i - 1)
-                return read(n - 1) if lag else last
+                if lag:
+                    last = read(n - 1)
+                    with torch.cuda.stream(side):
+                        images_to_host(imgs_h[(n - 1) % 2], osets[(n - 1) % 2])
+                    side.synchronize()
+                return last
 
             run(4)  # an even count keeps the pipelined input sets in phase
             side.synchronize()
@@ -706,17 +780,20 @@ def main_views(args, scene, rank, world, local):
 
         g_serial, err_serial = capture(serial_body, 1)
         serial_ms, loss_serial = run_e2e(g_serial, serial_body, 0)
+        img_serial = imgs_h[0][0][:, ::97, ::89].clone()
         g_pipe, err_pipe = capture(pipelined_body, 2)
         e2e_ms, loss_pipe = run_e2e(g_pipe, pipelined_body, 1)
+        img_pipe = imgs_h[(args.steps - 1) % 2][0][:, ::97, ::89].clone()
         del g_serial, g_pipe
-        e2e_how = ("two CUDA graphs alternating over two device input sets: each step copies the next step's "
-                   "inputs (pinned host memory, second stream) while it computes from the set the previous step "
-                   "filled, then copies its loss to pinned host memory; the host reads step i's loss after "
+        e2e_how = ("two CUDA graphs alternating over two device input sets and two image output sets: each step "
+                   "copies the next step's inputs in (pinned host memory, second stream) and the previous step's "
+                   "images out while it computes, then copies its loss out; the host reads step i's loss after "
                    "launching step i + 1" if err_pipe is None else "eager, pipelined: " + err_pipe)
         serial_how = ("one CUDA graph per step: H2D copies (colours and targets on a second stream, overlapping "
-                      "projection and binning), the step, the loss and its D2H read"
+                      "projection and binning), the step, the D2H copies of its images and loss, host wait"
                       if err_serial is None else "eager: " + err_serial)
         loss_match = abs(loss_pipe - loss_serial) <= 1e-6 * max(1.0, abs(loss_serial))
+        images_match = bool(torch.equal(img_serial, img_pipe))
         # ---- projection (a1) and its backward alone, CUDA events ----
         gr = state["gr"]
         proj_ms = tuple(time_enqueued(side, [
@@ -751,7 +828,8 @@ def main_views(args, scene, rank, world, local):
             if V == 1:
                 pl, rg, Kv = state["pl"], state["rg"], K
             else:
-                pl, rg, Kv = raster.bin_and_sort(plan, m2, pre["radii"][sl], dp, W, H)
+                pl, rg, Kv = raster.bin_and_sort(plan, m2, pre["radii"][sl], dp, W, H,
+                                                 conic_opacity=co if truncate else None)
 
             def static_pass():
                 fw = raster.render_forward(plan, m2, co, d["colors"], dp, pl, Kv, rg, W, H, (16, 16),
@@ -782,9 +860,9 @@ def main_views(args, scene, rank, world, local):
     roof["traffic"], roof["traffic_source"] = profiled_traffic(roof["kernel"], args.config, tuned)
     if roof["traffic"] is not None:
         roof["traffic_unit"] = "bytes per launch (DRAM read + write, ncu)"
-    # ---- FP64 CPU oracle on a bounded sample (rank 0, one GPU, single view) ----
+    # ---- FP64 CPU oracle on a bounded sample of every view (rank 0, one GPU) ----
     cpu = None
-    if rank == 0 and world == 1 and V == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, desc, _, _ = oracle_sample_run(scene, args.cpu_seconds)
         rate1, _, desc1, _, _ = oracle_sample_run(scene, 2.0, threads=1)
         cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc,
@@ -794,8 +872,12 @@ def main_views(args, scene, rank, world, local):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     binning = {"ms": bin_ms, "algorithmic_bytes": int(bin_bytes), "GB_s": bin_bytes / (bin_ms / 1e3) / 1e9,
                "hbm_peak_GB_s": hbm, "frac_of_hbm": bin_bytes / (bin_ms / 1e3) / 1e9 / hbm,
-               "note": "depth sort + counting-sort binning of K entries; algorithmic bytes = 16 B per "
-                       "projected record read + 4 B per entry + 8 B per tile written"}
+               "entries_kept": int(K), "entries_full_lists": int(K_full),
+               "truncated": bool(truncate),
+               "note": "depth sort + counting-sort binning; each tile's list cut after the depth block where "
+                       "every pixel of the tile is certified to have stopped (entries_kept of entries_full_lists "
+                       "written); algorithmic bytes = 32 B per projected record read (16 without truncation) + "
+                       "4 B per kept entry + 8 B per tile written"}
     projection = {"forward_ms": proj_ms[0], "backward_ms": proj_ms[1],
                   "forward_GB_s": proj_bytes[0] / (proj_ms[0] / 1e3) / 1e9,
                   "backward_GB_s": proj_bytes[1] / (proj_ms[1] / 1e3) / 1e9, "hbm_peak_GB_s": hbm,
@@ -833,10 +915,11 @@ def main_views(args, scene, rank, world, local):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": whole_job_value(eval_pairs, world, e2e_ms), "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms, "how": e2e_how,
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "how": e2e_how,
                 "serial": {"value": whole_job_value(eval_pairs, world, serial_ms), "ms_per_step": serial_ms,
                            "how": serial_how},
-                "loss": loss_pipe, "loss_matches_serial": bool(loss_match)},
+                "loss": loss_pipe, "loss_matches_serial": bool(loss_match), "images_match_serial": images_match,
+                "d2h": "every view's rendered colour planes + the loss"},
         "gpu_launches": int(launches_per_step * args.steps), "gpu_launches_per_step": int(launches_per_step),
         "gpu_launches_note": "libbgs kernels per graph replay, not counting CUB sort/scan kernels",
         "clocks": clk,

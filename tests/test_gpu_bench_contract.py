@@ -36,8 +36,12 @@ def test_bench_json_line_contract():
     assert cpu["kind"] == "oracle" and cpu["value"] > 0 and cpu["cores"] >= 1 and cpu["sample"]
     e2e = L["e2e"]
     assert e2e["value"] > 0 and e2e["unit"] == L["unit"] and e2e["h2d_bytes_per_step"] > 0
-    assert e2e["d2h_bytes_per_step"] > 0 and e2e["value"] < L["value"]  # copies are inside its timed region
+    # the step's rendered images (3 x 256 x 256 floats) and its loss come back every step
+    assert e2e["d2h_bytes_per_step"] == 3 * 256 * 256 * 4 + 4
+    assert e2e["value"] < L["value"]  # copies are inside its timed region
+    assert e2e["images_match_serial"] is True
     # the pipelined end-to-end loop computes what the serial one does
     assert e2e["serial"]["ms_per_step"] > 0 and e2e["loss_matches_serial"] is True and e2e["loss"] > 0
     clk = L["clocks"]
     assert clk["sm_mhz"] > 0 and clk["sm_max_mhz"] > 0 and isinstance(clk["reasons"], list)
+    assert clk["samples"] >= clk["samples_in_timed_region"] >= 0
