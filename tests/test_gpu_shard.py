@@ -1,0 +1,46 @@
+"""View sharding on one GPU: the per-Gaussian gradients of a multi-view step summed over the
+shards' separate steps (each shard renders only its views, as a rank would) equal the
+unsharded batched step's, element by element; and the sharded step with world = 1 is the
+unsharded one."""
+import numpy as np
+import pytest
+
+from helpers import ROW_EPS_PROJECTION, compare_grad
+from paper_2412_17378_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sum_over_view_shards_equals_unsharded_step(world):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_17378_gb300 import raster, shard
+    s = scenes.scene_config("cfg4", 0.01)  # 20k Gaussians, 16 uneven views
+    cams = [dict(c, W=c["W"] // 4, H=c["H"] // 4, fx=c["fx"] / 4, fy=c["fy"] / 4, cx=(c["W"] // 4 - 1) / 2,
+                 cy=(c["H"] // 4 - 1) / 2) for c in s["cameras"]]
+    g = {k: torch.from_numpy(v).cuda() for k, v in s["gaussians"].items()}
+    targets = [torch.from_numpy(scenes.target_image(40 + v, c["W"], c["H"])).cuda() for v, c in enumerate(cams)]
+    plan = raster.Plan()
+    full = shard.local_gaussian_grads(plan, g, cams, targets)
+    full = {k: v.cpu().numpy() for k, v in full.items()}
+    summed = {k: np.zeros_like(v) for k, v in full.items()}
+    parts = shard.partition_views(cams, world)
+    for part in parts:
+        loc = shard.local_gaussian_grads(plan, g, [cams[v] for v in part], [targets[v] for v in part])
+        for k in summed:
+            summed[k] += loc[k].cpu().numpy()
+    torch.cuda.synchronize()
+    plan.check()
+    # the same float32 terms summed in another order (atomics, view groupings); the render
+    # gradients' cancelling pixel sums pass their rounding on through the projection, so the
+    # per-Gaussian allowance of the projection tests applies
+    for k in shard.GRAD_KEYS:
+        assert np.abs(full[k]).max() > 0, k
+        compare_grad(summed[k], full[k], f"shards {world} {k}", rel_l2_max=1e-4, row_eps=ROW_EPS_PROJECTION)
+    one, mine = shard.sharded_gaussian_grads(plan, g, cams, targets, rank=0, world=1)
+    assert mine == list(range(len(cams)))
+    for k in shard.GRAD_KEYS:
+        compare_grad(one[k].cpu().numpy(), full[k], f"world 1 {k}", rel_l2_max=1e-4, row_eps=ROW_EPS_PROJECTION)
+    plan.close()
