@@ -512,7 +512,8 @@ def main_views(args, scene, rank, world, local):
     targets = [t.to(dev) for t in targets_h]
     N = d["means3D"].shape[0]
     plan = raster.Plan(device=local)
-    truncate = not args.full_lists
+    # list truncation: on unless --full-lists; the tuner keeps whichever binning is faster
+    opt = {"truncate": not args.full_lists}
     side = torch.cuda.Stream(device=dev)
     state = {}
     if args.quick:
@@ -530,7 +531,7 @@ def main_views(args, scene, rank, world, local):
         state["pre"] = pre
         pl, rg, K = raster.bin_and_sort_batched(plan, pre["means2D"], pre["radii"], pre["depths"], cams,
                                                 point_list=state.get("pl"), ranges=state.get("rg"), no_sync=no_sync,
-                                                conic_opacity=pre["conic_opacity"] if truncate else None)
+                                                conic_opacity=pre["conic_opacity"] if opt["truncate"] else None)
         state["pl"], state["rg"] = pl, rg
         ne = pl.numel() if no_sync else K
         if before_forward is not None:
@@ -550,15 +551,28 @@ def main_views(args, scene, rank, world, local):
 
     with torch.cuda.stream(side):
         K = step(no_sync=False)  # sizes the point_list and every workspace
-        state["pl"] = torch.empty(int(K * 1.15) + 1024, dtype=torch.int32, device=dev)
-        step(no_sync=False)
         pre = state["pre"]
+        # the complete lists' entry count (the truncation factor; untimed)
+        _, _, K_full = raster.bin_and_sort_batched(plan, pre["means2D"], pre["radii"], pre["depths"], cams)
+        state["pl"] = torch.empty(int(max(K, K_full) * 1.15) + 1024, dtype=torch.int32, device=dev)
+        # ---- binning alone (a2: depth sort + per-tile lists), CUDA events, no host sync, with
+        # and without list truncation; tuning keeps the faster ----
+        bin_t = {}
+        for tr in (True, False):
+            bin_t[tr], = time_enqueued(side, [lambda: raster.bin_and_sort_batched(
+                plan, pre["means2D"], pre["radii"], pre["depths"], cams, point_list=state["pl"], ranges=state["rg"],
+                no_sync=True, conic_opacity=pre["conic_opacity"] if tr else None)])
+        if not args.knobs and not args.no_tune and not args.full_lists and len(bin_t) == 2:
+            opt["truncate"] = bin_t[True] <= bin_t[False]
+        bin_ms = bin_t[opt["truncate"]]
+        tuned["truncate_lists"] = opt["truncate"]
+        K = step(no_sync=False)  # the chosen binning's lists and entry count
         # ---- knobs: autotuner (bgs_autotune_render), --knobs, or the plan defaults ----
         if not args.knobs and not args.no_tune:
             best_ms, knobs = raster.autotune_render(plan, pre["means2D"], pre["conic_opacity"], d["colors"],
                                                     pre["depths"], state["pl"], K, state["rg"], cams,
                                                     outs=state["outs"], grads_in=state["gin"], out=state["gr"])
-            tuned = {k: knobs[k] for k in ("pixel_rows", "heavy_threshold", "gw_pixels", "queue_chunk")}
+            tuned.update({k: knobs[k] for k in ("pixel_rows", "heavy_threshold", "gw_pixels", "queue_chunk")})
             tuned["render_ms"] = round(best_ms, 4)
         # ---- frame statistics (evaluated / contributing pairs, backward pairs) ----
         plan.reset_stats()
@@ -575,22 +589,11 @@ def main_views(args, scene, rank, world, local):
                                                 pre["depths"], state["pl"], K, state["rg"], cams, n_eval=True)
         tile_hist = tile_eval_histogram(outs_ne, cams)
         del outs_ne
-        # ---- binning alone (a2: depth sort + per-tile lists), CUDA events, no host sync ----
-        bin_ms, = time_enqueued(side, [lambda: raster.bin_and_sort_batched(
-            plan, pre["means2D"], pre["radii"], pre["depths"], cams, point_list=state["pl"], ranges=state["rg"],
-            no_sync=True, conic_opacity=pre["conic_opacity"] if truncate else None)])
         n_tiles = int(rgh.shape[0])
-        # entry count of the complete lists (once, untimed), for the truncation factor
-        K_full = K
-        if truncate:
-            _, _, K_full = raster.bin_and_sort_batched(plan, pre["means2D"], pre["radii"], pre["depths"], cams)
-            raster.bin_and_sort_batched(plan, pre["means2D"], pre["radii"], pre["depths"], cams,
-                                        point_list=state["pl"], ranges=state["rg"],
-                                        conic_opacity=pre["conic_opacity"])
         # algorithmic bytes: read means2D, radii, depths once (16 B per record; + 16 B of conic
         # and opacity with list truncation), write the point list (4 B per kept entry) and the
         # ranges (8 B per tile)
-        bin_bytes = (32 if truncate else 16) * N * V + 4 * K + 8 * n_tiles
+        bin_bytes = (32 if opt["truncate"] else 16) * N * V + 4 * K + 8 * n_tiles
         # ---- render kernels alone (CUDA events around the persistent launches) ----
         plan.timing(True)
         for _ in range(3):
@@ -829,7 +832,7 @@ def main_views(args, scene, rank, world, local):
                 pl, rg, Kv = state["pl"], state["rg"], K
             else:
                 pl, rg, Kv = raster.bin_and_sort(plan, m2, pre["radii"][sl], dp, W, H,
-                                                 conic_opacity=co if truncate else None)
+                                                 conic_opacity=co if opt["truncate"] else None)
 
             def static_pass():
                 fw = raster.render_forward(plan, m2, co, d["colors"], dp, pl, Kv, rg, W, H, (16, 16),
@@ -873,7 +876,8 @@ def main_views(args, scene, rank, world, local):
     binning = {"ms": bin_ms, "algorithmic_bytes": int(bin_bytes), "GB_s": bin_bytes / (bin_ms / 1e3) / 1e9,
                "hbm_peak_GB_s": hbm, "frac_of_hbm": bin_bytes / (bin_ms / 1e3) / 1e9 / hbm,
                "entries_kept": int(K), "entries_full_lists": int(K_full),
-               "truncated": bool(truncate),
+               "truncated": bool(opt["truncate"]),
+               "ms_by_mode": {("truncated" if k else "full_lists"): v for k, v in bin_t.items()},
                "note": "depth sort + counting-sort binning; each tile's list cut after the depth block where "
                        "every pixel of the tile is certified to have stopped (entries_kept of entries_full_lists "
                        "written); algorithmic bytes = 32 B per projected record read (16 without truncation) + "

@@ -42,12 +42,17 @@ __device__ __forceinline__ void rect_of(const float2 *__restrict__ means2D, cons
     const int r = radii[g];
     if (r <= 0) return;
     const float2 m = means2D[g];
-    // same float32 operations as the preprocess and oracle rectangles
+    // same float32 operations as the preprocess and oracle rectangles: a quotient rounded once
+    // (for a power-of-two tile side, the product by its exact reciprocal is that quotient)
     int x1, y1;
-    x0 = (int)floorf(__fdiv_rn(__fsub_rn(m.x, (float)r), (float)tw));
-    x1 = (int)floorf(__fdiv_rn(__fadd_rn(m.x, (float)(r + tw - 1)), (float)tw));
-    y0 = (int)floorf(__fdiv_rn(__fsub_rn(m.y, (float)r), (float)th));
-    y1 = (int)floorf(__fdiv_rn(__fadd_rn(m.y, (float)(r + th - 1)), (float)th));
+    const bool px2 = (tw & (tw - 1)) == 0, py2 = (th & (th - 1)) == 0;
+    const float itw = 1.f / (float)tw, ith = 1.f / (float)th;
+    const float ax = __fsub_rn(m.x, (float)r), bx = __fadd_rn(m.x, (float)(r + tw - 1));
+    const float ay = __fsub_rn(m.y, (float)r), by = __fadd_rn(m.y, (float)(r + th - 1));
+    x0 = (int)floorf(px2 ? __fmul_rn(ax, itw) : __fdiv_rn(ax, (float)tw));
+    x1 = (int)floorf(px2 ? __fmul_rn(bx, itw) : __fdiv_rn(bx, (float)tw));
+    y0 = (int)floorf(py2 ? __fmul_rn(ay, ith) : __fdiv_rn(ay, (float)th));
+    y1 = (int)floorf(py2 ? __fmul_rn(by, ith) : __fdiv_rn(by, (float)th));
     x0 = min(max(x0, 0), tx);
     x1 = min(max(x1, 0), tx);
     y0 = min(max(y0, 0), ty);
@@ -62,12 +67,13 @@ __global__ void __launch_bounds__(256) k_bin_count(long long N, int G, const uin
                                                    const float2 *__restrict__ means2D, const int *__restrict__ radii,
                                                    int tw, int th, int tx, int ty, uint32_t *__restrict__ H,
                                                    uint4 *__restrict__ rect, uint32_t *__restrict__ masks, int W32) {
-    extern __shared__ uint32_t d_s[];  // [T] tile counters, then [nC][16] mask words
+    extern __shared__ __align__(16) uint32_t d_s[];  // [T] tile counters, then (16-byte aligned) [nC][16] mask words
     const int T = tx * ty;
     const int ncx = (tx + kCbW - 1) / kCbW, nC = ncx * ((ty + kCbH - 1) / kCbH);
-    uint32_t *m_s = d_s + T;
+    const int T4 = (T + 3) & ~3;
+    uint32_t *m_s = d_s + T4;
     const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int t = threadIdx.x; t < T + 16 * nC; t += blockDim.x) d_s[t] = 0u;
+    for (int t = threadIdx.x; t < T4 + 16 * nC; t += blockDim.x) d_s[t] = 0u;
     __syncthreads();
     const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
     // 512 Gaussians (16 mask words per C) at a time
@@ -99,10 +105,12 @@ __global__ void __launch_bounds__(256) k_bin_count(long long N, int G, const uin
             rect[s] = make_uint4(px, py, g, 0u);
         }
         __syncthreads();
-        // the sub-block's mask words: (b, C) words [16 sub, 16 sub + 16)
-        for (int k = threadIdx.x; k < 16 * nC; k += blockDim.x) {
-            masks[((size_t)b * nC + (k >> 4)) * W32 + 16 * sub + (k & 15)] = m_s[k];
-            m_s[k] = 0u;
+        // the sub-block's mask words: (b, C) words [16 sub, 16 sub + 16), 16 bytes a store (the
+        // word arrays are 16-word aligned: W32 is a multiple of 16)
+        for (int k = threadIdx.x; k < 4 * nC; k += blockDim.x) {
+            uint4 *src = reinterpret_cast<uint4 *>(m_s) + k;
+            reinterpret_cast<uint4 *>(masks + ((size_t)b * nC + (k >> 2)) * W32 + 16 * sub)[k & 3] = *src;
+            *src = make_uint4(0u, 0u, 0u, 0u);
         }
         __syncthreads();
     }
@@ -156,38 +164,40 @@ __global__ void __launch_bounds__(256) k_bin_count(long long N, int G, const uin
 constexpr uint32_t kCreditThr = 2948;  // ceil(256 ln(1e5))
 constexpr int kCrWarps = 16;           // warps of a k_bin_credit block
 
-// Work units: one per (Gaussian, level, tile row inside that level set's vertical extent).
-// Each warp takes 32 Gaussians at a time and spreads their units evenly over its lanes (a
-// few large Gaussians would otherwise hold the warp for tens of rows); the warps of a block
-// share only the credit counters, so they run without block barriers until the final
-// prefix pass.
+// Work units: one per (Gaussian, tile row inside its lowest level set's vertical extent);
+// a unit credits the row for every level whose set spans it (the levels share the row's
+// chord centres).  Each warp takes 32 Gaussians at a time and spreads their units evenly
+// over its lanes (a few large Gaussians would otherwise hold the warp for tens of rows); the
+// warps of a block share only the credit counters, so they run without block barriers
+// until the final prefix pass.
 __global__ void __launch_bounds__(kCrWarps * 32) k_bin_credit(long long N, int G, const uint4 *__restrict__ rect,
                                                               const float2 *__restrict__ means2D,
                                                               const float4 *__restrict__ conic_opacity, int tw,
                                                               int th, int tx, int ty, uint16_t *__restrict__ D) {
     extern __shared__ uint32_t w_s[];  // [T] per-row difference arrays of the credits
-    // per warp, per lane's Gaussian: mx, my, qa, qb, det; per level: qa r^2, credit step,
-    // first row; the rectangle's columns
-    __shared__ float s_g[kCrWarps][32][5];
-    __shared__ float s_ar2[kCrWarps][32][3];
+    // per warp, per lane's Gaussian: mx, my, 1 / qa, qb / qa, det, qa r^2 of the 3 levels;
+    // the credit steps, first and end rows of the levels; the rectangle's columns, levels
+    __shared__ float s_g[kCrWarps][32][8];
     __shared__ uint32_t s_dw[kCrWarps][32][3];
-    __shared__ int s_j0[kCrWarps][32][3], s_n[kCrWarps][32][3], s_rx[kCrWarps][32][2];
+    __shared__ int s_j[kCrWarps][32][6];
+    __shared__ int s_rx[kCrWarps][32][2];
     __shared__ int s_scan[kCrWarps][32];
     const int T = tx * ty;
     const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < T; i += kCrWarps * 32) w_s[i] = 0u;
     __syncthreads();
     const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
+    const float fr[3] = {0.15f, 0.45f, 0.8f};
+    const float itw = 1.f / (float)tw, ith = 1.f / (float)th;
     // level set {o G >= a'} of a level a = f o, a' = a (1 + 2^-9): r^2 = 2 ln(o / a') is a
     // constant of f (0.999 shrinks it against float32 rounding); a level clamped at
-    // 1.01 / 255 computes its logarithm
-    const float fr[3] = {0.15f, 0.45f, 0.8f};
-    // ln(1 / (f (1 + 2^-9))) for f = 0.15, 0.45, 0.8, rounded down
+    // 1.01 / 255 computes its logarithm.  ln(1 / (f (1 + 2^-9))) for f = 0.15, 0.45, 0.8,
+    // rounded down:
     const float r2c[3] = {2.f * 1.8951687f * 0.999f, 2.f * 0.7965564f * 0.999f, 2.f * 0.2211923f * 0.999f};
     for (long long c0 = s0 + 32ll * warp; c0 < s1; c0 += 32ll * kCrWarps) {
         // (1) per Gaussian: its levels, their credits and the rows their level sets span
         const long long s = c0 + lane;
-        int n[3] = {0, 0, 0};
+        int units = 0;
         if (s < s1) {
             const uint4 rc = rect[s];
             const int rw = (int)(rc.x >> 16), rh = (int)(rc.y >> 16);
@@ -201,15 +211,22 @@ __global__ void __launch_bounds__(kCrWarps * 32) k_bin_credit(long long N, int G
                 if (qa > 0.f && det >= 1e-5f * qa * qc && 11.1f * qc >= det * (0.25f * tw * tw) &&
                     11.1f * qa >= det * (0.25f * th * th)) {
                     const float2 m = means2D[rc.z];
+                    const float iqa = 1.f / qa, idet = 1.f / det;
                     float *gp = s_g[warp][lane];
                     gp[0] = m.x;
                     gp[1] = m.y;
-                    gp[2] = qa;
-                    gp[3] = qb;
+                    gp[2] = iqa;
+                    gp[3] = qb * iqa;
                     gp[4] = det;
                     s_rx[warp][lane][0] = rx0;
                     s_rx[warp][lane][1] = rx0 + rw;
                     uint32_t wprev = 0u;
+                    int jlo = 0, jhi = 0;  // rows of the lowest credited level
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        s_dw[warp][lane][k] = 0u;
+                        s_j[warp][lane][2 * k] = s_j[warp][lane][2 * k + 1] = 0;
+                    }
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         const float fo = fr[k] * o;
@@ -224,25 +241,28 @@ __global__ void __launch_bounds__(kCrWarps * 32) k_bin_credit(long long N, int G
                         const uint32_t wk = (uint32_t)floorf(-256.f * __logf(1.f - fminf(lv, 0.99f)) * 0.999f);
                         if (wk <= wprev) continue;
                         // tile rows whose band [j th - 0.5, (j + 1) th - 0.5] lies within the level
-                        // set's vertical extent my -+ ey, inside the rectangle
-                        const float ey = fminf(sqrtf(r2 * qa / det), 1e8f);
-                        const int j0 = max(ry0, (int)ceilf((fmaxf(m.y - ey, -1e8f) + 0.5f) / (float)th));
-                        const int j1 = min(ry0 + rh, (int)floorf((fminf(m.y + ey, 1e8f) + 0.5f) / (float)th));
+                        // set's vertical extent my -+ ey, inside the rectangle (a row taken in
+                        // by rounding gets empty chords below and no credit)
+                        const float ey = fminf(__fsqrt_rn(r2 * qa * idet), 1e8f);
+                        const int j0 = max(ry0, (int)ceilf((fmaxf(m.y - ey, -1e8f) + 0.5f) * ith));
+                        const int j1 = min(ry0 + rh, (int)floorf((fminf(m.y + ey, 1e8f) + 0.5f) * ith));
                         if (j1 <= j0) break;  // the higher levels' sets lie inside this one
-                        s_ar2[warp][lane][k] = qa * r2;
+                        if (wprev == 0u) {
+                            jlo = j0;
+                            jhi = j1;
+                        }
+                        gp[5 + k] = qa * r2;
                         s_dw[warp][lane][k] = wk - wprev;
-                        s_j0[warp][lane][k] = j0;
-                        n[k] = j1 - j0;
+                        s_j[warp][lane][2 * k] = j0;
+                        s_j[warp][lane][2 * k + 1] = j1;
                         wprev = wk;
                     }
+                    units = jhi - jlo;
                 }
             }
         }
-        s_n[warp][lane][0] = n[0];
-        s_n[warp][lane][1] = n[1];
-        s_n[warp][lane][2] = n[2];
         // (2) inclusive scan of the lanes' unit counts
-        int v = n[0] + n[1] + n[2];
+        int v = units;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int u = __shfl_up_sync(0xffffffffu, v, off);
@@ -251,8 +271,8 @@ __global__ void __launch_bounds__(kCrWarps * 32) k_bin_credit(long long N, int G
         s_scan[warp][lane] = v;
         const int total = __shfl_sync(0xffffffffu, v, 31);
         __syncwarp();
-        // (3) the units: chords of the level-set ellipse at the row's two edges, their
-        // intersection, and one +/- pair of the row's difference array
+        // (3) the units: per level spanning the row, the level-set ellipse's chords at the
+        // row's two edges, their intersection, and one +/- pair of the row's difference array
         for (int u = lane; u < total; u += 32) {
             int lo = 0, hi = 31;  // owner: first lane g with scan[g] > u
             while (lo < hi) {
@@ -261,33 +281,47 @@ __global__ void __launch_bounds__(kCrWarps * 32) k_bin_credit(long long N, int G
                 else lo = mid + 1;
             }
             const int g = lo;
-            int r = u - (g > 0 ? s_scan[warp][g - 1] : 0);
-            int k = 0;
-            while (r >= s_n[warp][g][k]) r -= s_n[warp][g][k++];
-            const int j = s_j0[warp][g][k] + r;
             const float *gp = s_g[warp][g];
-            const float mx = gp[0], my = gp[1], qa = gp[2], qb = gp[3], det = gp[4];
-            const float ar2 = s_ar2[warp][g][k];
-            float lo_x = -1e8f, hi_x = 1e8f;
+            const float mx = gp[0], my = gp[1], iqa = gp[2], bqa = gp[3], det = gp[4];
+            // the first credited level's rows start the owner's unit range
+            int k0 = 0;
+            while (s_dw[warp][g][k0] == 0u) ++k0;
+            const int j = s_j[warp][g][2 * k0] + (u - (g > 0 ? s_scan[warp][g - 1] : 0));
+            float ctr[2], d2[2];
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {  // x in ctr -+ half at height y (empty: half < 0)
+            for (int e = 0; e < 2; ++e) {  // the row's edges: chord centres, det dy^2
                 const float dy = (float)((j + e) * th) - 0.5f - my;
-                const float disc = ar2 - det * dy * dy - 1e-6f * ar2;
-                const float half = disc > 0.f ? sqrtf(disc) / qa * 0.999f - 0.02f : -1e30f;
-                const float ctr = mx - qb * dy / qa;
-                lo_x = fmaxf(lo_x, ctr - half);
-                hi_x = fminf(hi_x, ctr + half);
+                ctr[e] = mx - bqa * dy;
+                d2[e] = det * dy * dy;
             }
-            lo_x = fmaxf(lo_x, -1e8f);
-            hi_x = fminf(hi_x, 1e8f);
-            if (!(hi_x - lo_x >= (float)tw)) continue;
-            // tiles i with [i tw - 0.5, i tw + tw - 0.5] inside [lo, hi], within the rectangle
-            const int i0 = max(s_rx[warp][g][0], (int)ceilf((lo_x + 0.5f) / (float)tw));
-            const int i1 = min(s_rx[warp][g][1], (int)floorf((hi_x + 0.5f) / (float)tw));
-            if (i1 <= i0) continue;
-            const uint32_t dw = s_dw[warp][g][k];
-            atomicAdd(&w_s[j * tx + i0], dw);
-            if (i1 < tx) atomicAdd(&w_s[j * tx + i1], 0u - dw);
+            const int rx0 = s_rx[warp][g][0], rx1 = s_rx[warp][g][1];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const uint32_t dw = s_dw[warp][g][k];
+                if (dw == 0u || j < s_j[warp][g][2 * k] || j >= s_j[warp][g][2 * k + 1]) continue;
+                const float ar2 = gp[5 + k];
+                float lo_x = -1e8f, hi_x = 1e8f;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {  // x in ctr -+ half (empty: half < 0)
+                    const float disc = ar2 - d2[e] - 1e-6f * ar2;
+                    // approximate square root and reciprocals: their few-ulp errors are far
+                    // inside the 0.1% + 0.02 px the half-width is shrunk by
+                    const float half = disc > 0.f ? disc * rsqrtf(disc) * iqa * 0.999f - 0.02f : -1e30f;
+                    lo_x = fmaxf(lo_x, ctr[e] - half);
+                    hi_x = fminf(hi_x, ctr[e] + half);
+                }
+                lo_x = fmaxf(lo_x, -1e8f);
+                hi_x = fminf(hi_x, 1e8f);
+                if (!(hi_x - lo_x >= (float)tw)) continue;
+                // tiles i with [i tw - 0.5, i tw + tw - 0.5] inside [lo, hi], within the
+                // rectangle (the product by 1 / tw rounds by far less than the 0.02 px the
+                // chords were shrunk by)
+                const int i0 = max(rx0, (int)ceilf((lo_x + 0.5f) * itw));
+                const int i1 = min(rx1, (int)floorf((hi_x + 0.5f) * itw));
+                if (i1 <= i0) continue;
+                atomicAdd(&w_s[j * tx + i0], dw);
+                if (i1 < tx) atomicAdd(&w_s[j * tx + i1], 0u - dw);
+            }
         }
         __syncwarp();
     }
@@ -484,14 +518,16 @@ __global__ void __launch_bounds__(1024) k_bin_items(int nC, int tx, int ty, int 
     if (tid == 1023) item_start[nC] = part[1023];
 }
 
-// Persistent: the blocks stride over the work items of k_bin_items; item -> (C, b).  Block
-// (b, C): one warp, lane l owns tile l of C; lanes whose list ends before b append nothing.
+// With truncated lists (bsat given) the blocks stride over the work items of k_bin_items,
+// item -> (C, b); with complete lists every (b, C) is an item and block i takes item i
+// (C = i / B, b = i % B) once.  Item (b, C): one warp, lane l owns tile l of C; lanes whose
+// list ends before b append nothing.
 __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const uint4 *__restrict__ rect, int tx, int ty,
                                                     const uint32_t *__restrict__ H, const uint32_t *__restrict__ start,
                                                     const uint32_t *__restrict__ masks,
                                                     uint32_t *__restrict__ point_list, uint32_t capacity, int vec_ok,
                                                     const uint32_t *__restrict__ bsat,
-                                                    const uint32_t *__restrict__ item_start, int nC,
+                                                    const uint32_t *__restrict__ item_start, int nC, int B,
                                                     const DevCtrl *ctrl) {
     // per flagged Gaussian of the pass: (lanes whose tile its rectangle covers, Gaussian
     // index), .y holding its sorted position until the hit is known; and the lanes' 16-word
@@ -501,18 +537,25 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const u
     __shared__ uint32_t ring_s[16 * 32];
     const int lane = threadIdx.x;
     const int ncx = (tx + kCbW - 1) / kCbW;
-    const uint32_t n_items = item_start[nC];
+    const bool listed = bsat != nullptr;
+    const uint32_t n_items = listed ? item_start[nC] : (uint32_t)B * (uint32_t)nC;
     const uint32_t base = (uint32_t)ctrl->bin_base;
     uint32_t *ring = ring_s + lane;
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-        int lo = 0, hi = nC - 1;  // C: the last group with item_start[C] <= it
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (item_start[mid] <= it) lo = mid;
-            else hi = mid - 1;
+        int C, b;
+        if (listed) {
+            int lo = 0, hi = nC - 1;  // C: the last group with item_start[C] <= it
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (item_start[mid] <= it) lo = mid;
+                else hi = mid - 1;
+            }
+            C = lo;
+            b = (int)(it - item_start[C]);
+        } else {
+            C = (int)(it / (uint32_t)B);
+            b = (int)(it % (uint32_t)B);
         }
-        const int C = lo;
-        const int b = (int)(it - item_start[C]);
         const int gx0 = (C % ncx) * kCbW, gy0 = (C / ncx) * kCbH;
         const int ltx = gx0 + (lane % kCbW), lty = gy0 + (lane / kCbW);
         const size_t t = (size_t)lty * tx + ltx;
@@ -609,7 +652,7 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const u
 
 size_t bin_count_smem(int tx, int ty) {
     const size_t nC = (size_t)((tx + kCbW - 1) / kCbW) * ((ty + kCbH - 1) / kCbH);
-    return sizeof(uint32_t) * ((size_t)tx * ty + 16 * nC);
+    return sizeof(uint32_t) * ((((size_t)tx * ty + 3) & ~(size_t)3) + 16 * nC);
 }
 
 int bin_mask_groups(int tx, int ty) { return ((tx + kCbW - 1) / kCbW) * ((ty + kCbH - 1) / kCbH); }
@@ -676,12 +719,16 @@ cudaError_t launch_bin_scatter(long long N, int G, int B, int W32, const uint4 *
     // indices, sorted positions and list slots are < 2^32 (checked by the callers)
     const uint32_t cap = capacity > BGS_MAX_ENTRIES ? (uint32_t)BGS_MAX_ENTRIES : (uint32_t)capacity;
     const int vec_ok = (reinterpret_cast<uintptr_t>(point_list) & 31u) == 0u;
-    k_bin_items<<<1, 1024, 0, s>>>(nC, tx, ty, B, bsat, item_start);
-    // persistent grid: 32 single-warp blocks per SM (the per-SM block limit), or fewer items
-    const long long grid = std::min<long long>((long long)num_sms * 32, (long long)B * nC);
+    // truncated lists: a persistent grid (32 single-warp blocks per SM, the per-SM block limit)
+    // over the open items; complete lists: one block per (b, C), scheduled by the hardware
+    long long grid = (long long)B * nC;
+    if (bsat) {
+        k_bin_items<<<1, 1024, 0, s>>>(nC, tx, ty, B, bsat, item_start);
+        grid = std::min<long long>((long long)num_sms * 32, grid);
+    }
     k_bin_scatter<<<(unsigned)std::max<long long>(1, grid), 32, 0, s>>>((uint32_t)G, W32, rect, tx, ty, Hm, start,
                                                                          masks, point_list, cap, vec_ok, bsat,
-                                                                         item_start, nC, ctrl);
+                                                                         item_start, nC, B, ctrl);
     return cudaGetLastError();
 }
 

@@ -348,6 +348,7 @@ cudaError_t launch_depth_keys(long long R, const float *depths, uint32_t *keys, 
     return cudaGetLastError();
 }
 
+
 // ---- a2: binning -----------------------------------------------------------------------
 // The per-tile lists must be ordered by (float32 depth, Gaussian index).  Instead of one
 // radix sort of 64-bit (tile, depth) keys over all K duplicated entries, the Gaussians are
