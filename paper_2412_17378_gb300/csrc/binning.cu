@@ -686,11 +686,11 @@ size_t bin_credit_smem(int tx, int ty) { return bin_credit_dyn_smem(tx, ty) + 44
 cudaError_t launch_bin_credit(long long N, int G, int B, const uint4 *rect, const float *means2D,
                               const float *conic_opacity, int W, int H, int tw, int th, uint16_t *D, cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
+    // the static tables (~40 KB) plus the counters pass the 48 KB default already on small grids:
+    // opt in to the dynamic size on every launch
     const size_t smem = bin_credit_dyn_smem(tx, ty);
-    if (smem > 24 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_bin_credit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    const cudaError_t e = cudaFuncSetAttribute(k_bin_credit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     k_bin_credit<<<B, kCrWarps * 32, smem, s>>>(N, G, rect, reinterpret_cast<const float2 *>(means2D),
                                       reinterpret_cast<const float4 *>(conic_opacity), tw, th, tx, ty, D);
     return cudaGetLastError();

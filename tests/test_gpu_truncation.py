@@ -110,6 +110,26 @@ def test_render_from_truncated_lists_matches_oracle(R, dense, mode):
     plan.close()
 
 
+@pytest.mark.parametrize("W,H", [(1280, 720), (64, 48)])
+def test_truncation_on_small_tile_grids(R, W, H):
+    """Tile grids whose credit counters are small (a few KB of shared memory beside the
+    kernel's fixed tables): truncation runs and keeps covering prefixes."""
+    s = scene("cfg3early", 0.1)
+    s["cameras"][0].update(W=W, H=H, cx=(W - 1) / 2, cy=(H - 1) / 2, fx=W, fy=W)
+    inp = oracle_render_inputs(s)
+    ref = oracle.render(inp["means2D"], inp["conic_opacity"], inp["colors"], inp["depths"], inp["point_list"],
+                        inp["ranges"], W, H)
+    g = to_gpu(inp)
+    plan = R.Plan()
+    pl, rg, K = R.bin_and_sort(plan, g["means2D"], g["radii"], g["depths"], W, H,
+                               conic_opacity=g["conic_opacity"])
+    torch.cuda.synchronize()
+    plan.check()
+    pl, rg = pl[:K].cpu().numpy().view(np.uint32), rg.cpu().numpy().view(np.uint32)
+    _check_prefixes(pl, rg, inp["point_list"], inp["ranges"], _tile_max(ref["n_eval"], W, H))
+    plan.close()
+
+
 def test_batched_truncation_per_view(R):
     """Three uneven views of one clustered scene: each view's truncated lists are covering
     prefixes of that view's oracle lists (record indices v N + g)."""
