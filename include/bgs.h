@@ -98,6 +98,13 @@ typedef struct bgs_plan_desc {
     int32_t bin_block;       /* binning: Gaussians per counting block, a multiple of 32, or 0
                                 for automatic (>= 2048, about 4 blocks per SM, enough to
                                 bound the tile histogram); changes speed only, not the lists */
+    int32_t gw_segment;      /* Gaussian-wise tiles: list entries per segment (a multiple of
+                                256, 256 .. 2^30; 2048).  A longer list is split into segments
+                                walked by separate warps, and a merge pass composes each
+                                pixel's segments (its stop taken by the sequential rule); the
+                                split is skipped (one segment per tile) when it would need more
+                                than 2^24 items or one per (segment, pixel group) over
+                                num_entries / gw_segment segments                           */
 } bgs_plan_desc;
 
 typedef struct bgs_plan bgs_plan;

@@ -52,7 +52,8 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("heavy_threshold", ctypes.c_int32), ("gw_pixels", ctypes.c_int32),
                 ("queue_chunk", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("lpt_order", ctypes.c_int32), ("device", ctypes.c_int32), ("pixel_rows", ctypes.c_int32),
-                ("select_period", ctypes.c_int32), ("bin_block", ctypes.c_int32)]
+                ("select_period", ctypes.c_int32), ("bin_block", ctypes.c_int32),
+                ("gw_segment", ctypes.c_int32)]
 
 
 class Camera(ctypes.Structure):

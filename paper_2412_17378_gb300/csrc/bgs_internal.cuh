@@ -36,6 +36,11 @@ struct DevCtrl {
     unsigned int wl_cnt[256];
     unsigned int wl_off[256];
     unsigned int wl_done;
+    unsigned int num_gauss0;    // Gaussian-wise items [0, num_gauss0) are first segments; the
+                                // items [num_gauss0, num_gauss) later segments of long lists
+    unsigned int gw_seg;        // entries per Gaussian-wise segment (0: lists are not split)
+    unsigned int pad2;
+    unsigned long long wl_extra;  // work-list build: later-segment items (returns to zero)
 };
 
 // End of a persistent pass, per warp (lane 0), for a block of `warps_per_block` warps whose
@@ -227,9 +232,11 @@ struct FwdArgs {
     ViewTable vt;
     ViewOut io;
     DevCtrl *ctrl;
-    const uint2 *items;
-    int pass_blocks;  // blocks of the persistent pass (both forward kernels when both run)          // work list (persistent kernels)
+    const uint2 *items;          // work list (persistent kernels)
+    int pass_blocks;             // blocks of the persistent pass (both forward kernels when both run)
     int gw_pixels;
+    const uint32_t *gw_exoff;    // per tile: its later-segment items' offset from num_gauss0
+    float4 *gw_sum;              // per Gaussian-wise item, per pixel: the segment summary
     int pixel_rows;              // Q of the pixel-wise items
     int chunk;
 };
@@ -328,9 +335,13 @@ cudaError_t launch_pack(long long N, const float *means2D, const float *conic_op
 // first items and the ctrl counts; k_wl_emit writes the items (positions past `capacity`
 // items raise BGS_CHECK_OVERFLOW and are skipped).  The order of tiles within one key is
 // unspecified.
+// gw_segment: entries per Gaussian-wise segment (0: lists are not split); exoff [num_tiles]
+// (nullable when gw_segment is 0) receives each tile's later-segment offset; extra_cap: the
+// most later-segment items the list may hold (beyond it the lists are not split).
 cudaError_t launch_worklist_buckets(const uint2 *ranges, int num_tiles, const ViewTable &vt, int tile_w, int tile_h,
                                     int mode, int heavy_threshold, int lpt, int gw_pixels, int pixel_rows,
-                                    uint32_t *slot, uint2 *items, long long capacity, DevCtrl *ctrl, cudaStream_t s);
+                                    int gw_segment, long long extra_cap, uint32_t *slot, uint32_t *exoff,
+                                    uint2 *items, long long capacity, DevCtrl *ctrl, cudaStream_t s);
 // queue of the current list: rewind for another pass / mark exhausted (fault injection)
 cudaError_t launch_rewind_queue(DevCtrl *ctrl, cudaStream_t s);
 cudaError_t launch_exhaust_queue(DevCtrl *ctrl, cudaStream_t s);
@@ -338,8 +349,11 @@ cudaError_t launch_exhaust_queue(DevCtrl *ctrl, cudaStream_t s);
 cudaError_t launch_forward_static(const FwdArgs &a, cudaStream_t s);
 cudaError_t launch_forward_gauss(const FwdArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_forward_pixel(const FwdArgs &a, int grid, bool after_gauss, cudaStream_t s);
+// composes the Gaussian-wise segment summaries per pixel; after both forward kernels
+cudaError_t launch_forward_gw_merge(const FwdArgs &a, int grid, cudaStream_t s);
 int forward_balanced_block_threads();
 const void *forward_gauss_kernel(int gw_pixels);
+const void *forward_gw_merge_kernel(int gw_pixels);
 const void *forward_pixel_kernel(int pixel_rows);
 
 cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s);

@@ -87,6 +87,7 @@ struct bgs_plan {
     int smem_optin = 0;
     // render
     Buf recs, tile_idx, items, grad_acc, warp_items;  // tile_idx: each tile's slot in its work-list bucket
+    Buf gw_exoff, gw_sum;  // Gaussian-wise segments: per-tile later-segment offsets, per-item summaries
     // batched binning: depth keys of every view
     Buf vkey, vkey_sorted;
     // captured CUDA graph
@@ -101,7 +102,7 @@ struct bgs_plan {
     struct WlKey {
         const void *ranges;
         bgs::ViewTable vt;
-        int tw, th, mode, heavy_threshold, gw_pixels, pixel_rows, lpt_order;
+        int tw, th, mode, heavy_threshold, gw_pixels, pixel_rows, lpt_order, gw_segment;
     } wl_key;
     bool rec_valid = false, wl_valid = false;
     unsigned int inject = 0;  // BGS_CHECK_* fault to inject into the next persistent pass
@@ -227,6 +228,7 @@ bgs_plan::WlKey worklist_key(const bgs_plan *p, const uint32_t *ranges, const bg
     k.gw_pixels = p->desc.gw_pixels;
     k.pixel_rows = p->desc.pixel_rows;
     k.lpt_order = p->desc.lpt_order;
+    k.gw_segment = p->desc.gw_segment;
     return k;
 }
 
@@ -243,6 +245,24 @@ bgs_plan::RecKey records_key(const float *means2D, const float *conic_opacity, c
     return k;
 }
 
+// Gaussian-wise items can be queued in this mode (AUTO: some list may pass the threshold).
+bool gauss_possible(const bgs_plan *p, int mode, int64_t num_entries) {
+    return mode == BGS_MODE_GAUSSIAN || (mode == BGS_MODE_AUTO && (int64_t)p->desc.heavy_threshold < num_entries);
+}
+
+// Pixel groups of a Gaussian-wise item over a whole tile.
+long long gw_groups(const bgs_plan *p, int tw, int th) {
+    return ((long long)tw * th + p->desc.gw_pixels - 1) / p->desc.gw_pixels;
+}
+
+// Most later-segment items a list over num_entries entries is given: one per (segment after
+// a tile's first, pixel group) when the tile ranges do not overlap, at most 2^24; beyond it
+// no list is split.
+long long gw_extra_cap(const bgs_plan *p, int tw, int th, int64_t num_entries) {
+    const long long L = p->desc.gw_segment;
+    return std::min<long long>(gw_groups(p, tw, th) * (num_entries / L + 1), 1ll << 24);
+}
+
 // mode: the render mode; AUTO with a threshold no list can exceed queues every tile
 // pixel-wise and builds the same list as PIXEL (so a backward can reuse it).
 int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt, int tw, int th, int mode,
@@ -254,13 +274,24 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
     const int item_w = bgs::pix_item_w(p->desc.pixel_rows), item_h = bgs::pix_item_h(p->desc.pixel_rows);
     const long long per_tile = std::max<long long>(((tw + item_w - 1) / item_w) * ((th + item_h - 1) / item_h),
                                                    (tw * th + P - 1) / P);
-    const long long max_items = (long long)T * per_tile;
+    const bool gauss = gauss_possible(p, mode, num_entries);
+    const long long extra_cap = gauss ? gw_extra_cap(p, tw, th, num_entries) : 0;
+    const long long max_items = (long long)T * per_tile + extra_cap;
     if (max_items >= (1ll << 31)) return fail(BGS_ERR_INVALID, "too many work items (%lld)", max_items);
     BGS_TRY(ensure(p, p->tile_idx, sizeof(uint32_t) * T, s, "tile_idx"));
     BGS_TRY(ensure(p, p->items, sizeof(uint2) * max_items, s, "items"));
+    if (gauss) {
+        BGS_TRY(ensure(p, p->gw_exoff, sizeof(uint32_t) * T, s, "gw_exoff"));
+        // summaries of the Gaussian-wise items: first segments of at most every tile, plus
+        // the later segments
+        const long long gw_items = (long long)T * gw_groups(p, tw, th) + extra_cap;
+        BGS_TRY(ensure(p, p->gw_sum, (size_t)gw_items * P * 2 * sizeof(float4), s, "gw_sum"));
+    }
     BGS_CUDA(bgs::launch_worklist_buckets(rg, T, vt, tw, th, mode, p->desc.heavy_threshold, p->desc.lpt_order, P,
-                                          p->desc.pixel_rows, (uint32_t *)p->tile_idx.p, (uint2 *)p->items.p,
-                                          (long long)(p->items.bytes / sizeof(uint2)), p->ctrl, s),
+                                          p->desc.pixel_rows, gauss ? p->desc.gw_segment : 0, extra_cap,
+                                          (uint32_t *)p->tile_idx.p, gauss ? (uint32_t *)p->gw_exoff.p : nullptr,
+                                          (uint2 *)p->items.p, (long long)(p->items.bytes / sizeof(uint2)), p->ctrl,
+                                          s),
              "build_worklist");
     p->host_launches += T > 0 ? 2 : 1;
     p->wl_key = worklist_key(p, ranges, vt, tw, th, mode);
@@ -273,7 +304,8 @@ bool valid_desc(const bgs_plan_desc *d) {
                                        d->gw_pixels == 8) &&
            d->queue_chunk >= 1 && d->queue_chunk <= 1024 && d->blocks_per_sm >= 0 && d->blocks_per_sm <= 64 &&
            (d->pixel_rows == 1 || d->pixel_rows == 2 || d->pixel_rows == 4 || d->pixel_rows == 8) &&
-           d->select_period >= 1 && d->bin_block >= 0 && d->bin_block % 32 == 0;
+           d->select_period >= 1 && d->bin_block >= 0 && d->bin_block % 32 == 0 && d->gw_segment >= 256 &&
+           d->gw_segment <= (1 << 30) && d->gw_segment % 256 == 0;
 }
 
 }  // namespace
@@ -293,6 +325,7 @@ void bgs_plan_desc_default(bgs_plan_desc *d) {
     d->pixel_rows = 2;
     d->select_period = 1000;
     d->bin_block = 0;
+    d->gw_segment = 2048;
 }
 
 int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out) {
@@ -408,6 +441,11 @@ size_t bgs_workspace_size(const bgs_plan *p, int64_t N, int64_t K, int64_t T, in
     s += 48 * N * 2;                    // packed records, gradient accumulators
     s += 4 * T;                         // work-list bucket slots
     s += 8 * T * (size_t)std::max(8, (256 + P - 1) / P);  // work items (16x16 tiles)
+    if ((int64_t)p->desc.heavy_threshold < K) {  // Gaussian-wise segments (AUTO)
+        const size_t groups = (256 + P - 1) / P;
+        const size_t extra = std::min<size_t>(groups * ((size_t)K / p->desc.gw_segment + 1), (size_t)1 << 24);
+        s += 8 * extra + 4 * T + (groups * T + extra) * P * 32;
+    }
     s += 64 << 20;                      // CUB temporaries (upper estimate)
     return s;
 }
@@ -466,7 +504,15 @@ int bgs_plan_reserve(bgs_plan *p, int64_t N, int64_t K, int64_t T, int64_t pixel
     BGS_TRY(ensure(p, p->grad_acc, sizeof(bgs::Rec) * N, s, "grad_acc"));
     const int P = p->desc.gw_pixels;
     BGS_TRY(ensure(p, p->tile_idx, 4 * T, s, "per-tile"));
-    BGS_TRY(ensure(p, p->items, 8 * T * (size_t)std::max(8, (256 + P - 1) / P), s, "items"));
+    // work items (16 x 16 tiles); with Gaussian-wise items possible in AUTO mode, the segment
+    // items and summaries too
+    const bool gauss = (int64_t)p->desc.heavy_threshold < K;
+    const long long extra = gauss ? gw_extra_cap(p, 16, 16, K) : 0;
+    BGS_TRY(ensure(p, p->items, 8 * (T * (size_t)std::max(8, (256 + P - 1) / P) + (size_t)extra), s, "items"));
+    if (gauss) {
+        BGS_TRY(ensure(p, p->gw_exoff, 4 * T, s, "gw_exoff"));
+        BGS_TRY(ensure(p, p->gw_sum, ((size_t)T * gw_groups(p, 16, 16) + (size_t)extra) * P * 32, s, "gw_sum"));
+    }
     // CUB temporaries: the largest of the depth sort, the N-scan, the tile sort and the tile scan
     size_t t[4] = {0, 0, 0, 0};
     const int64_t n1 = std::max<int64_t>(N, 1), k1 = std::max<int64_t>(K, 1);
@@ -833,15 +879,18 @@ int render_forward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewOu
     const int grid_g = grid_for(p, bgs::forward_gauss_kernel(a.gw_pixels), threads);
     const int grid_p = grid_for(p, bgs::forward_pixel_kernel(a.pixel_rows), threads);
     // AUTO with a threshold no list can exceed queues no Gaussian-wise item
-    const bool gauss = mode == BGS_MODE_GAUSSIAN ||
-                       (mode == BGS_MODE_AUTO && (int64_t)p->desc.heavy_threshold < num_entries);
+    const bool gauss = gauss_possible(p, mode, num_entries);
+    a.gw_exoff = gauss ? (const uint32_t *)p->gw_exoff.p : nullptr;
+    a.gw_sum = gauss ? (float4 *)p->gw_sum.p : nullptr;
     a.pass_blocks = (gauss ? grid_g : 0) + (mode != BGS_MODE_GAUSSIAN ? grid_p : 0);
     BGS_TRY(inject_pending_fault(p, s));
     KernelTimer kt(p, s, &p->ev_fwd);
     if (gauss) BGS_CUDA(bgs::launch_forward_gauss(a, grid_g, s), "forward_gauss");
     if (mode != BGS_MODE_GAUSSIAN) BGS_CUDA(bgs::launch_forward_pixel(a, grid_p, gauss, s), "forward_pixel");
+    if (gauss) BGS_CUDA(bgs::launch_forward_gw_merge(a, grid_for(p, bgs::forward_gw_merge_kernel(a.gw_pixels), threads), s),
+                        "forward_gw_merge");
     kt.stop();
-    p->host_launches += (gauss && mode != BGS_MODE_GAUSSIAN) ? 2 : 1;
+    p->host_launches += (gauss && mode != BGS_MODE_GAUSSIAN) ? 3 : (gauss ? 2 : 1);
     return BGS_OK;
 }
 
@@ -1413,6 +1462,14 @@ int bgs_autotune_render(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N
             if ((rc = run(d, t)) != BGS_OK) break;
             if (t < best_t) best_t = t, best = d;
         }
+    }
+    // stage 2b: segment length of the Gaussian-wise items, when the best uses them
+    for (int L : {512, 8192}) {
+        if (rc != BGS_OK || (int64_t)best.heavy_threshold >= num_entries) break;
+        d = best;
+        d.gw_segment = L;
+        if ((rc = run(d, t)) != BGS_OK) break;
+        if (t < best_t) best_t = t, best = d;
     }
     // stage 3: queue granularity
     for (int c : {2, 4}) {

@@ -12,9 +12,10 @@
 //                      first, then the pixel-wise ones; each kind has its own kernel (and
 //                      register budget) and its own queue cursor:
 //                        - Gaussian-wise (Sec. 4.2, Algorithm 6, fine-grained per
-//                          Sec. 4.3): P pixels of a tile processed one after another by
-//                          the whole warp, lanes splitting the list 32 entries at a time
-//                          and combining transmittance with a shuffle prefix product;
+//                          Sec. 4.3): P pixels of a tile, the lanes splitting a segment of
+//                          the list into contiguous chunks and composing them with a
+//                          shuffle prefix product; segments of one tile run on separate
+//                          warps and k_forward_gw_merge composes them per pixel;
 //                        - pixel-wise: an 8x8 sub-block of a tile, two pixels per lane,
 //                          walking the tile's list through a warp-private shared memory
 //                          window of 32 records.
@@ -266,58 +267,114 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
     }
 }
 
-// Gaussian-wise item: P pixels, lanes split the list 32 entries at a time.
-template <int P>
-__device__ __forceinline__ void gauss_item(const FwdArgs &a, int tile, int sub, int lane,
-                                           unsigned long long &st_eval, unsigned long long &st_acc) {
-    const TileGeom tg = tile_geom(a, tile);
+// ---- Gaussian-wise items (Sec. 4.2-4.3, Algorithm 6) ------------------------------------
+// The lanes of a warp split a tile's depth-sorted list and combine transmittance with a warp
+// prefix product, as in Algorithm 6, but at chunk granularity: each lane blends a contiguous
+// chunk of kGwChunk entries serially (its own transmittance starts at 1), then one prefix
+// product over the lanes composes the chunks with the over-operator
+// (C1, T1) o (C2, T2) = (C1 + T1 C2, T1 T2), once per round of 32 kGwChunk entries instead of
+// once per 32 entries.  The list is further cut into segments of gw_segment entries handled
+// by separate warps (cross-warp splitting of one pixel's list): a segment item walks its
+// segment for P pixels from transmittance 1 and writes each pixel's segment summary
+// (C, D, T, last contributor, contributing pairs).  k_forward_gw_merge then composes a
+// pixel's segments in list order and, in the segment where the composed transmittance falls
+// below 1e-4, walks the entries again one by one from the exact incoming transmittance with
+// Algorithm 5's rule, so the stop position, n_contrib and n_eval follow the sequential rule
+// (the composed products differ from the sequential chain by float32 reassociation only).
+constexpr int kGwChunk = 8;                 // entries a lane blends serially per round
+constexpr int kGwRound = 32 * kGwChunk;     // entries a warp covers per round
+constexpr int kGwIdx = kGwRound + kGwRound / kGwChunk;  // staged indices, skewed by one word per chunk
+
+struct GwSum {  // a pixel's summary of one segment (2 x 16 bytes)
+    float4 cd;  // colour and depth, accumulated with the segment's own transmittance from 1
+    float4 t;   // x = transmittance after the segment; y = last contributor (index in the
+                // tile's list, bits; -1: none); z = contributing pairs (bits); w = entries up
+                // to and including the stop (bits) when the pixel stopped in the segment, else 0
+};
+
+__device__ __forceinline__ void gw_item_pixel(const TileGeom &tg, int group, int P, int p, bool &ok, float &pxf,
+                                              float &pyf) {
     const int npix = tg.vw * tg.vh;
-    const uint2 rg = load_range(a, tile);
-    const int n = (int)(rg.y - rg.x);
-    float pxf[P], pyf[P], T[P], c0[P], c1[P], c2[P], D[P];
-    int last[P], neval[P], nacc[P];
-    bool done[P];
+    const int q = group * P + p;
+    ok = q < npix;
+    const int qq = ok ? q : 0;
+    pxf = (float)(tg.x0 + qq % tg.vw);
+    pyf = (float)(tg.y0 + qq / tg.vw);
+}
+
+// Walks entries [e0, e1) of a tile's list (which starts at list0) for the P pixels of a
+// Gaussian-wise item.  Per pixel p, on entry: Ts = transmittance in front of e0, live = still
+// walking; the lane accumulators (c0, c1, c2, d: this lane's share of colour and depth; nacc:
+// its contributing pairs) add to what they hold, last (warp-uniform) is the latest
+// contributor so far.  Per round each lane blends kGwChunk consecutive entries from a local
+// transmittance of 1; a shuffle prefix product over the lanes gives the transmittance in
+// front of each chunk.  When the round's composed transmittance falls below 1e-4:
+//   resolve = true (Ts exact): the lanes in front of the first lane whose product falls
+//     below 1e-4 compose as usual, and that lane walks the rest of the round entry by entry
+//     with Algorithm 5's rule from the transmittance in front of its chunk; the pixel stops
+//     at the first entry whose next transmittance is below 1e-4 (stop = entries up to and
+//     including it) -- if none does (float32 reassociation), the walk goes on;
+//   resolve = false: the pixel is left saturated (live = false, Ts < 1e-4), for the merge.
+template <int P>
+__device__ __forceinline__ void gw_walk(const FwdArgs &a, uint32_t e0, uint32_t e1, uint32_t list0, const float *pxf,
+                                        const float *pyf, bool resolve, uint32_t *idx_s, int lane, float *Ts,
+                                        float *ca0, float *ca1, float *ca2, float *da, int *last, int *nacc,
+                                        int *stop, bool *live) {
+    for (uint32_t base = e0; base < e1; base += (uint32_t)kGwRound) {
+        bool any = false;
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const int q = sub * P + p;
-        const bool ok = q < npix;
-        const int qq = ok ? q : 0;
-        pxf[p] = (float)(tg.x0 + qq % tg.vw);
-        pyf[p] = (float)(tg.y0 + qq / tg.vw);
-        T[p] = 1.f;
-        c0[p] = c1[p] = c2[p] = D[p] = 0.f;
-        last[p] = 0;
-        neval[p] = n;
-        nacc[p] = 0;
-        done[p] = !ok;
-    }
-    for (uint32_t base = rg.x; base < rg.y; base += 32) {
-        bool all_done = true;
+        for (int p = 0; p < P; ++p) any = any || live[p];
+        if (!any) break;
+        const uint32_t rend = (uint32_t)min((unsigned long long)e1, (unsigned long long)base + kGwRound);
+        // stage the round's indices (coalesced); entry m of the round sits at m + m / kGwChunk
+        __syncwarp();
 #pragma unroll
-        for (int p = 0; p < P; ++p) all_done = all_done && done[p];
-        if (all_done) break;
-        const uint32_t j = base + lane;
-        const bool inb = j < rg.y;
-        Rec r;
-        if (inb) {
-            r = load_rec(a, j);
-        } else {
-            r.a = make_float4(0.f, 0.f, 0.f, 0.f);
-            r.b = r.a;
-            r.c = r.a;
+        for (int k = 0; k < kGwChunk; ++k) {
+            const int m = 32 * k + lane;
+            const uint32_t j = base + (uint32_t)m;
+            idx_s[m + m / kGwChunk] = j < rend ? a.point_list[j] : 0u;
         }
-        const int pos0 = (int)(base - rg.x);
+        __syncwarp();
+        float Tl[P], c0[P], c1[P], c2[P], dl[P];
+        int ll[P], nl[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            if (done[p]) continue;  // warp-uniform
-            float dx, dy, G;
-            const float p2 = pair_power2(r.a, r.b.x, pxf[p], pyf[p], dx, dy);
-            const float al = pair_alpha(p2, r.b.y, G);
-            const bool valid = inb && p2 <= 0.f && al >= kAlphaMin;
-            const unsigned vmask = __ballot_sync(kFull, valid);
-            if (vmask == 0u) continue;  // no lane contributes: skip the scan (Algorithm 6's all-invalid test)
-            // inclusive prefix product of (1 - alpha) over the lanes (skipped lanes contribute 1)
-            float incl = valid ? 1.f - al : 1.f;
+            Tl[p] = 1.f;
+            c0[p] = c1[p] = c2[p] = dl[p] = 0.f;
+            ll[p] = -1;
+            nl[p] = 0;
+        }
+        const uint32_t jc = base + (uint32_t)(kGwChunk * lane);
+        for (int k = 0; k < kGwChunk; ++k) {
+            const uint32_t j = jc + (uint32_t)k;
+            if (j >= rend) break;
+            const uint32_t g = idx_s[kGwChunk * lane + k + lane];
+            if ((long long)g >= a.N) {
+                raise_check(a.ctrl, BGS_CHECK_INDEX);  // a transparent entry
+                continue;
+            }
+            const Rec r = a.recs[g];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                float dx, dy, G;
+                const float p2 = pair_power2(r.a, r.b.x, pxf[p], pyf[p], dx, dy);
+                const float al = pair_alpha(p2, r.b.y, G);
+                if (live[p] && p2 <= 0.f && al >= kAlphaMin) {
+                    const float w = al * Tl[p];
+                    c0[p] += w * r.c.x;
+                    c1[p] += w * r.c.y;
+                    c2[p] += w * r.c.z;
+                    dl[p] += w * r.c.w;
+                    Tl[p] = next_T(Tl[p], al);
+                    ll[p] = (int)(j - list0);
+                    ++nl[p];
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (!live[p]) continue;  // warp-uniform
+            float incl = Tl[p];
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const float v = __shfl_up_sync(kFull, incl, off);
@@ -325,54 +382,120 @@ __device__ __forceinline__ void gauss_item(const FwdArgs &a, int tile, int sub, 
             }
             float excl = __shfl_up_sync(kFull, incl, 1);
             if (lane == 0) excl = 1.f;
-            const float Tp = T[p];
-            const float tt = Tp * incl;  // transmittance after this lane's entry
-            // early stop (Algorithm 5's rule on the prefix-product T'): the first valid lane
-            // whose T' falls below 1e-4 stops the pixel and is not accumulated; the lanes
-            // before it are.  T' differs from the sequential FMA chain of the pixel-wise
-            // kernels by rounding only.
-            const unsigned smask = __ballot_sync(kFull, valid && tt < kTMin);
-            const int kstop = smask ? __ffs(smask) - 1 : 32;
-            const unsigned below = kstop >= 32 ? kFull : ((1u << kstop) - 1u);
-            const unsigned amask = vmask & below;
-            if (valid && lane < kstop) {
-                const float w = al * (Tp * excl);
-                c0[p] += w * r.c.x;
-                c1[p] += w * r.c.y;
-                c2[p] += w * r.c.z;
-                D[p] += w * r.c.w;
+            const float Tb = Ts[p] * excl;
+            const float Tround = Ts[p] * __shfl_sync(kFull, incl, 31);
+            if (Tround >= kTMin || !resolve) {
+                ca0[p] += Tb * c0[p];
+                ca1[p] += Tb * c1[p];
+                ca2[p] += Tb * c2[p];
+                da[p] += Tb * dl[p];
+                nacc[p] += nl[p];
+                last[p] = max(last[p], __reduce_max_sync(kFull, ll[p]));
+                Ts[p] = Tround;
+                // a pixel below 1e-4 from a transmittance of at most 1 stops within this
+                // segment: the rest of it is not needed
+                if (Tround < kTMin) live[p] = false;
+                continue;
             }
-            const float tnew = __shfl_sync(kFull, tt, kstop > 0 ? kstop - 1 : 0);
-            if (kstop > 0) T[p] = tnew;
-            if (amask) {
-                last[p] = pos0 + (32 - __clz(amask));
-                nacc[p] += __popc(amask);
+            // the crossing round: lanes in front of the first crossing chunk compose
+            const int lam = __ffs(__ballot_sync(kFull, Ts[p] * incl < kTMin)) - 1;
+            const bool front = lane < lam;
+            if (front) {
+                ca0[p] += Tb * c0[p];
+                ca1[p] += Tb * c1[p];
+                ca2[p] += Tb * c2[p];
+                da[p] += Tb * dl[p];
+                nacc[p] += nl[p];
             }
-            if (smask) {
-                done[p] = true;
-                neval[p] = pos0 + kstop + 1;
+            last[p] = max(last[p], __reduce_max_sync(kFull, front ? ll[p] : -1));
+            float T = __shfl_sync(kFull, Tb, lam);
+            int st = 0, lw = -1;
+            if (lane == lam) {
+                for (uint32_t j = jc; j < rend; ++j) {
+                    const uint32_t m = j - base;
+                    const uint32_t g = idx_s[m + m / kGwChunk];
+                    if ((long long)g >= a.N) continue;  // raised above
+                    const Rec r = a.recs[g];
+                    float dx, dy, G;
+                    const float p2 = pair_power2(r.a, r.b.x, pxf[p], pyf[p], dx, dy);
+                    const float al = pair_alpha(p2, r.b.y, G);
+                    if (p2 > 0.f || al < kAlphaMin) continue;
+                    const float tt = next_T(T, al);
+                    if (tt < kTMin) {
+                        st = (int)(j - list0 + 1u);
+                        break;
+                    }
+                    const float w = al * T;
+                    ca0[p] += w * r.c.x;
+                    ca1[p] += w * r.c.y;
+                    ca2[p] += w * r.c.z;
+                    da[p] += w * r.c.w;
+                    T = tt;
+                    lw = (int)(j - list0);
+                    ++nacc[p];
+                }
+            }
+            Ts[p] = __shfl_sync(kFull, T, lam);
+            last[p] = max(last[p], __shfl_sync(kFull, lw, lam));
+            st = __shfl_sync(kFull, st, lam);
+            if (st) {
+                stop[p] = st;
+                live[p] = false;
             }
         }
     }
-    // combine the lanes' partial sums and write the P pixels
+}
+
+__device__ __forceinline__ void warp_sum5(float &x0, float &x1, float &x2, float &x3, int &n) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 += __shfl_xor_sync(kFull, x0, o);
+        x1 += __shfl_xor_sync(kFull, x1, o);
+        x2 += __shfl_xor_sync(kFull, x2, o);
+        x3 += __shfl_xor_sync(kFull, x3, o);
+        n += __shfl_xor_sync(kFull, n, o);
+    }
+}
+
+// A Gaussian-wise segment item: P pixels of a tile over one segment of its list.  The first
+// segment starts from transmittance 1, which is exact, so its stops are resolved here; later
+// segments leave saturated pixels to the merge.
+template <int P>
+__device__ __forceinline__ void gw_segment_item(const FwdArgs &a, int tile, int sub, unsigned item, uint32_t *idx_s,
+                                                int lane) {
+    const TileGeom tg = tile_geom(a, tile);
+    const int groups = (tg.vw * tg.vh + P - 1) / P;
+    const int group = sub % groups, seg = sub / groups;
+    const uint2 rg = load_range(a, tile);
+    // segment size 0: the list is not split (one segment)
+    const unsigned int seg_len = *((volatile unsigned int *)&a.ctrl->gw_seg);
+    const unsigned long long L = seg_len ? (unsigned long long)seg_len : (1ull << 32);
+    const unsigned long long s0 = (unsigned long long)rg.x + (unsigned long long)seg * L;
+    const uint32_t e0 = (uint32_t)min((unsigned long long)rg.y, s0);
+    const uint32_t e1 = (uint32_t)min((unsigned long long)rg.y, s0 + L);
+    float pxf[P], pyf[P], Ts[P], ca0[P], ca1[P], ca2[P], da[P];
+    int last[P], nacc[P], stop[P];
+    bool live[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
+        bool ok;
+        gw_item_pixel(tg, group, P, p, ok, pxf[p], pyf[p]);
+        Ts[p] = 1.f;
+        ca0[p] = ca1[p] = ca2[p] = da[p] = 0.f;
+        last[p] = -1;
+        nacc[p] = stop[p] = 0;
+        live[p] = ok;
+    }
+    gw_walk<P>(a, e0, e1, rg.x, pxf, pyf, seg == 0, idx_s, lane, Ts, ca0, ca1, ca2, da, last, nacc, stop, live);
+    GwSum *out = reinterpret_cast<GwSum *>(a.gw_sum) + (size_t)item * P;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            c0[p] += __shfl_xor_sync(kFull, c0[p], o);
-            c1[p] += __shfl_xor_sync(kFull, c1[p], o);
-            c2[p] += __shfl_xor_sync(kFull, c2[p], o);
-            D[p] += __shfl_xor_sync(kFull, D[p], o);
-        }
-        const int q = sub * P + p;
-        if (q < npix) {
-            if (lane == p)
-                write_pixel(a, tg.v, (int)pxf[p], (int)pyf[p], T[p], c0[p], c1[p], c2[p], D[p], last[p],
-                            neval[p]);
-            if (lane == 0) {
-                st_eval += (unsigned long long)neval[p];
-                st_acc += (unsigned long long)nacc[p];
-            }
+    for (int p = 0; p < P; ++p) {
+        warp_sum5(ca0[p], ca1[p], ca2[p], da[p], nacc[p]);
+        if (lane == p) {
+            GwSum sm;
+            sm.cd = make_float4(ca0[p], ca1[p], ca2[p], da[p]);
+            sm.t = make_float4(Ts[p], __int_as_float(last[p]), __int_as_float(nacc[p]), __int_as_float(stop[p]));
+            out[p] = sm;
         }
     }
 }
@@ -391,19 +514,20 @@ __device__ __forceinline__ void flush_stats(const FwdArgs &a, int lane, unsigned
     }
 }
 
-// Gaussian-wise items [0, num_gauss) of the work list.  Launched first; lets the pixel-wise
-// kernel launch as soon as all its blocks are resident (programmatic dependent launch),
-// so that pixel-wise blocks take over SMs as Gaussian-wise blocks run out of items.
+// Gaussian-wise segment items [0, num_gauss) of the work list.  Launched first; lets the
+// pixel-wise kernel launch as soon as all its blocks are resident (programmatic dependent
+// launch), so that pixel-wise blocks take over SMs as Gaussian-wise blocks run out of items.
 template <int P>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_gauss(FwdArgs a) {
     asm volatile("griddepcontrol.launch_dependents;");
     __shared__ unsigned int blk[2];
+    __shared__ uint32_t idx_s[kWarpsPerBlock][kGwIdx];
     if (threadIdx.x == 0) blk[0] = blk[1] = 0u;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned num_items = a.ctrl->num_gauss;
     const unsigned chunk = (unsigned)a.chunk;
-    unsigned long long st_eval = 0, st_acc = 0, st_items = 0;
+    unsigned long long st_items = 0;
     while (true) {
         unsigned first = 0;
         if (lane == 0) first = atomicAdd(&a.ctrl->queue_head_g, chunk);
@@ -412,12 +536,96 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_gauss(FwdArgs a
         const unsigned end = min(first + chunk, num_items);
         for (unsigned it = first; it < end; ++it) {
             const uint2 item = a.items[it];
-            gauss_item<P>(a, (int)item.x, (int)(item.y & ~kKindGauss), lane, st_eval, st_acc);
+            gw_segment_item<P>(a, (int)item.x, (int)(item.y & ~kKindGauss), it, idx_s[warp], lane);
             ++st_items;
         }
     }
-    flush_stats(a, lane, st_eval, st_acc, st_items);
+    if (lane == 0) atomicAdd(&a.ctrl->items_done, st_items);
     if (lane == 0) finish_pass(a.ctrl, st_items, blk, kWarpsPerBlock, a.pass_blocks);
+}
+
+// A warp per first-segment item: for each of its P pixels, composes the segment summaries
+// in list order with (C1, T1) o (C2, T2) = (C1 + T1 C2, T1 T2) while the composed
+// transmittance stays >= 1e-4; a segment in which it would fall below is walked again from
+// the exact incoming transmittance with the stop resolved (gw_walk), after which the
+// composition goes on if the walk did not stop.  Writes the pixel's outputs and counts its
+// evaluated and contributing pairs.
+template <int P>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_gw_merge(FwdArgs a) {
+    __shared__ uint32_t idx_s[kWarpsPerBlock][kGwIdx];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned num_first = a.ctrl->num_gauss0;
+    const GwSum *sums = reinterpret_cast<const GwSum *>(a.gw_sum);
+    const uint32_t L = a.ctrl->gw_seg;
+    unsigned long long st_eval = 0, st_acc = 0;
+    for (unsigned it = blockIdx.x * kWarpsPerBlock + warp; it < num_first; it += gridDim.x * kWarpsPerBlock) {
+        const uint2 item = a.items[it];
+        const int tile = (int)item.x, sub = (int)(item.y & ~kKindGauss);
+        const TileGeom tg = tile_geom(a, tile);
+        const int groups = (tg.vw * tg.vh + P - 1) / P;
+        const uint2 rg = load_range(a, tile);
+        const uint32_t n = rg.y - rg.x;
+        const uint32_t S = (n == 0u || L == 0u) ? 1u : (n - 1u) / L + 1u;
+        // summary of segment sg >= 1: the tile's later-segment items, segment-major
+        const size_t later = S > 1u ? (size_t)num_first + a.gw_exoff[tile] + (size_t)sub : 0;
+        for (int p = 0; p < P; ++p) {
+            bool ok;
+            float pxf, pyf;
+            gw_item_pixel(tg, sub, P, p, ok, pxf, pyf);
+            if (!ok) break;
+            float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, D = 0.f;
+            int last = -1, nacc = 0, stop = 0;
+            for (uint32_t sg = 0; sg < S; ++sg) {
+                const size_t si = sg == 0u ? (size_t)it : later + (size_t)(sg - 1u) * groups;
+                const GwSum sm = sums[si * P + p];
+                const int sst = __float_as_int(sm.t.w);
+                if (sg == 0u && sst) {  // stopped in the first segment, resolved there
+                    T = sm.t.x;
+                    c0 = sm.cd.x, c1 = sm.cd.y, c2 = sm.cd.z, D = sm.cd.w;
+                    last = __float_as_int(sm.t.y);
+                    nacc = __float_as_int(sm.t.z);
+                    stop = sst;
+                    break;
+                }
+                if (T * sm.t.x >= kTMin) {
+                    c0 += T * sm.cd.x;
+                    c1 += T * sm.cd.y;
+                    c2 += T * sm.cd.z;
+                    D += T * sm.cd.w;
+                    T *= sm.t.x;
+                    last = max(last, __float_as_int(sm.t.y));
+                    nacc += __float_as_int(sm.t.z);
+                    continue;
+                }
+                const uint32_t e0 = S > 1u ? rg.x + sg * L : rg.x;
+                const uint32_t e1 = S > 1u ? (uint32_t)min((unsigned long long)rg.y, (unsigned long long)e0 + L) : rg.y;
+                float Tw = T, w0 = 0.f, w1 = 0.f, w2 = 0.f, wd = 0.f;
+                int lw = last, nw = 0, sw = 0;
+                bool live = true;
+                gw_walk<1>(a, e0, e1, rg.x, &pxf, &pyf, true, idx_s[warp], lane, &Tw, &w0, &w1, &w2, &wd, &lw, &nw,
+                           &sw, &live);
+                warp_sum5(w0, w1, w2, wd, nw);
+                c0 += w0, c1 += w1, c2 += w2, D += wd;
+                T = Tw;
+                last = lw;
+                nacc += nw;
+                if (sw) {
+                    stop = sw;
+                    break;
+                }
+            }
+            const int neval = stop ? stop : (int)n;
+            if (lane == 0) {
+                write_pixel(a, tg.v, (int)pxf, (int)pyf, T, c0, c1, c2, D, last + 1, neval);
+                st_eval += (unsigned long long)neval;
+                st_acc += (unsigned long long)nacc;
+            }
+        }
+    }
+    if (lane == 0 && (st_eval | st_acc)) {
+        atomicAdd(&a.ctrl->eval_pairs, st_eval);
+        atomicAdd(&a.ctrl->contrib_pairs, st_acc);
+    }
 }
 
 // Pixel-wise items [num_gauss, num_items) of the work list.
@@ -446,6 +654,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_pixel(FwdArgs a
     }
     flush_stats(a, lane, st_eval, st_acc, st_items);
     if (lane == 0) finish_pass(a.ctrl, st_items, blk, kWarpsPerBlock, a.pass_blocks);
+    // launched after k_forward_gauss with programmatic serialisation: complete only once the
+    // Gaussian-wise grid has (so that whatever follows on the stream, the merge included,
+    // sees its summaries); a no-op for an ordinary launch
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 int forward_balanced_block_threads() { return kWarpsPerBlock * 32; }
@@ -456,6 +668,16 @@ const void *forward_gauss_kernel(int gw_pixels) {
         case 2: return (const void *)k_forward_gauss<2>;
         case 4: return (const void *)k_forward_gauss<4>;
         case 8: return (const void *)k_forward_gauss<8>;
+        default: return nullptr;
+    }
+}
+
+const void *forward_gw_merge_kernel(int gw_pixels) {
+    switch (gw_pixels) {
+        case 1: return (const void *)k_forward_gw_merge<1>;
+        case 2: return (const void *)k_forward_gw_merge<2>;
+        case 4: return (const void *)k_forward_gw_merge<4>;
+        case 8: return (const void *)k_forward_gw_merge<8>;
         default: return nullptr;
     }
 }
@@ -477,6 +699,17 @@ cudaError_t launch_forward_gauss(const FwdArgs &a, int grid, cudaStream_t s) {
         case 2: k_forward_gauss<2><<<grid, threads, 0, s>>>(a); break;
         case 4: k_forward_gauss<4><<<grid, threads, 0, s>>>(a); break;
         case 8: k_forward_gauss<8><<<grid, threads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_gw_merge(const FwdArgs &a, int grid, cudaStream_t s) {
+    switch (a.gw_pixels) {
+        case 1: k_forward_gw_merge<1><<<grid, kWarpsPerBlock * 32, 0, s>>>(a); break;
+        case 2: k_forward_gw_merge<2><<<grid, kWarpsPerBlock * 32, 0, s>>>(a); break;
+        case 4: k_forward_gw_merge<4><<<grid, kWarpsPerBlock * 32, 0, s>>>(a); break;
+        case 8: k_forward_gw_merge<8><<<grid, kWarpsPerBlock * 32, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -5,8 +5,12 @@
 // between the Gaussian-wise and the pixel-wise kernel.  Here the choice is made per
 // tile from its list length n (the paper names "the Gaussians of a tile" as the key
 // load-balance metric, Sec. 4.4):
-//   n >  heavy_threshold -> Gaussian-wise items of P pixels (one warp each),
+//   n >  heavy_threshold -> Gaussian-wise items of P pixels (one warp each), and, for a list
+//                           longer than gw_segment entries, one item per further segment
+//                           of gw_segment entries and P pixels (the cross-warp split),
 //   n <= heavy_threshold -> pixel-wise items of 8 x 4Q pixels (one warp, Q pixels per lane).
+// The work list holds the Gaussian-wise first-segment items, then the later-segment items,
+// then the pixel-wise items.
 // Tiles of all views of a batched call share one global tile space.
 // Items of heavier tiles are queued first (longest-processing-time order) so the long
 // items start early and the light ones fill the tail.
@@ -20,7 +24,8 @@ __device__ __forceinline__ bool tile_is_gauss(int mode, int heavy_threshold, uin
     return mode == BGS_MODE_GAUSSIAN || (mode == BGS_MODE_AUTO && n > (uint32_t)heavy_threshold);
 }
 
-// Items of tile t: Gaussian-wise, P pixels each; else pixel-wise sub-blocks of its visible part.
+// Items of tile t: Gaussian-wise (first segments), P pixels each; else pixel-wise sub-blocks of
+// its visible part.
 __device__ __forceinline__ uint32_t tile_items(int t, bool gauss, const ViewTable &vt, int tile_w, int tile_h,
                                                int gw_pixels, int pixel_rows) {
     const int v = view_of(vt, t);
@@ -30,6 +35,13 @@ __device__ __forceinline__ uint32_t tile_items(int t, bool gauss, const ViewTabl
     if (gauss) return (uint32_t)((vw * vh + gw_pixels - 1) / gw_pixels);
     const int iw = pix_item_w(pixel_rows), ih = pix_item_h(pixel_rows);
     return (uint32_t)(((vw + iw - 1) / iw) * ((vh + ih - 1) / ih));
+}
+
+// Later-segment items of a Gaussian-wise tile with first-segment items `groups` and list
+// length n: one per (segment after the first, pixel group).
+__device__ __forceinline__ unsigned long long tile_extra(bool gauss, uint32_t groups, uint32_t n, int gw_segment) {
+    if (!gauss || gw_segment <= 0 || n <= (uint32_t)gw_segment) return 0ull;
+    return (unsigned long long)groups * (unsigned long long)((n - 1u) / (uint32_t)gw_segment);
 }
 
 // The list is ordered by a descending 8-bit key per tile: its kind in the top bit (Gaussian-
@@ -58,27 +70,45 @@ __device__ __forceinline__ uint32_t wl_sort_key(uint32_t n, bool gauss, int lpt)
 
 // Per block: items per key in shared memory (a tile's slot within its block's share is the
 // atomic's old value), then one global atomic per key gives the block's share its place in
-// the key's bucket.  The last block to finish reads the totals (clearing them for the next
-// build), scans them in descending key order into the buckets' first items and publishes
-// the list's item counts and queue cursors.
+// the key's bucket; a block scan of the tiles' later-segment items and one global atomic
+// give each tile its later-segment offset.  The last block to finish reads the totals
+// (clearing them for the next build), scans them in descending key order into the buckets'
+// first items and publishes the list's item counts and queue cursors.  When the
+// later-segment items exceed extra_cap, no list is split (segment size 0).
 __global__ void __launch_bounds__(kWlcThreads) k_wl_count(const uint2 *__restrict__ ranges, int T, const ViewTable vt,
                                                            int tile_w, int tile_h, int mode, int heavy_threshold,
-                                                           int lpt, int gw_pixels, int pixel_rows,
-                                                           uint32_t *__restrict__ slot, DevCtrl *ctrl) {
+                                                           int lpt, int gw_pixels, int pixel_rows, int gw_segment,
+                                                           long long extra_cap, uint32_t *__restrict__ slot,
+                                                           uint32_t *__restrict__ exoff, DevCtrl *ctrl) {
     using Scan = cub::BlockScan<uint32_t, kWlcThreads>;
-    __shared__ typename Scan::TempStorage scan_tmp;
+    using Scan64 = cub::BlockScan<unsigned long long, kWlcThreads>;
+    __shared__ union {
+        typename Scan::TempStorage s32;
+        typename Scan64::TempStorage s64;
+    } scan_tmp;
     __shared__ uint32_t s_cnt[256], s_base[256];
+    __shared__ unsigned long long s_xbase;
     __shared__ bool s_last;
     s_cnt[threadIdx.x] = 0u;
     __syncthreads();
     const int t = blockIdx.x * kWlcThreads + threadIdx.x;
     uint32_t key = 0u, local = 0u;
+    unsigned long long extra = 0ull;
     if (t < T) {
         const uint2 rg = ranges[t];
         const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
         const bool gauss = tile_is_gauss(mode, heavy_threshold, n);
         key = wl_sort_key(n, gauss, lpt);
-        local = atomicAdd(&s_cnt[key], tile_items(t, gauss, vt, tile_w, tile_h, gw_pixels, pixel_rows));
+        const uint32_t c = tile_items(t, gauss, vt, tile_w, tile_h, gw_pixels, pixel_rows);
+        local = atomicAdd(&s_cnt[key], c);
+        extra = tile_extra(gauss, c, n, gw_segment);
+    }
+    if (gw_segment > 0) {  // grid-uniform
+        unsigned long long xoff, xtotal;
+        Scan64(scan_tmp.s64).ExclusiveSum(extra, xoff, xtotal);
+        if (threadIdx.x == 0) s_xbase = xtotal ? atomicAdd(&ctrl->wl_extra, xtotal) : 0ull;
+        __syncthreads();
+        if (t < T) exoff[t] = (uint32_t)(s_xbase + xoff);  // used only when the total fits extra_cap
     }
     __syncthreads();
     {
@@ -93,20 +123,31 @@ __global__ void __launch_bounds__(kWlcThreads) k_wl_count(const uint2 *__restric
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    if (threadIdx.x == 0) {
+        const unsigned long long E = gw_segment > 0 ? atomicExch(&ctrl->wl_extra, 0ull) : 0ull;
+        const bool split = gw_segment > 0 && E <= (unsigned long long)extra_cap;
+        s_xbase = split ? E : 0ull;
+        ctrl->gw_seg = split ? (unsigned int)gw_segment : 0u;
+    }
+    __syncthreads();
+    const uint32_t E = (uint32_t)s_xbase;
     // thread i takes key 255 - i, so the scan runs in descending key order
     const int k = kWlcThreads - 1 - (int)threadIdx.x;
     const uint32_t c = atomicExch(&ctrl->wl_cnt[k], 0u);
     uint32_t off, total;
-    Scan(scan_tmp).ExclusiveSum(c, off, total);
-    ctrl->wl_off[k] = off;
-    // Gaussian-wise keys (kind bit set) are the largest: the first pixel-wise key's offset
-    // is the number of Gaussian-wise items
-    if (k == (lpt ? 127 : 0)) {
-        ctrl->num_gauss = off;
-        ctrl->queue_head = off;
+    Scan(scan_tmp.s32).ExclusiveSum(c, off, total);
+    // Gaussian-wise keys (kind bit set) are the largest; the pixel-wise buckets follow the
+    // later-segment items, and the first pixel-wise key's offset is the number of
+    // first-segment items
+    const int pix_top = lpt ? 127 : 0;
+    ctrl->wl_off[k] = k <= pix_top ? off + E : off;
+    if (k == pix_top) {
+        ctrl->num_gauss0 = off;
+        ctrl->num_gauss = off + E;
+        ctrl->queue_head = off + E;
     }
     if (threadIdx.x == 0) {
-        ctrl->num_items = total;
+        ctrl->num_items = total + E;
         ctrl->queue_head_g = 0u;
         ctrl->pass_items = 0u;
         ctrl->warps_done = 0u;
@@ -114,11 +155,14 @@ __global__ void __launch_bounds__(kWlcThreads) k_wl_count(const uint2 *__restric
     }
 }
 
-// A thread per tile writes the tile's items at its bucket's first item + its slot.
+// A thread per tile writes the tile's items at its bucket's first item + its slot, and its
+// later-segment items (sub-item index = segment * groups + group, segment >= 1) at
+// num_gauss0 + its offset.
 __global__ void __launch_bounds__(256) k_wl_emit(const uint2 *__restrict__ ranges, int T, const ViewTable vt,
                                                  int tile_w, int tile_h, int mode, int heavy_threshold, int lpt,
                                                  int gw_pixels, int pixel_rows, const uint32_t *__restrict__ slot,
-                                                 uint2 *__restrict__ items, long long capacity, DevCtrl *ctrl) {
+                                                 const uint32_t *__restrict__ exoff, uint2 *__restrict__ items,
+                                                 long long capacity, DevCtrl *ctrl) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     const uint2 rg = ranges[t];
@@ -132,19 +176,29 @@ __global__ void __launch_bounds__(256) k_wl_emit(const uint2 *__restrict__ range
     }
     const uint32_t kindbit = gauss ? kKindGauss : 0u;
     for (uint32_t q = 0; q < c; ++q) items[pos + q] = make_uint2((uint32_t)t, kindbit | q);
+    const int seg = (int)ctrl->gw_seg;
+    const unsigned long long x = tile_extra(gauss, c, n, seg);
+    if (x == 0ull) return;
+    const long long xpos = (long long)ctrl->num_gauss0 + exoff[t];
+    if (xpos + (long long)x > capacity) {
+        raise_check(ctrl, BGS_CHECK_OVERFLOW);
+        return;
+    }
+    for (uint32_t q = 0; q < (uint32_t)x; ++q) items[xpos + q] = make_uint2((uint32_t)t, kKindGauss | (c + q));
 }
 
 cudaError_t launch_worklist_buckets(const uint2 *ranges, int num_tiles, const ViewTable &vt, int tile_w, int tile_h,
                                     int mode, int heavy_threshold, int lpt, int gw_pixels, int pixel_rows,
-                                    uint32_t *slot, uint2 *items, long long capacity, DevCtrl *ctrl, cudaStream_t s) {
-    if (num_tiles < 0) return cudaErrorInvalidValue;
+                                    int gw_segment, long long extra_cap, uint32_t *slot, uint32_t *exoff,
+                                    uint2 *items, long long capacity, DevCtrl *ctrl, cudaStream_t s) {
+    if (num_tiles < 0 || (gw_segment > 0 && !exoff)) return cudaErrorInvalidValue;
     const int blocks = num_tiles > 0 ? (num_tiles + kWlcThreads - 1) / kWlcThreads : 1;
     k_wl_count<<<blocks, kWlcThreads, 0, s>>>(ranges, num_tiles, vt, tile_w, tile_h, mode, heavy_threshold, lpt,
-                                              gw_pixels, pixel_rows, slot, ctrl);
+                                              gw_pixels, pixel_rows, gw_segment, extra_cap, slot, exoff, ctrl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || num_tiles == 0) return e;
     k_wl_emit<<<(num_tiles + 255) / 256, 256, 0, s>>>(ranges, num_tiles, vt, tile_w, tile_h, mode, heavy_threshold,
-                                                      lpt, gw_pixels, pixel_rows, slot, items, capacity, ctrl);
+                                                      lpt, gw_pixels, pixel_rows, slot, exoff, items, capacity, ctrl);
     return cudaGetLastError();
 }
 

@@ -53,7 +53,7 @@ class Plan:
 
     def __init__(self, heavy_threshold: int = 512, gw_pixels: int = 4, queue_chunk: int = 1,
                  blocks_per_sm: int = 0, lpt_order: bool = True, device=None, pixel_rows: int = 2,
-                 select_period: int = 1000, bin_block: int = 0):
+                 select_period: int = 1000, bin_block: int = 0, gw_segment: int = 2048):
         self._lib = _lib.load()
         if device is None:
             device = torch.cuda.current_device()
@@ -65,6 +65,7 @@ class Plan:
         d.pixel_rows = pixel_rows
         d.select_period = select_period
         d.bin_block = bin_block
+        d.gw_segment = gw_segment
         h = ctypes.c_void_p()
         check(self._lib.bgs_plan_create(ctypes.byref(d), ctypes.byref(h)), "bgs_plan_create")
         self.handle = h

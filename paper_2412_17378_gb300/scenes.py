@@ -23,7 +23,7 @@ import math
 import numpy as np
 
 __all__ = ["camera", "look_at_camera", "scene_config", "CONFIGS", "frustum_uniform",
-           "cluster_points", "arc_cameras", "target_image"]
+           "cluster_points", "veil_points", "arc_cameras", "target_image"]
 
 
 def camera(W: int, H: int, viewmat=None, fx: float | None = None, fy: float | None = None,
@@ -199,6 +199,37 @@ def _config5(scale=1.0, sigma_c=(0.25, 0.2, 0.15)):
     return dict(name=f"cfg5_4k+8x1080p_{N}", gaussians=g, cameras=cams, backward=True)
 
 
+def veil_points(rng, n: int, W: int, H: int, u0: float, v0: float, half: float, z_lo=2.0, z_hi=6.0):
+    """Points whose projections fall uniformly in the (2 half)^2 pixel window centred on
+    (u0, v0) of the identity camera (fx = fy = W), depth z ~ U[z_lo, z_hi]."""
+    z = rng.uniform(z_lo, z_hi, n)
+    u = rng.uniform(u0 - half, u0 + half, n)
+    v = rng.uniform(v0 - half, v0 + half, n)
+    f = float(W)
+    return np.stack([(u - (W - 1) / 2.0) / f * z, (v - (H - 1) / 2.0) / f * z, z], 1)
+
+
+def _heavy(scale=1.0, W=1920, H=1080):
+    """A frame with a few ultra-heavy tiles: config 2's clustered scene at a fifth of its
+    Gaussians, plus a veil of 100k faint Gaussians (opacity U[0.001, 0.0045], most of
+    their pairs below the 1/255 cut; projected sigma ~ 5 px) over a 48 x 48 pixel window
+    in front of the scene (z in [1, 1.9]).  The ~35 tiles under the veil get lists of
+    tens of thousands of entries, and their pixels walk through the whole veil (its
+    transmittance stays near 0.5) before the scene behind it stops them, while the rest
+    of the frame is light: the workload for which the paper's Gaussian-wise parallelism
+    is meant (Sec. 4.2)."""
+    rng = np.random.default_rng(6)
+    Nb = max(1, int(200_000 * scale))
+    Nv = max(1, int(100_000 * scale))
+    bg = _clustered(rng, Nb, W, H)
+    veil = veil_points(rng, Nv, W, H, 0.62 * W, 0.4 * H, 24.0, 1.0, 1.9)
+    means = np.concatenate([bg, veil])
+    ls = np.concatenate([rng.normal(-4.0, 0.7, (Nb, 3)), rng.normal(-5.6, 0.15, (Nv, 3))])
+    op = np.concatenate([_sigmoid(rng.normal(0, 1.5, Nb)), rng.uniform(0.001, 0.0045, Nv)])
+    g = _gaussians(means, ls, _quats(rng, Nb + Nv), op, rng.uniform(0, 1, (Nb + Nv, 3)))
+    return dict(name=f"heavy_{W}x{H}_{Nb}+{Nv}veil", gaussians=g, cameras=[camera(W, H)], backward=True)
+
+
 def fd_crop_scene(seed: int = 5, n: int = 512, size: int = 64):
     """512 Gaussians whose centres fall in a 64x64 crop, rendered as a 64x64 image: the
     camera's principal point is shifted so that the crop becomes the whole image."""
@@ -223,6 +254,7 @@ CONFIGS = {
     "cfg3late": lambda scale=1.0: _config3("late", scale),
     "cfg4": _config4,
     "cfg5": _config5,
+    "heavy": _heavy,
     "fdcrop": lambda scale=1.0: fd_crop_scene(),
 }
 

@@ -47,7 +47,7 @@ def test_host_only_calls():
     d = _lib.PlanDesc()
     lib.bgs_plan_desc_default(ctypes.byref(d))
     assert (d.heavy_threshold, d.gw_pixels, d.queue_chunk, d.lpt_order, d.device, d.pixel_rows,
-            d.select_period, d.bin_block) == (512, 4, 1, 1, -1, 2, 1000, 0)
+            d.select_period, d.bin_block, d.gw_segment) == (512, 4, 1, 1, -1, 2, 1000, 0, 2048)
     assert lib.bgs_workspace_size(None, 10, 10, 10, 10) == 0
     # NULL output pointer is rejected before any CUDA call
     assert lib.bgs_plan_create(ctypes.byref(d), None) == _lib.BGS_ERR_INVALID
@@ -62,6 +62,11 @@ def test_host_only_calls():
     d.bin_block = 0
     d.gw_pixels = 3
     assert lib.bgs_plan_create(ctypes.byref(d), ctypes.byref(h)) == _lib.BGS_ERR_INVALID
+    d.gw_pixels = 4
+    for bad in (0, 128, 1000):  # segment lengths are multiples of 256
+        d.gw_segment = bad
+        assert lib.bgs_plan_create(ctypes.byref(d), ctypes.byref(h)) == _lib.BGS_ERR_INVALID
+    d.gw_segment = 2048
     # the selector query rejects a NULL plan
     assert lib.bgs_plan_selector(None, None, None, None, None, None) == _lib.BGS_ERR_INVALID
     # argument checks of the entry points run before any device work
