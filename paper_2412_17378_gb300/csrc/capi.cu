@@ -301,7 +301,7 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
 
 bool valid_desc(const bgs_plan_desc *d) {
     return d->heavy_threshold >= 0 && (d->gw_pixels == 1 || d->gw_pixels == 2 || d->gw_pixels == 4 ||
-                                       d->gw_pixels == 8) &&
+                                       d->gw_pixels == 8 || d->gw_pixels == 16) &&
            d->queue_chunk >= 1 && d->queue_chunk <= 1024 && d->blocks_per_sm >= 0 && d->blocks_per_sm <= 64 &&
            (d->pixel_rows == 1 || d->pixel_rows == 2 || d->pixel_rows == 4 || d->pixel_rows == 8) &&
            d->select_period >= 1 && d->bin_block >= 0 && d->bin_block % 32 == 0 && d->gw_segment >= 256 &&
@@ -1455,7 +1455,7 @@ int bgs_autotune_render(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N
     // stage 2: heavy-tile threshold and pixels per Gaussian-wise item
     for (int thr : {256, 1024, 4096, 16384}) {
         if (rc != BGS_OK) break;
-        for (int P : {2, 4}) {
+        for (int P : {4, 8, 16}) {
             d = best;
             d.heavy_threshold = thr;
             d.gw_pixels = P;

@@ -268,22 +268,42 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
 }
 
 // ---- Gaussian-wise items (Sec. 4.2-4.3, Algorithm 6) ------------------------------------
-// The lanes of a warp split a tile's depth-sorted list and combine transmittance with a warp
-// prefix product, as in Algorithm 6, but at chunk granularity: each lane blends a contiguous
-// chunk of kGwChunk entries serially (its own transmittance starts at 1), then one prefix
-// product over the lanes composes the chunks with the over-operator
-// (C1, T1) o (C2, T2) = (C1 + T1 C2, T1 T2), once per round of 32 kGwChunk entries instead of
-// once per 32 entries.  The list is further cut into segments of gw_segment entries handled
-// by separate warps (cross-warp splitting of one pixel's list): a segment item walks its
-// segment for P pixels from transmittance 1 and writes each pixel's segment summary
-// (C, D, T, last contributor, contributing pairs).  k_forward_gw_merge then composes a
-// pixel's segments in list order and, in the segment where the composed transmittance falls
-// below 1e-4, walks the entries again one by one from the exact incoming transmittance with
-// Algorithm 5's rule, so the stop position, n_contrib and n_eval follow the sequential rule
-// (the composed products differ from the sequential chain by float32 reassociation only).
-constexpr int kGwChunk = 8;                 // entries a lane blends serially per round
-constexpr int kGwRound = 32 * kGwChunk;     // entries a warp covers per round
-constexpr int kGwIdx = kGwRound + kGwRound / kGwChunk;  // staged indices, skewed by one word per chunk
+// The lanes of a warp split a tile's depth-sorted list and combine transmittance with a
+// prefix product over lanes, as in Algorithm 6, but at chunk granularity: each lane blends a
+// contiguous chunk of kGwChunk entries serially (its own transmittance starts at 1), then a
+// prefix product composes the chunks with the over-operator
+// (C1, T1) o (C2, T2) = (C1 + T1 C2, T1 T2), once per round instead of once per entry.
+// An item covers P pixels: the warp's lanes are PXL pixel-lanes x NCH = 32 / PXL chunk-lanes,
+// each lane holding PPL of the item's pixels, so that the PXL lanes of one chunk read the same
+// records (one gather serves PXL x PPL pixels) and a round covers NCH chunks.  The list is
+// further cut into segments of gw_segment entries handled by separate warps (cross-warp
+// splitting of one pixel's list): a segment item walks its segment for its P pixels from
+// transmittance 1 and writes each pixel's segment summary (C, D, T, last contributor,
+// contributing pairs).  k_forward_gw_merge then composes a pixel's segments in list order
+// and, in the segment where the composed transmittance falls below 1e-4, walks the entries
+// again one by one from the exact incoming transmittance with Algorithm 5's rule, so the
+// stop position, n_contrib and n_eval follow the sequential rule (the composed products
+// differ from the sequential chain by float32 reassociation only).
+constexpr int kGwChunk = 8;                          // entries a lane blends serially per round
+constexpr int kGwIdx = 32 * kGwChunk + 32;           // staged indices of the largest round, skewed
+
+template <int P>
+struct GwShape {
+    static constexpr int PPL = P >= 2 ? 2 : 1;  // pixels per lane
+    static constexpr int PXL = P / PPL;         // pixel-lanes
+    static_assert(PXL * PPL == P && 32 % PXL == 0, "pixels per Gaussian-wise item: 1, 2, 4, 8 or 16");
+};
+
+// Lanes pl, pl + PXL, pl + 2 PXL, ...: the chunk-lanes of pixel-lane pl.
+template <int PXL>
+__device__ __forceinline__ unsigned gw_group_mask(int pl) {
+    constexpr unsigned pat = PXL == 1 ? 0xffffffffu
+                           : PXL == 2 ? 0x55555555u
+                           : PXL == 4 ? 0x11111111u
+                           : PXL == 8 ? 0x01010101u
+                                      : 0x00010001u;
+    return pat << pl;
+}
 
 struct GwSum {  // a pixel's summary of one segment (2 x 16 bytes)
     float4 cd;  // colour and depth, accumulated with the segment's own transmittance from 1
@@ -302,60 +322,65 @@ __device__ __forceinline__ void gw_item_pixel(const TileGeom &tg, int group, int
     pyf = (float)(tg.y0 + qq / tg.vw);
 }
 
-// Walks entries [e0, e1) of a tile's list (which starts at list0) for the P pixels of a
-// Gaussian-wise item.  Per pixel p, on entry: Ts = transmittance in front of e0, live = still
-// walking; the lane accumulators (c0, c1, c2, d: this lane's share of colour and depth; nacc:
-// its contributing pairs) add to what they hold, last (warp-uniform) is the latest
-// contributor so far.  Per round each lane blends kGwChunk consecutive entries from a local
-// transmittance of 1; a shuffle prefix product over the lanes gives the transmittance in
-// front of each chunk.  When the round's composed transmittance falls below 1e-4:
-//   resolve = true (Ts exact): the lanes in front of the first lane whose product falls
+// Walks entries [e0, e1) of a tile's list (which starts at list0) for a lane's PPL pixels of
+// a Gaussian-wise item laid out as PXL pixel-lanes x (32 / PXL) chunk-lanes.  Per pixel p, on
+// entry: Ts = transmittance in front of e0, live = still walking (both the same on the
+// chunk-lanes of a pixel); the lane accumulators (c0, c1, c2, d: this lane's share of colour
+// and depth; nacc: its contributing pairs) add to what they hold, last (the same on the
+// pixel's lanes) is the latest contributor so far.  Per round each chunk-lane blends kGwChunk
+// consecutive entries from a local transmittance of 1; a shuffle prefix product over the
+// pixel's chunk-lanes gives the transmittance in front of each chunk.  When the round's
+// composed transmittance falls below 1e-4:
+//   resolve = true (Ts exact): the chunk-lanes in front of the first one whose product falls
 //     below 1e-4 compose as usual, and that lane walks the rest of the round entry by entry
 //     with Algorithm 5's rule from the transmittance in front of its chunk; the pixel stops
 //     at the first entry whose next transmittance is below 1e-4 (stop = entries up to and
 //     including it) -- if none does (float32 reassociation), the walk goes on;
 //   resolve = false: the pixel is left saturated (live = false, Ts < 1e-4), for the merge.
-template <int P>
+template <int PXL, int PPL>
 __device__ __forceinline__ void gw_walk(const FwdArgs &a, uint32_t e0, uint32_t e1, uint32_t list0, const float *pxf,
                                         const float *pyf, bool resolve, uint32_t *idx_s, int lane, float *Ts,
                                         float *ca0, float *ca1, float *ca2, float *da, int *last, int *nacc,
                                         int *stop, bool *live) {
-    for (uint32_t base = e0; base < e1; base += (uint32_t)kGwRound) {
+    constexpr int NCH = 32 / PXL, RND = NCH * kGwChunk;
+    const int pl = lane % PXL, ch = lane / PXL;
+    const unsigned gmask = gw_group_mask<PXL>(pl);
+    const int src_last = (NCH - 1) * PXL + pl;  // the pixel's last chunk-lane
+    for (uint32_t base = e0; base < e1; base += (uint32_t)RND) {
         bool any = false;
 #pragma unroll
-        for (int p = 0; p < P; ++p) any = any || live[p];
-        if (!any) break;
-        const uint32_t rend = (uint32_t)min((unsigned long long)e1, (unsigned long long)base + kGwRound);
+        for (int p = 0; p < PPL; ++p) any = any || live[p];
+        if (!__any_sync(kFull, any)) break;
+        const uint32_t rend = (uint32_t)min((unsigned long long)e1, (unsigned long long)base + RND);
         // stage the round's indices (coalesced); entry m of the round sits at m + m / kGwChunk
         __syncwarp();
 #pragma unroll
-        for (int k = 0; k < kGwChunk; ++k) {
-            const int m = 32 * k + lane;
+        for (int m = lane; m < RND; m += 32) {
             const uint32_t j = base + (uint32_t)m;
             idx_s[m + m / kGwChunk] = j < rend ? a.point_list[j] : 0u;
         }
         __syncwarp();
-        float Tl[P], c0[P], c1[P], c2[P], dl[P];
-        int ll[P], nl[P];
+        float Tl[PPL], c0[PPL], c1[PPL], c2[PPL], dl[PPL];
+        int ll[PPL], nl[PPL];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
+        for (int p = 0; p < PPL; ++p) {
             Tl[p] = 1.f;
             c0[p] = c1[p] = c2[p] = dl[p] = 0.f;
             ll[p] = -1;
             nl[p] = 0;
         }
-        const uint32_t jc = base + (uint32_t)(kGwChunk * lane);
+        const uint32_t jc = base + (uint32_t)(kGwChunk * ch);
         for (int k = 0; k < kGwChunk; ++k) {
             const uint32_t j = jc + (uint32_t)k;
             if (j >= rend) break;
-            const uint32_t g = idx_s[kGwChunk * lane + k + lane];
+            const uint32_t g = idx_s[kGwChunk * ch + k + ch];
             if ((long long)g >= a.N) {
                 raise_check(a.ctrl, BGS_CHECK_INDEX);  // a transparent entry
                 continue;
             }
             const Rec r = a.recs[g];
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
+            for (int p = 0; p < PPL; ++p) {
                 float dx, dy, G;
                 const float p2 = pair_power2(r.a, r.b.x, pxf[p], pyf[p], dx, dy);
                 const float al = pair_alpha(p2, r.b.y, G);
@@ -372,34 +397,22 @@ __device__ __forceinline__ void gw_walk(const FwdArgs &a, uint32_t e0, uint32_t 
             }
         }
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            if (!live[p]) continue;  // warp-uniform
+        for (int p = 0; p < PPL; ++p) {
             float incl = Tl[p];
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const float v = __shfl_up_sync(kFull, incl, off);
-                if (lane >= off) incl *= v;
+            for (int off = 1; off < NCH; off <<= 1) {
+                const float v = __shfl_up_sync(kFull, incl, off * PXL);
+                if (ch >= off) incl *= v;
             }
-            float excl = __shfl_up_sync(kFull, incl, 1);
-            if (lane == 0) excl = 1.f;
+            float excl = __shfl_up_sync(kFull, incl, PXL);
+            if (ch == 0) excl = 1.f;
             const float Tb = Ts[p] * excl;
-            const float Tround = Ts[p] * __shfl_sync(kFull, incl, 31);
-            if (Tround >= kTMin || !resolve) {
-                ca0[p] += Tb * c0[p];
-                ca1[p] += Tb * c1[p];
-                ca2[p] += Tb * c2[p];
-                da[p] += Tb * dl[p];
-                nacc[p] += nl[p];
-                last[p] = max(last[p], __reduce_max_sync(kFull, ll[p]));
-                Ts[p] = Tround;
-                // a pixel below 1e-4 from a transmittance of at most 1 stops within this
-                // segment: the rest of it is not needed
-                if (Tround < kTMin) live[p] = false;
-                continue;
-            }
-            // the crossing round: lanes in front of the first crossing chunk compose
-            const int lam = __ffs(__ballot_sync(kFull, Ts[p] * incl < kTMin)) - 1;
-            const bool front = lane < lam;
+            const float Tround = Ts[p] * __shfl_sync(kFull, incl, src_last);
+            // the same on the pixel's chunk-lanes
+            const bool cross = resolve && live[p] && Tround < kTMin;
+            const unsigned bal = __ballot_sync(kFull, cross && Ts[p] * incl < kTMin) & gmask;
+            const int lam = cross ? __ffs(bal) - 1 : lane;
+            const bool front = live[p] && (!cross || lane < lam);
             if (front) {
                 ca0[p] += Tb * c0[p];
                 ca1[p] += Tb * c1[p];
@@ -407,10 +420,14 @@ __device__ __forceinline__ void gw_walk(const FwdArgs &a, uint32_t e0, uint32_t 
                 da[p] += Tb * dl[p];
                 nacc[p] += nl[p];
             }
-            last[p] = max(last[p], __reduce_max_sync(kFull, front ? ll[p] : -1));
-            float T = __shfl_sync(kFull, Tb, lam);
+            int lmax = front ? ll[p] : -1;
+#pragma unroll
+            for (int off = PXL; off < 32; off <<= 1) lmax = max(lmax, __shfl_xor_sync(kFull, lmax, off));
+            last[p] = max(last[p], lmax);
+            // the crossing chunk-lane walks the rest of the round for this pixel
+            float T = Tb;
             int st = 0, lw = -1;
-            if (lane == lam) {
+            if (cross && lane == lam) {
                 for (uint32_t j = jc; j < rend; ++j) {
                     const uint32_t m = j - base;
                     const uint32_t g = idx_s[m + m / kGwChunk];
@@ -435,20 +452,31 @@ __device__ __forceinline__ void gw_walk(const FwdArgs &a, uint32_t e0, uint32_t 
                     ++nacc[p];
                 }
             }
-            Ts[p] = __shfl_sync(kFull, T, lam);
-            last[p] = max(last[p], __shfl_sync(kFull, lw, lam));
-            st = __shfl_sync(kFull, st, lam);
-            if (st) {
-                stop[p] = st;
-                live[p] = false;
+            const float Tn = __shfl_sync(kFull, T, lam);
+            const int lwn = __shfl_sync(kFull, lw, lam);
+            const int stn = __shfl_sync(kFull, st, lam);
+            if (cross) {
+                Ts[p] = Tn;
+                last[p] = max(last[p], lwn);
+                if (stn) {
+                    stop[p] = stn;
+                    live[p] = false;
+                }
+            } else if (live[p]) {
+                Ts[p] = Tround;
+                // a pixel below 1e-4 from a transmittance of at most 1 stops within this
+                // segment: the rest of it is not needed
+                if (Tround < kTMin) live[p] = false;
             }
         }
     }
 }
 
-__device__ __forceinline__ void warp_sum5(float &x0, float &x1, float &x2, float &x3, int &n) {
+// Sum over the chunk-lanes of each pixel-lane (xor offsets that keep lane % PXL).
+template <int PXL>
+__device__ __forceinline__ void gw_group_sum5(float &x0, float &x1, float &x2, float &x3, int &n) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = PXL; o < 32; o <<= 1) {
         x0 += __shfl_xor_sync(kFull, x0, o);
         x1 += __shfl_xor_sync(kFull, x1, o);
         x2 += __shfl_xor_sync(kFull, x2, o);
@@ -463,6 +491,7 @@ __device__ __forceinline__ void warp_sum5(float &x0, float &x1, float &x2, float
 template <int P>
 __device__ __forceinline__ void gw_segment_item(const FwdArgs &a, int tile, int sub, unsigned item, uint32_t *idx_s,
                                                 int lane) {
+    constexpr int PPL = GwShape<P>::PPL, PXL = GwShape<P>::PXL;
     const TileGeom tg = tile_geom(a, tile);
     const int groups = (tg.vw * tg.vh + P - 1) / P;
     const int group = sub % groups, seg = sub / groups;
@@ -473,29 +502,31 @@ __device__ __forceinline__ void gw_segment_item(const FwdArgs &a, int tile, int 
     const unsigned long long s0 = (unsigned long long)rg.x + (unsigned long long)seg * L;
     const uint32_t e0 = (uint32_t)min((unsigned long long)rg.y, s0);
     const uint32_t e1 = (uint32_t)min((unsigned long long)rg.y, s0 + L);
-    float pxf[P], pyf[P], Ts[P], ca0[P], ca1[P], ca2[P], da[P];
-    int last[P], nacc[P], stop[P];
-    bool live[P];
+    const int pl = lane % PXL;
+    float pxf[PPL], pyf[PPL], Ts[PPL], ca0[PPL], ca1[PPL], ca2[PPL], da[PPL];
+    int last[PPL], nacc[PPL], stop[PPL];
+    bool live[PPL];
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
+    for (int p = 0; p < PPL; ++p) {
         bool ok;
-        gw_item_pixel(tg, group, P, p, ok, pxf[p], pyf[p]);
+        gw_item_pixel(tg, group, P, pl * PPL + p, ok, pxf[p], pyf[p]);
         Ts[p] = 1.f;
         ca0[p] = ca1[p] = ca2[p] = da[p] = 0.f;
         last[p] = -1;
         nacc[p] = stop[p] = 0;
         live[p] = ok;
     }
-    gw_walk<P>(a, e0, e1, rg.x, pxf, pyf, seg == 0, idx_s, lane, Ts, ca0, ca1, ca2, da, last, nacc, stop, live);
+    gw_walk<PXL, PPL>(a, e0, e1, rg.x, pxf, pyf, seg == 0, idx_s, lane, Ts, ca0, ca1, ca2, da, last, nacc, stop,
+                      live);
     GwSum *out = reinterpret_cast<GwSum *>(a.gw_sum) + (size_t)item * P;
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-        warp_sum5(ca0[p], ca1[p], ca2[p], da[p], nacc[p]);
-        if (lane == p) {
+    for (int p = 0; p < PPL; ++p) {
+        gw_group_sum5<PXL>(ca0[p], ca1[p], ca2[p], da[p], nacc[p]);
+        if (lane < PXL) {  // chunk-lane 0 of each pixel-lane
             GwSum sm;
             sm.cd = make_float4(ca0[p], ca1[p], ca2[p], da[p]);
             sm.t = make_float4(Ts[p], __int_as_float(last[p]), __int_as_float(nacc[p]), __int_as_float(stop[p]));
-            out[p] = sm;
+            out[pl * PPL + p] = sm;
         }
     }
 }
@@ -602,9 +633,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_gw_merge(FwdArg
                 float Tw = T, w0 = 0.f, w1 = 0.f, w2 = 0.f, wd = 0.f;
                 int lw = last, nw = 0, sw = 0;
                 bool live = true;
-                gw_walk<1>(a, e0, e1, rg.x, &pxf, &pyf, true, idx_s[warp], lane, &Tw, &w0, &w1, &w2, &wd, &lw, &nw,
-                           &sw, &live);
-                warp_sum5(w0, w1, w2, wd, nw);
+                gw_walk<1, 1>(a, e0, e1, rg.x, &pxf, &pyf, true, idx_s[warp], lane, &Tw, &w0, &w1, &w2, &wd, &lw,
+                              &nw, &sw, &live);
+                gw_group_sum5<1>(w0, w1, w2, wd, nw);
                 c0 += w0, c1 += w1, c2 += w2, D += wd;
                 T = Tw;
                 last = lw;
@@ -668,6 +699,7 @@ const void *forward_gauss_kernel(int gw_pixels) {
         case 2: return (const void *)k_forward_gauss<2>;
         case 4: return (const void *)k_forward_gauss<4>;
         case 8: return (const void *)k_forward_gauss<8>;
+        case 16: return (const void *)k_forward_gauss<16>;
         default: return nullptr;
     }
 }
@@ -678,6 +710,7 @@ const void *forward_gw_merge_kernel(int gw_pixels) {
         case 2: return (const void *)k_forward_gw_merge<2>;
         case 4: return (const void *)k_forward_gw_merge<4>;
         case 8: return (const void *)k_forward_gw_merge<8>;
+        case 16: return (const void *)k_forward_gw_merge<16>;
         default: return nullptr;
     }
 }
@@ -699,6 +732,7 @@ cudaError_t launch_forward_gauss(const FwdArgs &a, int grid, cudaStream_t s) {
         case 2: k_forward_gauss<2><<<grid, threads, 0, s>>>(a); break;
         case 4: k_forward_gauss<4><<<grid, threads, 0, s>>>(a); break;
         case 8: k_forward_gauss<8><<<grid, threads, 0, s>>>(a); break;
+        case 16: k_forward_gauss<16><<<grid, threads, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -710,6 +744,7 @@ cudaError_t launch_forward_gw_merge(const FwdArgs &a, int grid, cudaStream_t s) 
         case 2: k_forward_gw_merge<2><<<grid, kWarpsPerBlock * 32, 0, s>>>(a); break;
         case 4: k_forward_gw_merge<4><<<grid, kWarpsPerBlock * 32, 0, s>>>(a); break;
         case 8: k_forward_gw_merge<8><<<grid, kWarpsPerBlock * 32, 0, s>>>(a); break;
+        case 16: k_forward_gw_merge<16><<<grid, kWarpsPerBlock * 32, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -81,7 +81,7 @@ STACK_STOPS = {"faint": (0, 12000), "mixed": (5 * 2041 + 1, 5 * 2042 + 1), "unif
 
 
 @pytest.mark.parametrize("kind", list(STACK_STOPS))
-@pytest.mark.parametrize("P,L", [(4, 256), (4, 2048), (1, 512), (8, 256), (2, 1024)])
+@pytest.mark.parametrize("P,L", [(4, 256), (4, 2048), (1, 512), (8, 256), (2, 1024), (16, 256), (16, 2048)])
 def test_heavy_stacks_match_oracle(R, kind, P, L):
     inp = stack(kind)
     ref = oracle_ref(inp)
@@ -102,7 +102,8 @@ def test_heavy_stacks_match_oracle(R, kind, P, L):
 
 
 @pytest.mark.parametrize("kind", ["mixed", "uniform"])
-@pytest.mark.parametrize("W,H,tile,P", [(37, 29, (16, 8), 8), (50, 21, (32, 8), 4), (17, 40, (8, 8), 2)])
+@pytest.mark.parametrize("W,H,tile,P", [(37, 29, (16, 8), 8), (50, 21, (32, 8), 4), (17, 40, (8, 8), 2),
+                                        (45, 27, (16, 16), 16)])
 def test_heavy_stacks_ragged_tiles(R, kind, W, H, tile, P):
     """Partial pixel groups (the tile's visible part not a multiple of P) and ragged tiles."""
     inp = stack(kind, W, H, tile, n=11000, seed=1)
@@ -127,7 +128,7 @@ def test_pixel_and_gaussian_items_agree_on_stacks(R):
         plan.close()
 
 
-@pytest.mark.parametrize("P", [1, 2, 4, 8])
+@pytest.mark.parametrize("P", [1, 2, 4, 8, 16])
 @pytest.mark.parametrize("L", [256, 768])
 def test_cfg1_short_segments(R, P, L):
     """Every tile Gaussian-wise with short segments: most pixels stop in a later segment."""
