@@ -84,7 +84,8 @@ typedef struct bgs_camera {
 
 /* ---- plan: tuning knobs + owned workspace ----------------------------------------- */
 typedef struct bgs_plan_desc {
-    int32_t heavy_threshold; /* AUTO mode: list length above which a tile is Gaussian-wise  */
+    int32_t heavy_threshold; /* AUTO mode: list length above which a tile is Gaussian-wise
+                                (2147483647: no tile is)                                    */
     int32_t gw_pixels;       /* pixels one Gaussian-wise warp item covers: 1, 2, 4, 8 or 16 */
     int32_t queue_chunk;     /* work items a warp claims per atomicAdd on the queue (>= 1)  */
     int32_t blocks_per_sm;   /* persistent grid = SMs x blocks_per_sm; 0 = max resident     */

@@ -27,6 +27,7 @@
 // The result is the stable (depth, index) order per tile.  Traffic is O(B T + K) words
 // instead of the ~26 bytes per entry of a two-pass radix sort of (tile, index) pairs.
 #include <algorithm>
+#include <mutex>
 
 #include "bgs_internal.cuh"
 
@@ -657,10 +658,28 @@ size_t bin_count_smem(int tx, int ty) {
 
 int bin_mask_groups(int tx, int ty) { return ((tx + kCbW - 1) / kCbW) * ((ty + kCbH - 1) / kCbH); }
 
+// Raises a kernel's dynamic shared-memory limit on the current device to at least `bytes`,
+// never lowering it: launches captured in a CUDA graph keep their own (possibly larger)
+// size, and a replay of them needs the limit the capture saw.  slot: one per kernel.
+static cudaError_t raise_dyn_smem(const void *kernel, int slot, size_t bytes) {
+    constexpr int kSlots = 2, kDevices = 64;
+    static std::mutex mu;
+    static int limit[kSlots][kDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kDevices || slot < 0 || slot >= kSlots) return cudaErrorInvalidValue;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)bytes <= limit[slot][dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) limit[slot][dev] = (int)bytes;
+    return e;
+}
+
 cudaError_t setup_bin_kernels(int tx, int ty) {
     const size_t sc = bin_count_smem(tx, ty);
     if (sc <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+    return raise_dyn_smem((const void *)k_bin_count, 0, sc);
 }
 
 cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
@@ -687,9 +706,9 @@ cudaError_t launch_bin_credit(long long N, int G, int B, const uint4 *rect, cons
                               const float *conic_opacity, int W, int H, int tw, int th, uint16_t *D, cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
     // the static tables (~40 KB) plus the counters pass the 48 KB default already on small grids:
-    // opt in to the dynamic size on every launch
+    // opt in to the dynamic size (the limit only ever grows)
     const size_t smem = bin_credit_dyn_smem(tx, ty);
-    const cudaError_t e = cudaFuncSetAttribute(k_bin_credit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = raise_dyn_smem((const void *)k_bin_credit, 1, smem);
     if (e != cudaSuccess) return e;
     k_bin_credit<<<B, kCrWarps * 32, smem, s>>>(N, G, rect, reinterpret_cast<const float2 *>(means2D),
                                       reinterpret_cast<const float4 *>(conic_opacity), tw, th, tx, ty, D);

@@ -247,7 +247,8 @@ bgs_plan::RecKey records_key(const float *means2D, const float *conic_opacity, c
 
 // Gaussian-wise items can be queued in this mode (AUTO: some list may pass the threshold).
 bool gauss_possible(const bgs_plan *p, int mode, int64_t num_entries) {
-    return mode == BGS_MODE_GAUSSIAN || (mode == BGS_MODE_AUTO && (int64_t)p->desc.heavy_threshold < num_entries);
+    return mode == BGS_MODE_GAUSSIAN || (mode == BGS_MODE_AUTO && p->desc.heavy_threshold != INT32_MAX &&
+                                         (int64_t)p->desc.heavy_threshold < num_entries);
 }
 
 // Pixel groups of a Gaussian-wise item over a whole tile.
@@ -267,7 +268,9 @@ long long gw_extra_cap(const bgs_plan *p, int tw, int th, int64_t num_entries) {
 // pixel-wise and builds the same list as PIXEL (so a backward can reuse it).
 int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt, int tw, int th, int mode,
                    int64_t num_entries, cudaStream_t s) {
-    if (mode == BGS_MODE_AUTO && (int64_t)p->desc.heavy_threshold >= num_entries) mode = BGS_MODE_PIXEL;
+    if (mode == BGS_MODE_AUTO && (p->desc.heavy_threshold == INT32_MAX ||
+                                  (int64_t)p->desc.heavy_threshold >= num_entries))
+        mode = BGS_MODE_PIXEL;
     const int T = vt.tile_base[vt.V];
     const int P = p->desc.gw_pixels;
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
@@ -1465,7 +1468,7 @@ int bgs_autotune_render(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N
     }
     // stage 2b: segment length of the Gaussian-wise items, when the best uses them
     for (int L : {512, 8192}) {
-        if (rc != BGS_OK || (int64_t)best.heavy_threshold >= num_entries) break;
+        if (rc != BGS_OK || best.heavy_threshold == INT32_MAX || (int64_t)best.heavy_threshold >= num_entries) break;
         d = best;
         d.gw_segment = L;
         if ((rc = run(d, t)) != BGS_OK) break;
