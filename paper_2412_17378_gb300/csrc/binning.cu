@@ -64,7 +64,9 @@ __device__ __forceinline__ void rect_of(const float2 *__restrict__ means2D, cons
     }
 }
 
-__global__ void __launch_bounds__(256) k_bin_count(long long N, int G, const uint32_t *__restrict__ order,
+constexpr int kCountThreads = 512;  // one thread per Gaussian of a 512-Gaussian sub-block
+
+__global__ void __launch_bounds__(kCountThreads) k_bin_count(long long N, int G, const uint32_t *__restrict__ order,
                                                    const float2 *__restrict__ means2D, const int *__restrict__ radii,
                                                    int tw, int th, int tx, int ty, uint32_t *__restrict__ H,
                                                    uint4 *__restrict__ rect, uint32_t *__restrict__ masks, int W32) {
@@ -163,7 +165,6 @@ __global__ void __launch_bounds__(256) k_bin_count(long long N, int G, const uin
 // tiles).  Near-singular conics (det < 1e-5 a c), whose pairs may round to a positive power
 // and be skipped, earn no credit.
 constexpr uint32_t kCreditThr = 2948;  // ceil(256 ln(1e5))
-constexpr int kCrWarps = 16;           // warps of a k_bin_credit block
 
 // Work units: one per (Gaussian, tile row inside its lowest level set's vertical extent);
 // a unit credits the row for every level whose set spans it (the levels share the row's
@@ -171,6 +172,7 @@ constexpr int kCrWarps = 16;           // warps of a k_bin_credit block
 // over its lanes (a few large Gaussians would otherwise hold the warp for tens of rows); the
 // warps of a block share only the credit counters, so they run without block barriers
 // until the final prefix pass.
+template <int kCrWarps>
 __global__ void __launch_bounds__(kCrWarps * 32) k_bin_credit(long long N, int G, const uint4 *__restrict__ rect,
                                                               const float2 *__restrict__ means2D,
                                                               const float4 *__restrict__ conic_opacity, int tw,
@@ -662,7 +664,7 @@ int bin_mask_groups(int tx, int ty) { return ((tx + kCbW - 1) / kCbW) * ((ty + k
 // never lowering it: launches captured in a CUDA graph keep their own (possibly larger)
 // size, and a replay of them needs the limit the capture saw.  slot: one per kernel.
 static cudaError_t raise_dyn_smem(const void *kernel, int slot, size_t bytes) {
-    constexpr int kSlots = 2, kDevices = 64;
+    constexpr int kSlots = 3, kDevices = 64;
     static std::mutex mu;
     static int limit[kSlots][kDevices] = {};
     int dev = 0;
@@ -686,7 +688,7 @@ cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, c
                              int W, int H, int tw, int th, uint32_t *Hm, uint4 *rect, uint32_t *masks, int W32,
                              cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
-    k_bin_count<<<B, 256, bin_count_smem(tx, ty), s>>>(N, G, order, reinterpret_cast<const float2 *>(means2D), radii,
+    k_bin_count<<<B, kCountThreads, bin_count_smem(tx, ty), s>>>(N, G, order, reinterpret_cast<const float2 *>(means2D), radii,
                                                         tw, th, tx, ty, Hm, rect, masks, W32);
     return cudaGetLastError();
 }
@@ -699,19 +701,32 @@ cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, const uint16_t *D, ui
 
 // dynamic shared memory of k_bin_credit (one credit counter per tile)
 static size_t bin_credit_dyn_smem(int tx, int ty) { return sizeof(uint32_t) * (size_t)tx * ty; }
-// all of k_bin_credit's shared memory: the counters and ~41 KB of per-warp unit tables
-size_t bin_credit_smem(int tx, int ty) { return bin_credit_dyn_smem(tx, ty) + 44 * 1024; }
+// static shared memory of k_bin_credit per warp (its unit tables)
+constexpr size_t kCrWarpSmem = 2560;
+// all of k_bin_credit's shared memory at its smallest block (16 warps): the counters and the
+// per-warp unit tables (+ slack)
+size_t bin_credit_smem(int tx, int ty) { return bin_credit_dyn_smem(tx, ty) + 16 * kCrWarpSmem + 4096; }
 
 cudaError_t launch_bin_credit(long long N, int G, int B, const uint4 *rect, const float *means2D,
                               const float *conic_opacity, int W, int H, int tw, int th, uint16_t *D, cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
-    // the static tables (~40 KB) plus the counters pass the 48 KB default already on small grids:
-    // opt in to the dynamic size (the limit only ever grows)
     const size_t smem = bin_credit_dyn_smem(tx, ty);
-    const cudaError_t e = raise_dyn_smem((const void *)k_bin_credit, 1, smem);
+    // 32 warps a block where their tables fit next to the counters (a large grid leaves room
+    // for one block per SM only), else 16; the static tables plus the counters pass the 48 KB
+    // default already on small grids: opt in to the dynamic size (the limit only ever grows)
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    k_bin_credit<<<B, kCrWarps * 32, smem, s>>>(N, G, rect, reinterpret_cast<const float2 *>(means2D),
-                                      reinterpret_cast<const float4 *>(conic_opacity), tw, th, tx, ty, D);
+    const float2 *m2 = reinterpret_cast<const float2 *>(means2D);
+    const float4 *co = reinterpret_cast<const float4 *>(conic_opacity);
+    if (smem + 32 * kCrWarpSmem + 4096 <= (size_t)optin) {
+        if ((e = raise_dyn_smem((const void *)k_bin_credit<32>, 2, smem)) != cudaSuccess) return e;
+        k_bin_credit<32><<<B, 32 * 32, smem, s>>>(N, G, rect, m2, co, tw, th, tx, ty, D);
+    } else {
+        if ((e = raise_dyn_smem((const void *)k_bin_credit<16>, 1, smem)) != cudaSuccess) return e;
+        k_bin_credit<16><<<B, 16 * 32, smem, s>>>(N, G, rect, m2, co, tw, th, tx, ty, D);
+    }
     return cudaGetLastError();
 }
 
