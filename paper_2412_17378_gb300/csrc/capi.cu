@@ -69,6 +69,8 @@ namespace bgs {
 int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
 }  // namespace bgs
 
+constexpr int kSortStreams = 4;
+
 struct bgs_plan {
     bgs_plan_desc desc;
     int device = 0;
@@ -90,6 +92,10 @@ struct bgs_plan {
     Buf gw_exoff, gw_sum;  // Gaussian-wise segments: per-tile later-segment offsets, per-item summaries
     // batched binning: depth keys of every view
     Buf vkey, vkey_sorted;
+    // the views' depth sorts run concurrently on kSortStreams streams forked from the caller's
+    cudaStream_t sort_stream[kSortStreams] = {};
+    cudaEvent_t sort_fork = nullptr, sort_join[kSortStreams] = {};
+    Buf sort_tmp[kSortStreams];
     // captured CUDA graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -352,9 +358,13 @@ int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess) e = cudaMalloc((void **)&p->ctrl, sizeof(bgs::DevCtrl));
     if (e == cudaSuccess) e = cudaMemset(p->ctrl, 0, sizeof(bgs::DevCtrl));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->sort_fork, cudaEventDisableTiming);
+    for (int i = 0; i < kSortStreams && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&p->sort_stream[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->sort_join[i], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
-        if (p->ctrl) cudaFree(p->ctrl);
-        delete p;
+        bgs_plan_destroy(p);
         return cuda_fail(e, "bgs_plan_create");
     }
     *out = p;
@@ -366,7 +376,13 @@ int bgs_plan_destroy(bgs_plan *p) {
     DeviceGuard g(p->device);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     if (p->graph) cudaGraphDestroy(p->graph);
-    Buf *bufs[] = {&p->vkey, &p->vkey_sorted, &p->bin_credit, &p->bin_sat, &p->bin_items, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_rect, &p->bin_mask, &p->touched, &p->touched_sorted, &p->dkey,
+    for (int i = 0; i < kSortStreams; ++i) {
+        if (p->sort_stream[i]) cudaStreamDestroy(p->sort_stream[i]);
+        if (p->sort_join[i]) cudaEventDestroy(p->sort_join[i]);
+        if (p->sort_tmp[i].p) cudaFree(p->sort_tmp[i].p);
+    }
+    if (p->sort_fork) cudaEventDestroy(p->sort_fork);
+    Buf *bufs[] = {&p->gw_exoff, &p->gw_sum, &p->vkey, &p->vkey_sorted, &p->bin_credit, &p->bin_sat, &p->bin_items, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_rect, &p->bin_mask, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_idx, &p->items, &p->warp_items,
@@ -527,6 +543,7 @@ int bgs_plan_reserve(bgs_plan *p, int64_t N, int64_t K, int64_t T, int64_t pixel
     BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, t[2], u, u, u, u, k1, 0, 32, s), "tile sort size");
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, t[3], u, u, tt, s), "tile scan size");
     BGS_TRY(ensure(p, p->cub_tmp, *std::max_element(t, t + 4), s, "cub_tmp"));
+    for (int i = 0; i < kSortStreams; ++i) BGS_TRY(ensure(p, p->sort_tmp[i], t[0], s, "sort_tmp"));
     return BGS_OK;
 }
 
@@ -1170,13 +1187,23 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
         size_t tmp = 0;
         BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, k0, k1, gidx, order, (int64_t)N, 0, 32, s),
                  "view depth sort (size)");
-        BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
-        tmp = p->cub_tmp.bytes;
+        // the views' sorts are independent: fork them over the side streams (a fork-join of
+        // events, which a graph capture records as such) and join before the binning
+        const int NS = std::min<int>(V, kSortStreams);
+        for (int i = 0; i < NS; ++i) BGS_TRY(ensure(p, p->sort_tmp[i], tmp, s, "sort_tmp"));
+        BGS_CUDA(cudaEventRecord(p->sort_fork, s), "sort fork");
+        for (int i = 0; i < NS; ++i) BGS_CUDA(cudaStreamWaitEvent(p->sort_stream[i], p->sort_fork, 0), "sort fork wait");
         for (int v = 0; v < V; ++v) {
             const size_t o = (size_t)v * N;
-            BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->cub_tmp.p, tmp, k0 + o, k1 + o, gidx + o, order + o,
-                                                     (int64_t)N, 0, 32, s),
+            const int i = v % NS;
+            size_t t = p->sort_tmp[i].bytes;
+            BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->sort_tmp[i].p, t, k0 + o, k1 + o, gidx + o, order + o,
+                                                     (int64_t)N, 0, 32, p->sort_stream[i]),
                      "view depth sort");
+        }
+        for (int i = 0; i < NS; ++i) {
+            BGS_CUDA(cudaEventRecord(p->sort_join[i], p->sort_stream[i]), "sort join");
+            BGS_CUDA(cudaStreamWaitEvent(s, p->sort_join[i], 0), "sort join wait");
         }
         p->host_launches += 1;
         for (int v = 0; v < V; ++v)  // view v's records are positions [v N, (v+1) N) of the order
