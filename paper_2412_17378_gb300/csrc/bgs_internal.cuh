@@ -16,6 +16,8 @@ constexpr float kTMin = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;  // log2(e): exp(x) = 2^(x log2 e)
 constexpr float kLn2 = 0.6931471805599453f;    // ln(2)
 
+constexpr int kMaxViews = 32;  // views of one batched call
+
 // ---- device control block (one per plan) --------------------------------------------
 struct DevCtrl {
     unsigned int queue_head;    // pixel-wise queue cursor (starts at num_gauss)
@@ -28,7 +30,7 @@ struct DevCtrl {
     unsigned long long items_done;
     unsigned int queue_head_g;  // Gaussian-wise queue cursor (starts at 0)
     unsigned int pass_items;    // items the current persistent pass completed
-    unsigned long long bin_base;  // binning: first point_list slot of the view being binned
+    unsigned long long bin_base;  // binning: entries of the call so far (= num_entries at its end)
     unsigned int warps_done;    // blocks of the current persistent pass that finished
     unsigned int pad1;
     // work-list build: items per sort key, each key's first item, blocks done (the counters
@@ -41,6 +43,9 @@ struct DevCtrl {
     unsigned int gw_seg;        // entries per Gaussian-wise segment (0: lists are not split)
     unsigned int pad2;
     unsigned long long wl_extra;  // work-list build: later-segment items (returns to zero)
+    // binning: each view's entry count and first point_list slot
+    unsigned long long view_k[kMaxViews];
+    unsigned long long view_base[kMaxViews];
 };
 
 // End of a persistent pass, per warp (lane 0), for a block of `warps_per_block` warps whose
@@ -189,7 +194,6 @@ __device__ __forceinline__ float pair_alpha(float power2, float o, float &G) {
 // A render call covers V views (1 for the single-view entry points).  Their tiles form
 // one global tile space: view v owns tile ids [tile_base[v], tile_base[v+1]).  Record
 // (and gradient) index v * n_per_view + g belongs to Gaussian g seen from view v.
-constexpr int kMaxViews = 32;
 
 struct ViewTable {
     int V;
@@ -309,16 +313,19 @@ cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, const uint16_t *D, ui
 size_t bin_credit_smem(int tx, int ty);
 cudaError_t launch_bin_credit(long long N, int G, int B, const uint4 *rect, const float *means2D,
                               const float *conic_opacity, int W, int H, int tw, int th, uint16_t *D, cudaStream_t s);
-// ranges of one view's tiles, offset by ctrl->bin_base (the view's first point_list slot)
-cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *total, uint2 *ranges, DevCtrl *ctrl,
-                              cudaStream_t s);
+// ranges of view v's tiles, offset by the view's first point_list slot (the sum of the entry
+// counts of views 0..v-1, stored in ctrl->view_base[v] for the scatter)
+cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *total, uint2 *ranges, int v,
+                              DevCtrl *ctrl, cudaStream_t s);
 cudaError_t launch_bin_scatter(long long N, int G, int B, int W32, const uint4 *rect, int W, int H, int tw, int th,
                                const uint32_t *Hm, const uint32_t *start, const uint32_t *masks, uint32_t *point_list,
-                               long long capacity, const uint32_t *bsat, uint32_t *item_start, int num_sms,
+                               long long capacity, const uint32_t *bsat, uint32_t *item_start, int num_sms, int v,
                                const DevCtrl *ctrl, cudaStream_t s);
-// bin_base += this view's entry count; num_entries = bin_base; raises BGS_CHECK_OVERFLOW past capacity
-cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *total, long long capacity, DevCtrl *ctrl,
-                               cudaStream_t s);
+// ctrl->view_k[v] = view v's entry count (64-bit sum of its tile totals)
+cudaError_t launch_bin_view_total(int T, const uint32_t *total, int v, DevCtrl *ctrl, cudaStream_t s);
+// num_entries = bin_base = the sum of the V views' counts; raises BGS_CHECK_OVERFLOW past
+// capacity or BGS_MAX_ENTRIES
+cudaError_t launch_bin_finish(int V, long long capacity, DevCtrl *ctrl, cudaStream_t s);
 
 // view-dependent colour from spherical harmonics (sh.cu); backward: dL_drgb -> dL_dsh,
 // dL_dmeans3D (summed over the V <= kMaxViews camera centres campos [V,3], host)

@@ -15,12 +15,15 @@
 //   2. k_bin_colscan - exclusive scan of every column of H over b (in place) and the tile
 //                      totals n[t]; with credits, each tile's list is cut after the block
 //                      at which its pixels are certified to have stopped.
-//   3. (CUB) exclusive scan of n -> tile start; k_bin_ranges writes ranges and K.
-//   4. k_bin_scatter - block (chunk of 8 depth blocks b, C), one warp, lane l owns tile l
-//                      of C and keeps its write position start[t] + H[b][t] in a register.
-//                      For each b of the chunk the warp visits the Gaussians flagged in the
-//                      (b, C) mask in depth order; every lane whose tile the rectangle covers
-//                      (and whose list was not cut before b) appends the index.  A lane stages
+//   3. (CUB) exclusive scan of n -> tile start; k_bin_view_total sums the view's count;
+//      k_bin_ranges writes the ranges, offset by the view's first point_list slot (the
+//      counts of the views before it: the views of a batched call run concurrently up to
+//      here, and each view's scatter waits only for the counts of the views before it).
+//   4. k_bin_scatter - item (b, C), one warp, lane l owns tile l of C and keeps its write
+//                      position start[t] + H[b][t] in a register.  The warp visits the
+//                      Gaussians flagged in the (b, C) mask in depth order; every lane whose
+//                      tile the rectangle covers (and whose list was not cut before b)
+//                      appends the index.  A lane stages
 //                      its appends in a 16-word ring in shared memory and writes each
 //                      completed 32-byte sector of its run with two 16-byte stores, so the
 //                      point list is written in whole sectors (not one word per request).
@@ -426,19 +429,22 @@ __global__ void __launch_bounds__(1024) k_bin_colscan(int B, int T, uint32_t *__
     }
 }
 
-// ranges[t] = bin_base + [start[t], start[t] + n[t]) for the tiles of one view ((0,0) for
-// an empty tile).
+// ranges[t] = base + [start[t], start[t] + n[t]) for the tiles of view v ((0,0) for an empty
+// tile), base = the entries of views 0..v-1; block 0 stores base for the scatter.
 __global__ void k_bin_ranges(int T, const uint32_t *__restrict__ start, const uint32_t *__restrict__ total,
-                             uint2 *__restrict__ ranges, const DevCtrl *ctrl) {
+                             uint2 *__restrict__ ranges, int v, DevCtrl *ctrl) {
+    unsigned long long b64 = 0;
+    for (int u = 0; u < v; ++u) b64 += ctrl->view_k[u];
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->view_base[v] = b64;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
-    const uint32_t base = (uint32_t)ctrl->bin_base;
+    const uint32_t base = (uint32_t)b64;  // past 2^32 the call raises BGS_CHECK_OVERFLOW
     const uint32_t a = base + start[t], n = total[t];
     ranges[t] = n ? make_uint2(a, a + n) : make_uint2(0u, 0u);
 }
 
-// Adds the view's entry count (computed in 64 bits from the per-tile totals) to bin_base.
-__global__ void k_bin_advance(int T, const uint32_t *__restrict__ total, long long capacity, DevCtrl *ctrl) {
+// view_k[v] = the view's entry count, summed in 64 bits from the per-tile totals.
+__global__ void k_bin_view_total(int T, const uint32_t *__restrict__ total, int v, DevCtrl *ctrl) {
     __shared__ unsigned long long part[32];
     unsigned long long n = 0;
     for (int t = threadIdx.x; t < T; t += blockDim.x) n += total[t];
@@ -448,12 +454,17 @@ __global__ void k_bin_advance(int T, const uint32_t *__restrict__ total, long lo
     if (threadIdx.x == 0) {
         unsigned long long k = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) k += part[w];
-        const unsigned long long next = ctrl->bin_base + k;
-        ctrl->bin_base = next;
-        ctrl->num_entries = next;
-        if ((long long)next > capacity || (long long)next > BGS_MAX_ENTRIES)
-            atomicOr(&ctrl->check_bits, (unsigned)BGS_CHECK_OVERFLOW);
+        ctrl->view_k[v] = k;
     }
+}
+
+// The call's entry count over its V views; overflow check.
+__global__ void k_bin_finish(int V, long long capacity, DevCtrl *ctrl) {
+    unsigned long long k = 0;
+    for (int u = 0; u < V; ++u) k += ctrl->view_k[u];
+    ctrl->bin_base = k;
+    ctrl->num_entries = k;
+    if ((long long)k > capacity || (long long)k > BGS_MAX_ENTRIES) atomicOr(&ctrl->check_bits, (unsigned)BGS_CHECK_OVERFLOW);
 }
 
 // Writes the completed sector [done, done + 8) of a lane's run from its ring (words below
@@ -531,7 +542,7 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const u
                                                     uint32_t *__restrict__ point_list, uint32_t capacity, int vec_ok,
                                                     const uint32_t *__restrict__ bsat,
                                                     const uint32_t *__restrict__ item_start, int nC, int B,
-                                                    const DevCtrl *ctrl) {
+                                                    int v, const DevCtrl *ctrl) {
     // per flagged Gaussian of the pass: (lanes whose tile its rectangle covers, Gaussian
     // index), .y holding its sorted position until the hit is known; and the lanes' 16-word
     // output rings, slot-major.  7 KB of shared memory a block in all, so that 32 blocks
@@ -542,7 +553,7 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const u
     const int ncx = (tx + kCbW - 1) / kCbW;
     const bool listed = bsat != nullptr;
     const uint32_t n_items = listed ? item_start[nC] : (uint32_t)B * (uint32_t)nC;
-    const uint32_t base = (uint32_t)ctrl->bin_base;
+    const uint32_t base = (uint32_t)ctrl->view_base[v];
     uint32_t *ring = ring_s + lane;
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
         int C, b;
@@ -730,22 +741,25 @@ cudaError_t launch_bin_credit(long long N, int G, int B, const uint4 *rect, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *total, uint2 *ranges, DevCtrl *ctrl,
-                              cudaStream_t s) {
-    k_bin_ranges<<<(T + 255) / 256, 256, 0, s>>>(T, start, total, ranges, ctrl);
+cudaError_t launch_bin_ranges(int T, const uint32_t *start, const uint32_t *total, uint2 *ranges, int v,
+                              DevCtrl *ctrl, cudaStream_t s) {
+    k_bin_ranges<<<std::max(1, (T + 255) / 256), 256, 0, s>>>(T, start, total, ranges, v, ctrl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_advance(int T, const uint32_t *start, const uint32_t *total, long long capacity, DevCtrl *ctrl,
-                               cudaStream_t s) {
-    (void)start;
-    k_bin_advance<<<1, 1024, 0, s>>>(T, total, capacity, ctrl);
+cudaError_t launch_bin_view_total(int T, const uint32_t *total, int v, DevCtrl *ctrl, cudaStream_t s) {
+    k_bin_view_total<<<1, 1024, 0, s>>>(T, total, v, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_finish(int V, long long capacity, DevCtrl *ctrl, cudaStream_t s) {
+    k_bin_finish<<<1, 1, 0, s>>>(V, capacity, ctrl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin_scatter(long long N, int G, int B, int W32, const uint4 *rect, int W, int H, int tw, int th,
                                const uint32_t *Hm, const uint32_t *start, const uint32_t *masks, uint32_t *point_list,
-                               long long capacity, const uint32_t *bsat, uint32_t *item_start, int num_sms,
+                               long long capacity, const uint32_t *bsat, uint32_t *item_start, int num_sms, int v,
                                const DevCtrl *ctrl, cudaStream_t s) {
     (void)N;
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
@@ -762,7 +776,7 @@ cudaError_t launch_bin_scatter(long long N, int G, int B, int W32, const uint4 *
     }
     k_bin_scatter<<<(unsigned)std::max<long long>(1, grid), 32, 0, s>>>((uint32_t)G, W32, rect, tx, ty, Hm, start,
                                                                          masks, point_list, cap, vec_ok, bsat,
-                                                                         item_start, nC, B, ctrl);
+                                                                         item_start, nC, B, v, ctrl);
     return cudaGetLastError();
 }
 

@@ -83,9 +83,13 @@ struct bgs_plan {
     unsigned long long host_launches = 0;
     // binning
     Buf touched, touched_sorted, dkey, dkey_sorted, gidx, order, offsets, keys_in, keys_out, vals_in, cub_tmp;
-    Buf bin_h, bin_total, bin_start, bin_rect, bin_mask;  // counting-sort binning
-    Buf bin_credit, bin_sat;                              // list truncation (credits, last block per tile)
-    Buf bin_items;                                        // the scatter's work items per tile group
+    // counting-sort binning, one buffer set per concurrent view (stream slot): tile histogram,
+    // totals, starts, packed rectangles, masks; list truncation (credits, last block per
+    // tile); the scatter's work items per tile group; the tile scan's temporaries
+    struct BinSlot {
+        Buf h, total, start, rect, mask, credit, sat, items, scan_tmp;
+    } bin_slot[kSortStreams];
+    cudaEvent_t view_done[bgs::kMaxViews] = {};  // a view's entry count is known
     int smem_optin = 0;
     // render
     Buf recs, tile_idx, items, grad_acc, warp_items;  // tile_idx: each tile's slot in its work-list bucket
@@ -363,6 +367,8 @@ int bgs_plan_create(const bgs_plan_desc *desc, bgs_plan **out) {
         e = cudaStreamCreateWithFlags(&p->sort_stream[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->sort_join[i], cudaEventDisableTiming);
     }
+    for (int v = 0; v < bgs::kMaxViews && e == cudaSuccess; ++v)
+        e = cudaEventCreateWithFlags(&p->view_done[v], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         bgs_plan_destroy(p);
         return cuda_fail(e, "bgs_plan_create");
@@ -382,7 +388,14 @@ int bgs_plan_destroy(bgs_plan *p) {
         if (p->sort_tmp[i].p) cudaFree(p->sort_tmp[i].p);
     }
     if (p->sort_fork) cudaEventDestroy(p->sort_fork);
-    Buf *bufs[] = {&p->gw_exoff, &p->gw_sum, &p->vkey, &p->vkey_sorted, &p->bin_credit, &p->bin_sat, &p->bin_items, &p->bin_h, &p->bin_total, &p->bin_start, &p->bin_rect, &p->bin_mask, &p->touched, &p->touched_sorted, &p->dkey,
+    for (cudaEvent_t e : p->view_done)
+        if (e) cudaEventDestroy(e);
+    for (auto &sl : p->bin_slot) {
+        Buf *sb[] = {&sl.h, &sl.total, &sl.start, &sl.rect, &sl.mask, &sl.credit, &sl.sat, &sl.items, &sl.scan_tmp};
+        for (Buf *b : sb)
+            if (b->p) cudaFree(b->p);
+    }
+    Buf *bufs[] = {&p->gw_exoff, &p->gw_sum, &p->vkey, &p->vkey_sorted, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_idx, &p->items, &p->warp_items,
@@ -632,17 +645,27 @@ int bgs_preprocess_backward(bgs_plan *p, int64_t N, const float *means3D, const 
 
 namespace {
 
-// Counting-sort binning of one view (binning.cu): order holds the view's records in depth
-// order (global record indices); ranges points at the view's first tile.  Writes its lists
-// from point_list slot ctrl->bin_base on and advances bin_base.  No host synchronisation.
-// With flag_overflow, an entry count past capacity raises BGS_CHECK_OVERFLOW on the device
-// (graph-safe callers check it with bgs_check); otherwise the host checks the count.
-int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const float *means2D, const int32_t *radii,
-                      const float *conic_opacity, int W, int H, int tw, int th, uint32_t *point_list,
-                      long long capacity, uint32_t *ranges, bool flag_overflow, cudaStream_t s) {
-    const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
-    const long long T = (long long)tiles_x * tiles_y;
-    const size_t smem = bgs::bin_count_smem(tiles_x, tiles_y);
+// Counting-sort binning of one view (binning.cu), in two halves on stream s with the buffer
+// set `slot`.  order holds the view's records in depth order (global record indices);
+// ranges points at the view's first tile.  bin_view_a counts (tile histogram, masks,
+// credits, truncated totals, tile starts) and stores the view's entry count in
+// ctrl->view_k[v]; bin_view_b writes the ranges and the lists from the view's first
+// point_list slot (the counts of views 0..v-1, which must be stored by then) on.  No host
+// synchronisation; bgs::launch_bin_finish then totals the call's views.
+struct BinView {
+    int tiles_x, tiles_y;
+    long long T, G, B, W32, nC;
+    bool trunc;
+};
+
+int bin_view_a(bgs_plan *p, int slot, int v, long long n, const uint32_t *order, const float *means2D,
+               const int32_t *radii, const float *conic_opacity, int W, int H, int tw, int th, BinView &bv,
+               cudaStream_t s) {
+    bgs_plan::BinSlot &sl = p->bin_slot[slot];
+    bv.tiles_x = (W + tw - 1) / tw;
+    bv.tiles_y = (H + th - 1) / th;
+    const long long T = bv.T = (long long)bv.tiles_x * bv.tiles_y;
+    const size_t smem = bgs::bin_count_smem(bv.tiles_x, bv.tiles_y);
     if (smem > (size_t)p->smem_optin) return fail(BGS_ERR_INVALID, "tile grid too large for counting-sort binning");
     // G: a multiple of 32.  Automatic: at least 2048, about 4 counting blocks per SM (fewer,
     // longer blocks keep the scatter's per-(block, tile group) overhead down), and large
@@ -652,33 +675,32 @@ int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const flo
         G = std::max<long long>(2048, (n + 4ll * p->num_sms - 1) / (4ll * std::max(1, p->num_sms)));
         G = std::max<long long>(G, (n * T + (1ll << 24) - 1) >> 24);
     }
-    G = (G + 31) & ~31ll;
-    const long long B = std::max<long long>(1, (n + G - 1) / G);
-    const long long W32 = ((G + 511) / 512) * 16;  // mask words per (block, tile group)
-    const long long nC = bgs::bin_mask_groups(tiles_x, tiles_y);
+    G = bv.G = (G + 31) & ~31ll;
+    const long long B = bv.B = std::max<long long>(1, (n + G - 1) / G);
+    const long long W32 = bv.W32 = ((G + 511) / 512) * 16;  // mask words per (block, tile group)
+    const long long nC = bv.nC = bgs::bin_mask_groups(bv.tiles_x, bv.tiles_y);
     if (B * T >= (1ll << 31) || B * nC * W32 >= (1ll << 40)) return fail(BGS_ERR_INVALID, "tile histogram too large");
-    BGS_TRY(ensure(p, p->bin_h, sizeof(uint32_t) * B * T, s, "bin_h"));
-    BGS_TRY(ensure(p, p->bin_total, sizeof(uint32_t) * T, s, "bin_total"));
-    BGS_TRY(ensure(p, p->bin_start, sizeof(uint32_t) * T, s, "bin_start"));
-    BGS_TRY(ensure(p, p->bin_rect, sizeof(uint4) * n, s, "bin_rect"));
-    BGS_TRY(ensure(p, p->bin_mask, sizeof(uint32_t) * B * nC * W32, s, "bin_mask"));
-    uint32_t *Hm = (uint32_t *)p->bin_h.p, *tot = (uint32_t *)p->bin_total.p, *start = (uint32_t *)p->bin_start.p;
-    uint4 *rect = (uint4 *)p->bin_rect.p;
-    uint32_t *masks = (uint32_t *)p->bin_mask.p;
-    if (smem > 48 * 1024) BGS_CUDA(bgs::setup_bin_kernels(tiles_x, tiles_y), "bin smem attribute");
-    BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, rect, masks, (int)W32,
-                                   s),
+    BGS_TRY(ensure(p, sl.h, sizeof(uint32_t) * B * T, s, "bin_h"));
+    BGS_TRY(ensure(p, sl.total, sizeof(uint32_t) * T, s, "bin_total"));
+    BGS_TRY(ensure(p, sl.start, sizeof(uint32_t) * T, s, "bin_start"));
+    BGS_TRY(ensure(p, sl.rect, sizeof(uint4) * n, s, "bin_rect"));
+    BGS_TRY(ensure(p, sl.mask, sizeof(uint32_t) * B * nC * W32, s, "bin_mask"));
+    uint32_t *Hm = (uint32_t *)sl.h.p, *tot = (uint32_t *)sl.total.p, *start = (uint32_t *)sl.start.p;
+    uint4 *rect = (uint4 *)sl.rect.p;
+    if (smem > 48 * 1024) BGS_CUDA(bgs::setup_bin_kernels(bv.tiles_x, bv.tiles_y), "bin smem attribute");
+    BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, rect,
+                                   (uint32_t *)sl.mask.p, (int)W32, s),
              "bin_count");
     // list truncation: per-block credits toward the certificate that a tile's pixels have all
     // stopped (needs the conics, and the credit counters of one block in shared memory)
-    const bool trunc = conic_opacity && bgs::bin_credit_smem(tiles_x, tiles_y) <= (size_t)p->smem_optin;  // incl. static
+    bv.trunc = conic_opacity && bgs::bin_credit_smem(bv.tiles_x, bv.tiles_y) <= (size_t)p->smem_optin;
     uint16_t *credit = nullptr;
     uint32_t *bsat = nullptr;
-    if (trunc) {
-        BGS_TRY(ensure(p, p->bin_credit, sizeof(uint16_t) * B * T, s, "bin_credit"));
-        BGS_TRY(ensure(p, p->bin_sat, sizeof(uint32_t) * T, s, "bin_sat"));
-        credit = (uint16_t *)p->bin_credit.p;
-        bsat = (uint32_t *)p->bin_sat.p;
+    if (bv.trunc) {
+        BGS_TRY(ensure(p, sl.credit, sizeof(uint16_t) * B * T, s, "bin_credit"));
+        BGS_TRY(ensure(p, sl.sat, sizeof(uint32_t) * T, s, "bin_sat"));
+        credit = (uint16_t *)sl.credit.p;
+        bsat = (uint32_t *)sl.sat.p;
         BGS_CUDA(bgs::launch_bin_credit(n, (int)G, (int)B, rect, means2D, conic_opacity, W, H, tw, th, credit, s),
                  "bin_credit");
         p->host_launches += 1;
@@ -686,18 +708,28 @@ int bin_view_counting(bgs_plan *p, long long n, const uint32_t *order, const flo
     BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, credit, tot, bsat, s), "bin_colscan");
     size_t tmp = 0;
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tot, start, (int)T, s), "tile scan (size)");
-    BGS_TRY(ensure(p, p->cub_tmp, tmp, s, "cub_tmp"));
-    tmp = p->cub_tmp.bytes;
-    BGS_CUDA(cub::DeviceScan::ExclusiveSum(p->cub_tmp.p, tmp, tot, start, (int)T, s), "tile scan");
-    BGS_CUDA(bgs::launch_bin_ranges((int)T, start, tot, reinterpret_cast<uint2 *>(ranges), p->ctrl, s), "bin_ranges");
-    BGS_TRY(ensure(p, p->bin_items, sizeof(uint32_t) * (nC + 1), s, "bin_items"));
-    BGS_CUDA(bgs::launch_bin_scatter(n, (int)G, (int)B, (int)W32, rect, W, H, tw, th, Hm, start, masks, point_list,
-                                     capacity, bsat, (uint32_t *)p->bin_items.p, p->num_sms, p->ctrl, s),
+    BGS_TRY(ensure(p, sl.scan_tmp, tmp, s, "scan_tmp"));
+    tmp = sl.scan_tmp.bytes;
+    BGS_CUDA(cub::DeviceScan::ExclusiveSum(sl.scan_tmp.p, tmp, tot, start, (int)T, s), "tile scan");
+    BGS_CUDA(bgs::launch_bin_view_total((int)T, tot, v, p->ctrl, s), "bin_view_total");
+    p->host_launches += 3;  // count, colscan, view total
+    return BGS_OK;
+}
+
+int bin_view_b(bgs_plan *p, int slot, int v, long long n, const BinView &bv, int W, int H, int tw, int th,
+               uint32_t *point_list, long long capacity, uint32_t *ranges, cudaStream_t s) {
+    bgs_plan::BinSlot &sl = p->bin_slot[slot];
+    const uint32_t *Hm = (const uint32_t *)sl.h.p, *tot = (const uint32_t *)sl.total.p;
+    const uint32_t *start = (const uint32_t *)sl.start.p;
+    BGS_CUDA(bgs::launch_bin_ranges((int)bv.T, start, tot, reinterpret_cast<uint2 *>(ranges), v, p->ctrl, s),
+             "bin_ranges");
+    BGS_TRY(ensure(p, sl.items, sizeof(uint32_t) * (bv.nC + 1), s, "bin_items"));
+    BGS_CUDA(bgs::launch_bin_scatter(n, (int)bv.G, (int)bv.B, (int)bv.W32, (const uint4 *)sl.rect.p, W, H, tw, th, Hm,
+                                     start, (const uint32_t *)sl.mask.p, point_list, capacity,
+                                     bv.trunc ? (const uint32_t *)sl.sat.p : nullptr, (uint32_t *)sl.items.p,
+                                     p->num_sms, v, p->ctrl, s),
              "bin_scatter");
-    p->host_launches += 1;  // the scatter's work list
-    BGS_CUDA(bgs::launch_bin_advance((int)T, start, tot, flag_overflow ? capacity : (1ll << 62), p->ctrl, s),
-             "bin_advance");
-    p->host_launches += 5;  // count, colscan, ranges, scatter, advance
+    p->host_launches += bv.trunc ? 3 : 2;  // ranges, (work list), scatter
     return BGS_OK;
 }
 
@@ -773,9 +805,10 @@ int bgs_bin_and_sort(bgs_plan *p, int64_t N, const float *means2D, const int32_t
              "depth sort");
     // (2) counting sort over tile rectangles when the per-tile counters fit in shared memory
     if (bgs::bin_count_smem(tiles_x, tiles_y) <= (size_t)p->smem_optin) {
-        BGS_CUDA(cudaMemsetAsync(&p->ctrl->bin_base, 0, sizeof(unsigned long long), s), "clear bin base");
-        BGS_TRY(bin_view_counting(p, N, order, means2D, radii, conic_opacity, W, H, tw, th, point_list, capacity,
-                                  ranges, false, s));
+        BinView bv;
+        BGS_TRY(bin_view_a(p, 0, 0, N, order, means2D, radii, conic_opacity, W, H, tw, th, bv, s));
+        BGS_TRY(bin_view_b(p, 0, 0, N, bv, W, H, tw, th, point_list, capacity, ranges, s));
+        BGS_CUDA(bgs::launch_bin_finish(1, 1ll << 62, p->ctrl, s), "bin_finish");  // the host checks K
         unsigned long long K = 0;
         BGS_CUDA(cudaMemcpyAsync(&K, &p->ctrl->num_entries, sizeof K, cudaMemcpyDeviceToHost, s), "read K");
         BGS_CUDA(cudaStreamSynchronize(s), "sync K");
@@ -1201,14 +1234,28 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
                                                      (int64_t)N, 0, 32, p->sort_stream[i]),
                      "view depth sort");
         }
-        for (int i = 0; i < NS; ++i) {
-            BGS_CUDA(cudaEventRecord(p->sort_join[i], p->sort_stream[i]), "sort join");
-            BGS_CUDA(cudaStreamWaitEvent(s, p->sort_join[i], 0), "sort join wait");
-        }
         p->host_launches += 1;
-        for (int v = 0; v < V; ++v)  // view v's records are positions [v N, (v+1) N) of the order
-            BGS_TRY(bin_view_counting(p, N, order + (size_t)v * N, means2D, radii, conic_opacity, Ws[v], Hs[v], tw,
-                                      th, point_list, capacity, ranges + 2ull * vt.tile_base[v], !sync, s));
+        // then each view's binning on its sort's stream (view v's records are positions
+        // [v N, (v+1) N) of the order; views v, v + NS, ... share the stream's buffer set):
+        // counts, then -- once the counts of the views before it are stored -- its lists
+        for (int v = 0; v < V; ++v) {
+            const int i = v % NS;
+            cudaStream_t si = p->sort_stream[i];
+            BinView bv;
+            BGS_TRY(bin_view_a(p, i, v, N, order + (size_t)v * N, means2D, radii, conic_opacity, Ws[v], Hs[v], tw, th,
+                               bv, si));
+            BGS_CUDA(cudaEventRecord(p->view_done[v], si), "view count done");
+            for (int u = 0; u < v; ++u)
+                if (u % NS != i) BGS_CUDA(cudaStreamWaitEvent(si, p->view_done[u], 0), "earlier view counts");
+            BGS_TRY(bin_view_b(p, i, v, N, bv, Ws[v], Hs[v], tw, th, point_list, capacity,
+                               ranges + 2ull * vt.tile_base[v], si));
+        }
+        for (int i = 0; i < NS; ++i) {
+            BGS_CUDA(cudaEventRecord(p->sort_join[i], p->sort_stream[i]), "binning join");
+            BGS_CUDA(cudaStreamWaitEvent(s, p->sort_join[i], 0), "binning join wait");
+        }
+        BGS_CUDA(bgs::launch_bin_finish(V, sync ? (1ll << 62) : capacity, p->ctrl, s), "bin_finish");
+        p->host_launches += 1;
     }
     if (!sync) return BGS_OK;
     unsigned long long K = 0;
