@@ -301,9 +301,14 @@ cudaError_t setup_bin_kernels(int tx, int ty);
 // also writes each sorted position's record rect[s] = (x0 | w << 16, y0 | h << 16, Gaussian
 // index, 0) (both rectangle words 0 when empty) and the (block, tile group) masks, W32
 // words each (a multiple of 16)
-cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
-                             int W, int H, int tw, int th, uint32_t *Hm, uint4 *rect, uint32_t *masks, int W32,
-                             cudaStream_t s);
+// blocks [b_lo, b_hi) of the counting pass; skipP (nullable): the exclusive 2D prefix of the
+// tiles known to have stopped before b_lo (k_bin_stopped), whose Gaussians are left out
+cudaError_t launch_bin_count(long long N, int G, int b_lo, int b_hi, const uint32_t *order, const float *means2D,
+                             const int *radii, int W, int H, int tw, int th, uint32_t *Hm, uint4 *rect, uint32_t *masks,
+                             int W32, const int *skipP, cudaStream_t s);
+// the tiles whose credits over blocks [0, B1) certify that every pixel stopped, as the
+// exclusive 2D prefix P [(ty + 1) x (tx + 1)] of their indicator
+cudaError_t launch_bin_stopped(int B1, int tx, int ty, const uint16_t *D, int *P, cudaStream_t s);
 // per tile column: exclusive prefix of H over the blocks and the total; with the credits D
 // (nullable) the column is cut after the block b_sat[t] at which they certify that every
 // pixel of the tile has stopped (b_sat written when bsat is not null)
@@ -311,7 +316,7 @@ cudaError_t launch_bin_colscan(int B, int T, uint32_t *Hm, const uint16_t *D, ui
                                cudaStream_t s);
 // per block and tile: fixed-point credits toward that certificate (k_bin_credit)
 size_t bin_credit_smem(int tx, int ty);
-cudaError_t launch_bin_credit(long long N, int G, int B, const uint4 *rect, const float *means2D,
+cudaError_t launch_bin_credit(long long N, int G, int b_lo, int b_hi, const uint4 *rect, const float *means2D,
                               const float *conic_opacity, int W, int H, int tw, int th, uint16_t *D, cudaStream_t s);
 // ranges of view v's tiles, offset by the view's first point_list slot (the sum of the entry
 // counts of views 0..v-1, stored in ctrl->view_base[v] for the scatter)

@@ -72,13 +72,14 @@ constexpr int kCountThreads = 512;  // one thread per Gaussian of a 512-Gaussian
 __global__ void __launch_bounds__(kCountThreads) k_bin_count(long long N, int G, const uint32_t *__restrict__ order,
                                                    const float2 *__restrict__ means2D, const int *__restrict__ radii,
                                                    int tw, int th, int tx, int ty, uint32_t *__restrict__ H,
-                                                   uint4 *__restrict__ rect, uint32_t *__restrict__ masks, int W32) {
+                                                   uint4 *__restrict__ rect, uint32_t *__restrict__ masks, int W32,
+                                                   int b_off, const int *__restrict__ skipP) {
     extern __shared__ __align__(16) uint32_t d_s[];  // [T] tile counters, then (16-byte aligned) [nC][16] mask words
     const int T = tx * ty;
     const int ncx = (tx + kCbW - 1) / kCbW, nC = ncx * ((ty + kCbH - 1) / kCbH);
     const int T4 = (T + 3) & ~3;
     uint32_t *m_s = d_s + T4;
-    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int b = blockIdx.x + b_off, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int t = threadIdx.x; t < T4 + 16 * nC; t += blockDim.x) d_s[t] = 0u;
     __syncthreads();
     const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
@@ -89,6 +90,12 @@ __global__ void __launch_bounds__(kCountThreads) k_bin_count(long long N, int G,
             int x0, y0, w, c;
             const uint32_t g = order[s];
             rect_of(means2D, radii, g, tw, th, tx, ty, x0, y0, w, c);
+            if (c > 0 && skipP) {
+                // every tile the rectangle covers stopped in the blocks before this pass: the
+                // Gaussian is past the end of all its lists (treated as covering nothing)
+                const int x1 = x0 + w, y1 = y0 + c / w, w1 = tx + 1;
+                if (skipP[y1 * w1 + x1] - skipP[y0 * w1 + x1] - skipP[y1 * w1 + x0] + skipP[y0 * w1 + x0] == c) c = 0;
+            }
             uint32_t px = 0u, py = 0u;  // packed (x0 | w << 16, y0 | h << 16); h = 0 if empty
             if (c > 0) {
                 const int h = c / w, x1 = x0 + w, y1 = y0 + h;
@@ -179,7 +186,8 @@ template <int kCrWarps>
 __global__ void __launch_bounds__(kCrWarps * 32) k_bin_credit(long long N, int G, const uint4 *__restrict__ rect,
                                                               const float2 *__restrict__ means2D,
                                                               const float4 *__restrict__ conic_opacity, int tw,
-                                                              int th, int tx, int ty, uint16_t *__restrict__ D) {
+                                                              int th, int tx, int ty, uint16_t *__restrict__ D,
+                                                              int b_off) {
     extern __shared__ uint32_t w_s[];  // [T] per-row difference arrays of the credits
     // per warp, per lane's Gaussian: mx, my, 1 / qa, qb / qa, det, qa r^2 of the 3 levels;
     // the credit steps, first and end rows of the levels; the rectangle's columns, levels
@@ -189,7 +197,7 @@ __global__ void __launch_bounds__(kCrWarps * 32) k_bin_credit(long long N, int G
     __shared__ int s_rx[kCrWarps][32][2];
     __shared__ int s_scan[kCrWarps][32];
     const int T = tx * ty;
-    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x + b_off, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < T; i += kCrWarps * 32) w_s[i] = 0u;
     __syncthreads();
     const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
@@ -695,12 +703,64 @@ cudaError_t setup_bin_kernels(int tx, int ty) {
     return raise_dyn_smem((const void *)k_bin_count, 0, sc);
 }
 
-cudaError_t launch_bin_count(long long N, int G, int B, const uint32_t *order, const float *means2D, const int *radii,
-                             int W, int H, int tw, int th, uint32_t *Hm, uint4 *rect, uint32_t *masks, int W32,
-                             cudaStream_t s) {
+cudaError_t launch_bin_count(long long N, int G, int b_lo, int b_hi, const uint32_t *order, const float *means2D,
+                             const int *radii, int W, int H, int tw, int th, uint32_t *Hm, uint4 *rect, uint32_t *masks,
+                             int W32, const int *skipP, cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
-    k_bin_count<<<B, kCountThreads, bin_count_smem(tx, ty), s>>>(N, G, order, reinterpret_cast<const float2 *>(means2D), radii,
-                                                        tw, th, tx, ty, Hm, rect, masks, W32);
+    if (b_hi <= b_lo) return cudaSuccess;
+    k_bin_count<<<b_hi - b_lo, kCountThreads, bin_count_smem(tx, ty), s>>>(
+        N, G, order, reinterpret_cast<const float2 *>(means2D), radii, tw, th, tx, ty, Hm, rect, masks, W32, b_lo, skipP);
+    return cudaGetLastError();
+}
+
+// Tiles whose credits over blocks [0, B1) reach thr (every pixel stopped there): their
+// exclusive 2D prefix P[y][x] = #stopped tiles (x' < x, y' < y), (ty + 1) x (tx + 1).
+__global__ void k_bin_stopped(int B1, int tx, int ty, const uint16_t *__restrict__ D, uint32_t thr,
+                              int *__restrict__ P) {
+    const int T = tx * ty;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    uint32_t sum = 0;
+    for (int b = 0; b < B1; ++b) sum = min(sum + (uint32_t)D[(size_t)b * T + t], 0x7fffffffu);
+    const int x = t % tx, y = t / tx;
+    P[(y + 1) * (tx + 1) + x + 1] = sum >= thr ? 1 : 0;
+    if (x == 0) P[(y + 1) * (tx + 1)] = 0;
+    if (y == 0) P[x + 1] = 0;
+    if (t == 0) P[0] = 0;
+}
+
+// In place: the indicator rows 1..ty, columns 1..tx of P -> their 2D inclusive prefix (one block).
+__global__ void __launch_bounds__(1024) k_bin_prefix2d(int tx, int ty, int *__restrict__ P) {
+    const int w1 = tx + 1, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int y = 1 + warp; y <= ty; y += nwarps) {  // along x, a warp per row
+        int carry = 0;
+        for (int xb = 1; xb <= tx; xb += 32) {
+            const int x = xb + lane;
+            int v = x <= tx ? P[y * w1 + x] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (x <= tx) P[y * w1 + x] = v + carry;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+    for (int x = 1 + (int)threadIdx.x; x <= tx; x += blockDim.x) {  // along y, a thread per column
+        int run = 0;
+        for (int y = 1; y <= ty; ++y) {
+            run += P[y * w1 + x];
+            P[y * w1 + x] = run;
+        }
+    }
+}
+
+cudaError_t launch_bin_stopped(int B1, int tx, int ty, const uint16_t *D, int *P, cudaStream_t s) {
+    const int T = tx * ty;
+    k_bin_stopped<<<std::max(1, (T + 255) / 256), 256, 0, s>>>(B1, tx, ty, D, kCreditThr, P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_bin_prefix2d<<<1, 1024, 0, s>>>(tx, ty, P);
     return cudaGetLastError();
 }
 
@@ -718,9 +778,10 @@ constexpr size_t kCrWarpSmem = 2560;
 // per-warp unit tables (+ slack)
 size_t bin_credit_smem(int tx, int ty) { return bin_credit_dyn_smem(tx, ty) + 16 * kCrWarpSmem + 4096; }
 
-cudaError_t launch_bin_credit(long long N, int G, int B, const uint4 *rect, const float *means2D,
+cudaError_t launch_bin_credit(long long N, int G, int b_lo, int b_hi, const uint4 *rect, const float *means2D,
                               const float *conic_opacity, int W, int H, int tw, int th, uint16_t *D, cudaStream_t s) {
     const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th;
+    if (b_hi <= b_lo) return cudaSuccess;
     const size_t smem = bin_credit_dyn_smem(tx, ty);
     // 32 warps a block where their tables fit next to the counters (a large grid leaves room
     // for one block per SM only), else 16; the static tables plus the counters pass the 48 KB
@@ -733,10 +794,10 @@ cudaError_t launch_bin_credit(long long N, int G, int B, const uint4 *rect, cons
     const float4 *co = reinterpret_cast<const float4 *>(conic_opacity);
     if (smem + 32 * kCrWarpSmem + 4096 <= (size_t)optin) {
         if ((e = raise_dyn_smem((const void *)k_bin_credit<32>, 2, smem)) != cudaSuccess) return e;
-        k_bin_credit<32><<<B, 32 * 32, smem, s>>>(N, G, rect, m2, co, tw, th, tx, ty, D);
+        k_bin_credit<32><<<b_hi - b_lo, 32 * 32, smem, s>>>(N, G, rect, m2, co, tw, th, tx, ty, D, b_lo);
     } else {
         if ((e = raise_dyn_smem((const void *)k_bin_credit<16>, 1, smem)) != cudaSuccess) return e;
-        k_bin_credit<16><<<B, 16 * 32, smem, s>>>(N, G, rect, m2, co, tw, th, tx, ty, D);
+        k_bin_credit<16><<<b_hi - b_lo, 16 * 32, smem, s>>>(N, G, rect, m2, co, tw, th, tx, ty, D, b_lo);
     }
     return cudaGetLastError();
 }

@@ -87,7 +87,7 @@ struct bgs_plan {
     // totals, starts, packed rectangles, masks; list truncation (credits, last block per
     // tile); the scatter's work items per tile group; the tile scan's temporaries
     struct BinSlot {
-        Buf h, total, start, rect, mask, credit, sat, items, scan_tmp;
+        Buf h, total, start, rect, mask, credit, sat, items, scan_tmp, stopped;
     } bin_slot[kSortStreams];
     cudaEvent_t view_done[bgs::kMaxViews] = {};  // a view's entry count is known
     int smem_optin = 0;
@@ -391,7 +391,8 @@ int bgs_plan_destroy(bgs_plan *p) {
     for (cudaEvent_t e : p->view_done)
         if (e) cudaEventDestroy(e);
     for (auto &sl : p->bin_slot) {
-        Buf *sb[] = {&sl.h, &sl.total, &sl.start, &sl.rect, &sl.mask, &sl.credit, &sl.sat, &sl.items, &sl.scan_tmp};
+        Buf *sb[] = {&sl.h,     &sl.total, &sl.start, &sl.rect,     &sl.mask,
+                     &sl.credit, &sl.sat,  &sl.items, &sl.scan_tmp, &sl.stopped};
         for (Buf *b : sb)
             if (b->p) cudaFree(b->p);
     }
@@ -688,9 +689,6 @@ int bin_view_a(bgs_plan *p, int slot, int v, long long n, const uint32_t *order,
     uint32_t *Hm = (uint32_t *)sl.h.p, *tot = (uint32_t *)sl.total.p, *start = (uint32_t *)sl.start.p;
     uint4 *rect = (uint4 *)sl.rect.p;
     if (smem > 48 * 1024) BGS_CUDA(bgs::setup_bin_kernels(bv.tiles_x, bv.tiles_y), "bin smem attribute");
-    BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B, order, means2D, radii, W, H, tw, th, Hm, rect,
-                                   (uint32_t *)sl.mask.p, (int)W32, s),
-             "bin_count");
     // list truncation: per-block credits toward the certificate that a tile's pixels have all
     // stopped (needs the conics, and the credit counters of one block in shared memory)
     bv.trunc = conic_opacity && bgs::bin_credit_smem(bv.tiles_x, bv.tiles_y) <= (size_t)p->smem_optin;
@@ -701,10 +699,31 @@ int bin_view_a(bgs_plan *p, int slot, int v, long long n, const uint32_t *order,
         BGS_TRY(ensure(p, sl.sat, sizeof(uint32_t) * T, s, "bin_sat"));
         credit = (uint16_t *)sl.credit.p;
         bsat = (uint32_t *)sl.sat.p;
-        BGS_CUDA(bgs::launch_bin_credit(n, (int)G, (int)B, rect, means2D, conic_opacity, W, H, tw, th, credit, s),
-                 "bin_credit");
-        p->host_launches += 1;
     }
+    // With truncation, two passes: the first eighth of the depth order, then the rest without
+    // the Gaussians all of whose tiles the first pass's credits already certify as stopped
+    // (their entries lie past the ends of all their lists, so the lists are the same)
+    const long long B1 = (bv.trunc && B >= 16) ? (B + 7) / 8 : B;
+    uint32_t *masks = (uint32_t *)sl.mask.p;
+    BGS_CUDA(bgs::launch_bin_count(n, (int)G, 0, (int)B1, order, means2D, radii, W, H, tw, th, Hm, rect, masks,
+                                   (int)W32, nullptr, s),
+             "bin_count");
+    if (bv.trunc)
+        BGS_CUDA(bgs::launch_bin_credit(n, (int)G, 0, (int)B1, rect, means2D, conic_opacity, W, H, tw, th, credit, s),
+                 "bin_credit");
+    if (B1 < B) {
+        BGS_TRY(ensure(p, sl.stopped, sizeof(int) * (bv.tiles_x + 1) * (bv.tiles_y + 1), s, "bin_stopped"));
+        int *P = (int *)sl.stopped.p;
+        BGS_CUDA(bgs::launch_bin_stopped((int)B1, bv.tiles_x, bv.tiles_y, credit, P, s), "bin_stopped");
+        BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B1, (int)B, order, means2D, radii, W, H, tw, th, Hm, rect,
+                                       masks, (int)W32, P, s),
+                 "bin_count (second pass)");
+        BGS_CUDA(bgs::launch_bin_credit(n, (int)G, (int)B1, (int)B, rect, means2D, conic_opacity, W, H, tw, th,
+                                        credit, s),
+                 "bin_credit (second pass)");
+        p->host_launches += 4;
+    }
+    if (bv.trunc) p->host_launches += 1;
     BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, credit, tot, bsat, s), "bin_colscan");
     size_t tmp = 0;
     BGS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, tot, start, (int)T, s), "tile scan (size)");
