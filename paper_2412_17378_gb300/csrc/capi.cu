@@ -653,6 +653,9 @@ namespace {
 // ctrl->view_k[v]; bin_view_b writes the ranges and the lists from the view's first
 // point_list slot (the counts of views 0..v-1, which must be stored by then) on.  No host
 // synchronisation; bgs::launch_bin_finish then totals the call's views.
+// depth-order fractions 1 / d at which truncated binning starts its second and third passes
+constexpr long long kBinPassDiv[2] = {8, 2};
+
 struct BinView {
     int tiles_x, tiles_y;
     long long T, G, B, W32, nC;
@@ -700,28 +703,34 @@ int bin_view_a(bgs_plan *p, int slot, int v, long long n, const uint32_t *order,
         credit = (uint16_t *)sl.credit.p;
         bsat = (uint32_t *)sl.sat.p;
     }
-    // With truncation, two passes: the first eighth of the depth order, then the rest without
-    // the Gaussians all of whose tiles the first pass's credits already certify as stopped
-    // (their entries lie past the ends of all their lists, so the lists are the same)
-    const long long B1 = (bv.trunc && B >= 16) ? (B + 7) / 8 : B;
+    // With truncation, in passes over the depth order ([0, B / 8), [B / 8, B / 2), [B / 2, B)):
+    // a later pass leaves out the Gaussians all of whose tiles the earlier passes' credits
+    // already certify as stopped (their entries lie past the ends of all their lists, so the
+    // lists are the same)
+    long long bounds[4] = {0, B, B, B};
+    int passes = 1;
+    if (bv.trunc && B >= 32) {
+        bounds[1] = B / kBinPassDiv[0];
+        bounds[2] = B / kBinPassDiv[1];
+        bounds[3] = B;
+        passes = 3;
+    }
     uint32_t *masks = (uint32_t *)sl.mask.p;
-    BGS_CUDA(bgs::launch_bin_count(n, (int)G, 0, (int)B1, order, means2D, radii, W, H, tw, th, Hm, rect, masks,
-                                   (int)W32, nullptr, s),
-             "bin_count");
-    if (bv.trunc)
-        BGS_CUDA(bgs::launch_bin_credit(n, (int)G, 0, (int)B1, rect, means2D, conic_opacity, W, H, tw, th, credit, s),
-                 "bin_credit");
-    if (B1 < B) {
+    int *P = nullptr;
+    if (passes > 1) {
         BGS_TRY(ensure(p, sl.stopped, sizeof(int) * (bv.tiles_x + 1) * (bv.tiles_y + 1), s, "bin_stopped"));
-        int *P = (int *)sl.stopped.p;
-        BGS_CUDA(bgs::launch_bin_stopped((int)B1, bv.tiles_x, bv.tiles_y, credit, P, s), "bin_stopped");
-        BGS_CUDA(bgs::launch_bin_count(n, (int)G, (int)B1, (int)B, order, means2D, radii, W, H, tw, th, Hm, rect,
-                                       masks, (int)W32, P, s),
-                 "bin_count (second pass)");
-        BGS_CUDA(bgs::launch_bin_credit(n, (int)G, (int)B1, (int)B, rect, means2D, conic_opacity, W, H, tw, th,
-                                        credit, s),
-                 "bin_credit (second pass)");
-        p->host_launches += 4;
+        P = (int *)sl.stopped.p;
+    }
+    for (int k = 0; k < passes; ++k) {
+        const int lo = (int)bounds[k], hi = (int)bounds[k + 1];
+        if (k > 0) BGS_CUDA(bgs::launch_bin_stopped(lo, bv.tiles_x, bv.tiles_y, credit, P, s), "bin_stopped");
+        BGS_CUDA(bgs::launch_bin_count(n, (int)G, lo, hi, order, means2D, radii, W, H, tw, th, Hm, rect, masks,
+                                       (int)W32, k > 0 ? P : nullptr, s),
+                 "bin_count");
+        if (bv.trunc)
+            BGS_CUDA(bgs::launch_bin_credit(n, (int)G, lo, hi, rect, means2D, conic_opacity, W, H, tw, th, credit, s),
+                     "bin_credit");
+        p->host_launches += k > 0 ? 4 : 1;
     }
     if (bv.trunc) p->host_launches += 1;
     BGS_CUDA(bgs::launch_bin_colscan((int)B, (int)T, Hm, credit, tot, bsat, s), "bin_colscan");
