@@ -41,6 +41,8 @@ WORKLOADS = {
     "cfg3late": "training-stage sweep, late: 1280x720, 3M small opaque Gaussians, fwd+bwd",
     "cfg4": "16 uneven views (4x640x360, 8x1280x720, 4x1920x1080) of 2M clustered Gaussians, fwd+bwd",
     "cfg5": "3840x2160 + 8x1920x1080 views of 4M Gaussians in 3 clusters, fwd+bwd",
+    "heavy": "single view 1920x1080: 200k clustered Gaussians and a veil of 100k faint ones over ~35 tiles "
+             "(lists of 2-8e4 entries walked to their ends), fwd+bwd",
 }
 DEFAULT_CONFIG = "cfg5"
 
@@ -232,9 +234,11 @@ def tile_eval_histogram(outs, cams, tile=16):
             "log2_hist": hist}
 
 
-PROFILED = {  # dominant-kernel ncu summaries that carry DRAM traffic (workload cfg2, tuned knobs)
-    "k_backward_balanced": "profiles/k_backward_balanced_cfg2_1920x1080_1M.md",
-    "k_forward_balanced": "profiles/k_forward_pixel_cfg2_1920x1080_1M.md",
+PROFILED = {  # ncu summaries carrying the DRAM traffic of a dominant kernel, per workload and knobs
+    "k_backward_balanced": ["profiles/k_backward_balanced_cfg5_4k+8x1080p_4M.md",
+                            "profiles/k_backward_balanced_cfg2_1920x1080_1M.md"],
+    "k_forward_balanced": ["profiles/k_forward_pixel_cfg5_4k+8x1080p_4M.md",
+                           "profiles/k_forward_pixel_cfg2_1920x1080_1M.md"],
 }
 
 
@@ -292,25 +296,33 @@ def kernel_code_hash(files) -> str:
 
 
 def profiled_traffic(kernel: str, config: str, tuned: dict):
-    """DRAM read + write bytes per launch of the kernel from its committed ncu summary,
-    when that capture was taken on this workload and knobs and the kernel's source files
-    are unchanged since (their code hash is recorded in the summary); else (None, reason)."""
-    path = PROFILED.get(kernel)
-    if path is None or not os.path.exists(os.path.join(ROOT, path)):
-        return None, "no capture for this kernel"
-    if config != "cfg2" or tuned.get("pixel_rows") != 4 or tuned.get("heavy_threshold", 0) < 2 ** 31 - 1:
-        return None, "capture taken on cfg2 with pixel_rows=4, every tile pixel-wise"
-    fields = {}
-    for line in open(os.path.join(ROOT, path)):
-        if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "kernel_source_sha256_16"):
-            k, v = line.split(":", 1)
-            fields[k] = v.strip()
-    if "traffic_bytes_per_launch" not in fields:
-        return None, "capture has no traffic line"
-    digest, files = fields["kernel_source_sha256_16"].split(" ", 1)
-    if kernel_code_hash(files.strip("()").split(", ")) != digest:
-        return None, "kernel code changed since the capture"
-    return int(fields["traffic_bytes_per_launch"]), path
+    """DRAM read + write bytes per launch of the kernel from a committed ncu summary taken on
+    this workload (its `config:` line) with these knobs (its `knobs:` line), whose kernel
+    source files are unchanged since (their code hash is recorded in the summary); else
+    (None, reason)."""
+    reason = "no capture for this kernel"
+    for path in PROFILED.get(kernel, []):
+        if not os.path.exists(os.path.join(ROOT, path)):
+            continue
+        fields = {}
+        for line in open(os.path.join(ROOT, path)):
+            if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "kernel_source_sha256_16", "config",
+                                                      "knobs"):
+                k, v = line.split(":", 1)
+                fields[k] = v.strip()
+        if "traffic_bytes_per_launch" not in fields or "config" not in fields:
+            reason = "capture has no traffic line"
+            continue
+        knobs = dict(kv.split("=") for kv in fields.get("knobs", "").split(",") if "=" in kv)
+        if fields["config"] != config or any(int(tuned.get(k, -1)) != int(v) for k, v in knobs.items()):
+            reason = f"no capture for workload {config} with these knobs"
+            continue
+        digest, files = fields["kernel_source_sha256_16"].split(" ", 1)
+        if kernel_code_hash(files.strip("()").split(", ")) != digest:
+            reason = "kernel code changed since the capture"
+            continue
+        return int(fields["traffic_bytes_per_launch"]), path
+    return None, reason
 
 
 def load_peaks():
@@ -572,7 +584,8 @@ def main_views(args, scene, rank, world, local):
             best_ms, knobs = raster.autotune_render(plan, pre["means2D"], pre["conic_opacity"], d["colors"],
                                                     pre["depths"], state["pl"], K, state["rg"], cams,
                                                     outs=state["outs"], grads_in=state["gin"], out=state["gr"])
-            tuned.update({k: knobs[k] for k in ("pixel_rows", "heavy_threshold", "gw_pixels", "queue_chunk")})
+            tuned.update({k: knobs[k] for k in ("pixel_rows", "heavy_threshold", "gw_pixels", "queue_chunk",
+                                                "gw_segment")})
             tuned["render_ms"] = round(best_ms, 4)
         # ---- frame statistics (evaluated / contributing pairs, backward pairs) ----
         plan.reset_stats()
@@ -860,7 +873,8 @@ def main_views(args, scene, rank, world, local):
     dom = "forward" if fwd_ms >= bwd_ms else "backward"
     roof = roofline_obj(dom, eval_pairs, contrib_pairs, bwd_pairs, fwd_ms, bwd_ms, plan.num_sms, fp32_rate, ex2_rate,
                         clk.get("sm_mhz"))
-    roof["traffic"], roof["traffic_source"] = profiled_traffic(roof["kernel"], args.config, tuned)
+    roof["traffic"], roof["traffic_source"] = profiled_traffic(
+        roof["kernel"], args.config if args.scale == 1.0 else f"{args.config}@{args.scale}", tuned)
     if roof["traffic"] is not None:
         roof["traffic_unit"] = "bytes per launch (DRAM read + write, ncu)"
     # ---- FP64 CPU oracle on a bounded sample of every view (rank 0, one GPU) ----

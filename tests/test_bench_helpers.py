@@ -51,8 +51,8 @@ def test_roofline_forward_and_duration_scaling(peaks_1ghz):
     assert r2["frac"] == pytest.approx(r["frac"] / 2) and r2["peak"] == pytest.approx(r["peak"])
 
 
-def _summary(path, digest, files, traffic=123456):
-    path.write_text(f"# test capture\n\ntraffic_bytes_per_launch: {traffic}\n"
+def _summary(path, digest, files, traffic=123456, config="cfg2", knobs="pixel_rows=4,heavy_threshold=2147483647"):
+    path.write_text(f"# test capture\n\nconfig: {config}\nknobs: {knobs}\ntraffic_bytes_per_launch: {traffic}\n"
                     f"kernel_source_sha256_16: {digest} ({', '.join(files)})\n")
 
 
@@ -63,15 +63,21 @@ def test_profiled_traffic_reads_a_current_capture(tmp_path, monkeypatch):
     files = ["render_bwd.cu", "bgs_internal.cuh"]
     p = tmp_path / "cap.md"
     _summary(p, bench.kernel_code_hash(files), files)
-    monkeypatch.setitem(bench.PROFILED, "k_test", str(p))
+    monkeypatch.setitem(bench.PROFILED, "k_test", [str(p)])
     assert bench.profiled_traffic("k_test", "cfg2", TUNED) == (123456, str(p))
+    # several captures: the one of the run's workload is used
+    q = tmp_path / "cap5.md"
+    _summary(q, bench.kernel_code_hash(files), files, traffic=777, config="cfg5")
+    monkeypatch.setitem(bench.PROFILED, "k_test", [str(p), str(q)])
+    assert bench.profiled_traffic("k_test", "cfg5", TUNED) == (777, str(q))
+    assert bench.profiled_traffic("k_test", "cfg5@0.25", TUNED)[0] is None  # a reduced scale is another workload
 
 
 def test_profiled_traffic_rejects_stale_or_foreign_captures(tmp_path, monkeypatch):
     files = ["render_bwd.cu", "bgs_internal.cuh"]
     p = tmp_path / "cap.md"
     _summary(p, "0" * 16, files)  # recorded against other kernel sources
-    monkeypatch.setitem(bench.PROFILED, "k_test", str(p))
+    monkeypatch.setitem(bench.PROFILED, "k_test", [str(p)])
     t, why = bench.profiled_traffic("k_test", "cfg2", TUNED)
     assert t is None and "changed" in why
     _summary(p, bench.kernel_code_hash(files), files)
