@@ -245,6 +245,25 @@ struct FwdArgs {
     int chunk;
 };
 
+// A pixel's record of one Gaussian-wise segment (2 x 16 bytes), per (segment item, pixel).
+// Written by the segment item:
+//   cd = colour and depth accumulated with the segment's own transmittance from 1;
+//   t  = (transmittance after the segment, last contributor (index in the tile's list, bits;
+//        -1: none), contributing pairs (bits), entries up to and including the stop (bits)
+//        when the pixel stopped in the segment, else 0).
+// Rewritten by the merge, for every segment the pixel reaches when its list has several:
+//   cd = colour and depth accumulated behind the segment (with absolute weights, the
+//        background's T_f bg included);  t.x = the transmittance behind the segment.
+// That is the state a back-to-front walk holds when it enters the segment from behind.
+struct GwSum {
+    float4 cd;
+    float4 t;
+};
+
+__device__ __forceinline__ bool tile_is_gauss(int mode, int heavy_threshold, uint32_t n) {
+    return mode == BGS_MODE_GAUSSIAN || (mode == BGS_MODE_AUTO && n > (uint32_t)heavy_threshold);
+}
+
 struct BwdArgs {
     const Rec *recs;
     const float *means2D, *conic_opacity, *colors, *depths;
@@ -262,6 +281,11 @@ struct BwdArgs {
     unsigned int *warp_items;  // per warp of the persistent pass: items it completed
     int pixel_rows;
     int chunk;
+    // segmented walk of the tiles the last forward split (bseg_mode: its render mode, -1:
+    // none): the forward's per-tile segment item positions and boundary states
+    int bseg_mode, heavy_threshold, gw_pixels;
+    const uint2 *gw_tile;
+    const GwSum *gw_sum;
 };
 
 // Records a message for bgs_last_error() and returns code.
@@ -350,10 +374,16 @@ cudaError_t launch_pack(long long N, const float *means2D, const float *conic_op
 // gw_segment: entries per Gaussian-wise segment (0: lists are not split); exoff [num_tiles]
 // (nullable when gw_segment is 0) receives each tile's later-segment offset; extra_cap: the
 // most later-segment items the list may hold (beyond it the lists are not split).
+// bseg_mode >= 0 (a pixel-wise list for the backward): the tiles that the last forward, in
+// that render mode, split into segments get their pixel-wise items once per segment
+// (ctrl->gw_seg, the forward's segment length, is kept).  gw_tile [num_tiles] (nullable):
+// per Gaussian-wise tile of a forward list, (first first-segment item, first later-segment
+// item).
 cudaError_t launch_worklist_buckets(const uint2 *ranges, int num_tiles, const ViewTable &vt, int tile_w, int tile_h,
                                     int mode, int heavy_threshold, int lpt, int gw_pixels, int pixel_rows,
                                     int gw_segment, long long extra_cap, uint32_t *slot, uint32_t *exoff,
-                                    uint2 *items, long long capacity, DevCtrl *ctrl, cudaStream_t s);
+                                    uint2 *items, long long capacity, int bseg_mode, uint2 *gw_tile, DevCtrl *ctrl,
+                                    cudaStream_t s);
 // queue of the current list: rewind for another pass / mark exhausted (fault injection)
 cudaError_t launch_rewind_queue(DevCtrl *ctrl, cudaStream_t s);
 cudaError_t launch_exhaust_queue(DevCtrl *ctrl, cudaStream_t s);

@@ -93,7 +93,8 @@ struct bgs_plan {
     int smem_optin = 0;
     // render
     Buf recs, tile_idx, items, grad_acc, warp_items;  // tile_idx: each tile's slot in its work-list bucket
-    Buf gw_exoff, gw_sum;  // Gaussian-wise segments: per-tile later-segment offsets, per-item summaries
+    Buf gw_exoff, gw_sum, gw_tile;  // Gaussian-wise segments: per-tile later-segment offsets, per-item
+                                    // summaries, per-tile segment item positions
     // batched binning: depth keys of every view
     Buf vkey, vkey_sorted;
     // the views' depth sorts run concurrently on kSortStreams streams forked from the caller's
@@ -112,8 +113,13 @@ struct bgs_plan {
     struct WlKey {
         const void *ranges;
         bgs::ViewTable vt;
-        int tw, th, mode, heavy_threshold, gw_pixels, pixel_rows, lpt_order, gw_segment;
+        int tw, th, mode, heavy_threshold, gw_pixels, pixel_rows, lpt_order, gw_segment, bseg_mode;
     } wl_key;
+    // the last forward split Gaussian-wise lists into segments on the list of this key: a
+    // backward on the same arrays walks those tiles segment by segment from the boundary
+    // states the forward left in gw_sum (per tile: gw_tile)
+    WlKey gw_fwd_key;
+    bool gw_fwd_valid = false;
     bool rec_valid = false, wl_valid = false;
     unsigned int inject = 0;  // BGS_CHECK_* fault to inject into the next persistent pass
     // BGS_MODE_SELECT (Sec. 4.4)
@@ -226,7 +232,7 @@ int grid_for(const bgs_plan *p, const void *kernel, int threads) {
 
 // Builds the work list of the persistent kernels over the global tile space of the views (a3).
 bgs_plan::WlKey worklist_key(const bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt, int tw, int th,
-                             int mode) {
+                             int mode, int bseg_mode = -1) {
     bgs_plan::WlKey k;
     memset(&k, 0, sizeof k);  // padding included: keys are compared with memcmp
     k.ranges = ranges;
@@ -239,6 +245,7 @@ bgs_plan::WlKey worklist_key(const bgs_plan *p, const uint32_t *ranges, const bg
     k.pixel_rows = p->desc.pixel_rows;
     k.lpt_order = p->desc.lpt_order;
     k.gw_segment = p->desc.gw_segment;
+    k.bseg_mode = bseg_mode;
     return k;
 }
 
@@ -275,9 +282,11 @@ long long gw_extra_cap(const bgs_plan *p, int tw, int th, int64_t num_entries) {
 }
 
 // mode: the render mode; AUTO with a threshold no list can exceed queues every tile
-// pixel-wise and builds the same list as PIXEL (so a backward can reuse it).
+// pixel-wise and builds the same list as PIXEL (so a backward can reuse it).  bseg_mode >= 0
+// (with mode PIXEL, for a backward): the render mode of the last forward on these arrays,
+// whose split Gaussian-wise tiles get their pixel-wise items once per segment.
 int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt, int tw, int th, int mode,
-                   int64_t num_entries, cudaStream_t s) {
+                   int64_t num_entries, cudaStream_t s, int bseg_mode = -1) {
     if (mode == BGS_MODE_AUTO && (p->desc.heavy_threshold == INT32_MAX ||
                                   (int64_t)p->desc.heavy_threshold >= num_entries))
         mode = BGS_MODE_PIXEL;
@@ -289,7 +298,12 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
                                                    (tw * th + P - 1) / P);
     const bool gauss = gauss_possible(p, mode, num_entries);
     const long long extra_cap = gauss ? gw_extra_cap(p, tw, th, num_entries) : 0;
-    const long long max_items = (long long)T * per_tile + extra_cap;
+    // a segmented backward list: the tiles' pixel-wise items once per segment, at most as many
+    // more segments as the forward's split (which fit its budget) had
+    const long long pix_per_tile = ((tw + item_w - 1) / item_w) * ((th + item_h - 1) / item_h);
+    const long long bseg_extra =
+        bseg_mode >= 0 ? pix_per_tile * (gw_extra_cap(p, tw, th, num_entries) / gw_groups(p, tw, th) + 1) : 0;
+    const long long max_items = (long long)T * per_tile + extra_cap + bseg_extra;
     if (max_items >= (1ll << 31)) return fail(BGS_ERR_INVALID, "too many work items (%lld)", max_items);
     BGS_TRY(ensure(p, p->tile_idx, sizeof(uint32_t) * T, s, "tile_idx"));
     BGS_TRY(ensure(p, p->items, sizeof(uint2) * max_items, s, "items"));
@@ -299,15 +313,16 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
         // the later segments
         const long long gw_items = (long long)T * gw_groups(p, tw, th) + extra_cap;
         BGS_TRY(ensure(p, p->gw_sum, (size_t)gw_items * P * 2 * sizeof(float4), s, "gw_sum"));
+        BGS_TRY(ensure(p, p->gw_tile, sizeof(uint2) * T, s, "gw_tile"));
     }
     BGS_CUDA(bgs::launch_worklist_buckets(rg, T, vt, tw, th, mode, p->desc.heavy_threshold, p->desc.lpt_order, P,
                                           p->desc.pixel_rows, gauss ? p->desc.gw_segment : 0, extra_cap,
                                           (uint32_t *)p->tile_idx.p, gauss ? (uint32_t *)p->gw_exoff.p : nullptr,
-                                          (uint2 *)p->items.p, (long long)(p->items.bytes / sizeof(uint2)), p->ctrl,
-                                          s),
+                                          (uint2 *)p->items.p, (long long)(p->items.bytes / sizeof(uint2)), bseg_mode,
+                                          gauss ? (uint2 *)p->gw_tile.p : nullptr, p->ctrl, s),
              "build_worklist");
     p->host_launches += T > 0 ? 2 : 1;
-    p->wl_key = worklist_key(p, ranges, vt, tw, th, mode);
+    p->wl_key = worklist_key(p, ranges, vt, tw, th, mode, bseg_mode);
     p->wl_valid = true;
     return BGS_OK;
 }
@@ -396,7 +411,7 @@ int bgs_plan_destroy(bgs_plan *p) {
         for (Buf *b : sb)
             if (b->p) cudaFree(b->p);
     }
-    Buf *bufs[] = {&p->gw_exoff, &p->gw_sum, &p->vkey, &p->vkey_sorted, &p->touched, &p->touched_sorted, &p->dkey,
+    Buf *bufs[] = {&p->gw_exoff, &p->gw_sum, &p->gw_tile, &p->vkey, &p->vkey_sorted, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_idx, &p->items, &p->warp_items,
@@ -970,6 +985,8 @@ int render_forward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewOu
     if (mode != BGS_MODE_GAUSSIAN) BGS_CUDA(bgs::launch_forward_pixel(a, grid_p, gauss, s), "forward_pixel");
     if (gauss) BGS_CUDA(bgs::launch_forward_gw_merge(a, grid_for(p, bgs::forward_gw_merge_kernel(a.gw_pixels), threads), s),
                         "forward_gw_merge");
+    p->gw_fwd_valid = gauss;
+    p->gw_fwd_key = p->wl_key;
     kt.stop();
     p->host_launches += (gauss && mode != BGS_MODE_GAUSSIAN) ? 3 : (gauss ? 2 : 1);
     return BGS_OK;
@@ -985,6 +1002,7 @@ int render_backward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewG
     BGS_CUDA(cudaMemsetAsync(p->grad_acc.p, 0, sizeof(bgs::Rec) * n_records, s), "clear grad_acc");
     bgs::BwdArgs a;
     memset(&a, 0, sizeof a);
+    a.bseg_mode = -1;
     a.means2D = means2D;
     a.conic_opacity = conic_opacity;
     a.colors = colors;
@@ -1026,13 +1044,21 @@ int render_backward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewG
             p->rec_valid = true;
         }
         a.recs = (const bgs::Rec *)p->recs.p;
-        const bgs_plan::WlKey wk = worklist_key(p, ranges, vt, tw, th, BGS_MODE_PIXEL);
+        // the last forward on these arrays split Gaussian-wise lists: walk those tiles per segment
+        const bgs_plan::WlKey fk = worklist_key(p, ranges, vt, tw, th, mode);
+        const int bseg = (p->gw_fwd_valid && memcmp(&fk, &p->gw_fwd_key, sizeof fk) == 0) ? mode : -1;
+        a.bseg_mode = bseg;
+        a.heavy_threshold = p->desc.heavy_threshold;
+        a.gw_pixels = p->desc.gw_pixels;
+        a.gw_tile = bseg >= 0 ? (const uint2 *)p->gw_tile.p : nullptr;
+        a.gw_sum = bseg >= 0 ? (const bgs::GwSum *)p->gw_sum.p : nullptr;
+        const bgs_plan::WlKey wk = worklist_key(p, ranges, vt, tw, th, BGS_MODE_PIXEL, bseg);
         if (p->wl_valid && memcmp(&wk, &p->wl_key, sizeof wk) == 0) {
             // same list (no Gaussian-wise items): rewind its queue
             BGS_CUDA(bgs::launch_rewind_queue(p->ctrl, s), "rewind queue");
             p->host_launches += 1;
         } else {
-            BGS_TRY(build_worklist(p, ranges, vt, tw, th, BGS_MODE_PIXEL, num_entries, s));
+            BGS_TRY(build_worklist(p, ranges, vt, tw, th, BGS_MODE_PIXEL, num_entries, s, bseg));
         }
         a.items = (const uint2 *)p->items.p;
         const int grid = grid_for(p, bgs::backward_balanced_kernel(a), bgs::backward_balanced_block_threads());
@@ -1250,16 +1276,21 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
                  "view depth sort (size)");
         // the views' sorts are independent: fork them over the side streams (a fork-join of
         // events, which a graph capture records as such) and join before the binning
+        // (one view: no fork, everything on the caller's stream)
         const int NS = std::min<int>(V, kSortStreams);
+        auto stream_of = [&](int i) { return NS > 1 ? p->sort_stream[i] : s; };
         for (int i = 0; i < NS; ++i) BGS_TRY(ensure(p, p->sort_tmp[i], tmp, s, "sort_tmp"));
-        BGS_CUDA(cudaEventRecord(p->sort_fork, s), "sort fork");
-        for (int i = 0; i < NS; ++i) BGS_CUDA(cudaStreamWaitEvent(p->sort_stream[i], p->sort_fork, 0), "sort fork wait");
+        if (NS > 1) {
+            BGS_CUDA(cudaEventRecord(p->sort_fork, s), "sort fork");
+            for (int i = 0; i < NS; ++i)
+                BGS_CUDA(cudaStreamWaitEvent(p->sort_stream[i], p->sort_fork, 0), "sort fork wait");
+        }
         for (int v = 0; v < V; ++v) {
             const size_t o = (size_t)v * N;
             const int i = v % NS;
             size_t t = p->sort_tmp[i].bytes;
             BGS_CUDA(cub::DeviceRadixSort::SortPairs(p->sort_tmp[i].p, t, k0 + o, k1 + o, gidx + o, order + o,
-                                                     (int64_t)N, 0, 32, p->sort_stream[i]),
+                                                     (int64_t)N, 0, 32, stream_of(i)),
                      "view depth sort");
         }
         p->host_launches += 1;
@@ -1268,17 +1299,19 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
         // counts, then -- once the counts of the views before it are stored -- its lists
         for (int v = 0; v < V; ++v) {
             const int i = v % NS;
-            cudaStream_t si = p->sort_stream[i];
+            cudaStream_t si = stream_of(i);
             BinView bv;
             BGS_TRY(bin_view_a(p, i, v, N, order + (size_t)v * N, means2D, radii, conic_opacity, Ws[v], Hs[v], tw, th,
                                bv, si));
-            BGS_CUDA(cudaEventRecord(p->view_done[v], si), "view count done");
-            for (int u = 0; u < v; ++u)
-                if (u % NS != i) BGS_CUDA(cudaStreamWaitEvent(si, p->view_done[u], 0), "earlier view counts");
+            if (NS > 1) {
+                BGS_CUDA(cudaEventRecord(p->view_done[v], si), "view count done");
+                for (int u = 0; u < v; ++u)
+                    if (u % NS != i) BGS_CUDA(cudaStreamWaitEvent(si, p->view_done[u], 0), "earlier view counts");
+            }
             BGS_TRY(bin_view_b(p, i, v, N, bv, Ws[v], Hs[v], tw, th, point_list, capacity,
                                ranges + 2ull * vt.tile_base[v], si));
         }
-        for (int i = 0; i < NS; ++i) {
+        for (int i = 0; i < NS && NS > 1; ++i) {
             BGS_CUDA(cudaEventRecord(p->sort_join[i], p->sort_stream[i]), "binning join");
             BGS_CUDA(cudaStreamWaitEvent(s, p->sort_join[i], 0), "binning join wait");
         }

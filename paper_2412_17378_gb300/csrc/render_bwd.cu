@@ -263,10 +263,15 @@ cudaError_t launch_backward_static(const BwdArgs &a, cudaStream_t s) {
 // =====================================================================================
 // Pixel-wise item: an 8 x 4Q sub-block; lane l owns the pixels (l % 8, l / 8 + 4 q).  The
 // lane adds its pixels' contributions before the warp-wide reduction, so one reduction
-// serves 32 Q pixels.
+// serves 32 Q pixels.  In a tile that the last forward split into segments of L entries
+// (Gaussian-wise, reading the forward's boundary states), the item walks one segment
+// [e0, e1) of the list: a pixel whose last contributor lies behind the segment enters it
+// with the state the merge stored for it (T behind the segment, colour and depth behind it
+// over that T); one whose last contributor lies inside starts there as usual; the others
+// have nothing in it.
 template <int Q, bool Extra>
-__device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int sub, Rec *buf, uint32_t *gbuf,
-                                               int lane) {
+__device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int sub, unsigned L, Rec *buf,
+                                               uint32_t *gbuf, int lane) {
     constexpr int kItemW = pix_item_w(Q), kItemH = pix_item_h(Q), kRowStep = pix_row_step(Q);
     const int v = view_of(a.vt, tile);
     const int lt = tile - a.vt.tile_base[v];
@@ -274,19 +279,48 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
     const int x0 = tx * a.tile_w, y0 = ty * a.tile_h;
     const int vw = min(a.tile_w, a.vt.W[v] - x0), vh = min(a.tile_h, a.vt.H[v] - y0);
     const int cxs = (vw + kItemW - 1) / kItemW;
+    const uint2 rg = load_range_bwd(a, tile);
+    const int n = (int)(rg.y - rg.x);
+    // the segment of a split tile (seg < 0: the whole list)
+    int seg = -1;
+    uint32_t e0 = rg.x, e1 = rg.y;
+    if (L != 0u && (uint32_t)n > L && tile_is_gauss(a.bseg_mode, a.heavy_threshold, (uint32_t)n)) {
+        const int per_tile = cxs * ((vh + kItemH - 1) / kItemH);
+        seg = sub / per_tile;
+        sub -= seg * per_tile;
+        e0 = rg.x + (uint32_t)seg * L;
+        e1 = (uint32_t)min((unsigned long long)rg.y, (unsigned long long)e0 + L);
+    }
     const int sx = sub % cxs, sy = sub / cxs;
     const int px = x0 + sx * kItemW + (lane % kItemW);
     const int py0 = y0 + sy * kItemH + (lane / kItemW);
-    const uint2 rg = load_range_bwd(a, tile);
-    const int n = (int)(rg.y - rg.x);
     PixState s[Q];
     float pyf[Q];
     int maxnc = 0;
+    const int P = a.gw_pixels, groups = (vw * vh + P - 1) / P;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int py = py0 + kRowStep * q;
-        s[q] = load_pixel(a, v, px, py, px < x0 + vw && py < y0 + vh);
+        const bool inside = px < x0 + vw && py < y0 + vh;
+        s[q] = load_pixel(a, v, px, py, inside);
         if (s[q].nc > n) s[q].nc = n;
+        if (seg >= 0) {
+            const uint32_t end = rg.x + (uint32_t)s[q].nc;  // one past the last contributor
+            if (end <= e0) {
+                s[q].nc = 0;  // nothing of this pixel in the segment
+            } else if (end >= e1 && inside) {
+                // enter from behind: the merge's state at the segment's end
+                const int qp = (py - y0) * vw + (px - x0), group = qp / P;
+                const uint2 gt = a.gw_tile[tile];
+                const size_t si = seg == 0 ? (size_t)gt.x + group : (size_t)gt.y + (size_t)(seg - 1) * groups + group;
+                const GwSum st = a.gw_sum[si * P + qp % P];
+                const float iT = 1.f / st.t.x;
+                s[q].T = st.t.x;
+                s[q].Rg = (st.cd.x * s[q].g0 + st.cd.y * s[q].g1 + st.cd.z * s[q].g2) * iT;
+                s[q].Rd = st.cd.w * iT;
+                s[q].nc = (int)(e1 - rg.x);
+            }
+        }
         maxnc = max(maxnc, s[q].nc);
         pyf[q] = (float)py;
     }
@@ -295,8 +329,8 @@ __device__ __forceinline__ void bwd_pixel_item(const BwdArgs &a, int tile, int s
     const float pxf = (float)px;
     const float bcx = (float)(x0 + sx * kItemW) + 0.5f * (kItemW - 1);
     const float bcy = (float)(y0 + sy * kItemH) + 0.5f * (kItemH - 1);
-    for (uint32_t top = hi; top > rg.x;) {
-        const uint32_t lo = top - min(32u, top - rg.x);
+    for (uint32_t top = hi; top > e0;) {
+        const uint32_t lo = top - min(32u, top - e0);
         const int cnt = (int)(top - lo);
         bool hit = false;
         __syncwarp();
@@ -340,6 +374,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32, (Q <= 4 && !Extra) ? 4 : (Q <=
     uint32_t *gbuf = sidx[warp];
     const unsigned num_items = a.ctrl->num_items;
     const unsigned chunk = (unsigned)a.chunk;
+    // segment length of the tiles the last forward split (0: no segmented walk)
+    const unsigned L = a.bseg_mode >= 0 ? a.ctrl->gw_seg : 0u;
     unsigned long long st_items = 0;
     while (true) {
         unsigned first = 0;
@@ -349,7 +385,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, (Q <= 4 && !Extra) ? 4 : (Q <=
         const unsigned end = min(first + chunk, num_items);
         for (unsigned it = first; it < end; ++it) {
             const uint2 item = a.items[it];
-            bwd_pixel_item<Q, Extra>(a, (int)item.x, (int)(item.y & ~kKindGauss), buf, gbuf, lane);
+            bwd_pixel_item<Q, Extra>(a, (int)item.x, (int)(item.y & ~kKindGauss), L, buf, gbuf, lane);
             ++st_items;
         }
     }

@@ -305,13 +305,6 @@ __device__ __forceinline__ unsigned gw_group_mask(int pl) {
     return pat << pl;
 }
 
-struct GwSum {  // a pixel's summary of one segment (2 x 16 bytes)
-    float4 cd;  // colour and depth, accumulated with the segment's own transmittance from 1
-    float4 t;   // x = transmittance after the segment; y = last contributor (index in the
-                // tile's list, bits; -1: none); z = contributing pairs (bits); w = entries up
-                // to and including the stop (bits) when the pixel stopped in the segment, else 0
-};
-
 __device__ __forceinline__ void gw_item_pixel(const TileGeom &tg, int group, int P, int p, bool &ok, float &pxf,
                                               float &pyf) {
     const int npix = tg.vw * tg.vh;
@@ -586,7 +579,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_gw_merge(FwdArg
     __shared__ uint32_t idx_s[kWarpsPerBlock][kGwIdx];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned num_first = a.ctrl->num_gauss0;
-    const GwSum *sums = reinterpret_cast<const GwSum *>(a.gw_sum);
+    GwSum *sums = reinterpret_cast<GwSum *>(a.gw_sum);  // rewritten in place, see below
     const uint32_t L = a.ctrl->gw_seg;
     unsigned long long st_eval = 0, st_acc = 0;
     for (unsigned it = blockIdx.x * kWarpsPerBlock + warp; it < num_first; it += gridDim.x * kWarpsPerBlock) {
@@ -606,9 +599,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_gw_merge(FwdArg
             if (!ok) break;
             float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, D = 0.f;
             int last = -1, nacc = 0, stop = 0;
+            uint32_t s_end = S - 1u;  // the last segment the pixel reaches
             for (uint32_t sg = 0; sg < S; ++sg) {
                 const size_t si = sg == 0u ? (size_t)it : later + (size_t)(sg - 1u) * groups;
-                const GwSum sm = sums[si * P + p];
+                GwSum *slot = sums + si * P + p;
+                const GwSum sm = *slot;
                 const int sst = __float_as_int(sm.t.w);
                 if (sg == 0u && sst) {  // stopped in the first segment, resolved there
                     T = sm.t.x;
@@ -616,33 +611,66 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_gw_merge(FwdArg
                     last = __float_as_int(sm.t.y);
                     nacc = __float_as_int(sm.t.z);
                     stop = sst;
+                    s_end = 0u;
                     break;
                 }
+                const float T_in = T;
+                float a0, a1, a2, ad;  // the segment's colour and depth with absolute weights
+                bool stopped = false;
                 if (T * sm.t.x >= kTMin) {
-                    c0 += T * sm.cd.x;
-                    c1 += T * sm.cd.y;
-                    c2 += T * sm.cd.z;
-                    D += T * sm.cd.w;
+                    a0 = T * sm.cd.x, a1 = T * sm.cd.y, a2 = T * sm.cd.z, ad = T * sm.cd.w;
                     T *= sm.t.x;
                     last = max(last, __float_as_int(sm.t.y));
                     nacc += __float_as_int(sm.t.z);
-                    continue;
+                } else {
+                    const uint32_t e0 = S > 1u ? rg.x + sg * L : rg.x;
+                    const uint32_t e1 =
+                        S > 1u ? (uint32_t)min((unsigned long long)rg.y, (unsigned long long)e0 + L) : rg.y;
+                    float Tw = T, w0 = 0.f, w1 = 0.f, w2 = 0.f, wd = 0.f;
+                    int lw = last, nw = 0, sw = 0;
+                    bool live = true;
+                    gw_walk<1, 1>(a, e0, e1, rg.x, &pxf, &pyf, true, idx_s[warp], lane, &Tw, &w0, &w1, &w2, &wd, &lw,
+                                  &nw, &sw, &live);
+                    gw_group_sum5<1>(w0, w1, w2, wd, nw);
+                    a0 = w0, a1 = w1, a2 = w2, ad = wd;
+                    T = Tw;
+                    last = lw;
+                    nacc += nw;
+                    if (sw) {
+                        stop = sw;
+                        stopped = true;
+                    }
                 }
-                const uint32_t e0 = S > 1u ? rg.x + sg * L : rg.x;
-                const uint32_t e1 = S > 1u ? (uint32_t)min((unsigned long long)rg.y, (unsigned long long)e0 + L) : rg.y;
-                float Tw = T, w0 = 0.f, w1 = 0.f, w2 = 0.f, wd = 0.f;
-                int lw = last, nw = 0, sw = 0;
-                bool live = true;
-                gw_walk<1, 1>(a, e0, e1, rg.x, &pxf, &pyf, true, idx_s[warp], lane, &Tw, &w0, &w1, &w2, &wd, &lw,
-                              &nw, &sw, &live);
-                gw_group_sum5<1>(w0, w1, w2, wd, nw);
-                c0 += w0, c1 += w1, c2 += w2, D += wd;
-                T = Tw;
-                last = lw;
-                nacc += nw;
-                if (sw) {
-                    stop = sw;
+                c0 += a0, c1 += a1, c2 += a2, D += ad;
+                // the slot now holds the segment's absolute contribution and entry T (the
+                // backward's boundary states are formed from them below); every lane has read it
+                __syncwarp();
+                if (S > 1u && lane == 0) {
+                    GwSum o;
+                    o.cd = make_float4(a0, a1, a2, ad);
+                    o.t = make_float4(T_in, 0.f, 0.f, 0.f);
+                    *slot = o;
+                }
+                if (stopped) {
+                    s_end = sg;
                     break;
+                }
+            }
+            // Boundary states for a segmented backward: per segment u the pixel reaches, the
+            // transmittance behind it (in front of segment u + 1, or the final T) and the
+            // colour and depth accumulated behind it with absolute weights, background
+            // included -- summed from the back, so no difference of two sums is formed.
+            if (S > 1u && lane == 0 && s_end > 0u) {
+                float b0 = T * a.bg[0], b1 = T * a.bg[1], b2 = T * a.bg[2], bd = 0.f, Tnext = T;
+                for (int u = (int)s_end; u >= 0; --u) {
+                    GwSum *slot = sums + ((u == 0 ? (size_t)it : later + (size_t)(u - 1) * groups) * P + p);
+                    const GwSum sm = *slot;
+                    GwSum o;
+                    o.cd = make_float4(b0, b1, b2, bd);
+                    o.t = make_float4(Tnext, 0.f, 0.f, 0.f);
+                    *slot = o;
+                    b0 += sm.cd.x, b1 += sm.cd.y, b2 += sm.cd.z, bd += sm.cd.w;
+                    Tnext = sm.t.x;
                 }
             }
             const int neval = stop ? stop : (int)n;

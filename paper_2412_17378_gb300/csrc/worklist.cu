@@ -20,10 +20,6 @@
 
 namespace bgs {
 
-__device__ __forceinline__ bool tile_is_gauss(int mode, int heavy_threshold, uint32_t n) {
-    return mode == BGS_MODE_GAUSSIAN || (mode == BGS_MODE_AUTO && n > (uint32_t)heavy_threshold);
-}
-
 // Items of tile t: Gaussian-wise (first segments), P pixels each; else pixel-wise sub-blocks of
 // its visible part.
 __device__ __forceinline__ uint32_t tile_items(int t, bool gauss, const ViewTable &vt, int tile_w, int tile_h,
@@ -35,6 +31,15 @@ __device__ __forceinline__ uint32_t tile_items(int t, bool gauss, const ViewTabl
     if (gauss) return (uint32_t)((vw * vh + gw_pixels - 1) / gw_pixels);
     const int iw = pix_item_w(pixel_rows), ih = pix_item_h(pixel_rows);
     return (uint32_t)(((vw + iw - 1) / iw) * ((vh + ih - 1) / ih));
+}
+
+// Items of a pixel-wise list's tile that the forward rendered Gaussian-wise with its list
+// split into segments of L entries (bseg_mode: the forward's render mode, -1 for a list
+// without segments): the tile's c pixel-wise items once per segment (sub-item = segment *
+// c + item), so that the backward walks each segment on its own.
+__device__ __forceinline__ uint32_t bwd_segments(int bseg_mode, int heavy_threshold, unsigned L, uint32_t n) {
+    if (bseg_mode < 0 || L == 0u || n <= L || !tile_is_gauss(bseg_mode, heavy_threshold, n)) return 1u;
+    return (n - 1u) / L + 1u;
 }
 
 // Later-segment items of a Gaussian-wise tile with first-segment items `groups` and list
@@ -79,7 +84,7 @@ __global__ void __launch_bounds__(kWlcThreads) k_wl_count(const uint2 *__restric
                                                            int tile_w, int tile_h, int mode, int heavy_threshold,
                                                            int lpt, int gw_pixels, int pixel_rows, int gw_segment,
                                                            long long extra_cap, uint32_t *__restrict__ slot,
-                                                           uint32_t *__restrict__ exoff, DevCtrl *ctrl) {
+                                                           uint32_t *__restrict__ exoff, int bseg_mode, DevCtrl *ctrl) {
     using Scan = cub::BlockScan<uint32_t, kWlcThreads>;
     using Scan64 = cub::BlockScan<unsigned long long, kWlcThreads>;
     __shared__ union {
@@ -92,6 +97,8 @@ __global__ void __launch_bounds__(kWlcThreads) k_wl_count(const uint2 *__restric
     s_cnt[threadIdx.x] = 0u;
     __syncthreads();
     const int t = blockIdx.x * kWlcThreads + threadIdx.x;
+    // a backward list segmented like the last forward: that forward's segment length
+    const unsigned Lb = bseg_mode >= 0 ? *((volatile unsigned int *)&ctrl->gw_seg) : 0u;
     uint32_t key = 0u, local = 0u;
     unsigned long long extra = 0ull;
     if (t < T) {
@@ -99,7 +106,8 @@ __global__ void __launch_bounds__(kWlcThreads) k_wl_count(const uint2 *__restric
         const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
         const bool gauss = tile_is_gauss(mode, heavy_threshold, n);
         key = wl_sort_key(n, gauss, lpt);
-        const uint32_t c = tile_items(t, gauss, vt, tile_w, tile_h, gw_pixels, pixel_rows);
+        const uint32_t c = tile_items(t, gauss, vt, tile_w, tile_h, gw_pixels, pixel_rows) *
+                           (gauss ? 1u : bwd_segments(bseg_mode, heavy_threshold, Lb, n));
         local = atomicAdd(&s_cnt[key], c);
         extra = tile_extra(gauss, c, n, gw_segment);
     }
@@ -127,7 +135,8 @@ __global__ void __launch_bounds__(kWlcThreads) k_wl_count(const uint2 *__restric
         const unsigned long long E = gw_segment > 0 ? atomicExch(&ctrl->wl_extra, 0ull) : 0ull;
         const bool split = gw_segment > 0 && E <= (unsigned long long)extra_cap;
         s_xbase = split ? E : 0ull;
-        ctrl->gw_seg = split ? (unsigned int)gw_segment : 0u;
+        // a segmented backward list keeps the forward's segment length (its kernel reads it)
+        if (bseg_mode < 0) ctrl->gw_seg = split ? (unsigned int)gw_segment : 0u;
     }
     __syncthreads();
     const uint32_t E = (uint32_t)s_xbase;
@@ -162,13 +171,16 @@ __global__ void __launch_bounds__(256) k_wl_emit(const uint2 *__restrict__ range
                                                  int tile_w, int tile_h, int mode, int heavy_threshold, int lpt,
                                                  int gw_pixels, int pixel_rows, const uint32_t *__restrict__ slot,
                                                  const uint32_t *__restrict__ exoff, uint2 *__restrict__ items,
-                                                 long long capacity, DevCtrl *ctrl) {
+                                                 long long capacity, int bseg_mode, uint2 *__restrict__ gw_tile,
+                                                 DevCtrl *ctrl) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     const uint2 rg = ranges[t];
     const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
     const bool gauss = tile_is_gauss(mode, heavy_threshold, n);
-    const uint32_t c = tile_items(t, gauss, vt, tile_w, tile_h, gw_pixels, pixel_rows);
+    const unsigned Lb = bseg_mode >= 0 ? ctrl->gw_seg : 0u;
+    const uint32_t c = tile_items(t, gauss, vt, tile_w, tile_h, gw_pixels, pixel_rows) *
+                       (gauss ? 1u : bwd_segments(bseg_mode, heavy_threshold, Lb, n));
     const long long pos = (long long)ctrl->wl_off[wl_sort_key(n, gauss, lpt)] + slot[t];
     if (pos + (long long)c > capacity) {
         raise_check(ctrl, BGS_CHECK_OVERFLOW);
@@ -178,6 +190,8 @@ __global__ void __launch_bounds__(256) k_wl_emit(const uint2 *__restrict__ range
     for (uint32_t q = 0; q < c; ++q) items[pos + q] = make_uint2((uint32_t)t, kindbit | q);
     const int seg = (int)ctrl->gw_seg;
     const unsigned long long x = tile_extra(gauss, c, n, seg);
+    // where a Gaussian-wise tile's segment items sit (for a backward that reads their summaries)
+    if (gw_tile && gauss) gw_tile[t] = make_uint2((uint32_t)pos, x ? ctrl->num_gauss0 + exoff[t] : 0u);
     if (x == 0ull) return;
     const long long xpos = (long long)ctrl->num_gauss0 + exoff[t];
     if (xpos + (long long)x > capacity) {
@@ -190,15 +204,18 @@ __global__ void __launch_bounds__(256) k_wl_emit(const uint2 *__restrict__ range
 cudaError_t launch_worklist_buckets(const uint2 *ranges, int num_tiles, const ViewTable &vt, int tile_w, int tile_h,
                                     int mode, int heavy_threshold, int lpt, int gw_pixels, int pixel_rows,
                                     int gw_segment, long long extra_cap, uint32_t *slot, uint32_t *exoff,
-                                    uint2 *items, long long capacity, DevCtrl *ctrl, cudaStream_t s) {
+                                    uint2 *items, long long capacity, int bseg_mode, uint2 *gw_tile, DevCtrl *ctrl,
+                                    cudaStream_t s) {
     if (num_tiles < 0 || (gw_segment > 0 && !exoff)) return cudaErrorInvalidValue;
     const int blocks = num_tiles > 0 ? (num_tiles + kWlcThreads - 1) / kWlcThreads : 1;
     k_wl_count<<<blocks, kWlcThreads, 0, s>>>(ranges, num_tiles, vt, tile_w, tile_h, mode, heavy_threshold, lpt,
-                                              gw_pixels, pixel_rows, gw_segment, extra_cap, slot, exoff, ctrl);
+                                              gw_pixels, pixel_rows, gw_segment, extra_cap, slot, exoff, bseg_mode,
+                                              ctrl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || num_tiles == 0) return e;
     k_wl_emit<<<(num_tiles + 255) / 256, 256, 0, s>>>(ranges, num_tiles, vt, tile_w, tile_h, mode, heavy_threshold,
-                                                      lpt, gw_pixels, pixel_rows, slot, exoff, items, capacity, ctrl);
+                                                      lpt, gw_pixels, pixel_rows, slot, exoff, items, capacity,
+                                                      bseg_mode, gw_tile, ctrl);
     return cudaGetLastError();
 }
 

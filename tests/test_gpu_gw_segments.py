@@ -212,3 +212,86 @@ def test_autotuner_picks_gaussian_wise_on_the_heavy_frame(R):
         assert (a["n_contrib"] != b["n_contrib"]).float().mean().item() < 1e-4
     finally:
         plan.close()
+
+
+# ----------------------------------------------------------------- segmented backward
+
+def _backward(R, plan, inp, mode, seed=0, extra=True, bg=(0.2, 0.4, 0.6)):
+    """Forward then backward on one plan (a Gaussian-wise forward that split lists makes the
+    backward walk those tiles segment by segment); the oracle's gradient for the same
+    upstream gradients, with its |term| sums."""
+    from helpers import compare_grads  # noqa: F401  (used by the callers)
+    W, H = inp["W"], inp["H"]
+    rng = np.random.default_rng(seed)
+    ref_f = oracle_ref(inp, bg=bg)
+    gC = rng.normal(size=(3, H, W)).astype(np.float32)
+    gD = (0.1 * rng.normal(size=(H, W))).astype(np.float32) if extra else None
+    gA = rng.normal(size=(H, W)).astype(np.float32) if extra else None
+    fl = ref_f["flags"] != 0
+    gC[:, fl] = 0
+    if extra:
+        gD[fl] = 0
+        gA[fl] = 0
+    ref = oracle.render_backward(inp["means2D"], inp["conic_opacity"], inp["colors"], inp["depths"],
+                                 inp["point_list"], inp["ranges"], W, H, gC, gD, gA, inp["tile"][0], inp["tile"][1],
+                                 bg=bg, abs_terms=True)
+    g = to_gpu(inp)
+    out = R.render_forward(plan, g["means2D"], g["conic_opacity"], g["colors"], g["depths"], g["point_list"], g["K"],
+                           g["ranges"], W, H, inp["tile"], bg, mode)
+    dev = lambda a: None if a is None else torch.from_numpy(a).cuda()
+    plan.reset_stats()
+    grads = R.render_backward(plan, g["means2D"], g["conic_opacity"], g["colors"], g["depths"], g["point_list"],
+                              g["K"], g["ranges"], W, H, out["final_T"], out["n_contrib"], dev(gC), dev(gD), dev(gA),
+                              inp["tile"], bg, mode)
+    torch.cuda.synchronize()
+    plan.check()
+    return {k: v.detach().cpu().numpy() for k, v in grads.items()}, ref, int(ref_f["n_contrib"].max()), plan.stats()
+
+
+@pytest.mark.parametrize("kind", ["mixed", "uniform", "open"])
+@pytest.mark.parametrize("P,L,rows", [(4, 256, 2), (8, 2048, 4), (16, 512, 1)])
+def test_segmented_backward_on_heavy_stacks(R, kind, P, L, rows):
+    """The backward of a forward that split the stack's lists walks every segment on its own
+    from the boundary state the merge stored; element-wise against the oracle."""
+    from helpers import compare_grads
+    inp = stack(kind, n=11000, seed=4)
+    plan = R.Plan(heavy_threshold=64, gw_pixels=P, gw_segment=L, pixel_rows=rows)
+    try:
+        got, ref, ncmax, st = _backward(R, plan, inp, "auto")
+        # one pixel-wise item per (sub-block, segment): more items than the tiles' sub-blocks
+        per_tile = (16 // 8) * (16 // (4 * rows))
+        assert st["last_num_items"] > 4 * per_tile, st
+        compare_grads(got, ref, keys=("means2D", "conic", "opacity", "colors", "depths"),
+                      what=f"{kind} P={P} L={L}", n_contrib_max=ncmax)
+    finally:
+        plan.close()
+
+
+def test_segmented_backward_equals_the_unsegmented_walk(R):
+    """Same frame, same upstream gradients: the segmented walk (after a Gaussian-wise forward)
+    and the plain walk from the last contributor (after a pixel-wise forward) agree to the
+    per-tensor parity bar (rel-L2 1e-3): the plain walk recovers T through ~10^4 divisions
+    from the final T, the segmented one from each segment's end (both are within the
+    element-wise oracle bounds, tested above)."""
+    inp = stack("mixed", 37, 29, (16, 8), n=10500, seed=5)
+    plan = R.Plan(heavy_threshold=64, gw_pixels=8, gw_segment=256)
+    try:
+        seg, ref, _, st_seg = _backward(R, plan, inp, "auto", seed=3)
+        pix, _, _, st_pix = _backward(R, plan, inp, "pixel", seed=3)
+        assert st_seg["last_num_items"] > st_pix["last_num_items"]
+        for k in ("means2D", "conic", "opacity", "colors", "depths"):
+            d = np.linalg.norm(seg[k] - pix[k]) / max(np.linalg.norm(pix[k]), 1e-30)
+            assert d < 1e-3, (k, d)
+    finally:
+        plan.close()
+
+
+def test_segmented_backward_on_the_heavy_veil_frame(R, heavy):
+    from helpers import compare_grads
+    inp = heavy
+    plan = R.Plan(heavy_threshold=2048, gw_pixels=8, gw_segment=2048, pixel_rows=2)
+    try:
+        got, ref, ncmax, st = _backward(R, plan, inp, "auto", extra=False, bg=(0.0, 0.0, 0.0))
+        compare_grads(got, ref, what="heavy veil", n_contrib_max=ncmax)
+    finally:
+        plan.close()
