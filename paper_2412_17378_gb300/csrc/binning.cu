@@ -74,13 +74,32 @@ __global__ void __launch_bounds__(kCountThreads) k_bin_count(long long N, int G,
                                                    int tw, int th, int tx, int ty, uint32_t *__restrict__ H,
                                                    uint4 *__restrict__ rect, uint32_t *__restrict__ masks, int W32,
                                                    int b_off, const int *__restrict__ skipP) {
-    extern __shared__ __align__(16) uint32_t d_s[];  // [T] tile counters, then (16-byte aligned) [nC][16] mask words
+    // [T] tile counters, then (16-byte aligned) [nC][16] mask words, then [nC / 32] bits of
+    // the groups whose tiles all stopped before this pass
+    extern __shared__ __align__(16) uint32_t d_s[];
     const int T = tx * ty;
-    const int ncx = (tx + kCbW - 1) / kCbW, nC = ncx * ((ty + kCbH - 1) / kCbH);
+    const int ncx = (tx + kCbW - 1) / kCbW, ncy = (ty + kCbH - 1) / kCbH, nC = ncx * ncy;
     const int T4 = (T + 3) & ~3;
-    uint32_t *m_s = d_s + T4;
+    uint32_t *m_s = d_s + T4, *closed_s = m_s + 16 * nC;
     const int b = blockIdx.x + b_off, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int t = threadIdx.x; t < T4 + 16 * nC; t += blockDim.x) d_s[t] = 0u;
+    if (skipP) {
+        // a group whose tiles all stopped before this pass: no list reaches this block there,
+        // and the scatter opens no (block, group) item of it, so its mask words are not written
+        const int w1 = tx + 1;
+        for (int c0 = warp * 32; c0 < nC; c0 += nwarps * 32) {
+            const int C = c0 + lane;
+            bool closed = false;
+            if (C < nC) {
+                const int gx0 = (C % ncx) * kCbW, gy0 = (C / ncx) * kCbH;
+                const int gx1 = min(gx0 + kCbW, tx), gy1 = min(gy0 + kCbH, ty);
+                const int n = skipP[gy1 * w1 + gx1] - skipP[gy0 * w1 + gx1] - skipP[gy1 * w1 + gx0] + skipP[gy0 * w1 + gx0];
+                closed = n == (gx1 - gx0) * (gy1 - gy0);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, closed);
+            if (lane == 0) closed_s[c0 >> 5] = m;
+        }
+    }
     __syncthreads();
     const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
     // 512 Gaussians (16 mask words per C) at a time
@@ -122,7 +141,9 @@ __global__ void __launch_bounds__(kCountThreads) k_bin_count(long long N, int G,
         // word arrays are 16-word aligned: W32 is a multiple of 16)
         for (int k = threadIdx.x; k < 4 * nC; k += blockDim.x) {
             uint4 *src = reinterpret_cast<uint4 *>(m_s) + k;
-            reinterpret_cast<uint4 *>(masks + ((size_t)b * nC + (k >> 2)) * W32 + 16 * sub)[k & 3] = *src;
+            const int C = k >> 2;
+            if (!skipP || !((closed_s[C >> 5] >> (C & 31)) & 1u))
+                reinterpret_cast<uint4 *>(masks + ((size_t)b * nC + C) * W32 + 16 * sub)[k & 3] = *src;
             *src = make_uint4(0u, 0u, 0u, 0u);
         }
         __syncthreads();
@@ -674,7 +695,7 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const u
 
 size_t bin_count_smem(int tx, int ty) {
     const size_t nC = (size_t)((tx + kCbW - 1) / kCbW) * ((ty + kCbH - 1) / kCbH);
-    return sizeof(uint32_t) * ((((size_t)tx * ty + 3) & ~(size_t)3) + 16 * nC);
+    return sizeof(uint32_t) * ((((size_t)tx * ty + 3) & ~(size_t)3) + 16 * nC + (nC + 31) / 32);
 }
 
 int bin_mask_groups(int tx, int ty) { return ((tx + kCbW - 1) / kCbW) * ((ty + kCbH - 1) / kCbH); }
