@@ -611,24 +611,10 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const u
         uint32_t done = pos & ~7u;  // positions below done are written (or precede the run)
         const uint32_t *mk = masks + ((size_t)b * nC + C) * W32;
         const uint32_t s0 = (uint32_t)b * G;
-        for (int wb = 0; wb < W32; wb += 16) {  // 512 Gaussians per pass
-            uint32_t word = lane < 16 ? mk[wb + lane] : 0u;
-            const uint32_t cnt = (uint32_t)__popc(word);
-            uint32_t incl = cnt;
-            for (int o = 1; o < 16; o <<= 1) {
-                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += u;
-            }
-            int total = (int)__shfl_sync(0xffffffffu, incl, 15);
-            if (total == 0) continue;
-            // compact the flagged positions in depth order (word by word, bit by bit)
-            uint32_t off = incl - cnt;
-            while (word) {
-                const int bit = __ffs(word) - 1;
-                word &= word - 1u;
-                hit_s[off++].y = s0 + 32u * (uint32_t)(wb + lane) + (uint32_t)bit;
-            }
-            __syncwarp();
+        // The flagged positions of the item's mask words, 16 words (512 Gaussians) a pass,
+        // gathered in depth order into hit_s across passes and visited in batches of up to 512
+        // hits: one round of rectangle gathers serves all passes of a sparse item.
+        auto visit = [&](int total) {
             // per flagged Gaussian: the lanes whose tile its rectangle covers (a nonempty
             // rectangle meeting the group: the masks flag no other), among the lanes whose
             // list is still open; hits that reach no such lane are dropped (in place: a hit
@@ -654,11 +640,10 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const u
                 kept += __popc(keep);
             }
             __syncwarp();
-            total = kept;
-            // depth order, 8 visits at a time, then the remaining total % 8 one by one; at most 8
+            // depth order, 8 visits at a time, then the remaining kept % 8 one by one; at most 8
             // appends between two checks: at most one newly completed sector, and no ring slot
             // overwritten before it is written out
-            const int full = total & ~7;
+            const int full = kept & ~7;
             for (int k0 = 0; k0 < full; k0 += 8) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -673,8 +658,8 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const u
                     done += 8u;
                 }
             }
-            if (full < total) {
-                for (int k = full; k < total; ++k) {
+            if (full < kept) {
+                for (int k = full; k < kept; ++k) {
                     const uint2 e = hit_s[k];
                     ring[(pos & 15u) << 5] = e.y;
                     pos += (e.x >> lane) & 1u;
@@ -685,7 +670,35 @@ __global__ void __launch_bounds__(32) k_bin_scatter(uint32_t G, int W32, const u
                 }
             }
             __syncwarp();
+        };
+        int acc = 0;  // hits gathered in hit_s[0, acc)
+        uint32_t next = lane < 16 ? mk[lane] : 0u;
+        for (int wb = 0; wb < W32; wb += 16) {
+            uint32_t word = next;
+            next = (lane < 16 && wb + 16 < W32) ? mk[wb + 16 + lane] : 0u;  // the next pass's words, early
+            const uint32_t cnt = (uint32_t)__popc(word);
+            uint32_t incl = cnt;
+            for (int o = 1; o < 16; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            const int total = (int)__shfl_sync(0xffffffffu, incl, 15);
+            if (total == 0) continue;
+            if (acc + total > 512) {
+                visit(acc);
+                acc = 0;
+            }
+            // compact the flagged positions in depth order (word by word, bit by bit)
+            uint32_t off = (uint32_t)acc + incl - cnt;
+            while (word) {
+                const int bit = __ffs(word) - 1;
+                word &= word - 1u;
+                hit_s[off++].y = s0 + 32u * (uint32_t)(wb + lane) + (uint32_t)bit;
+            }
+            __syncwarp();
+            acc += total;
         }
+        if (acc) visit(acc);
         // the last, partial sector
         for (uint32_t p = done; p < pos; ++p)
             if (p >= run0 && p < capacity) point_list[p] = ring[(p & 15u) << 5];
