@@ -179,10 +179,11 @@ __device__ __forceinline__ float pair_power2(float4 a, float qc, float px, float
 // Transmittance after a pair, T (1 - alpha), as one fused multiply-add T - T alpha (one
 // rounding); the pixel-wise kernels (static, persistent, allocation-free) and the
 // backward's T recovery take their stop decision T' < 1e-4 on this value.  The
-// Gaussian-wise kernel forms T' as T times a warp prefix product of (1 - alpha), which
-// differs from this sequential chain by float32 rounding (a few ulp per 32-entry window);
-// a decision can only flip where T' lies within that rounding of 1e-4, inside the oracle's
-// |T' - 1e-4| < 1e-9 flag window.
+// Gaussian-wise kernels walk the entries of the stopping chunk with it too, but from a T in
+// front of the chunk that is a product of chunk products (reassociated: about 2 ulp per
+// 8-entry chunk and composition against this sequential chain), so a decision can only
+// flip where T' lies within that rounding of 1e-4: inside the oracle's |T' - 1e-4| < 1e-9
+// flag window at the list lengths of the tests.
 __device__ __forceinline__ float next_T(float T, float al) { return __fmaf_rn(-T, al, T); }
 
 __device__ __forceinline__ float pair_alpha(float power2, float o, float &G) {

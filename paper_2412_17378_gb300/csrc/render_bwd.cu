@@ -421,8 +421,34 @@ cudaError_t launch_backward_balanced(const BwdArgs &a, int grid, cudaStream_t s)
 
 // ---- accumulator -> ABI gradient arrays ----------------------------------------------
 // Record i's accumulator row -> its gradients.  Colours are shared by the views of a
-// batched call: when n_colors < N, the colour gradient of Gaussian g sums the rows
-// g, g + n_colors, ... (one per view) in k_grad_colors instead.
+// batched call when n_colors < N (records g, g + n_colors, ... are Gaussian g seen from
+// each view): then a thread takes Gaussian g, finalizes its records one view after another
+// and writes its colour gradient summed over them, reading each accumulator row once.
+__device__ __forceinline__ void finalize_record(long long i, const float4 *__restrict__ acc,
+                                                const float4 *__restrict__ conic_opacity,
+                                                float *__restrict__ dL_dmeans2D, float *__restrict__ dL_dconic,
+                                                float *__restrict__ dL_dopacity, float *__restrict__ dL_ddepths,
+                                                float &cr, float &cg, float &cb) {
+    const float4 a0 = acc[3 * i], a1 = acc[3 * i + 1], a2 = acc[3 * i + 2];
+    const float4 co = conic_opacity[i];
+    // power = ln2 * power2 with power2 = qa dx^2 + qb dx dy + qc dy^2 and (qa, qb, qc) the
+    // record's pre-scaled conic; d power / d mean = ln2 (2 qa dx + qb dy, 2 qc dy + qb dx),
+    // summed over the pairs from the moments sum gp dx (a0.x) and sum gp dy (a0.y);
+    // d power / d(a, b, c) = (-dx^2 / 2, -dx dy, -dy^2 / 2)
+    const float qa = -0.5f * kLog2e * co.x, qb = -kLog2e * co.y, qc = -0.5f * kLog2e * co.z;
+    dL_dmeans2D[2 * i] = kLn2 * (2.f * qa * a0.x + qb * a0.y);
+    dL_dmeans2D[2 * i + 1] = kLn2 * (2.f * qc * a0.y + qb * a0.x);
+    dL_dconic[3 * i] = -0.5f * a0.z;
+    dL_dconic[3 * i + 1] = -a0.w;
+    dL_dconic[3 * i + 2] = -0.5f * a1.x;
+    // sum gp / o = sum G dL/dalpha (a record with o = 0 has alpha = 0 everywhere: no pair)
+    dL_dopacity[i] = co.w > 0.f ? a1.y / co.w : 0.f;
+    if (dL_ddepths) dL_ddepths[i] = a2.y;
+    cr += a1.z;
+    cg += a1.w;
+    cb += a2.x;
+}
+
 __global__ void __launch_bounds__(256) k_grad_finalize(long long N, long long n_colors, const float4 *__restrict__ acc,
                                                        const float4 *__restrict__ conic_opacity,
                                                        float *__restrict__ dL_dmeans2D, float *__restrict__ dL_dconic,
@@ -444,44 +470,19 @@ __global__ void __launch_bounds__(256) k_grad_finalize(long long N, long long n_
             if (total != ctrl->num_items) atomicOr(&ctrl->check_bits, BGS_CHECK_QUEUE);
         }
     }
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const float4 a0 = acc[3 * i], a1 = acc[3 * i + 1], a2 = acc[3 * i + 2];
-    const float4 co = conic_opacity[i];
-    // power = ln2 * power2 with power2 = qa dx^2 + qb dx dy + qc dy^2 and (qa, qb, qc) the
-    // record's pre-scaled conic; d power / d mean = ln2 (2 qa dx + qb dy, 2 qc dy + qb dx),
-    // summed over the pairs from the moments sum gp dx (a0.x) and sum gp dy (a0.y);
-    // d power / d(a, b, c) = (-dx^2 / 2, -dx dy, -dy^2 / 2)
-    const float qa = -0.5f * kLog2e * co.x, qb = -kLog2e * co.y, qc = -0.5f * kLog2e * co.z;
-    dL_dmeans2D[2 * i] = kLn2 * (2.f * qa * a0.x + qb * a0.y);
-    dL_dmeans2D[2 * i + 1] = kLn2 * (2.f * qc * a0.y + qb * a0.x);
-    dL_dconic[3 * i] = -0.5f * a0.z;
-    dL_dconic[3 * i + 1] = -a0.w;
-    dL_dconic[3 * i + 2] = -0.5f * a1.x;
-    // sum gp / o = sum G dL/dalpha (a record with o = 0 has alpha = 0 everywhere: no pair)
-    dL_dopacity[i] = co.w > 0.f ? a1.y / co.w : 0.f;
-    if (n_colors == N) {
-        dL_dcolors[3 * i] = a1.z;
-        dL_dcolors[3 * i + 1] = a1.w;
-        dL_dcolors[3 * i + 2] = a2.x;
+    // a thread per record (colours per record), or per Gaussian over its views (shared colours)
+    const bool shared = n_colors > 0 && n_colors < N;
+    const long long stride = shared ? n_colors : N;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= stride) return;
+    float cr = 0.f, cg = 0.f, cb = 0.f;
+    for (long long i = g; i < N; i += stride)
+        finalize_record(i, acc, conic_opacity, dL_dmeans2D, dL_dconic, dL_dopacity, dL_ddepths, cr, cg, cb);
+    if (n_colors > 0) {
+        dL_dcolors[3 * g] = cr;
+        dL_dcolors[3 * g + 1] = cg;
+        dL_dcolors[3 * g + 2] = cb;
     }
-    if (dL_ddepths) dL_ddepths[i] = a2.y;
-}
-
-__global__ void __launch_bounds__(256) k_grad_colors(long long N, long long n_colors, const float4 *__restrict__ acc,
-                                                     float *__restrict__ dL_dcolors) {
-    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_colors) return;
-    float r = 0.f, gg = 0.f, b = 0.f;
-    for (long long i = g; i < N; i += n_colors) {
-        const float4 a1 = acc[3 * i + 1], a2 = acc[3 * i + 2];
-        r += a1.z;
-        gg += a1.w;
-        b += a2.x;
-    }
-    dL_dcolors[3 * g] = r;
-    dL_dcolors[3 * g + 1] = gg;
-    dL_dcolors[3 * g + 2] = b;
 }
 
 cudaError_t launch_grad_finalize(long long N, long long n_colors, const float4 *acc, const float *conic_opacity,
@@ -489,11 +490,10 @@ cudaError_t launch_grad_finalize(long long N, long long n_colors, const float4 *
                                  float *dL_ddepths, const unsigned int *warp_items, int n_warps, DevCtrl *ctrl,
                                  cudaStream_t s) {
     if (N == 0 && n_warps == 0) return cudaSuccess;
-    k_grad_finalize<<<(unsigned)std::max<long long>(1, (N + 255) / 256), 256, 0, s>>>(
+    const long long threads = (n_colors > 0 && n_colors < N) ? n_colors : N;
+    k_grad_finalize<<<(unsigned)std::max<long long>(1, (threads + 255) / 256), 256, 0, s>>>(
         N, n_colors, acc, reinterpret_cast<const float4 *>(conic_opacity), dL_dmeans2D, dL_dconic, dL_dopacity,
         dL_dcolors, dL_ddepths, warp_items, n_warps, ctrl);
-    if (n_colors != N && n_colors > 0)
-        k_grad_colors<<<(unsigned)((n_colors + 255) / 256), 256, 0, s>>>(N, n_colors, acc, dL_dcolors);
     return cudaGetLastError();
 }
 
