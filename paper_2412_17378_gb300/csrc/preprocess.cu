@@ -127,6 +127,9 @@ __device__ __forceinline__ bool project(const CamDev &cam, const float *__restri
 }
 
 // Record i = v * N + g projects Gaussian g into view v (one view for the single-view call).
+// A thread per Gaussian, over the views: the Gaussian's parameters are read from DRAM once
+// (the views' later reads hit L1), and record v N + g of every view is written (coalesced
+// per view).
 __global__ void __launch_bounds__(256) k_preprocess(long long N, const float *__restrict__ means3D,
                                                     const float *__restrict__ log_scales,
                                                     const float *__restrict__ quats,
@@ -134,40 +137,42 @@ __global__ void __launch_bounds__(256) k_preprocess(long long N, const float *__
                                                     float2 *__restrict__ means2D, float4 *__restrict__ conic_opacity,
                                                     float *__restrict__ depths, int *__restrict__ radii,
                                                     uint32_t *__restrict__ tiles_touched) {
-    const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (rec >= N * ct.V) return;
-    const int view = (int)(rec / N);
-    const long long g = rec - (long long)view * N;
-    const CamDev &cam = ct.cam[view];
-    Proj o;
-    const bool ok = project(cam, means3D, log_scales, quats, g, o);
-    float2 m2 = make_float2(0.f, 0.f);
-    float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
-    int radius = 0;
-    uint32_t touched = 0;
-    depths[rec] = o.tz;
-    if (ok) {
-        const float mid = 0.5f * (o.c00 + o.c11);
-        // mid^2 - det = ((A - C) / 2)^2 + B^2, written without cancellation
-        const float hd = 0.5f * (o.c00 - o.c11);
-        const float lam = mid + sqrtf(fmaxf(0.1f, hd * hd + o.c01 * o.c01));
-        const int r = (int)ceilf(3.f * sqrtf(lam));
-        const float idet = 1.f / o.det;
-        const float u = cam.fx * o.tx * o.iz + cam.cx, v = cam.fy * o.ty * o.iz + cam.cy;
-        m2 = make_float2(u, v);
-        co = make_float4(o.c11 * idet, -o.c01 * idet, o.c00 * idet, opacities[g]);
-        int x0, x1, y0, y1;
-        tile_rect(u, v, r, cam.tile_w, cam.tile_h, cam.tiles_x, cam.tiles_y, x0, x1, y0, y1);
-        const long long area = (long long)(x1 - x0) * (long long)(y1 - y0);
-        if (area > 0) {
-            radius = r;
-            touched = (uint32_t)area;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N) return;
+    const float op = opacities[g];
+    for (int view = 0; view < ct.V; ++view) {
+        const long long rec = (long long)view * N + g;
+        const CamDev &cam = ct.cam[view];
+        Proj o;
+        const bool ok = project(cam, means3D, log_scales, quats, g, o);
+        float2 m2 = make_float2(0.f, 0.f);
+        float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
+        int radius = 0;
+        uint32_t touched = 0;
+        depths[rec] = o.tz;
+        if (ok) {
+            const float mid = 0.5f * (o.c00 + o.c11);
+            // mid^2 - det = ((A - C) / 2)^2 + B^2, written without cancellation
+            const float hd = 0.5f * (o.c00 - o.c11);
+            const float lam = mid + sqrtf(fmaxf(0.1f, hd * hd + o.c01 * o.c01));
+            const int r = (int)ceilf(3.f * sqrtf(lam));
+            const float idet = 1.f / o.det;
+            const float u = cam.fx * o.tx * o.iz + cam.cx, v = cam.fy * o.ty * o.iz + cam.cy;
+            m2 = make_float2(u, v);
+            co = make_float4(o.c11 * idet, -o.c01 * idet, o.c00 * idet, op);
+            int x0, x1, y0, y1;
+            tile_rect(u, v, r, cam.tile_w, cam.tile_h, cam.tiles_x, cam.tiles_y, x0, x1, y0, y1);
+            const long long area = (long long)(x1 - x0) * (long long)(y1 - y0);
+            if (area > 0) {
+                radius = r;
+                touched = (uint32_t)area;
+            }
         }
+        means2D[rec] = m2;
+        conic_opacity[rec] = co;
+        radii[rec] = radius;
+        tiles_touched[rec] = touched;
     }
-    means2D[rec] = m2;
-    conic_opacity[rec] = co;
-    radii[rec] = radius;
-    tiles_touched[rec] = touched;
 }
 
 // Projection backward: thread per Gaussian, summing its records over the views.  Records
@@ -309,7 +314,7 @@ cudaError_t launch_preprocess(long long N, int V, const float *means3D, const fl
     for (int v = 0; v < V; ++v) ct.cam[v] = cam_dev(cams[v], tile_w, tile_h);
     if (N == 0) return cudaSuccess;
     const int threads = 256;
-    const long long blocks = (N * V + threads - 1) / threads;
+    const long long blocks = (N + threads - 1) / threads;
     k_preprocess<<<(unsigned)blocks, threads, 0, s>>>(N, means3D, log_scales, quats, opacities, ct,
                                                        reinterpret_cast<float2 *>(means2D),
                                                        reinterpret_cast<float4 *>(conic_opacity), depths, radii,
