@@ -255,9 +255,12 @@ int bgs_render_forward(bgs_plan *plan, int64_t N, const float *means2D, const fl
    dL_dcolors [N,3], dL_ddepths [N] (nullable).  Where o exp(power) > 0.99 the alpha
    clamp is active and the pair passes no gradient to o or to the Gaussian's shape.
    The arrays must hold what the forward read (final_T and n_contrib only describe that
-   blend).  When they are the same arrays (pointers and sizes) as the plan's last forward
-   and that forward queued every tile pixel-wise, the packed records and the work list
-   of that forward are reused instead of being rebuilt. */
+   blend).  When they are the same arrays (pointers and sizes) as the plan's last forward,
+   its packed records are reused instead of being rebuilt; and when that forward split
+   Gaussian-wise lists into segments (same render mode and knobs), the backward walks
+   those tiles segment by segment from the boundary states it left in the plan.  The
+   backward's own work list is ordered heaviest first by each tile's largest n_contrib
+   (built once and reused by later backwards on the same list key). */
 int bgs_render_backward(bgs_plan *plan, int64_t N, const float *means2D, const float *conic_opacity,
                         const float *colors, const float *depths, const uint32_t *point_list,
                         int64_t num_entries, const uint32_t *ranges, int32_t W, int32_t H, int32_t tile_w,

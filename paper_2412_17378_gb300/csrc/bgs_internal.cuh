@@ -379,12 +379,16 @@ cudaError_t launch_pack(long long N, const float *means2D, const float *conic_op
 // that render mode, split into segments get their pixel-wise items once per segment
 // (ctrl->gw_seg, the forward's segment length, is kept).  gw_tile [num_tiles] (nullable):
 // per Gaussian-wise tile of a forward list, (first first-segment item, first later-segment
-// item).
+// item).  cost [num_tiles] (nullable): the per-tile load that orders the list heaviest first
+// (default: the list length).
 cudaError_t launch_worklist_buckets(const uint2 *ranges, int num_tiles, const ViewTable &vt, int tile_w, int tile_h,
                                     int mode, int heavy_threshold, int lpt, int gw_pixels, int pixel_rows,
                                     int gw_segment, long long extra_cap, uint32_t *slot, uint32_t *exoff,
-                                    uint2 *items, long long capacity, int bseg_mode, uint2 *gw_tile, DevCtrl *ctrl,
-                                    cudaStream_t s);
+                                    uint2 *items, long long capacity, int bseg_mode, uint2 *gw_tile,
+                                    const uint32_t *cost, DevCtrl *ctrl, cudaStream_t s);
+// per tile of the views: the largest n_contrib of its pixels (the backward's cost)
+cudaError_t launch_tile_cost(const ViewTable &vt, int tile_w, int tile_h, const ViewGradIn &gi, uint32_t *cost,
+                             cudaStream_t s);
 // queue of the current list: rewind for another pass / mark exhausted (fault injection)
 cudaError_t launch_rewind_queue(DevCtrl *ctrl, cudaStream_t s);
 cudaError_t launch_exhaust_queue(DevCtrl *ctrl, cudaStream_t s);

@@ -95,6 +95,7 @@ struct bgs_plan {
     Buf recs, tile_idx, items, grad_acc, warp_items;  // tile_idx: each tile's slot in its work-list bucket
     Buf gw_exoff, gw_sum, gw_tile;  // Gaussian-wise segments: per-tile later-segment offsets, per-item
                                     // summaries, per-tile segment item positions
+    Buf tile_cost;                  // backward: per-tile largest n_contrib (its list's order)
     // batched binning: depth keys of every view
     Buf vkey, vkey_sorted;
     // the views' depth sorts run concurrently on kSortStreams streams forked from the caller's
@@ -113,7 +114,7 @@ struct bgs_plan {
     struct WlKey {
         const void *ranges;
         bgs::ViewTable vt;
-        int tw, th, mode, heavy_threshold, gw_pixels, pixel_rows, lpt_order, gw_segment, bseg_mode;
+        int tw, th, mode, heavy_threshold, gw_pixels, pixel_rows, lpt_order, gw_segment, bseg_mode, costed;
     } wl_key;
     // the last forward split Gaussian-wise lists into segments on the list of this key: a
     // backward on the same arrays walks those tiles segment by segment from the boundary
@@ -232,7 +233,7 @@ int grid_for(const bgs_plan *p, const void *kernel, int threads) {
 
 // Builds the work list of the persistent kernels over the global tile space of the views (a3).
 bgs_plan::WlKey worklist_key(const bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt, int tw, int th,
-                             int mode, int bseg_mode = -1) {
+                             int mode, int bseg_mode = -1, int costed = 0) {
     bgs_plan::WlKey k;
     memset(&k, 0, sizeof k);  // padding included: keys are compared with memcmp
     k.ranges = ranges;
@@ -246,6 +247,7 @@ bgs_plan::WlKey worklist_key(const bgs_plan *p, const uint32_t *ranges, const bg
     k.lpt_order = p->desc.lpt_order;
     k.gw_segment = p->desc.gw_segment;
     k.bseg_mode = bseg_mode;
+    k.costed = costed;
     return k;
 }
 
@@ -286,7 +288,7 @@ long long gw_extra_cap(const bgs_plan *p, int tw, int th, int64_t num_entries) {
 // (with mode PIXEL, for a backward): the render mode of the last forward on these arrays,
 // whose split Gaussian-wise tiles get their pixel-wise items once per segment.
 int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt, int tw, int th, int mode,
-                   int64_t num_entries, cudaStream_t s, int bseg_mode = -1) {
+                   int64_t num_entries, cudaStream_t s, int bseg_mode = -1, const uint32_t *cost = nullptr) {
     if (mode == BGS_MODE_AUTO && (p->desc.heavy_threshold == INT32_MAX ||
                                   (int64_t)p->desc.heavy_threshold >= num_entries))
         mode = BGS_MODE_PIXEL;
@@ -319,10 +321,10 @@ int build_worklist(bgs_plan *p, const uint32_t *ranges, const bgs::ViewTable &vt
                                           p->desc.pixel_rows, gauss ? p->desc.gw_segment : 0, extra_cap,
                                           (uint32_t *)p->tile_idx.p, gauss ? (uint32_t *)p->gw_exoff.p : nullptr,
                                           (uint2 *)p->items.p, (long long)(p->items.bytes / sizeof(uint2)), bseg_mode,
-                                          gauss ? (uint2 *)p->gw_tile.p : nullptr, p->ctrl, s),
+                                          gauss ? (uint2 *)p->gw_tile.p : nullptr, cost, p->ctrl, s),
              "build_worklist");
     p->host_launches += T > 0 ? 2 : 1;
-    p->wl_key = worklist_key(p, ranges, vt, tw, th, mode, bseg_mode);
+    p->wl_key = worklist_key(p, ranges, vt, tw, th, mode, bseg_mode, cost ? 1 : 0);
     p->wl_valid = true;
     return BGS_OK;
 }
@@ -411,7 +413,7 @@ int bgs_plan_destroy(bgs_plan *p) {
         for (Buf *b : sb)
             if (b->p) cudaFree(b->p);
     }
-    Buf *bufs[] = {&p->gw_exoff, &p->gw_sum, &p->gw_tile, &p->vkey, &p->vkey_sorted, &p->touched, &p->touched_sorted, &p->dkey,
+    Buf *bufs[] = {&p->gw_exoff, &p->gw_sum, &p->gw_tile, &p->tile_cost, &p->vkey, &p->vkey_sorted, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_idx, &p->items, &p->warp_items,
@@ -1052,13 +1054,20 @@ int render_backward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewG
         a.gw_pixels = p->desc.gw_pixels;
         a.gw_tile = bseg >= 0 ? (const uint2 *)p->gw_tile.p : nullptr;
         a.gw_sum = bseg >= 0 ? (const bgs::GwSum *)p->gw_sum.p : nullptr;
-        const bgs_plan::WlKey wk = worklist_key(p, ranges, vt, tw, th, BGS_MODE_PIXEL, bseg);
+        // heaviest first by what the backward walks: each tile's largest n_contrib (its list
+        // length overstates the walk where pixels stop early); the order changes no result
+        const bgs_plan::WlKey wk = worklist_key(p, ranges, vt, tw, th, BGS_MODE_PIXEL, bseg, 1);
         if (p->wl_valid && memcmp(&wk, &p->wl_key, sizeof wk) == 0) {
-            // same list (no Gaussian-wise items): rewind its queue
+            // same list: rewind its queue
             BGS_CUDA(bgs::launch_rewind_queue(p->ctrl, s), "rewind queue");
             p->host_launches += 1;
         } else {
-            BGS_TRY(build_worklist(p, ranges, vt, tw, th, BGS_MODE_PIXEL, num_entries, s, bseg));
+            const int T = vt.tile_base[vt.V];
+            BGS_TRY(ensure(p, p->tile_cost, sizeof(uint32_t) * std::max(T, 1), s, "tile_cost"));
+            BGS_CUDA(bgs::launch_tile_cost(vt, tw, th, gi, (uint32_t *)p->tile_cost.p, s), "tile_cost");
+            p->host_launches += 1;
+            BGS_TRY(build_worklist(p, ranges, vt, tw, th, BGS_MODE_PIXEL, num_entries, s, bseg,
+                                   (const uint32_t *)p->tile_cost.p));
         }
         a.items = (const uint2 *)p->items.p;
         const int grid = grid_for(p, bgs::backward_balanced_kernel(a), bgs::backward_balanced_block_threads());

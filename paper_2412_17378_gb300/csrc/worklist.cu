@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(kWlcThreads) k_wl_count(const uint2 *__restric
                                                            int tile_w, int tile_h, int mode, int heavy_threshold,
                                                            int lpt, int gw_pixels, int pixel_rows, int gw_segment,
                                                            long long extra_cap, uint32_t *__restrict__ slot,
-                                                           uint32_t *__restrict__ exoff, int bseg_mode, DevCtrl *ctrl) {
+                                                           uint32_t *__restrict__ exoff, int bseg_mode,
+                                                           const uint32_t *__restrict__ cost, DevCtrl *ctrl) {
     using Scan = cub::BlockScan<uint32_t, kWlcThreads>;
     using Scan64 = cub::BlockScan<unsigned long long, kWlcThreads>;
     __shared__ union {
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kWlcThreads) k_wl_count(const uint2 *__restric
         const uint2 rg = ranges[t];
         const uint32_t n = rg.y >= rg.x ? rg.y - rg.x : 0u;
         const bool gauss = tile_is_gauss(mode, heavy_threshold, n);
-        key = wl_sort_key(n, gauss, lpt);
+        key = wl_sort_key(cost ? cost[t] : n, gauss, lpt);
         const uint32_t c = tile_items(t, gauss, vt, tile_w, tile_h, gw_pixels, pixel_rows) *
                            (gauss ? 1u : bwd_segments(bseg_mode, heavy_threshold, Lb, n));
         local = atomicAdd(&s_cnt[key], c);
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(256) k_wl_emit(const uint2 *__restrict__ range
                                                  int gw_pixels, int pixel_rows, const uint32_t *__restrict__ slot,
                                                  const uint32_t *__restrict__ exoff, uint2 *__restrict__ items,
                                                  long long capacity, int bseg_mode, uint2 *__restrict__ gw_tile,
-                                                 DevCtrl *ctrl) {
+                                                 const uint32_t *__restrict__ cost, DevCtrl *ctrl) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     const uint2 rg = ranges[t];
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(256) k_wl_emit(const uint2 *__restrict__ range
     const unsigned Lb = bseg_mode >= 0 ? ctrl->gw_seg : 0u;
     const uint32_t c = tile_items(t, gauss, vt, tile_w, tile_h, gw_pixels, pixel_rows) *
                        (gauss ? 1u : bwd_segments(bseg_mode, heavy_threshold, Lb, n));
-    const long long pos = (long long)ctrl->wl_off[wl_sort_key(n, gauss, lpt)] + slot[t];
+    const long long pos = (long long)ctrl->wl_off[wl_sort_key(cost ? cost[t] : n, gauss, lpt)] + slot[t];
     if (pos + (long long)c > capacity) {
         raise_check(ctrl, BGS_CHECK_OVERFLOW);
         return;
@@ -204,18 +205,51 @@ __global__ void __launch_bounds__(256) k_wl_emit(const uint2 *__restrict__ range
 cudaError_t launch_worklist_buckets(const uint2 *ranges, int num_tiles, const ViewTable &vt, int tile_w, int tile_h,
                                     int mode, int heavy_threshold, int lpt, int gw_pixels, int pixel_rows,
                                     int gw_segment, long long extra_cap, uint32_t *slot, uint32_t *exoff,
-                                    uint2 *items, long long capacity, int bseg_mode, uint2 *gw_tile, DevCtrl *ctrl,
-                                    cudaStream_t s) {
+                                    uint2 *items, long long capacity, int bseg_mode, uint2 *gw_tile,
+                                    const uint32_t *cost, DevCtrl *ctrl, cudaStream_t s) {
     if (num_tiles < 0 || (gw_segment > 0 && !exoff)) return cudaErrorInvalidValue;
     const int blocks = num_tiles > 0 ? (num_tiles + kWlcThreads - 1) / kWlcThreads : 1;
     k_wl_count<<<blocks, kWlcThreads, 0, s>>>(ranges, num_tiles, vt, tile_w, tile_h, mode, heavy_threshold, lpt,
                                               gw_pixels, pixel_rows, gw_segment, extra_cap, slot, exoff, bseg_mode,
-                                              ctrl);
+                                              cost, ctrl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || num_tiles == 0) return e;
     k_wl_emit<<<(num_tiles + 255) / 256, 256, 0, s>>>(ranges, num_tiles, vt, tile_w, tile_h, mode, heavy_threshold,
                                                       lpt, gw_pixels, pixel_rows, slot, exoff, items, capacity,
-                                                      bseg_mode, gw_tile, ctrl);
+                                                      bseg_mode, gw_tile, cost, ctrl);
+    return cudaGetLastError();
+}
+
+// Per tile of the views: the most entries any of its pixels walks back through in the
+// backward (its largest n_contrib), the backward's per-tile cost for its work list's
+// heaviest-first order (a tile's list length overstates it where pixels stop early).
+__global__ void __launch_bounds__(256) k_tile_cost(const ViewTable vt, int tile_w, int tile_h, const ViewGradIn gi,
+                                                   uint32_t *__restrict__ cost) {
+    const int t = blockIdx.x;
+    const int v = view_of(vt, t);
+    const int lt = t - vt.tile_base[v];
+    const int tx = lt % vt.tiles_x[v], ty = lt / vt.tiles_x[v];
+    const int x0 = tx * tile_w, y0 = ty * tile_h;
+    const int vw = min(tile_w, vt.W[v] - x0), vh = min(tile_h, vt.H[v] - y0);
+    const int *nc = gi.n_contrib[v];
+    int m = 0;
+    for (int q = threadIdx.x; q < vw * vh; q += blockDim.x)
+        m = max(m, nc[(long long)(y0 + q / vw) * vt.W[v] + x0 + q % vw]);
+    m = __reduce_max_sync(0xffffffffu, m);
+    __shared__ int s_m[8];
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_m[w]);
+        cost[t] = (uint32_t)max(m, 0);
+    }
+}
+
+cudaError_t launch_tile_cost(const ViewTable &vt, int tile_w, int tile_h, const ViewGradIn &gi, uint32_t *cost,
+                             cudaStream_t s) {
+    const int T = vt.tile_base[vt.V];
+    if (T == 0) return cudaSuccess;
+    k_tile_cost<<<T, 256, 0, s>>>(vt, tile_w, tile_h, gi, cost);
     return cudaGetLastError();
 }
 

@@ -258,9 +258,9 @@ def test_backward_fd_crop(R, plan, mode):
 
 @pytest.mark.parametrize("mode,threshold", [("pixel", 64), ("auto", 1 << 30), ("auto", 64)])
 def test_backward_reuses_or_rebuilds_forward_state(R, cfg1, mode, threshold):
-    """A backward on the arrays of the plan's last forward reuses its packed records and
-    (when every tile was queued pixel-wise) its work list; after a forward on other arrays
-    it rebuilds them; a plan that ran no forward builds them.  All three give the same
+    """A backward on the arrays of the plan's last forward reuses its packed records (and
+    builds its own, cost-ordered work list); after a forward on other arrays it rebuilds
+    the records; a plan that ran no forward builds them.  All three give the same
     gradients."""
     W, H, tile = cfg1["W"], cfg1["H"], cfg1["tile"]
     rng = np.random.default_rng(4)
