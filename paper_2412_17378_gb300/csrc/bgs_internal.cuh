@@ -242,6 +242,7 @@ struct FwdArgs {
     int gw_pixels;
     const uint32_t *gw_exoff;    // per tile: its later-segment items' offset from num_gauss0
     float4 *gw_sum;              // per Gaussian-wise item, per pixel: the segment summary
+    unsigned int *tile_cost;     // per tile (nullable, zeroed): the largest n_contrib of its pixels
     int pixel_rows;              // Q of the pixel-wise items
     int chunk;
 };
@@ -386,9 +387,7 @@ cudaError_t launch_worklist_buckets(const uint2 *ranges, int num_tiles, const Vi
                                     int gw_segment, long long extra_cap, uint32_t *slot, uint32_t *exoff,
                                     uint2 *items, long long capacity, int bseg_mode, uint2 *gw_tile,
                                     const uint32_t *cost, DevCtrl *ctrl, cudaStream_t s);
-// per tile of the views: the largest n_contrib of its pixels (the backward's cost)
-cudaError_t launch_tile_cost(const ViewTable &vt, int tile_w, int tile_h, const ViewGradIn &gi, uint32_t *cost,
-                             cudaStream_t s);
+
 // queue of the current list: rewind for another pass / mark exhausted (fault injection)
 cudaError_t launch_rewind_queue(DevCtrl *ctrl, cudaStream_t s);
 cudaError_t launch_exhaust_queue(DevCtrl *ctrl, cudaStream_t s);

@@ -95,7 +95,8 @@ struct bgs_plan {
     Buf recs, tile_idx, items, grad_acc, warp_items;  // tile_idx: each tile's slot in its work-list bucket
     Buf gw_exoff, gw_sum, gw_tile;  // Gaussian-wise segments: per-tile later-segment offsets, per-item
                                     // summaries, per-tile segment item positions
-    Buf tile_cost;                  // backward: per-tile largest n_contrib (its list's order)
+    Buf tile_cost;                  // per-tile largest n_contrib, from the last forward (the
+                                    // backward's work-list order); valid for cost_key's tiles
     // batched binning: depth keys of every view
     Buf vkey, vkey_sorted;
     // the views' depth sorts run concurrently on kSortStreams streams forked from the caller's
@@ -121,6 +122,8 @@ struct bgs_plan {
     // states the forward left in gw_sum (per tile: gw_tile)
     WlKey gw_fwd_key;
     bool gw_fwd_valid = false;
+    WlKey cost_key;  // the tiles tile_cost describes
+    bool cost_valid = false;
     bool rec_valid = false, wl_valid = false;
     unsigned int inject = 0;  // BGS_CHECK_* fault to inject into the next persistent pass
     // BGS_MODE_SELECT (Sec. 4.4)
@@ -962,6 +965,7 @@ int render_forward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewOu
         BGS_CUDA(bgs::launch_forward_static(a, s), "forward_static");
         kt.stop();
         p->host_launches += 1;
+        p->cost_valid = false;  // no per-tile cost gathered
         return BGS_OK;
     }
     BGS_TRY(ensure(p, p->recs, sizeof(bgs::Rec) * std::max<int64_t>(n_records, 1), s, "recs"));
@@ -980,6 +984,14 @@ int render_forward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewOu
     const bool gauss = gauss_possible(p, mode, num_entries);
     a.gw_exoff = gauss ? (const uint32_t *)p->gw_exoff.p : nullptr;
     a.gw_sum = gauss ? (float4 *)p->gw_sum.p : nullptr;
+    {  // the backward's per-tile cost, gathered by the forward kernels
+        const int T = vt.tile_base[vt.V];
+        BGS_TRY(ensure(p, p->tile_cost, sizeof(uint32_t) * std::max(T, 1), s, "tile_cost"));
+        BGS_CUDA(cudaMemsetAsync(p->tile_cost.p, 0, sizeof(uint32_t) * std::max(T, 1), s), "clear tile_cost");
+        a.tile_cost = (unsigned int *)p->tile_cost.p;
+        p->cost_key = worklist_key(p, ranges, vt, tw, th, BGS_MODE_PIXEL);
+        p->cost_valid = true;
+    }
     a.pass_blocks = (gauss ? grid_g : 0) + (mode != BGS_MODE_GAUSSIAN ? grid_p : 0);
     BGS_TRY(inject_pending_fault(p, s));
     KernelTimer kt(p, s, &p->ev_fwd);
@@ -1054,20 +1066,19 @@ int render_backward_impl(bgs_plan *p, const bgs::ViewTable &vt, const bgs::ViewG
         a.gw_pixels = p->desc.gw_pixels;
         a.gw_tile = bseg >= 0 ? (const uint2 *)p->gw_tile.p : nullptr;
         a.gw_sum = bseg >= 0 ? (const bgs::GwSum *)p->gw_sum.p : nullptr;
-        // heaviest first by what the backward walks: each tile's largest n_contrib (its list
-        // length overstates the walk where pixels stop early); the order changes no result
-        const bgs_plan::WlKey wk = worklist_key(p, ranges, vt, tw, th, BGS_MODE_PIXEL, bseg, 1);
+        // heaviest first by what the backward walks: each tile's largest n_contrib, which the
+        // last forward on these tiles gathered (its list length overstates the walk where
+        // pixels stop early); the order changes no result
+        const bgs_plan::WlKey ck = worklist_key(p, ranges, vt, tw, th, BGS_MODE_PIXEL);
+        const bool costed = p->cost_valid && memcmp(&ck, &p->cost_key, sizeof ck) == 0;
+        const bgs_plan::WlKey wk = worklist_key(p, ranges, vt, tw, th, BGS_MODE_PIXEL, bseg, costed ? 1 : 0);
         if (p->wl_valid && memcmp(&wk, &p->wl_key, sizeof wk) == 0) {
             // same list: rewind its queue
             BGS_CUDA(bgs::launch_rewind_queue(p->ctrl, s), "rewind queue");
             p->host_launches += 1;
         } else {
-            const int T = vt.tile_base[vt.V];
-            BGS_TRY(ensure(p, p->tile_cost, sizeof(uint32_t) * std::max(T, 1), s, "tile_cost"));
-            BGS_CUDA(bgs::launch_tile_cost(vt, tw, th, gi, (uint32_t *)p->tile_cost.p, s), "tile_cost");
-            p->host_launches += 1;
             BGS_TRY(build_worklist(p, ranges, vt, tw, th, BGS_MODE_PIXEL, num_entries, s, bseg,
-                                   (const uint32_t *)p->tile_cost.p));
+                                   costed ? (const uint32_t *)p->tile_cost.p : nullptr));
         }
         a.items = (const uint2 *)p->items.p;
         const int grid = grid_for(p, bgs::backward_balanced_kernel(a), bgs::backward_balanced_block_threads());

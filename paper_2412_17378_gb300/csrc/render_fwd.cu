@@ -257,13 +257,20 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
             }
         }
     }
+    int mlast = 0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (inside[q]) {
             write_pixel(a, tg.v, px, py0 + kRowStep * q, T[q], c0[q], c1[q], c2[q], D[q], last[q], neval[q]);
             st_eval += (unsigned long long)neval[q];
             st_acc += (unsigned long long)nacc[q];
+            mlast = max(mlast, last[q]);
         }
+    }
+    // the tile's largest n_contrib: the backward's per-tile cost (its work list's order)
+    if (a.tile_cost) {
+        mlast = __reduce_max_sync(kFull, mlast);
+        if (lane == 0 && mlast > 0) atomicMax(a.tile_cost + tile, (unsigned int)mlast);
     }
 }
 
@@ -676,6 +683,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_gw_merge(FwdArg
             const int neval = stop ? stop : (int)n;
             if (lane == 0) {
                 write_pixel(a, tg.v, (int)pxf, (int)pyf, T, c0, c1, c2, D, last + 1, neval);
+                if (a.tile_cost && last >= 0) atomicMax(a.tile_cost + tile, (unsigned int)(last + 1));
                 st_eval += (unsigned long long)neval;
                 st_acc += (unsigned long long)nacc;
             }

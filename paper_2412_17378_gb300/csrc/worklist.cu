@@ -220,39 +220,6 @@ cudaError_t launch_worklist_buckets(const uint2 *ranges, int num_tiles, const Vi
     return cudaGetLastError();
 }
 
-// Per tile of the views: the most entries any of its pixels walks back through in the
-// backward (its largest n_contrib), the backward's per-tile cost for its work list's
-// heaviest-first order (a tile's list length overstates it where pixels stop early).
-__global__ void __launch_bounds__(256) k_tile_cost(const ViewTable vt, int tile_w, int tile_h, const ViewGradIn gi,
-                                                   uint32_t *__restrict__ cost) {
-    const int t = blockIdx.x;
-    const int v = view_of(vt, t);
-    const int lt = t - vt.tile_base[v];
-    const int tx = lt % vt.tiles_x[v], ty = lt / vt.tiles_x[v];
-    const int x0 = tx * tile_w, y0 = ty * tile_h;
-    const int vw = min(tile_w, vt.W[v] - x0), vh = min(tile_h, vt.H[v] - y0);
-    const int *nc = gi.n_contrib[v];
-    int m = 0;
-    for (int q = threadIdx.x; q < vw * vh; q += blockDim.x)
-        m = max(m, nc[(long long)(y0 + q / vw) * vt.W[v] + x0 + q % vw]);
-    m = __reduce_max_sync(0xffffffffu, m);
-    __shared__ int s_m[8];
-    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_m[w]);
-        cost[t] = (uint32_t)max(m, 0);
-    }
-}
-
-cudaError_t launch_tile_cost(const ViewTable &vt, int tile_w, int tile_h, const ViewGradIn &gi, uint32_t *cost,
-                             cudaStream_t s) {
-    const int T = vt.tile_base[vt.V];
-    if (T == 0) return cudaSuccess;
-    k_tile_cost<<<T, 256, 0, s>>>(vt, tile_w, tile_h, gi, cost);
-    return cudaGetLastError();
-}
-
 // Rewinds the queue of the current (pixel-wise) list for another persistent pass.
 __global__ void k_rewind_queue(DevCtrl *ctrl) {
     ctrl->queue_head = ctrl->num_gauss;
