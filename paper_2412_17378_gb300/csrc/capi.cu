@@ -1610,15 +1610,19 @@ int bgs_autotune_render(bgs_plan *p, int32_t V, const bgs_view *views, int64_t N
         if ((rc = run(d, t)) != BGS_OK) break;
         if (t < best_t) best_t = t, best = d;
     }
-    // stage 2: heavy-tile threshold and pixels per Gaussian-wise item
+    // stage 2: heavy-tile threshold and pixels per Gaussian-wise item; Gaussian-wise items are
+    // kept only when they gain more than 1 % over the best without them (a threshold above
+    // every list queues none and would win or lose on timing noise alone)
+    const bgs_plan_desc no_gw = best;
+    const double no_gw_t = best_t;
     for (int thr : {256, 1024, 4096, 16384}) {
         if (rc != BGS_OK) break;
         for (int P : {4, 8, 16}) {
-            d = best;
+            d = no_gw;
             d.heavy_threshold = thr;
             d.gw_pixels = P;
             if ((rc = run(d, t)) != BGS_OK) break;
-            if (t < best_t) best_t = t, best = d;
+            if (t < best_t && t < 0.99 * no_gw_t) best_t = t, best = d;
         }
     }
     // stage 2b: segment length of the Gaussian-wise items, when the best uses them
