@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -68,7 +69,9 @@ FP32_LANES_PER_SM_CLK = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: enough graph replays for about 1 s, at least 10; 10 for the "
+                         "reference arm and --quick)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default=DEFAULT_CONFIG)
@@ -415,6 +418,8 @@ def reference_arm(args):
     rank, world, _ = dist_init(args)
     if rank != 0:
         return
+    if args.steps is None:
+        args.steps = 10
     from paper_2412_17378_gb300 import scenes
     scene = scenes.scene_config(args.config, args.scale)
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
@@ -613,7 +618,7 @@ def main_views(args, scene, rank, world, local):
             step()
         side.synchronize()
         plan.kernel_ms()
-        for _ in range(max(3, args.steps // 2)):
+        for _ in range(max(3, (args.steps or 10) // 2)):
             step()
         f_ms, nf, b_ms, nb = plan.kernel_ms()
         plan.timing(False)
@@ -633,12 +638,19 @@ def main_views(args, scene, rank, world, local):
         # timed region, whose host-side window selects the samples that are reported
         clocks = ClockSampler(local)
         clocks.start()
+        n_load, t_load = 0, time.perf_counter()
         if not args.quick:
-            t_load = time.perf_counter()
             while time.perf_counter() - t_load < 1.0:
                 for _ in range(4):
                     raster.graph_launch(plan)
                 side.synchronize()
+                n_load += 4
+        if args.steps is None:
+            # about 1 s of timed replays (the clock samples fall inside), at least 10; the same
+            # count on every rank
+            step_s = (time.perf_counter() - t_load) / n_load if n_load else 0.0
+            k = max(10, int(math.ceil(1.0 / step_s))) if step_s > 0 else 10
+            args.steps = int(max_over_ranks(float(k), world, dev))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         side.synchronize()
         if world > 1:
