@@ -45,3 +45,21 @@ def test_bench_json_line_contract():
     clk = L["clocks"]
     assert clk["sm_mhz"] > 0 and clk["sm_max_mhz"] > 0 and isinstance(clk["reasons"], list)
     assert clk["samples"] >= clk["samples_in_timed_region"] >= 0
+
+
+def test_bench_default_steps_cover_clock_samples():
+    """Without --steps the timed region is sized to about a second of replays (at least 10
+    steps), so the clock sampler records samples inside it."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    r = subprocess.run([sys.executable, "bench.py", "--config", "cfg1", "--warmup", "3", "--cpu-seconds", "1"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    L = json.loads(lines[0])
+    assert L["steps"] >= 10
+    assert L["steps"] * L["ms_per_step"] >= 250.0  # about a second of replays, host waits included in the sizing
+    clk = L["clocks"]
+    if clk["samples"] > 0:
+        assert clk["samples_in_timed_region"] >= 1
