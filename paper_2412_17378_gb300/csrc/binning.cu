@@ -38,14 +38,13 @@ namespace bgs {
 
 constexpr int kCbW = 8, kCbH = 4;  // tile group of one scatter warp (a tile per lane)
 
-__device__ __forceinline__ void rect_of(const float2 *__restrict__ means2D, const int *__restrict__ radii, uint32_t g,
-                                        int tw, int th, int tx, int ty, int &x0, int &y0, int &w, int &cnt) {
+// The tile rectangle of a record with mean m and radius r (r <= 0: empty).
+__device__ __forceinline__ void rect_of(float2 m, int r, int tw, int th, int tx, int ty, int &x0, int &y0, int &w,
+                                        int &cnt) {
     x0 = y0 = 0;
     w = 1;
     cnt = 0;
-    const int r = radii[g];
     if (r <= 0) return;
-    const float2 m = means2D[g];
     // same float32 operations as the preprocess and oracle rectangles: a quotient rounded once
     // (for a power-of-two tile side, the product by its exact reciprocal is that quotient)
     int x1, y1;
@@ -68,6 +67,7 @@ __device__ __forceinline__ void rect_of(const float2 *__restrict__ means2D, cons
 }
 
 constexpr int kCountThreads = 512;  // one thread per Gaussian of a 512-Gaussian sub-block
+constexpr int kLaneGroups = 8;      // tile groups a lane flags by itself (more: the whole warp)
 
 __global__ void __launch_bounds__(kCountThreads) k_bin_count(long long N, int G, const uint32_t *__restrict__ order,
                                                    const float2 *__restrict__ means2D, const int *__restrict__ radii,
@@ -102,13 +102,39 @@ __global__ void __launch_bounds__(kCountThreads) k_bin_count(long long N, int G,
     }
     __syncthreads();
     const long long s0 = (long long)b * G, s1 = min(N, s0 + G);
-    // 512 Gaussians (16 mask words per C) at a time
-    for (int sub = 0; sub < W32 / 16; ++sub) {
-        const long long c0 = s0 + 512ll * sub, c1 = min(s1, c0 + 512);
-        for (long long s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
+    // 512 Gaussians (16 mask words per C) at a time, a thread per Gaussian.  The loads are
+    // pipelined across the sub-blocks: a thread holds the depth order two sub-blocks ahead
+    // and the mean and radius one ahead, so the two dependent gathers of a sub-block overlap
+    // the atomics, barriers and mask stores of the one before it.
+    const int nb = (int)(s1 - s0);  // Gaussians of this block (<= G)
+    const uint32_t *ord = order + s0;
+    uint4 *rec = rect + s0;
+    int i = threadIdx.x;  // position in the block
+    uint32_t g = 0u, g_next = 0u;
+    float2 m = make_float2(0.f, 0.f);
+    int r = 0;
+    if (i < nb) g = ord[i];
+    if (i + kCountThreads < nb) g_next = ord[i + kCountThreads];
+    if (i < nb) {
+        r = radii[g];
+        m = means2D[g];
+    }
+    for (int sub = 0; sub < W32 / 16; ++sub, i += kCountThreads) {
+        float2 m_next = make_float2(0.f, 0.f);
+        int r_next = 0;
+        uint32_t g_after = 0u;
+        if (i + kCountThreads < nb) {
+            r_next = radii[g_next];
+            m_next = means2D[g_next];
+        }
+        if (i + 2 * kCountThreads < nb) g_after = ord[i + 2 * kCountThreads];
+        // a rectangle meeting more than kLaneGroups tile groups is flagged by the whole warp
+        // below (one group per lane), not by its own lane's loop: the warp would otherwise
+        // wait on its largest Gaussian's loop with one lane active
+        int gx0 = 0, gy0 = 0, ngx = 1, ng = 0;
+        if (i < nb) {
             int x0, y0, w, c;
-            const uint32_t g = order[s];
-            rect_of(means2D, radii, g, tw, th, tx, ty, x0, y0, w, c);
+            rect_of(m, r, tw, th, tx, ty, x0, y0, w, c);
             if (c > 0 && skipP) {
                 // every tile the rectangle covers stopped in the blocks before this pass: the
                 // Gaussian is past the end of all its lists (treated as covering nothing)
@@ -128,14 +154,32 @@ __global__ void __launch_bounds__(kCountThreads) k_bin_count(long long N, int G,
                     atomicAdd(&d_s[y1 * tx + x0], 0xffffffffu);
                     if (x1 < tx) atomicAdd(&d_s[y1 * tx + x1], 1u);
                 }
-                const int li = (int)(s - c0);
-                const uint32_t bit = 1u << (li & 31);
-                for (int cy = y0 / kCbH; cy <= (y1 - 1) / kCbH; ++cy)
-                    for (int cx = x0 / kCbW; cx <= (x1 - 1) / kCbW; ++cx)
-                        atomicOr(&m_s[(cy * ncx + cx) * 16 + (li >> 5)], bit);
+                // the Gaussian's bit (lane) in word `warp` of every group its rectangle meets
+                gx0 = x0 / kCbW;
+                gy0 = y0 / kCbH;
+                ngx = (x1 - 1) / kCbW - gx0 + 1;
+                ng = ngx * ((y1 - 1) / kCbH - gy0 + 1);
+                if (ng <= kLaneGroups) {
+                    for (int cy = gy0; cy <= (y1 - 1) / kCbH; ++cy)
+                        for (int cx = gx0; cx < gx0 + ngx; ++cx)
+                            atomicOr(&m_s[(cy * ncx + cx) * 16 + warp], 1u << lane);
+                }
             }
-            rect[s] = make_uint4(px, py, g, 0u);
+            rec[i] = make_uint4(px, py, g, 0u);
         }
+        for (unsigned big = __ballot_sync(0xffffffffu, ng > kLaneGroups); big; big &= big - 1u) {
+            const int src = __ffs(big) - 1;
+            const int bgx0 = __shfl_sync(0xffffffffu, gx0, src), bgy0 = __shfl_sync(0xffffffffu, gy0, src);
+            const int bngx = __shfl_sync(0xffffffffu, ngx, src), bng = __shfl_sync(0xffffffffu, ng, src);
+            for (int k = lane; k < bng; k += 32) {
+                const int cy = bgy0 + k / bngx, cx = bgx0 + k % bngx;
+                atomicOr(&m_s[(cy * ncx + cx) * 16 + warp], 1u << src);
+            }
+        }
+        g = g_next;
+        m = m_next;
+        r = r_next;
+        g_next = g_after;
         __syncthreads();
         // the sub-block's mask words: (b, C) words [16 sub, 16 sub + 16), 16 bytes a store (the
         // word arrays are 16-word aligned: W32 is a multiple of 16)
@@ -229,12 +273,16 @@ __global__ void __launch_bounds__(kCrWarps * 32) k_bin_credit(long long N, int G
     // 1.01 / 255 computes its logarithm.  ln(1 / (f (1 + 2^-9))) for f = 0.15, 0.45, 0.8,
     // rounded down:
     const float r2c[3] = {2.f * 1.8951687f * 0.999f, 2.f * 0.7965564f * 0.999f, 2.f * 0.2211923f * 0.999f};
+    // the next round's rectangle is loaded a round ahead (the conic gather behind it then
+    // waits for one memory round trip, not two)
+    uint4 rc_next = s0 + 32ll * warp + lane < s1 ? rect[s0 + 32ll * warp + lane] : make_uint4(0u, 0u, 0u, 0u);
     for (long long c0 = s0 + 32ll * warp; c0 < s1; c0 += 32ll * kCrWarps) {
         // (1) per Gaussian: its levels, their credits and the rows their level sets span
         const long long s = c0 + lane;
+        const uint4 rc = rc_next;
+        if (s + 32ll * kCrWarps < s1) rc_next = rect[s + 32ll * kCrWarps];
         int units = 0;
         if (s < s1) {
-            const uint4 rc = rect[s];
             const int rw = (int)(rc.x >> 16), rh = (int)(rc.y >> 16);
             if (rw > 0 && rh > 0) {
                 const int rx0 = (int)(rc.x & 0xffffu), ry0 = (int)(rc.y & 0xffffu);
