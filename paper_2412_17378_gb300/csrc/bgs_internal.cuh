@@ -186,10 +186,9 @@ __device__ __forceinline__ float pair_power2(float4 a, float qc, float px, float
 // flag window at the list lengths of the tests.
 __device__ __forceinline__ float next_T(float T, float al) { return __fmaf_rn(-T, al, T); }
 
-__device__ __forceinline__ float pair_alpha(float power2, float o, float &G) {
-    G = ex2_approx(power2);
-    return fminf(kAlphaMax, __fmul_rn(o, G));
-}
+// o G of a pair.  A pair is accumulated when power2 <= 0 and o G >= 1/255 (the same as
+// alpha = min(0.99, o G) >= 1/255, since 1/255 < 0.99); alpha is formed only for those.
+__device__ __forceinline__ float pair_oG(float power2, float o) { return __fmul_rn(o, ex2_approx(power2)); }
 
 // ---- views ---------------------------------------------------------------------------
 // A render call covers V views (1 for the single-view entry points).  Their tiles form

@@ -132,10 +132,11 @@ __global__ void __launch_bounds__(kNaWarps * 32) k_na_forward(NaArgs a, NaScratc
             for (int k = 0; k < cnt; ++k) {
                 const float4 ra = buf[k].a;
                 const float4 rb = buf[k].b;
-                float dx, dy, G;
+                float dx, dy;
                 const float p2 = pair_power2(ra, rb.x, pxf, pyf, dx, dy);
-                const float al = pair_alpha(p2, rb.y, G);
-                if (!done && p2 <= 0.f && al >= kAlphaMin) {
+                const float oG = pair_oG(p2, rb.y);
+                if (!done && p2 <= 0.f && oG >= kAlphaMin) {
+                    const float al = fminf(kAlphaMax, oG);
                     const float tt = next_T(T, al);
                     if (tt < kTMin) {
                         done = true;

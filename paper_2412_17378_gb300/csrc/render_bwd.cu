@@ -85,10 +85,10 @@ __device__ __forceinline__ bool pair_backward(const Rec &r, const PairX &x, floa
                                               PairSums &a) {
     float dy;
     const float p2 = pair_power2_y(x, r.a.y, r.b.x, pyf, dy);
-    const float oG = __fmul_rn(r.b.y, ex2_approx(p2));
-    const float al = fminf(kAlphaMax, oG);
-    const bool valid = active && p2 <= 0.f && al >= kAlphaMin;
+    const float oG = pair_oG(p2, r.b.y);
+    const bool valid = active && p2 <= 0.f && oG >= kAlphaMin;
     if (valid) {
+        const float al = fminf(kAlphaMax, oG);
         const float om = 1.f - al;
         const float io = rcp_approx(om);  // om in [0.01, 1]
         s.T = s.T * io;                   // T_i

@@ -20,7 +20,7 @@
 //                          walking the tile's list through a warp-private shared memory
 //                          window of 32 records.
 //
-// All evaluate each (pixel, entry) pair with the same code (pair_power2 / pair_alpha), so
+// All evaluate each (pixel, entry) pair with the same code (pair_power2 / pair_oG), so
 // their skip decisions agree bit for bit, and the pixel-wise kernels' stop decisions too;
 // the Gaussian-wise kernel's transmittance product is reassociated (see next_T).
 // Results of all kernels equal the sequential rule of Algorithm 5 up to float32
@@ -111,10 +111,11 @@ __global__ void __launch_bounds__(1024) k_forward_static(FwdArgs a) {
         for (int k = 0; !done && k < cnt; ++k) {
             const float4 ra = srec[k].a;
             const float4 rb = srec[k].b;
-            float dx, dy, G;
+            float dx, dy;
             const float p2 = pair_power2(ra, rb.x, pxf, pyf, dx, dy);
-            const float al = pair_alpha(p2, rb.y, G);
-            if (p2 > 0.f || al < kAlphaMin) continue;
+            const float oG = pair_oG(p2, rb.y);
+            if (!(p2 <= 0.f && oG >= kAlphaMin)) continue;
+            const float al = fminf(kAlphaMax, oG);
             const float tt = next_T(T, al);
             if (tt < kTMin) {
                 done = true;
@@ -234,10 +235,11 @@ __device__ __forceinline__ void pixel_item(const FwdArgs &a, int tile, int sub, 
             const PairX px2 = pair_x(ra, pxf);  // shared by the lane's pixels (same column)
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                float dy, G;
+                float dy;
                 const float p2 = pair_power2_y(px2, ra.y, rb.x, pyf[q], dy);
-                const float al = pair_alpha(p2, rb.y, G);
-                if (!done[q] && p2 <= 0.f && al >= kAlphaMin) {
+                const float oG = pair_oG(p2, rb.y);
+                if (!done[q] && p2 <= 0.f && oG >= kAlphaMin) {
+                    const float al = fminf(kAlphaMax, oG);
                     const float tt = next_T(T[q], al);
                     if (tt < kTMin) {
                         done[q] = true;
@@ -381,10 +383,11 @@ __device__ __forceinline__ void gw_walk(const FwdArgs &a, uint32_t e0, uint32_t 
             const Rec r = a.recs[g];
 #pragma unroll
             for (int p = 0; p < PPL; ++p) {
-                float dx, dy, G;
+                float dx, dy;
                 const float p2 = pair_power2(r.a, r.b.x, pxf[p], pyf[p], dx, dy);
-                const float al = pair_alpha(p2, r.b.y, G);
-                if (live[p] && p2 <= 0.f && al >= kAlphaMin) {
+                const float oG = pair_oG(p2, r.b.y);
+                if (live[p] && p2 <= 0.f && oG >= kAlphaMin) {
+                    const float al = fminf(kAlphaMax, oG);
                     const float w = al * Tl[p];
                     c0[p] += w * r.c.x;
                     c1[p] += w * r.c.y;
@@ -433,10 +436,11 @@ __device__ __forceinline__ void gw_walk(const FwdArgs &a, uint32_t e0, uint32_t 
                     const uint32_t g = idx_s[m + m / kGwChunk];
                     if ((long long)g >= a.N) continue;  // raised above
                     const Rec r = a.recs[g];
-                    float dx, dy, G;
+                    float dx, dy;
                     const float p2 = pair_power2(r.a, r.b.x, pxf[p], pyf[p], dx, dy);
-                    const float al = pair_alpha(p2, r.b.y, G);
-                    if (p2 > 0.f || al < kAlphaMin) continue;
+                    const float oG = pair_oG(p2, r.b.y);
+                    if (!(p2 <= 0.f && oG >= kAlphaMin)) continue;
+                    const float al = fminf(kAlphaMax, oG);
                     const float tt = next_T(T, al);
                     if (tt < kTMin) {
                         st = (int)(j - list0 + 1u);
