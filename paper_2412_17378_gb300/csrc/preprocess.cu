@@ -21,12 +21,17 @@ struct CamTable {
 // Tile rectangle of a Gaussian: x in [floor((u-r)/tw), floor((u+(r+tw-1))/tw)), clamped.
 // Float32 with one IEEE rounding per operation (no contraction), the same operations the
 // binning kernel and the host-side checks use.
+// For a power-of-two tile side the quotient is the product by its exact reciprocal.
+__device__ __forceinline__ float tile_quot(float a, int t) {
+    return (t & (t - 1)) == 0 ? __fmul_rn(a, 1.f / (float)t) : __fdiv_rn(a, (float)t);
+}
+
 __device__ __forceinline__ void tile_rect(float u, float v, int r, int tw, int th, int tx, int ty, int &x0,
                                           int &x1, int &y0, int &y1) {
-    x0 = (int)floorf(__fdiv_rn(__fsub_rn(u, (float)r), (float)tw));
-    x1 = (int)floorf(__fdiv_rn(__fadd_rn(u, (float)(r + tw - 1)), (float)tw));
-    y0 = (int)floorf(__fdiv_rn(__fsub_rn(v, (float)r), (float)th));
-    y1 = (int)floorf(__fdiv_rn(__fadd_rn(v, (float)(r + th - 1)), (float)th));
+    x0 = (int)floorf(tile_quot(__fsub_rn(u, (float)r), tw));
+    x1 = (int)floorf(tile_quot(__fadd_rn(u, (float)(r + tw - 1)), tw));
+    y0 = (int)floorf(tile_quot(__fsub_rn(v, (float)r), th));
+    y1 = (int)floorf(tile_quot(__fadd_rn(v, (float)(r + th - 1)), th));
     x0 = min(max(x0, 0), tx);
     x1 = min(max(x1, 0), tx);
     y0 = min(max(y0, 0), ty);
@@ -49,16 +54,10 @@ struct Proj {
     float c00, c01, c11, det;      // 2D covariance (+ low-pass) and its determinant
 };
 
-// Returns false when the Gaussian is culled (z <= near or det <= 0); tz is always set.
-__device__ __forceinline__ bool project(const CamDev &cam, const float *__restrict__ means3D,
-                                        const float *__restrict__ log_scales, const float *__restrict__ quats,
-                                        long long g, Proj &o) {
-    const float px = means3D[3 * g], py = means3D[3 * g + 1], pz = means3D[3 * g + 2];
-    const float *V = cam.V;
-    o.tx = V[0] * px + V[1] * py + V[2] * pz + V[3];
-    o.ty = V[4] * px + V[5] * py + V[6] * pz + V[7];
-    o.tz = V[8] * px + V[9] * py + V[10] * pz + V[11];
-    if (!(o.tz > cam.near_plane)) return false;
+// The view-independent part of a Gaussian's projection: the normalised quaternion, R, the
+// scales and M = R S (computed once per Gaussian, then shared by its views).
+__device__ __forceinline__ void gauss_frame(const float *__restrict__ log_scales, const float *__restrict__ quats,
+                                            long long g, Proj &o) {
     // R from the normalised quaternion (w, x, y, z)
     float qw = quats[4 * g], qx = quats[4 * g + 1], qy = quats[4 * g + 2], qz = quats[4 * g + 3];
     o.qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
@@ -75,6 +74,16 @@ __device__ __forceinline__ bool project(const CamDev &cam, const float *__restri
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int k = 0; k < 3; ++k) o.M[r][k] = o.R[r][k] * o.s[k];
+}
+
+// The projection of a Gaussian with centre p (world space) and frame o (gauss_frame) into one
+// view.  Returns false when the Gaussian is culled (z <= near or det <= 0); tz is always set.
+__device__ __forceinline__ bool project(const CamDev &cam, float px, float py, float pz, Proj &o) {
+    const float *V = cam.V;
+    o.tx = V[0] * px + V[1] * py + V[2] * pz + V[3];
+    o.ty = V[4] * px + V[5] * py + V[6] * pz + V[7];
+    o.tz = V[8] * px + V[9] * py + V[10] * pz + V[11];
+    if (!(o.tz > cam.near_plane)) return false;
     // Jacobian of the pinhole map at the tangent-clamped point
     o.iz = 1.f / o.tz;
     const float ux = o.tx * o.iz, uy = o.ty * o.iz;
@@ -140,11 +149,14 @@ __global__ void __launch_bounds__(256) k_preprocess(long long N, const float *__
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N) return;
     const float op = opacities[g];
+    const float px = means3D[3 * g], py = means3D[3 * g + 1], pz = means3D[3 * g + 2];
+    Proj frame;
+    gauss_frame(log_scales, quats, g, frame);
     for (int view = 0; view < ct.V; ++view) {
         const long long rec = (long long)view * N + g;
         const CamDev &cam = ct.cam[view];
-        Proj o;
-        const bool ok = project(cam, means3D, log_scales, quats, g, o);
+        Proj o = frame;
+        const bool ok = project(cam, px, py, pz, o);
         float2 m2 = make_float2(0.f, 0.f);
         float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
         int radius = 0;
@@ -197,12 +209,15 @@ __global__ void __launch_bounds__(256) k_preprocess_backward(long long N, const 
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N) return;
     float gp[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+    const float px = means3D[3 * g], py = means3D[3 * g + 1], pz = means3D[3 * g + 2];
+    Proj frame;
+    gauss_frame(log_scales, quats, g, frame);
     for (int view = 0; view < ct.V; ++view) {
         const long long rec = (long long)view * N + g;
         if (radii[rec] <= 0) continue;
         const CamDev &cam = ct.cam[view];
-        Proj o;
-        if (!project(cam, means3D, log_scales, quats, g, o)) continue;
+        Proj o = frame;
+        if (!project(cam, px, py, pz, o)) continue;
         const float *V = cam.V;
         const float2 gm = dL_dmeans2D[rec];
         const float ga = dL_dconic[3 * rec], gb = dL_dconic[3 * rec + 1], gc = dL_dconic[3 * rec + 2];
