@@ -687,6 +687,7 @@ def main_views(args, scene, rank, world, local):
         img_bytes = sum(3 * c["W"] * c["H"] * 4 for c in cams)
         d2h = img_bytes + 4
         copy_s = torch.cuda.Stream(device=dev)
+        copy_out = torch.cuda.Stream(device=dev)  # the pipelined steps' image read-back
         imgs_h = [[torch.empty((3, c["H"], c["W"]), pin_memory=True) for c in cams] for _ in range(2)]
         loss_h = torch.empty(1, pin_memory=True)
         loss_hp = torch.empty(2, pin_memory=True)  # the pipelined steps' losses, by step parity
@@ -721,31 +722,36 @@ def main_views(args, scene, rank, world, local):
         # (2) pipelined, as a prefetching loader runs: two device input sets and two image
         # output sets; step i computes from input set i % 2 (filled while step i - 1 ran) into
         # output set i % 2, while a second stream copies step i + 1's inputs into the other
-        # input set and step i - 1's images (the other output set) to the host.  A set is
-        # overwritten only after the step that read it has ended (the steps run in order on
-        # one stream, and a step's graph ends after its second-stream copies).
+        # input set and a third copies step i - 1's images (the other output set) to the host
+        # (the two directions at once).  A set is overwritten only after the step that read it
+        # has ended (the steps run in order on one stream, and a step's graph ends after its
+        # copies).
         bufs = [(d, targets), ({k: torch.empty_like(v) for k, v in d.items()}, [torch.empty_like(t) for t in targets])]
         osets = ["", "_b"]
         step(oset="_b")  # allocates the second output set
         side.synchronize()
-        pev = [(torch.cuda.Event(), torch.cuda.Event()) for _ in range(2)]
+        pev = [(torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()) for _ in range(2)]
 
         def pipelined_body(i):
             k = i % 2
-            ev_f, ev_j = pev[k]
+            ev_f, ev_j, ev_o = pev[k]
             ev_f.record(side)
             copy_s.wait_event(ev_f)
+            copy_out.wait_event(ev_f)
             with torch.cuda.stream(copy_s):
                 nd, nt = bufs[1 - k]
                 for key in host:
                     nd[key].copy_(host[key], non_blocking=True)
                 for t, th in zip(nt, targets_h):
                     t.copy_(th, non_blocking=True)
-                images_to_host(imgs_h[1 - k], osets[1 - k])  # the previous step's images
                 ev_j.record(copy_s)
+            with torch.cuda.stream(copy_out):
+                images_to_host(imgs_h[1 - k], osets[1 - k])  # the previous step's images
+                ev_o.record(copy_out)
             step(inp=bufs[k], oset=osets[k])
             loss_to_host(loss_hp[k:k + 1], osets[k])
             side.wait_event(ev_j)
+            side.wait_event(ev_o)
 
         def capture(body, n):
             """n CUDA graphs of body(0..n-1) (torch.cuda.graph: its private memory pool keeps
@@ -815,7 +821,7 @@ def main_views(args, scene, rank, world, local):
         del g_serial, g_pipe
         e2e_how = ("two CUDA graphs alternating over two device input sets and two image output sets: each step "
                    "copies the next step's inputs in (pinned host memory, second stream) and the previous step's "
-                   "images out while it computes, then copies its loss out; the host reads step i's loss after "
+                   "images out (third stream) while it computes, then copies its loss out; the host reads step i's loss after "
                    "launching step i + 1" if err_pipe is None else "eager, pipelined: " + err_pipe)
         serial_how = ("one CUDA graph per step: H2D copies (colours and targets on a second stream, overlapping "
                       "projection and binning), the step, the D2H copies of its images and loss, host wait"
