@@ -304,7 +304,8 @@ cudaError_t launch_preprocess_backward(long long N, int V, const float *means3D,
                                        const float *quats, const bgs_camera *cams, const int *radii,
                                        const float *dL_dmeans2D, const float *dL_dconic, const float *dL_ddepths,
                                        float *dL_dmeans3D, float *dL_dlog_scales, float *dL_dquats, cudaStream_t s);
-cudaError_t launch_depth_keys(long long R, const float *depths, uint32_t *keys, uint32_t *idx, cudaStream_t s);
+// idx[i] = i for i in [lo, hi)
+cudaError_t launch_iota(long long lo, long long hi, uint32_t *idx, cudaStream_t s);
 
 cudaError_t launch_touched(long long N, const float *means2D, const int *radii, const float *depths, int W, int H,
                            int tile_w, int tile_h, uint32_t *touched, uint32_t *dkey, uint32_t *idx, cudaStream_t s);
@@ -332,7 +333,8 @@ cudaError_t launch_bin_count(long long N, int G, int b_lo, int b_hi, const uint3
                              const int *radii, int W, int H, int tw, int th, uint32_t *Hm, uint4 *rect, uint32_t *masks,
                              int W32, const int *skipP, cudaStream_t s);
 // the tiles whose credits over blocks [0, B1) certify that every pixel stopped, as the
-// exclusive 2D prefix P [(ty + 1) x (tx + 1)] of their indicator
+// exclusive 2D prefix P [(ty + 1) x (tx + 1)] of their indicator; P's buffer holds tx ty more
+// words behind the prefix (the per-tile sums)
 cudaError_t launch_bin_stopped(int B1, int tx, int ty, const uint16_t *D, int *P, cudaStream_t s);
 // per tile column: exclusive prefix of H over the blocks and the total; with the credits D
 // (nullable) the column is cut after the block b_sat[t] at which they certify that every

@@ -765,7 +765,7 @@ int bin_mask_groups(int tx, int ty) { return ((tx + kCbW - 1) / kCbW) * ((ty + k
 // never lowering it: launches captured in a CUDA graph keep their own (possibly larger)
 // size, and a replay of them needs the limit the capture saw.  slot: one per kernel.
 static cudaError_t raise_dyn_smem(const void *kernel, int slot, size_t bytes) {
-    constexpr int kSlots = 3, kDevices = 64;
+    constexpr int kSlots = 4, kDevices = 64;
     static std::mutex mu;
     static int limit[kSlots][kDevices] = {};
     int dev = 0;
@@ -795,35 +795,41 @@ cudaError_t launch_bin_count(long long N, int G, int b_lo, int b_hi, const uint3
     return cudaGetLastError();
 }
 
-// Tiles whose credits over blocks [0, B1) reach thr (every pixel stopped there): their
-// exclusive 2D prefix P[y][x] = #stopped tiles (x' < x, y' < y), (ty + 1) x (tx + 1).
-__global__ void k_bin_stopped(int B1, int tx, int ty, const uint16_t *__restrict__ D, uint32_t thr,
-                              int *__restrict__ P) {
-    const int T = tx * ty;
+// Per tile, the credits of blocks [0, B1): a thread per (tile, chunk of `chunk` blocks) adds
+// its chunk's sum, capped at thr (only whether the total reaches thr matters; the cap keeps
+// the total far below 2^32), to S[t].
+__global__ void k_bin_stopped(int B1, int T, int chunk, const uint16_t *__restrict__ D, uint32_t thr,
+                              uint32_t *__restrict__ S) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
+    const int b0 = (int)blockIdx.y * chunk, b1 = min(B1, b0 + chunk);
     uint32_t sum = 0;
-    for (int b = 0; b < B1; ++b) sum = min(sum + (uint32_t)D[(size_t)b * T + t], 0x7fffffffu);
-    const int x = t % tx, y = t / tx;
-    P[(y + 1) * (tx + 1) + x + 1] = sum >= thr ? 1 : 0;
-    if (x == 0) P[(y + 1) * (tx + 1)] = 0;
-    if (y == 0) P[x + 1] = 0;
-    if (t == 0) P[0] = 0;
+    for (int b = b0; b < b1; ++b) sum += (uint32_t)D[(size_t)b * T + t];
+    if (sum) atomicAdd(&S[t], min(sum, thr));
 }
 
-// In place: the indicator rows 1..ty, columns 1..tx of P -> their 2D inclusive prefix (one block).
-__global__ void __launch_bounds__(1024) k_bin_prefix2d(int tx, int ty, int *__restrict__ P) {
-    const int w1 = tx + 1, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+// P [(ty + 1) x (tx + 1)]: the exclusive 2D prefix of the stopped tiles' indicator (S[t] >=
+// thr), P[y][x] = #stopped tiles (x' < x, y' < y), built in shared memory by one block.
+__global__ void __launch_bounds__(1024) k_bin_prefix2d(int tx, int ty, const uint32_t *__restrict__ S, uint32_t thr,
+                                                       int *__restrict__ P) {
+    extern __shared__ int p_s[];
+    const int w1 = tx + 1, n = (tx + 1) * (ty + 1), lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int y = i / w1, x = i - y * w1;
+        p_s[i] = (x > 0 && y > 0 && S[(y - 1) * tx + (x - 1)] >= thr) ? 1 : 0;
+    }
+    __syncthreads();
     for (int y = 1 + warp; y <= ty; y += nwarps) {  // along x, a warp per row
         int carry = 0;
         for (int xb = 1; xb <= tx; xb += 32) {
             const int x = xb + lane;
-            int v = x <= tx ? P[y * w1 + x] : 0;
+            int v = x <= tx ? p_s[y * w1 + x] : 0;
             for (int o = 1; o < 32; o <<= 1) {
                 const int u = __shfl_up_sync(0xffffffffu, v, o);
                 if (lane >= o) v += u;
             }
-            if (x <= tx) P[y * w1 + x] = v + carry;
+            if (x <= tx) p_s[y * w1 + x] = v + carry;
             carry += __shfl_sync(0xffffffffu, v, 31);
         }
     }
@@ -831,18 +837,31 @@ __global__ void __launch_bounds__(1024) k_bin_prefix2d(int tx, int ty, int *__re
     for (int x = 1 + (int)threadIdx.x; x <= tx; x += blockDim.x) {  // along y, a thread per column
         int run = 0;
         for (int y = 1; y <= ty; ++y) {
-            run += P[y * w1 + x];
-            P[y * w1 + x] = run;
+            run += p_s[y * w1 + x];
+            p_s[y * w1 + x] = run;
         }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) P[i] = p_s[i];
 }
+
+size_t bin_stopped_smem(int tx, int ty) { return sizeof(int) * (size_t)(tx + 1) * (ty + 1); }
 
 cudaError_t launch_bin_stopped(int B1, int tx, int ty, const uint16_t *D, int *P, cudaStream_t s) {
     const int T = tx * ty;
-    k_bin_stopped<<<std::max(1, (T + 255) / 256), 256, 0, s>>>(B1, tx, ty, D, kCreditThr, P);
-    cudaError_t e = cudaGetLastError();
+    // the per-tile sums live behind the prefix in P's buffer
+    uint32_t *S = reinterpret_cast<uint32_t *>(P + (size_t)(tx + 1) * (ty + 1));
+    cudaError_t e = cudaMemsetAsync(S, 0, sizeof(uint32_t) * (size_t)T, s);
     if (e != cudaSuccess) return e;
-    k_bin_prefix2d<<<1, 1024, 0, s>>>(tx, ty, P);
+    if (B1 > 0) {
+        const int chunk = std::max(32, (B1 + 65534) / 65535);
+        const dim3 grid((unsigned)std::max(1, (T + 255) / 256), (unsigned)((B1 + chunk - 1) / chunk));
+        k_bin_stopped<<<grid, 256, 0, s>>>(B1, T, chunk, D, kCreditThr, S);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const size_t smem = bin_stopped_smem(tx, ty);
+    if (smem > 48 * 1024 && (e = raise_dyn_smem((const void *)k_bin_prefix2d, 3, smem)) != cudaSuccess) return e;
+    k_bin_prefix2d<<<1, 1024, smem, s>>>(tx, ty, S, kCreditThr, P);
     return cudaGetLastError();
 }
 

@@ -98,7 +98,8 @@ struct bgs_plan {
     Buf tile_cost;                  // per-tile largest n_contrib, from the last forward (the
                                     // backward's work-list order); valid for cost_key's tiles
     // batched binning: depth keys of every view
-    Buf vkey, vkey_sorted;
+    Buf vkey_sorted;
+    long long iota_n = 0;  // gidx[0, iota_n) holds 0, 1, ... (the batched depth sort's values)
     // the views' depth sorts run concurrently on kSortStreams streams forked from the caller's
     cudaStream_t sort_stream[kSortStreams] = {};
     cudaEvent_t sort_fork = nullptr, sort_join[kSortStreams] = {};
@@ -150,6 +151,7 @@ int ensure(bgs_plan *p, Buf &b, size_t bytes, cudaStream_t s, const char *what) 
                                       "call bgs_plan_reserve before capture", what, bytes);
     if (&b == &p->recs) p->rec_valid = false;
     if (&b == &p->items) p->wl_valid = false;
+    if (&b == &p->gidx) p->iota_n = 0;
     if (b.p) {
         cudaError_t e = cudaFree(b.p);
         b.p = nullptr;
@@ -416,7 +418,7 @@ int bgs_plan_destroy(bgs_plan *p) {
         for (Buf *b : sb)
             if (b->p) cudaFree(b->p);
     }
-    Buf *bufs[] = {&p->gw_exoff, &p->gw_sum, &p->gw_tile, &p->tile_cost, &p->vkey, &p->vkey_sorted, &p->touched, &p->touched_sorted, &p->dkey,
+    Buf *bufs[] = {&p->gw_exoff, &p->gw_sum, &p->gw_tile, &p->tile_cost, &p->vkey_sorted, &p->touched, &p->touched_sorted, &p->dkey,
                    &p->dkey_sorted, &p->gidx, &p->order, &p->offsets,
                    &p->keys_in, &p->keys_out, &p->vals_in, &p->cub_tmp, &p->recs,
                    &p->tile_idx, &p->items, &p->warp_items,
@@ -738,7 +740,7 @@ int bin_view_a(bgs_plan *p, int slot, int v, long long n, const uint32_t *order,
     uint32_t *masks = (uint32_t *)sl.mask.p;
     int *P = nullptr;
     if (passes > 1) {
-        BGS_TRY(ensure(p, sl.stopped, sizeof(int) * (bv.tiles_x + 1) * (bv.tiles_y + 1), s, "bin_stopped"));
+        BGS_TRY(ensure(p, sl.stopped, sizeof(int) * ((bv.tiles_x + 1) * (bv.tiles_y + 1) + bv.T), s, "bin_stopped"));
         P = (int *)sl.stopped.p;
     }
     for (int k = 0; k < passes; ++k) {
@@ -1284,13 +1286,21 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
     if (R > 0) {
         // depth order of every view's records: one 32-bit key sort per view slice (a single
         // sort of 64-bit (view, depth) keys over all V N records was measured slower)
-        BGS_TRY(ensure(p, p->vkey, 4 * R, s, "dkey"));
         BGS_TRY(ensure(p, p->vkey_sorted, 4 * R, s, "dkey_sorted"));
         BGS_TRY(ensure(p, p->gidx, 4 * R, s, "gidx"));
         BGS_TRY(ensure(p, p->order, 4 * R, s, "order"));
-        uint32_t *k0 = (uint32_t *)p->vkey.p, *k1 = (uint32_t *)p->vkey_sorted.p;
+        // keys: the depths' float32 bit patterns (the order both sides sort on); values: record
+        // indices, kept in gidx from one call to the next (a call under stream capture records
+        // the fill without counting it as done, so that its graph fills them on every replay)
+        const uint32_t *k0 = reinterpret_cast<const uint32_t *>(depths);
+        uint32_t *k1 = (uint32_t *)p->vkey_sorted.p;
         uint32_t *gidx = (uint32_t *)p->gidx.p, *order = (uint32_t *)p->order.p;
-        BGS_CUDA(bgs::launch_depth_keys(R, depths, k0, gidx, s), "depth keys");
+        if (p->iota_n < R) {
+            BGS_CUDA(bgs::launch_iota(p->iota_n, R, gidx, s), "record indices");
+            p->host_launches += 1;
+            cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusNone) p->iota_n = R;
+        }
         size_t tmp = 0;
         BGS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, k0, k1, gidx, order, (int64_t)N, 0, 32, s),
                  "view depth sort (size)");
@@ -1313,7 +1323,6 @@ int bgs_bin_and_sort_batched(bgs_plan *p, int32_t V, const bgs_view *views, int6
                                                      (int64_t)N, 0, 32, stream_of(i)),
                      "view depth sort");
         }
-        p->host_launches += 1;
         // then each view's binning on its sort's stream (view v's records are positions
         // [v N, (v+1) N) of the order; views v, v + NS, ... share the stream's buffer set):
         // counts, then -- once the counts of the views before it are stored -- its lists

@@ -352,19 +352,16 @@ cudaError_t launch_preprocess_backward(long long N, int V, const float *means3D,
     return cudaGetLastError();
 }
 
-// Depth sort keys of a batched binning: float bits of every record's depth, value = record
-// index (each view's slice [v N, (v + 1) N) is then sorted on its own).
-__global__ void __launch_bounds__(256) k_depth_keys(long long R, const float *__restrict__ depths,
-                                                    uint32_t *__restrict__ keys, uint32_t *__restrict__ idx) {
-    const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (rec >= R) return;
-    keys[rec] = __float_as_uint(depths[rec]);
-    idx[rec] = (uint32_t)rec;
+// idx[i] = i for i in [lo, hi): the values of the batched depth sort (its keys are the depths'
+// float32 bit patterns themselves), filled once and kept by the plan.
+__global__ void __launch_bounds__(256) k_iota(long long lo, long long hi, uint32_t *__restrict__ idx) {
+    const long long i = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < hi) idx[i] = (uint32_t)i;
 }
 
-cudaError_t launch_depth_keys(long long R, const float *depths, uint32_t *keys, uint32_t *idx, cudaStream_t s) {
-    if (R == 0) return cudaSuccess;
-    k_depth_keys<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(R, depths, keys, idx);
+cudaError_t launch_iota(long long lo, long long hi, uint32_t *idx, cudaStream_t s) {
+    if (hi <= lo) return cudaSuccess;
+    k_iota<<<(unsigned)((hi - lo + 255) / 256), 256, 0, s>>>(lo, hi, idx);
     return cudaGetLastError();
 }
 
@@ -533,20 +530,24 @@ template cudaError_t launch_ranges<uint32_t>(const uint32_t *, long long, uint2 
 
 // ---- render input packing ------------------------------------------------------------------
 // recs[i] packs record i; the colour comes from Gaussian i % n_colors (views share colours).
-__global__ void __launch_bounds__(256) k_pack(long long N, const float *__restrict__ means2D,
+// A thread per record on a grid of (colour rows, views): record v n_colors + c of view
+// blockIdx.y = v takes colour row c, with no division.
+__global__ void __launch_bounds__(256) k_pack(long long n_colors, const float *__restrict__ means2D,
                                               const float *__restrict__ conic_opacity,
-                                              const float *__restrict__ colors, long long n_colors,
-                                              const float *__restrict__ depths, Rec *__restrict__ recs) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const long long c = (n_colors == N) ? i : i % n_colors;
+                                              const float *__restrict__ colors, const float *__restrict__ depths,
+                                              Rec *__restrict__ recs) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_colors) return;
+    const long long i = (long long)blockIdx.y * n_colors + c;
     recs[i] = make_rec(means2D, conic_opacity, colors, depths, (unsigned int)i, (unsigned int)c);
 }
 
 cudaError_t launch_pack(long long N, const float *means2D, const float *conic_opacity, const float *colors,
                         long long n_colors, const float *depths, Rec *recs, cudaStream_t s) {
     if (N == 0) return cudaSuccess;
-    k_pack<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, means2D, conic_opacity, colors, n_colors, depths, recs);
+    if (n_colors <= 0 || N % n_colors != 0 || N / n_colors > 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((n_colors + 255) / 256), (unsigned)(N / n_colors));
+    k_pack<<<grid, 256, 0, s>>>(n_colors, means2D, conic_opacity, colors, depths, recs);
     return cudaGetLastError();
 }
 
