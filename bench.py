@@ -338,11 +338,14 @@ def load_peaks():
 # ----------------------------------------------------------------------------- oracle leg
 
 _ORACLE_SETUP = {}
+_ORACLE_SAMPLES = {}
 
 
 def oracle_setup(scene):
     """Oracle projection of every view of the frame (done once, outside any timed region):
-    per view the float32 render inputs the oracle consumes and the view's tile count."""
+    per view the float32 render inputs (for the oracle's binning), the same values as float64
+    arrays (the form its render takes them in, so that no timed call converts the whole
+    Gaussian set), the depth order and the view's tile count."""
     key = id(scene)
     if key not in _ORACLE_SETUP:
         import oracle
@@ -353,65 +356,84 @@ def oracle_setup(scene):
             m2, co, dp = (pp[k].astype(np.float32) for k in ("means2D", "conic_opacity", "depth"))
             W, H = cam["W"], cam["H"]
             views.append(dict(m2=m2, co=co, dp=dp, radius=pp["radius"], W=W, H=H,
+                              m2d=m2.astype(np.float64), cod=co.astype(np.float64), dpd=dp.astype(np.float64),
                               T=((W + 15) // 16) * ((H + 15) // 16), order=oracle.depth_order(pp["radius"], dp)))
             del pp
-        _ORACLE_SETUP[key] = views
+        _ORACLE_SETUP[key] = dict(views=views, colors=np.ascontiguousarray(g["colors"], np.float64))
     return _ORACLE_SETUP[key]
 
 
-def oracle_sample_run(scene, budget_s: float, rng_seed: int = 0, threads: int = 0):
+def oracle_sample_run(scene, budget_s: float, rng_seed: int = 0, threads: int = 0, n_tiles: int = 0):
     """Times the FP64 oracle's render forward + backward on a bounded sample of the frame's
     tiles (chosen uniformly at random over the tiles of all views), sized to about
-    ``budget_s`` seconds of CPU work, on all host cores (threads = 0) or the given number of
-    threads.  Only the render forward + backward is timed; the sampled tiles' lists are
-    built beforehand by the oracle's own binning (``bin_tiles_subset``).
-    Returns (pairs/s, cores, description, measured pairs, seconds)."""
+    ``budget_s`` seconds of CPU work (or of ``n_tiles`` tiles when given), on all host cores
+    (threads = 0) or the given number of threads.  Only the render forward + backward is
+    timed; the sampled tiles' lists are built beforehand by the oracle's own binning
+    (``bin_tiles_subset``).  Returns (pairs/s, cores, description, measured pairs, seconds,
+    tiles sampled)."""
     import oracle
     if threads:
         all_threads = oracle.num_threads()
         oracle.set_threads(threads)
         try:
-            return oracle_sample_run(scene, budget_s, rng_seed)
+            return oracle_sample_run(scene, budget_s, rng_seed, n_tiles=n_tiles)
         finally:
             oracle.set_threads(all_threads)
-    views = oracle_setup(scene)
-    cl = scene["gaussians"]["colors"]
+    setup = oracle_setup(scene)
+    views, cl = setup["views"], setup["colors"]
     base = np.cumsum([0] + [v["T"] for v in views])
     T = int(base[-1])
     order = np.random.default_rng(rng_seed).permutation(T)
 
+    def sample(tiles_global):
+        """Per view: the sampled tiles, their lists (the oracle's binning) and pixels; built
+        once per sample and kept (untimed)."""
+        ck = (id(scene), rng_seed, tiles_global.size)
+        if ck not in _ORACLE_SAMPLES:
+            per = []
+            for vi, v in enumerate(views):
+                sel = np.sort(tiles_global[(tiles_global >= base[vi]) & (tiles_global < base[vi + 1])] - base[vi])
+                if sel.size == 0:
+                    continue
+                W, H = v["W"], v["H"]
+                tx = (W + 15) // 16
+                pl, rg = oracle.bin_tiles_subset(v["m2"], v["radius"], v["dp"], W, H, sel, order=v["order"])
+                pix = []
+                for t in sel:
+                    x0, y0 = (t % tx) * 16, (t // tx) * 16
+                    ys, xs = np.mgrid[y0:min(y0 + 16, H), x0:min(x0 + 16, W)]
+                    pix.append((ys * W + xs).ravel())
+                per.append((vi, sel, pl, rg, np.concatenate(pix)))
+            _ORACLE_SAMPLES[ck] = per
+        return _ORACLE_SAMPLES[ck]
+
     def run(tiles_global):
         pairs, dt = 0, 0.0
-        for vi, v in enumerate(views):
-            sel = np.sort(tiles_global[(tiles_global >= base[vi]) & (tiles_global < base[vi + 1])] - base[vi])
-            if sel.size == 0:
-                continue
+        for vi, sel, pl, rg, pix in sample(tiles_global):
+            v = views[vi]
             W, H = v["W"], v["H"]
-            tx = (W + 15) // 16
-            pl, rg = oracle.bin_tiles_subset(v["m2"], v["radius"], v["dp"], W, H, sel, order=v["order"])
-            pix = []
-            for t in sel:
-                x0, y0 = (t % tx) * 16, (t // tx) * 16
-                ys, xs = np.mgrid[y0:min(y0 + 16, H), x0:min(x0 + 16, W)]
-                pix.append((ys * W + xs).ravel())
-            pix = np.concatenate(pix)
             t0 = time.perf_counter()
-            out = oracle.render(v["m2"], v["co"], cl, v["dp"], pl, rg, W, H, pixels=pix)
+            out = oracle.render(v["m2d"], v["cod"], cl, v["dpd"], pl, rg, W, H, pixels=pix)
             gC = np.zeros((3, H, W))
             gC.reshape(3, -1)[:, pix] = out["color"]
-            oracle.render_backward(v["m2"], v["co"], cl, v["dp"], pl, rg, W, H, gC, tiles=sel.astype(np.int64))
+            oracle.render_backward(v["m2d"], v["cod"], cl, v["dpd"], pl, rg, W, H, gC, tiles=sel.astype(np.int64))
             dt += time.perf_counter() - t0
             pairs += int(out["n_eval"].sum())
         return pairs, dt
 
-    n = 16
-    pairs, dt = run(order[:n])
-    while dt < budget_s / 4 and n < T:
-        n = min(T, n * 4)
+    if n_tiles:
+        n = min(T, n_tiles)
         pairs, dt = run(order[:n])
+    else:
+        n = 16
+        pairs, dt = run(order[:n])
+        while dt < budget_s / 4 and n < T:
+            # grow by 4x at least, or straight to about half the budget at the rate measured
+            n = min(T, max(4 * n, int(n * budget_s / (2.0 * max(dt, 1e-3)))))
+            pairs, dt = run(order[:n])
     where = f"{len(views)} views" if len(views) > 1 else "the frame"
     desc = f"{n} random 16x16 tiles of {T} ({100.0 * n / T:.1f}% of {where}), render fwd+bwd"
-    return pairs / dt, oracle.num_threads(), desc, pairs, dt
+    return pairs / dt, oracle.num_threads(), desc, pairs, dt, n
 
 
 def reference_arm(args):
@@ -423,12 +445,16 @@ def reference_arm(args):
     from paper_2412_17378_gb300 import scenes
     scene = scenes.scene_config(args.config, args.scale)
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        oracle_sample_run(scene, per_step / 4)
+    # the first warm-up step sizes a random tile sample to about per_step seconds of oracle
+    # work (its lists are built once, untimed); every step renders that sample forward and
+    # backward
+    n_tiles = 0
+    for k in range(max(1, args.warmup)):
+        n_tiles = oracle_sample_run(scene, per_step, n_tiles=n_tiles)[5]
     t_all, p_all = 0.0, 0
     rate = cores = desc = None
     for k in range(args.steps):
-        rate, cores, desc, pairs, dt = oracle_sample_run(scene, per_step, rng_seed=k)
+        rate, cores, desc, pairs, dt, _ = oracle_sample_run(scene, per_step, n_tiles=n_tiles)
         t_all += dt
         p_all += pairs
     value = p_all / t_all
@@ -898,8 +924,8 @@ def main_views(args, scene, rank, world, local):
     # ---- FP64 CPU oracle on a bounded sample of every view (rank 0, one GPU) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, desc, _, _ = oracle_sample_run(scene, args.cpu_seconds)
-        rate1, _, desc1, _, _ = oracle_sample_run(scene, 2.0, threads=1)
+        rate, cores, desc, _, _, _ = oracle_sample_run(scene, args.cpu_seconds)
+        rate1, _, desc1, _, _, _ = oracle_sample_run(scene, 2.0, threads=1)
         cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc,
                "cpu_model": cpu_model(),
                "single_thread": {"value": rate1, "unit": "pairs/s", "cores": 1, "sample": desc1}}
