@@ -127,3 +127,30 @@ def test_tile_eval_histogram_on_ragged_views():
         if b != "0":
             k = int(b[2:])
             assert n == int(((expect >= 2 ** k) & (expect < 2 ** (k + 1))).sum())
+
+
+def test_oracle_sample_counts_the_full_render_pairs_of_its_tiles():
+    """The CPU baseline's sample (bench.oracle_sample_run): the evaluated pairs it times on a
+    fixed set of tiles, from the oracle's own binning of those tiles only, equal the full-frame
+    oracle render's n_eval summed over the same tiles; a second call reuses the kept sample."""
+    import numpy as np
+    import oracle
+    from paper_2412_17378_gb300 import scenes
+    sc = scenes.scene_config("cfg1", 1.0)
+    n = 24
+    r1 = bench.oracle_sample_run(sc, 0.5, n_tiles=n)
+    r2 = bench.oracle_sample_run(sc, 0.5, n_tiles=n)
+    assert r1[5] == r2[5] == n and r1[3] == r2[3] > 0 and r1[4] > 0
+    assert sum(1 for k in bench._ORACLE_SAMPLES if k[0] == id(sc)) == 1
+    # the same tiles of the full frame
+    g, cam = sc["gaussians"], sc["cameras"][0]
+    W, H = cam["W"], cam["H"]
+    pp = oracle.preprocess(g["means3D"], g["log_scales"], g["quats"], g["opacities"], cam)
+    m2, co, dp = (pp[k].astype(np.float32) for k in ("means2D", "conic_opacity", "depth"))
+    pl, rg = oracle.bin_tiles(m2, pp["radius"], dp, W, H)
+    full = oracle.render(m2, co, g["colors"], dp, pl, rg, W, H)
+    tx, T = (W + 15) // 16, ((W + 15) // 16) * ((H + 15) // 16)
+    tiles = np.random.default_rng(0).permutation(T)[:n]
+    ne = full["n_eval"].reshape(H, W)
+    expect = sum(int(ne[(t // tx) * 16:(t // tx) * 16 + 16, (t % tx) * 16:(t % tx) * 16 + 16].sum()) for t in tiles)
+    assert r1[3] == expect
